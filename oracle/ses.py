@@ -1,0 +1,303 @@
+"""Smallest Enclosing Sphere through the primal-dual meta-algorithm, FP64.
+
+Follows Sec. 4.1 (problem SES, its split into the easy set C and the hard set
+F, the dual/primal pair (dualses)/(primalses), the bounds D, the closed-form
+ORACLE of Eq. (ses_oracle), the width rho <= 3D/sqrt2 and T of Theorem 8),
+Sec. 3 (the alpha-FTP of Theorem 6, the hyperplane update of Eq. (implement),
+the primal solution of Eq. (primal_construction), the search from
+feasibility to optimisation) and Sec. 5 (per-iteration objective f^t, the
+early-exit and early-stop rules).
+
+Inputs: V is the (n, d) array of centres v_1..v_n, gamma the (n,) radii (None
+means points, gamma = 0). Row 0 is v_1, the constraint kept as the easy set C
+("the first one", Sec. 4.1); rows 1..n-1 form the product cone
+K = prod_{i>=2} Q^{d+1} of rank r = 2(n-1).
+
+Readings of the paper taken here (each is listed in the design doc):
+  * gamma-bar, the running mean of the oracle's gamma outputs, equals alpha
+    inside one alpha-FTP because the ORACLE always returns gamma = alpha.
+  * When g = sum_i w_i = 0 (always at t = 0, where p^1 = e/r) the ORACLE's
+    maximiser is not unique; u = v_1, the centre of the ball, is returned.
+  * An ORACLE value exactly 0 counts as success (Sec. 3: "non-negative").
+  * f^0, before any iterate exists, is evaluated at ubar^0 = v_1.
+"""
+
+import math
+
+import numpy as np
+
+from .eja import SQRT2, scmwu_soc, soc_inner
+
+OUT_SEPARATED = "separated"      # ORACLE value < 0: alpha < OPT (Sec. 3)
+OUT_FEASIBLE = "feasible"        # T iterations without separation (Theorem 6)
+OUT_BELOW_ALPHA = "below_alpha"  # f^t < alpha: affirmative early exit (Sec. 5)
+OUT_STALLED = "stalled"          # |f^t - f^{t-1}|/f^{t-1} < delta, patience times (Sec. 5)
+OUT_FIXED = "fixed"              # FIXED_ITERS mode ran its T iterations
+
+MODE_PRACTICAL = "practical"
+MODE_THEORY = "theory"
+MODE_FIXED = "fixed"
+
+
+def _prep(V, gamma):
+    V = np.asarray(V, dtype=np.float64)
+    if V.ndim != 2 or V.shape[0] < 2:
+        raise ValueError("SES needs an (n, d) array with n >= 2")
+    g = np.zeros(V.shape[0]) if gamma is None else np.asarray(gamma, dtype=np.float64)
+    return V, g
+
+
+# ------------------------------------------------------------- constants
+def ses_D(V, gamma=None):
+    """D = max_{i>=2} ||v_1 - v_i|| + gamma_1 + gamma_i; OPT in [D/2, D] (Sec. 4.1)."""
+    V, gm = _prep(V, gamma)
+    dist = np.sqrt(np.sum((V[1:] - V[0]) ** 2, axis=1))
+    return float(np.max(dist + gm[0] + gm[1:]))
+
+
+def ses_width(D):
+    """Width of the SES ORACLE, rho <= 3D/sqrt2 (Sec. 4.1)."""
+    return 3.0 * D / SQRT2
+
+
+def ses_rank(n):
+    """Rank r = 2(n-1) of K = prod_{i>=2} Q^{d+1} (Sec. 4.1)."""
+    return 2 * (n - 1)
+
+
+SES_R = SQRT2  # b_{d+1} after scaling the last primal constraint by sqrt2 (Sec. 4.1)
+
+
+def ses_T(D, n, eps, alpha):
+    """T = ceil(36 D^2 ln(2n-2) / (eps^2 alpha^2)) (Sec. 4.1, from Theorem 6)."""
+    return int(math.ceil(36.0 * D * D * math.log(2 * n - 2) / (eps * eps * alpha * alpha)))
+
+
+def theorem_eta(r, T):
+    """Step size eta = sqrt(ln r / T) of Theorems 6 and 7."""
+    return math.sqrt(math.log(r) / T)
+
+
+# ------------------------------------------------- one iteration, step by step
+def ses_exponent(V, gamma, ubar, alpha, k):
+    """Accumulated exponent of Eq. (implement) for the SES split.
+
+    sum_j a_j ybar_j - c = prod_{i>=2} (ubar - v_i; alpha - gamma_i)  (Eq. dualses
+    with ybar = (ubar; alpha)), scaled by -k where k = eta t / rho.
+    Returns the (n-1, d+1) array X.
+    """
+    V, gm = _prep(V, gamma)
+    ubar = np.asarray(ubar, dtype=np.float64)
+    X = np.empty((V.shape[0] - 1, V.shape[1] + 1))
+    X[:, :-1] = ubar[None, :] - V[1:]
+    X[:, -1] = alpha - gm[1:]
+    return -k * X
+
+
+def ses_weights(V, gamma, ubar, alpha, k):
+    """p^{t+1} = exp(X)/Tr(exp(X)) with X from :func:`ses_exponent` (Eq. implement).
+
+    Returns P, the (n-1, d+1) array whose row i-2 is (w_i; s_i) (Sec. 4.1).
+    """
+    P, _, _ = scmwu_soc(ses_exponent(V, gamma, ubar, alpha, k))
+    return P
+
+
+def ses_oracle(V, gamma, P, alpha):
+    """Closed-form ORACLE of Eq. (ses_oracle).
+
+    max_{u,gamma} g^T u + gamma/sqrt2 - sum v_i^T w_i - sum gamma_i s_i
+    s.t. gamma <= alpha, ||u - v_1|| <= gamma - gamma_1, with g = sum_{i>=2} w_i.
+    The optimum takes gamma = alpha and u = v_1 + (alpha - gamma_1) g/||g||.
+    Returns (u, value, g).
+    """
+    V, gm = _prep(V, gamma)
+    w, s = P[:, :-1], P[:, -1]
+    g = np.sum(w, axis=0)
+    ng = math.sqrt(float(g @ g))
+    if ng > 0.0:
+        u = V[0] + (alpha - gm[0]) * g / ng
+    else:
+        u = V[0].copy()
+    value = float(g @ u) + alpha / SQRT2 - float(np.sum(V[1:] * w)) - float(gm[1:] @ s)
+    return u, value, g
+
+
+def ses_program_value(V, gamma, P, u, gam):
+    """Objective of Eq. (oracle_program) for y = (u; gam), unsimplified.
+
+    (sum_j a_j y_j - c) . p = sum_{i>=2} (u - v_i; gam - gamma_i) . (w_i; s_i),
+    with the SOC inner product of Sec. 2.1.
+    """
+    V, gm = _prep(V, gamma)
+    Y = np.empty((V.shape[0] - 1, V.shape[1] + 1))
+    Y[:, :-1] = np.asarray(u)[None, :] - V[1:]
+    Y[:, -1] = gam - gm[1:]
+    return float(np.sum(soc_inner(Y, P)))
+
+
+def ses_primal_lb(V, gamma, P):
+    """Value of the primal solution (z~ p; x~') of Eq. (primal_construction).
+
+    Problem D there, for the SES data of Eq. (dualses): maximise
+    (c . p) z + c' . x' subject to (a_j . p) z + a'_j . x' = b_j, z >= 0,
+    x' in K' = Q^{d+1}. With g_j = a_j . p (j <= d), sigma = a_{d+1} . p
+    = sum s_i and b = (0; 1): x' = (-z g; 1 - z sigma), feasible iff
+    z <= 1/(||g|| + sigma), value gamma_1 + z (c . p - v_1^T g - gamma_1 sigma).
+    (z~ p; x~') is primal feasible for (SCP), so by weak duality the value is a
+    lower bound on OPT, the optimal radius.
+    """
+    V, gm = _prep(V, gamma)
+    w, s = P[:, :-1], P[:, -1]
+    g = np.sum(w, axis=0)
+    sigma = float(np.sum(s))
+    cp = float(np.sum(V[1:] * w)) + float(gm[1:] @ s)
+    coef = cp - float(V[0] @ g) - gm[0] * sigma
+    zmax = 1.0 / (math.sqrt(float(g @ g)) + sigma)
+    return float(gm[0] + max(coef, 0.0) * zmax)
+
+
+def ses_objective(V, gamma, c):
+    """f = max_{i in [n]} ||c - v_i|| + gamma_i: radius of the smallest ball
+    centred at c enclosing every input sphere (Sec. 5)."""
+    V, gm = _prep(V, gamma)
+    return float(np.max(np.sqrt(np.sum((V - np.asarray(c)[None, :]) ** 2, axis=1)) + gm))
+
+
+def ses_step(V, gamma, ubar, t, alpha, eta, rho):
+    """One iteration of the alpha-FTP (Sec. 3, Theorem 6) for SES.
+
+    ``t`` oracle calls have completed and ``ubar`` is the mean of their u's (any
+    value when t = 0). Computes p^{t+1} (Eq. implement with k = eta t/rho), the
+    ORACLE answer, the primal lower bound and f at ubar. If the ORACLE succeeds
+    the mean is advanced to ubar^{t+1}. Returns a dict record.
+    """
+    V, gm = _prep(V, gamma)
+    k = eta * t / rho
+    P = ses_weights(V, gm, ubar, alpha, k)
+    u, value, g = ses_oracle(V, gm, P, alpha)
+    rec = {
+        "t": t,
+        "k": k,
+        "objective": ses_objective(V, gm, ubar),
+        "oracle_value": value,
+        "lower_bound": ses_primal_lb(V, gm, P),
+        "u": u,
+        "g": g,
+        "failed": value < 0.0,
+    }
+    if value >= 0.0:
+        rec["ubar_next"] = np.asarray(ubar, dtype=np.float64) + (u - ubar) / (t + 1)
+    else:
+        rec["ubar_next"] = np.asarray(ubar, dtype=np.float64).copy()
+    return rec
+
+
+# ------------------------------------------------------------ the alpha-FTP
+def ses_ftp(V, gamma, alpha, eta, rho, T, mode=MODE_FIXED, delta=1e-4, patience=10,
+            keep_trace=False):
+    """alpha-feasibility test of Theorem 6 for SES, run for at most T iterations.
+
+    Modes: FIXED runs exactly T iterations unless the ORACLE separates;
+    THEORY is the same with the conclusion of Theorem 6 (OPT <= (1+eps) alpha
+    when T is the theorem's count); PRACTICAL adds the two rules of Sec. 5:
+    stop with an affirmative answer as soon as f^t < alpha, and stop when
+    |f^t - f^{t-1}|/f^{t-1} < delta for ``patience`` consecutive iterations
+    (the ratio is skipped when f^{t-1} = 0).
+    Returns a dict with the outcome, the iteration count, the final mean, the
+    best enclosing ball seen (c_best, f_best), the best primal lower bound and,
+    if asked, the per-iteration records.
+    """
+    V, gm = _prep(V, gamma)
+    ubar = V[0].copy()
+    f_best, c_best = math.inf, ubar.copy()
+    lb_best = 0.0
+    trace = []
+    f_prev, streak = None, 0
+    outcome = OUT_FIXED if mode == MODE_FIXED else OUT_FEASIBLE
+    t = 0
+    while t < T:
+        rec = ses_step(V, gm, ubar, t, alpha, eta, rho)
+        if keep_trace:
+            trace.append(rec)
+        if t > 0 and rec["objective"] < f_best:
+            f_best, c_best = rec["objective"], ubar.copy()
+        lb_best = max(lb_best, rec["lower_bound"])
+        if rec["failed"]:
+            outcome = OUT_SEPARATED
+            break
+        if mode == MODE_PRACTICAL and t > 0:
+            f = rec["objective"]
+            if f < alpha:
+                outcome = OUT_BELOW_ALPHA
+                break
+            if f_prev is not None and f_prev > 0.0:
+                streak = streak + 1 if abs(f - f_prev) / f_prev < delta else 0
+                if streak >= patience:
+                    outcome = OUT_STALLED
+                    break
+            f_prev = f
+        ubar = rec["ubar_next"]
+        t += 1
+    f_end = ses_objective(V, gm, ubar)
+    if t > 0 and f_end < f_best:
+        f_best, c_best = f_end, ubar.copy()
+    return {"outcome": outcome, "iters": t, "ubar": ubar, "f_best": f_best,
+            "c_best": c_best, "lb_best": lb_best, "trace": trace}
+
+
+# ------------------------------------------------- feasibility -> optimisation
+def ses_solve(V, gamma=None, eps=1e-2, mode=MODE_PRACTICAL, max_iters=10**7,
+              delta=1e-4, patience=10, max_steps=200, eta=None):
+    """(1+eps)-approximate SES by the search of Sec. 3 over alpha in [D/2, D].
+
+    Step i: alpha_i = L + (U-L)/3, eps_i = (U-L)/(3 alpha_i), T_i and eta_i from
+    Theorem 6 (Sec. 4.1 constants). Separation -> L = alpha_i; otherwise the
+    FTP's conclusion OPT <= (1+eps_i) alpha_i -> U = (1+eps_i) alpha_i. The
+    paper's PRACTICAL rules (Sec. 5) replace the T_i iterations by its early
+    exit / early stop; a stalled run is taken as the affirmative answer, as the
+    paper's experiments do.
+
+    Two pairs of bounds are kept. (L, U) is the search range. (lb, ub) are
+    certificates: ub is the radius f of an actual enclosing ball (the best
+    centre seen), lb the best primal value of Eq. (primal_construction) seen,
+    both valid whatever the mode. The loop ends when U <= (1+eps) L, when
+    ub <= (1+eps) lb, or when ``max_iters`` MWU iterations have run.
+
+    ``eta`` None uses eta_i = sqrt(ln r / T_i) of Theorem 6 in every step; a
+    number fixes the step size (Theorem 1 allows any eta in (0, 1]; the
+    guarantee of Theorem 6 then no longer applies, the certificates still do).
+    """
+    V, gm = _prep(V, gamma)
+    n = V.shape[0]
+    D = ses_D(V, gm)
+    rho = ses_width(D)
+    r = ses_rank(n)
+    L, U = D / 2.0, D
+    lb, ub, center = 0.0, ses_objective(V, gm, V[0]), V[0].copy()
+    total, steps = 0, []
+    if D == 0.0:
+        return {"radius": ub, "center": center, "lower_bound": ub, "upper_bound": ub,
+                "iters": 0, "steps": steps, "L": 0.0, "U": 0.0}
+    while U > (1.0 + eps) * L and ub > (1.0 + eps) * lb and total < max_iters and len(steps) < max_steps:
+        alpha = L + (U - L) / 3.0
+        eps_i = (U - L) / (3.0 * alpha)
+        T = ses_T(D, n, eps_i, alpha)
+        eta_i = theorem_eta(r, T) if eta is None else float(eta)
+        res = ses_ftp(V, gm, alpha, eta_i, rho, min(T, max_iters - total), mode=mode,
+                      delta=delta, patience=patience)
+        total += res["iters"]
+        if res["f_best"] < ub:
+            ub, center = res["f_best"], res["c_best"]
+        lb = max(lb, res["lb_best"])
+        if res["outcome"] == OUT_SEPARATED:
+            L = max(L, alpha)
+        elif res["iters"] >= T or res["outcome"] in (OUT_STALLED, OUT_BELOW_ALPHA):
+            U = min(U, (1.0 + eps_i) * alpha, ub)
+        L = max(L, lb)
+        steps.append({"alpha": alpha, "eps_i": eps_i, "T": T, "eta": eta_i,
+                      "outcome": res["outcome"], "iters": res["iters"], "L": L, "U": U})
+        if res["outcome"] not in (OUT_SEPARATED, OUT_STALLED, OUT_BELOW_ALPHA) and res["iters"] < T:
+            break  # iteration budget exhausted inside the step
+    return {"radius": ub, "center": center, "lower_bound": lb, "upper_bound": ub,
+            "iters": total, "steps": steps, "L": L, "U": U}
