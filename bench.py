@@ -1,0 +1,414 @@
+"""Benchmark of the MWU hot path on one GB300 (or N replicas under torchrun).
+
+A step is one MWU iteration of the alpha-FTP (one mwu_step launch: the SOC
+exponential of every cone, the trace normaliser, the weighted n x d reduction,
+the closed-form ORACLE and the running-mean update) over the SES workload
+n = 1,000,000 points i.i.d. N(0, I_32), float32, seed 0, at the first search
+step alpha_1 = 2D/3 with Theorem 6's step size. The input (128 MB) is smaller
+than L2, so L2 is flushed by a 512 MB write between timed steps; each step is
+timed with CUDA events on the launching stream and the flush is outside the
+events.
+
+Prints one JSON line. `--impl reference` times the FP64 oracle (the CPU
+reference of this method) on the host cores instead.
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SES/SVM time-to-(1+ε) & MWU iters/s vs plain FP32 on GB300; % of HBM roofline"
+UNIT = "MWU iters/s"
+N_POINTS, DIM, SEED = 1_000_000, 32, 0
+WORKLOAD = "SES n=1e6 d=32 N(0,I) fp32 seed 0, one MWU iteration per step at alpha_1=2D/3"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p["hbm_gbs"], "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def theorem_eta_ses(D, n, alpha, eps_i):
+    T = math.ceil(36.0 * D * D * math.log(2 * n - 2) / (eps_i * eps_i * alpha * alpha))
+    return math.sqrt(math.log(2 * n - 2) / T), T
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names[1:], parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- oracle timing
+def oracle_rate(V64, alpha, eta, rho, budget_s, max_steps=None):
+    """Iterations per second of the FP64 oracle on the rows of V64, timed on
+    the host. Runs steps until budget_s seconds (at least one)."""
+    from oracle import ses as oses
+    ubar = V64[0].copy()
+    t, t0 = 0, time.perf_counter()
+    while True:
+        rec = oses.ses_step(V64, None, ubar, t, alpha, eta, rho)
+        ubar = rec["ubar_next"]
+        t += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_steps is not None and t >= max_steps):
+            return t / el, t, el
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2405_09157_gb300 import datagen
+    from oracle import ses as oses
+    V = datagen.ses_gaussian(N_POINTS, DIM, SEED).astype(np.float64)
+    D = oses.ses_D(V)
+    rho = oses.ses_width(D)
+    alpha = 2.0 * D / 3.0
+    eta, _ = theorem_eta_ses(D, N_POINTS, alpha, 0.25)
+    # size each step's row sample so the whole K+W run stays within ~2 minutes
+    probe_rows = 100_000
+    r_probe, _, _ = oracle_rate(V[:probe_rows], alpha, eta, rho, 1.0, max_steps=3)
+    per_row = 1.0 / (r_probe * probe_rows)
+    total_steps = args.steps + args.warmup
+    rows = int(min(N_POINTS, max(10_000, 120.0 / (total_steps * per_row))))
+    Vs = V[:rows]
+    ubar = Vs[0].copy()
+    for t in range(args.warmup):
+        ubar = oses.ses_step(Vs, None, ubar, t, alpha, eta, rho)["ubar_next"]
+    t0 = time.perf_counter()
+    for t in range(args.warmup, args.warmup + args.steps):
+        ubar = oses.ses_step(Vs, None, ubar, t, alpha, eta, rho)["ubar_next"]
+    el = time.perf_counter() - t0
+    ms_per_step = 1e3 * el / args.steps
+    value = (rows / N_POINTS) * args.steps / el  # full-workload iterations per second
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_POINTS, "d": DIM, "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{rows} of {N_POINTS} rows per step, scaled by rows/n"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2405_09157_gb300 import _ffi, api, datagen
+
+    n, d = args.n, args.d
+    tdt = torch.bfloat16 if args.dtype == "bf16" else torch.float32
+    ebytes = 2 if args.dtype == "bf16" else 4
+    if args.problem == "ses":
+        V32 = datagen.ses_gaussian(n, d, SEED + rank)
+        pts = torch.from_numpy(V32).to(dev).to(tdt)
+        m = api.MWU(_ffi.SES, pts)
+        D = float(api.bounds(_ffi.SES, pts).item())
+        rho = 3.0 * D / math.sqrt(2.0)
+        alpha = 2.0 * D / 3.0
+        eta, T1 = theorem_eta_ses(D, n, alpha, 0.25)
+        alg_bytes = n * d * ebytes
+        label_D = 0.0
+    else:
+        V32, y = datagen.svm_clusters(n // 2, n - n // 2, d, seed=SEED + rank)
+        pts = torch.from_numpy(V32).to(dev).to(tdt)
+        m = api.MWU(_ffi.SVM, pts, labels=torch.from_numpy(y).to(dev))
+        D = float(api.bounds(_ffi.SVM, pts).item())
+        rho = 2.0 * D
+        alpha = 4.0 * D / 3.0
+        T1 = math.ceil(64.0 * D * D * math.log(n) / (0.25 * alpha * alpha))
+        eta = math.sqrt(math.log(n) / T1)
+        alg_bytes = n * d * ebytes + n
+        label_D = D
+    eor = eta / rho
+    default_workload = (args.problem == "ses" and n == N_POINTS and d == DIM and args.dtype == "f32")
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    flush = torch.empty(max(4 * l2, 512 << 20) // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    out = api.new_steps(1, dev)
+
+    def step():
+        m.step(alpha, eor, out=out[0], D=label_D)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    w0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tot_ms = float(tt.item())
+    ms_per_step = tot_ms / args.steps
+    value = world * args.steps / (tot_ms / 1e3)
+    rec = api.decode_steps(out)[0]
+
+    # roofline of the dominant (only) kernel: algorithmic bytes = n d (element bytes)
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (ms_per_step * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "ses_iter_n1e6_d32_traffic.json")
+    if default_workload and os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                pj = json.load(f)
+            if pj.get("kernel_rev") == kernel_rev():
+                traffic = pj["dram_bytes_per_launch"]
+        except Exception:
+            traffic = None
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": WORKLOAD if default_workload else
+                   f"{args.problem.upper()} n={n} d={d} {args.dtype} (non-default case)",
+                   "n": n, "d": d, "alpha": alpha, "eta": eta,
+                   "eta_over_rho": eor, "theorem_T1": T1,
+                   "l2": "flushed between timed steps by a 512 MB write outside the events",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                     "alg_bytes_per_launch": alg_bytes},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "wall_ms_per_step_incl_flush": 1e3 * wall / args.steps,
+        "last_step": {"t": int(rec["t"]), "oracle_value": float(rec["oracle_value"]),
+                      "objective": float(rec["objective"]), "status": int(rec["status"])},
+    }
+    if rank == 0 and not args.skip_extras and default_workload:
+        result["e2e"] = e2e_host(args, V32, alpha, eor, dev)
+        result["cpu_baseline"] = cpu_baseline(V32, alpha, eta, rho)
+        result["variants"] = variants(dev, flush)
+        result["time_to_eps"] = time_to_eps(pts)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result))
+
+
+def kernel_rev():
+    """Hash of the kernel sources: a stored ncu traffic figure is used only
+    for the kernel revision it was measured on."""
+    import hashlib
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2405_09157_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def e2e_host(args, V32, alpha, eor, dev):
+    """Same metric through the public API with host buffers: every step copies
+    the points from pinned host memory to the device, runs the iteration and
+    reads the step record back."""
+    import torch
+    from paper_2405_09157_gb300 import _ffi, api
+    host = torch.from_numpy(V32).pin_memory()
+    dpts = torch.empty_like(host, device=dev)
+    dpts.copy_(host)
+    m = api.MWU(_ffi.SES, dpts)
+    out = api.new_steps(1, dev)
+    rec_host = torch.empty((1, api.STEP_BYTES), dtype=torch.uint8).pin_memory()
+    K = max(10, min(args.steps, 200))
+    for _ in range(3):
+        dpts.copy_(host, non_blocking=True)
+        m.step(alpha, eor, out=out[0])
+        rec_host.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(K):
+        dpts.copy_(host, non_blocking=True)
+        m.step(alpha, eor, out=out[0])
+        rec_host.copy_(out, non_blocking=True)
+    e.record()
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e) / K
+    return {"value": 1e3 / ms, "unit": UNIT, "h2d_bytes_per_step": int(V32.nbytes),
+            "d2h_bytes_per_step": api.STEP_BYTES, "ms_per_step": ms, "steps": K}
+
+
+def cpu_baseline(V32, alpha, eta, rho):
+    V64 = V32.astype(np.float64)
+    rate, steps, el = oracle_rate(V64, alpha, eta, rho, budget_s=15.0)
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} oracle iterations over all {V32.shape[0]} points ({el:.1f} s), FP64 numpy, 1 thread"}
+
+
+def _time_steps(m, alpha, eor, D, flush, K=50):
+    import torch
+    s = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    for i in range(K + 5):
+        flush.zero_()
+        if i >= 5:
+            s[i - 5].record()
+        m.step(alpha, eor, D=D)
+        if i >= 5:
+            e[i - 5].record()
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in zip(s, e)) / K
+
+
+def variants(dev, flush):
+    """Per-iteration time of the other hot-path forms (same timing rules)."""
+    import torch
+    from paper_2405_09157_gb300 import _ffi, api, datagen
+    peak, _ = peaks()
+    out = {}
+    V32 = datagen.ses_gaussian(N_POINTS, DIM, SEED)
+    pb = torch.from_numpy(V32).to(dev).to(torch.bfloat16)
+    m = api.MWU(_ffi.SES, pb)
+    D = float(api.bounds(_ffi.SES, pb).item())
+    ms = _time_steps(m, 2 * D / 3, 0.01 / (3 * D / math.sqrt(2)), 0.0, flush)
+    b = N_POINTS * DIM * 2
+    out["ses_n1e6_d32_bf16"] = {"ms_per_iter": ms, "iters_per_s": 1e3 / ms, "GBps": b / ms / 1e6,
+                               "frac_hbm": b / ms / 1e6 / peak}
+    del pb, m
+    X32, y = datagen.svm_clusters(500_000, 500_000, 128, seed=0)
+    X = torch.from_numpy(X32).to(dev)
+    lab = torch.from_numpy(y).to(dev)
+    D = float(api.bounds(_ffi.SVM, X).item())
+    for name, pts, eb in (("svm_n1e6_d128_f32", X, 4), ("svm_n1e6_d128_bf16", X.to(torch.bfloat16), 2)):
+        m = api.MWU(_ffi.SVM, pts, labels=lab)
+        ms = _time_steps(m, D, 0.01 / (2 * D), D, flush)
+        b = 1_000_000 * 128 * eb + 1_000_000
+        out[name] = {"ms_per_iter": ms, "iters_per_s": 1e3 / ms, "GBps": b / ms / 1e6, "frac_hbm": b / ms / 1e6 / peak}
+    return out
+
+
+def time_to_eps(pts):
+    """ses_solve at eps = 1e-3 (paper's practical rules, Theorem 6 step size)
+    within a 200,000-iteration budget: wall time and the certificate reached."""
+    import torch
+    from paper_2405_09157_gb300 import api
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, rep = api.ses_solve(pts, eps=1e-3, max_iters=200_000, poll_every=512)
+    el = time.perf_counter() - t0
+    return {"seconds": el, "iters": rep["iters"], "radius": rep["value"], "lower_bound": rep["lower_bound"],
+            "gap": rep["value"] / rep["lower_bound"] - 1 if rep["lower_bound"] > 0 else None,
+            "search_range": [rep["search_L"], rep["search_U"]], "status": rep["status"],
+            "note": "certificate gap = radius / primal lower bound - 1; status 5 = budget spent"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-extras", action="store_true", help="only the timed steps (for profiling)")
+    ap.add_argument("--problem", default="ses", choices=["ses", "svm"], help="non-default cases: profiling only")
+    ap.add_argument("--n", type=int, default=N_POINTS)
+    ap.add_argument("--d", type=int, default=DIM)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

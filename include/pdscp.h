@@ -1,0 +1,260 @@
+/*
+ * pdscp.h — C ABI of the GB300 library for the primal-dual symmetric-cone MWU
+ * framework (Zheng, Varvitsiotis, Tan, Lin, arXiv 2405.09157), specialised to
+ * its two applications: the Smallest Enclosing Sphere (SES, Sec. 4.1) and the
+ * hard-margin SVM / polytope distance (Sec. 4.2).
+ *
+ * Conventions for every entry point
+ *   - Pointers named *_dev are device pointers (cudaMalloc'd or framework
+ *     tensors on the current device); *_host are host pointers. The caller
+ *     owns every buffer. The library allocates no device memory and keeps no
+ *     state between calls other than the thread-local error message.
+ *   - Points are row-major n x d, element type selected by `dtype`
+ *     (PDSCP_F32 = float32, PDSCP_BF16 = bfloat16), rows contiguous (pitch d).
+ *     Vectorised 16-byte loads are used when the base address is 16-byte
+ *     aligned and d * sizeof(element) is a multiple of 16; other inputs take a
+ *     scalar-load path with identical results.
+ *   - All device work is enqueued on `stream` (a cudaStream_t; NULL is the
+ *     legacy default stream) in call order. Entry points that return a host
+ *     value synchronise the stream; the doc comment says so.
+ *   - Errors are returned as pdscp_status and never thrown or aborted across
+ *     the ABI; pdscp_last_error() gives a message for the calling thread.
+ *     Numeric and device-side problems are reported in the status word of the
+ *     step record / state header written on the device.
+ */
+#ifndef PDSCP_H
+#define PDSCP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* pdscp_stream; /* == cudaStream_t */
+
+typedef enum pdscp_status {
+  PDSCP_OK = 0,
+  PDSCP_ERR_INVALID_ARG = 1,     /* bad size, pointer, alignment or option */
+  PDSCP_ERR_CUDA = 2,            /* a CUDA runtime call failed */
+  PDSCP_ERR_TIMEOUT = 3,         /* a bounded device wait gave up */
+  PDSCP_ERR_NOT_SEPARABLE = 4,   /* SVM: certificate shows margin 0 */
+  PDSCP_ERR_NOT_CONVERGED = 5,   /* iteration budget spent before the target */
+  PDSCP_ERR_NUMERIC = 6,         /* NaN/Inf or an underflowed normaliser */
+  PDSCP_ERR_NOT_IMPLEMENTED = 7, /* unsupported d / dtype combination */
+  PDSCP_ERR_WORKSPACE = 8        /* workspace too small */
+} pdscp_status;
+
+/* problem kinds */
+#define PDSCP_SES 0 /* Smallest Enclosing Sphere, K = prod_{i>=2} Q^{d+1} */
+#define PDSCP_SVM 1 /* hard-margin SVM (min variant), K = R^n_+ */
+
+/* point storage */
+#define PDSCP_F32 0
+#define PDSCP_BF16 1
+
+/* alpha-FTP stopping rules (Sec. 3 Theorems 6/7, Sec. 5) */
+#define PDSCP_RULES_NONE 0      /* stop only when the ORACLE separates */
+#define PDSCP_RULES_PRACTICAL 1 /* also: f beats alpha; |df|/f < delta `patience` times */
+
+/* solve modes */
+#define PDSCP_MODE_PRACTICAL 0  /* Sec. 5 rules inside each alpha-FTP */
+#define PDSCP_MODE_THEORY 1     /* T_i iterations of Theorem 6/7 per FTP */
+
+/* Largest supported dimension d. */
+#define PDSCP_MAX_D 1024
+
+/*
+ * Per-step record written on the device by mwu_step (Sec. 3 alpha-FTP
+ * iteration t -> t+1; Sec. 5 objective). 64 bytes.
+ *   oracle_value  value of the ORACLE program at p^{t+1}: Eq. (ses_oracle) /
+ *                 Eq. (svm_oracle). Negative = separated.
+ *   objective     f at the mean read by this step (ubar^t or wbar^t), Sec. 5:
+ *                 SES radius max_i ||ubar - v_i|| + gamma_i; SVM margin.
+ *   lower_bound   SES: value of the primal solution of Eq. (primal_construction)
+ *                 built from p^{t+1} (<= OPT). SVM: the margin f (<= OPT).
+ *   upper_bound   SES: f (>= OPT). SVM: Claim 10 PD value (>= OPT).
+ *   t             completed ORACLE calls after the step.
+ *   failed        1 if the ORACLE separated (alpha < OPT for SES; OPT < alpha
+ *                 for SVM).
+ *   stopped       1 if the alpha-FTP has ended (separation or a rule).
+ *   status        pdscp_status of the device computation.
+ */
+typedef struct pdscp_step_out {
+  double oracle_value;
+  double objective;
+  double lower_bound;
+  double upper_bound;
+  int64_t t;
+  int32_t failed;
+  int32_t stopped;
+  int32_t status;
+  int32_t outcome;
+  double k;
+} pdscp_step_out;
+
+/* Outcome codes in pdscp_step_out.outcome / pdscp_state header. */
+#define PDSCP_OUT_RUNNING 0
+#define PDSCP_OUT_SEPARATED 1  /* ORACLE value < 0 */
+#define PDSCP_OUT_BEAT_ALPHA 2 /* SES f < alpha / SVM f > alpha (Sec. 5) */
+#define PDSCP_OUT_STALLED 3    /* Sec. 5 delta/patience rule */
+
+typedef struct pdscp_options {
+  double eps;         /* target (1+eps) accuracy of the search, > 0 */
+  double delta;       /* Sec. 5 stability threshold (paper: 1e-4) */
+  int32_t patience;   /* Sec. 5 consecutive iterations (paper: 10) */
+  int32_t mode;       /* PDSCP_MODE_* */
+  int64_t max_iters;  /* MWU iterations over the whole search */
+  int32_t poll_every; /* host polls the device state every k iterations */
+  int32_t max_steps;  /* search steps (alpha values) at most */
+  double eta;         /* 0: eta_i = sqrt(ln r / T_i) (Theorems 6/7); else fixed */
+} pdscp_options;
+
+typedef struct pdscp_report {
+  double value;       /* SES: radius of the returned ball; SVM: its margin */
+  double lower_bound; /* certificate: OPT >= lower_bound */
+  double upper_bound; /* certificate: OPT <= upper_bound */
+  double D;           /* bound of Sec. 4.1 (SES) / Lemma 9 (SVM) */
+  double search_L;    /* final search range [L, U] of Sec. 3 */
+  double search_U;
+  int64_t iters;      /* MWU iterations run */
+  int32_t search_steps;
+  int32_t status;
+} pdscp_report;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int32_t pdscp_version(void);
+
+/* Message describing the last failing call on this thread ("" if none). */
+const char* pdscp_last_error(void);
+
+/*
+ * Bytes of device workspace needed by pdscp_bounds / mwu_step / the solves for
+ * a problem of this kind and size on the current device. The workspace holds
+ * per-CTA partial sums and a completion counter; it must be zeroed once before
+ * first use (mwu_state_init and the solves do this) and may be reused by
+ * consecutive calls on one stream. Calls that share a workspace must not
+ * overlap on the GPU.
+ */
+pdscp_status pdscp_workspace_size(int32_t problem, int64_t n, int32_t d, size_t* bytes_host);
+
+/* Bytes of device state for mwu_step (a header plus O(d) doubles/floats). */
+pdscp_status pdscp_state_size(int32_t problem, int32_t d, size_t* bytes_host);
+
+/*
+ * Bounds pre-pass (Sec. 4.1 / Lemma 9). Writes D to *D_dev (one double):
+ *   SES: D = max_{i>=2} ||v_1 - v_i|| + gamma_1 + gamma_i  (OPT in [D/2, D])
+ *   SVM: D = max_i ||x_i||                                  (s_1, s_2 <= D)
+ * radii_dev (SES, may be NULL = all zero) holds n float radii.
+ * Asynchronous. Requires n >= 2 (SES) or n >= 1 (SVM), 1 <= d <= PDSCP_MAX_D.
+ */
+pdscp_status pdscp_bounds(int32_t problem, const void* pts_dev, int32_t dtype,
+                          const float* radii_dev, int64_t n, int32_t d,
+                          void* ws_dev, size_t ws_bytes, pdscp_stream stream,
+                          double* D_dev);
+
+/*
+ * Start an alpha-FTP (Sec. 3): t = 0, the running mean set to v_1 (SES; any
+ * value works because the exponent is 0 at t = 0) or to (w, s1, s2) = 0
+ * (SVM), no best point yet, stop rules `rules` (PDSCP_RULES_*) with the Sec. 5
+ * parameters delta and patience. Also zeroes the workspace's counter.
+ * Asynchronous.
+ */
+pdscp_status mwu_state_init(int32_t problem, const void* pts_dev, int32_t dtype,
+                            int64_t n, int32_t d, int32_t rules, double delta,
+                            int32_t patience, void* state_dev, void* ws_dev,
+                            size_t ws_bytes, pdscp_stream stream);
+
+/*
+ * One iteration t -> t+1 of the alpha-FTP (Sec. 3; Eq. implement for SES,
+ * Eq. min_implement for SVM), as one kernel launch over the n points:
+ *   SES (Sec. 4.1): per cone i >= 2 the exponent -(eta t/rho)(ubar - v_i;
+ *     alpha - gamma_i), its closed-form SOC exponential (Sec. 2.1), the trace
+ *     normaliser, g = sum w_i, the ORACLE u = v_1 + (alpha - gamma_1) g/||g||,
+ *     its value, the primal bound of Eq. (primal_construction), f^t, and the
+ *     running-mean update ubar^{t+1}.
+ *   SVM (Sec. 4.2): per point the exponent -(eta t/rho)(y_i x_i^T wbar -
+ *     sbar_{class i}), the normaliser, z = P mu - Q gamma, the ORACLE
+ *     (w, s1, s2) of Eq. (svm_oracle), its value, the Claim 10 bound, f^t,
+ *     and the running means.
+ * eta_over_rho = eta/rho (> 0); k = eta_over_rho * t is formed on the device.
+ * alpha > 0. D (SVM) must be >= the largest point norm (pdscp_bounds); it is
+ * ignored for SES. labels_dev (SVM): n int8 in {+1,-1}. radii_dev (SES) may be
+ * NULL. out_dev (may be NULL) receives one pdscp_step_out. If the state's
+ * alpha-FTP has stopped, the launch returns at once and writes nothing.
+ * eval_only != 0 evaluates f at the current mean (and the best-point
+ * bookkeeping) without an ORACLE step. Asynchronous; no host sync.
+ */
+pdscp_status mwu_step(int32_t problem, const void* pts_dev, int32_t dtype,
+                      const float* radii_dev, const int8_t* labels_dev,
+                      int64_t n, int32_t d, double alpha, double eta_over_rho,
+                      double D, int32_t eval_only, void* state_dev,
+                      void* ws_dev, size_t ws_bytes, pdscp_stream stream,
+                      pdscp_step_out* out_dev);
+
+/*
+ * Resume an alpha-FTP from a checkpoint (t, running mean): sets t and the
+ * mean from mean_dev (device doubles; SES: ubar, d values; SVM: wbar, then
+ * s1bar and s2bar, d+2 values), clears the stop flags and best-point records
+ * (rules PDSCP_RULES_NONE), then runs one evaluation pass over the points at
+ * that mean to recompute the exponent-shift bound. D as for mwu_step (SVM
+ * only). Asynchronous.
+ */
+pdscp_status mwu_state_set(int32_t problem, const void* pts_dev, int32_t dtype,
+                           const float* radii_dev, const int8_t* labels_dev,
+                           int64_t n, int32_t d, int64_t t, const double* mean_dev,
+                           double D, void* state_dev, void* ws_dev, size_t ws_bytes,
+                           pdscp_stream stream);
+
+/*
+ * Read the running mean (SES: ubar, d floats; SVM: wbar then s1bar, s2bar:
+ * d+2 floats) and the best point seen (SES: centre with the smallest f; SVM:
+ * direction with the largest margin; d floats) of a state into device
+ * buffers (either may be NULL). Asynchronous.
+ */
+pdscp_status mwu_state_read(int32_t problem, int32_t d, const void* state_dev,
+                            float* mean_dev, float* best_dev, pdscp_stream stream);
+
+/*
+ * (1+eps)-approximate Smallest Enclosing Sphere (Sec. 4.1) by the search of
+ * Sec. 3 over alpha in [D/2, D], each alpha-FTP run on the device with the
+ * host polling every opts->poll_every iterations (this synchronises the
+ * stream). Writes the best centre (d floats) to center_dev and fills
+ * *report_host: radius of an actual enclosing ball (upper bound), the best
+ * primal lower bound of Eq. (primal_construction), the search range.
+ * Returns PDSCP_ERR_NOT_CONVERGED (with a valid report) when opts->max_iters
+ * ran out before the range or the certificate gap closed.
+ */
+pdscp_status ses_solve(const void* pts_dev, int32_t dtype, const float* radii_dev,
+                       int64_t n, int32_t d, const pdscp_options* opts,
+                       void* ws_dev, size_t ws_bytes, pdscp_stream stream,
+                       float* center_dev, pdscp_report* report_host);
+
+/*
+ * (1-eps)-approximate hard-margin SVM / (1+eps) polytope distance (Sec. 4.2)
+ * by the minimisation search over alpha in (0, 2D]. Writes the best
+ * direction w (d floats, unit norm) to w_dev and its margin and Claim 10
+ * upper bound to *report_host. Synchronises like ses_solve.
+ */
+pdscp_status svm_solve(const void* X_dev, int32_t dtype, const int8_t* labels_dev,
+                       int64_t n, int32_t d, const pdscp_options* opts,
+                       void* ws_dev, size_t ws_bytes, pdscp_stream stream,
+                       float* w_dev, pdscp_report* report_host);
+
+/*
+ * Reverse-mode sweep through T unrolled MWU iterations at fixed alpha (the
+ * gradient of the final objective with respect to the points). Not built yet:
+ * returns PDSCP_ERR_NOT_IMPLEMENTED.
+ */
+pdscp_status mwu_backward(int32_t problem, const void* pts_dev, int32_t dtype,
+                          const int8_t* labels_dev, int64_t n, int32_t d,
+                          double alpha, double eta_over_rho, double D, int64_t T,
+                          int32_t ckpt_every, void* ws_dev, size_t ws_bytes,
+                          pdscp_stream stream, float* grad_pts_dev);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDSCP_H */

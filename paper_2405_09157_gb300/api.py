@@ -1,0 +1,183 @@
+"""Thin PyTorch-facing binding of the C ABI (argument marshalling only).
+
+Torch supplies device memory (tensors) and the stream; every step of the
+method runs in the library's CUDA kernels. Names follow include/pdscp.h.
+"""
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _ffi
+from ._ffi import BF16, F32, SES, SVM, check, load
+
+STEP_DTYPE = np.dtype([("oracle_value", "<f8"), ("objective", "<f8"), ("lower_bound", "<f8"),
+                       ("upper_bound", "<f8"), ("t", "<i8"), ("failed", "<i4"), ("stopped", "<i4"),
+                       ("status", "<i4"), ("outcome", "<i4"), ("k", "<f8")])
+STEP_BYTES = 64
+
+
+def _vp(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def dtype_code(t):
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.bfloat16:
+        return BF16
+    raise TypeError(f"points must be float32 or bfloat16, got {t.dtype}")
+
+
+def _points(pts):
+    if not pts.is_cuda or pts.dim() != 2 or not pts.is_contiguous():
+        raise ValueError("points must be a contiguous 2-D CUDA tensor (n, d)")
+    return pts.shape[0], pts.shape[1], dtype_code(pts)
+
+
+def workspace_size(problem, n, d):
+    out = ctypes.c_size_t()
+    check(load().pdscp_workspace_size(problem, n, d, ctypes.byref(out)), "pdscp_workspace_size")
+    return out.value
+
+
+def state_size(problem, d):
+    out = ctypes.c_size_t()
+    check(load().pdscp_state_size(problem, d, ctypes.byref(out)), "pdscp_state_size")
+    return out.value
+
+
+def workspace(problem, n, d, device="cuda"):
+    """Zeroed device workspace for this problem size (uint8 tensor)."""
+    return torch.zeros(workspace_size(problem, n, d), dtype=torch.uint8, device=device)
+
+
+def new_state(problem, d, device="cuda"):
+    return torch.zeros(state_size(problem, d), dtype=torch.uint8, device=device)
+
+
+def new_steps(k, device="cuda"):
+    """Device buffer for k pdscp_step_out records."""
+    return torch.zeros((k, STEP_BYTES), dtype=torch.uint8, device=device)
+
+
+def decode_steps(buf):
+    """pdscp_step_out records (uint8 tensor, any device) -> numpy structured array."""
+    a = buf.detach().to("cpu").contiguous().numpy().reshape(-1)
+    return a.view(STEP_DTYPE)
+
+
+def bounds(problem, pts, radii=None, ws=None, stream=None):
+    """D of Sec. 4.1 (SES) or Lemma 9 (SVM) as a (1,) float64 CUDA tensor."""
+    n, d, dt = _points(pts)
+    ws = workspace(problem, n, d, pts.device) if ws is None else ws
+    out = torch.empty(1, dtype=torch.float64, device=pts.device)
+    check(load().pdscp_bounds(problem, _vp(pts), dt, _vp(radii), n, d, _vp(ws), ws.numel(),
+                              _stream(stream), _vp(out)), "pdscp_bounds")
+    return out
+
+
+def state_init(problem, pts, state, ws, rules=_ffi.RULES_NONE, delta=1e-4, patience=10, stream=None):
+    n, d, dt = _points(pts)
+    check(load().mwu_state_init(problem, _vp(pts), dt, n, d, rules, delta, patience, _vp(state),
+                                _vp(ws), ws.numel(), _stream(stream)), "mwu_state_init")
+
+
+def mwu_step(problem, pts, alpha, eta_over_rho, state, ws, out=None, D=0.0, radii=None, labels=None,
+             eval_only=False, stream=None):
+    """One alpha-FTP iteration on the device (no host sync)."""
+    n, d, dt = _points(pts)
+    check(load().mwu_step(problem, _vp(pts), dt, _vp(radii), _vp(labels), n, d, float(alpha),
+                          float(eta_over_rho), float(D), int(bool(eval_only)), _vp(state), _vp(ws),
+                          ws.numel(), _stream(stream), _vp(out)), "mwu_step")
+
+
+def state_read(problem, d, state, stream=None, device="cuda"):
+    """(mean, best) float32 tensors of a state: SES (ubar, best centre); SVM
+    ((wbar, s1bar, s2bar), best direction)."""
+    m = torch.empty(d + (2 if problem == SVM else 0), dtype=torch.float32, device=device)
+    b = torch.empty(d, dtype=torch.float32, device=device)
+    check(load().mwu_state_read(problem, d, _vp(state), _vp(m), _vp(b), _stream(stream)), "mwu_state_read")
+    return m, b
+
+
+def state_set(problem, pts, t, mean, state, ws, radii=None, labels=None, D=0.0, stream=None):
+    """Resume from a checkpoint: t and the running mean (float64 CUDA tensor;
+    SVM: wbar then s1bar, s2bar)."""
+    n, d, dt = _points(pts)
+    mean = mean.to(device=pts.device, dtype=torch.float64).contiguous()
+    check(load().mwu_state_set(problem, _vp(pts), dt, _vp(radii), _vp(labels), n, d, int(t), _vp(mean),
+                               float(D), _vp(state), _vp(ws), ws.numel(), _stream(stream)), "mwu_state_set")
+
+
+class MWU:
+    """One alpha-FTP over resident points: state, workspace and step records."""
+
+    def __init__(self, problem, pts, labels=None, radii=None, rules=_ffi.RULES_NONE, delta=1e-4,
+                 patience=10):
+        self.problem, self.pts, self.labels, self.radii = problem, pts, labels, radii
+        self.n, self.d, _ = _points(pts)
+        self.ws = workspace(problem, self.n, self.d, pts.device)
+        self.state = new_state(problem, self.d, pts.device)
+        self.rules, self.delta, self.patience = rules, delta, patience
+        self.init()
+
+    def init(self, stream=None):
+        state_init(self.problem, self.pts, self.state, self.ws, self.rules, self.delta, self.patience, stream)
+
+    def step(self, alpha, eta_over_rho, out=None, D=0.0, eval_only=False, stream=None):
+        mwu_step(self.problem, self.pts, alpha, eta_over_rho, self.state, self.ws, out, D, self.radii,
+                 self.labels, eval_only, stream)
+
+    def set(self, t, mean, D=0.0, stream=None):
+        state_set(self.problem, self.pts, t, mean, self.state, self.ws, self.radii, self.labels, D, stream)
+
+    def read(self, stream=None):
+        return state_read(self.problem, self.d, self.state, stream, self.pts.device)
+
+
+def _options(eps, mode, max_iters, poll_every, max_steps, eta, delta, patience):
+    m = {"practical": _ffi.MODE_PRACTICAL, "theory": _ffi.MODE_THEORY}[mode]
+    return _ffi.Options(eps, delta, patience, m, max_iters, poll_every, max_steps, eta or 0.0)
+
+
+def _report(r):
+    return {k: getattr(r, k) for k, _ in _ffi.Report._fields_}
+
+
+def ses_solve(pts, radii=None, eps=1e-3, mode="practical", max_iters=1_000_000, poll_every=256,
+              max_steps=200, eta=None, delta=1e-4, patience=10, ws=None, stream=None, raise_on_budget=False):
+    """(1+eps)-approximate smallest enclosing sphere; returns (centre tensor, report dict)."""
+    n, d, dt = _points(pts)
+    ws = workspace(SES, n, d, pts.device) if ws is None else ws
+    center = torch.empty(d, dtype=torch.float32, device=pts.device)
+    opts = _options(eps, mode, max_iters, poll_every, max_steps, eta, delta, patience)
+    rep = _ffi.Report()
+    st = load().ses_solve(_vp(pts), dt, _vp(radii), n, d, ctypes.byref(opts), _vp(ws), ws.numel(),
+                          _stream(stream), _vp(center), ctypes.byref(rep))
+    if st != _ffi.PDSCP_OK and (raise_on_budget or st != 5):
+        check(st, "ses_solve")
+    return center, _report(rep)
+
+
+def svm_solve(X, labels, eps=1e-3, mode="practical", max_iters=1_000_000, poll_every=256, max_steps=200,
+              eta=None, delta=1e-4, patience=10, ws=None, stream=None, raise_on_budget=False):
+    """(1-eps)-approximate hard-margin SVM; returns (best mean direction wbar, report dict)."""
+    n, d, dt = _points(X)
+    if labels.dtype != torch.int8 or not labels.is_cuda or labels.numel() != n:
+        raise ValueError("labels must be an int8 CUDA tensor of n entries in {+1, -1}")
+    ws = workspace(SVM, n, d, X.device) if ws is None else ws
+    w = torch.empty(d, dtype=torch.float32, device=X.device)
+    opts = _options(eps, mode, max_iters, poll_every, max_steps, eta, delta, patience)
+    rep = _ffi.Report()
+    st = load().svm_solve(_vp(X), dt, _vp(labels), n, d, ctypes.byref(opts), _vp(ws), ws.numel(),
+                          _stream(stream), _vp(w), ctypes.byref(rep))
+    if st != _ffi.PDSCP_OK and (raise_on_budget or st != 5):
+        check(st, "svm_solve")
+    return w, _report(rep)

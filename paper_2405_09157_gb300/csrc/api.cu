@@ -1,0 +1,510 @@
+// Host side of the C ABI declared in include/pdscp.h: argument checks, the
+// workspace layout, the bounds pre-pass, alpha-FTP state handling, one-step
+// launches and the two search drivers (Sec. 3 "From feasibility to
+// optimization", Sec. 4.1 and 4.2 constants, Sec. 5 stopping rules).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "bounds_kernel.cuh"
+#include "dispatch.cuh"
+#include "ses_kernel.cuh"
+#include "svm_kernel.cuh"
+
+namespace pdscp {
+
+cudaError_t launch_ses(const SesParams& p, int dtype, bool vec, cudaStream_t stream);
+cudaError_t launch_svm(const SvmParams& p, int dtype, bool vec, cudaStream_t stream);
+
+namespace {
+
+thread_local std::string g_err;
+
+pdscp_status fail(pdscp_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+pdscp_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(PDSCP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+constexpr int kRing = 4096;  // step records kept by the solves between polls
+
+size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t partials, state, ring, dval, total;
+};
+
+// Workspace: [counter 256 B][per-CTA partials][solve state][step ring][D]
+Layout layout(int problem, int d) {
+  Layout L;
+  const int st = problem == PDSCP_SES ? ses_partial_stride(d) : svm_partial_stride(d);
+  const size_t rows = (size_t)device_sm_count() * kMaxBlocksPerSM;
+  L.partials = kHeadBytes;
+  L.state = L.partials + round256(rows * (size_t)st * sizeof(float));
+  L.ring = L.state + round256(state_bytes(d));
+  L.dval = L.ring + round256((size_t)kRing * sizeof(pdscp_step_out));
+  L.total = L.dval + 256;
+  return L;
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+size_t elem_size(int dtype) { return dtype == PDSCP_BF16 ? 2 : 4; }
+
+pdscp_status check_common(int problem, const void* pts, int dtype, int64_t n, int d) {
+  if (problem != PDSCP_SES && problem != PDSCP_SVM) return fail(PDSCP_ERR_INVALID_ARG, "unknown problem %d", problem);
+  if (dtype != PDSCP_F32 && dtype != PDSCP_BF16) return fail(PDSCP_ERR_INVALID_ARG, "unknown dtype %d", dtype);
+  if (d < 1 || d > PDSCP_MAX_D) return fail(PDSCP_ERR_NOT_IMPLEMENTED, "d=%d outside [1, %d]", d, PDSCP_MAX_D);
+  if (problem == PDSCP_SES && n < 2) return fail(PDSCP_ERR_INVALID_ARG, "SES needs n >= 2 (got %lld)", (long long)n);
+  if (problem == PDSCP_SVM && n < 2) return fail(PDSCP_ERR_INVALID_ARG, "SVM needs n >= 2 (got %lld)", (long long)n);
+  if (!pts) return fail(PDSCP_ERR_INVALID_ARG, "points pointer is null");
+  if (!aligned(pts, elem_size(dtype))) return fail(PDSCP_ERR_INVALID_ARG, "points pointer not aligned to its element");
+  return PDSCP_OK;
+}
+
+bool use_vec(const void* pts, int dtype, int d) {
+  return aligned(pts, 16) && ((size_t)d * elem_size(dtype)) % 16 == 0;
+}
+
+// --- bounds launch (instances live here; the pass is a one-off per solve) ---
+template <typename T>
+struct BoundsLauncher {
+  const BoundsParams& p;
+  cudaStream_t stream;
+  template <int VW, int LPP, int NCH>
+  cudaError_t go() {
+    constexpr int U = Unroll<VW, NCH>::value;
+    auto kern = bounds_kernel<T, VW, LPP, NCH, U>;
+    const int grid = pass_grid(kern, 0, p.n, (32 / LPP) * U * kWarps);
+    kern<<<grid, kBlock, 0, stream>>>(p);
+    return cudaGetLastError();
+  }
+};
+
+cudaError_t launch_bounds(const BoundsParams& p, int dtype, bool vec, cudaStream_t s) {
+  if (dtype == PDSCP_F32) return dispatch_shape<4>(p.d, vec, BoundsLauncher<float>{p, s});
+  return dispatch_shape<8>(p.d, vec, BoundsLauncher<__nv_bfloat16>{p, s});
+}
+
+cudaError_t launch_state_init(int problem, const void* pts, int dtype, int d, int rules, double delta,
+                              int patience, void* state, unsigned int* counter, cudaStream_t s) {
+  if (dtype == PDSCP_F32)
+    state_init_kernel<float><<<1, 256, 0, s>>>((const float*)pts, d, problem, rules, delta, patience, state, counter);
+  else
+    state_init_kernel<__nv_bfloat16>
+        <<<1, 256, 0, s>>>((const __nv_bfloat16*)pts, d, problem, rules, delta, patience, state, counter);
+  return cudaGetLastError();
+}
+
+pdscp_status do_step(int problem, const void* pts, int dtype, const float* radii, const int8_t* labels,
+                     int64_t n, int d, double alpha, double eta_over_rho, double D, int eval_only,
+                     void* state, void* ws, cudaStream_t stream, pdscp_step_out* out) {
+  const Layout L = layout(problem, d);
+  const bool vec = use_vec(pts, dtype, d);
+  unsigned int* counter = reinterpret_cast<unsigned int*>(ws);
+  float* partials = reinterpret_cast<float*>(reinterpret_cast<char*>(ws) + L.partials);
+  cudaError_t e;
+  if (problem == PDSCP_SES) {
+    SesParams p{pts, radii, n, d, eval_only, alpha, eta_over_rho, state, partials, counter, out};
+    e = launch_ses(p, dtype, vec, stream);
+  } else {
+    SvmParams p{pts, labels, n, d, eval_only, alpha, eta_over_rho, D, state, partials, counter, out};
+    e = launch_svm(p, dtype, vec, stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "mwu_step launch");
+  return PDSCP_OK;
+}
+
+}  // namespace
+
+int device_sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (cached[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
+}  // namespace pdscp
+
+using namespace pdscp;
+
+extern "C" {
+
+int32_t pdscp_version(void) { return 100; }
+
+const char* pdscp_last_error(void) { return g_err.c_str(); }
+
+pdscp_status pdscp_workspace_size(int32_t problem, int64_t n, int32_t d, size_t* bytes) {
+  if (!bytes) return fail(PDSCP_ERR_INVALID_ARG, "bytes pointer is null");
+  if (problem != PDSCP_SES && problem != PDSCP_SVM) return fail(PDSCP_ERR_INVALID_ARG, "unknown problem %d", problem);
+  if (d < 1 || d > PDSCP_MAX_D) return fail(PDSCP_ERR_NOT_IMPLEMENTED, "d=%d outside [1, %d]", d, PDSCP_MAX_D);
+  if (n < 1) return fail(PDSCP_ERR_INVALID_ARG, "n must be >= 1");
+  *bytes = layout(problem, d).total;
+  return PDSCP_OK;
+}
+
+pdscp_status pdscp_state_size(int32_t problem, int32_t d, size_t* bytes) {
+  if (!bytes) return fail(PDSCP_ERR_INVALID_ARG, "bytes pointer is null");
+  if (problem != PDSCP_SES && problem != PDSCP_SVM) return fail(PDSCP_ERR_INVALID_ARG, "unknown problem %d", problem);
+  if (d < 1 || d > PDSCP_MAX_D) return fail(PDSCP_ERR_NOT_IMPLEMENTED, "d=%d outside [1, %d]", d, PDSCP_MAX_D);
+  *bytes = state_bytes(d);
+  return PDSCP_OK;
+}
+
+pdscp_status pdscp_bounds(int32_t problem, const void* pts, int32_t dtype, const float* radii, int64_t n,
+                          int32_t d, void* ws, size_t ws_bytes, pdscp_stream stream, double* D_dev) {
+  pdscp_status st = check_common(problem, pts, dtype, n, d);
+  if (st != PDSCP_OK) return st;
+  if (!ws || !D_dev) return fail(PDSCP_ERR_INVALID_ARG, "workspace or output pointer is null");
+  if (!aligned(ws, 16) || !aligned(D_dev, 8)) return fail(PDSCP_ERR_INVALID_ARG, "misaligned workspace/output");
+  const Layout L = layout(problem, d);
+  if (ws_bytes < L.state) return fail(PDSCP_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws_bytes, L.state);
+  BoundsParams p{pts, problem == PDSCP_SES ? radii : nullptr, n, d, problem,
+                 reinterpret_cast<float*>(reinterpret_cast<char*>(ws) + L.partials),
+                 reinterpret_cast<unsigned int*>(ws), D_dev};
+  cudaError_t e = launch_bounds(p, dtype, use_vec(pts, dtype, d), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bounds launch");
+  return PDSCP_OK;
+}
+
+pdscp_status mwu_state_init(int32_t problem, const void* pts, int32_t dtype, int64_t n, int32_t d, int32_t rules,
+                            double delta, int32_t patience, void* state, void* ws, size_t ws_bytes,
+                            pdscp_stream stream) {
+  pdscp_status st = check_common(problem, pts, dtype, n, d);
+  if (st != PDSCP_OK) return st;
+  if (!state || !ws) return fail(PDSCP_ERR_INVALID_ARG, "state or workspace pointer is null");
+  if (!aligned(state, 16) || !aligned(ws, 16)) return fail(PDSCP_ERR_INVALID_ARG, "state/workspace not 16-byte aligned");
+  if (rules != PDSCP_RULES_NONE && rules != PDSCP_RULES_PRACTICAL) return fail(PDSCP_ERR_INVALID_ARG, "unknown rules %d", rules);
+  if (!(delta >= 0.0) || patience < 1) return fail(PDSCP_ERR_INVALID_ARG, "delta must be >= 0 and patience >= 1");
+  if (ws_bytes < layout(problem, d).state) return fail(PDSCP_ERR_WORKSPACE, "workspace too small");
+  cudaError_t e = launch_state_init(problem, pts, dtype, d, rules, delta, patience, state,
+                                    reinterpret_cast<unsigned int*>(ws), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "state init launch");
+  return PDSCP_OK;
+}
+
+pdscp_status mwu_step(int32_t problem, const void* pts, int32_t dtype, const float* radii, const int8_t* labels,
+                      int64_t n, int32_t d, double alpha, double eta_over_rho, double D, int32_t eval_only,
+                      void* state, void* ws, size_t ws_bytes, pdscp_stream stream, pdscp_step_out* out) {
+  pdscp_status st = check_common(problem, pts, dtype, n, d);
+  if (st != PDSCP_OK) return st;
+  if (!state || !ws) return fail(PDSCP_ERR_INVALID_ARG, "state or workspace pointer is null");
+  if (!aligned(state, 16) || !aligned(ws, 16)) return fail(PDSCP_ERR_INVALID_ARG, "state/workspace not 16-byte aligned");
+  if (out && !aligned(out, 8)) return fail(PDSCP_ERR_INVALID_ARG, "out pointer not 8-byte aligned");
+  if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(PDSCP_ERR_INVALID_ARG, "alpha must be finite and > 0");
+  if (!(eta_over_rho >= 0.0) || !std::isfinite(eta_over_rho)) return fail(PDSCP_ERR_INVALID_ARG, "eta/rho must be finite and >= 0");
+  if (problem == PDSCP_SVM) {
+    if (!labels) return fail(PDSCP_ERR_INVALID_ARG, "SVM needs labels");
+    if (!(D > 0.0) || !std::isfinite(D)) return fail(PDSCP_ERR_INVALID_ARG, "SVM needs D > 0 (the largest point norm)");
+  }
+  if (ws_bytes < layout(problem, d).state) return fail(PDSCP_ERR_WORKSPACE, "workspace too small");
+  return do_step(problem, pts, dtype, problem == PDSCP_SES ? radii : nullptr, labels, n, d, alpha, eta_over_rho, D,
+                 eval_only, state, ws, (cudaStream_t)stream, out);
+}
+
+pdscp_status mwu_state_read(int32_t problem, int32_t d, const void* state, float* mean_dev, float* best_dev,
+                            pdscp_stream stream) {
+  if (problem != PDSCP_SES && problem != PDSCP_SVM) return fail(PDSCP_ERR_INVALID_ARG, "unknown problem %d", problem);
+  if (d < 1 || d > PDSCP_MAX_D) return fail(PDSCP_ERR_NOT_IMPLEMENTED, "d outside range");
+  if (!state) return fail(PDSCP_ERR_INVALID_ARG, "state pointer is null");
+  state_read_kernel<<<1, 256, 0, (cudaStream_t)stream>>>(d, problem, state, mean_dev, best_dev);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "state read launch");
+  return PDSCP_OK;
+}
+
+pdscp_status mwu_state_set(int32_t problem, const void* pts, int32_t dtype, const float* radii,
+                           const int8_t* labels, int64_t n, int32_t d, int64_t t, const double* mean_dev, double D,
+                           void* state, void* ws, size_t ws_bytes, pdscp_stream stream) {
+  pdscp_status st = check_common(problem, pts, dtype, n, d);
+  if (st != PDSCP_OK) return st;
+  if (!state || !ws || !mean_dev) return fail(PDSCP_ERR_INVALID_ARG, "state, workspace or mean pointer is null");
+  if (!aligned(state, 16) || !aligned(ws, 16) || !aligned(mean_dev, 8))
+    return fail(PDSCP_ERR_INVALID_ARG, "misaligned state/workspace/mean");
+  if (t < 0) return fail(PDSCP_ERR_INVALID_ARG, "t must be >= 0");
+  if (problem == PDSCP_SVM && (!labels || !(D > 0.0))) return fail(PDSCP_ERR_INVALID_ARG, "SVM needs labels and D > 0");
+  if (ws_bytes < layout(problem, d).state) return fail(PDSCP_ERR_WORKSPACE, "workspace too small");
+  state_set_kernel<<<1, 256, 0, (cudaStream_t)stream>>>(d, problem, t, mean_dev, state, reinterpret_cast<unsigned int*>(ws));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "state set launch");
+  // evaluation pass at the mean: sets the shift bound (hint) and f
+  return do_step(problem, pts, dtype, problem == PDSCP_SES ? radii : nullptr, labels, n, d, 1.0, 0.0,
+                 problem == PDSCP_SVM ? D : 0.0, 1, state, ws, (cudaStream_t)stream, nullptr);
+}
+
+pdscp_status mwu_backward(int32_t, const void*, int32_t, const int8_t*, int64_t, int32_t, double, double, double,
+                          int64_t, int32_t, void*, size_t, pdscp_stream, float*) {
+  return fail(PDSCP_ERR_NOT_IMPLEMENTED, "mwu_backward is not built yet");
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Search drivers
+// ---------------------------------------------------------------------------
+namespace {
+
+struct FtpResult {
+  StateHdr hdr;
+  int64_t iters;
+};
+
+pdscp_status check_opts(const pdscp_options* o) {
+  if (!o) return fail(PDSCP_ERR_INVALID_ARG, "options pointer is null");
+  if (!(o->eps > 0.0) || !std::isfinite(o->eps)) return fail(PDSCP_ERR_INVALID_ARG, "eps must be > 0");
+  if (!(o->delta >= 0.0)) return fail(PDSCP_ERR_INVALID_ARG, "delta must be >= 0");
+  if (o->patience < 1) return fail(PDSCP_ERR_INVALID_ARG, "patience must be >= 1");
+  if (o->mode != PDSCP_MODE_PRACTICAL && o->mode != PDSCP_MODE_THEORY) return fail(PDSCP_ERR_INVALID_ARG, "unknown mode");
+  if (o->max_iters < 1) return fail(PDSCP_ERR_INVALID_ARG, "max_iters must be >= 1");
+  if (o->poll_every < 1 || o->poll_every > kRing) return fail(PDSCP_ERR_INVALID_ARG, "poll_every outside [1, %d]", kRing);
+  if (o->max_steps < 1) return fail(PDSCP_ERR_INVALID_ARG, "max_steps must be >= 1");
+  if (!(o->eta >= 0.0) || o->eta > 1.0) return fail(PDSCP_ERR_INVALID_ARG, "eta must be 0 (theorem) or in (0, 1]");
+  return PDSCP_OK;
+}
+
+// Runs one alpha-FTP on the device: T (capped by budget) iterations, polling
+// the state every poll_every launches; evaluates f at the final mean when the
+// loop ended without a stop (as the oracle's end-of-FTP evaluation does).
+pdscp_status run_ftp(int problem, const void* pts, int dtype, const float* radii, const int8_t* labels, int64_t n,
+                     int d, double alpha, double eta_over_rho, double D, int rules, const pdscp_options* o,
+                     int64_t budget, void* ws, size_t ws_bytes, cudaStream_t s, FtpResult* res) {
+  const Layout L = layout(problem, d);
+  void* state = reinterpret_cast<char*>(ws) + L.state;
+  pdscp_step_out* ring = reinterpret_cast<pdscp_step_out*>(reinterpret_cast<char*>(ws) + L.ring);
+  pdscp_status st = mwu_state_init(problem, pts, dtype, n, d, rules, o->delta, o->patience, state, ws, ws_bytes,
+                                   (pdscp_stream)s);
+  if (st != PDSCP_OK) return st;
+  int64_t ran = 0;
+  StateHdr h;
+  bool stopped = false;
+  while (ran < budget) {
+    const int64_t chunk = std::min<int64_t>(o->poll_every, budget - ran);
+    for (int64_t j = 0; j < chunk; ++j) {
+      st = do_step(problem, pts, dtype, radii, labels, n, d, alpha, eta_over_rho, D, 0, state, ws, s, ring + j);
+      if (st != PDSCP_OK) return st;
+    }
+    ran += chunk;
+    cudaError_t e = cudaMemcpyAsync(&h, state, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "ftp poll");
+    if (h.status != PDSCP_OK) return fail((pdscp_status)h.status, "device status %d in alpha-FTP", h.status);
+    if (h.stopped) {
+      stopped = true;
+      break;
+    }
+  }
+  if (!stopped) {
+    st = do_step(problem, pts, dtype, radii, labels, n, d, alpha, eta_over_rho, D, 1, state, ws, s, nullptr);
+    if (st != PDSCP_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(&h, state, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "ftp final read");
+  }
+  res->hdr = h;
+  res->iters = h.t;
+  return PDSCP_OK;
+}
+
+int64_t theorem_T(double c, double D, double logr, double eps_i, double alpha) {
+  const double T = std::ceil(c * D * D * logr / (eps_i * eps_i * alpha * alpha));
+  return T > 4.0e18 ? (int64_t)4e18 : (int64_t)T;
+}
+
+}  // namespace
+
+extern "C" {
+
+pdscp_status ses_solve(const void* pts, int32_t dtype, const float* radii, int64_t n, int32_t d,
+                       const pdscp_options* o, void* ws, size_t ws_bytes, pdscp_stream stream, float* center,
+                       pdscp_report* rep) {
+  pdscp_status st = check_common(PDSCP_SES, pts, dtype, n, d);
+  if (st != PDSCP_OK) return st;
+  if ((st = check_opts(o)) != PDSCP_OK) return st;
+  if (!ws || !center || !rep) return fail(PDSCP_ERR_INVALID_ARG, "null workspace/center/report pointer");
+  if (!aligned(ws, 256)) return fail(PDSCP_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  const Layout L = layout(PDSCP_SES, d);
+  if (ws_bytes < L.total) return fail(PDSCP_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws_bytes, L.total);
+  cudaStream_t s = (cudaStream_t)stream;
+  memset(rep, 0, sizeof(*rep));
+  double* Ddev = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + L.dval);
+  if ((st = mwu_state_init(PDSCP_SES, pts, dtype, n, d, 0, 0.0, 1, reinterpret_cast<char*>(ws) + L.state, ws,
+                           ws_bytes, stream)) != PDSCP_OK)
+    return st;
+  if ((st = pdscp_bounds(PDSCP_SES, pts, dtype, radii, n, d, ws, ws_bytes, stream, Ddev)) != PDSCP_OK) return st;
+  double D = 0.0;
+  cudaError_t e = cudaMemcpyAsync(&D, Ddev, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "bounds read");
+  if (!std::isfinite(D)) return fail(PDSCP_ERR_NUMERIC, "bounds pass produced a non-finite D");
+  rep->D = D;
+  const size_t esz = elem_size(dtype);
+  float gam1 = 0.f;
+  if (radii) {
+    e = cudaMemcpyAsync(&gam1, radii, sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "radius read");
+  }
+  // centre fallback: v_1 with radius D encloses every sphere
+  auto copy_v1 = [&]() -> pdscp_status {
+    void* st0 = reinterpret_cast<char*>(ws) + L.state;
+    if (mwu_state_init(PDSCP_SES, pts, dtype, n, d, 0, 0.0, 1, st0, ws, ws_bytes, stream) != PDSCP_OK) return PDSCP_ERR_CUDA;
+    return mwu_state_read(PDSCP_SES, d, st0, center, nullptr, stream);
+  };
+  (void)esz;
+  if (D <= 0.0) {  // all spheres share a centre and have radius 0
+    if ((st = copy_v1()) != PDSCP_OK) return st;
+    rep->value = rep->lower_bound = rep->upper_bound = 0.0;
+    rep->status = PDSCP_OK;
+    return PDSCP_OK;
+  }
+  const double rho = 3.0 * D / std::sqrt(2.0);
+  const double logr = std::log(2.0 * (double)(n - 1));
+  double Lo = D / 2.0, Up = D, lb = 0.0, ub = INFINITY;
+  int64_t total = 0;
+  int steps = 0;
+  bool have_center = false;
+  const double eps = o->eps;
+  const int rules = o->mode == PDSCP_MODE_PRACTICAL ? PDSCP_RULES_PRACTICAL : PDSCP_RULES_NONE;
+  while (Up > (1.0 + eps) * Lo && ub > (1.0 + eps) * lb && total < o->max_iters && steps < o->max_steps) {
+    const double alpha = Lo + (Up - Lo) / 3.0;
+    const double eps_i = (Up - Lo) / (3.0 * alpha);
+    const int64_t T = theorem_T(36.0, D, logr, eps_i, alpha);
+    const double eta = o->eta > 0.0 ? o->eta : std::sqrt(logr / (double)T);
+    const int64_t budget = std::min<int64_t>(T, o->max_iters - total);
+    FtpResult r;
+    if ((st = run_ftp(PDSCP_SES, pts, dtype, radii, nullptr, n, d, alpha, eta / rho, 0.0, rules, o, budget, ws,
+                      ws_bytes, s, &r)) != PDSCP_OK)
+      return st;
+    total += r.iters;
+    if (r.hdr.best_f < ub) {
+      ub = r.hdr.best_f;
+      if ((st = mwu_state_read(PDSCP_SES, d, reinterpret_cast<char*>(ws) + L.state, nullptr, center, stream)) != PDSCP_OK)
+        return st;
+      have_center = true;
+    }
+    if (r.hdr.lb_best > lb) lb = r.hdr.lb_best;
+    const int oc = r.hdr.stopped ? r.hdr.outcome : PDSCP_OUT_RUNNING;
+    if (oc == PDSCP_OUT_SEPARATED) {
+      Lo = std::max(Lo, alpha);
+    } else if (r.iters >= T || oc == PDSCP_OUT_STALLED || oc == PDSCP_OUT_BEAT_ALPHA) {
+      Up = std::min(std::min(Up, (1.0 + eps_i) * alpha), ub);
+    }
+    Lo = std::max(Lo, lb);
+    ++steps;
+    if (oc == PDSCP_OUT_RUNNING && r.iters < T) break;  // budget spent inside the step
+  }
+  if (!have_center) {
+    if ((st = copy_v1()) != PDSCP_OK) return st;
+    ub = D;
+  }
+  (void)gam1;
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "ses_solve final sync");
+  rep->value = ub;
+  rep->lower_bound = lb;
+  rep->upper_bound = ub;
+  rep->search_L = Lo;
+  rep->search_U = Up;
+  rep->iters = total;
+  rep->search_steps = steps;
+  const bool done = Up <= (1.0 + eps) * Lo || ub <= (1.0 + eps) * lb;
+  rep->status = done ? PDSCP_OK : PDSCP_ERR_NOT_CONVERGED;
+  if (!done) fail(PDSCP_ERR_NOT_CONVERGED, "iteration budget spent (range [%g, %g], certificate [%g, %g])", Lo, Up, lb, ub);
+  return (pdscp_status)rep->status;
+}
+
+pdscp_status svm_solve(const void* X, int32_t dtype, const int8_t* labels, int64_t n, int32_t d,
+                       const pdscp_options* o, void* ws, size_t ws_bytes, pdscp_stream stream, float* w_out,
+                       pdscp_report* rep) {
+  pdscp_status st = check_common(PDSCP_SVM, X, dtype, n, d);
+  if (st != PDSCP_OK) return st;
+  if ((st = check_opts(o)) != PDSCP_OK) return st;
+  if (!labels || !ws || !w_out || !rep) return fail(PDSCP_ERR_INVALID_ARG, "null labels/workspace/w/report pointer");
+  if (!aligned(ws, 256)) return fail(PDSCP_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  const Layout L = layout(PDSCP_SVM, d);
+  if (ws_bytes < L.total) return fail(PDSCP_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws_bytes, L.total);
+  cudaStream_t s = (cudaStream_t)stream;
+  memset(rep, 0, sizeof(*rep));
+  double* Ddev = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + L.dval);
+  if ((st = mwu_state_init(PDSCP_SVM, X, dtype, n, d, 0, 0.0, 1, reinterpret_cast<char*>(ws) + L.state, ws, ws_bytes,
+                           stream)) != PDSCP_OK)
+    return st;
+  if ((st = pdscp_bounds(PDSCP_SVM, X, dtype, nullptr, n, d, ws, ws_bytes, stream, Ddev)) != PDSCP_OK) return st;
+  double D = 0.0;
+  cudaError_t e = cudaMemcpyAsync(&D, Ddev, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "bounds read");
+  if (!(D > 0.0) || !std::isfinite(D)) return fail(PDSCP_ERR_NUMERIC, "largest point norm D=%g is not positive", D);
+  rep->D = D;
+  const double rho = 2.0 * D;
+  const double logr = std::log((double)n);
+  double Lo = 0.0, Up = 2.0 * D, lb = 0.0, ub = INFINITY;
+  int64_t total = 0;
+  int steps = 0;
+  bool have_w = false;
+  const double eps = o->eps;
+  const int rules = o->mode == PDSCP_MODE_PRACTICAL ? PDSCP_RULES_PRACTICAL : PDSCP_RULES_NONE;
+  while (Up > (1.0 + eps) * Lo && ub > (1.0 + eps) * lb && total < o->max_iters && steps < o->max_steps) {
+    const double alpha = Up - (Up - Lo) / 3.0;
+    const double eps_i = (Up - Lo) / (3.0 * alpha);
+    const int64_t T = theorem_T(64.0, D, logr, eps_i, alpha);
+    const double eta = o->eta > 0.0 ? o->eta : std::sqrt(logr / (double)T);
+    const int64_t budget = std::min<int64_t>(T, o->max_iters - total);
+    FtpResult r;
+    if ((st = run_ftp(PDSCP_SVM, X, dtype, nullptr, labels, n, d, alpha, eta / rho, D, rules, o, budget, ws, ws_bytes,
+                      s, &r)) != PDSCP_OK)
+      return st;
+    total += r.iters;
+    if (r.hdr.best_f > lb) {
+      lb = r.hdr.best_f;
+      if ((st = mwu_state_read(PDSCP_SVM, d, reinterpret_cast<char*>(ws) + L.state, nullptr, w_out, stream)) != PDSCP_OK)
+        return st;
+      have_w = true;
+    }
+    if (r.hdr.ub_best < ub) ub = r.hdr.ub_best;
+    const int oc = r.hdr.stopped ? r.hdr.outcome : PDSCP_OUT_RUNNING;
+    if (oc == PDSCP_OUT_SEPARATED) {
+      Up = std::min(Up, alpha);
+    } else if (r.iters >= T || oc == PDSCP_OUT_STALLED || oc == PDSCP_OUT_BEAT_ALPHA) {
+      Lo = std::max(std::max(Lo, (1.0 - eps_i) * alpha), lb);
+    }
+    Up = std::min(Up, ub);
+    Lo = std::max(Lo, lb);
+    ++steps;
+    if (oc == PDSCP_OUT_RUNNING && r.iters < T) break;
+  }
+  if (!have_w) {
+    e = cudaMemsetAsync(w_out, 0, sizeof(float) * d, s);
+    if (e != cudaSuccess) return cuda_fail(e, "w reset");
+  }
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "svm_solve final sync");
+  rep->value = lb;
+  rep->lower_bound = lb;
+  rep->upper_bound = ub;
+  rep->search_L = Lo;
+  rep->search_U = Up;
+  rep->iters = total;
+  rep->search_steps = steps;
+  const bool done = Up <= (1.0 + eps) * Lo || ub <= (1.0 + eps) * lb;
+  rep->status = done ? PDSCP_OK : PDSCP_ERR_NOT_CONVERGED;
+  if (!done) fail(PDSCP_ERR_NOT_CONVERGED, "iteration budget spent (range [%g, %g], certificate [%g, %g])", Lo, Up, lb, ub);
+  return (pdscp_status)rep->status;
+}
+
+}  // extern "C"

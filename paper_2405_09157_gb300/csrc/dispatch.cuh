@@ -1,0 +1,70 @@
+// Shape dispatch shared by the point-pass kernels: picks lanes-per-point and
+// chunks-per-lane for a dimension d (see the table in shape_for()).
+#pragma once
+
+#include "common.cuh"
+
+namespace pdscp {
+
+// Launch configuration of one kernel instance on the current device.
+struct LaunchCfg {
+  int grid;
+  size_t smem;
+  cudaStream_t stream;
+};
+
+int device_sm_count();
+
+// Calls L.template go<VW, LPP, NCH>() for the instance that serves d.
+// vec: rows start on 16-byte boundaries and hold a whole number of 16-byte
+// chunks of VWV elements (VWV = 4 for float32, 8 for bfloat16).
+//   vector path: nch = d / VWV chunks per row; lanes per point = the next
+//     power of two >= nch up to 32, then 2, 4 or 8 chunks per lane;
+//   scalar path: one element per chunk; 2, 8 or 32 lanes per point, then up
+//     to 32 elements per lane.
+template <int VWV, typename L>
+cudaError_t dispatch_shape(int d, bool vec, L&& l) {
+  if (vec) {
+    const int nch = d / VWV;
+    if (nch <= 1) return l.template go<VWV, 1, 1>();
+    if (nch <= 2) return l.template go<VWV, 2, 1>();
+    if (nch <= 4) return l.template go<VWV, 4, 1>();
+    if (nch <= 8) return l.template go<VWV, 8, 1>();
+    if (nch <= 16) return l.template go<VWV, 16, 1>();
+    if (nch <= 32) return l.template go<VWV, 32, 1>();
+    if (nch <= 64) return l.template go<VWV, 32, 2>();
+    if (nch <= 128) return l.template go<VWV, 32, 4>();
+    if (nch <= 256) return l.template go<VWV, 32, 8>();
+    return cudaErrorInvalidValue;
+  }
+  if (d <= 2) return l.template go<1, 2, 1>();
+  if (d <= 8) return l.template go<1, 8, 1>();
+  if (d <= 32) return l.template go<1, 32, 1>();
+  if (d <= 64) return l.template go<1, 32, 2>();
+  if (d <= 128) return l.template go<1, 32, 4>();
+  if (d <= 256) return l.template go<1, 32, 8>();
+  if (d <= 512) return l.template go<1, 32, 16>();
+  if (d <= 1024) return l.template go<1, 32, 32>();
+  return cudaErrorInvalidValue;
+}
+
+// Points in flight per lane group, by the number of floats a lane holds.
+template <int VW, int NCH>
+struct Unroll {
+  static constexpr int value = (VW * NCH <= 8) ? 4 : ((VW * NCH <= 16) ? 2 : 1);
+};
+
+// Grid for a point pass: enough CTAs to fill every SM at the occupancy the
+// instance allows (at most kMaxBlocksPerSM per SM), no more than the work needs.
+template <typename KernelFn>
+int pass_grid(KernelFn kern, size_t smem, int64_t n, int points_per_cta_step) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBlock, smem) != cudaSuccess || occ < 1) occ = 1;
+  if (occ > kMaxBlocksPerSM) occ = kMaxBlocksPerSM;
+  const int64_t full = (int64_t)device_sm_count() * occ;
+  int64_t need = (n + points_per_cta_step - 1) / points_per_cta_step;
+  if (need < 1) need = 1;
+  return (int)(need < full ? need : full);
+}
+
+}  // namespace pdscp

@@ -1,0 +1,36 @@
+// Instances of the SES iteration kernel (float32 and bfloat16 points).
+#include "dispatch.cuh"
+#include "ses_kernel.cuh"
+
+namespace pdscp {
+
+namespace {
+template <typename T>
+struct SesLauncher {
+  const SesParams& p;
+  cudaStream_t stream;
+  template <int VW, int LPP, int NCH>
+  cudaError_t go() {
+    constexpr int U = Unroll<VW, NCH>::value;
+    auto kern = ses_iter_kernel<T, VW, LPP, NCH, U>;
+    const int dp = dpad4(p.d);
+    size_t smem = (size_t)kWarps * dp * sizeof(float);
+    const size_t fin = (size_t)(4 + dp) * sizeof(double);
+    if (fin > smem) smem = fin;
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    const int grid = pass_grid(kern, smem, p.n, (32 / LPP) * U * kWarps);
+    kern<<<grid, kBlock, smem, stream>>>(p);
+    return cudaGetLastError();
+  }
+};
+}  // namespace
+
+cudaError_t launch_ses(const SesParams& p, int dtype, bool vec, cudaStream_t stream) {
+  if (dtype == PDSCP_F32) return dispatch_shape<4>(p.d, vec, SesLauncher<float>{p, stream});
+  return dispatch_shape<8>(p.d, vec, SesLauncher<__nv_bfloat16>{p, stream});
+}
+
+}  // namespace pdscp

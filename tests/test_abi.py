@@ -1,0 +1,75 @@
+"""The C-ABI library loads and exports every entry point of include/pdscp.h,
+and rejects bad arguments before touching a GPU (CPU-only tests)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2405_09157_gb300 import _ffi, build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "pdscp.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(build.LIB):
+        build.build()
+    return _ffi.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:pdscp_status|int32_t|const char\*)\s+(\w+)\s*\(", src, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported_and_bound(lib):
+    names = declared_functions()
+    assert len(names) >= 11
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in _ffi.SIGNATURES, name
+    assert set(_ffi.SIGNATURES) == set(names)
+
+
+def test_version_and_sizes(lib):
+    assert lib.pdscp_version() >= 100
+    out = ctypes.c_size_t()
+    assert lib.pdscp_state_size(_ffi.SES, 32, ctypes.byref(out)) == 0
+    assert out.value == 128 + 32 * 8 + 2 * 32 * 4
+    assert lib.pdscp_workspace_size(_ffi.SVM, 1000, 128, ctypes.byref(out)) == 0 and out.value > 0
+    assert lib.pdscp_workspace_size(_ffi.SES, 10, 0, ctypes.byref(out)) == 7
+
+
+def test_argument_validation_without_gpu(lib):
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: every call below fails validation first
+    st = lib.mwu_step(_ffi.SES, fake, _ffi.F32, None, None, 1, 4, 1.0, 0.1, 0.0, 0, fake, fake, 1 << 30, None, None)
+    assert st == 1 and b"n >= 2" in lib.pdscp_last_error()
+    st = lib.mwu_step(_ffi.SES, fake, _ffi.F32, None, None, 10, 0, 1.0, 0.1, 0.0, 0, fake, fake, 1 << 30, None, None)
+    assert st == 7
+    st = lib.mwu_step(_ffi.SES, fake, 9, None, None, 10, 4, 1.0, 0.1, 0.0, 0, fake, fake, 1 << 30, None, None)
+    assert st == 1
+    st = lib.mwu_step(_ffi.SES, fake, _ffi.F32, None, None, 10, 4, -1.0, 0.1, 0.0, 0, fake, fake, 1 << 30, None, None)
+    assert st == 1 and b"alpha" in lib.pdscp_last_error()
+    st = lib.mwu_step(_ffi.SVM, fake, _ffi.F32, None, None, 10, 4, 1.0, 0.1, 1.0, 0, fake, fake, 1 << 30, None, None)
+    assert st == 1 and b"labels" in lib.pdscp_last_error()
+    st = lib.mwu_step(_ffi.SVM, fake, _ffi.F32, None, fake, 10, 4, 1.0, 0.1, 0.0, 0, fake, fake, 1 << 30, None, None)
+    assert st == 1 and b"D > 0" in lib.pdscp_last_error()
+    st = lib.mwu_step(_ffi.SES, fake, _ffi.F32, None, None, 10, 4, 1.0, 0.1, 0.0, 0, None, fake, 1 << 30, None, None)
+    assert st == 1
+    st = lib.mwu_step(_ffi.SES, ctypes.c_void_p((1 << 20) + 2), _ffi.F32, None, None, 10, 4, 1.0, 0.1, 0.0, 0,
+                      fake, fake, 1 << 30, None, None)
+    assert st == 1 and b"aligned" in lib.pdscp_last_error()
+    st = lib.mwu_step(_ffi.SES, fake, _ffi.F32, None, None, 10, 4, 1.0, 0.1, 0.0, 0, fake, fake, 16, None, None)
+    assert st == 8
+    opts = _ffi.Options(0.0, 1e-4, 10, 0, 1000, 16, 10, 0.0)
+    rep = _ffi.Report()
+    st = lib.ses_solve(fake, _ffi.F32, None, 10, 4, ctypes.byref(opts), fake, 1 << 30, None, fake, ctypes.byref(rep))
+    assert st == 1 and b"eps" in lib.pdscp_last_error()
+    opts = _ffi.Options(1e-3, 1e-4, 10, 0, 1000, 0, 10, 0.0)
+    st = lib.svm_solve(fake, _ffi.F32, fake, 10, 4, ctypes.byref(opts), fake, 1 << 30, None, fake, ctypes.byref(rep))
+    assert st == 1 and b"poll_every" in lib.pdscp_last_error()
+    st = lib.mwu_backward(_ffi.SES, fake, _ffi.F32, None, 10, 4, 1.0, 0.1, 1.0, 10, 5, fake, 1 << 30, None, fake)
+    assert st == 7
