@@ -41,16 +41,18 @@ constexpr int kRing = 4096;  // step records kept by the solves between polls
 size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t partials, state, ring, dval, total;
+  size_t partials, grows, state, ring, dval, total;
 };
 
-// Workspace: [counter 256 B][per-CTA partials][solve state][step ring][D]
+// Workspace: [counters][per-CTA partial rows (float)][per-group rows (double)]
+//            [solve state][step ring][D]
 Layout layout(int problem, int d) {
   Layout L;
   const int st = problem == PDSCP_SES ? ses_partial_stride(d) : svm_partial_stride(d);
   const size_t rows = (size_t)device_sm_count() * kMaxBlocksPerSM;
   L.partials = kHeadBytes;
-  L.state = L.partials + round256(rows * (size_t)st * sizeof(float));
+  L.grows = L.partials + round256(rows * (size_t)st * sizeof(float));
+  L.state = L.grows + round256((size_t)kMaxGroups * st * sizeof(float2));
   L.ring = L.state + round256(state_bytes(d));
   L.dval = L.ring + round256((size_t)kRing * sizeof(pdscp_step_out));
   L.total = L.dval + 256;
@@ -113,12 +115,13 @@ pdscp_status do_step(int problem, const void* pts, int dtype, const float* radii
   const bool vec = use_vec(pts, dtype, d);
   unsigned int* counter = reinterpret_cast<unsigned int*>(ws);
   float* partials = reinterpret_cast<float*>(reinterpret_cast<char*>(ws) + L.partials);
+  float2* grows = reinterpret_cast<float2*>(reinterpret_cast<char*>(ws) + L.grows);
   cudaError_t e;
   if (problem == PDSCP_SES) {
-    SesParams p{pts, radii, n, d, eval_only, alpha, eta_over_rho, state, partials, counter, out};
+    SesParams p{pts, radii, n, d, eval_only, alpha, eta_over_rho, state, partials, grows, counter, out};
     e = launch_ses(p, dtype, vec, stream);
   } else {
-    SvmParams p{pts, labels, n, d, eval_only, alpha, eta_over_rho, D, state, partials, counter, out};
+    SvmParams p{pts, labels, n, d, eval_only, alpha, eta_over_rho, D, state, partials, grows, counter, out};
     e = launch_svm(p, dtype, vec, stream);
   }
   if (e != cudaSuccess) return cuda_fail(e, "mwu_step launch");

@@ -90,11 +90,14 @@ __global__ void __launch_bounds__(kBlock) bounds_kernel(BoundsParams p) {
     p.partials[blockIdx.x] = b;
   }
   if (!arrive_last(p.counter, &s_last)) return;
-  if (threadIdx.x == 0) {
-    double D = -INFINITY;
-    for (int b = 0; b < (int)gridDim.x; ++b) D = fmax(D, (double)__ldcg(p.partials + b));
-    *p.D_out = D;
-    *p.counter = 0u;
+  if (threadIdx.x < 32) {  // one warp: lanes stride over the CTAs' maxima
+    float D = -INFINITY;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) D = fmaxf(D, __ldcg(p.partials + b));
+    D = warp_max(D);
+    if (threadIdx.x == 0) {
+      *p.D_out = (double)D;
+      *p.counter = 0u;
+    }
   }
 }
 
@@ -135,8 +138,9 @@ __global__ void state_init_kernel(const T* pts, int d, int problem, int rules, d
     h.reserved[0] = 0.0;
     h.reserved[1] = 0.0;
     *hdr = h;
-    if (counter) *counter = 0u;
   }
+  if (counter)
+    for (int j = threadIdx.x; j < (int)(kHeadBytes / sizeof(unsigned int)); j += blockDim.x) counter[j] = 0u;
 }
 
 // Resume from a checkpoint: t and the running mean (FP64; SVM: wbar, then
@@ -177,8 +181,9 @@ __global__ void state_set_kernel(int d, int problem, int64_t t, const double* me
     h.reserved[0] = 0.0;
     h.reserved[1] = 0.0;
     *hdr = h;
-    if (counter) *counter = 0u;
   }
+  if (counter)
+    for (int j = threadIdx.x; j < (int)(kHeadBytes / sizeof(unsigned int)); j += blockDim.x) counter[j] = 0u;
 }
 
 template <int kUnused = 0>

@@ -14,7 +14,8 @@ constexpr double kSqrt2 = 1.41421356237309504880;
 constexpr int kBlock = 256;           // threads per CTA of the point passes
 constexpr int kWarps = kBlock / 32;
 constexpr int kMaxBlocksPerSM = 8;    // upper bound used to size the workspace
-constexpr size_t kHeadBytes = 256;    // workspace: completion counter + flags
+constexpr size_t kHeadBytes = 1024;   // workspace: completion counters (top + per group)
+constexpr int kMaxGroups = 64;        // group rows reserved in the workspace
 
 // ---------------------------------------------------------------------------
 // Device state of one alpha-FTP. 128-byte header, then the running mean in
@@ -157,6 +158,189 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
   return s;
 }
 
+// Column operations of a partial row: 0 sum, 1 max, 2 min.
+// Sums are carried as compensated FP32 pairs (s, c) (Neumaier's variant of
+// Kahan summation): the error of a sum of m terms is about 2^-24 |sum| plus
+// m 2^-48 sum|terms|, i.e. FP64-grade for these reductions, at FP32 speed
+// (FP64 throughput on this GPU is ~1/64 of FP32).
+__device__ __forceinline__ void neu_add(float& s, float& c, float v) {
+  const float t = s + v;
+  c += (fabsf(s) >= fabsf(v)) ? (s - t) + v : (v - t) + s;
+  s = t;
+}
+__device__ __forceinline__ float2 col_init2(int op) {
+  return make_float2(op == 0 ? 0.f : (op == 1 ? -INFINITY : INFINITY), 0.f);
+}
+__device__ __forceinline__ void col_comb2(int op, float2& a, float2 b) {
+  if (op == 0) {
+    neu_add(a.x, a.y, b.x);
+    a.y += b.y;
+  } else {
+    a.x = op == 1 ? fmaxf(a.x, b.x) : fminf(a.x, b.x);
+  }
+}
+__device__ __forceinline__ float2 as_pair(float v) { return make_float2(v, 0.f); }
+__device__ __forceinline__ float2 as_pair(float2 v) { return v; }
+
+// Column-wise reduction of rows [r0, r1) of a row-major (rows x stride)
+// matrix of float or float2 pairs into out[0..stride) (float2 pairs), by
+// every thread of the CTA. The rows are split R ways (R a power of two,
+// R * stride <= blockDim) so each thread issues few loads, all independent;
+// the R partial results are combined in a fixed order (deterministic).
+// opof(pc) gives the operation of column pc. `scratch` holds blockDim
+// float2. Ends with a barrier; every thread must call it.
+template <typename TIn, typename OpOf>
+__device__ void reduce_rows(const TIn* m, int r0, int r1, int stride, float2* out, float2* scratch, OpOf opof) {
+  const int nt = blockDim.x;
+  int R = 1;
+  while (2 * R * stride <= nt && R < 32) R *= 2;
+  if (R == 1) {
+    for (int pc = threadIdx.x; pc < stride; pc += nt) {
+      const int op = opof(pc);
+      float2 acc = col_init2(op);
+#pragma unroll 8
+      for (int r = r0; r < r1; ++r) col_comb2(op, acc, as_pair(__ldcg(m + (size_t)r * stride + pc)));
+      out[pc] = acc;
+    }
+    __syncthreads();
+    return;
+  }
+  const int t = threadIdx.x;
+  if (t < R * stride) {
+    const int pc = t % stride, q = t / stride;
+    const int op = opof(pc);
+    float2 acc = col_init2(op);
+#pragma unroll 8
+    for (int r = r0 + q; r < r1; r += R) col_comb2(op, acc, as_pair(__ldcg(m + (size_t)r * stride + pc)));
+    scratch[q * stride + pc] = acc;
+  }
+  __syncthreads();
+  for (int pc = threadIdx.x; pc < stride; pc += nt) {
+    const int op = opof(pc);
+    float2 acc = scratch[pc];
+    for (int q = 1; q < R; ++q) col_comb2(op, acc, scratch[q * stride + pc]);
+    out[pc] = acc;
+  }
+  __syncthreads();
+}
+
+// Reciprocal and reciprocal square root in FP64 from the FP32 results
+// refined by Newton's iteration (one step for 1/x: r <- r (2 - x r); one
+// step for 1/sqrt(x): y <- y (3 - x y^2) / 2), each step squaring the
+// relative error (2^-24 -> ~2^-47). Far cheaper than FP64 divide/sqrt on
+// this GPU. x must be positive and within the FP32 range.
+__device__ __forceinline__ double recip_d(double x) {
+  const double r = (double)(1.0f / (float)x);
+  return r * (2.0 - x * r);
+}
+__device__ __forceinline__ double rsqrt_d(double x) {
+  const double y = (double)rsqrtf((float)x);
+  return y * (1.5 - 0.5 * x * y * y);
+}
+__device__ __forceinline__ double sqrt_d(double x) { return x > 0.0 ? x * rsqrt_d(x) : 0.0; }
+
+// CTAs per completion group for a grid of nb CTAs (about sqrt(nb)).
+__host__ __device__ inline int group_size(int nb) {
+  int g = 1;
+  while (g * g < nb) ++g;
+  return g;
+}
+
+// Two-level completion. Every CTA has written its partial row (stride
+// floats) to rows[blockIdx.x]. CTA b belongs to group b / gs; the last CTA
+// to arrive in a group reduces the group's rows into grows[group] (pairs),
+// then arrives at the top counter. Returns true in exactly one CTA, the last
+// group reducer to arrive, when every group row is complete. Counters are
+// reset by their last arriver, so the workspace is ready for the next launch.
+// No CTA waits for another: there is no spin anywhere.
+template <typename OpOf>
+__device__ bool arrive_two_level(const float* rows, int stride, float2* grows, unsigned int* counters,
+                                 float2* scratch, bool* s_flag, OpOf opof) {
+  const int nb = gridDim.x;
+  const int gs = group_size(nb);
+  const int g = blockIdx.x / gs;
+  const int r0 = g * gs, r1 = min(nb, r0 + gs);
+  // CTA barrier, then one thread's device-scope fence and atomic: the fence is
+  // cumulative over the writes the barrier ordered before it.
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int prev = atomicAdd(&counters[1 + g], 1u);
+    __threadfence();
+    *s_flag = (prev == (unsigned int)(r1 - r0 - 1));
+  }
+  __syncthreads();
+  if (!*s_flag) return false;
+  reduce_rows(rows, r0, r1, stride, grows + (size_t)g * stride, scratch, opof);  // ends with a barrier
+  const int G = (nb + gs - 1) / gs;
+  if (threadIdx.x == 0) {
+    counters[1 + g] = 0u;
+    __threadfence();
+    const unsigned int prev = atomicAdd(&counters[0], 1u);
+    __threadfence();
+    *s_flag = (prev == (unsigned int)(G - 1));
+  }
+  __syncthreads();
+  if (!*s_flag) return false;
+  if (threadIdx.x == 0) counters[0] = 0u;
+  return true;
+}
+
+// Two sums at once over the whole block (same barriers as block_sum_d).
+__device__ __forceinline__ void block_sum2_d(double& a, double& b, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  a = warp_sum_d(a);
+  b = warp_sum_d(b);
+  __syncthreads();
+  if (lane == 0) {
+    red[warp] = a;
+    red[16 + warp] = b;
+  }
+  __syncthreads();
+  double sa = 0.0, sb = 0.0;
+  for (int w = 0; w < nw; ++w) {
+    sa += red[w];
+    sb += red[16 + w];
+  }
+  a = sa;
+  b = sb;
+}
+
+// Sums of up to four doubles per thread over the whole block in one pass
+// (fixed order, deterministic); every thread gets the totals. `red` holds
+// 4 * 32 doubles. Contains barriers: every thread must call it.
+template <int K>
+__device__ __forceinline__ void block_sum_k(double (&v)[K], double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[k * 32 + warp] = v[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = red[k * 32];
+    for (int w = 1; w < nw; ++w) s += red[k * 32 + w];
+    v[k] = s;
+  }
+}
+
+// Warp-wide sums of K doubles (fixed butterfly order: every lane gets the
+// same, deterministic totals).
+template <int K>
+__device__ __forceinline__ void warp_sum_k(double (&v)[K]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+}
+
 // Completion counter: the CTA whose arrival is the last one runs the O(d)
 // finalize. Returns true in every thread of that CTA. The writes of the
 // partial row must precede the call.
@@ -172,5 +356,58 @@ __device__ __forceinline__ bool arrive_last(unsigned int* counter, bool* flag_sm
   if (last) __threadfence();
   return last;
 }
+
+}  // namespace pdscp
+
+namespace pdscp {
+
+// Reduce-scatter across the LPP lanes of a lane group. On entry v[r] is this
+// lane's partial sum for point r (r < NI). Stage s (xor-mask m = LPP >> (s+1))
+// keeps the upper half of the remaining points in the lane whose bit m is set
+// and adds the other half received from its partner.
+//   NI >= LPP: after log2(LPP) stages v[k], k < NI/LPP, holds the full sum for
+//              point r = (NI/LPP) * gl + k (gl = lane index in the group);
+//   NI <  LPP: after log2(NI) stages a butterfly over the remaining masks
+//              leaves in v[0] the full sum for point r = gl / (LPP/NI), held by
+//              LPP/NI lanes.
+template <int LPP, int NI>
+struct GroupScatter {
+  static_assert((NI & (NI - 1)) == 0 && (LPP & (LPP - 1)) == 0, "powers of two");
+  static constexpr int OWN = NI >= LPP ? NI / LPP : 1;    // points owned per lane
+  static constexpr int SHARE = NI >= LPP ? 1 : LPP / NI;  // lanes per owned point
+  static constexpr int STAGES = (NI >= LPP ? LPP : NI) == 1 ? 0 : __builtin_ctz(NI >= LPP ? LPP : NI);
+
+  static __device__ __forceinline__ void run(float (&v)[NI], int gl) {
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) {
+      const int m = LPP >> (s + 1);
+      const int half = NI >> (s + 1);
+      const bool upper = (gl & m) != 0;
+#pragma unroll
+      for (int i = 0; i < half; ++i) {
+        const float send = upper ? v[i] : v[i + half];
+        const float keep = upper ? v[i + half] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+      }
+    }
+    if (NI < LPP) {
+#pragma unroll
+      for (int m = SHARE / 2; m > 0; m >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], m);
+    }
+  }
+  // index (0..NI-1) of the k-th point owned by lane gl
+  static __device__ __forceinline__ int owned(int gl, int k) { return NI >= LPP ? OWN * gl + k : gl / SHARE; }
+  // lane (within the group) and slot holding point r's result
+  static __device__ __forceinline__ int src_lane(int r) { return (r / OWN) * SHARE; }
+};
+
+// Points per round for the reduce-scatter kernels: enough 16-byte loads in
+// flight per lane (>= 8) with at most 64 point values held in registers.
+template <int VW, int LPP>
+struct RoundSize {
+  static constexpr int a = LPP > 8 ? LPP : 8;
+  static constexpr int cap = 64 / VW;
+  static constexpr int value = a < cap ? a : cap;
+};
 
 }  // namespace pdscp

@@ -40,13 +40,14 @@ struct SesParams {
   double alpha;
   double eta_over_rho;
   void* state;
-  float* partials;
-  unsigned int* counter;
-  pdscp_step_out* out;  // may be null
+  float* partials;       // one row of ses_partial_stride(d) floats per CTA
+  float2* grows;         // one compensated-FP32 row per completion group
+  unsigned int* counter; // completion counters: [0] top, [1 + g] group g
+  pdscp_step_out* out;   // may be null
 };
 
 template <typename T>
-__device__ void ses_finalize(const SesParams& p, double* sD, double* s_red, double* s_bc);
+__device__ void ses_finish(const SesParams& p, unsigned char* smem_raw);
 
 // T: element type of the points; VW: elements per chunk; LPP: lanes per point
 // (power of two); NCH: chunks per lane; U: points in flight per lane group.
@@ -54,9 +55,6 @@ template <typename T, int VW, int LPP, int NCH, int U>
 __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float s_sc[kWarps][3];
-  __shared__ double s_red[32];
-  __shared__ double s_bc[8];
-  __shared__ bool s_last;
 
   StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
   if (hdr->stopped && !p.eval_only) return;
@@ -185,129 +183,140 @@ __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
     prow[2] = m;
     prow[3] = 0.f;
   }
-  if (!arrive_last(p.counter, &s_last)) return;
-  ses_finalize<T>(p, reinterpret_cast<double*>(smem_raw), s_red, s_bc);
+  ses_finish<T>(p, smem_raw);
 }
 
-// O(d) finish of one SES iteration, run by every thread of the last CTA.
+// O(d) finish of one SES iteration. Every CTA calls it after writing its
+// partial row [S, Wt, maxd, 0, G'_1..G'_d]; the two-level completion elects
+// one CTA, which reduces the group rows in FP64 and does the rest.
 template <typename T>
-__device__ void ses_finalize(const SesParams& p, double* sD, double* s_red, double* s_bc) {
+__device__ void ses_finish(const SesParams& p, unsigned char* smem_raw) {
+  __shared__ float2 s_scr[kBlock];
+  __shared__ __align__(16) double s_hdr[sizeof(StateHdr) / 8];
+  __shared__ bool s_flag;
   const int d = p.d;
-  const int nb = gridDim.x;
   const int st = ses_partial_stride(d);
+  auto opof = [](int pc) { return pc == 2 ? 1 : 0; };  // maxd is a max, the rest sums
+  if (!arrive_two_level(p.partials, st, p.grows, p.counter, s_scr, &s_flag, opof)) return;
+
   StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
   double* mean = state_mean(p.state);
   float* mean32 = state_mean32(p.state, d);
   float* best = state_best(p.state, d);
   const T* pts = reinterpret_cast<const T*>(p.pts);
-
-  // column sums of the per-CTA partials, in FP64, fixed order
-  for (int col = threadIdx.x; col < 3 + d; col += blockDim.x) {
-    if (col == 2) {
-      double m = -INFINITY;
-      for (int b = 0; b < nb; ++b) m = fmax(m, (double)__ldcg(p.partials + (size_t)b * st + 2));
-      sD[2] = m;
-    } else {
-      const int pc = col < 2 ? col : col + 1;
-      double s = 0.0;
-      for (int b = 0; b < nb; ++b) s += (double)__ldcg(p.partials + (size_t)b * st + pc);
-      sD[col] = s;
-    }
+  const int tid = threadIdx.x;
+  const int dp = dpad4(d);
+  // dynamic shared memory: column totals as (s, c) pairs | mean | v_1
+  float2* raw = reinterpret_cast<float2*>(smem_raw);
+  double* s_mean = reinterpret_cast<double*>(smem_raw) + st;
+  double* s_v1 = s_mean + dp;
+  // loads the finish needs, issued before the reduction so their latency overlaps it
+  constexpr int HW = (int)(sizeof(StateHdr) / 8);
+  const double hw = tid < HW ? reinterpret_cast<const double*>(hdr)[tid] : 0.0;
+  const double m0 = tid < d ? mean[tid] : 0.0;
+  const double v0 = tid < d ? (double)elem_to_float<T>(pts + tid) : 0.0;
+  const double gam1 = p.radii ? (double)__ldg(p.radii) : 0.0;
+  const int nb = gridDim.x;
+  const int G = (nb + group_size(nb) - 1) / group_size(nb);
+  reduce_rows(p.grows, 0, G, st, raw, s_scr, opof);
+  if (tid < HW) s_hdr[tid] = hw;
+  if (tid < d) {
+    s_mean[tid] = m0;
+    s_v1[tid] = v0;
+  }
+  for (int j = tid + blockDim.x; j < d; j += blockDim.x) {
+    s_mean[j] = mean[j];
+    s_v1[j] = (double)elem_to_float<T>(pts + j);
   }
   __syncthreads();
-  const double S = sD[0], Wt = sD[1], maxd = sD[2];
+  // The O(d) math runs in warp 0 alone: FP64 work is slow on this GPU and
+  // would only contend across warps; no block barrier follows.
+  if (tid >= 32) return;
+  const int lane = tid;
+  const StateHdr& h = *reinterpret_cast<const StateHdr*>(s_hdr);
+  auto tot = [&](int pc) { return (double)raw[pc].x + (double)raw[pc].y; };
+  const double S = tot(0), Wt = tot(1), maxd = (double)raw[2].x;
   const double alpha = p.alpha;
-  const double gam1 = p.radii ? (double)p.radii[0] : 0.0;
-  const double inv = 1.0 / (kSqrt2 * S);  // g = G' / (sqrt2 S)
-
-  double ng2 = 0.0;
-  for (int j = threadIdx.x; j < d; j += blockDim.x) {
-    const double g = sD[3 + j] * inv;
-    ng2 += g * g;
+  const double inv = recip_d(kSqrt2 * S);  // g = G' / (sqrt2 S)
+  // A = |g|^2, B = g . (v_1 - ubar), C = |ubar - v_1|^2
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int j = lane; j < d; j += 32) {
+    const double g = tot(4 + j) * inv;
+    const double dv = s_v1[j] - s_mean[j];
+    acc[0] += g * g;
+    acc[1] += g * dv;
+    acc[2] += dv * dv;
   }
-  ng2 = block_sum_d(ng2, s_red);
-  const double ng = sqrt(ng2);
+  warp_sum_k<3>(acc);
+  const double A = acc[0], B = acc[1], C = acc[2];
   const double rad = alpha - gam1;
-  double gu = 0.0, d1 = 0.0;
-  for (int j = threadIdx.x; j < d; j += blockDim.x) {
-    const double g = sD[3 + j] * inv;
-    const double v1 = (double)elem_to_float<T>(pts + j);
-    const double u = ng > 0.0 ? v1 + rad * g / ng : v1;
-    const double m = mean[j];
-    gu += g * (u - m);
-    d1 += (m - v1) * (m - v1);
-  }
-  gu = block_sum_d(gu, s_red);
-  d1 = block_sum_d(d1, s_red);
-  const double V = gu + Wt * inv;                                // Eq. (ses_oracle) value
-  const double LB = fmax(gam1, alpha - V / (ng + 1.0 / kSqrt2));  // Eq. (primal_construction)
-  const double f = fmax(maxd, sqrt(d1) + gam1);                   // f at the mean read (Sec. 5)
-  const int64_t t = hdr->t;
+  const double rng = A > 0.0 ? rsqrt_d(A) : 0.0;
+  const double ng = A * rng;                 // ||g||
+  const double step = rad * rng;             // u = v_1 + step g  (u = v_1 when g = 0)
+  const double V = B + step * A + Wt * inv;  // g.(u - ubar) + Wt/(sqrt2 S): Eq. (ses_oracle) value
+  const double LB = fmax(gam1, alpha - V * recip_d(ng + 1.0 / kSqrt2));  // Eq. (primal_construction)
+  const double f = fmax(maxd, sqrt_d(C) + gam1);                           // f at the mean read (Sec. 5)
 
-  if (threadIdx.x == 0) {
-    int status = PDSCP_OK;
-    if (!(S > 0.0) || !isfinite(S) || !isfinite(V) || !isfinite(f)) status = PDSCP_ERR_NUMERIC;
-    bool stop = false, failed = false;
-    int outcome = PDSCP_OUT_RUNNING;
-    const bool better = (t > 0 && f < hdr->best_f);
-    if (!p.eval_only) {
-      if (LB > hdr->lb_best) hdr->lb_best = LB;
-      failed = V < 0.0;
-      if (status != PDSCP_OK) {
+  const int64_t t = h.t;
+  int status = PDSCP_OK;
+  if (!(S > 0.0) || !isfinite(S) || !isfinite(V) || !isfinite(f)) status = PDSCP_ERR_NUMERIC;
+  bool stop = false, failed = false;
+  int outcome = PDSCP_OUT_RUNNING;
+  const bool better = (t > 0 && f < h.best_f);
+  int streak = h.streak;
+  bool set_fprev = false;
+  if (!p.eval_only) {
+    failed = V < 0.0;
+    if (status != PDSCP_OK) {
+      stop = true;
+    } else if (failed) {
+      stop = true;
+      outcome = PDSCP_OUT_SEPARATED;
+    } else if (h.rules == PDSCP_RULES_PRACTICAL && t > 0) {
+      if (f < alpha) {
         stop = true;
-      } else if (failed) {
-        stop = true;
-        outcome = PDSCP_OUT_SEPARATED;
-      } else if (hdr->rules == PDSCP_RULES_PRACTICAL && t > 0) {
-        if (f < alpha) {
-          stop = true;
-          outcome = PDSCP_OUT_BEAT_ALPHA;
-        } else {
-          if (hdr->f_prev > 0.0) {
-            hdr->streak = (fabs(f - hdr->f_prev) / hdr->f_prev < hdr->delta) ? hdr->streak + 1 : 0;
-            if (hdr->streak >= hdr->patience) {
-              stop = true;
-              outcome = PDSCP_OUT_STALLED;
-            }
+        outcome = PDSCP_OUT_BEAT_ALPHA;
+      } else {
+        const double fp = h.f_prev;
+        if (fp > 0.0) {
+          streak = (fabs(f - fp) / fp < h.delta) ? streak + 1 : 0;
+          if (streak >= h.patience) {
+            stop = true;
+            outcome = PDSCP_OUT_STALLED;
           }
-          if (!stop) hdr->f_prev = f;
         }
+        set_fprev = !stop;
       }
     }
-    s_bc[0] = better ? 1.0 : 0.0;
-    s_bc[1] = (!p.eval_only && !stop) ? 1.0 : 0.0;
-    s_bc[2] = stop ? 1.0 : 0.0;
-    s_bc[3] = (double)outcome;
-    s_bc[4] = (double)status;
-    s_bc[5] = failed ? 1.0 : 0.0;
   }
-  __syncthreads();
-  const bool better = s_bc[0] != 0.0, advance = s_bc[1] != 0.0;
-  double mv = 0.0;
-  for (int j = threadIdx.x; j < d; j += blockDim.x) {
-    const double m = mean[j];
+  const bool advance = !p.eval_only && !stop;
+  const double rtp1 = recip_d((double)t + 1.0);  // 1 / (t + 1)
+  for (int j = lane; j < d; j += 32) {
+    const double m = s_mean[j];
     if (better) best[j] = (float)m;
     if (advance) {
-      const double g = sD[3 + j] * inv;
-      const double v1 = (double)elem_to_float<T>(pts + j);
-      const double u = ng > 0.0 ? v1 + rad * g / ng : v1;
-      const double nm = m + (u - m) / (double)(t + 1);
+      const double u = s_v1[j] + step * (tot(4 + j) * inv);
+      const double nm = m + (u - m) * rtp1;
       mean[j] = nm;
       mean32[j] = (float)nm;
-      mv += (nm - m) * (nm - m);
     }
   }
-  mv = block_sum_d(mv, s_red);
-  if (threadIdx.x == 0) {
+  if (lane == 0) {
+    if (!p.eval_only && LB > h.lb_best) hdr->lb_best = LB;
+    if (streak != h.streak) hdr->streak = streak;
+    if (set_fprev) hdr->f_prev = f;
     if (better) hdr->best_f = f;
     hdr->hint = maxd;
-    hdr->move = advance ? sqrt(mv) : 0.0;
-    if (advance) hdr->t = t + 1;
-    if (s_bc[2] != 0.0) {
+    // ||ubar^{t+1} - ubar^t|| = ||u - ubar|| / (t+1), ||u - ubar||^2 = C + 2 step B + step^2 A
+    const double mv2 = C + 2.0 * step * B + step * step * A;
+    hdr->move = advance ? rtp1 * sqrt_d(fmax(mv2, 0.0)) * (1.0 + 1e-6) : 0.0;
+    const int64_t tn = t + (advance ? 1 : 0);
+    hdr->t = tn;
+    if (stop) {
       hdr->stopped = 1;
-      hdr->outcome = (int)s_bc[3];
+      hdr->outcome = outcome;
     }
-    if ((int)s_bc[4] != PDSCP_OK) hdr->status = (int)s_bc[4];
+    if (status != PDSCP_OK) hdr->status = status;
     hdr->last_value = V;
     if (p.out) {
       pdscp_step_out o;
@@ -315,16 +324,153 @@ __device__ void ses_finalize(const SesParams& p, double* sD, double* s_red, doub
       o.objective = f;
       o.lower_bound = LB;
       o.upper_bound = f;
-      o.t = hdr->t;
-      o.failed = s_bc[5] != 0.0;
-      o.stopped = hdr->stopped;
-      o.status = (int)s_bc[4];
-      o.outcome = (int)s_bc[3];
+      o.t = tn;
+      o.failed = failed ? 1 : 0;
+      o.stopped = (stop || h.stopped) ? 1 : 0;
+      o.status = status;
+      o.outcome = outcome;
       o.k = (double)t * p.eta_over_rho;
       *p.out = o;
     }
-    *p.counter = 0u;
   }
+}
+
+}  // namespace pdscp
+
+namespace pdscp {
+
+// Vector-path form of ses_iter_kernel for rows of at most 32 chunks: every
+// lane holds one 16-byte chunk of each of NI points per round, and the
+// scalar work of each point (sqrt, exp, expm1, divide) is done once, by the
+// lane that owns the point after a reduce-scatter of the partial squared
+// distances (GroupScatter), instead of on all LPP lanes of the point's group.
+// The weighted sums G' are then accumulated from the broadcast
+// coefficients. Same arithmetic per point as ses_iter_kernel; only the order
+// of the FP32 partial sums differs.
+template <typename T, int VW, int LPP, int NI>
+__global__ void __launch_bounds__(kBlock) ses_iter_t_kernel(SesParams p) {
+  using GS = GroupScatter<LPP, NI>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float s_sc[kWarps][3];
+
+  StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
+  if (hdr->stopped && !p.eval_only) return;
+
+  const int d = p.d;
+  const int dp = dpad4(d);
+  const int nch = d / VW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / LPP, gl = lane % LPP;
+  constexpr int PPW = 32 / LPP;  // points per load instruction per warp
+  const bool owner = (gl % GS::SHARE) == 0;
+  const bool has_chunk = gl < nch;
+
+  const float kr = p.eval_only ? 0.f : (float)((double)hdr->t * p.eta_over_rho / kSqrt2);
+  const float H = (float)(hdr->hint + hdr->move);
+  const float alpha = (float)p.alpha;
+  const float* mean32 = state_mean32(p.state, d);
+
+  float ub[VW], G[VW];
+#pragma unroll
+  for (int e = 0; e < VW; ++e) {
+    ub[e] = has_chunk ? mean32[gl * VW + e] : 0.f;
+    G[e] = 0.f;
+  }
+  float S = 0.f, W = 0.f, maxd = -INFINITY;
+
+  const T* pts = reinterpret_cast<const T*>(p.pts);
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
+  constexpr int ROUND = PPW * NI;
+  for (int64_t base = gw * ROUND; base < p.n; base += nwarps * ROUND) {
+    float x[NI][VW];
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const int64_t i = base + r * PPW + grp;
+      if (i < p.n && has_chunk) {
+        Chunk<T, VW>::load(pts + i * d, gl, x[r]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) x[r][e] = 0.f;
+      }
+    }
+    float part[NI];
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      float a = 0.f;
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        x[r][e] -= ub[e];
+        a = fmaf(x[r][e], x[r][e], a);
+      }
+      part[r] = has_chunk ? a : 0.f;
+    }
+    GS::run(part, gl);
+    float c[GS::OWN];
+#pragma unroll
+    for (int k = 0; k < GS::OWN; ++k) {
+      const int64_t i = base + GS::owned(gl, k) * PPW + grp;
+      c[k] = 0.f;
+      if (i >= 1 && i < p.n) {
+        const float dist = sqrtf(part[k]);
+        const float gam = p.radii ? __ldg(p.radii + i) : 0.f;
+        const float a = alpha - gam;
+        const float E1 = expf(kr * ((dist + gam) - H));
+        const float em = -expm1f(-2.f * kr * dist);
+        const float dif = E1 * em;
+        const float sum = E1 * (2.f - em);
+        c[k] = dist > 0.f ? dif / dist : 2.f * kr * E1;
+        if (owner) {
+          S += sum;
+          W += a * sum - dist * dif;
+          maxd = fmaxf(maxd, dist + gam);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const float cr = __shfl_sync(0xffffffffu, c[r % GS::OWN], grp * LPP + GS::src_lane(r));
+#pragma unroll
+      for (int e = 0; e < VW; ++e) G[e] = fmaf(cr, x[r][e], G[e]);
+    }
+  }
+
+#pragma unroll
+  for (int o = LPP; o < 32; o <<= 1)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) G[e] += __shfl_xor_sync(0xffffffffu, G[e], o);
+  S = warp_sum(S);
+  W = warp_sum(W);
+  maxd = warp_max(maxd);
+  float* sG = reinterpret_cast<float*>(smem_raw);
+  if (grp == 0 && has_chunk)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) sG[warp * dp + gl * VW + e] = G[e];
+  if (lane == 0) {
+    s_sc[warp][0] = S;
+    s_sc[warp][1] = W;
+    s_sc[warp][2] = maxd;
+  }
+  __syncthreads();
+  float* prow = p.partials + (size_t)blockIdx.x * ses_partial_stride(d);
+  for (int j = threadIdx.x; j < d; j += kBlock) {
+    float s = 0.f;
+    for (int w = 0; w < kWarps; ++w) s += sG[w * dp + j];
+    prow[4 + j] = s;
+  }
+  if (threadIdx.x == 0) {
+    float s0 = 0.f, s1 = 0.f, m = -INFINITY;
+    for (int w = 0; w < kWarps; ++w) {
+      s0 += s_sc[w][0];
+      s1 += s_sc[w][1];
+      m = fmaxf(m, s_sc[w][2]);
+    }
+    prow[0] = s0;
+    prow[1] = s1;
+    prow[2] = m;
+    prow[3] = 0.f;
+  }
+  ses_finish<T>(p, smem_raw);
 }
 
 }  // namespace pdscp

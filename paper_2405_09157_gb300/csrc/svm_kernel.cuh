@@ -36,21 +36,19 @@ struct SvmParams {
   double eta_over_rho;
   double D;
   void* state;
-  float* partials;
-  unsigned int* counter;
+  float* partials;       // one row of svm_partial_stride(d) floats per CTA
+  float2* grows;         // one compensated-FP32 row per completion group
+  unsigned int* counter; // completion counters: [0] top, [1 + g] group g
   pdscp_step_out* out;
 };
 
 template <typename T>
-__device__ void svm_finalize(const SvmParams& p, double* sD, double* s_red, double* s_bc);
+__device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw);
 
 template <typename T, int VW, int LPP, int NCH, int U>
 __global__ void __launch_bounds__(kBlock) svm_iter_kernel(SvmParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float s_sc[kWarps][4];
-  __shared__ double s_red[32];
-  __shared__ double s_bc[8];
-  __shared__ bool s_last;
 
   StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
   if (hdr->stopped && !p.eval_only) return;
@@ -189,139 +187,145 @@ __global__ void __launch_bounds__(kBlock) svm_iter_kernel(SvmParams p) {
     prow[2] = mn;
     prow[3] = mx;
   }
-  if (!arrive_last(p.counter, &s_last)) return;
-  svm_finalize<T>(p, reinterpret_cast<double*>(smem_raw), s_red, s_bc);
+  svm_finish<T>(p, smem_raw);
 }
 
+// O(d) finish of one SVM iteration. Every CTA calls it after writing its
+// partial row [S_P, S_Q, minP, maxQ, Z_P (dp), Z_Q (dp)]; the two-level
+// completion elects one CTA, which reduces the group rows in FP64 and does
+// the rest.
 template <typename T>
-__device__ void svm_finalize(const SvmParams& p, double* sD, double* s_red, double* s_bc) {
+__device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
+  __shared__ float2 s_scr[kBlock];
+  __shared__ __align__(16) double s_hdr[sizeof(StateHdr) / 8];
+  __shared__ bool s_flag;
   const int d = p.d;
   const int dp = dpad4(d);
-  const int nb = gridDim.x;
   const int st = svm_partial_stride(d);
+  auto opof = [](int pc) { return pc == 2 ? 2 : (pc == 3 ? 1 : 0); };  // minP min, maxQ max
+  if (!arrive_two_level(p.partials, st, p.grows, p.counter, s_scr, &s_flag, opof)) return;
+
   StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
   double* mean = state_mean(p.state);
   float* mean32 = state_mean32(p.state, d);
   float* best = state_best(p.state, d);
-
-  // sD layout: [0]=S_P [1]=S_Q [2]=minP [3]=maxQ [4..4+d)=Z_P [4+d..4+2d)=Z_Q
-  for (int col = threadIdx.x; col < 4 + 2 * d; col += blockDim.x) {
-    int pc;
-    if (col < 4) pc = col;
-    else if (col < 4 + d) pc = col;
-    else pc = 4 + dp + (col - 4 - d);
-    double acc;
-    if (col == 2) {
-      acc = INFINITY;
-      for (int b = 0; b < nb; ++b) acc = fmin(acc, (double)__ldcg(p.partials + (size_t)b * st + pc));
-    } else if (col == 3) {
-      acc = -INFINITY;
-      for (int b = 0; b < nb; ++b) acc = fmax(acc, (double)__ldcg(p.partials + (size_t)b * st + pc));
-    } else {
-      acc = 0.0;
-      for (int b = 0; b < nb; ++b) acc += (double)__ldcg(p.partials + (size_t)b * st + pc);
-    }
-    sD[col] = acc;
-  }
+  const int tid = threadIdx.x;
+  // dynamic shared memory: column totals as (s, c) pairs | mean
+  float2* raw = reinterpret_cast<float2*>(smem_raw);
+  double* s_mean = reinterpret_cast<double*>(smem_raw) + st;
+  constexpr int HW = (int)(sizeof(StateHdr) / 8);
+  const double hw = tid < HW ? reinterpret_cast<const double*>(hdr)[tid] : 0.0;
+  const double m0 = tid < d ? mean[tid] : 0.0;
+  const int nb = gridDim.x;
+  const int G = (nb + group_size(nb) - 1) / group_size(nb);
+  reduce_rows(p.grows, 0, G, st, raw, s_scr, opof);
+  if (tid < HW) s_hdr[tid] = hw;
+  if (tid < d) s_mean[tid] = m0;
+  for (int j = tid + blockDim.x; j < d; j += blockDim.x) s_mean[j] = mean[j];
   __syncthreads();
-  const double SP = sD[0], SQ = sD[1], minP = sD[2], maxQ = sD[3];
+  // The O(d) math runs in warp 0 alone (see ses_finish).
+  if (tid >= 32) return;
+  const int lane = tid;
+  const StateHdr& h = *reinterpret_cast<const StateHdr*>(s_hdr);
+  auto tot = [&](int pc) { return (double)raw[pc].x + (double)raw[pc].y; };
+  const double SP = tot(0), SQ = tot(1), minP = (double)raw[2].x, maxQ = (double)raw[3].x;
   const double S = SP + SQ;
-  const double trmu = SP / S, trga = SQ / S;
+  const double rS = recip_d(S);
+  const double rSP = SP > 0.0 ? recip_d(SP) : 0.0, rSQ = SQ > 0.0 ? recip_d(SQ) : 0.0;
+  const double trmu = SP * rS, trga = SQ * rS;
   const double alpha = p.alpha, D = p.D;
-
-  double nz2 = 0.0, ub2 = 0.0, nw2 = 0.0;
-  for (int j = threadIdx.x; j < d; j += blockDim.x) {
-    const double zp = sD[4 + j], zq = sD[4 + d + j];
-    const double z = (zp - zq) / S;
-    nz2 += z * z;
-    const double df = zp / SP - zq / SQ;
-    ub2 += df * df;
-    nw2 += mean[j] * mean[j];
+  const double s1b = h.s1bar, s2b = h.s2bar;
+  // |z|^2, Claim 10 |P mu/Tr mu - Q gamma/Tr gamma|^2, |wbar|^2, z . wbar
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int j = lane; j < d; j += 32) {
+    const double zp = tot(4 + j), zq = tot(4 + dp + j);
+    const double z = (zp - zq) * rS;
+    const double df = zp * rSP - zq * rSQ;
+    const double m = s_mean[j];
+    acc[0] += z * z;
+    acc[1] += df * df;
+    acc[2] += m * m;
+    acc[3] += z * m;
   }
-  nz2 = block_sum_d(nz2, s_red);
-  ub2 = block_sum_d(ub2, s_red);
-  nw2 = block_sum_d(nw2, s_red);
-  const double nz = sqrt(nz2);
+  warp_sum_k<4>(acc);
+  const double rnz = acc[0] > 0.0 ? rsqrt_d(acc[0]) : 0.0;
+  const double nz = acc[0] * rnz;
   const double s1 = (trmu <= trga) ? D : alpha - D;
   const double s2 = alpha - s1;
-  const double V = nz - trmu * s1 - trga * s2;                       // Eq. (svm_oracle)
-  const double UB = (SP > 0.0 && SQ > 0.0) ? sqrt(ub2) : INFINITY;   // Claim 10
-  const double nw = sqrt(nw2);
-  const double f = nw > 0.0 ? fmax((minP - maxQ) / nw, 0.0) : 0.0;   // Sec. 5
-  const int64_t t = hdr->t;
-  const double s1b = hdr->s1bar, s2b = hdr->s2bar;
+  const double V = nz - trmu * s1 - trga * s2;                           // Eq. (svm_oracle)
+  const double UB = (SP > 0.0 && SQ > 0.0) ? sqrt_d(acc[1]) : INFINITY;  // Claim 10
+  const double rnw = acc[2] > 0.0 ? rsqrt_d(acc[2]) : 0.0;
+  const double f = acc[2] > 0.0 ? fmax((minP - maxQ) * rnw, 0.0) : 0.0;  // Sec. 5
+  const double wscale = rS * rnz;                                        // w = (Z_P - Z_Q) wscale
 
-  if (threadIdx.x == 0) {
-    int status = PDSCP_OK;
-    if (!(S > 0.0) || !isfinite(S) || !isfinite(V)) status = PDSCP_ERR_NUMERIC;
-    bool stop = false, failed = false;
-    int outcome = PDSCP_OUT_RUNNING;
-    const bool better = f > hdr->best_f;
-    if (!p.eval_only) {
-      if (UB < hdr->ub_best) hdr->ub_best = UB;
-      failed = V < 0.0;
-      if (status != PDSCP_OK) {
+  const int64_t t = h.t;
+  int status = PDSCP_OK;
+  if (!(S > 0.0) || !isfinite(S) || !isfinite(V)) status = PDSCP_ERR_NUMERIC;
+  bool stop = false, failed = false;
+  int outcome = PDSCP_OUT_RUNNING;
+  const bool better = f > h.best_f;
+  int streak = h.streak;
+  bool set_fprev = false;
+  if (!p.eval_only) {
+    failed = V < 0.0;
+    if (status != PDSCP_OK) {
+      stop = true;
+    } else if (failed) {
+      stop = true;
+      outcome = PDSCP_OUT_SEPARATED;
+    } else if (h.rules == PDSCP_RULES_PRACTICAL && t > 0) {
+      if (f > alpha) {
         stop = true;
-      } else if (failed) {
-        stop = true;
-        outcome = PDSCP_OUT_SEPARATED;
-      } else if (hdr->rules == PDSCP_RULES_PRACTICAL && t > 0) {
-        if (f > alpha) {
-          stop = true;
-          outcome = PDSCP_OUT_BEAT_ALPHA;
-        } else {
-          if (hdr->f_prev > 0.0) {
-            hdr->streak = (fabs(f - hdr->f_prev) / hdr->f_prev < hdr->delta) ? hdr->streak + 1 : 0;
-            if (hdr->streak >= hdr->patience) {
-              stop = true;
-              outcome = PDSCP_OUT_STALLED;
-            }
+        outcome = PDSCP_OUT_BEAT_ALPHA;
+      } else {
+        const double fp = h.f_prev;
+        if (fp > 0.0) {
+          streak = (fabs(f - fp) / fp < h.delta) ? streak + 1 : 0;
+          if (streak >= h.patience) {
+            stop = true;
+            outcome = PDSCP_OUT_STALLED;
           }
-          if (!stop) hdr->f_prev = f;
         }
+        set_fprev = !stop;
       }
     }
-    s_bc[0] = better ? 1.0 : 0.0;
-    s_bc[1] = (!p.eval_only && !stop) ? 1.0 : 0.0;
-    s_bc[2] = stop ? 1.0 : 0.0;
-    s_bc[3] = (double)outcome;
-    s_bc[4] = (double)status;
-    s_bc[5] = failed ? 1.0 : 0.0;
   }
-  __syncthreads();
-  const bool better = s_bc[0] != 0.0, advance = s_bc[1] != 0.0;
-  double mv = 0.0;
-  const double tp1 = (double)(t + 1);
-  for (int j = threadIdx.x; j < d; j += blockDim.x) {
-    const double m = mean[j];
+  const bool advance = !p.eval_only && !stop;
+  const double rtp1 = recip_d((double)t + 1.0);
+  for (int j = lane; j < d; j += 32) {
+    const double m = s_mean[j];
     if (better) best[j] = (float)m;
     if (advance) {
-      const double z = (sD[4 + j] - sD[4 + d + j]) / S;
-      const double w = nz > 0.0 ? z / nz : 0.0;
-      const double nm = m + (w - m) / tp1;
+      const double w = (tot(4 + j) - tot(4 + dp + j)) * wscale;
+      const double nm = m + (w - m) * rtp1;
       mean[j] = nm;
       mean32[j] = (float)nm;
-      mv += (nm - m) * (nm - m);
     }
   }
-  mv = block_sum_d(mv, s_red);
-  if (threadIdx.x == 0) {
+  if (lane == 0) {
+    if (!p.eval_only && UB < h.ub_best) hdr->ub_best = UB;
+    if (streak != h.streak) hdr->streak = streak;
+    if (set_fprev) hdr->f_prev = f;
     if (better) hdr->best_f = f;
     hdr->hint = fmin(minP - s1b, -maxQ - s2b);
+    const int64_t tn = t + (advance ? 1 : 0);
     if (advance) {
-      const double n1 = s1b + (s1 - s1b) / tp1, n2 = s2b + (s2 - s2b) / tp1;
-      hdr->move = D * sqrt(mv) + fmax(fabs(n1 - s1b), fabs(n2 - s2b));
+      // ||w - wbar||^2 = |w|^2 - 2 w.wbar + |wbar|^2, |w| = 1 (or w = 0)
+      const double ww = acc[0] > 0.0 ? 1.0 : 0.0;
+      const double mv2 = ww - 2.0 * acc[3] * rnz + acc[2];
+      const double n1 = s1b + (s1 - s1b) * rtp1, n2 = s2b + (s2 - s2b) * rtp1;
+      hdr->move = (D * rtp1 * sqrt_d(fmax(mv2, 0.0)) + fmax(fabs(n1 - s1b), fabs(n2 - s2b))) * (1.0 + 1e-6);
       hdr->s1bar = n1;
       hdr->s2bar = n2;
-      hdr->t = t + 1;
     } else {
       hdr->move = 0.0;
     }
-    if (s_bc[2] != 0.0) {
+    hdr->t = tn;
+    if (stop) {
       hdr->stopped = 1;
-      hdr->outcome = (int)s_bc[3];
+      hdr->outcome = outcome;
     }
-    if ((int)s_bc[4] != PDSCP_OK) hdr->status = (int)s_bc[4];
+    if (status != PDSCP_OK) hdr->status = status;
     hdr->last_value = V;
     if (p.out) {
       pdscp_step_out o;
@@ -329,16 +333,166 @@ __device__ void svm_finalize(const SvmParams& p, double* sD, double* s_red, doub
       o.objective = f;
       o.lower_bound = f;
       o.upper_bound = UB;
-      o.t = hdr->t;
-      o.failed = s_bc[5] != 0.0;
-      o.stopped = hdr->stopped;
-      o.status = (int)s_bc[4];
-      o.outcome = (int)s_bc[3];
+      o.t = tn;
+      o.failed = failed ? 1 : 0;
+      o.stopped = (stop || h.stopped) ? 1 : 0;
+      o.status = status;
+      o.outcome = outcome;
       o.k = (double)t * p.eta_over_rho;
       *p.out = o;
     }
-    *p.counter = 0u;
   }
+}
+
+}  // namespace pdscp
+
+namespace pdscp {
+
+// Vector-path form of svm_iter_kernel for rows of at most 32 chunks (see
+// ses_iter_t_kernel): the partial dot products x_i^T wbar are
+// reduce-scattered so that one lane per point forms the margin, the label
+// test and the exponential; the signed weight y_i e^{...} is broadcast back
+// for the per-class weighted sums Z_P, Z_Q.
+template <typename T, int VW, int LPP, int NI>
+__global__ void __launch_bounds__(kBlock) svm_iter_t_kernel(SvmParams p) {
+  using GS = GroupScatter<LPP, NI>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float s_sc[kWarps][4];
+
+  StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
+  if (hdr->stopped && !p.eval_only) return;
+
+  const int d = p.d;
+  const int dp = dpad4(d);
+  const int nch = d / VW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / LPP, gl = lane % LPP;
+  constexpr int PPW = 32 / LPP;
+  const bool owner = (gl % GS::SHARE) == 0;
+  const bool has_chunk = gl < nch;
+
+  const float k = p.eval_only ? 0.f : (float)((double)hdr->t * p.eta_over_rho);
+  const float Hm = (float)(hdr->hint - hdr->move);
+  const float s1 = (float)hdr->s1bar, s2 = (float)hdr->s2bar;
+  const float* mean32 = state_mean32(p.state, d);
+
+  float wb[VW], ZP[VW], ZQ[VW];
+#pragma unroll
+  for (int e = 0; e < VW; ++e) {
+    wb[e] = has_chunk ? mean32[gl * VW + e] : 0.f;
+    ZP[e] = 0.f;
+    ZQ[e] = 0.f;
+  }
+  float SP = 0.f, SQ = 0.f, minP = INFINITY, maxQ = -INFINITY;
+
+  const T* pts = reinterpret_cast<const T*>(p.pts);
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
+  constexpr int ROUND = PPW * NI;
+  for (int64_t base = gw * ROUND; base < p.n; base += nwarps * ROUND) {
+    float x[NI][VW];
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const int64_t i = base + r * PPW + grp;
+      if (i < p.n && has_chunk) {
+        Chunk<T, VW>::load(pts + i * d, gl, x[r]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) x[r][e] = 0.f;
+      }
+    }
+    float part[NI];
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      float a = 0.f;
+#pragma unroll
+      for (int e = 0; e < VW; ++e) a = fmaf(x[r][e], wb[e], a);
+      part[r] = a;
+    }
+    GS::run(part, gl);
+    float q[GS::OWN];  // y_i e^{-k (m_i - Hm)}, signed by the label
+#pragma unroll
+    for (int kk = 0; kk < GS::OWN; ++kk) {
+      const int64_t i = base + GS::owned(gl, kk) * PPW + grp;
+      q[kk] = 0.f;
+      if (i < p.n) {
+        const float dot = part[kk];
+        const bool pos = __ldg(p.labels + i) > 0;
+        const float margin = pos ? dot - s1 : -dot - s2;
+        const float pt = expf(-k * (margin - Hm));
+        q[kk] = pos ? pt : -pt;
+        if (owner) {
+          if (pos) {
+            SP += pt;
+            minP = fminf(minP, dot);
+          } else {
+            SQ += pt;
+            maxQ = fmaxf(maxQ, dot);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const float qr = __shfl_sync(0xffffffffu, q[r % GS::OWN], grp * LPP + GS::src_lane(r));
+      const float qp = fmaxf(qr, 0.f), qq = fmaxf(-qr, 0.f);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        ZP[e] = fmaf(qp, x[r][e], ZP[e]);
+        ZQ[e] = fmaf(qq, x[r][e], ZQ[e]);
+      }
+    }
+  }
+
+#pragma unroll
+  for (int o = LPP; o < 32; o <<= 1)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      ZP[e] += __shfl_xor_sync(0xffffffffu, ZP[e], o);
+      ZQ[e] += __shfl_xor_sync(0xffffffffu, ZQ[e], o);
+    }
+  SP = warp_sum(SP);
+  SQ = warp_sum(SQ);
+  minP = warp_min(minP);
+  maxQ = warp_max(maxQ);
+  float* sZ = reinterpret_cast<float*>(smem_raw);
+  if (grp == 0 && has_chunk)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      sZ[warp * 2 * dp + gl * VW + e] = ZP[e];
+      sZ[warp * 2 * dp + dp + gl * VW + e] = ZQ[e];
+    }
+  if (lane == 0) {
+    s_sc[warp][0] = SP;
+    s_sc[warp][1] = SQ;
+    s_sc[warp][2] = minP;
+    s_sc[warp][3] = maxQ;
+  }
+  __syncthreads();
+  float* prow = p.partials + (size_t)blockIdx.x * svm_partial_stride(d);
+  for (int j = threadIdx.x; j < d; j += kBlock) {
+    float a = 0.f, b = 0.f;
+    for (int w = 0; w < kWarps; ++w) {
+      a += sZ[w * 2 * dp + j];
+      b += sZ[w * 2 * dp + dp + j];
+    }
+    prow[4 + j] = a;
+    prow[4 + dp + j] = b;
+  }
+  if (threadIdx.x == 0) {
+    float a = 0.f, b = 0.f, mn = INFINITY, mx = -INFINITY;
+    for (int w = 0; w < kWarps; ++w) {
+      a += s_sc[w][0];
+      b += s_sc[w][1];
+      mn = fminf(mn, s_sc[w][2]);
+      mx = fmaxf(mx, s_sc[w][3]);
+    }
+    prow[0] = a;
+    prow[1] = b;
+    prow[2] = mn;
+    prow[3] = mx;
+  }
+  svm_finish<T>(p, smem_raw);
 }
 
 }  // namespace pdscp
