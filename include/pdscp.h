@@ -208,6 +208,30 @@ pdscp_status mwu_state_set(int32_t problem, const void* pts_dev, int32_t dtype,
                            pdscp_stream stream);
 
 /*
+ * mwu_step without a workspace argument, for callers that cannot allocate
+ * device memory: code running inside a host program that owns all GPU memory
+ * through its own pool, or that must not risk the implicit device
+ * synchronisation an allocation can bring. The paper has no counterpart; it
+ * is a deployment convenience. Same arguments and results as mwu_step minus
+ * ws_dev/ws_bytes: the per-CTA partial sums and completion counters live in a
+ * 2 MiB array built into the library, which every GPU that loads the library
+ * reserves until the process exits. Problems whose scratch does not fit
+ * (roughly d > 384 for SES and d > 190 for SVM on a 152-SM GPU) are rejected
+ * with PDSCP_ERR_WORKSPACE and a message; use mwu_step for them.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Each call clears the counters on `stream` (cudaMemsetAsync) and allocates
+ * nothing. All calls on a device share the one array: calls that overlap on
+ * the GPU (different streams, or several threads) race and give wrong
+ * results; serialise them on one stream.
+ */
+pdscp_status mwu_step_noalloc(int32_t problem, const void* pts_dev, int32_t dtype,
+                              const float* radii_dev, const int8_t* labels_dev,
+                              int64_t n, int32_t d, double alpha, double eta_over_rho,
+                              double D, int32_t eval_only, void* state_dev,
+                              pdscp_stream stream, pdscp_step_out* out_dev);
+
+/*
  * Read the running mean (SES: ubar, d floats; SVM: wbar then s1bar, s2bar:
  * d+2 floats) and the best point seen (SES: centre with the smallest f; SVM:
  * direction with the largest margin; d floats) of a state into device

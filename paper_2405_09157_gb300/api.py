@@ -98,6 +98,17 @@ def mwu_step(problem, pts, alpha, eta_over_rho, state, ws, out=None, D=0.0, radi
                           ws.numel(), _stream(stream), _vp(out)), "mwu_step")
 
 
+def mwu_step_noalloc(problem, pts, alpha, eta_over_rho, state, out=None, D=0.0, radii=None, labels=None,
+                     eval_only=False, stream=None):
+    """mwu_step for callers that cannot allocate device memory: the scratch is
+    the library's built-in 2 MiB array (shared by all calls on a device, so
+    calls must not overlap on the GPU)."""
+    n, d, dt = _points(pts)
+    check(load().mwu_step_noalloc(problem, _vp(pts), dt, _vp(radii), _vp(labels), n, d, float(alpha),
+                                  float(eta_over_rho), float(D), int(bool(eval_only)), _vp(state),
+                                  _stream(stream), _vp(out)), "mwu_step_noalloc")
+
+
 def state_read(problem, d, state, stream=None, device="cuda"):
     """(mean, best) float32 tensors of a state: SES (ubar, best centre); SVM
     ((wbar, s1bar, s2bar), best direction)."""

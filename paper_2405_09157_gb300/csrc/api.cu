@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "bounds_kernel.cuh"
@@ -248,6 +249,78 @@ pdscp_status mwu_state_set(int32_t problem, const void* pts, int32_t dtype, cons
   // evaluation pass at the mean: sets the shift bound (hint) and f
   return do_step(problem, pts, dtype, problem == PDSCP_SES ? radii : nullptr, labels, n, d, 1.0, 0.0,
                  problem == PDSCP_SVM ? D : 0.0, 1, state, ws, (cudaStream_t)stream, nullptr);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Built-in scratch for mwu_step_noalloc. Some callers cannot allocate device
+// memory at all (for example code running inside a host program that owns
+// every byte of GPU memory through its own pool and forbids cudaMalloc, or
+// plug-ins that must not trigger the implicit synchronisation an allocation
+// can cause). For them the workspace of mwu_step lives in this file-scope
+// array instead. Every GPU that loads the library reserves it until the
+// process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticScratchBytes = 2u << 20;  // 2 MiB
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_scratch_mu;
+void* g_scratch_addr[64] = {nullptr};
+
+// Device address of g_static_scratch on the current device. The name is
+// only a host-side stand-in for the array, so its address is looked up once
+// per device, with that device current, through cudaGetSymbolAddress.
+pdscp_status static_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "mwu_step_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= 64) return fail(PDSCP_ERR_INVALID_ARG, "mwu_step_noalloc: device index %d unsupported", dev);
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e, "mwu_step_noalloc: cudaGetSymbolAddress");
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return PDSCP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pdscp_status mwu_step_noalloc(int32_t problem, const void* pts, int32_t dtype, const float* radii,
+                              const int8_t* labels, int64_t n, int32_t d, double alpha, double eta_over_rho,
+                              double D, int32_t eval_only, void* state, pdscp_stream stream, pdscp_step_out* out) {
+  pdscp_status st = check_common(problem, pts, dtype, n, d);
+  if (st != PDSCP_OK) return st;
+  if (!state) return fail(PDSCP_ERR_INVALID_ARG, "state pointer is null");
+  if (!aligned(state, 16)) return fail(PDSCP_ERR_INVALID_ARG, "state not 16-byte aligned");
+  if (out && !aligned(out, 8)) return fail(PDSCP_ERR_INVALID_ARG, "out pointer not 8-byte aligned");
+  if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(PDSCP_ERR_INVALID_ARG, "alpha must be finite and > 0");
+  if (!(eta_over_rho >= 0.0) || !std::isfinite(eta_over_rho)) return fail(PDSCP_ERR_INVALID_ARG, "eta/rho must be finite and >= 0");
+  if (problem == PDSCP_SVM) {
+    if (!labels) return fail(PDSCP_ERR_INVALID_ARG, "SVM needs labels");
+    if (!(D > 0.0) || !std::isfinite(D)) return fail(PDSCP_ERR_INVALID_ARG, "SVM needs D > 0 (the largest point norm)");
+  }
+  const size_t need = layout(problem, d).state;  // counters + partial rows + group rows
+  if (need > kStaticScratchBytes)
+    return fail(PDSCP_ERR_WORKSPACE,
+                "mwu_step_noalloc: this problem needs %zu bytes of scratch but the built-in scratch holds %zu "
+                "bytes (d=%d is too large for it); call mwu_step with a caller-provided workspace instead",
+                need, kStaticScratchBytes, d);
+  void* ws = nullptr;
+  if ((st = static_scratch(&ws)) != PDSCP_OK) return st;
+  // The completion counters must start at zero; the scratch keeps whatever
+  // the previous call left, so clear them on the caller's stream first.
+  cudaError_t e = cudaMemsetAsync(ws, 0, kHeadBytes, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "mwu_step_noalloc: clearing counters");
+  return do_step(problem, pts, dtype, problem == PDSCP_SES ? radii : nullptr, labels, n, d, alpha, eta_over_rho, D,
+                 eval_only, state, ws, (cudaStream_t)stream, out);
 }
 
 pdscp_status mwu_backward(int32_t, const void*, int32_t, const int8_t*, int64_t, int32_t, double, double, double,
