@@ -5,7 +5,7 @@ exponential of every cone, the trace normaliser, the weighted n x d reduction,
 the closed-form ORACLE and the running-mean update) over the SES workload
 n = 1,000,000 points i.i.d. N(0, I_32), float32, seed 0, at alpha = D (an
 upper bound on OPT, so the ORACLE never separates and every step does the
-full work) with the step size Theorem 6 gives the first search step. The
+full work) with the step size Theorem 2 gives the first search step. The
 input (128 MB) is smaller than L2, so L2 is flushed between timed steps by
 writing a 512 MB buffer and then reading 256 MB of it (the lines left in L2
 are clean, so the timed step pays for no write-back of the flush); each step
@@ -248,13 +248,17 @@ def run_ours(args):
     peak, peak_kind = peaks()
     achieved = alg_bytes / (ms_per_step * 1e-3) / 1e9
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "ses_iter_n1e6_d32_traffic.json")
+    prof = os.path.join(ROOT, "profiles", "ses_iter_n1e6_d32_traffic.txt")
     if default_workload and os.path.exists(prof):
         try:
+            kv = {}
             with open(prof) as f:
-                pj = json.load(f)
-            if pj.get("kernel_rev") == kernel_rev():
-                traffic = pj["dram_bytes_per_launch"]
+                for line in f:
+                    if ":" in line and not line.startswith("#"):
+                        k, v = line.split(":", 1)
+                        kv[k.strip()] = v.strip()
+            if kv.get("kernel_rev") == kernel_rev():
+                traffic = int(kv["dram_bytes_per_launch"])
         except Exception:
             traffic = None
 
@@ -402,7 +406,7 @@ def variants(dev, flush):
 
 
 def time_to_eps(pts):
-    """ses_solve at eps = 1e-3 (paper's practical rules, Theorem 6 step size)
+    """ses_solve at eps = 1e-3 (paper's practical rules, Theorem 2 step size)
     within a 200,000-iteration budget: wall time and the certificate reached."""
     import torch
     from paper_2405_09157_gb300 import api

@@ -54,13 +54,13 @@ typedef enum pdscp_status {
 #define PDSCP_F32 0
 #define PDSCP_BF16 1
 
-/* alpha-FTP stopping rules (Sec. 3 Theorems 6/7, Sec. 5) */
+/* alpha-FTP stopping rules (Sec. 3 Theorems 2/3, Sec. 5) */
 #define PDSCP_RULES_NONE 0      /* stop only when the ORACLE separates */
 #define PDSCP_RULES_PRACTICAL 1 /* also: f beats alpha; |df|/f < delta `patience` times */
 
 /* solve modes */
 #define PDSCP_MODE_PRACTICAL 0  /* Sec. 5 rules inside each alpha-FTP */
-#define PDSCP_MODE_THEORY 1     /* T_i iterations of Theorem 6/7 per FTP */
+#define PDSCP_MODE_THEORY 1     /* T_i iterations of Theorem 2/3 per FTP */
 
 /* Largest supported dimension d. */
 #define PDSCP_MAX_D 1024
@@ -74,7 +74,7 @@ typedef enum pdscp_status {
  *                 SES radius max_i ||ubar - v_i|| + gamma_i; SVM margin.
  *   lower_bound   SES: value of the primal solution of Eq. (primal_construction)
  *                 built from p^{t+1} (<= OPT). SVM: the margin f (<= OPT).
- *   upper_bound   SES: f (>= OPT). SVM: Claim 10 PD value (>= OPT).
+ *   upper_bound   SES: f (>= OPT). SVM: Claim 8 PD value (>= OPT).
  *   t             completed ORACLE calls after the step.
  *   failed        1 if the ORACLE separated (alpha < OPT for SES; OPT < alpha
  *                 for SVM).
@@ -108,14 +108,14 @@ typedef struct pdscp_options {
   int64_t max_iters;  /* MWU iterations over the whole search */
   int32_t poll_every; /* host polls the device state every k iterations */
   int32_t max_steps;  /* search steps (alpha values) at most */
-  double eta;         /* 0: eta_i = sqrt(ln r / T_i) (Theorems 6/7); else fixed */
+  double eta;         /* 0: eta_i = sqrt(ln r / T_i) (Theorems 2/3); else fixed */
 } pdscp_options;
 
 typedef struct pdscp_report {
   double value;       /* SES: radius of the returned ball; SVM: its margin */
   double lower_bound; /* certificate: OPT >= lower_bound */
   double upper_bound; /* certificate: OPT <= upper_bound */
-  double D;           /* bound of Sec. 4.1 (SES) / Lemma 9 (SVM) */
+  double D;           /* bound of Sec. 4.1 (SES) / Lemma 6 (SVM) */
   double search_L;    /* final search range [L, U] of Sec. 3 */
   double search_U;
   int64_t iters;      /* MWU iterations run */
@@ -143,7 +143,7 @@ pdscp_status pdscp_workspace_size(int32_t problem, int64_t n, int32_t d, size_t*
 pdscp_status pdscp_state_size(int32_t problem, int32_t d, size_t* bytes_host);
 
 /*
- * Bounds pre-pass (Sec. 4.1 / Lemma 9). Writes D to *D_dev (one double):
+ * Bounds pre-pass (Sec. 4.1 / Lemma 6). Writes D to *D_dev (one double):
  *   SES: D = max_{i>=2} ||v_1 - v_i|| + gamma_1 + gamma_i  (OPT in [D/2, D])
  *   SVM: D = max_i ||x_i||                                  (s_1, s_2 <= D)
  * radii_dev (SES, may be NULL = all zero) holds n float radii.
@@ -176,7 +176,7 @@ pdscp_status mwu_state_init(int32_t problem, const void* pts_dev, int32_t dtype,
  *     running-mean update ubar^{t+1}.
  *   SVM (Sec. 4.2): per point the exponent -(eta t/rho)(y_i x_i^T wbar -
  *     sbar_{class i}), the normaliser, z = P mu - Q gamma, the ORACLE
- *     (w, s1, s2) of Eq. (svm_oracle), its value, the Claim 10 bound, f^t,
+ *     (w, s1, s2) of Eq. (svm_oracle), its value, the Claim 8 bound, f^t,
  *     and the running means.
  * eta_over_rho = eta/rho (> 0); k = eta_over_rho * t is formed on the device.
  * alpha > 0. D (SVM) must be >= the largest point norm (pdscp_bounds); it is
@@ -258,7 +258,7 @@ pdscp_status ses_solve(const void* pts_dev, int32_t dtype, const float* radii_de
 /*
  * (1-eps)-approximate hard-margin SVM / (1+eps) polytope distance (Sec. 4.2)
  * by the minimisation search over alpha in (0, 2D]. Writes the best
- * direction w (d floats, unit norm) to w_dev and its margin and Claim 10
+ * direction w (d floats, unit norm) to w_dev and its margin and Claim 8
  * upper bound to *report_host. Synchronises like ses_solve.
  */
 pdscp_status svm_solve(const void* X_dev, int32_t dtype, const int8_t* labels_dev,

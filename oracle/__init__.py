@@ -14,9 +14,9 @@ float64 through numpy; inputs are promoted to float64 on entry.
 Modules
   eja     Jordan-algebra primitives of the second-order cone and R^n_+ (Sec. 2.1)
   ses     Smallest Enclosing Sphere: SCMWU weights, closed-form ORACLE, the
-          alpha-FTP loop of Theorem 6 and the search of Sec. 3 (Sec. 4.1)
+          alpha-FTP loop of Theorem 2 and the search of Sec. 3 (Sec. 4.1)
   svm     Hard-margin SVM / polytope distance, the minimisation variant
-          (Theorem 7) with the closed-form ORACLE of Sec. 4.2
+          (Theorem 3) with the closed-form ORACLE of Sec. 4.2
   exact   Textbook exact solvers used to pin the oracle on tiny inputs
           (Welzl-style minimum enclosing circle, support-set enumeration for
           balls, active-set enumeration for polytope distance)

@@ -2,8 +2,8 @@
 
 Follows Sec. 4.1 (problem SES, its split into the easy set C and the hard set
 F, the dual/primal pair (dualses)/(primalses), the bounds D, the closed-form
-ORACLE of Eq. (ses_oracle), the width rho <= 3D/sqrt2 and T of Theorem 8),
-Sec. 3 (the alpha-FTP of Theorem 6, the hyperplane update of Eq. (implement),
+ORACLE of Eq. (ses_oracle), the width rho <= 3D/sqrt2 and T of Theorem 4),
+Sec. 3 (the alpha-FTP of Theorem 2, the hyperplane update of Eq. (implement),
 the primal solution of Eq. (primal_construction), the search from
 feasibility to optimisation) and Sec. 5 (per-iteration objective f^t, the
 early-exit and early-stop rules).
@@ -29,7 +29,7 @@ import numpy as np
 from .eja import SQRT2, scmwu_soc, soc_inner
 
 OUT_SEPARATED = "separated"      # ORACLE value < 0: alpha < OPT (Sec. 3)
-OUT_FEASIBLE = "feasible"        # T iterations without separation (Theorem 6)
+OUT_FEASIBLE = "feasible"        # T iterations without separation (Theorem 2)
 OUT_BELOW_ALPHA = "below_alpha"  # f^t < alpha: affirmative early exit (Sec. 5)
 OUT_STALLED = "stalled"          # |f^t - f^{t-1}|/f^{t-1} < delta, patience times (Sec. 5)
 OUT_FIXED = "fixed"              # FIXED_ITERS mode ran its T iterations
@@ -69,12 +69,12 @@ SES_R = SQRT2  # b_{d+1} after scaling the last primal constraint by sqrt2 (Sec.
 
 
 def ses_T(D, n, eps, alpha):
-    """T = ceil(36 D^2 ln(2n-2) / (eps^2 alpha^2)) (Sec. 4.1, from Theorem 6)."""
+    """T = ceil(36 D^2 ln(2n-2) / (eps^2 alpha^2)) (Sec. 4.1, from Theorem 2)."""
     return int(math.ceil(36.0 * D * D * math.log(2 * n - 2) / (eps * eps * alpha * alpha)))
 
 
 def theorem_eta(r, T):
-    """Step size eta = sqrt(ln r / T) of Theorems 6 and 7."""
+    """Step size eta = sqrt(ln r / T) of Theorems 2 and 3."""
     return math.sqrt(math.log(r) / T)
 
 
@@ -165,7 +165,7 @@ def ses_objective(V, gamma, c):
 
 
 def ses_step(V, gamma, ubar, t, alpha, eta, rho):
-    """One iteration of the alpha-FTP (Sec. 3, Theorem 6) for SES.
+    """One iteration of the alpha-FTP (Sec. 3, Theorem 2) for SES.
 
     ``t`` oracle calls have completed and ``ubar`` is the mean of their u's (any
     value when t = 0). Computes p^{t+1} (Eq. implement with k = eta t/rho), the
@@ -196,10 +196,10 @@ def ses_step(V, gamma, ubar, t, alpha, eta, rho):
 # ------------------------------------------------------------ the alpha-FTP
 def ses_ftp(V, gamma, alpha, eta, rho, T, mode=MODE_FIXED, delta=1e-4, patience=10,
             keep_trace=False):
-    """alpha-feasibility test of Theorem 6 for SES, run for at most T iterations.
+    """alpha-feasibility test of Theorem 2 for SES, run for at most T iterations.
 
     Modes: FIXED runs exactly T iterations unless the ORACLE separates;
-    THEORY is the same with the conclusion of Theorem 6 (OPT <= (1+eps) alpha
+    THEORY is the same with the conclusion of Theorem 2 (OPT <= (1+eps) alpha
     when T is the theorem's count); PRACTICAL adds the two rules of Sec. 5:
     stop with an affirmative answer as soon as f^t < alpha, and stop when
     |f^t - f^{t-1}|/f^{t-1} < delta for ``patience`` consecutive iterations
@@ -252,7 +252,7 @@ def ses_solve(V, gamma=None, eps=1e-2, mode=MODE_PRACTICAL, max_iters=10**7,
     """(1+eps)-approximate SES by the search of Sec. 3 over alpha in [D/2, D].
 
     Step i: alpha_i = L + (U-L)/3, eps_i = (U-L)/(3 alpha_i), T_i and eta_i from
-    Theorem 6 (Sec. 4.1 constants). Separation -> L = alpha_i; otherwise the
+    Theorem 2 (Sec. 4.1 constants). Separation -> L = alpha_i; otherwise the
     FTP's conclusion OPT <= (1+eps_i) alpha_i -> U = (1+eps_i) alpha_i. The
     paper's PRACTICAL rules (Sec. 5) replace the T_i iterations by its early
     exit / early stop; a stalled run is taken as the affirmative answer, as the
@@ -264,9 +264,9 @@ def ses_solve(V, gamma=None, eps=1e-2, mode=MODE_PRACTICAL, max_iters=10**7,
     both valid whatever the mode. The loop ends when U <= (1+eps) L, when
     ub <= (1+eps) lb, or when ``max_iters`` MWU iterations have run.
 
-    ``eta`` None uses eta_i = sqrt(ln r / T_i) of Theorem 6 in every step; a
+    ``eta`` None uses eta_i = sqrt(ln r / T_i) of Theorem 2 in every step; a
     number fixes the step size (Theorem 1 allows any eta in (0, 1]; the
-    guarantee of Theorem 6 then no longer applies, the certificates still do).
+    guarantee of Theorem 2 then no longer applies, the certificates still do).
     """
     V, gm = _prep(V, gamma)
     n = V.shape[0]

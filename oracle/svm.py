@@ -1,12 +1,12 @@
 """Hard-margin SVM / polytope distance through the minimisation variant, FP64.
 
-Follows Sec. 4.2: problem (SVM) and its dual (PD); Lemma 9 (s_1, s_2 <= D
+Follows Sec. 4.2: problem (SVM) and its dual (PD); Lemma 6 (s_1, s_2 <= D
 with D the largest point norm); the split into C = {||w|| <= 1, s_1, s_2 <= D}
 and F = {P^T w >= s_1 1, -Q^T w >= s_2 1}; the min-form SCP (svm_dual_scp)
 with K = R^n_+ (r = n) and R = 2; the closed-form ORACLE of Eq. (svm_oracle)
-and its solution; Claim 10 (the normalised weights are PD-feasible); the
+and its solution; Claim 8 (the normalised weights are PD-feasible); the
 width rho <= 2D and T = ceil(64 D^2 ln n / (eps^2 alpha^2)). Sec. 3 supplies
-the minimisation variant (Eq. min_implement, Theorem 7). Sec. 5 supplies the
+the minimisation variant (Eq. min_implement, Theorem 3). Sec. 5 supplies the
 margin f^t and the early rules.
 
 Inputs: X is the (n, d) array of points, y the (n,) labels in {+1, -1}.
@@ -23,7 +23,7 @@ Readings of the paper taken here (each is listed in the design doc):
     unit vector; its value does not depend on it).
   * The search for the minimisation variant mirrors Sec. 3: alpha_i =
     U - (U-L)/3, eps_i = (U-L)/(3 alpha_i); separation (value < 0, so
-    OPT < alpha_i) gives U = alpha_i, the Theorem 7 conclusion gives
+    OPT < alpha_i) gives U = alpha_i, the Theorem 3 conclusion gives
     L = (1 - eps_i) alpha_i.
 """
 
@@ -33,7 +33,7 @@ import numpy as np
 
 from .eja import scmwu_orthant
 
-OUT_SEPARATED = "separated"      # ORACLE value < 0: OPT < alpha (Theorem 7)
+OUT_SEPARATED = "separated"      # ORACLE value < 0: OPT < alpha (Theorem 3)
 OUT_FEASIBLE = "feasible"        # T iterations without separation
 OUT_ABOVE_ALPHA = "above_alpha"  # margin f^t > alpha: affirmative early exit (Sec. 5)
 OUT_STALLED = "stalled"
@@ -59,7 +59,7 @@ def _prep(X, y):
 
 
 def svm_D(X):
-    """D = max point norm over P and Q (Lemma 9)."""
+    """D = max point norm over P and Q (Lemma 6)."""
     X = np.asarray(X, dtype=np.float64)
     return float(np.max(np.sqrt(np.sum(X * X, axis=1))))
 
@@ -70,7 +70,7 @@ def svm_width(D):
 
 
 def svm_T(D, n, eps, alpha):
-    """T = ceil(64 D^2 ln n / (eps^2 alpha^2)) (Sec. 4.2, from Theorem 7)."""
+    """T = ceil(64 D^2 ln n / (eps^2 alpha^2)) (Sec. 4.2, from Theorem 3)."""
     return int(math.ceil(64.0 * D * D * math.log(n) / (eps * eps * alpha * alpha)))
 
 
@@ -122,7 +122,7 @@ def svm_program_value(X, y, p, w, s1, s2):
 
 
 def svm_pd_value(X, y, p):
-    """Claim 10: (mu/Tr mu; gamma/Tr gamma) is PD-feasible; returns its PD objective
+    """Claim 8: (mu/Tr mu; gamma/Tr gamma) is PD-feasible; returns its PD objective
     ||P mu/Tr mu - Q gamma/Tr gamma||, an upper bound on OPT (Eq. PD)."""
     X, y = _prep(X, y)
     mu = np.where(y > 0, p, 0.0)
@@ -143,9 +143,9 @@ def svm_margin(X, y, wbar):
 
 
 def svm_step(X, y, wbar, s1bar, s2bar, t, alpha, eta, rho, D):
-    """One iteration of the minimisation alpha-FTP (Sec. 3, Theorem 7) for SVM.
+    """One iteration of the minimisation alpha-FTP (Sec. 3, Theorem 3) for SVM.
 
-    Computes p^{t+1} (k = eta t/rho), the ORACLE answer, the Claim 10 upper
+    Computes p^{t+1} (k = eta t/rho), the ORACLE answer, the Claim 8 upper
     bound and the margin f at wbar; advances the means when the ORACLE succeeds.
     """
     X, y = _prep(X, y)
@@ -172,7 +172,7 @@ def svm_step(X, y, wbar, s1bar, s2bar, t, alpha, eta, rho, D):
 
 def svm_ftp(X, y, alpha, eta, rho, T, D, mode=MODE_FIXED, delta=1e-4, patience=10,
             keep_trace=False):
-    """Minimisation alpha-FTP of Theorem 7 for SVM, at most T iterations.
+    """Minimisation alpha-FTP of Theorem 3 for SVM, at most T iterations.
 
     Same modes as the SES test. PRACTICAL stops affirmatively once the margin
     f^t exceeds alpha and on the delta/patience rule of Sec. 5.
@@ -221,9 +221,9 @@ def svm_solve(X, y, eps=1e-2, mode=MODE_PRACTICAL, max_iters=10**7, delta=1e-4,
     """(1-eps)-approximate max margin by the search over alpha in (0, 2D] (Sec. 4.2).
 
     Certificates: lb = best margin f of an actual separating direction, ub =
-    best Claim 10 PD value; the loop ends when U <= (1+eps) L, when
+    best Claim 8 PD value; the loop ends when U <= (1+eps) L, when
     ub <= (1+eps) lb, or when ``max_iters`` iterations have run. ``eta`` as in
-    the SES search: None for Theorem 7's eta_i, a number to fix it.
+    the SES search: None for Theorem 3's eta_i, a number to fix it.
     """
     X, y = _prep(X, y)
     n = X.shape[0]

@@ -74,7 +74,7 @@ def decode_steps(buf):
 
 
 def bounds(problem, pts, radii=None, ws=None, stream=None):
-    """D of Sec. 4.1 (SES) or Lemma 9 (SVM) as a (1,) float64 CUDA tensor."""
+    """D of Sec. 4.1 (SES) or Lemma 6 (SVM) as a (1,) float64 CUDA tensor."""
     n, d, dt = _points(pts)
     ws = workspace(problem, n, d, pts.device) if ws is None else ws
     out = torch.empty(1, dtype=torch.float64, device=pts.device)

@@ -1,6 +1,6 @@
 // Bounds pre-pass (one streaming pass, max reduction):
 //   SES (Sec. 4.1):  D = max_{i>=2} ||v_1 - v_i|| + gamma_1 + gamma_i
-//   SVM (Lemma 9):   D = max_i ||x_i||
+//   SVM (Lemma 6):   D = max_i ||x_i||
 // plus the small state-initialisation and state-read kernels.
 #pragma once
 

@@ -36,7 +36,7 @@ struct StateHdr {
   double f_prev;    // previous f (-1: none yet)
   double best_f;    // SES: smallest f seen; SVM: largest margin seen
   double lb_best;   // SES: best primal lower bound
-  double ub_best;   // SVM: best Claim 10 upper bound
+  double ub_best;   // SVM: best Claim 8 upper bound
   double s1bar;     // SVM running means of s_1, s_2
   double s2bar;
   double last_value;

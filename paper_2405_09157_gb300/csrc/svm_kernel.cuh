@@ -11,7 +11,7 @@
 // and min_P x^T wbar, max_Q x^T wbar. Then Tr(mu) = S_P/S, Tr(gamma) = S_Q/S,
 // z = P mu - Q gamma = (Z_P - Z_Q)/S, and the ORACLE of Eq. (svm_oracle) is
 // w = z/||z||, s_1 = D if Tr(mu) <= Tr(gamma) else alpha - D, s_2 = alpha - s_1,
-// value ||z|| - Tr(mu) s_1 - Tr(gamma) s_2. Claim 10's PD value is
+// value ||z|| - Tr(mu) s_1 - Tr(gamma) s_2. Claim 8's PD value is
 // ||Z_P/S_P - Z_Q/S_Q||; the margin f^t of Sec. 5 is
 // max{(min_P x^T wbar - max_Q x^T wbar)/||wbar||, 0}.
 //
@@ -235,7 +235,7 @@ __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
   const double trmu = SP * rS, trga = SQ * rS;
   const double alpha = p.alpha, D = p.D;
   const double s1b = h.s1bar, s2b = h.s2bar;
-  // |z|^2, Claim 10 |P mu/Tr mu - Q gamma/Tr gamma|^2, |wbar|^2, z . wbar
+  // |z|^2, Claim 8 |P mu/Tr mu - Q gamma/Tr gamma|^2, |wbar|^2, z . wbar
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int j = lane; j < d; j += 32) {
     const double zp = tot(4 + j), zq = tot(4 + dp + j);
@@ -253,7 +253,7 @@ __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
   const double s1 = (trmu <= trga) ? D : alpha - D;
   const double s2 = alpha - s1;
   const double V = nz - trmu * s1 - trga * s2;                           // Eq. (svm_oracle)
-  const double UB = (SP > 0.0 && SQ > 0.0) ? sqrt_d(acc[1]) : INFINITY;  // Claim 10
+  const double UB = (SP > 0.0 && SQ > 0.0) ? sqrt_d(acc[1]) : INFINITY;  // Claim 8
   const double rnw = acc[2] > 0.0 ? rsqrt_d(acc[2]) : 0.0;
   const double f = acc[2] > 0.0 ? fmax((minP - maxQ) * rnw, 0.0) : 0.0;  // Sec. 5
   const double wscale = rS * rnz;                                        // w = (Z_P - Z_Q) wscale

@@ -3,7 +3,7 @@
 Each test checks the oracle against something other than itself: the
 unsimplified program it solves, brute force over feasible points, the SCMWU
 definition with explicitly accumulated losses, the regret bound of Theorem 1,
-the guarantee of Theorem 6, weak duality against exact solvers (Welzl,
+the guarantee of Theorem 2, weak duality against exact solvers (Welzl,
 support-set enumeration) and closed forms.
 """
 
@@ -130,7 +130,7 @@ def test_running_mean_form_equals_scmwu_definition_and_regret_bound():
 
 
 @pytest.mark.parametrize("rel", [1.15, 0.8])
-def test_theorem6_guarantee_small_instance(rel):
+def test_theorem2_guarantee_small_instance(rel):
     V = datagen.ses_uniform(6, 2, seed=6).astype(np.float64)
     _, opt = exact.mec_2d(V)
     D = ses.ses_D(V)

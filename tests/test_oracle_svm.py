@@ -1,8 +1,8 @@
 """Pins for the SVM oracle (Sec. 3 minimisation variant, Sec. 4.2, Sec. 5).
 
 Checked against: brute force over feasible ORACLE points, the unsimplified
-ORACLE program, Claim 10, weak duality against exact polytope distance,
-the regret bound of Theorem 1 on R^n_+ and the guarantee of Theorem 7.
+ORACLE program, Claim 8, weak duality against exact polytope distance,
+the regret bound of Theorem 1 on R^n_+ and the guarantee of Theorem 3.
 """
 
 import math
@@ -47,7 +47,7 @@ def test_weights_sum_to_one_and_init_uniform():
     assert math.isclose(float(np.sum(p)), 1.0, rel_tol=1e-13) and np.all(p > 0)
 
 
-def test_claim10_and_pd_upper_bound_against_bruteforce():
+def test_claim8_and_pd_upper_bound_against_bruteforce():
     X, y = _inst(5, 4, 2, 3)
     P, Q = X[y > 0], X[y < 0]
     opt, _, _ = exact.pd_bruteforce(P, Q)
@@ -60,7 +60,7 @@ def test_claim10_and_pd_upper_bound_against_bruteforce():
         for alpha in np.linspace(0.1, 2 * D, 15):
             value = svm.svm_oracle(X, y, p, alpha, D)[3]
             if value < 0:
-                assert ub < alpha                      # Claim 10
+                assert ub < alpha                      # Claim 8
 
 
 def test_margin_is_a_lower_bound_and_single_pair_closed_form():
@@ -106,7 +106,7 @@ def test_regret_bound_on_the_orthant():
 
 
 @pytest.mark.parametrize("rel", [0.85, 1.25])
-def test_theorem7_guarantee_small_instance(rel):
+def test_theorem3_guarantee_small_instance(rel):
     X, y = _inst(4, 4, 2, 6)
     P, Q = X[y > 0], X[y < 0]
     opt, _, _ = exact.pd_bruteforce(P, Q)
@@ -119,7 +119,7 @@ def test_theorem7_guarantee_small_instance(rel):
         assert opt < alpha
     else:
         assert res["iters"] == T
-        # dual repair (Theorem 7): (wbar; s1bar - eps alpha/R; s2bar - eps alpha/R) is
+        # dual repair (Theorem 3): (wbar; s1bar - eps alpha/R; s2bar - eps alpha/R) is
         # feasible for (SVM) with value >= (1 - eps) alpha
         d = eps * alpha / svm.SVM_R
         w = res["wbar"]
