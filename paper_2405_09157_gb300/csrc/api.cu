@@ -119,10 +119,10 @@ pdscp_status do_step(int problem, const void* pts, int dtype, const float* radii
   float2* grows = reinterpret_cast<float2*>(reinterpret_cast<char*>(ws) + L.grows);
   cudaError_t e;
   if (problem == PDSCP_SES) {
-    SesParams p{pts, radii, n, d, eval_only, alpha, eta_over_rho, state, partials, grows, counter, out};
+    SesParams p{pts, radii, n, d, eval_only, alpha, eta_over_rho, state, partials, grows, counter, 0, out};
     e = launch_ses(p, dtype, vec, stream);
   } else {
-    SvmParams p{pts, labels, n, d, eval_only, alpha, eta_over_rho, D, state, partials, grows, counter, out};
+    SvmParams p{pts, labels, n, d, eval_only, alpha, eta_over_rho, D, state, partials, grows, counter, 0, out};
     e = launch_svm(p, dtype, vec, stream);
   }
   if (e != cudaSuccess) return cuda_fail(e, "mwu_step launch");

@@ -13,7 +13,11 @@ namespace pdscp {
 constexpr double kSqrt2 = 1.41421356237309504880;
 constexpr int kBlock = 256;           // threads per CTA of the point passes
 constexpr int kWarps = kBlock / 32;
+constexpr int kMaxBlock = 1024;       // largest CTA of any pass kernel
 constexpr int kMaxBlocksPerSM = 8;    // upper bound used to size the workspace
+// Completion stages every partial row in the last CTA's shared memory when
+// they fit in this many bytes; larger rows take the two-level completion.
+constexpr size_t kStageBytes = 96 * 1024;
 constexpr size_t kHeadBytes = 1024;   // workspace: completion counters (top + per group)
 constexpr int kMaxGroups = 64;        // group rows reserved in the workspace
 
@@ -189,8 +193,14 @@ __device__ __forceinline__ float2 as_pair(float2 v) { return v; }
 // the R partial results are combined in a fixed order (deterministic).
 // opof(pc) gives the operation of column pc. `scratch` holds blockDim
 // float2. Ends with a barrier; every thread must call it.
+template <typename TIn>
+__device__ __forceinline__ TIn load_row_elem(const TIn* p, bool shared_src) {
+  return shared_src ? *p : __ldcg(p);
+}
+
 template <typename TIn, typename OpOf>
-__device__ void reduce_rows(const TIn* m, int r0, int r1, int stride, float2* out, float2* scratch, OpOf opof) {
+__device__ void reduce_rows(const TIn* m, int r0, int r1, int stride, float2* out, float2* scratch, OpOf opof,
+                            bool shared_src = false) {
   const int nt = blockDim.x;
   int R = 1;
   while (2 * R * stride <= nt && R < 32) R *= 2;
@@ -199,7 +209,7 @@ __device__ void reduce_rows(const TIn* m, int r0, int r1, int stride, float2* ou
       const int op = opof(pc);
       float2 acc = col_init2(op);
 #pragma unroll 8
-      for (int r = r0; r < r1; ++r) col_comb2(op, acc, as_pair(__ldcg(m + (size_t)r * stride + pc)));
+      for (int r = r0; r < r1; ++r) col_comb2(op, acc, as_pair(load_row_elem(m + (size_t)r * stride + pc, shared_src)));
       out[pc] = acc;
     }
     __syncthreads();
@@ -211,7 +221,7 @@ __device__ void reduce_rows(const TIn* m, int r0, int r1, int stride, float2* ou
     const int op = opof(pc);
     float2 acc = col_init2(op);
 #pragma unroll 8
-    for (int r = r0 + q; r < r1; r += R) col_comb2(op, acc, as_pair(__ldcg(m + (size_t)r * stride + pc)));
+    for (int r = r0 + q; r < r1; r += R) col_comb2(op, acc, as_pair(load_row_elem(m + (size_t)r * stride + pc, shared_src)));
     scratch[q * stride + pc] = acc;
   }
   __syncthreads();
@@ -307,6 +317,69 @@ __device__ __forceinline__ void block_sum2_d(double& a, double& b, double* red) 
   b = sb;
 }
 
+// Whether the completion of a grid of nb CTAs with partial rows of `stride`
+// floats stages every row in shared memory (single level).
+__host__ __device__ inline bool single_level(int nb, int stride) {
+  return (size_t)nb * stride * sizeof(float) <= kStageBytes;
+}
+
+// Completion of one pass, in two calls. Every CTA has written its partial
+// row (stride floats) to rows[blockIdx.x].
+//   arrive_pass: returns true in exactly one CTA, the one that finishes;
+//   final_reduce: in that CTA, the column totals of all rows into raw[0..stride)
+//     as compensated pairs.
+// Single level: the last CTA to arrive loads every row into shared memory
+// `stage` with one round of independent 16-byte loads and reduces there.
+// Two levels (rows too large to stage): arrive_two_level, then the group rows.
+// Between the two calls the finishing CTA can issue its other loads so that
+// their latency overlaps the staging. No CTA waits on another.
+template <typename OpOf>
+__device__ bool arrive_pass(const float* rows, int stride, float2* grows, unsigned int* counters, float2* scratch,
+                            bool* s_flag, OpOf opof, bool single) {
+  if (!single) return arrive_two_level(rows, stride, grows, counters, scratch, s_flag, opof);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int prev = atomicAdd(&counters[0], 1u);
+    __threadfence();
+    *s_flag = (prev == (unsigned int)(gridDim.x - 1));
+  }
+  __syncthreads();
+  return *s_flag;
+}
+
+template <typename OpOf>
+__device__ void final_reduce(const float* rows, int stride, const float2* grows, unsigned int* counters,
+                             float2* scratch, OpOf opof, float2* raw, float* stage, bool single) {
+  const int nb = gridDim.x;
+  if (!single) {
+    const int G = (nb + group_size(nb) - 1) / group_size(nb);
+    reduce_rows(grows, 0, G, stride, raw, scratch, opof);
+    return;
+  }
+  // stride is a multiple of 4 and rows starts on a 256-byte boundary
+  const int n4 = nb * stride / 4;
+  const float4* src = reinterpret_cast<const float4*>(rows);
+  float4* dst = reinterpret_cast<float4*>(stage);
+  constexpr int kInFlight = 4;
+  for (int i0 = threadIdx.x; i0 < n4; i0 += kInFlight * blockDim.x) {
+    float4 v[kInFlight];
+#pragma unroll
+    for (int k = 0; k < kInFlight; ++k) {
+      const int i = i0 + k * blockDim.x;
+      if (i < n4) v[k] = __ldcg(src + i);
+    }
+#pragma unroll
+    for (int k = 0; k < kInFlight; ++k) {
+      const int i = i0 + k * blockDim.x;
+      if (i < n4) dst[i] = v[k];
+    }
+  }
+  if (threadIdx.x == 0) counters[0] = 0u;
+  __syncthreads();
+  reduce_rows(stage, 0, nb, stride, raw, scratch, opof, true);
+}
+
 // Sums of up to four doubles per thread over the whole block in one pass
 // (fixed order, deterministic); every thread gets the totals. `red` holds
 // 4 * 32 doubles. Contains barriers: every thread must call it.
@@ -335,6 +408,14 @@ __device__ __forceinline__ void block_sum_k(double (&v)[K], double* red) {
 // same, deterministic totals).
 template <int K>
 __device__ __forceinline__ void warp_sum_k(double (&v)[K]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+}
+
+template <int K>
+__device__ __forceinline__ void warp_sum_kf(float (&v)[K]) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
 #pragma unroll

@@ -48,6 +48,14 @@ cudaError_t dispatch_shape(int d, bool vec, L&& l) {
   return cudaErrorInvalidValue;
 }
 
+// Threads per CTA of the reduce-scatter kernels: one CTA per SM, as many
+// warps as the register file allows at the instance's register use (rounds
+// of up to 32 point floats per lane fit 85 registers, 64 floats 128).
+template <int VW, int NI>
+struct PassBlock {
+  static constexpr int value = (VW * NI <= 32) ? 768 : 512;
+};
+
 // Points in flight per lane group, by the number of floats a lane holds.
 template <int VW, int NCH>
 struct Unroll {
@@ -57,9 +65,9 @@ struct Unroll {
 // Grid for a point pass: enough CTAs to fill every SM at the occupancy the
 // instance allows (at most kMaxBlocksPerSM per SM), no more than the work needs.
 template <typename KernelFn>
-int pass_grid(KernelFn kern, size_t smem, int64_t n, int points_per_cta_step) {
+int pass_grid(KernelFn kern, size_t smem, int64_t n, int points_per_cta_step, int block = kBlock) {
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBlock, smem) != cudaSuccess || occ < 1) occ = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) != cudaSuccess || occ < 1) occ = 1;
   if (occ > kMaxBlocksPerSM) occ = kMaxBlocksPerSM;
   const int64_t full = (int64_t)device_sm_count() * occ;
   int64_t need = (n + points_per_cta_step - 1) / points_per_cta_step;

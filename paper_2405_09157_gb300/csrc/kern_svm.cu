@@ -9,18 +9,28 @@ template <typename T>
 struct SvmLauncher {
   const SvmParams& p;
   cudaStream_t stream;
+  // Dynamic shared memory: the per-warp partial sums of the pass, or in the
+  // finishing CTA the column totals, the mean and (single-level
+  // completion) every partial row, whichever is larger.
   template <typename Kern>
-  cudaError_t launch(Kern kern, int points_per_lane_step, int lpp) {
+  cudaError_t launch(Kern kern, int points_per_lane_step, int lpp, int block) {
     const int dp = dpad4(p.d);
-    size_t smem = (size_t)kWarps * 2 * dp * sizeof(float);
-    const size_t fin = (size_t)(svm_partial_stride(p.d) + dp) * sizeof(double);
-    if (fin > smem) smem = fin;
+    const int st = svm_partial_stride(p.d);
+    const size_t pass_smem = (size_t)(block / 32) * 2 * dp * sizeof(float);
+    const size_t fin_base = (size_t)(st + 1 * dp) * sizeof(double);
+    size_t smem = pass_smem > fin_base ? pass_smem : fin_base;
+    const int grid = pass_grid(kern, smem, p.n, (32 / lpp) * points_per_lane_step * (block / 32), block);
+    SvmParams q = p;
+    q.single = single_level(grid, st) ? 1 : 0;
+    if (q.single) {
+      const size_t fin = fin_base + (size_t)grid * st * sizeof(float);
+      if (fin > smem) smem = fin;
+    }
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
     }
-    const int grid = pass_grid(kern, smem, p.n, (32 / lpp) * points_per_lane_step * kWarps);
-    kern<<<grid, kBlock, smem, stream>>>(p);
+    kern<<<grid, block, smem, stream>>>(q);
     return cudaGetLastError();
   }
   template <int VW, int LPP, int NCH>
@@ -28,10 +38,11 @@ struct SvmLauncher {
     if constexpr (VW > 1 && NCH == 1) {
       // vector rows of at most 32 chunks: the reduce-scatter form
       constexpr int NI = RoundSize<VW, LPP>::value;
-      return launch(svm_iter_t_kernel<T, VW, LPP, NI>, NI, LPP);
+      constexpr int B = PassBlock<VW, NI>::value;
+      return launch(svm_iter_t_kernel<T, VW, LPP, NI, B>, NI, LPP, B);
     } else {
       constexpr int U = Unroll<VW, NCH>::value;
-      return launch(svm_iter_kernel<T, VW, LPP, NCH, U>, U, LPP);
+      return launch(svm_iter_kernel<T, VW, LPP, NCH, U>, U, LPP, kBlock);
     }
   }
 };

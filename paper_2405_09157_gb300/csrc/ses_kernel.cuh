@@ -43,6 +43,7 @@ struct SesParams {
   float* partials;       // one row of ses_partial_stride(d) floats per CTA
   float2* grows;         // one compensated-FP32 row per completion group
   unsigned int* counter; // completion counters: [0] top, [1 + g] group g
+  int single;            // completion stages all partial rows in shared memory (single_level)
   pdscp_step_out* out;   // may be null
 };
 
@@ -191,13 +192,13 @@ __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
 // one CTA, which reduces the group rows in FP64 and does the rest.
 template <typename T>
 __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw) {
-  __shared__ float2 s_scr[kBlock];
+  __shared__ float2 s_scr[kMaxBlock];
   __shared__ __align__(16) double s_hdr[sizeof(StateHdr) / 8];
   __shared__ bool s_flag;
   const int d = p.d;
   const int st = ses_partial_stride(d);
   auto opof = [](int pc) { return pc == 2 ? 1 : 0; };  // maxd is a max, the rest sums
-  if (!arrive_two_level(p.partials, st, p.grows, p.counter, s_scr, &s_flag, opof)) return;
+  if (!arrive_pass(p.partials, st, p.grows, p.counter, s_scr, &s_flag, opof, p.single)) return;
 
   StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
   double* mean = state_mean(p.state);
@@ -206,19 +207,18 @@ __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw) {
   const T* pts = reinterpret_cast<const T*>(p.pts);
   const int tid = threadIdx.x;
   const int dp = dpad4(d);
-  // dynamic shared memory: column totals as (s, c) pairs | mean | v_1
+  // dynamic shared memory: column totals as (s, c) pairs | mean | v_1 | staged partial rows
   float2* raw = reinterpret_cast<float2*>(smem_raw);
   double* s_mean = reinterpret_cast<double*>(smem_raw) + st;
   double* s_v1 = s_mean + dp;
+  float* stage = reinterpret_cast<float*>(s_v1 + dp);
   // loads the finish needs, issued before the reduction so their latency overlaps it
   constexpr int HW = (int)(sizeof(StateHdr) / 8);
   const double hw = tid < HW ? reinterpret_cast<const double*>(hdr)[tid] : 0.0;
   const double m0 = tid < d ? mean[tid] : 0.0;
   const double v0 = tid < d ? (double)elem_to_float<T>(pts + tid) : 0.0;
   const double gam1 = p.radii ? (double)__ldg(p.radii) : 0.0;
-  const int nb = gridDim.x;
-  const int G = (nb + group_size(nb) - 1) / group_size(nb);
-  reduce_rows(p.grows, 0, G, st, raw, s_scr, opof);
+  final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single);
   if (tid < HW) s_hdr[tid] = hw;
   if (tid < d) {
     s_mean[tid] = m0;
@@ -234,52 +234,59 @@ __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw) {
   if (tid >= 32) return;
   const int lane = tid;
   const StateHdr& h = *reinterpret_cast<const StateHdr*>(s_hdr);
-  auto tot = [&](int pc) { return (double)raw[pc].x + (double)raw[pc].y; };
-  const double S = tot(0), Wt = tot(1), maxd = (double)raw[2].x;
-  const double alpha = p.alpha;
-  const double inv = recip_d(kSqrt2 * S);  // g = G' / (sqrt2 S)
+  // The finish works in FP32 (FP64 is slow here and its dependent chains
+  // dominated this step): its inputs are compensated sums accurate to ~1e-7,
+  // and its results feed tolerances of 1e-5. FP64 is kept for the running
+  // mean, which accumulates over the whole alpha-FTP, and for the Sec. 5
+  // ratio test, which decides an integer as the oracle does.
+  auto tot = [&](int pc) { return raw[pc].x + raw[pc].y; };
+  const float S = tot(0), Wt = tot(1), maxd = raw[2].x;
+  const float alpha = (float)p.alpha;
+  const float gam1f = (float)gam1;
+  const float inv = 1.0f / ((float)kSqrt2 * S);  // g = G' / (sqrt2 S)
   // A = |g|^2, B = g . (v_1 - ubar), C = |ubar - v_1|^2
-  double acc[3] = {0.0, 0.0, 0.0};
+  float acc[3] = {0.f, 0.f, 0.f};
   for (int j = lane; j < d; j += 32) {
-    const double g = tot(4 + j) * inv;
-    const double dv = s_v1[j] - s_mean[j];
-    acc[0] += g * g;
-    acc[1] += g * dv;
-    acc[2] += dv * dv;
+    const float g = tot(4 + j) * inv;
+    const float dv = (float)(s_v1[j] - s_mean[j]);
+    acc[0] = fmaf(g, g, acc[0]);
+    acc[1] = fmaf(g, dv, acc[1]);
+    acc[2] = fmaf(dv, dv, acc[2]);
   }
-  warp_sum_k<3>(acc);
-  const double A = acc[0], B = acc[1], C = acc[2];
-  const double rad = alpha - gam1;
-  const double rng = A > 0.0 ? rsqrt_d(A) : 0.0;
-  const double ng = A * rng;                 // ||g||
-  const double step = rad * rng;             // u = v_1 + step g  (u = v_1 when g = 0)
-  const double V = B + step * A + Wt * inv;  // g.(u - ubar) + Wt/(sqrt2 S): Eq. (ses_oracle) value
-  const double LB = fmax(gam1, alpha - V * recip_d(ng + 1.0 / kSqrt2));  // Eq. (primal_construction)
-  const double f = fmax(maxd, sqrt_d(C) + gam1);                           // f at the mean read (Sec. 5)
+  warp_sum_kf<3>(acc);
+  const float A = acc[0], B = acc[1], C = acc[2];
+  const float rad = alpha - gam1f;
+  const float rng = A > 0.f ? 1.0f / sqrtf(A) : 0.f;
+  const float ng = A * rng;                 // ||g||
+  const float step = rad * rng;             // u = v_1 + step g  (u = v_1 when g = 0)
+  const float V = B + step * A + Wt * inv;  // g.(u - ubar) + Wt/(sqrt2 S): Eq. (ses_oracle) value
+  const float LB = fmaxf(gam1f, alpha - V / (ng + (float)(1.0 / kSqrt2)));  // Eq. (primal_construction)
+  const float f = fmaxf(maxd, sqrtf(C) + gam1f);                             // f at the mean read (Sec. 5)
+  const double fd = (double)f;
 
   const int64_t t = h.t;
   int status = PDSCP_OK;
-  if (!(S > 0.0) || !isfinite(S) || !isfinite(V) || !isfinite(f)) status = PDSCP_ERR_NUMERIC;
+  if (!(S > 0.f) || !isfinite(S) || !isfinite(V) || !isfinite(f)) status = PDSCP_ERR_NUMERIC;
   bool stop = false, failed = false;
   int outcome = PDSCP_OUT_RUNNING;
-  const bool better = (t > 0 && f < h.best_f);
+  const bool better = (t > 0 && fd < h.best_f);
   int streak = h.streak;
   bool set_fprev = false;
   if (!p.eval_only) {
-    failed = V < 0.0;
+    failed = V < 0.f;
     if (status != PDSCP_OK) {
       stop = true;
     } else if (failed) {
       stop = true;
       outcome = PDSCP_OUT_SEPARATED;
     } else if (h.rules == PDSCP_RULES_PRACTICAL && t > 0) {
-      if (f < alpha) {
+      if (fd < p.alpha) {
         stop = true;
         outcome = PDSCP_OUT_BEAT_ALPHA;
       } else {
         const double fp = h.f_prev;
         if (fp > 0.0) {
-          streak = (fabs(f - fp) / fp < h.delta) ? streak + 1 : 0;
+          streak = (fabs(fd - fp) / fp < h.delta) ? streak + 1 : 0;
           if (streak >= h.patience) {
             stop = true;
             outcome = PDSCP_OUT_STALLED;
@@ -290,26 +297,27 @@ __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw) {
     }
   }
   const bool advance = !p.eval_only && !stop;
-  const double rtp1 = recip_d((double)t + 1.0);  // 1 / (t + 1)
+  const float rtp1 = 1.0f / (float)(t + 1);  // 1 / (t + 1)
   for (int j = lane; j < d; j += 32) {
     const double m = s_mean[j];
     if (better) best[j] = (float)m;
     if (advance) {
-      const double u = s_v1[j] + step * (tot(4 + j) * inv);
-      const double nm = m + (u - m) * rtp1;
+      const float mf = (float)m;
+      const float u = (float)s_v1[j] + step * (tot(4 + j) * inv);
+      const double nm = m + (double)((u - mf) * rtp1);
       mean[j] = nm;
       mean32[j] = (float)nm;
     }
   }
   if (lane == 0) {
-    if (!p.eval_only && LB > h.lb_best) hdr->lb_best = LB;
+    if (!p.eval_only && (double)LB > h.lb_best) hdr->lb_best = (double)LB;
     if (streak != h.streak) hdr->streak = streak;
-    if (set_fprev) hdr->f_prev = f;
-    if (better) hdr->best_f = f;
-    hdr->hint = maxd;
+    if (set_fprev) hdr->f_prev = fd;
+    if (better) hdr->best_f = fd;
+    hdr->hint = (double)maxd;
     // ||ubar^{t+1} - ubar^t|| = ||u - ubar|| / (t+1), ||u - ubar||^2 = C + 2 step B + step^2 A
-    const double mv2 = C + 2.0 * step * B + step * step * A;
-    hdr->move = advance ? rtp1 * sqrt_d(fmax(mv2, 0.0)) * (1.0 + 1e-6) : 0.0;
+    const float mv2 = C + 2.f * step * B + step * step * A;
+    hdr->move = advance ? (double)(rtp1 * sqrtf(fmaxf(mv2, 0.f))) * (1.0 + 1e-5) : 0.0;
     const int64_t tn = t + (advance ? 1 : 0);
     hdr->t = tn;
     if (stop) {
@@ -317,13 +325,13 @@ __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw) {
       hdr->outcome = outcome;
     }
     if (status != PDSCP_OK) hdr->status = status;
-    hdr->last_value = V;
+    hdr->last_value = (double)V;
     if (p.out) {
       pdscp_step_out o;
-      o.oracle_value = V;
-      o.objective = f;
-      o.lower_bound = LB;
-      o.upper_bound = f;
+      o.oracle_value = (double)V;
+      o.objective = fd;
+      o.lower_bound = (double)LB;
+      o.upper_bound = fd;
       o.t = tn;
       o.failed = failed ? 1 : 0;
       o.stopped = (stop || h.stopped) ? 1 : 0;
@@ -333,6 +341,7 @@ __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw) {
       *p.out = o;
     }
   }
+
 }
 
 }  // namespace pdscp
@@ -347,14 +356,12 @@ namespace pdscp {
 // The weighted sums G' are then accumulated from the broadcast
 // coefficients. Same arithmetic per point as ses_iter_kernel; only the order
 // of the FP32 partial sums differs.
-template <typename T, int VW, int LPP, int NI>
-__global__ void __launch_bounds__(kBlock) ses_iter_t_kernel(SesParams p) {
+template <typename T, int VW, int LPP, int NI, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
   using GS = GroupScatter<LPP, NI>;
+  constexpr int NW = BLOCK / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ float s_sc[kWarps][3];
-
-  StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
-  if (hdr->stopped && !p.eval_only) return;
+  __shared__ float s_sc[NW][3];
 
   const int d = p.d;
   const int dp = dpad4(d);
@@ -364,6 +371,28 @@ __global__ void __launch_bounds__(kBlock) ses_iter_t_kernel(SesParams p) {
   constexpr int PPW = 32 / LPP;  // points per load instruction per warp
   const bool owner = (gl % GS::SHARE) == 0;
   const bool has_chunk = gl < nch;
+  const T* pts = reinterpret_cast<const T*>(p.pts);
+  const int64_t nwarps = (int64_t)gridDim.x * NW;
+  const int64_t gw = (int64_t)blockIdx.x * NW + warp;
+  constexpr int ROUND = PPW * NI;
+  // the first round's point loads do not depend on the state: issue them first
+  float x[NI][VW];
+  auto load_round = [&](int64_t base) {
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+        const int64_t i = base + r * PPW + grp;
+        if (i < p.n && has_chunk) {
+          Chunk<T, VW>::load(pts + i * d, gl, x[r]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VW; ++e) x[r][e] = 0.f;
+        }
+      }
+  };
+  load_round(gw * ROUND);
+
+  StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
+  if (hdr->stopped && !p.eval_only) return;
 
   const float kr = p.eval_only ? 0.f : (float)((double)hdr->t * p.eta_over_rho / kSqrt2);
   const float H = (float)(hdr->hint + hdr->move);
@@ -378,22 +407,8 @@ __global__ void __launch_bounds__(kBlock) ses_iter_t_kernel(SesParams p) {
   }
   float S = 0.f, W = 0.f, maxd = -INFINITY;
 
-  const T* pts = reinterpret_cast<const T*>(p.pts);
-  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
-  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
-  constexpr int ROUND = PPW * NI;
   for (int64_t base = gw * ROUND; base < p.n; base += nwarps * ROUND) {
-    float x[NI][VW];
-#pragma unroll
-    for (int r = 0; r < NI; ++r) {
-      const int64_t i = base + r * PPW + grp;
-      if (i < p.n && has_chunk) {
-        Chunk<T, VW>::load(pts + i * d, gl, x[r]);
-      } else {
-#pragma unroll
-        for (int e = 0; e < VW; ++e) x[r][e] = 0.f;
-      }
-    }
+    if (base != gw * ROUND) load_round(base);
     float part[NI];
 #pragma unroll
     for (int r = 0; r < NI; ++r) {
@@ -453,14 +468,14 @@ __global__ void __launch_bounds__(kBlock) ses_iter_t_kernel(SesParams p) {
   }
   __syncthreads();
   float* prow = p.partials + (size_t)blockIdx.x * ses_partial_stride(d);
-  for (int j = threadIdx.x; j < d; j += kBlock) {
+  for (int j = threadIdx.x; j < d; j += BLOCK) {
     float s = 0.f;
-    for (int w = 0; w < kWarps; ++w) s += sG[w * dp + j];
+    for (int w = 0; w < NW; ++w) s += sG[w * dp + j];
     prow[4 + j] = s;
   }
   if (threadIdx.x == 0) {
     float s0 = 0.f, s1 = 0.f, m = -INFINITY;
-    for (int w = 0; w < kWarps; ++w) {
+    for (int w = 0; w < NW; ++w) {
       s0 += s_sc[w][0];
       s1 += s_sc[w][1];
       m = fmaxf(m, s_sc[w][2]);

@@ -39,6 +39,7 @@ struct SvmParams {
   float* partials;       // one row of svm_partial_stride(d) floats per CTA
   float2* grows;         // one compensated-FP32 row per completion group
   unsigned int* counter; // completion counters: [0] top, [1 + g] group g
+  int single;            // completion stages all partial rows in shared memory (single_level)
   pdscp_step_out* out;
 };
 
@@ -196,29 +197,28 @@ __global__ void __launch_bounds__(kBlock) svm_iter_kernel(SvmParams p) {
 // the rest.
 template <typename T>
 __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
-  __shared__ float2 s_scr[kBlock];
+  __shared__ float2 s_scr[kMaxBlock];
   __shared__ __align__(16) double s_hdr[sizeof(StateHdr) / 8];
   __shared__ bool s_flag;
   const int d = p.d;
   const int dp = dpad4(d);
   const int st = svm_partial_stride(d);
   auto opof = [](int pc) { return pc == 2 ? 2 : (pc == 3 ? 1 : 0); };  // minP min, maxQ max
-  if (!arrive_two_level(p.partials, st, p.grows, p.counter, s_scr, &s_flag, opof)) return;
+  if (!arrive_pass(p.partials, st, p.grows, p.counter, s_scr, &s_flag, opof, p.single)) return;
 
   StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
   double* mean = state_mean(p.state);
   float* mean32 = state_mean32(p.state, d);
   float* best = state_best(p.state, d);
   const int tid = threadIdx.x;
-  // dynamic shared memory: column totals as (s, c) pairs | mean
+  // dynamic shared memory: column totals as (s, c) pairs | mean | staged partial rows
   float2* raw = reinterpret_cast<float2*>(smem_raw);
   double* s_mean = reinterpret_cast<double*>(smem_raw) + st;
+  float* stage = reinterpret_cast<float*>(s_mean + dp);
   constexpr int HW = (int)(sizeof(StateHdr) / 8);
   const double hw = tid < HW ? reinterpret_cast<const double*>(hdr)[tid] : 0.0;
   const double m0 = tid < d ? mean[tid] : 0.0;
-  const int nb = gridDim.x;
-  const int G = (nb + group_size(nb) - 1) / group_size(nb);
-  reduce_rows(p.grows, 0, G, st, raw, s_scr, opof);
+  final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single);
   if (tid < HW) s_hdr[tid] = hw;
   if (tid < d) s_mean[tid] = m0;
   for (int j = tid + blockDim.x; j < d; j += blockDim.x) s_mean[j] = mean[j];
@@ -227,60 +227,62 @@ __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
   if (tid >= 32) return;
   const int lane = tid;
   const StateHdr& h = *reinterpret_cast<const StateHdr*>(s_hdr);
-  auto tot = [&](int pc) { return (double)raw[pc].x + (double)raw[pc].y; };
-  const double SP = tot(0), SQ = tot(1), minP = (double)raw[2].x, maxQ = (double)raw[3].x;
-  const double S = SP + SQ;
-  const double rS = recip_d(S);
-  const double rSP = SP > 0.0 ? recip_d(SP) : 0.0, rSQ = SQ > 0.0 ? recip_d(SQ) : 0.0;
-  const double trmu = SP * rS, trga = SQ * rS;
-  const double alpha = p.alpha, D = p.D;
+  // FP32 finish, FP64 running means (see ses_finish).
+  auto tot = [&](int pc) { return raw[pc].x + raw[pc].y; };
+  const float SP = tot(0), SQ = tot(1), minP = raw[2].x, maxQ = raw[3].x;
+  const float S = SP + SQ;
+  const float rS = 1.0f / S;
+  const float rSP = SP > 0.f ? 1.0f / SP : 0.f, rSQ = SQ > 0.f ? 1.0f / SQ : 0.f;
+  const float trmu = SP * rS, trga = SQ * rS;
+  const float alpha = (float)p.alpha, D = (float)p.D;
   const double s1b = h.s1bar, s2b = h.s2bar;
   // |z|^2, Claim 8 |P mu/Tr mu - Q gamma/Tr gamma|^2, |wbar|^2, z . wbar
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
   for (int j = lane; j < d; j += 32) {
-    const double zp = tot(4 + j), zq = tot(4 + dp + j);
-    const double z = (zp - zq) * rS;
-    const double df = zp * rSP - zq * rSQ;
-    const double m = s_mean[j];
-    acc[0] += z * z;
-    acc[1] += df * df;
-    acc[2] += m * m;
-    acc[3] += z * m;
+    const float zp = tot(4 + j), zq = tot(4 + dp + j);
+    const float z = (zp - zq) * rS;
+    const float df = zp * rSP - zq * rSQ;
+    const float m = (float)s_mean[j];
+    acc[0] = fmaf(z, z, acc[0]);
+    acc[1] = fmaf(df, df, acc[1]);
+    acc[2] = fmaf(m, m, acc[2]);
+    acc[3] = fmaf(z, m, acc[3]);
   }
-  warp_sum_k<4>(acc);
-  const double rnz = acc[0] > 0.0 ? rsqrt_d(acc[0]) : 0.0;
-  const double nz = acc[0] * rnz;
-  const double s1 = (trmu <= trga) ? D : alpha - D;
-  const double s2 = alpha - s1;
-  const double V = nz - trmu * s1 - trga * s2;                           // Eq. (svm_oracle)
-  const double UB = (SP > 0.0 && SQ > 0.0) ? sqrt_d(acc[1]) : INFINITY;  // Claim 8
-  const double rnw = acc[2] > 0.0 ? rsqrt_d(acc[2]) : 0.0;
-  const double f = acc[2] > 0.0 ? fmax((minP - maxQ) * rnw, 0.0) : 0.0;  // Sec. 5
-  const double wscale = rS * rnz;                                        // w = (Z_P - Z_Q) wscale
+  warp_sum_kf<4>(acc);
+  const float rnz = acc[0] > 0.f ? 1.0f / sqrtf(acc[0]) : 0.f;
+  const float nz = acc[0] * rnz;
+  const float s1 = (trmu <= trga) ? D : alpha - D;
+  const float s2 = alpha - s1;
+  const float V = nz - trmu * s1 - trga * s2;                           // Eq. (svm_oracle)
+  const float UB = (SP > 0.f && SQ > 0.f) ? sqrtf(acc[1]) : INFINITY;  // Claim 8
+  const float rnw = acc[2] > 0.f ? 1.0f / sqrtf(acc[2]) : 0.f;
+  const float f = acc[2] > 0.f ? fmaxf((minP - maxQ) * rnw, 0.f) : 0.f;  // Sec. 5
+  const float wscale = rS * rnz;                                        // w = (Z_P - Z_Q) wscale
+  const double fd = (double)f;
 
   const int64_t t = h.t;
   int status = PDSCP_OK;
-  if (!(S > 0.0) || !isfinite(S) || !isfinite(V)) status = PDSCP_ERR_NUMERIC;
+  if (!(S > 0.f) || !isfinite(S) || !isfinite(V)) status = PDSCP_ERR_NUMERIC;
   bool stop = false, failed = false;
   int outcome = PDSCP_OUT_RUNNING;
-  const bool better = f > h.best_f;
+  const bool better = fd > h.best_f;
   int streak = h.streak;
   bool set_fprev = false;
   if (!p.eval_only) {
-    failed = V < 0.0;
+    failed = V < 0.f;
     if (status != PDSCP_OK) {
       stop = true;
     } else if (failed) {
       stop = true;
       outcome = PDSCP_OUT_SEPARATED;
     } else if (h.rules == PDSCP_RULES_PRACTICAL && t > 0) {
-      if (f > alpha) {
+      if (fd > p.alpha) {
         stop = true;
         outcome = PDSCP_OUT_BEAT_ALPHA;
       } else {
         const double fp = h.f_prev;
         if (fp > 0.0) {
-          streak = (fabs(f - fp) / fp < h.delta) ? streak + 1 : 0;
+          streak = (fabs(fd - fp) / fp < h.delta) ? streak + 1 : 0;
           if (streak >= h.patience) {
             stop = true;
             outcome = PDSCP_OUT_STALLED;
@@ -291,30 +293,31 @@ __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
     }
   }
   const bool advance = !p.eval_only && !stop;
-  const double rtp1 = recip_d((double)t + 1.0);
+  const float rtp1 = 1.0f / (float)(t + 1);
   for (int j = lane; j < d; j += 32) {
     const double m = s_mean[j];
     if (better) best[j] = (float)m;
     if (advance) {
-      const double w = (tot(4 + j) - tot(4 + dp + j)) * wscale;
-      const double nm = m + (w - m) * rtp1;
+      const float w = (tot(4 + j) - tot(4 + dp + j)) * wscale;
+      const double nm = m + (double)((w - (float)m) * rtp1);
       mean[j] = nm;
       mean32[j] = (float)nm;
     }
   }
   if (lane == 0) {
-    if (!p.eval_only && UB < h.ub_best) hdr->ub_best = UB;
+    if (!p.eval_only && (double)UB < h.ub_best) hdr->ub_best = (double)UB;
     if (streak != h.streak) hdr->streak = streak;
-    if (set_fprev) hdr->f_prev = f;
-    if (better) hdr->best_f = f;
-    hdr->hint = fmin(minP - s1b, -maxQ - s2b);
+    if (set_fprev) hdr->f_prev = fd;
+    if (better) hdr->best_f = fd;
+    hdr->hint = fmin((double)minP - s1b, -(double)maxQ - s2b);
     const int64_t tn = t + (advance ? 1 : 0);
     if (advance) {
       // ||w - wbar||^2 = |w|^2 - 2 w.wbar + |wbar|^2, |w| = 1 (or w = 0)
-      const double ww = acc[0] > 0.0 ? 1.0 : 0.0;
-      const double mv2 = ww - 2.0 * acc[3] * rnz + acc[2];
-      const double n1 = s1b + (s1 - s1b) * rtp1, n2 = s2b + (s2 - s2b) * rtp1;
-      hdr->move = (D * rtp1 * sqrt_d(fmax(mv2, 0.0)) + fmax(fabs(n1 - s1b), fabs(n2 - s2b))) * (1.0 + 1e-6);
+      const float ww = acc[0] > 0.f ? 1.f : 0.f;
+      const float mv2 = ww - 2.f * acc[3] * rnz + acc[2];
+      const double n1 = s1b + (double)((s1 - (float)s1b) * rtp1);
+      const double n2 = s2b + (double)((s2 - (float)s2b) * rtp1);
+      hdr->move = ((double)(D * rtp1 * sqrtf(fmaxf(mv2, 0.f))) + fmax(fabs(n1 - s1b), fabs(n2 - s2b))) * (1.0 + 1e-5);
       hdr->s1bar = n1;
       hdr->s2bar = n2;
     } else {
@@ -326,13 +329,13 @@ __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
       hdr->outcome = outcome;
     }
     if (status != PDSCP_OK) hdr->status = status;
-    hdr->last_value = V;
+    hdr->last_value = (double)V;
     if (p.out) {
       pdscp_step_out o;
-      o.oracle_value = V;
-      o.objective = f;
-      o.lower_bound = f;
-      o.upper_bound = UB;
+      o.oracle_value = (double)V;
+      o.objective = fd;
+      o.lower_bound = fd;
+      o.upper_bound = (double)UB;
       o.t = tn;
       o.failed = failed ? 1 : 0;
       o.stopped = (stop || h.stopped) ? 1 : 0;
@@ -342,6 +345,7 @@ __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
       *p.out = o;
     }
   }
+
 }
 
 }  // namespace pdscp
@@ -353,14 +357,12 @@ namespace pdscp {
 // reduce-scattered so that one lane per point forms the margin, the label
 // test and the exponential; the signed weight y_i e^{...} is broadcast back
 // for the per-class weighted sums Z_P, Z_Q.
-template <typename T, int VW, int LPP, int NI>
-__global__ void __launch_bounds__(kBlock) svm_iter_t_kernel(SvmParams p) {
+template <typename T, int VW, int LPP, int NI, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
   using GS = GroupScatter<LPP, NI>;
+  constexpr int NW = BLOCK / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ float s_sc[kWarps][4];
-
-  StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
-  if (hdr->stopped && !p.eval_only) return;
+  __shared__ float s_sc[NW][4];
 
   const int d = p.d;
   const int dp = dpad4(d);
@@ -370,6 +372,28 @@ __global__ void __launch_bounds__(kBlock) svm_iter_t_kernel(SvmParams p) {
   constexpr int PPW = 32 / LPP;
   const bool owner = (gl % GS::SHARE) == 0;
   const bool has_chunk = gl < nch;
+  const T* pts = reinterpret_cast<const T*>(p.pts);
+  const int64_t nwarps = (int64_t)gridDim.x * NW;
+  const int64_t gw = (int64_t)blockIdx.x * NW + warp;
+  constexpr int ROUND = PPW * NI;
+  // the first round's point loads do not depend on the state: issue them first
+  float x[NI][VW];
+  auto load_round = [&](int64_t base) {
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+        const int64_t i = base + r * PPW + grp;
+        if (i < p.n && has_chunk) {
+          Chunk<T, VW>::load(pts + i * d, gl, x[r]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VW; ++e) x[r][e] = 0.f;
+        }
+      }
+  };
+  load_round(gw * ROUND);
+
+  StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
+  if (hdr->stopped && !p.eval_only) return;
 
   const float k = p.eval_only ? 0.f : (float)((double)hdr->t * p.eta_over_rho);
   const float Hm = (float)(hdr->hint - hdr->move);
@@ -385,22 +409,8 @@ __global__ void __launch_bounds__(kBlock) svm_iter_t_kernel(SvmParams p) {
   }
   float SP = 0.f, SQ = 0.f, minP = INFINITY, maxQ = -INFINITY;
 
-  const T* pts = reinterpret_cast<const T*>(p.pts);
-  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
-  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
-  constexpr int ROUND = PPW * NI;
   for (int64_t base = gw * ROUND; base < p.n; base += nwarps * ROUND) {
-    float x[NI][VW];
-#pragma unroll
-    for (int r = 0; r < NI; ++r) {
-      const int64_t i = base + r * PPW + grp;
-      if (i < p.n && has_chunk) {
-        Chunk<T, VW>::load(pts + i * d, gl, x[r]);
-      } else {
-#pragma unroll
-        for (int e = 0; e < VW; ++e) x[r][e] = 0.f;
-      }
-    }
+    if (base != gw * ROUND) load_round(base);
     float part[NI];
 #pragma unroll
     for (int r = 0; r < NI; ++r) {
@@ -470,9 +480,9 @@ __global__ void __launch_bounds__(kBlock) svm_iter_t_kernel(SvmParams p) {
   }
   __syncthreads();
   float* prow = p.partials + (size_t)blockIdx.x * svm_partial_stride(d);
-  for (int j = threadIdx.x; j < d; j += kBlock) {
+  for (int j = threadIdx.x; j < d; j += BLOCK) {
     float a = 0.f, b = 0.f;
-    for (int w = 0; w < kWarps; ++w) {
+    for (int w = 0; w < NW; ++w) {
       a += sZ[w * 2 * dp + j];
       b += sZ[w * 2 * dp + dp + j];
     }
@@ -481,7 +491,7 @@ __global__ void __launch_bounds__(kBlock) svm_iter_t_kernel(SvmParams p) {
   }
   if (threadIdx.x == 0) {
     float a = 0.f, b = 0.f, mn = INFINITY, mx = -INFINITY;
-    for (int w = 0; w < kWarps; ++w) {
+    for (int w = 0; w < NW; ++w) {
       a += s_sc[w][0];
       b += s_sc[w][1];
       mn = fminf(mn, s_sc[w][2]);

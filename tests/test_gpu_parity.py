@@ -200,9 +200,13 @@ def test_ses_duplicates_and_two_points():
     gr, gmean = gpu_ses_traj(V32, None, 0.9 * D, 0.5 / rho, 40)
     orr, omean = oracle_ses_traj(run_V, None, 0.9 * D, 0.5, rho, 40)
     compare_ses(gr, orr, gmean, omean, D)
+    # n = 2 at alpha = 1.01 > OPT = 1: u^1 = v_1, then every ORACLE answer is
+    # v_1 + alpha e_1, so ubar^T = (T-1)/T * alpha e_1 exactly. (At alpha = OPT the
+    # ORACLE value sqrt2 E2/S tends to 0 and its sign is decided by rounding.)
     two = np.array([[0.0, 0.0, 0.0], [2.0, 0.0, 0.0]], dtype=np.float32)
-    gr, gmean = gpu_ses_traj(two, None, 1.0, 1.0 / oses.ses_width(2.0), 50)
-    assert np.allclose(gmean, [49 / 50, 0, 0], atol=1e-6)
+    gr, gmean = gpu_ses_traj(two, None, 1.01, 1.0 / oses.ses_width(2.0), 50)
+    assert np.allclose(gmean, [49 / 50 * 1.01, 0, 0], atol=1e-6)
+    assert np.all(gr["failed"] == 0) and gr["t"][-1] == 50
 
 
 def test_ses_full_size_trajectory():
