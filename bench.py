@@ -159,6 +159,21 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
+def aggregate_timing(local_ms, steps, world, device):
+    """Whole-job timing over ranks: the slowest rank's time for `steps` steps
+    decides (MAX all-reduce); every rank processed `steps` iterations of its
+    own replica, so the job's throughput is world * steps / max time.
+    Returns (ms_per_step, iterations per second)."""
+    tot_ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([tot_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tot_ms = float(tt.item())
+    return tot_ms / steps, world * steps / (tot_ms / 1e3)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -232,13 +247,7 @@ def run_ours(args):
     wall = time.perf_counter() - w0
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    tot_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tot_ms = float(tt.item())
-    ms_per_step = tot_ms / args.steps
-    value = world * args.steps / (tot_ms / 1e3)
+    ms_per_step, value = aggregate_timing(sum(step_ms), args.steps, world, dev)
     rec = api.decode_steps(out)[0]
     if int(rec["t"]) != args.warmup + args.steps or int(rec["status"]) != 0:
         raise RuntimeError(f"not every timed step ran the full iteration: t={int(rec['t'])}, "

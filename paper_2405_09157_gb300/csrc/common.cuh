@@ -16,8 +16,12 @@ constexpr int kWarps = kBlock / 32;
 constexpr int kMaxBlock = 1024;       // largest CTA of any pass kernel
 constexpr int kMaxBlocksPerSM = 8;    // upper bound used to size the workspace
 // Completion stages every partial row in the last CTA's shared memory when
-// they fit in this many bytes; larger rows take the two-level completion.
-constexpr size_t kStageBytes = 96 * 1024;
+// they fit in this many bytes (kernels with one CTA per SM can spare much
+// more shared memory than those with several; rows much wider than 128
+// floats reduce faster through the two-level path); larger rows take the
+// two-level completion.
+constexpr size_t kStageBytesOneCta = 96 * 1024;
+constexpr size_t kStageBytesManyCta = 48 * 1024;
 constexpr size_t kHeadBytes = 1024;   // workspace: completion counters (top + per group)
 constexpr int kMaxGroups = 64;        // group rows reserved in the workspace
 
@@ -319,8 +323,8 @@ __device__ __forceinline__ void block_sum2_d(double& a, double& b, double* red) 
 
 // Whether the completion of a grid of nb CTAs with partial rows of `stride`
 // floats stages every row in shared memory (single level).
-__host__ __device__ inline bool single_level(int nb, int stride) {
-  return (size_t)nb * stride * sizeof(float) <= kStageBytes;
+__host__ __device__ inline bool single_level(int nb, int stride, size_t limit) {
+  return (size_t)nb * stride * sizeof(float) <= limit;
 }
 
 // Completion of one pass, in two calls. Every CTA has written its partial
@@ -357,24 +361,18 @@ __device__ void final_reduce(const float* rows, int stride, const float2* grows,
     reduce_rows(grows, 0, G, stride, raw, scratch, opof);
     return;
   }
-  // stride is a multiple of 4 and rows starts on a 256-byte boundary
+  // stride is a multiple of 4 and rows starts on a 256-byte boundary: copy
+  // 16-byte pieces global -> shared with cp.async (L2 only, no registers),
+  // all in flight at once, then wait for this thread's copies.
   const int n4 = nb * stride / 4;
   const float4* src = reinterpret_cast<const float4*>(rows);
   float4* dst = reinterpret_cast<float4*>(stage);
-  constexpr int kInFlight = 4;
-  for (int i0 = threadIdx.x; i0 < n4; i0 += kInFlight * blockDim.x) {
-    float4 v[kInFlight];
-#pragma unroll
-    for (int k = 0; k < kInFlight; ++k) {
-      const int i = i0 + k * blockDim.x;
-      if (i < n4) v[k] = __ldcg(src + i);
-    }
-#pragma unroll
-    for (int k = 0; k < kInFlight; ++k) {
-      const int i = i0 + k * blockDim.x;
-      if (i < n4) dst[i] = v[k];
-    }
+  for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+    const unsigned int saddr = (unsigned int)__cvta_generic_to_shared(dst + i);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(src + i) : "memory");
   }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   if (threadIdx.x == 0) counters[0] = 0u;
   __syncthreads();
   reduce_rows(stage, 0, nb, stride, raw, scratch, opof, true);

@@ -19,12 +19,19 @@ struct SesLauncher {
     const size_t pass_smem = (size_t)(block / 32) * 1 * dp * sizeof(float);
     const size_t fin_base = (size_t)(st + 2 * dp) * sizeof(double);
     size_t smem = pass_smem > fin_base ? pass_smem : fin_base;
-    const int grid = pass_grid(kern, smem, p.n, (32 / lpp) * points_per_lane_step * (block / 32), block);
+    int grid = pass_grid(kern, smem, p.n, (32 / lpp) * points_per_lane_step * (block / 32), block);
     SesParams q = p;
-    q.single = single_level(grid, st) ? 1 : 0;
+    q.single = single_level(grid, st, block >= 512 ? kStageBytesOneCta : kStageBytesManyCta) ? 1 : 0;
     if (q.single) {
       const size_t fin = fin_base + (size_t)grid * st * sizeof(float);
       if (fin > smem) smem = fin;
+      // the staging area may lower the CTAs per SM: keep the grid to one wave
+      if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+      }
+      const int g1 = pass_grid(kern, smem, p.n, (32 / lpp) * points_per_lane_step * (block / 32), block);
+      if (g1 < grid) grid = g1;
     }
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -375,13 +375,17 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
   const int64_t nwarps = (int64_t)gridDim.x * NW;
   const int64_t gw = (int64_t)blockIdx.x * NW + warp;
   constexpr int ROUND = PPW * NI;
+  // each warp streams one contiguous range of points, equal up to 8 points
+  // (balanced bytes per warp; starts on 8-point boundaries)
+  auto split = [&](int64_t w) { return w >= nwarps ? p.n : ((w * p.n / nwarps) & ~(int64_t)7); };
+  const int64_t lo = split(gw), hi = split(gw + 1);
   // the first round's point loads do not depend on the state: issue them first
   float x[NI][VW];
   auto load_round = [&](int64_t base) {
 #pragma unroll
     for (int r = 0; r < NI; ++r) {
         const int64_t i = base + r * PPW + grp;
-        if (i < p.n && has_chunk) {
+        if (i < hi && has_chunk) {
           Chunk<T, VW>::load(pts + i * d, gl, x[r]);
         } else {
 #pragma unroll
@@ -389,7 +393,7 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
         }
       }
   };
-  load_round(gw * ROUND);
+  load_round(lo);
 
   StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
   if (hdr->stopped && !p.eval_only) return;
@@ -407,8 +411,8 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
   }
   float S = 0.f, W = 0.f, maxd = -INFINITY;
 
-  for (int64_t base = gw * ROUND; base < p.n; base += nwarps * ROUND) {
-    if (base != gw * ROUND) load_round(base);
+  for (int64_t base = lo; base < hi; base += ROUND) {
+    if (base != lo) load_round(base);
     float part[NI];
 #pragma unroll
     for (int r = 0; r < NI; ++r) {
@@ -426,7 +430,7 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
     for (int k = 0; k < GS::OWN; ++k) {
       const int64_t i = base + GS::owned(gl, k) * PPW + grp;
       c[k] = 0.f;
-      if (i >= 1 && i < p.n) {
+      if (i >= 1 && i < hi) {
         const float dist = sqrtf(part[k]);
         const float gam = p.radii ? __ldg(p.radii + i) : 0.f;
         const float a = alpha - gam;
