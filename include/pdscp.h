@@ -267,6 +267,36 @@ pdscp_status svm_solve(const void* X_dev, int32_t dtype, const int8_t* labels_de
                        float* w_dev, pdscp_report* report_host);
 
 /*
+ * Batched SES (many independent instances, one launch per iteration for all).
+ * Instance i has n_i >= 2 points of dimension 1 <= d_i <= 64, stored row-major
+ * in one float32 buffer of pts_len floats starting at element offset_i
+ * (16-byte aligned starts enable 16-byte loads when d_i % 4 == 0). Each
+ * instance runs its own alpha-FTP (Sec. 3 with the SES data of Sec. 4.1)
+ * with its own state, kept in the workspace. Rows are cut into tiles of
+ * tile_rows (>= 32); a persistent grid takes tiles from a counter and the
+ * CTA that completes an instance's last tile finishes that instance.
+ *   ses_batch_workspace_size: bytes of the workspace (host sizes).
+ *   ses_batch_init: builds the tile tables (host -> workspace, synchronises
+ *     the stream) and starts every instance's alpha-FTP (t = 0, mean = v_1).
+ *   ses_batch_step: one MWU iteration of every instance (asynchronous);
+ *     alpha_dev and eta_over_rho_dev hold one double per instance; out_dev
+ *     (may be NULL) receives one pdscp_step_out per instance.
+ *   ses_batch_read: each instance's running mean and best centre, packed one
+ *     after another (instance i's d_i values after those of instances < i).
+ */
+pdscp_status ses_batch_workspace_size(int32_t num, const int64_t* n_host, const int32_t* d_host,
+                                      int32_t tile_rows, size_t* bytes_host);
+pdscp_status ses_batch_init(int32_t num, const float* pts_dev, int64_t pts_len,
+                            const int64_t* offset_host, const int64_t* n_host,
+                            const int32_t* d_host, int32_t tile_rows, void* ws_dev,
+                            size_t ws_bytes, pdscp_stream stream);
+pdscp_status ses_batch_step(int32_t num, const float* pts_dev, const double* alpha_dev,
+                            const double* eta_over_rho_dev, void* ws_dev, size_t ws_bytes,
+                            pdscp_stream stream, pdscp_step_out* out_dev);
+pdscp_status ses_batch_read(int32_t num, const void* ws_dev, float* mean_dev, float* best_dev,
+                            pdscp_stream stream);
+
+/*
  * Reverse-mode sweep through T unrolled MWU iterations at fixed alpha (the
  * gradient of the final objective with respect to the points). Not built yet:
  * returns PDSCP_ERR_NOT_IMPLEMENTED.

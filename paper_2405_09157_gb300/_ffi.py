@@ -66,6 +66,10 @@ SIGNATURES = {
                           c_vp, ctypes.POINTER(Report)]),
     "svm_solve": (c_i32, [c_vp, c_i32, c_vp, c_i64, c_i32, ctypes.POINTER(Options), c_vp, c_sz, c_vp,
                           c_vp, ctypes.POINTER(Report)]),
+    "ses_batch_workspace_size": (c_i32, [c_i32, c_vp, c_vp, c_i32, ctypes.POINTER(c_sz)]),
+    "ses_batch_init": (c_i32, [c_i32, c_vp, c_i64, c_vp, c_vp, c_vp, c_i32, c_vp, c_sz, c_vp]),
+    "ses_batch_step": (c_i32, [c_i32, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp, c_vp]),
+    "ses_batch_read": (c_i32, [c_i32, c_vp, c_vp, c_vp, c_vp]),
     "mwu_backward": (c_i32, [c_i32, c_vp, c_i32, c_vp, c_i64, c_i32, c_dbl, c_dbl, c_dbl, c_i64, c_i32,
                              c_vp, c_sz, c_vp, c_vp]),
 }

@@ -192,3 +192,60 @@ def svm_solve(X, labels, eps=1e-3, mode="practical", max_iters=1_000_000, poll_e
     if st != _ffi.PDSCP_OK and (raise_on_budget or st != 5):
         check(st, "svm_solve")
     return w, _report(rep)
+
+
+# ------------------------------------------------------------------ batched SES
+def pack_instances(arrays, device="cuda"):
+    """Pack float32 (n_i, d_i) arrays into one device buffer, each instance
+    starting on a 16-byte boundary. Returns (pts, offsets, n, d) where offsets,
+    n (int64) and d (int32) are numpy arrays."""
+    n = np.array([a.shape[0] for a in arrays], dtype=np.int64)
+    d = np.array([a.shape[1] for a in arrays], dtype=np.int32)
+    offs = np.zeros(len(arrays), dtype=np.int64)
+    pos = 0
+    for i, a in enumerate(arrays):
+        pos = (pos + 3) & ~3
+        offs[i] = pos
+        pos += a.size
+    host = np.zeros(max(pos, 4), dtype=np.float32)
+    for i, a in enumerate(arrays):
+        host[offs[i]:offs[i] + a.size] = np.ascontiguousarray(a, dtype=np.float32).reshape(-1)
+    return torch.from_numpy(host).to(device), offs, n, d
+
+
+class SesBatch:
+    """Many independent SES alpha-FTPs advanced together, one launch per iteration."""
+
+    def __init__(self, pts, offsets, n, d, tile_rows=4096, stream=None):
+        self.pts, self.num = pts, len(n)
+        self.offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        self.n = np.ascontiguousarray(n, dtype=np.int64)
+        self.d = np.ascontiguousarray(d, dtype=np.int32)
+        self.tile_rows = int(tile_rows)
+        lib = load()
+        size = ctypes.c_size_t()
+        check(lib.ses_batch_workspace_size(self.num, self.n.ctypes.data, self.d.ctypes.data, self.tile_rows,
+                                           ctypes.byref(size)), "ses_batch_workspace_size")
+        self.ws = torch.zeros(size.value, dtype=torch.uint8, device=pts.device)
+        self.init(stream)
+
+    def init(self, stream=None):
+        check(load().ses_batch_init(self.num, _vp(self.pts), self.pts.numel(), self.offsets.ctypes.data,
+                                    self.n.ctypes.data, self.d.ctypes.data, self.tile_rows, _vp(self.ws),
+                                    self.ws.numel(), _stream(stream)), "ses_batch_init")
+
+    def step(self, alpha, eta_over_rho, out=None, stream=None):
+        """alpha, eta_over_rho: float64 CUDA tensors of one value per instance."""
+        check(load().ses_batch_step(self.num, _vp(self.pts), _vp(alpha), _vp(eta_over_rho), _vp(self.ws),
+                                    self.ws.numel(), _stream(stream), _vp(out)), "ses_batch_step")
+
+    def read(self, stream=None):
+        """(means, bests): lists of float32 numpy arrays, one per instance."""
+        tot = int(self.d.sum())
+        m = torch.empty(tot, dtype=torch.float32, device=self.pts.device)
+        b = torch.empty(tot, dtype=torch.float32, device=self.pts.device)
+        check(load().ses_batch_read(self.num, _vp(self.ws), _vp(m), _vp(b), _stream(stream)), "ses_batch_read")
+        torch.cuda.synchronize()
+        cut = np.concatenate([[0], np.cumsum(self.d)])
+        mh, bh = m.cpu().numpy(), b.cpu().numpy()
+        return [mh[cut[i]:cut[i + 1]] for i in range(self.num)], [bh[cut[i]:cut[i + 1]] for i in range(self.num)]

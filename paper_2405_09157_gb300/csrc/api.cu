@@ -131,6 +131,12 @@ pdscp_status do_step(int problem, const void* pts, int dtype, const float* radii
 
 }  // namespace
 
+// Error reporting for the other translation units of the library.
+pdscp_status report_error(pdscp_status s, const char* msg) {
+  g_err = msg;
+  return s;
+}
+
 int device_sm_count() {
   static int cached[64] = {0};
   int dev = 0;

@@ -1,0 +1,163 @@
+// Host side of the batched SES iteration (batch_kernel.cuh): workspace
+// layout, per-instance tables and states, one-iteration launches.
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "batch_kernel.cuh"
+#include "dispatch.cuh"
+
+namespace pdscp {
+namespace {
+
+size_t r256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+pdscp_status err(pdscp_status s, const char* fmt, long long a = 0, long long b = 0) {
+  char buf[320];
+  snprintf(buf, sizeof(buf), fmt, a, b);
+  return report_error(s, buf);
+}
+
+struct BatchLayout {
+  int64_t ntiles;
+  size_t inst_off, instcnt_off, tile_off, partial_off, state_off, total;
+};
+
+pdscp_status batch_layout(int num, const int64_t* n, const int32_t* d, int tile_rows, BatchLayout* L,
+                          std::vector<BatchInst>* insts, std::vector<BatchTile>* tiles, const int64_t* offs) {
+  if (num < 1) return err(PDSCP_ERR_INVALID_ARG, "batch: num must be >= 1 (got %lld)", num);
+  if (!n || !d) return err(PDSCP_ERR_INVALID_ARG, "batch: null size arrays");
+  if (tile_rows < 32) return err(PDSCP_ERR_INVALID_ARG, "batch: tile_rows must be >= 32 (got %lld)", tile_rows);
+  int64_t T = 0;
+  for (int i = 0; i < num; ++i) {
+    if (n[i] < 2) return err(PDSCP_ERR_INVALID_ARG, "batch: instance %lld has n = %lld < 2", i, n[i]);
+    if (d[i] < 1 || d[i] > kBatchMaxD)
+      return err(PDSCP_ERR_NOT_IMPLEMENTED, "batch: instance %lld has d = %lld outside [1, 64]", i, d[i]);
+    T += (n[i] + tile_rows - 1) / tile_rows;
+  }
+  L->ntiles = T;
+  L->inst_off = 1024;
+  L->instcnt_off = L->inst_off + r256((size_t)num * sizeof(BatchInst));
+  L->tile_off = L->instcnt_off + r256((size_t)num * sizeof(unsigned int));
+  L->partial_off = L->tile_off + r256((size_t)T * sizeof(BatchTile));
+  L->state_off = L->partial_off + r256((size_t)T * kBatchStride * sizeof(float));
+  size_t so = L->state_off;
+  int64_t t0 = 0, moff = 0;
+  for (int i = 0; i < num; ++i) {
+    const int64_t nt = (n[i] + tile_rows - 1) / tile_rows;
+    if (insts) {
+      BatchInst in;
+      in.pt_off = offs ? offs[i] : 0;
+      in.n = n[i];
+      in.state_off = (int64_t)so;
+      in.tile0 = t0;
+      in.mean_off = moff;
+      in.ntiles = (int32_t)nt;
+      in.d = d[i];
+      in.shape = batch_shape(d[i], offs ? (offs[i] % 4 == 0) : false);
+      in.pad = 0;
+      insts->push_back(in);
+      for (int64_t k = 0; k < nt; ++k) {
+        BatchTile tl;
+        tl.inst = i;
+        tl.pad = 0;
+        tl.r0 = k * tile_rows;
+        tl.r1 = (k + 1) * tile_rows < n[i] ? (k + 1) * tile_rows : n[i];
+        tiles->push_back(tl);
+      }
+    }
+    so += r256(state_bytes(d[i]));
+    t0 += nt;
+    moff += d[i];
+  }
+  L->total = so;
+  return PDSCP_OK;
+}
+
+}  // namespace
+}  // namespace pdscp
+
+using namespace pdscp;
+
+extern "C" {
+
+pdscp_status ses_batch_workspace_size(int32_t num, const int64_t* n_host, const int32_t* d_host, int32_t tile_rows,
+                                      size_t* bytes_host) {
+  if (!bytes_host) return err(PDSCP_ERR_INVALID_ARG, "batch: null output pointer");
+  BatchLayout L;
+  pdscp_status st = batch_layout(num, n_host, d_host, tile_rows, &L, nullptr, nullptr, nullptr);
+  if (st != PDSCP_OK) return st;
+  *bytes_host = L.total;
+  return PDSCP_OK;
+}
+
+pdscp_status ses_batch_init(int32_t num, const float* pts_dev, int64_t pts_len, const int64_t* offset_host,
+                            const int64_t* n_host, const int32_t* d_host, int32_t tile_rows, void* ws_dev,
+                            size_t ws_bytes, pdscp_stream stream) {
+  if (!pts_dev || !offset_host || !ws_dev || !n_host || !d_host)
+    return err(PDSCP_ERR_INVALID_ARG, "batch: null pointer argument");
+  if (((uintptr_t)pts_dev % 4) != 0 || ((uintptr_t)ws_dev % 256) != 0)
+    return err(PDSCP_ERR_INVALID_ARG, "batch: points must be 4-byte and workspace 256-byte aligned");
+  for (int i = 0; i < num; ++i) {
+    if (offset_host[i] < 0) return err(PDSCP_ERR_INVALID_ARG, "batch: negative offset for instance %lld", i);
+    if (n_host[i] < 0 || d_host[i] < 0 || offset_host[i] + n_host[i] * (int64_t)d_host[i] > pts_len)
+      return err(PDSCP_ERR_INVALID_ARG, "batch: instance %lld extends past the %lld points' floats", i, pts_len);
+  }
+  BatchLayout L;
+  std::vector<BatchInst> insts;
+  std::vector<BatchTile> tiles;
+  insts.reserve(num);
+  pdscp_status st = batch_layout(num, n_host, d_host, tile_rows, &L, &insts, &tiles, offset_host);
+  if (st != PDSCP_OK) return st;
+  if (ws_bytes < L.total) return err(PDSCP_ERR_WORKSPACE, "batch: workspace %lld < %lld bytes", (long long)ws_bytes,
+                                     (long long)L.total);
+  // 16-byte loads need each instance's rows to start on a 16-byte boundary
+  for (auto& in : insts)
+    if (in.shape <= 4 && (((uintptr_t)(pts_dev + in.pt_off)) % 16) != 0) in.shape = batch_shape(in.d, false);
+  unsigned char* ws = reinterpret_cast<unsigned char*>(ws_dev);
+  cudaStream_t s = (cudaStream_t)stream;
+  BatchHeader bh{num, L.ntiles, (int64_t)L.inst_off, (int64_t)L.instcnt_off, (int64_t)L.tile_off,
+                 (int64_t)L.partial_off};
+  cudaError_t e = cudaMemsetAsync(ws, 0, 256, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ws + 256, &bh, sizeof(bh), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ws + L.inst_off, insts.data(), insts.size() * sizeof(BatchInst), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ws + L.tile_off, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host tables go out of scope
+  if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: table upload failed (%lld)", (long long)e);
+  ses_batch_init_kernel<<<num, 64, 0, s>>>(pts_dev, reinterpret_cast<const BatchInst*>(ws + L.inst_off), ws,
+                                            reinterpret_cast<unsigned int*>(ws + L.instcnt_off));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: init launch failed (%lld)", (long long)e);
+  return PDSCP_OK;
+}
+
+pdscp_status ses_batch_step(int32_t num, const float* pts_dev, const double* alpha_dev,
+                            const double* eta_over_rho_dev, void* ws_dev, size_t ws_bytes, pdscp_stream stream,
+                            pdscp_step_out* out_dev) {
+  if (num < 1 || !pts_dev || !alpha_dev || !eta_over_rho_dev || !ws_dev)
+    return err(PDSCP_ERR_INVALID_ARG, "batch: bad argument to ses_batch_step");
+  if (ws_bytes < 1024) return err(PDSCP_ERR_WORKSPACE, "batch: workspace too small");
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ses_batch_kernel, kBatchBlock, 0) != cudaSuccess || occ < 1)
+    occ = 1;
+  const int grid = device_sm_count() * occ;
+  BatchParams p{pts_dev, alpha_dev, eta_over_rho_dev, reinterpret_cast<unsigned char*>(ws_dev), out_dev};
+  ses_batch_kernel<<<grid, kBatchBlock, 0, (cudaStream_t)stream>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: step launch failed (%lld)", (long long)e);
+  return PDSCP_OK;
+}
+
+pdscp_status ses_batch_read(int32_t num, const void* ws_dev, float* mean_dev, float* best_dev, pdscp_stream stream) {
+  if (num < 1 || !ws_dev) return err(PDSCP_ERR_INVALID_ARG, "batch: bad argument to ses_batch_read");
+  unsigned char* ws = reinterpret_cast<unsigned char*>(const_cast<void*>(ws_dev));
+  ses_batch_read_kernel<<<num, 64, 0, (cudaStream_t)stream>>>(reinterpret_cast<const BatchInst*>(ws + 1024), ws,
+                                                              mean_dev, best_dev);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: read launch failed (%lld)", (long long)e);
+  return PDSCP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,313 @@
+// Batched SES iteration: one launch runs one MWU iteration (Sec. 4.1 with
+// Eq. implement and Eq. ses_oracle, as in ses_kernel.cuh) for every instance
+// of a batch of independent SES problems of uneven size n_i and dimension
+// d_i <= 64. The instances' points are packed in one float32 buffer; each
+// instance is cut into tiles of consecutive rows. A persistent grid takes
+// tiles from a global counter; the CTA that completes an instance's last
+// tile reduces that instance's partial rows and runs its O(d) finish while
+// the other CTAs keep streaming. No CTA waits on another.
+#pragma once
+
+#include "ses_kernel.cuh"
+
+namespace pdscp {
+
+constexpr int kBatchMaxD = 64;
+constexpr int kBatchStride = 4 + kBatchMaxD;  // partial row: S, Wt, maxd, 0, G'_1..G'_d
+constexpr int kBatchBlock = 256;
+constexpr int kBatchWarps = kBatchBlock / 32;
+
+struct BatchInst {
+  int64_t pt_off;     // element offset of the instance's row 0 in the packed buffer
+  int64_t n;          // rows (points) of the instance
+  int64_t state_off;  // byte offset of the instance's state in the workspace
+  int64_t tile0;      // first tile of the instance
+  int64_t mean_off;   // offset of the instance's d values in packed per-instance outputs
+  int32_t ntiles;
+  int32_t d;
+  int32_t shape;      // load/lane layout (batch_shape)
+  int32_t pad;
+};
+static_assert(sizeof(BatchInst) == 56, "instance record layout");
+
+struct BatchTile {
+  int32_t inst;
+  int32_t pad;
+  int64_t r0, r1;  // rows [r0, r1) of the instance
+};
+
+// Workspace of a batch: [counters 256 B][BatchHeader at 256][...] with the
+// tables at the offsets the header records (written once by ses_batch_init).
+struct BatchHeader {
+  int64_t num, ntiles;
+  int64_t inst_off, instcnt_off, tile_off, partial_off;
+};
+
+struct BatchParams {
+  const float* pts;
+  const double* alpha;         // per instance
+  const double* eta_over_rho;  // per instance
+  unsigned char* ws;           // workspace base
+  pdscp_step_out* out;         // per instance, may be null
+};
+
+// Load/lane layouts, chosen on the host per instance:
+//   0..4: 16-byte chunks, LPP = 1, 2, 4, 8, 16 (d = 4 * LPP or less, d % 4 == 0, aligned)
+//   5: scalar, 2 lanes (d <= 2); 6: scalar, 8 lanes (d <= 8); 7: scalar, 32 lanes (d <= 32);
+//   8: scalar, 32 lanes x 2 (d <= 64)
+inline int batch_shape(int d, bool aligned16) {
+  if (d % 4 == 0 && aligned16) {
+    const int c = d / 4;
+    return c <= 1 ? 0 : c <= 2 ? 1 : c <= 4 ? 2 : c <= 8 ? 3 : 4;
+  }
+  return d <= 2 ? 5 : d <= 8 ? 6 : d <= 32 ? 7 : 8;
+}
+
+// Streams rows [r0, r1) of one instance at mean ubar (in shared memory, FP32)
+// and leaves the CTA's totals in sG/s_sc (per warp). Same per-point
+// arithmetic as ses_iter_kernel (rows 0 of the instance, v_1, excluded).
+template <int VW, int LPP, int NCH, int U>
+__device__ void batch_tile(const float* pts, int d, int64_t r0, int64_t r1, const float* s_ub, float kr, float H,
+                           float alpha, float* sG, float (*s_sc)[3]) {
+  const int nch = (d + VW - 1) / VW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / LPP, gl = lane % LPP;
+  constexpr int PPW = 32 / LPP;
+  float ub[NCH][VW], G[NCH][VW];
+#pragma unroll
+  for (int j = 0; j < NCH; ++j) {
+    const int c = gl + j * LPP;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      ub[j][e] = (c < nch) ? s_ub[c * VW + e] : 0.f;
+      G[j][e] = 0.f;
+    }
+  }
+  float S = 0.f, W = 0.f, maxd = -INFINITY;
+  for (int64_t base = r0 + (int64_t)warp * (PPW * U); base < r1; base += (int64_t)kBatchWarps * (PPW * U)) {
+    float x[U][NCH][VW];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * PPW + grp;
+      const float* row = pts + i * d;
+#pragma unroll
+      for (int j = 0; j < NCH; ++j) {
+        const int c = gl + j * LPP;
+        if (i < r1 && c < nch) {
+          Chunk<float, VW>::load(row, c, x[u][j]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VW; ++e) x[u][j][e] = 0.f;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * PPW + grp;
+      float part = 0.f;
+#pragma unroll
+      for (int j = 0; j < NCH; ++j)
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          x[u][j][e] -= ub[j][e];
+          part = fmaf(x[u][j][e], x[u][j][e], part);
+        }
+      const float dist2 = group_sum<LPP>(part);
+      float c = 0.f;
+      if (i >= 1 && i < r1) {
+        const float dist = sqrtf(dist2);
+        const float E1 = expf(kr * (dist - H));
+        const float em = -expm1f(-2.f * kr * dist);
+        const float dif = E1 * em;
+        const float sum = E1 * (2.f - em);
+        c = dist > 0.f ? dif / dist : 2.f * kr * E1;
+        if (gl == 0) {
+          S += sum;
+          W += alpha * sum - dist * dif;
+          maxd = fmaxf(maxd, dist);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NCH; ++j)
+#pragma unroll
+        for (int e = 0; e < VW; ++e) G[j][e] = fmaf(c, x[u][j][e], G[j][e]);
+    }
+  }
+#pragma unroll
+  for (int o = LPP; o < 32; o <<= 1)
+#pragma unroll
+    for (int j = 0; j < NCH; ++j)
+#pragma unroll
+      for (int e = 0; e < VW; ++e) G[j][e] += __shfl_xor_sync(0xffffffffu, G[j][e], o);
+  S = warp_sum(S);
+  W = warp_sum(W);
+  maxd = warp_max(maxd);
+  if (grp == 0) {
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) {
+      const int c = gl + j * LPP;
+      if (c < nch)
+#pragma unroll
+        for (int e = 0; e < VW; ++e) sG[warp * kBatchMaxD + c * VW + e] = G[j][e];
+    }
+  }
+  if (lane == 0) {
+    s_sc[warp][0] = S;
+    s_sc[warp][1] = W;
+    s_sc[warp][2] = maxd;
+  }
+}
+
+__global__ void __launch_bounds__(kBatchBlock) ses_batch_kernel(BatchParams p) {
+  __shared__ float sG[kBatchWarps * kBatchMaxD];
+  __shared__ float s_sc[kBatchWarps][3];
+  __shared__ float s_ub[kBatchMaxD];
+  __shared__ float2 raw[kBatchStride];
+  __shared__ double s_mean[kBatchMaxD];
+  __shared__ double s_v1[kBatchMaxD];
+  __shared__ float2 s_scr[kBatchBlock];
+  __shared__ __align__(16) double s_hdr[sizeof(StateHdr) / 8];
+  __shared__ long long s_tile;
+  __shared__ bool s_flag;
+  const int tid = threadIdx.x;
+  auto opof = [](int pc) { return pc == 2 ? 1 : 0; };
+  const BatchHeader bh = *reinterpret_cast<const BatchHeader*>(p.ws + 256);
+  unsigned int* counters = reinterpret_cast<unsigned int*>(p.ws);  // [0] next tile, [1] CTAs done
+  unsigned int* inst_counters = reinterpret_cast<unsigned int*>(p.ws + bh.instcnt_off);
+  const BatchInst* insts = reinterpret_cast<const BatchInst*>(p.ws + bh.inst_off);
+  const BatchTile* tiles = reinterpret_cast<const BatchTile*>(p.ws + bh.tile_off);
+  float* partials = reinterpret_cast<float*>(p.ws + bh.partial_off);
+
+  for (;;) {
+    if (tid == 0) s_tile = (long long)atomicAdd(&counters[0], 1u);
+    __syncthreads();
+    const long long tile = s_tile;
+    if (tile >= bh.ntiles) break;
+    const BatchTile tl = tiles[tile];
+    const BatchInst in = insts[tl.inst];
+    void* state = p.ws + in.state_off;
+    const StateHdr* hdr = reinterpret_cast<const StateHdr*>(state);
+    const int d = in.d;
+    const float* pts = p.pts + in.pt_off;
+    const bool stopped = hdr->stopped != 0;
+    if (!stopped) {
+      const float kr = (float)((double)hdr->t * p.eta_over_rho[tl.inst] / kSqrt2);
+      const float H = (float)(hdr->hint + hdr->move);
+      const float alpha = (float)p.alpha[tl.inst];
+      const float* mean32 = state_mean32(state, d);
+      if (tid < d) s_ub[tid] = mean32[tid];
+      __syncthreads();
+      switch (in.shape) {
+        case 0: batch_tile<4, 1, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
+        case 1: batch_tile<4, 2, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
+        case 2: batch_tile<4, 4, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
+        case 3: batch_tile<4, 8, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
+        case 4: batch_tile<4, 16, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
+        case 5: batch_tile<1, 2, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
+        case 6: batch_tile<1, 8, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
+        case 7: batch_tile<1, 32, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
+        default: batch_tile<1, 32, 2, 2>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
+      }
+      __syncthreads();
+      float* prow = partials + (size_t)tile * kBatchStride;
+      for (int j = tid; j < d; j += kBatchBlock) {
+        float s = 0.f;
+        for (int w = 0; w < kBatchWarps; ++w) s += sG[w * kBatchMaxD + j];
+        prow[4 + j] = s;
+      }
+      if (tid == 0) {
+        float s0 = 0.f, s1 = 0.f, m = -INFINITY;
+        for (int w = 0; w < kBatchWarps; ++w) {
+          s0 += s_sc[w][0];
+          s1 += s_sc[w][1];
+          m = fmaxf(m, s_sc[w][2]);
+        }
+        prow[0] = s0;
+        prow[1] = s1;
+        prow[2] = m;
+        prow[3] = 0.f;
+      }
+    }
+    // arrival of this tile at its instance
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      const unsigned int prev = atomicAdd(&inst_counters[tl.inst], 1u);
+      __threadfence();
+      s_flag = (prev == (unsigned int)(in.ntiles - 1));
+    }
+    __syncthreads();
+    if (s_flag) {
+      // this CTA completed the instance: reduce its rows and finish it
+      if (tid == 0) inst_counters[tl.inst] = 0u;
+      if (!stopped) {
+        constexpr int HW = (int)(sizeof(StateHdr) / 8);
+        if (tid < HW) s_hdr[tid] = reinterpret_cast<const double*>(hdr)[tid];
+        const double* mean = state_mean(state);
+        if (tid < d) {
+          s_mean[tid] = mean[tid];
+          s_v1[tid] = (double)pts[tid];
+        }
+        const int st = 4 + dpad4(d);
+        // rows of this instance: stride kBatchStride, the first st columns used
+        reduce_rows(partials + (size_t)in.tile0 * kBatchStride, 0, in.ntiles, st, raw, s_scr, opof, false,
+                    kBatchStride);
+        if (tid < 32)
+          ses_finish_warp(raw, s_mean, s_v1, *reinterpret_cast<const StateHdr*>(s_hdr), state, d,
+                          p.alpha[tl.inst], 0.0, p.eta_over_rho[tl.inst], 0, p.out ? p.out + tl.inst : nullptr);
+      }
+    }
+    __syncthreads();
+  }
+  // last CTA out resets the tile counter for the next launch
+  if (tid == 0) {
+    __threadfence();
+    const unsigned int prev = atomicAdd(&counters[1], 1u);
+    if (prev == gridDim.x - 1) {
+      counters[0] = 0u;
+      counters[1] = 0u;
+      __threadfence();
+    }
+  }
+}
+
+// Fresh alpha-FTP states for every instance (t = 0, mean = v_1); one CTA per instance.
+__global__ void ses_batch_init_kernel(const float* pts, const BatchInst* inst, unsigned char* ws,
+                                      unsigned int* inst_counters) {
+  const BatchInst in = inst[blockIdx.x];
+  void* state = ws + in.state_off;
+  const int d = in.d;
+  const int dp = dpad4(d);
+  double* mean = state_mean(state);
+  float* mean32 = state_mean32(state, d);
+  float* best = state_best(state, d);
+  for (int j = threadIdx.x; j < dp; j += blockDim.x) {
+    const double v = j < d ? (double)pts[in.pt_off + j] : 0.0;
+    mean[j] = v;
+    mean32[j] = (float)v;
+    best[j] = (float)v;
+  }
+  if (threadIdx.x == 0) {
+    StateHdr h;
+    memset(&h, 0, sizeof(h));
+    h.rules = PDSCP_RULES_NONE;
+    h.patience = 1;
+    h.f_prev = -1.0;
+    h.best_f = INFINITY;
+    h.ub_best = INFINITY;
+    *reinterpret_cast<StateHdr*>(state) = h;
+    inst_counters[blockIdx.x] = 0u;
+  }
+}
+
+// Means and best centres of every instance, packed at inst.mean_off.
+__global__ void ses_batch_read_kernel(const BatchInst* inst, unsigned char* ws, float* mean_out, float* best_out) {
+  const BatchInst in = inst[blockIdx.x];
+  void* state = ws + in.state_off;
+  for (int j = threadIdx.x; j < in.d; j += blockDim.x) {
+    if (mean_out) mean_out[in.mean_off + j] = state_mean32(state, in.d)[j];
+    if (best_out) best_out[in.mean_off + j] = state_best(state, in.d)[j];
+  }
+}
+
+}  // namespace pdscp

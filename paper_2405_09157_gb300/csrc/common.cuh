@@ -204,7 +204,8 @@ __device__ __forceinline__ TIn load_row_elem(const TIn* p, bool shared_src) {
 
 template <typename TIn, typename OpOf>
 __device__ void reduce_rows(const TIn* m, int r0, int r1, int stride, float2* out, float2* scratch, OpOf opof,
-                            bool shared_src = false) {
+                            bool shared_src = false, int ld = 0) {
+  const size_t pitch = ld > 0 ? (size_t)ld : (size_t)stride;  // row pitch; the first `stride` columns are reduced
   const int nt = blockDim.x;
   int R = 1;
   while (2 * R * stride <= nt && R < 32) R *= 2;
@@ -213,7 +214,7 @@ __device__ void reduce_rows(const TIn* m, int r0, int r1, int stride, float2* ou
       const int op = opof(pc);
       float2 acc = col_init2(op);
 #pragma unroll 8
-      for (int r = r0; r < r1; ++r) col_comb2(op, acc, as_pair(load_row_elem(m + (size_t)r * stride + pc, shared_src)));
+      for (int r = r0; r < r1; ++r) col_comb2(op, acc, as_pair(load_row_elem(m + (size_t)r * pitch + pc, shared_src)));
       out[pc] = acc;
     }
     __syncthreads();
@@ -225,7 +226,7 @@ __device__ void reduce_rows(const TIn* m, int r0, int r1, int stride, float2* ou
     const int op = opof(pc);
     float2 acc = col_init2(op);
 #pragma unroll 8
-    for (int r = r0 + q; r < r1; r += R) col_comb2(op, acc, as_pair(load_row_elem(m + (size_t)r * stride + pc, shared_src)));
+    for (int r = r0 + q; r < r1; r += R) col_comb2(op, acc, as_pair(load_row_elem(m + (size_t)r * pitch + pc, shared_src)));
     scratch[q * stride + pc] = acc;
   }
   __syncthreads();

@@ -14,6 +14,7 @@ struct LaunchCfg {
 };
 
 int device_sm_count();
+pdscp_status report_error(pdscp_status s, const char* msg);  // sets pdscp_last_error()
 
 // Calls L.template go<VW, LPP, NCH>() for the instance that serves d.
 // vec: rows start on 16-byte boundaries and hold a whole number of 16-byte

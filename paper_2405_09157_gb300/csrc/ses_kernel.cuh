@@ -190,6 +190,130 @@ __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
 // O(d) finish of one SES iteration. Every CTA calls it after writing its
 // partial row [S, Wt, maxd, 0, G'_1..G'_d]; the two-level completion elects
 // one CTA, which reduces the group rows in FP64 and does the rest.
+// The O(d) finish of one SES iteration from the column totals: run by one
+// warp (lane = threadIdx.x & 31). raw: [S, Wt, maxd, 0, G'_1..G'_d] as
+// compensated pairs; s_mean, s_v1: the mean read by the pass and v_1 (FP64,
+// shared memory); h: a copy of the state header. Writes the state and the
+// step record (out, may be null).
+static __device__ __noinline__ void ses_finish_warp(const float2* raw, const double* s_mean, const double* s_v1,
+                                             const StateHdr& h, void* state, int d, double alpha_d, double gam1,
+                                             double eta_over_rho, int eval_only, pdscp_step_out* out) {
+  const int lane = threadIdx.x & 31;
+  StateHdr* hdr = reinterpret_cast<StateHdr*>(state);
+  double* mean = state_mean(state);
+  float* mean32 = state_mean32(state, d);
+  float* best = state_best(state, d);
+  const double alpha_in = alpha_d;
+  // The finish works in FP32 (FP64 is slow here and its dependent chains
+  // dominated this step): its inputs are compensated sums accurate to ~1e-7,
+  // and its results feed tolerances of 1e-5. FP64 is kept for the running
+  // mean, which accumulates over the whole alpha-FTP, and for the Sec. 5
+  // ratio test, which decides an integer as the oracle does.
+  auto tot = [&](int pc) { return raw[pc].x + raw[pc].y; };
+  const float S = tot(0), Wt = tot(1), maxd = raw[2].x;
+  const float alpha = (float)alpha_in;
+  const float gam1f = (float)gam1;
+  const float inv = 1.0f / ((float)kSqrt2 * S);  // g = G' / (sqrt2 S)
+  // A = |g|^2, B = g . (v_1 - ubar), C = |ubar - v_1|^2
+  float acc[3] = {0.f, 0.f, 0.f};
+  for (int j = lane; j < d; j += 32) {
+    const float g = tot(4 + j) * inv;
+    const float dv = (float)(s_v1[j] - s_mean[j]);
+    acc[0] = fmaf(g, g, acc[0]);
+    acc[1] = fmaf(g, dv, acc[1]);
+    acc[2] = fmaf(dv, dv, acc[2]);
+  }
+  warp_sum_kf<3>(acc);
+  const float A = acc[0], B = acc[1], C = acc[2];
+  const float rad = alpha - gam1f;
+  const float rng = A > 0.f ? 1.0f / sqrtf(A) : 0.f;
+  const float ng = A * rng;                 // ||g||
+  const float step = rad * rng;             // u = v_1 + step g  (u = v_1 when g = 0)
+  const float V = B + step * A + Wt * inv;  // g.(u - ubar) + Wt/(sqrt2 S): Eq. (ses_oracle) value
+  const float LB = fmaxf(gam1f, alpha - V / (ng + (float)(1.0 / kSqrt2)));  // Eq. (primal_construction)
+  const float f = fmaxf(maxd, sqrtf(C) + gam1f);                             // f at the mean read (Sec. 5)
+  const double fd = (double)f;
+
+  const int64_t t = h.t;
+  int status = PDSCP_OK;
+  if (!(S > 0.f) || !isfinite(S) || !isfinite(V) || !isfinite(f)) status = PDSCP_ERR_NUMERIC;
+  bool stop = false, failed = false;
+  int outcome = PDSCP_OUT_RUNNING;
+  const bool better = (t > 0 && fd < h.best_f);
+  int streak = h.streak;
+  bool set_fprev = false;
+  if (!eval_only) {
+    failed = V < 0.f;
+    if (status != PDSCP_OK) {
+      stop = true;
+    } else if (failed) {
+      stop = true;
+      outcome = PDSCP_OUT_SEPARATED;
+    } else if (h.rules == PDSCP_RULES_PRACTICAL && t > 0) {
+      if (fd < alpha_in) {
+        stop = true;
+        outcome = PDSCP_OUT_BEAT_ALPHA;
+      } else {
+        const double fp = h.f_prev;
+        if (fp > 0.0) {
+          streak = (fabs(fd - fp) / fp < h.delta) ? streak + 1 : 0;
+          if (streak >= h.patience) {
+            stop = true;
+            outcome = PDSCP_OUT_STALLED;
+          }
+        }
+        set_fprev = !stop;
+      }
+    }
+  }
+  const bool advance = !eval_only && !stop;
+  const float rtp1 = 1.0f / (float)(t + 1);  // 1 / (t + 1)
+  for (int j = lane; j < d; j += 32) {
+    const double m = s_mean[j];
+    if (better) best[j] = (float)m;
+    if (advance) {
+      const float mf = (float)m;
+      const float u = (float)s_v1[j] + step * (tot(4 + j) * inv);
+      const double nm = m + (double)((u - mf) * rtp1);
+      mean[j] = nm;
+      mean32[j] = (float)nm;
+    }
+  }
+  if (lane == 0) {
+    if (!eval_only && (double)LB > h.lb_best) hdr->lb_best = (double)LB;
+    if (streak != h.streak) hdr->streak = streak;
+    if (set_fprev) hdr->f_prev = fd;
+    if (better) hdr->best_f = fd;
+    hdr->hint = (double)maxd;
+    // ||ubar^{t+1} - ubar^t|| = ||u - ubar|| / (t+1), ||u - ubar||^2 = C + 2 step B + step^2 A
+    const float mv2 = C + 2.f * step * B + step * step * A;
+    hdr->move = advance ? (double)(rtp1 * sqrtf(fmaxf(mv2, 0.f))) * (1.0 + 1e-5) : 0.0;
+    const int64_t tn = t + (advance ? 1 : 0);
+    hdr->t = tn;
+    if (stop) {
+      hdr->stopped = 1;
+      hdr->outcome = outcome;
+    }
+    if (status != PDSCP_OK) hdr->status = status;
+    hdr->last_value = (double)V;
+    if (out) {
+      pdscp_step_out o;
+      o.oracle_value = (double)V;
+      o.objective = fd;
+      o.lower_bound = (double)LB;
+      o.upper_bound = fd;
+      o.t = tn;
+      o.failed = failed ? 1 : 0;
+      o.stopped = (stop || h.stopped) ? 1 : 0;
+      o.status = status;
+      o.outcome = outcome;
+      o.k = (double)t * eta_over_rho;
+      *out = o;
+    }
+  }
+
+}
+
 template <typename T>
 __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw) {
   __shared__ float2 s_scr[kMaxBlock];
@@ -233,115 +357,9 @@ __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw) {
   // would only contend across warps; no block barrier follows.
   if (tid >= 32) return;
   const int lane = tid;
-  const StateHdr& h = *reinterpret_cast<const StateHdr*>(s_hdr);
-  // The finish works in FP32 (FP64 is slow here and its dependent chains
-  // dominated this step): its inputs are compensated sums accurate to ~1e-7,
-  // and its results feed tolerances of 1e-5. FP64 is kept for the running
-  // mean, which accumulates over the whole alpha-FTP, and for the Sec. 5
-  // ratio test, which decides an integer as the oracle does.
-  auto tot = [&](int pc) { return raw[pc].x + raw[pc].y; };
-  const float S = tot(0), Wt = tot(1), maxd = raw[2].x;
-  const float alpha = (float)p.alpha;
-  const float gam1f = (float)gam1;
-  const float inv = 1.0f / ((float)kSqrt2 * S);  // g = G' / (sqrt2 S)
-  // A = |g|^2, B = g . (v_1 - ubar), C = |ubar - v_1|^2
-  float acc[3] = {0.f, 0.f, 0.f};
-  for (int j = lane; j < d; j += 32) {
-    const float g = tot(4 + j) * inv;
-    const float dv = (float)(s_v1[j] - s_mean[j]);
-    acc[0] = fmaf(g, g, acc[0]);
-    acc[1] = fmaf(g, dv, acc[1]);
-    acc[2] = fmaf(dv, dv, acc[2]);
-  }
-  warp_sum_kf<3>(acc);
-  const float A = acc[0], B = acc[1], C = acc[2];
-  const float rad = alpha - gam1f;
-  const float rng = A > 0.f ? 1.0f / sqrtf(A) : 0.f;
-  const float ng = A * rng;                 // ||g||
-  const float step = rad * rng;             // u = v_1 + step g  (u = v_1 when g = 0)
-  const float V = B + step * A + Wt * inv;  // g.(u - ubar) + Wt/(sqrt2 S): Eq. (ses_oracle) value
-  const float LB = fmaxf(gam1f, alpha - V / (ng + (float)(1.0 / kSqrt2)));  // Eq. (primal_construction)
-  const float f = fmaxf(maxd, sqrtf(C) + gam1f);                             // f at the mean read (Sec. 5)
-  const double fd = (double)f;
-
-  const int64_t t = h.t;
-  int status = PDSCP_OK;
-  if (!(S > 0.f) || !isfinite(S) || !isfinite(V) || !isfinite(f)) status = PDSCP_ERR_NUMERIC;
-  bool stop = false, failed = false;
-  int outcome = PDSCP_OUT_RUNNING;
-  const bool better = (t > 0 && fd < h.best_f);
-  int streak = h.streak;
-  bool set_fprev = false;
-  if (!p.eval_only) {
-    failed = V < 0.f;
-    if (status != PDSCP_OK) {
-      stop = true;
-    } else if (failed) {
-      stop = true;
-      outcome = PDSCP_OUT_SEPARATED;
-    } else if (h.rules == PDSCP_RULES_PRACTICAL && t > 0) {
-      if (fd < p.alpha) {
-        stop = true;
-        outcome = PDSCP_OUT_BEAT_ALPHA;
-      } else {
-        const double fp = h.f_prev;
-        if (fp > 0.0) {
-          streak = (fabs(fd - fp) / fp < h.delta) ? streak + 1 : 0;
-          if (streak >= h.patience) {
-            stop = true;
-            outcome = PDSCP_OUT_STALLED;
-          }
-        }
-        set_fprev = !stop;
-      }
-    }
-  }
-  const bool advance = !p.eval_only && !stop;
-  const float rtp1 = 1.0f / (float)(t + 1);  // 1 / (t + 1)
-  for (int j = lane; j < d; j += 32) {
-    const double m = s_mean[j];
-    if (better) best[j] = (float)m;
-    if (advance) {
-      const float mf = (float)m;
-      const float u = (float)s_v1[j] + step * (tot(4 + j) * inv);
-      const double nm = m + (double)((u - mf) * rtp1);
-      mean[j] = nm;
-      mean32[j] = (float)nm;
-    }
-  }
-  if (lane == 0) {
-    if (!p.eval_only && (double)LB > h.lb_best) hdr->lb_best = (double)LB;
-    if (streak != h.streak) hdr->streak = streak;
-    if (set_fprev) hdr->f_prev = fd;
-    if (better) hdr->best_f = fd;
-    hdr->hint = (double)maxd;
-    // ||ubar^{t+1} - ubar^t|| = ||u - ubar|| / (t+1), ||u - ubar||^2 = C + 2 step B + step^2 A
-    const float mv2 = C + 2.f * step * B + step * step * A;
-    hdr->move = advance ? (double)(rtp1 * sqrtf(fmaxf(mv2, 0.f))) * (1.0 + 1e-5) : 0.0;
-    const int64_t tn = t + (advance ? 1 : 0);
-    hdr->t = tn;
-    if (stop) {
-      hdr->stopped = 1;
-      hdr->outcome = outcome;
-    }
-    if (status != PDSCP_OK) hdr->status = status;
-    hdr->last_value = (double)V;
-    if (p.out) {
-      pdscp_step_out o;
-      o.oracle_value = (double)V;
-      o.objective = fd;
-      o.lower_bound = (double)LB;
-      o.upper_bound = fd;
-      o.t = tn;
-      o.failed = failed ? 1 : 0;
-      o.stopped = (stop || h.stopped) ? 1 : 0;
-      o.status = status;
-      o.outcome = outcome;
-      o.k = (double)t * p.eta_over_rho;
-      *p.out = o;
-    }
-  }
-
+  (void)lane;
+  ses_finish_warp(raw, s_mean, s_v1, *reinterpret_cast<const StateHdr*>(s_hdr), p.state, d, p.alpha, gam1,
+                  p.eta_over_rho, p.eval_only, p.out);
 }
 
 }  // namespace pdscp

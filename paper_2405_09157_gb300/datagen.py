@@ -59,6 +59,16 @@ def svm_clusters(n1, n2, d, mu_norm=3.0, band=0.1, seed=0):
     return X, y
 
 
+def batched_ses_sizes(num, n_min=100, n_max=100_000, dims=(2, 3, 8, 16, 32, 64), seed=0):
+    """Sizes of the batched workload: (n, d, scale) arrays of `num` instances,
+    n log-uniform in [n_min, n_max], d uniform over `dims`, scale U[0.1, 10]."""
+    rng = _rng(seed)
+    n = np.round(np.exp(rng.uniform(np.log(n_min), np.log(n_max), num))).astype(np.int64)
+    d = np.asarray(dims, dtype=np.int32)[rng.integers(len(dims), size=num)]
+    scale = rng.uniform(0.1, 10.0, num)
+    return n, d, scale
+
+
 def batched_ses(num, n_min=100, n_max=100_000, dims=(2, 3, 8, 16, 32, 64), seed=0):
     """List of `num` SES instances (float32 (n_i, d_i) arrays): n_i log-uniform
     in [n_min, n_max], d_i uniform over `dims`, points N(0, I) times a

@@ -73,3 +73,20 @@ def test_argument_validation_without_gpu(lib):
     assert st == 1 and b"poll_every" in lib.pdscp_last_error()
     st = lib.mwu_backward(_ffi.SES, fake, _ffi.F32, None, 10, 4, 1.0, 0.1, 1.0, 10, 5, fake, 1 << 30, None, fake)
     assert st == 7
+
+
+def test_batch_validation_without_gpu(lib):
+    n = (ctypes.c_int64 * 2)(100, 1)
+    d = (ctypes.c_int32 * 2)(8, 8)
+    size = ctypes.c_size_t()
+    assert lib.ses_batch_workspace_size(2, n, d, 4096, ctypes.byref(size)) == 1  # n < 2
+    n[1] = 50
+    d[1] = 65
+    assert lib.ses_batch_workspace_size(2, n, d, 4096, ctypes.byref(size)) == 7  # d > 64
+    d[1] = 8
+    assert lib.ses_batch_workspace_size(2, n, d, 16, ctypes.byref(size)) == 1    # tile_rows < 32
+    assert lib.ses_batch_workspace_size(2, n, d, 4096, ctypes.byref(size)) == 0 and size.value > 0
+    offs = (ctypes.c_int64 * 2)(0, 800)
+    fake = ctypes.c_void_p(1 << 20)
+    st = lib.ses_batch_init(2, fake, 1000, offs, n, d, 4096, fake, 1 << 30, None)  # 800 + 400 > 1000
+    assert st == 1 and b"extends past" in lib.pdscp_last_error()
