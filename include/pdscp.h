@@ -297,6 +297,49 @@ pdscp_status ses_batch_read(int32_t num, const void* ws_dev, float* mean_dev, fl
                             pdscp_stream stream);
 
 /*
+ * Row-sharded iteration: the rows (cones) split across G GPUs, one shard per
+ * GPU. An MWU iteration over a product of cones (Sec. 3, Eq. implement /
+ * min_implement) needs, besides the replicated O(d) state, only column sums
+ * and extrema over the points (Sec. 4.1: S, G', Wt, max dist; Sec. 4.2: S_P,
+ * S_Q, Z_P, Z_Q, min/max margins), so each GPU streams its shard into one
+ * row of column totals, the caller exchanges the G rows (an all-gather of
+ * width x 8 bytes per GPU, e.g. NCCL), and every GPU runs the same O(d)
+ * finish on the rows in rank order, which keeps the replicated states
+ * identical. Sums are compensated FP32 pairs; the rank order fixes the result.
+ *   mwu_shard_row_width: the row width in (float, float) pairs (host int).
+ *   mwu_shard_init: starts the alpha-FTP on this GPU's replica of the state;
+ *     first_dev = v_1 (SES: the easy cone's centre, d elements of dtype,
+ *     replicated on every GPU; SVM: unused, may be NULL); clears the
+ *     workspace counters. ws as for mwu_step with this shard's n.
+ *   mwu_shard_partial: one pass over this GPU's shard (n >= 1 rows, layout as
+ *     mwu_step); holds_first = 1 on the GPU whose shard starts with v_1 (that
+ *     row is the easy cone and is skipped), else 0; state_dev is read only;
+ *     writes 2 * width floats to row_dev (8-byte aligned, caller-owned).
+ *     Writes nothing when the FTP has stopped (as mwu_step).
+ *   mwu_shard_finish: reduces rows_dev (ranks rows of 2 * width floats, rank
+ *     order) and finishes the iteration exactly as mwu_step does: state
+ *     update, step record to out_dev (may be NULL). first_dev / dtype /
+ *     first_radius_dev (may be NULL: 0) give v_1 and gamma_1 for SES.
+ * alpha, eta_over_rho, D and eval_only have mwu_step's meaning and must be the
+ * same in the partial calls and the finish. Asynchronous on `stream`; errors
+ * as mwu_step.
+ */
+pdscp_status mwu_shard_row_width(int32_t problem, int32_t d, int32_t* width_host);
+pdscp_status mwu_shard_init(int32_t problem, const void* first_dev, int32_t dtype, int32_t d,
+                            int32_t rules, double delta, int32_t patience, void* state_dev,
+                            void* ws_dev, size_t ws_bytes, pdscp_stream stream);
+pdscp_status mwu_shard_partial(int32_t problem, const void* pts_dev, int32_t dtype,
+                               const float* radii_dev, const int8_t* labels_dev, int64_t n,
+                               int32_t d, int32_t holds_first, double alpha, double eta_over_rho,
+                               double D, int32_t eval_only, const void* state_dev, void* ws_dev,
+                               size_t ws_bytes, pdscp_stream stream, float* row_dev);
+pdscp_status mwu_shard_finish(int32_t problem, const float* rows_dev, int32_t ranks,
+                              const void* first_dev, int32_t dtype, const float* first_radius_dev,
+                              int32_t d, double alpha, double eta_over_rho, double D,
+                              int32_t eval_only, void* state_dev, pdscp_stream stream,
+                              pdscp_step_out* out_dev);
+
+/*
  * Reverse-mode sweep through T unrolled MWU iterations at fixed alpha (the
  * gradient of the final objective with respect to the points). Not built yet:
  * returns PDSCP_ERR_NOT_IMPLEMENTED.

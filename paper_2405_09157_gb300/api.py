@@ -127,6 +127,92 @@ def state_set(problem, pts, t, mean, state, ws, radii=None, labels=None, D=0.0, 
                                float(D), _vp(state), _vp(ws), ws.numel(), _stream(stream)), "mwu_state_set")
 
 
+# --- row-sharded iteration -------------------------------------------------
+
+def shard_rows(n, world, rank):
+    """[lo, hi) of `rank`'s contiguous block of rows: n split as evenly as
+    possible, in rank order (rank 0 holds row 0, the SES easy cone v_1)."""
+    if not (0 <= rank < world) or n < world:
+        raise ValueError(f"cannot split {n} rows over {world} ranks (rank {rank})")
+    base, rem = divmod(n, world)
+    lo = rank * base + min(rank, rem)
+    return lo, lo + base + (1 if rank < rem else 0)
+
+
+def shard_row_width(problem, d):
+    """Width, in (float, float) pairs, of a shard's row of column totals."""
+    w = ctypes.c_int32()
+    check(load().mwu_shard_row_width(problem, d, ctypes.byref(w)), "mwu_shard_row_width")
+    return w.value
+
+
+def exchange_rows(row, world, group=None):
+    """All-gather of one row per rank into a (world, len) tensor in rank order
+    (torch.distributed: NCCL for CUDA tensors, gloo for CPU ones)."""
+    if world == 1:
+        return row.view(1, -1)
+    import torch.distributed as dist
+    rows = torch.empty((world, row.numel()), dtype=row.dtype, device=row.device)
+    dist.all_gather(list(rows.unbind(0)), row.contiguous(), group=group)
+    return rows
+
+
+def shard_init(problem, first, d, state, ws, dtype=F32, rules=_ffi.RULES_NONE, delta=1e-4, patience=10,
+               stream=None):
+    check(load().mwu_shard_init(problem, _vp(first), dtype, d, rules, delta, patience, _vp(state), _vp(ws),
+                                ws.numel(), _stream(stream)), "mwu_shard_init")
+
+
+def shard_partial(problem, pts, holds_first, alpha, eta_over_rho, state, ws, row, D=0.0, radii=None,
+                  labels=None, eval_only=False, stream=None):
+    """One pass over this shard; writes its column totals to `row` (float32
+    CUDA tensor of 2 * shard_row_width floats)."""
+    n, d, dt = _points(pts)
+    check(load().mwu_shard_partial(problem, _vp(pts), dt, _vp(radii), _vp(labels), n, d, int(bool(holds_first)),
+                                   float(alpha), float(eta_over_rho), float(D), int(bool(eval_only)), _vp(state),
+                                   _vp(ws), ws.numel(), _stream(stream), _vp(row)), "mwu_shard_partial")
+
+
+def shard_finish(problem, rows, d, alpha, eta_over_rho, state, first=None, first_radius=None, dtype=F32, D=0.0,
+                 eval_only=False, out=None, stream=None):
+    """Reduces the shards' rows ((ranks, 2 * width) float32, rank order) and
+    finishes the iteration on this replica of the state."""
+    check(load().mwu_shard_finish(problem, _vp(rows), rows.shape[0], _vp(first), dtype, _vp(first_radius), d,
+                                  float(alpha), float(eta_over_rho), float(D), int(bool(eval_only)), _vp(state),
+                                  _stream(stream), _vp(out)), "mwu_shard_finish")
+
+
+class ShardedMWU:
+    """One alpha-FTP whose rows are split over the ranks of a process group
+    (one GPU per rank, `shard` = this rank's rows from shard_rows). Every rank
+    keeps a replica of the O(d) state; an iteration is a pass over the shard,
+    an all-gather of one row of column totals per rank, and the same finish on
+    every rank. first: v_1 (SES; the first row of rank 0's shard), on every
+    rank."""
+
+    def __init__(self, problem, shard, first, rank, world, labels=None, radii=None, first_radius=None,
+                 group=None, rules=_ffi.RULES_NONE, delta=1e-4, patience=10, stream=None):
+        n, d, dt = _points(shard)
+        self.problem, self.shard, self.first, self.rank, self.world = problem, shard, first, rank, world
+        self.labels, self.radii, self.first_radius, self.group = labels, radii, first_radius, group
+        self.d, self.dtype = d, dt
+        self.width = shard_row_width(problem, d)
+        self.row = torch.zeros(2 * self.width, dtype=torch.float32, device=shard.device)
+        self.ws = workspace(problem, n, d, shard.device)
+        self.state = new_state(problem, d, shard.device)
+        shard_init(problem, first, d, self.state, self.ws, dt, rules, delta, patience, stream)
+
+    def step(self, alpha, eta_over_rho, D=0.0, out=None, eval_only=False, stream=None):
+        shard_partial(self.problem, self.shard, self.rank == 0, alpha, eta_over_rho, self.state, self.ws, self.row,
+                      D, self.radii, self.labels, eval_only, stream)
+        rows = exchange_rows(self.row, self.world, self.group)
+        shard_finish(self.problem, rows, self.d, alpha, eta_over_rho, self.state, self.first, self.first_radius,
+                     self.dtype, D, eval_only, out, stream)
+
+    def read(self, stream=None):
+        return state_read(self.problem, self.d, self.state, stream, self.shard.device)
+
+
 class MWU:
     """One alpha-FTP over resident points: state, workspace and step records."""
 

@@ -18,6 +18,8 @@ namespace pdscp {
 
 cudaError_t launch_ses(const SesParams& p, int dtype, bool vec, cudaStream_t stream);
 cudaError_t launch_svm(const SvmParams& p, int dtype, bool vec, cudaStream_t stream);
+cudaError_t launch_ses_merge(const SesMergeParams& m, int dtype, cudaStream_t stream);
+cudaError_t launch_svm_merge(const SvmMergeParams& m, cudaStream_t stream);
 
 namespace {
 
@@ -111,7 +113,7 @@ cudaError_t launch_state_init(int problem, const void* pts, int dtype, int d, in
 
 pdscp_status do_step(int problem, const void* pts, int dtype, const float* radii, const int8_t* labels,
                      int64_t n, int d, double alpha, double eta_over_rho, double D, int eval_only,
-                     void* state, void* ws, cudaStream_t stream, pdscp_step_out* out) {
+                     void* state, void* ws, cudaStream_t stream, pdscp_step_out* out, float* tape = nullptr) {
   const Layout L = layout(problem, d);
   const bool vec = use_vec(pts, dtype, d);
   unsigned int* counter = reinterpret_cast<unsigned int*>(ws);
@@ -119,10 +121,11 @@ pdscp_status do_step(int problem, const void* pts, int dtype, const float* radii
   float2* grows = reinterpret_cast<float2*>(reinterpret_cast<char*>(ws) + L.grows);
   cudaError_t e;
   if (problem == PDSCP_SES) {
-    SesParams p{pts, radii, n, d, eval_only, alpha, eta_over_rho, state, partials, grows, counter, 0, out};
+    SesParams p{pts, radii, n, d, eval_only, alpha, eta_over_rho, state, partials, grows, counter, 0, out, 1, nullptr,
+                tape};
     e = launch_ses(p, dtype, vec, stream);
   } else {
-    SvmParams p{pts, labels, n, d, eval_only, alpha, eta_over_rho, D, state, partials, grows, counter, 0, out};
+    SvmParams p{pts, labels, n, d, eval_only, alpha, eta_over_rho, D, state, partials, grows, counter, 0, out, nullptr};
     e = launch_svm(p, dtype, vec, stream);
   }
   if (e != cudaSuccess) return cuda_fail(e, "mwu_step launch");
@@ -327,6 +330,101 @@ pdscp_status mwu_step_noalloc(int32_t problem, const void* pts, int32_t dtype, c
   if (e != cudaSuccess) return cuda_fail(e, "mwu_step_noalloc: clearing counters");
   return do_step(problem, pts, dtype, problem == PDSCP_SES ? radii : nullptr, labels, n, d, alpha, eta_over_rho, D,
                  eval_only, state, ws, (cudaStream_t)stream, out);
+}
+
+// --- row-sharded iteration (one shard of the rows per GPU) -----------------
+
+pdscp_status mwu_shard_row_width(int32_t problem, int32_t d, int32_t* width) {
+  if (problem != PDSCP_SES && problem != PDSCP_SVM) return fail(PDSCP_ERR_INVALID_ARG, "unknown problem %d", problem);
+  if (d < 1 || d > PDSCP_MAX_D) return fail(PDSCP_ERR_NOT_IMPLEMENTED, "d=%d outside [1, %d]", d, PDSCP_MAX_D);
+  if (!width) return fail(PDSCP_ERR_INVALID_ARG, "width pointer is null");
+  *width = problem == PDSCP_SES ? ses_partial_stride(d) : svm_partial_stride(d);
+  return PDSCP_OK;
+}
+
+pdscp_status mwu_shard_init(int32_t problem, const void* first, int32_t dtype, int32_t d, int32_t rules, double delta,
+                            int32_t patience, void* state, void* ws, size_t ws_bytes, pdscp_stream stream) {
+  if (problem != PDSCP_SES && problem != PDSCP_SVM) return fail(PDSCP_ERR_INVALID_ARG, "unknown problem %d", problem);
+  if (dtype != PDSCP_F32 && dtype != PDSCP_BF16) return fail(PDSCP_ERR_INVALID_ARG, "unknown dtype %d", dtype);
+  if (d < 1 || d > PDSCP_MAX_D) return fail(PDSCP_ERR_NOT_IMPLEMENTED, "d=%d outside [1, %d]", d, PDSCP_MAX_D);
+  if (problem == PDSCP_SES && (!first || !aligned(first, elem_size(dtype))))
+    return fail(PDSCP_ERR_INVALID_ARG, "SES shards need v_1 (first), aligned to its element");
+  if (!state || !ws) return fail(PDSCP_ERR_INVALID_ARG, "state or workspace pointer is null");
+  if (!aligned(state, 16) || !aligned(ws, 16)) return fail(PDSCP_ERR_INVALID_ARG, "state/workspace not 16-byte aligned");
+  if (rules != PDSCP_RULES_NONE && rules != PDSCP_RULES_PRACTICAL) return fail(PDSCP_ERR_INVALID_ARG, "unknown rules %d", rules);
+  if (!(delta >= 0.0) || patience < 1) return fail(PDSCP_ERR_INVALID_ARG, "delta must be >= 0 and patience >= 1");
+  if (ws_bytes < layout(problem, d).state) return fail(PDSCP_ERR_WORKSPACE, "workspace too small");
+  cudaError_t e = launch_state_init(problem, first, dtype, d, rules, delta, patience, state,
+                                    reinterpret_cast<unsigned int*>(ws), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "state init launch");
+  return PDSCP_OK;
+}
+
+pdscp_status mwu_shard_partial(int32_t problem, const void* pts, int32_t dtype, const float* radii,
+                               const int8_t* labels, int64_t n, int32_t d, int32_t holds_first, double alpha,
+                               double eta_over_rho, double D, int32_t eval_only, const void* state, void* ws,
+                               size_t ws_bytes, pdscp_stream stream, float* row_out) {
+  if (problem != PDSCP_SES && problem != PDSCP_SVM) return fail(PDSCP_ERR_INVALID_ARG, "unknown problem %d", problem);
+  if (dtype != PDSCP_F32 && dtype != PDSCP_BF16) return fail(PDSCP_ERR_INVALID_ARG, "unknown dtype %d", dtype);
+  if (d < 1 || d > PDSCP_MAX_D) return fail(PDSCP_ERR_NOT_IMPLEMENTED, "d=%d outside [1, %d]", d, PDSCP_MAX_D);
+  if (n < 1) return fail(PDSCP_ERR_INVALID_ARG, "a shard needs n >= 1 (got %lld)", (long long)n);
+  if (!pts || !aligned(pts, elem_size(dtype))) return fail(PDSCP_ERR_INVALID_ARG, "points pointer null or misaligned");
+  if (!state || !ws || !row_out) return fail(PDSCP_ERR_INVALID_ARG, "state, workspace or row pointer is null");
+  if (!aligned(state, 16) || !aligned(ws, 16)) return fail(PDSCP_ERR_INVALID_ARG, "state/workspace not 16-byte aligned");
+  if (!aligned(row_out, 8)) return fail(PDSCP_ERR_INVALID_ARG, "row pointer not 8-byte aligned");
+  if (holds_first != 0 && holds_first != 1) return fail(PDSCP_ERR_INVALID_ARG, "holds_first must be 0 or 1");
+  if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(PDSCP_ERR_INVALID_ARG, "alpha must be finite and > 0");
+  if (!(eta_over_rho >= 0.0) || !std::isfinite(eta_over_rho)) return fail(PDSCP_ERR_INVALID_ARG, "eta/rho must be finite and >= 0");
+  if (problem == PDSCP_SVM) {
+    if (!labels) return fail(PDSCP_ERR_INVALID_ARG, "SVM needs labels");
+    if (!(D > 0.0) || !std::isfinite(D)) return fail(PDSCP_ERR_INVALID_ARG, "SVM needs D > 0 (the largest point norm)");
+  }
+  if (ws_bytes < layout(problem, d).state) return fail(PDSCP_ERR_WORKSPACE, "workspace too small");
+  const Layout L = layout(problem, d);
+  const bool vec = use_vec(pts, dtype, d);
+  unsigned int* counter = reinterpret_cast<unsigned int*>(ws);
+  float* partials = reinterpret_cast<float*>(reinterpret_cast<char*>(ws) + L.partials);
+  float2* grows = reinterpret_cast<float2*>(reinterpret_cast<char*>(ws) + L.grows);
+  void* st_rw = const_cast<void*>(state);  // the pass only reads the state
+  float2* row = reinterpret_cast<float2*>(row_out);
+  cudaError_t e;
+  if (problem == PDSCP_SES) {
+    SesParams p{pts, radii, n, d, eval_only, alpha, eta_over_rho, st_rw, partials, grows, counter, 0, nullptr,
+                holds_first ? 1 : 0, row, nullptr};
+    e = launch_ses(p, dtype, vec, (cudaStream_t)stream);
+  } else {
+    SvmParams p{pts, labels, n, d, eval_only, alpha, eta_over_rho, D, st_rw, partials, grows, counter, 0, nullptr, row};
+    e = launch_svm(p, dtype, vec, (cudaStream_t)stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "mwu_shard_partial launch");
+  return PDSCP_OK;
+}
+
+pdscp_status mwu_shard_finish(int32_t problem, const float* rows, int32_t ranks, const void* first, int32_t dtype,
+                              const float* first_radius, int32_t d, double alpha, double eta_over_rho, double D,
+                              int32_t eval_only, void* state, pdscp_stream stream, pdscp_step_out* out) {
+  if (problem != PDSCP_SES && problem != PDSCP_SVM) return fail(PDSCP_ERR_INVALID_ARG, "unknown problem %d", problem);
+  if (dtype != PDSCP_F32 && dtype != PDSCP_BF16) return fail(PDSCP_ERR_INVALID_ARG, "unknown dtype %d", dtype);
+  if (d < 1 || d > PDSCP_MAX_D) return fail(PDSCP_ERR_NOT_IMPLEMENTED, "d=%d outside [1, %d]", d, PDSCP_MAX_D);
+  if (ranks < 1) return fail(PDSCP_ERR_INVALID_ARG, "ranks must be >= 1 (got %d)", ranks);
+  if (!rows || !aligned(rows, 8)) return fail(PDSCP_ERR_INVALID_ARG, "rows pointer null or not 8-byte aligned");
+  if (!state || !aligned(state, 16)) return fail(PDSCP_ERR_INVALID_ARG, "state pointer null or not 16-byte aligned");
+  if (out && !aligned(out, 8)) return fail(PDSCP_ERR_INVALID_ARG, "out pointer not 8-byte aligned");
+  if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(PDSCP_ERR_INVALID_ARG, "alpha must be finite and > 0");
+  if (!(eta_over_rho >= 0.0) || !std::isfinite(eta_over_rho)) return fail(PDSCP_ERR_INVALID_ARG, "eta/rho must be finite and >= 0");
+  cudaError_t e;
+  if (problem == PDSCP_SES) {
+    if (!first || !aligned(first, elem_size(dtype))) return fail(PDSCP_ERR_INVALID_ARG, "SES needs v_1 (first), aligned to its element");
+    SesMergeParams m{reinterpret_cast<const float2*>(rows), ranks, first, first_radius, d, eval_only, alpha,
+                     eta_over_rho, state, out};
+    e = launch_ses_merge(m, dtype, (cudaStream_t)stream);
+  } else {
+    if (!(D > 0.0) || !std::isfinite(D)) return fail(PDSCP_ERR_INVALID_ARG, "SVM needs D > 0 (the largest point norm)");
+    SvmMergeParams m{reinterpret_cast<const float2*>(rows), ranks, d, eval_only, alpha, eta_over_rho, D, state, out};
+    e = launch_svm_merge(m, (cudaStream_t)stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "mwu_shard_finish launch");
+  return PDSCP_OK;
 }
 
 pdscp_status mwu_backward(int32_t, const void*, int32_t, const int8_t*, int64_t, int32_t, double, double, double,

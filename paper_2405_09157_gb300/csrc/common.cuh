@@ -71,6 +71,9 @@ __host__ __device__ inline float* state_best(void* s, int d) {
 
 // Per-CTA partial row width (floats).
 __host__ __device__ inline int ses_partial_stride(int d) { return 4 + dpad4(d); }
+// One entry of the forward tape a reverse sweep reads (floats): S, |g|, k/sqrt2,
+// the exponent shift, then the mean the pass read (dp) and g (dp).
+__host__ __device__ inline int ses_tape_stride(int d) { return 4 + 2 * dpad4(d); }
 __host__ __device__ inline int svm_partial_stride(int d) { return 4 + 2 * dpad4(d); }
 
 // ---------------------------------------------------------------------------

@@ -60,4 +60,11 @@ cudaError_t launch_ses(const SesParams& p, int dtype, bool vec, cudaStream_t str
   return dispatch_shape<8>(p.d, vec, SesLauncher<__nv_bfloat16>{p, stream});
 }
 
+cudaError_t launch_ses_merge(const SesMergeParams& m, int dtype, cudaStream_t stream) {
+  const size_t smem = (size_t)(ses_partial_stride(m.d) + 2 * dpad4(m.d)) * sizeof(double);
+  if (dtype == PDSCP_F32) ses_merge_kernel<float><<<1, kMergeBlock, smem, stream>>>(m);
+  else ses_merge_kernel<__nv_bfloat16><<<1, kMergeBlock, smem, stream>>>(m);
+  return cudaGetLastError();
+}
+
 }  // namespace pdscp

@@ -60,4 +60,10 @@ cudaError_t launch_svm(const SvmParams& p, int dtype, bool vec, cudaStream_t str
   return dispatch_shape<8>(p.d, vec, SvmLauncher<__nv_bfloat16>{p, stream});
 }
 
+cudaError_t launch_svm_merge(const SvmMergeParams& m, cudaStream_t stream) {
+  const size_t smem = (size_t)(svm_partial_stride(m.d) + dpad4(m.d)) * sizeof(double);
+  svm_merge_kernel<0><<<1, kSvmMergeBlock, smem, stream>>>(m);
+  return cudaGetLastError();
+}
+
 }  // namespace pdscp

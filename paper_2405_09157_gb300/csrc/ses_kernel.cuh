@@ -45,6 +45,9 @@ struct SesParams {
   unsigned int* counter; // completion counters: [0] top, [1 + g] group g
   int single;            // completion stages all partial rows in shared memory (single_level)
   pdscp_step_out* out;   // may be null
+  int64_t first;         // first row of the pass: 1 when row 0 is v_1 (the easy cone), else 0
+  float2* row_out;       // non-null: a shard's pass; write the column totals here, no finish
+  float* tape;           // non-null: the finish records entry t (ses_tape_stride floats) for a reverse sweep
 };
 
 template <typename T>
@@ -118,7 +121,7 @@ __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
         }
       const float dist2 = group_sum<LPP>(part);
       float c = 0.f;
-      if (i >= 1 && i < p.n) {
+      if (i >= p.first && i < p.n) {
         const float dist = sqrtf(dist2);
         const float gam = p.radii ? __ldg(p.radii + i) : 0.f;
         const float a = alpha - gam;
@@ -197,7 +200,8 @@ __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
 // step record (out, may be null).
 static __device__ __noinline__ void ses_finish_warp(const float2* raw, const double* s_mean, const double* s_v1,
                                              const StateHdr& h, void* state, int d, double alpha_d, double gam1,
-                                             double eta_over_rho, int eval_only, pdscp_step_out* out) {
+                                             double eta_over_rho, int eval_only, pdscp_step_out* out,
+                                             float* tape = nullptr) {
   const int lane = threadIdx.x & 31;
   StateHdr* hdr = reinterpret_cast<StateHdr*>(state);
   double* mean = state_mean(state);
@@ -279,6 +283,21 @@ static __device__ __noinline__ void ses_finish_warp(const float2* raw, const dou
       mean32[j] = (float)nm;
     }
   }
+  if (tape && advance) {
+    // what the pass used (same expressions as the pass kernels) and what it produced
+    float* ent = tape + (size_t)t * ses_tape_stride(d);
+    const int dp = dpad4(d);
+    for (int j = lane; j < d; j += 32) {
+      ent[4 + j] = (float)s_mean[j];
+      ent[4 + dp + j] = tot(4 + j) * inv;
+    }
+    if (lane == 0) {
+      ent[0] = S;
+      ent[1] = ng;
+      ent[2] = (float)((double)t * eta_over_rho / kSqrt2);
+      ent[3] = (float)(h.hint + h.move);
+    }
+  }
   if (lane == 0) {
     if (!eval_only && (double)LB > h.lb_best) hdr->lb_best = (double)LB;
     if (streak != h.streak) hdr->streak = streak;
@@ -343,6 +362,10 @@ __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw) {
   const double v0 = tid < d ? (double)elem_to_float<T>(pts + tid) : 0.0;
   const double gam1 = p.radii ? (double)__ldg(p.radii) : 0.0;
   final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single);
+  if (p.row_out) {  // a shard of a row-sharded iteration: hand the totals to the merge
+    for (int pc = tid; pc < st; pc += blockDim.x) p.row_out[pc] = raw[pc];
+    return;
+  }
   if (tid < HW) s_hdr[tid] = hw;
   if (tid < d) {
     s_mean[tid] = m0;
@@ -359,7 +382,7 @@ __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw) {
   const int lane = tid;
   (void)lane;
   ses_finish_warp(raw, s_mean, s_v1, *reinterpret_cast<const StateHdr*>(s_hdr), p.state, d, p.alpha, gam1,
-                  p.eta_over_rho, p.eval_only, p.out);
+                  p.eta_over_rho, p.eval_only, p.out, p.tape);
 }
 
 }  // namespace pdscp
@@ -448,7 +471,7 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
     for (int k = 0; k < GS::OWN; ++k) {
       const int64_t i = base + GS::owned(gl, k) * PPW + grp;
       c[k] = 0.f;
-      if (i >= 1 && i < hi) {
+      if (i >= p.first && i < hi) {
         const float dist = sqrtf(part[k]);
         const float gam = p.radii ? __ldg(p.radii + i) : 0.f;
         const float a = alpha - gam;
@@ -508,6 +531,59 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
     prow[3] = 0.f;
   }
   ses_finish<T>(p, smem_raw);
+}
+
+}  // namespace pdscp
+
+namespace pdscp {
+
+// Row-sharded iteration, second half: the column totals of the shards
+// (`ranks` rows of ses_partial_stride(d) compensated pairs, in rank order)
+// are reduced in that fixed order, and the O(d) finish runs as in the
+// unsharded kernel. v1 / radius1: the easy cone's centre and radius, which
+// only the first shard holds. One CTA of kMergeBlock threads.
+struct SesMergeParams {
+  const float2* rows;
+  int ranks;
+  const void* v1;
+  const float* radius1;  // may be null
+  int d;
+  int eval_only;
+  double alpha;
+  double eta_over_rho;
+  void* state;
+  pdscp_step_out* out;
+};
+
+constexpr int kMergeBlock = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kMergeBlock) ses_merge_kernel(SesMergeParams m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float2 s_scr[kMergeBlock];
+  __shared__ __align__(16) double s_hdr[sizeof(StateHdr) / 8];
+  const StateHdr* hdr = reinterpret_cast<const StateHdr*>(m.state);
+  if (hdr->stopped && !m.eval_only) return;  // as the pass kernels: a stopped FTP is left as is
+  const int d = m.d, dp = dpad4(d), st = ses_partial_stride(d);
+  const int tid = threadIdx.x;
+  // dynamic shared memory: column totals (s, c) | mean | v_1
+  float2* raw = reinterpret_cast<float2*>(smem_raw);
+  double* s_mean = reinterpret_cast<double*>(smem_raw) + st;
+  double* s_v1 = s_mean + dp;
+  constexpr int HW = (int)(sizeof(StateHdr) / 8);
+  if (tid < HW) s_hdr[tid] = reinterpret_cast<const double*>(hdr)[tid];
+  const double* mean = state_mean(m.state);
+  const T* v1 = reinterpret_cast<const T*>(m.v1);
+  for (int j = tid; j < d; j += blockDim.x) {
+    s_mean[j] = mean[j];
+    s_v1[j] = (double)elem_to_float<T>(v1 + j);
+  }
+  auto opof = [](int pc) { return pc == 2 ? 1 : 0; };
+  reduce_rows(m.rows, 0, m.ranks, st, raw, s_scr, opof);  // ends with a barrier
+  if (tid >= 32) return;
+  const double gam1 = m.radius1 ? (double)__ldg(m.radius1) : 0.0;
+  ses_finish_warp(raw, s_mean, s_v1, *reinterpret_cast<const StateHdr*>(s_hdr), m.state, d, m.alpha, gam1,
+                  m.eta_over_rho, m.eval_only, m.out);
 }
 
 }  // namespace pdscp

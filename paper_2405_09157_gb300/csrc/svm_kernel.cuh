@@ -41,6 +41,7 @@ struct SvmParams {
   unsigned int* counter; // completion counters: [0] top, [1 + g] group g
   int single;            // completion stages all partial rows in shared memory (single_level)
   pdscp_step_out* out;
+  float2* row_out;       // non-null: a shard's pass; write the column totals here, no finish
 };
 
 template <typename T>
@@ -191,50 +192,28 @@ __global__ void __launch_bounds__(kBlock) svm_iter_kernel(SvmParams p) {
   svm_finish<T>(p, smem_raw);
 }
 
-// O(d) finish of one SVM iteration. Every CTA calls it after writing its
-// partial row [S_P, S_Q, minP, maxQ, Z_P (dp), Z_Q (dp)]; the two-level
-// completion elects one CTA, which reduces the group rows in FP64 and does
-// the rest.
-template <typename T>
-__device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
-  __shared__ float2 s_scr[kMaxBlock];
-  __shared__ __align__(16) double s_hdr[sizeof(StateHdr) / 8];
-  __shared__ bool s_flag;
-  const int d = p.d;
+// The O(d) finish of one SVM iteration from the column totals: run by one
+// warp (lane = threadIdx.x & 31). raw: [S_P, S_Q, minP, maxQ, Z_P (dp),
+// Z_Q (dp)] as compensated pairs; s_mean: the mean read by the pass (FP64,
+// shared memory); h: a copy of the state header. Writes the state and the
+// step record (out, may be null). FP32 math, FP64 running means (as in
+// ses_finish_warp).
+static __device__ __noinline__ void svm_finish_warp(const float2* raw, const double* s_mean, const StateHdr& h,
+                                             void* state, int d, double alpha_d, double D_d, double eta_over_rho,
+                                             int eval_only, pdscp_step_out* out) {
+  const int lane = threadIdx.x & 31;
   const int dp = dpad4(d);
-  const int st = svm_partial_stride(d);
-  auto opof = [](int pc) { return pc == 2 ? 2 : (pc == 3 ? 1 : 0); };  // minP min, maxQ max
-  if (!arrive_pass(p.partials, st, p.grows, p.counter, s_scr, &s_flag, opof, p.single)) return;
-
-  StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
-  double* mean = state_mean(p.state);
-  float* mean32 = state_mean32(p.state, d);
-  float* best = state_best(p.state, d);
-  const int tid = threadIdx.x;
-  // dynamic shared memory: column totals as (s, c) pairs | mean | staged partial rows
-  float2* raw = reinterpret_cast<float2*>(smem_raw);
-  double* s_mean = reinterpret_cast<double*>(smem_raw) + st;
-  float* stage = reinterpret_cast<float*>(s_mean + dp);
-  constexpr int HW = (int)(sizeof(StateHdr) / 8);
-  const double hw = tid < HW ? reinterpret_cast<const double*>(hdr)[tid] : 0.0;
-  const double m0 = tid < d ? mean[tid] : 0.0;
-  final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single);
-  if (tid < HW) s_hdr[tid] = hw;
-  if (tid < d) s_mean[tid] = m0;
-  for (int j = tid + blockDim.x; j < d; j += blockDim.x) s_mean[j] = mean[j];
-  __syncthreads();
-  // The O(d) math runs in warp 0 alone (see ses_finish).
-  if (tid >= 32) return;
-  const int lane = tid;
-  const StateHdr& h = *reinterpret_cast<const StateHdr*>(s_hdr);
-  // FP32 finish, FP64 running means (see ses_finish).
+  StateHdr* hdr = reinterpret_cast<StateHdr*>(state);
+  double* mean = state_mean(state);
+  float* mean32 = state_mean32(state, d);
+  float* best = state_best(state, d);
   auto tot = [&](int pc) { return raw[pc].x + raw[pc].y; };
   const float SP = tot(0), SQ = tot(1), minP = raw[2].x, maxQ = raw[3].x;
   const float S = SP + SQ;
   const float rS = 1.0f / S;
   const float rSP = SP > 0.f ? 1.0f / SP : 0.f, rSQ = SQ > 0.f ? 1.0f / SQ : 0.f;
   const float trmu = SP * rS, trga = SQ * rS;
-  const float alpha = (float)p.alpha, D = (float)p.D;
+  const float alpha = (float)alpha_d, D = (float)D_d;
   const double s1b = h.s1bar, s2b = h.s2bar;
   // |z|^2, Claim 8 |P mu/Tr mu - Q gamma/Tr gamma|^2, |wbar|^2, z . wbar
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -268,7 +247,7 @@ __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
   const bool better = fd > h.best_f;
   int streak = h.streak;
   bool set_fprev = false;
-  if (!p.eval_only) {
+  if (!eval_only) {
     failed = V < 0.f;
     if (status != PDSCP_OK) {
       stop = true;
@@ -276,7 +255,7 @@ __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
       stop = true;
       outcome = PDSCP_OUT_SEPARATED;
     } else if (h.rules == PDSCP_RULES_PRACTICAL && t > 0) {
-      if (fd > p.alpha) {
+      if (fd > alpha_d) {
         stop = true;
         outcome = PDSCP_OUT_BEAT_ALPHA;
       } else {
@@ -292,7 +271,7 @@ __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
       }
     }
   }
-  const bool advance = !p.eval_only && !stop;
+  const bool advance = !eval_only && !stop;
   const float rtp1 = 1.0f / (float)(t + 1);
   for (int j = lane; j < d; j += 32) {
     const double m = s_mean[j];
@@ -305,7 +284,7 @@ __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
     }
   }
   if (lane == 0) {
-    if (!p.eval_only && (double)UB < h.ub_best) hdr->ub_best = (double)UB;
+    if (!eval_only && (double)UB < h.ub_best) hdr->ub_best = (double)UB;
     if (streak != h.streak) hdr->streak = streak;
     if (set_fprev) hdr->f_prev = fd;
     if (better) hdr->best_f = fd;
@@ -330,7 +309,7 @@ __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
     }
     if (status != PDSCP_OK) hdr->status = status;
     hdr->last_value = (double)V;
-    if (p.out) {
+    if (out) {
       pdscp_step_out o;
       o.oracle_value = (double)V;
       o.objective = fd;
@@ -341,11 +320,49 @@ __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
       o.stopped = (stop || h.stopped) ? 1 : 0;
       o.status = status;
       o.outcome = outcome;
-      o.k = (double)t * p.eta_over_rho;
-      *p.out = o;
+      o.k = (double)t * eta_over_rho;
+      *out = o;
     }
   }
+}
 
+// O(d) finish of one SVM iteration. Every CTA calls it after writing its
+// partial row [S_P, S_Q, minP, maxQ, Z_P (dp), Z_Q (dp)]; the completion
+// elects one CTA, which reduces the rows and hands the totals to warp 0.
+template <typename T>
+__device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
+  __shared__ float2 s_scr[kMaxBlock];
+  __shared__ __align__(16) double s_hdr[sizeof(StateHdr) / 8];
+  __shared__ bool s_flag;
+  const int d = p.d;
+  const int dp = dpad4(d);
+  const int st = svm_partial_stride(d);
+  auto opof = [](int pc) { return pc == 2 ? 2 : (pc == 3 ? 1 : 0); };  // minP min, maxQ max
+  if (!arrive_pass(p.partials, st, p.grows, p.counter, s_scr, &s_flag, opof, p.single)) return;
+
+  StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
+  double* mean = state_mean(p.state);
+  const int tid = threadIdx.x;
+  // dynamic shared memory: column totals as (s, c) pairs | mean | staged partial rows
+  float2* raw = reinterpret_cast<float2*>(smem_raw);
+  double* s_mean = reinterpret_cast<double*>(smem_raw) + st;
+  float* stage = reinterpret_cast<float*>(s_mean + dp);
+  constexpr int HW = (int)(sizeof(StateHdr) / 8);
+  const double hw = tid < HW ? reinterpret_cast<const double*>(hdr)[tid] : 0.0;
+  const double m0 = tid < d ? mean[tid] : 0.0;
+  final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single);
+  if (p.row_out) {  // a shard of a row-sharded iteration: hand the totals to the merge
+    for (int pc = tid; pc < st; pc += blockDim.x) p.row_out[pc] = raw[pc];
+    return;
+  }
+  if (tid < HW) s_hdr[tid] = hw;
+  if (tid < d) s_mean[tid] = m0;
+  for (int j = tid + blockDim.x; j < d; j += blockDim.x) s_mean[j] = mean[j];
+  __syncthreads();
+  // The O(d) math runs in warp 0 alone (see ses_finish).
+  if (tid >= 32) return;
+  svm_finish_warp(raw, s_mean, *reinterpret_cast<const StateHdr*>(s_hdr), p.state, d, p.alpha, p.D,
+                  p.eta_over_rho, p.eval_only, p.out);
 }
 
 }  // namespace pdscp
@@ -507,6 +524,49 @@ __global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
     prow[3] = mx;
   }
   svm_finish<T>(p, smem_raw);
+}
+
+}  // namespace pdscp
+
+namespace pdscp {
+
+// Row-sharded iteration, second half, for SVM (see ses_merge_kernel): the
+// shards' column totals, `ranks` rows of svm_partial_stride(d) pairs in rank
+// order, reduced in that order, then the O(d) finish. One CTA.
+struct SvmMergeParams {
+  const float2* rows;
+  int ranks;
+  int d;
+  int eval_only;
+  double alpha;
+  double eta_over_rho;
+  double D;
+  void* state;
+  pdscp_step_out* out;
+};
+
+constexpr int kSvmMergeBlock = 256;
+
+template <int kUnused = 0>  // a template so that only the launching unit instantiates it
+__global__ void __launch_bounds__(kSvmMergeBlock) svm_merge_kernel(SvmMergeParams m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float2 s_scr[kSvmMergeBlock];
+  __shared__ __align__(16) double s_hdr[sizeof(StateHdr) / 8];
+  const StateHdr* hdr = reinterpret_cast<const StateHdr*>(m.state);
+  if (hdr->stopped && !m.eval_only) return;
+  const int d = m.d, st = svm_partial_stride(d);
+  const int tid = threadIdx.x;
+  float2* raw = reinterpret_cast<float2*>(smem_raw);
+  double* s_mean = reinterpret_cast<double*>(smem_raw) + st;
+  constexpr int HW = (int)(sizeof(StateHdr) / 8);
+  if (tid < HW) s_hdr[tid] = reinterpret_cast<const double*>(hdr)[tid];
+  const double* mean = state_mean(m.state);
+  for (int j = tid; j < d; j += blockDim.x) s_mean[j] = mean[j];
+  auto opof = [](int pc) { return pc == 2 ? 2 : (pc == 3 ? 1 : 0); };
+  reduce_rows(m.rows, 0, m.ranks, st, raw, s_scr, opof);  // ends with a barrier
+  if (tid >= 32) return;
+  svm_finish_warp(raw, s_mean, *reinterpret_cast<const StateHdr*>(s_hdr), m.state, d, m.alpha, m.D,
+                  m.eta_over_rho, m.eval_only, m.out);
 }
 
 }  // namespace pdscp

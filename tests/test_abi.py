@@ -90,3 +90,28 @@ def test_batch_validation_without_gpu(lib):
     fake = ctypes.c_void_p(1 << 20)
     st = lib.ses_batch_init(2, fake, 1000, offs, n, d, 4096, fake, 1 << 30, None)  # 800 + 400 > 1000
     assert st == 1 and b"extends past" in lib.pdscp_last_error()
+
+
+def test_shard_validation_without_gpu(lib):
+    w = ctypes.c_int32()
+    assert lib.mwu_shard_row_width(_ffi.SES, 32, ctypes.byref(w)) == 0 and w.value == 4 + 32
+    assert lib.mwu_shard_row_width(_ffi.SVM, 5, ctypes.byref(w)) == 0 and w.value == 4 + 2 * 8
+    assert lib.mwu_shard_row_width(_ffi.SES, 0, ctypes.byref(w)) == 7
+    fake = ctypes.c_void_p(1 << 20)
+    st = lib.mwu_shard_partial(_ffi.SES, fake, _ffi.F32, None, None, 0, 4, 1, 1.0, 0.1, 0.0, 0, fake, fake,
+                               1 << 30, None, fake)
+    assert st == 1 and b"n >= 1" in lib.pdscp_last_error()
+    st = lib.mwu_shard_partial(_ffi.SES, fake, _ffi.F32, None, None, 5, 4, 2, 1.0, 0.1, 0.0, 0, fake, fake,
+                               1 << 30, None, fake)
+    assert st == 1 and b"holds_first" in lib.pdscp_last_error()
+    st = lib.mwu_shard_partial(_ffi.SES, fake, _ffi.F32, None, None, 5, 4, 1, 1.0, 0.1, 0.0, 0, fake, fake,
+                               1 << 30, None, None)
+    assert st == 1
+    st = lib.mwu_shard_finish(_ffi.SES, fake, 0, fake, _ffi.F32, None, 4, 1.0, 0.1, 0.0, 0, fake, None, None)
+    assert st == 1 and b"ranks" in lib.pdscp_last_error()
+    st = lib.mwu_shard_finish(_ffi.SES, fake, 2, None, _ffi.F32, None, 4, 1.0, 0.1, 0.0, 0, fake, None, None)
+    assert st == 1 and b"v_1" in lib.pdscp_last_error()
+    st = lib.mwu_shard_finish(_ffi.SVM, fake, 2, None, _ffi.F32, None, 4, 1.0, 0.1, 0.0, 0, fake, None, None)
+    assert st == 1 and b"D > 0" in lib.pdscp_last_error()
+    st = lib.mwu_shard_init(_ffi.SES, None, _ffi.F32, 4, 0, 1e-4, 10, fake, fake, 1 << 30, None)
+    assert st == 1 and b"v_1" in lib.pdscp_last_error()
