@@ -296,6 +296,7 @@ def run_ours(args):
         result["cpu_baseline"] = cpu_baseline(V32, alpha, eta, rho)
         result["variants"] = variants(dev, flush)
         result["variants"]["batched_ses_4096"] = batched_variant(dev)
+        result["variants"]["ses_backward_n1e5_d64_T2000"] = backward_variant(dev)
         result["time_to_eps"] = time_to_eps(pts)
     if world > 1:
         dist.barrier()
@@ -462,6 +463,49 @@ def batched_variant(dev, K=10, W=3):
     return {"instances": int(len(n)), "points": int(n.sum()), "bytes_per_iter": b, "ms_per_iter": ms,
             "instance_iters_per_s": len(n) * 1e3 / ms, "GBps": b / ms / 1e6, "frac_hbm": b / ms / 1e6 / peak,
             "l2": "input larger than L2, no flush"}
+
+
+def backward_variant(dev, n=100_000, d=64, T=2000):
+    """Reverse sweep through T unrolled SES iterations (gradient of the final
+    radius with respect to the points), n x d N(0, I) FP32 points at alpha = D.
+    Times the whole mwu_backward call (T forward iterations recording the tape,
+    then T reverse passes) and the T forward iterations alone, with CUDA
+    events; the reverse passes take the difference. Each reverse pass reads
+    the points and reads and writes the n x d gradient (12 n d bytes); at this
+    size both (51 MB) stay in L2 across passes."""
+    import torch
+    from paper_2405_09157_gb300 import _ffi, api, datagen
+    V32 = datagen.ses_gaussian(n, d, seed=0)
+    pts = torch.from_numpy(V32).to(dev)
+    D = float(api.bounds(_ffi.SES, pts).item())
+    rho = 3.0 * D / np.sqrt(2.0)
+    eor = 0.5 / rho
+    ws = torch.empty(api.backward_workspace_size(n, d, T), dtype=torch.uint8, device=dev)
+    out = api.new_steps(1, dev)
+    api.mwu_backward(pts, D, eor, T, ws=ws, out=out)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    grad, _ = api.mwu_backward(pts, D, eor, T, ws=ws, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    total = e0.elapsed_time(e1)
+    rec = api.decode_steps(out)[0]
+    if not (rec["t"] == T and rec["status"] == 0):
+        raise RuntimeError("the reverse sweep did not run every iteration")
+    m = api.MWU(_ffi.SES, pts)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(T):
+        m.step(D, eor)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd = e0.elapsed_time(e1)
+    rev = (total - fwd) / T
+    b = 12 * n * d
+    return {"workload": f"SES n={n} d={d} T={T} fp32, alpha = D", "ms_total": total, "ms_forward": fwd,
+            "ms_per_reverse_step": rev, "GBps_reverse": b / rev / 1e6,
+            "note": "points and gradient (51 MB) are L2-resident across passes: GB/s is not an HBM figure"}
 
 
 def time_to_eps(pts):

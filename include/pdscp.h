@@ -340,15 +340,37 @@ pdscp_status mwu_shard_finish(int32_t problem, const float* rows_dev, int32_t ra
                               pdscp_step_out* out_dev);
 
 /*
- * Reverse-mode sweep through T unrolled MWU iterations at fixed alpha (the
- * gradient of the final objective with respect to the points). Not built yet:
- * returns PDSCP_ERR_NOT_IMPLEMENTED.
+ * Reverse-mode sweep through T unrolled iterations of the SES alpha-FTP at
+ * fixed alpha and eta/rho (Sec. 3, Eq. implement, ORACLE Eq. ses_oracle): the
+ * gradient of L = seed * f(ubar^T), f(c) = max_i ||c - v_i|| + gamma_i the
+ * radius of Sec. 5, with respect to the points. The sweep first runs the T
+ * forward iterations from t = 0 (as mwu_state_init + T mwu_step calls with
+ * rules PDSCP_RULES_NONE), recording O(d) values per iteration (the mean, g,
+ * the normaliser, |g|, the exponent scale and shift) in the workspace, then
+ * one streaming pass per iteration in reverse order, each adding that
+ * iteration's dL/dv_i to grad_dev and summing the adjoint of the mean.
+ * If the ORACLE separates at step t_f < T, the sweep differentiates the t_f
+ * iterations taken. f is a maximum: the row attaining it (smallest index on
+ * ties) receives the subgradient; radii are constants.
+ *   problem: PDSCP_SES (SVM returns PDSCP_ERR_NOT_IMPLEMENTED); dtype:
+ *     PDSCP_F32 (BF16 returns PDSCP_ERR_NOT_IMPLEMENTED); labels_dev, D: unused.
+ *   seed_dev: dL/df, one device double (NULL: 1).
+ *   ws_dev: mwu_backward_workspace_size bytes (256-byte aligned); on return
+ *     it holds the forward's final state and tape (caller-owned).
+ *   grad_dev: n x d float32, row-major, overwritten (16-byte alignment with
+ *     d % 4 == 0 takes the vector path).
+ *   out_dev (may be NULL): one pdscp_step_out: objective = upper_bound =
+ *     f(ubar^T), t = iterations taken, oracle_value/lower_bound/outcome of
+ *     the forward, k = the index of the row attaining f.
+ * Asynchronous on `stream` (2T + 3 launches); errors as mwu_step.
  */
+pdscp_status mwu_backward_workspace_size(int32_t problem, int64_t n, int32_t d, int64_t T,
+                                         size_t* bytes_host);
 pdscp_status mwu_backward(int32_t problem, const void* pts_dev, int32_t dtype,
-                          const int8_t* labels_dev, int64_t n, int32_t d,
-                          double alpha, double eta_over_rho, double D, int64_t T,
-                          int32_t ckpt_every, void* ws_dev, size_t ws_bytes,
-                          pdscp_stream stream, float* grad_pts_dev);
+                          const float* radii_dev, const int8_t* labels_dev, int64_t n,
+                          int32_t d, double alpha, double eta_over_rho, double D, int64_t T,
+                          const double* seed_dev, void* ws_dev, size_t ws_bytes,
+                          pdscp_stream stream, float* grad_dev, pdscp_step_out* out_dev);
 
 #ifdef __cplusplus
 }

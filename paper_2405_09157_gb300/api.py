@@ -127,6 +127,59 @@ def state_set(problem, pts, t, mean, state, ws, radii=None, labels=None, D=0.0, 
                                float(D), _vp(state), _vp(ws), ws.numel(), _stream(stream)), "mwu_state_set")
 
 
+# --- reverse sweep (SES) ----------------------------------------------------
+
+def backward_workspace_size(n, d, T):
+    out = ctypes.c_size_t()
+    check(load().mwu_backward_workspace_size(SES, n, d, T, ctypes.byref(out)), "mwu_backward_workspace_size")
+    return out.value
+
+
+def mwu_backward(pts, alpha, eta_over_rho, T, radii=None, seed=None, ws=None, out=None, stream=None):
+    """Gradient of seed * f(ubar^T) (SES radius after T alpha-FTP iterations
+    from t = 0 at fixed alpha, eta/rho) with respect to the float32 points.
+    seed: one-element float64 CUDA tensor or None (1). Returns (grad, ws)."""
+    n, d, dt = _points(pts)
+    if ws is None:
+        ws = torch.empty(backward_workspace_size(n, d, T), dtype=torch.uint8, device=pts.device)
+    grad = torch.empty((n, d), dtype=torch.float32, device=pts.device)
+    if seed is not None:
+        seed = seed.to(device=pts.device, dtype=torch.float64).contiguous()
+    check(load().mwu_backward(SES, _vp(pts), dt, _vp(radii), None, n, d, float(alpha), float(eta_over_rho), 0.0,
+                              int(T), _vp(seed), _vp(ws), ws.numel(), _stream(stream), _vp(grad), _vp(out)),
+          "mwu_backward")
+    return grad, ws
+
+
+class SesUnrolledRadius(torch.autograd.Function):
+    """f(ubar^T) of the SES alpha-FTP as a differentiable function of the
+    points: forward = T mwu_step iterations and one evaluation pass; backward =
+    mwu_backward seeded with the incoming gradient."""
+
+    @staticmethod
+    def forward(ctx, pts, alpha, eta_over_rho, T, radii=None):
+        m = MWU(SES, pts.detach(), radii=radii)
+        for _ in range(T):
+            m.step(alpha, eta_over_rho)
+        rec = new_steps(1, pts.device)
+        m.step(alpha, eta_over_rho, out=rec, eval_only=True)
+        ctx.save_for_backward(pts)
+        ctx.args = (alpha, eta_over_rho, T, radii)
+        return rec.view(torch.float64)[0, 1].clone()  # the record's objective: f at the final mean
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (pts,) = ctx.saved_tensors
+        alpha, eta_over_rho, T, radii = ctx.args
+        grad, _ = mwu_backward(pts.detach(), alpha, eta_over_rho, T, radii, seed=grad_out.reshape(1))
+        return grad, None, None, None, None
+
+
+def ses_unrolled_radius(pts, alpha, eta_over_rho, T, radii=None):
+    """Differentiable SES radius after T alpha-FTP iterations (float64 0-dim tensor)."""
+    return SesUnrolledRadius.apply(pts, alpha, eta_over_rho, T, radii)
+
+
 # --- row-sharded iteration -------------------------------------------------
 
 def shard_rows(n, world, rank):

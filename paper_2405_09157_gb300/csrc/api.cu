@@ -10,6 +10,7 @@
 #include <string>
 
 #include "bounds_kernel.cuh"
+#include "bwd_kernel.cuh"
 #include "dispatch.cuh"
 #include "ses_kernel.cuh"
 #include "svm_kernel.cuh"
@@ -20,6 +21,8 @@ cudaError_t launch_ses(const SesParams& p, int dtype, bool vec, cudaStream_t str
 cudaError_t launch_svm(const SvmParams& p, int dtype, bool vec, cudaStream_t stream);
 cudaError_t launch_ses_merge(const SesMergeParams& m, int dtype, cudaStream_t stream);
 cudaError_t launch_svm_merge(const SvmMergeParams& m, cudaStream_t stream);
+cudaError_t launch_ses_bwd_seed(const BwdParams& p, bool vec, cudaStream_t stream);
+cudaError_t launch_ses_bwd_step(const BwdParams& p, bool vec, cudaStream_t stream);
 
 namespace {
 
@@ -60,6 +63,24 @@ Layout layout(int problem, int d) {
   L.dval = L.ring + round256((size_t)kRing * sizeof(pdscp_step_out));
   L.total = L.dval + 256;
   return L;
+}
+
+// Reverse-sweep workspace: mwu_step's counters, per-CTA rows and group rows,
+// then [state][tape: T entries][adjoint scratch][argmax candidates].
+struct BwdLayout {
+  size_t state, tape, bw, cval, cidx, total;
+};
+BwdLayout bwd_layout(int d, int64_t T) {
+  const Layout L = layout(PDSCP_SES, d);
+  const size_t rows = (size_t)device_sm_count() * kMaxBlocksPerSM;
+  BwdLayout B;
+  B.state = L.state;
+  B.tape = B.state + round256(state_bytes(d));
+  B.bw = B.tape + round256((size_t)T * ses_tape_stride(d) * sizeof(float));
+  B.cval = B.bw + round256(bwd_scratch_bytes(d));
+  B.cidx = B.cval + round256(rows * sizeof(float));
+  B.total = B.cidx + round256(rows * sizeof(long long));
+  return B;
 }
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
@@ -427,9 +448,80 @@ pdscp_status mwu_shard_finish(int32_t problem, const float* rows, int32_t ranks,
   return PDSCP_OK;
 }
 
-pdscp_status mwu_backward(int32_t, const void*, int32_t, const int8_t*, int64_t, int32_t, double, double, double,
-                          int64_t, int32_t, void*, size_t, pdscp_stream, float*) {
-  return fail(PDSCP_ERR_NOT_IMPLEMENTED, "mwu_backward is not built yet");
+// --- reverse sweep (SES) -------------------------------------------------------
+
+pdscp_status mwu_backward_workspace_size(int32_t problem, int64_t n, int32_t d, int64_t T, size_t* bytes) {
+  if (problem != PDSCP_SES) return fail(PDSCP_ERR_NOT_IMPLEMENTED, "the reverse sweep is built for SES only");
+  if (d < 1 || d > PDSCP_MAX_D) return fail(PDSCP_ERR_NOT_IMPLEMENTED, "d=%d outside [1, %d]", d, PDSCP_MAX_D);
+  if (n < 2 || T < 1) return fail(PDSCP_ERR_INVALID_ARG, "need n >= 2 and T >= 1");
+  if (!bytes) return fail(PDSCP_ERR_INVALID_ARG, "bytes pointer is null");
+  *bytes = bwd_layout(d, T).total;
+  return PDSCP_OK;
+}
+
+pdscp_status mwu_backward(int32_t problem, const void* pts, int32_t dtype, const float* radii, const int8_t* labels,
+                          int64_t n, int32_t d, double alpha, double eta_over_rho, double D, int64_t T,
+                          const double* seed, void* ws, size_t ws_bytes, pdscp_stream stream, float* grad,
+                          pdscp_step_out* out) {
+  (void)labels;
+  (void)D;
+  pdscp_status st = check_common(problem, pts, dtype, n, d);
+  if (st != PDSCP_OK) return st;
+  if (problem != PDSCP_SES) return fail(PDSCP_ERR_NOT_IMPLEMENTED, "the reverse sweep is built for SES only");
+  if (dtype != PDSCP_F32) return fail(PDSCP_ERR_NOT_IMPLEMENTED, "the reverse sweep takes float32 points");
+  if (T < 1) return fail(PDSCP_ERR_INVALID_ARG, "T must be >= 1");
+  if (!ws || !grad) return fail(PDSCP_ERR_INVALID_ARG, "workspace or gradient pointer is null");
+  if (!aligned(ws, 256)) return fail(PDSCP_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  if (!aligned(grad, 4)) return fail(PDSCP_ERR_INVALID_ARG, "gradient pointer not 4-byte aligned");
+  if (out && !aligned(out, 8)) return fail(PDSCP_ERR_INVALID_ARG, "out pointer not 8-byte aligned");
+  if (seed && !aligned(seed, 8)) return fail(PDSCP_ERR_INVALID_ARG, "seed pointer not 8-byte aligned");
+  if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(PDSCP_ERR_INVALID_ARG, "alpha must be finite and > 0");
+  if (!(eta_over_rho >= 0.0) || !std::isfinite(eta_over_rho)) return fail(PDSCP_ERR_INVALID_ARG, "eta/rho must be finite and >= 0");
+  const BwdLayout B = bwd_layout(d, T);
+  if (ws_bytes < B.total) return fail(PDSCP_ERR_WORKSPACE, "workspace too small for the reverse sweep");
+  cudaStream_t s = (cudaStream_t)stream;
+  char* w = reinterpret_cast<char*>(ws);
+  void* state = w + B.state;
+  float* tape = reinterpret_cast<float*>(w + B.tape);
+  unsigned int* counter = reinterpret_cast<unsigned int*>(ws);
+  cudaError_t e = launch_state_init(PDSCP_SES, pts, dtype, d, PDSCP_RULES_NONE, 1e-4, 10, state, counter, s);
+  if (e != cudaSuccess) return cuda_fail(e, "state init launch");
+  e = cudaMemsetAsync(grad, 0, (size_t)n * d * sizeof(float), s);
+  if (e != cudaSuccess) return cuda_fail(e, "gradient clear");
+  // forward, recording the tape (a stopped alpha-FTP leaves the later launches idle)
+  for (int64_t t = 0; t < T; ++t) {
+    st = do_step(PDSCP_SES, pts, dtype, radii, nullptr, n, d, alpha, eta_over_rho, 0.0, 0, state, ws, s, nullptr, tape);
+    if (st != PDSCP_OK) return st;
+  }
+  const Layout L = layout(PDSCP_SES, d);
+  BwdParams bp{};
+  bp.pts = reinterpret_cast<const float*>(pts);
+  bp.radii = radii;
+  bp.n = n;
+  bp.d = d;
+  bp.alpha = alpha;
+  bp.s = T - 1;
+  bp.state = state;
+  bp.tape = tape;
+  bp.bw = reinterpret_cast<unsigned char*>(w + B.bw);
+  bp.grad = grad;
+  bp.partials = reinterpret_cast<float*>(w + L.partials);
+  bp.grows = reinterpret_cast<float2*>(w + L.grows);
+  bp.counter = counter;
+  bp.cand_val = reinterpret_cast<float*>(w + B.cval);
+  bp.cand_idx = reinterpret_cast<long long*>(w + B.cidx);
+  bp.ncand = device_sm_count() * kMaxBlocksPerSM;
+  bp.seed = seed;
+  bp.out = out;
+  const bool vec = use_vec(pts, dtype, d) && aligned(grad, 16);
+  e = launch_ses_bwd_seed(bp, vec, s);
+  if (e != cudaSuccess) return cuda_fail(e, "reverse-sweep seed launch");
+  for (int64_t k = T - 1; k >= 1; --k) {
+    bp.s = k;
+    e = launch_ses_bwd_step(bp, vec, s);
+    if (e != cudaSuccess) return cuda_fail(e, "reverse-step launch");
+  }
+  return PDSCP_OK;
 }
 
 }  // extern "C"

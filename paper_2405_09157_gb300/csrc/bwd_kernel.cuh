@@ -1,0 +1,410 @@
+// Reverse sweep through the unrolled SES alpha-FTP (Sec. 3, Eq. implement with
+// the ORACLE of Eq. ses_oracle) at fixed alpha and eta/rho: the gradient of
+//   L = f(ubar^T) = max_i ||ubar^T - v_i|| + gamma_i        (f of Sec. 5)
+// with respect to the points v_1..v_n.
+//
+// Forward step t (ubar = ubar^t, kr = eta t/(rho sqrt2), cones i >= 2):
+//   delta_i = v_i - ubar, dist_i = |delta_i|, E1, E2 as in the iteration kernel
+//   (the SOC exponential of Sec. 2.1, shifted by the tape's common factor),
+//   s_i = E1 + E2, c_i = (E1 - E2)/dist_i, S = sum s_i, G' = sum c_i delta_i,
+//   g = G'/(sqrt2 S), u = v_1 + r g/|g| (r = alpha - gamma_1; u = v_1 if g = 0),
+//   ubar^{t+1} = (t ubar^t + u)/(t + 1).
+// Reverse step t, given B = dL/dubar^{t+1}:
+//   B' = B/(t+1) reaches v_1 through u; with ghat = g/|g|,
+//   gbar = (r/|g|)(B' - ghat (ghat . B')), Gbar = gbar/(sqrt2 S), Sbar = -(gbar . g)/S;
+//   ds_i/ddist = kr (E1 - E2), dc_i/ddist = (kr s_i - c_i)/dist_i, so
+//   dL/ddelta_i = c_i Gbar + beta_i delta_i,
+//   beta_i = [(Gbar . delta_i)(kr s_i - c_i)/dist_i + Sbar kr (E1 - E2)]/dist_i,
+//   (beta_i delta_i -> 0 as dist_i -> 0; beta_i = 0 at dist_i = 0);
+//   dL/dv_i += dL/ddelta_i,  dL/dubar^t = t/(t+1) B - sum_i dL/ddelta_i.
+// At t = 0 every exponent is 0 (g = 0, u = v_1): step 0 only hands B to v_1,
+// and ubar^0 = v_1 receives nothing more (its coefficient t/(t+1) is 0).
+// The common shift of E1 and E2 cancels in g and in its derivative, so the
+// reverse pass reuses the forward's shift from the tape.
+//
+// Kernels: ses_bwd_argmax_kernel (i* = argmax of f at ubar^T, smallest index on
+// ties), ses_bwd_seed_kernel (one CTA: B = dL/dubar^T, row i*, then the
+// bookkeeping of step T-1), ses_bwd_step_kernel (one per step s = T-1 .. 1: a
+// streaming pass that updates dL/dv_i for every cone and sums dL/ddelta_i,
+// then the last CTA updates B and prepares step s-1). Steps the forward did
+// not take (it stopped early) are skipped on the device.
+#pragma once
+
+#include "common.cuh"
+
+namespace pdscp {
+
+// Adjoint scratch (in the workspace): B (double, dp) | v_1 adjoint (double,
+// dp) | Gbar (float, dp) | Sbar (float) ...
+__host__ __device__ inline size_t bwd_scratch_bytes(int d) {
+  return (size_t)dpad4(d) * (8 + 8 + 4) + 16;
+}
+
+struct BwdParams {
+  const float* pts;
+  const float* radii;  // may be null
+  int64_t n;
+  int d;
+  double alpha;
+  int64_t s;             // reverse step of this launch
+  const void* state;     // the forward's final state: t = steps taken, mean = ubar^T
+  const float* tape;     // forward tape, ses_tape_stride(d) floats per step
+  unsigned char* bw;     // adjoint scratch
+  float* grad;           // n x d, dL/dv
+  float* partials;       // one row of ses_partial_stride(d) floats per CTA
+  float2* grows;
+  unsigned int* counter;
+  int single;
+  // argmax / seed
+  float* cand_val;       // one candidate per CTA of the argmax pass
+  long long* cand_idx;
+  int ncand;
+  const double* seed;    // dL/df (may be null: 1)
+  pdscp_step_out* out;   // seed: f at ubar^T and the steps taken (may be null)
+};
+
+__device__ __forceinline__ double* bwd_B(unsigned char* bw) { return reinterpret_cast<double*>(bw); }
+__device__ __forceinline__ double* bwd_V1(unsigned char* bw, int d) {
+  return reinterpret_cast<double*>(bw) + dpad4(d);
+}
+__device__ __forceinline__ float* bwd_Gbar(unsigned char* bw, int d) {
+  return reinterpret_cast<float*>(reinterpret_cast<double*>(bw) + 2 * dpad4(d));
+}
+__device__ __forceinline__ float* bwd_Sbar(unsigned char* bw, int d) { return bwd_Gbar(bw, d) + dpad4(d); }
+
+// Bookkeeping of reverse step s, run by one warp, given B = dL/dubar^{s+1} in
+// the scratch: v_1's share B/(s+1), then Gbar and Sbar of step s from the
+// tape; at s = 0 the accumulated v_1 adjoint goes to row 0 of grad.
+static __device__ void bwd_prologue(int64_t s, const float* tape, int d, float rad, unsigned char* bw, float* grad) {
+  const int lane = threadIdx.x & 31;
+  const int dp = dpad4(d);
+  double* B = bwd_B(bw);
+  double* V1 = bwd_V1(bw, d);
+  float* Gb = bwd_Gbar(bw, d);
+  const double inv = 1.0 / (double)(s + 1);
+  for (int j = lane; j < d; j += 32) V1[j] += B[j] * inv;
+  if (s == 0) {
+    for (int j = lane; j < d; j += 32) grad[j] += (float)V1[j];
+    return;
+  }
+  const float* ent = tape + (size_t)s * ses_tape_stride(d);
+  const float S = ent[0], ng = ent[1];
+  const float* g = ent + 4 + dp;
+  if (!(ng > 0.f)) {  // u = v_1 at this step: nothing flows to the cones
+    for (int j = lane; j < d; j += 32) Gb[j] = 0.f;
+    if (lane == 0) *bwd_Sbar(bw, d) = 0.f;
+    return;
+  }
+  const float rng = 1.0f / ng;
+  float dot1 = 0.f;
+  for (int j = lane; j < d; j += 32) dot1 = fmaf(g[j] * rng, (float)(B[j] * inv), dot1);
+  dot1 = warp_sum(dot1);
+  const float scale = rad * rng;
+  const float rS = 1.0f / S;
+  const float gsc = rS * (float)(1.0 / kSqrt2);
+  float dot2 = 0.f;
+  for (int j = lane; j < d; j += 32) {
+    const float gh = g[j] * rng;
+    const float gb = scale * ((float)(B[j] * inv) - gh * dot1);
+    dot2 = fmaf(gb, g[j], dot2);
+    Gb[j] = gb * gsc;
+  }
+  dot2 = warp_sum(dot2);
+  if (lane == 0) *bwd_Sbar(bw, d) = -dot2 * rS;
+}
+
+// One reverse step s >= 1: a streaming pass over the cones, then (last CTA)
+// B <- s/(s+1) B - sum_i dL/ddelta_i and the bookkeeping of step s - 1.
+template <int VW, int LPP, int NCH, int U>
+__global__ void __launch_bounds__(kBlock) ses_bwd_step_kernel(BwdParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float2 s_scr[kMaxBlock];
+  __shared__ bool s_flag;
+  const StateHdr* hdr = reinterpret_cast<const StateHdr*>(p.state);
+  if (p.s >= hdr->t) return;  // the forward stopped before step s
+
+  const int d = p.d;
+  const int dp = dpad4(d);
+  const int nch = (d + VW - 1) / VW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / LPP, gl = lane % LPP;
+  constexpr int PPW = 32 / LPP;
+  const float* ent = p.tape + (size_t)p.s * ses_tape_stride(d);
+  const float kr = ent[2], H = ent[3];
+  const float* ubar = ent + 4;
+  const float* Gbar = bwd_Gbar(p.bw, d);
+  const float Sbar = *bwd_Sbar(p.bw, d);
+
+  float ub[NCH][VW], gb[NCH][VW], acc[NCH][VW];
+#pragma unroll
+  for (int j = 0; j < NCH; ++j) {
+    const int c = gl + j * LPP;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      ub[j][e] = (c < nch) ? ubar[c * VW + e] : 0.f;
+      gb[j][e] = (c < nch) ? Gbar[c * VW + e] : 0.f;
+      acc[j][e] = 0.f;
+    }
+  }
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
+  for (int64_t base = gw * (PPW * U); base < p.n; base += nwarps * (PPW * U)) {
+    float x[U][NCH][VW];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * PPW + grp;
+#pragma unroll
+      for (int j = 0; j < NCH; ++j) {
+        const int c = gl + j * LPP;
+        if (i < p.n && c < nch) {
+          Chunk<float, VW>::load(p.pts + i * d, c, x[u][j]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VW; ++e) x[u][j][e] = 0.f;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * PPW + grp;
+      float p2 = 0.f, pd = 0.f;
+#pragma unroll
+      for (int j = 0; j < NCH; ++j)
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          x[u][j][e] -= ub[j][e];  // delta_i = v_i - ubar
+          p2 = fmaf(x[u][j][e], x[u][j][e], p2);
+          pd = fmaf(gb[j][e], x[u][j][e], pd);
+        }
+      const float dist2 = group_sum<LPP>(p2);
+      const float gdot = group_sum<LPP>(pd);
+      float c = 0.f, beta = 0.f;
+      const bool cone = i >= 1 && i < p.n;
+      if (cone) {
+        const float dist = sqrtf(dist2);
+        const float gam = p.radii ? __ldg(p.radii + i) : 0.f;
+        const float E1 = expf(kr * ((dist + gam) - H));
+        const float em = -expm1f(-2.f * kr * dist);
+        const float dif = E1 * em;          // E1 - E2
+        const float sum = E1 * (2.f - em);  // E1 + E2
+        if (dist > 0.f) {
+          const float rd = 1.0f / dist;
+          c = dif * rd;
+          beta = (gdot * (kr * sum - c) * rd + Sbar * kr * dif) * rd;
+        } else {
+          c = 2.f * kr * E1;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NCH; ++j) {
+        const int ch = gl + j * LPP;
+        float dd[VW];
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          dd[e] = cone ? fmaf(c, gb[j][e], beta * x[u][j][e]) : 0.f;
+          acc[j][e] += dd[e];
+        }
+        if (cone && ch < nch) {
+          float* gp = p.grad + i * d + ch * VW;
+          if constexpr (VW == 4) {
+            float4 v = *reinterpret_cast<float4*>(gp);
+            v.x += dd[0]; v.y += dd[1]; v.z += dd[2]; v.w += dd[3];
+            *reinterpret_cast<float4*>(gp) = v;
+          } else {
+#pragma unroll
+            for (int e = 0; e < VW; ++e) gp[e] += dd[e];
+          }
+        }
+      }
+    }
+  }
+  // CTA sum of dL/ddelta: across the lane groups of a warp, then across warps
+#pragma unroll
+  for (int o = LPP; o < 32; o <<= 1)
+#pragma unroll
+    for (int j = 0; j < NCH; ++j)
+#pragma unroll
+      for (int e = 0; e < VW; ++e) acc[j][e] += __shfl_xor_sync(0xffffffffu, acc[j][e], o);
+  float* sA = reinterpret_cast<float*>(smem_raw);  // [kWarps][dp]
+  if (grp == 0) {
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) {
+      const int c = gl + j * LPP;
+      if (c < nch)
+#pragma unroll
+        for (int e = 0; e < VW; ++e) sA[warp * dp + c * VW + e] = acc[j][e];
+    }
+  }
+  __syncthreads();
+  const int st = ses_partial_stride(d);
+  float* prow = p.partials + (size_t)blockIdx.x * st;
+  for (int j = threadIdx.x; j < dp; j += kBlock) {
+    float s = 0.f;
+    if (j < d)
+      for (int w = 0; w < kWarps; ++w) s += sA[w * dp + j];
+    prow[4 + j] = s;
+  }
+  if (threadIdx.x < 4) prow[threadIdx.x] = 0.f;
+
+  auto opof = [](int) { return 0; };
+  if (!arrive_pass(p.partials, st, p.grows, p.counter, s_scr, &s_flag, opof, p.single)) return;
+  float2* raw = reinterpret_cast<float2*>(smem_raw);
+  float* stage = reinterpret_cast<float*>(raw + st);
+  final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single);
+  if (threadIdx.x >= 32) return;
+  double* B = bwd_B(p.bw);
+  const double keep = (double)p.s / (double)(p.s + 1);
+  for (int j = lane; j < d; j += 32) B[j] = keep * B[j] - ((double)raw[4 + j].x + (double)raw[4 + j].y);
+  __syncwarp();
+  const float rad = (float)(p.alpha - (p.radii ? (double)__ldg(p.radii) : 0.0));
+  bwd_prologue(p.s - 1, p.tape, d, rad, p.bw, p.grad);
+}
+
+// argmax_i dist(ubar^T, v_i) + gamma_i over every row (v_1 included): one
+// candidate (value, smallest index) per CTA.
+template <int VW, int LPP, int NCH, int U>
+__global__ void __launch_bounds__(kBlock) ses_bwd_argmax_kernel(BwdParams p) {
+  __shared__ float s_val[kWarps];
+  __shared__ long long s_idx[kWarps];
+  const int d = p.d;
+  const int nch = (d + VW - 1) / VW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / LPP, gl = lane % LPP;
+  constexpr int PPW = 32 / LPP;
+  const float* mean32 = state_mean32(const_cast<void*>(p.state), d);
+  float ub[NCH][VW];
+#pragma unroll
+  for (int j = 0; j < NCH; ++j) {
+    const int c = gl + j * LPP;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) ub[j][e] = (c < nch) ? mean32[c * VW + e] : 0.f;
+  }
+  float best = -INFINITY;
+  long long bidx = 0x7fffffffffffffffLL;
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
+  for (int64_t base = gw * (PPW * U); base < p.n; base += nwarps * (PPW * U)) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * PPW + grp;
+      float part = 0.f;
+#pragma unroll
+      for (int j = 0; j < NCH; ++j) {
+        const int c = gl + j * LPP;
+        float x[VW];
+        if (i < p.n && c < nch) {
+          Chunk<float, VW>::load(p.pts + i * d, c, x);
+#pragma unroll
+          for (int e = 0; e < VW; ++e) {
+            const float dl = x[e] - ub[j][e];
+            part = fmaf(dl, dl, part);
+          }
+        }
+      }
+      const float dist2 = group_sum<LPP>(part);
+      if (i < p.n) {
+        const float v = sqrtf(dist2) + (p.radii ? __ldg(p.radii + i) : 0.f);
+        if (v > best || (v == best && i < bidx)) {
+          best = v;
+          bidx = i;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const long long oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+    if (ov > best || (ov == best && oi < bidx)) {
+      best = ov;
+      bidx = oi;
+    }
+  }
+  if (lane == 0) {
+    s_val[warp] = best;
+    s_idx[warp] = bidx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float bv = s_val[0];
+    long long bi = s_idx[0];
+    for (int w = 1; w < kWarps; ++w)
+      if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] < bi)) {
+        bv = s_val[w];
+        bi = s_idx[w];
+      }
+    p.cand_val[blockIdx.x] = bv;
+    p.cand_idx[blockIdx.x] = bi;
+  }
+}
+
+// One CTA: picks i* from the candidates, seeds B = dL/dubar^T = seed (ubar^T -
+// v_i*)/|ubar^T - v_i*| and row i* of grad, then the bookkeeping of step T-1.
+template <int kUnused = 0>  // a template so that only the launching unit instantiates it
+__global__ void __launch_bounds__(32) ses_bwd_seed_kernel(BwdParams p) {
+  const int lane = threadIdx.x;
+  const int d = p.d;
+  float bv = -INFINITY;
+  long long bi = 0x7fffffffffffffffLL;
+  for (int k = lane; k < p.ncand; k += 32) {
+    const float v = p.cand_val[k];
+    const long long i = p.cand_idx[k];
+    if (v > bv || (v == bv && i < bi)) {
+      bv = v;
+      bi = i;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > bv || (ov == bv && oi < bi)) {
+      bv = ov;
+      bi = oi;
+    }
+  }
+  const StateHdr* hdr = reinterpret_cast<const StateHdr*>(p.state);
+  const int64_t T = hdr->t;
+  const float* mean32 = state_mean32(const_cast<void*>(p.state), d);
+  const float* row = p.pts + bi * d;
+  // the direction in FP32 from the values the argmax pass compared
+  float n2 = 0.f;
+  for (int j = lane; j < d; j += 32) {
+    const float dl = mean32[j] - row[j];
+    n2 = fmaf(dl, dl, n2);
+  }
+  n2 = warp_sum(n2);
+  const float rn = n2 > 0.f ? 1.0f / sqrtf(n2) : 0.f;  // f is not differentiable at a zero distance: 0
+  const double sd = p.seed ? *p.seed : 1.0;
+  double* B = bwd_B(p.bw);
+  double* V1 = bwd_V1(p.bw, d);
+  for (int j = lane; j < d; j += 32) {
+    const double dir = (double)((mean32[j] - row[j]) * rn);
+    B[j] = sd * dir;
+    V1[j] = 0.0;
+    p.grad[bi * d + j] -= (float)(sd * dir);
+  }
+  __syncwarp();
+  if (lane == 0 && p.out) {
+    pdscp_step_out o;
+    o.oracle_value = hdr->last_value;
+    o.objective = (double)bv;
+    o.lower_bound = hdr->lb_best;
+    o.upper_bound = (double)bv;
+    o.t = T;
+    o.failed = hdr->outcome == PDSCP_OUT_SEPARATED ? 1 : 0;
+    o.stopped = hdr->stopped;
+    o.status = hdr->status;
+    o.outcome = hdr->outcome;
+    o.k = (double)bi;  // the row that attains f
+    *p.out = o;
+  }
+  if (T == 0) {  // ubar^0 = v_1
+    for (int j = lane; j < d; j += 32) p.grad[j] += (float)B[j];
+    return;
+  }
+  const float rad = (float)(p.alpha - (p.radii ? (double)__ldg(p.radii) : 0.0));
+  bwd_prologue(T - 1, p.tape, d, rad, p.bw, p.grad);
+}
+
+}  // namespace pdscp

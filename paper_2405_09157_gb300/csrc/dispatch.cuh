@@ -63,6 +63,18 @@ struct Unroll {
   static constexpr int value = (VW * NCH <= 8) ? 4 : ((VW * NCH <= 16) ? 2 : 1);
 };
 
+// Opts a kernel in to `dyn` bytes of dynamic shared memory when that, plus
+// the kernel's static shared memory, exceeds the default per-block limit of
+// 48 KB (the launch fails with an invalid argument otherwise).
+template <typename KernelFn>
+cudaError_t allow_smem(KernelFn kern, size_t dyn) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, kern);
+  if (e != cudaSuccess) return e;
+  if (dyn + a.sharedSizeBytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+}
+
 // Grid for a point pass: enough CTAs to fill every SM at the occupancy the
 // instance allows (at most kMaxBlocksPerSM per SM), no more than the work needs.
 template <typename KernelFn>

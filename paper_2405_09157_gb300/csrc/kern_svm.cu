@@ -26,15 +26,15 @@ struct SvmLauncher {
       const size_t fin = fin_base + (size_t)grid * st * sizeof(float);
       if (fin > smem) smem = fin;
       // the staging area may lower the CTAs per SM: keep the grid to one wave
-      if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      {
+        cudaError_t e = allow_smem(kern, smem);
         if (e != cudaSuccess) return e;
       }
       const int g1 = pass_grid(kern, smem, p.n, (32 / lpp) * points_per_lane_step * (block / 32), block);
       if (g1 < grid) grid = g1;
     }
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+      cudaError_t e = allow_smem(kern, smem);
       if (e != cudaSuccess) return e;
     }
     kern<<<grid, block, smem, stream>>>(q);

@@ -71,8 +71,17 @@ def test_argument_validation_without_gpu(lib):
     opts = _ffi.Options(1e-3, 1e-4, 10, 0, 1000, 0, 10, 0.0)
     st = lib.svm_solve(fake, _ffi.F32, fake, 10, 4, ctypes.byref(opts), fake, 1 << 30, None, fake, ctypes.byref(rep))
     assert st == 1 and b"poll_every" in lib.pdscp_last_error()
-    st = lib.mwu_backward(_ffi.SES, fake, _ffi.F32, None, 10, 4, 1.0, 0.1, 1.0, 10, 5, fake, 1 << 30, None, fake)
-    assert st == 7
+    bwd = lambda problem, dtype, T, ws_bytes: lib.mwu_backward(problem, fake, dtype, None, None, 10, 4, 1.0, 0.1,
+                                                               0.0, T, None, fake, ws_bytes, None, fake, None)
+    assert bwd(_ffi.SVM, _ffi.F32, 5, 1 << 30) == 7 and b"SES only" in lib.pdscp_last_error()
+    assert bwd(_ffi.SES, _ffi.BF16, 5, 1 << 30) == 7 and b"float32" in lib.pdscp_last_error()
+    assert bwd(_ffi.SES, _ffi.F32, 0, 1 << 30) == 1
+    assert bwd(_ffi.SES, _ffi.F32, 5, 1024) == 8
+    size = ctypes.c_size_t()
+    assert lib.mwu_backward_workspace_size(_ffi.SES, 10, 4, 5, ctypes.byref(size)) == 0
+    small = size.value
+    assert lib.mwu_backward_workspace_size(_ffi.SES, 10, 4, 500, ctypes.byref(size)) == 0
+    assert size.value >= small + 495 * (4 + 2 * 4) * 4  # one tape entry per iteration
 
 
 def test_batch_validation_without_gpu(lib):

@@ -1,0 +1,113 @@
+"""Reverse sweep (mwu_backward) against the FP64 autograd oracle, through the C ABI.
+
+Tolerance. The forward runs in FP32 per point (relative error ~k D 2^-24 per
+weight, k D <= 10 here) and the sweep differentiates the same FP32 values, so
+the GPU gradient differs from the FP64 one by the sensitivity of the gradient
+to those perturbations. Gradients are compared in the max norm relative to the
+largest entry, at GRAD_RTOL = 2e-4, over trajectories short enough (T <= 15)
+that the alpha-FTP dynamics do not amplify rounding (see test_gpu_parity.py).
+At the full size the oracle is out of reach; there the sweep is checked
+against identities that hold at any size: f is invariant under a common
+translation of all points (so the rows of the gradient sum to zero) and
+equivariant under rotations (so sum_i v_i grad_i^T is symmetric).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import ses as oses
+from oracle import ses_grad
+from paper_2405_09157_gb300 import _ffi, api, datagen
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-5
+GRAD_RTOL = 2e-4
+
+
+def _case(n, d, seed, radii, rel_alpha=0.9):
+    V32 = datagen.ses_gaussian(n, d, seed)
+    g32 = (0.1 * np.random.default_rng(seed).random(n)).astype(np.float32) if radii else None
+    V = V32.astype(np.float64)
+    g = None if g32 is None else g32.astype(np.float64)
+    D = oses.ses_D(V, g)
+    return V32, g32, V, g, D, rel_alpha * D, oses.ses_width(D)
+
+
+def _gpu(V32, g32, alpha, eor, T, seed=None):
+    pts = torch.from_numpy(V32).cuda()
+    radii = None if g32 is None else torch.from_numpy(g32).cuda()
+    out = api.new_steps(1)
+    grad, _ = api.mwu_backward(pts, alpha, eor, T, radii=radii, seed=seed, out=out)
+    torch.cuda.synchronize()
+    return grad.cpu().numpy().astype(np.float64), api.decode_steps(out)[0]
+
+
+@pytest.mark.parametrize("n,d,T,radii", [(300, 3, 10, False), (2000, 8, 15, True), (5000, 32, 12, False),
+                                         (20000, 64, 8, False), (1001, 5, 6, True), (4099, 16, 15, False),
+                                         (2, 3, 5, False)])
+def test_backward_matches_oracle(n, d, T, radii):
+    V32, g32, V, g, D, alpha, rho = _case(n, d, 21, radii)
+    eta = 0.5
+    L, want, steps = ses_grad.ses_unrolled_radius_grad(V, g, alpha, eta / rho, T)
+    got, rec = _gpu(V32, g32, alpha, eta / rho, T)
+    assert rec["status"] == 0 and rec["t"] == steps == T
+    assert abs(rec["objective"] - L) <= RTOL * D
+    # entries of the gradient of a radius with respect to the points are O(1):
+    # the bound is relative to the largest entry, with 1 as its floor (for the
+    # two-point case, whose radius alpha (T-1)/T does not depend on the points)
+    scale = max(np.max(np.abs(want)), 1.0)
+    err = np.max(np.abs(got - want))
+    assert err <= GRAD_RTOL * scale, (err / scale, np.unravel_index(np.argmax(np.abs(got - want)), want.shape))
+
+
+def test_backward_after_separation_differentiates_the_steps_taken():
+    # alpha below OPT: the forward separates at some t_f < T (the run of test_ses_separation_then_noop)
+    V32, _, V, _, D, _, rho = _case(800, 4, 6, False)
+    alpha, eta, T = 0.45 * D, 1.0, 40
+    L, want, steps = ses_grad.ses_unrolled_radius_grad(V, None, alpha, eta / rho, T)
+    assert steps < T
+    got, rec = _gpu(V32, None, alpha, eta / rho, T)
+    assert rec["t"] == steps and rec["failed"] == 1
+    assert abs(rec["objective"] - L) <= RTOL * D
+    assert np.max(np.abs(got - want)) <= GRAD_RTOL * np.max(np.abs(want))
+
+
+def test_one_iteration_closed_form_and_seed():
+    V32, _, V, _, D, alpha, rho = _case(500, 8, 9, False)
+    seed = torch.tensor([2.5], dtype=torch.float64, device="cuda")
+    got, rec = _gpu(V32, None, alpha, 0.5 / rho, 1, seed=seed)
+    dist = np.linalg.norm(V - V[0], axis=1)
+    k = int(np.argmax(dist))
+    want = np.zeros_like(V)
+    want[0] = 2.5 * (V[0] - V[k]) / dist[k]
+    want[k] = -want[0]
+    assert int(rec["k"]) == k and rec["t"] == 1
+    assert np.max(np.abs(got - want)) <= 1e-6
+
+
+def test_autograd_function_matches_the_sweep():
+    V32, _, V, _, D, alpha, rho = _case(3000, 16, 4, False)
+    eor, T = 0.5 / rho, 10
+    pts = torch.from_numpy(V32).cuda().requires_grad_(True)
+    f = api.ses_unrolled_radius(pts, alpha, eor, T)
+    (3.0 * f).backward()
+    direct, _ = api.mwu_backward(pts.detach(), alpha, eor, T)
+    torch.cuda.synchronize()
+    assert torch.allclose(pts.grad, 3.0 * direct, rtol=1e-6, atol=1e-7)
+    L, _, _ = ses_grad.ses_unrolled_radius_grad(V, None, alpha, eor, T)
+    assert abs(float(f) - L) <= RTOL * D
+
+
+@pytest.mark.parametrize("n,d,T", [(100_000, 64, 2000), (200_000, 32, 300)])
+def test_full_size_invariances(n, d, T):
+    V32, _, V, _, D, alpha, rho = _case(n, d, 0, False, rel_alpha=1.0)
+    eta = 0.5
+    got, rec = _gpu(V32, None, alpha, eta / rho, T)
+    assert rec["status"] == 0 and rec["t"] == T and np.all(np.isfinite(got))
+    tot = np.abs(got).sum(axis=0)
+    # translation invariance: sum_i dL/dv_i = 0
+    assert np.all(np.abs(got.sum(axis=0)) <= 1e-4 * np.maximum(tot, 1e-30) + 1e-6)
+    # rotation equivariance: sum_i v_i grad_i^T is symmetric
+    Mv = V.T @ got
+    assert np.max(np.abs(Mv - Mv.T)) <= 1e-4 * np.abs(V).max() * tot.sum() + 1e-6

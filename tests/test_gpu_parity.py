@@ -160,6 +160,19 @@ def test_ses_single_steps_full_size():
     forced_ses(1_000_000, 32, seed=0, kDs=[10.0, 64.0], rel_alpha=2 / 3)
 
 
+@pytest.mark.parametrize("n,d,dtype", [(100_000, 64, torch.float32), (100_000, 64, torch.bfloat16),
+                                       (300_000, 16, torch.float32), (60_000, 128, torch.float32)])
+def test_ses_single_steps_large_grids(n, d, dtype):
+    # grids of one CTA per SM whose completion stages every partial row in
+    # shared memory next to the kernel's static shared memory
+    forced_ses(n, d, seed=d, kDs=[10.0, 64.0], dtype=dtype)
+
+
+@pytest.mark.parametrize("d,dtype", [(64, torch.float32), (32, torch.bfloat16)])
+def test_svm_single_steps_large_grids(d, dtype):
+    forced_svm(50_000, 50_000, d, seed=d, kDs=[10.0, 64.0], dtype=dtype)
+
+
 def test_ses_with_radii():
     run_ses_case(2000, 8, seed=3, radii=True)
 
