@@ -297,6 +297,49 @@ pdscp_status ses_batch_read(int32_t num, const void* ws_dev, float* mean_dev, fl
                             pdscp_stream stream);
 
 /*
+ * Batched search: every instance runs the whole search of Sec. 3 (alpha in
+ * [D/2, D], alpha_i = L + (U-L)/3, eps_i and T_i of Theorem 2 with the Sec.
+ * 4.1 constants, the Sec. 5 rules when opts->mode is PDSCP_MODE_PRACTICAL),
+ * with the decisions of ses_solve, on the device: the CTA that finishes an
+ * instance's iteration also updates its search and starts its next
+ * alpha-FTP. An instance's first launch is an evaluation pass at v_1 (which
+ * gives D); a finished instance's tiles are skipped.
+ *   ses_batch_solve_init: as ses_batch_init, plus the search records and
+ *     options (opts->poll_every is not used; opts->max_iters counts MWU
+ *     iterations per instance). Synchronises the stream.
+ *   ses_batch_solve_run: replays a CUDA graph of launches_per_poll launches
+ *     on `stream` until every instance is done or max_launches launches ran
+ *     (host polls a device counter after each replay); reports the launches
+ *     run and the instances done (host pointers, may be NULL).
+ *   ses_batch_solve_read: one pdscp_report per instance (value = upper_bound
+ *     = radius of the returned centre, lower_bound = best primal bound of Eq.
+ *     primal_construction, search_L/U, iters, search_steps, status: OK when
+ *     U <= (1+eps) L or ub <= (1+eps) lb, PDSCP_ERR_NOT_CONVERGED otherwise)
+ *     to reports_dev and the centres, packed as in ses_batch_read, to
+ *     centers_dev (either may be NULL).
+ *   ses_batch_autotune: times the launch for tile_rows in {512, ..., 32768}
+ *     (the candidates whose workspace fits ws_bytes) on this batch and returns
+ *     the fastest; leaves the workspace set up for the last candidate tried,
+ *     so ses_batch_solve_init must follow.
+ */
+pdscp_status ses_batch_solve_init(int32_t num, const float* pts_dev, int64_t pts_len,
+                                  const int64_t* offset_host, const int64_t* n_host,
+                                  const int32_t* d_host, int32_t tile_rows,
+                                  const pdscp_options* opts, void* ws_dev, size_t ws_bytes,
+                                  pdscp_stream stream);
+pdscp_status ses_batch_solve_run(int32_t num, const float* pts_dev, void* ws_dev, size_t ws_bytes,
+                                 int32_t launches_per_poll, int64_t max_launches,
+                                 pdscp_stream stream, int64_t* launches_host, int32_t* done_host);
+pdscp_status ses_batch_solve_read(int32_t num, const void* ws_dev, double eps,
+                                  pdscp_report* reports_dev, float* centers_dev,
+                                  pdscp_stream stream);
+pdscp_status ses_batch_autotune(int32_t num, const float* pts_dev, int64_t pts_len,
+                                const int64_t* offset_host, const int64_t* n_host,
+                                const int32_t* d_host, const pdscp_options* opts, void* ws_dev,
+                                size_t ws_bytes, pdscp_stream stream, int32_t* tile_rows_host,
+                                float* ms_per_launch_host);
+
+/*
  * Row-sharded iteration: the rows (cones) split across G GPUs, one shard per
  * GPU. An MWU iteration over a product of cones (Sec. 3, Eq. implement /
  * min_implement) needs, besides the replicated O(d) state, only column sums

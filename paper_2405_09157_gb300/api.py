@@ -16,6 +16,9 @@ STEP_DTYPE = np.dtype([("oracle_value", "<f8"), ("objective", "<f8"), ("lower_bo
                        ("upper_bound", "<f8"), ("t", "<i8"), ("failed", "<i4"), ("stopped", "<i4"),
                        ("status", "<i4"), ("outcome", "<i4"), ("k", "<f8")])
 STEP_BYTES = 64
+REPORT_DTYPE = np.dtype([("value", "<f8"), ("lower_bound", "<f8"), ("upper_bound", "<f8"), ("D", "<f8"),
+                         ("search_L", "<f8"), ("search_U", "<f8"), ("iters", "<i8"), ("search_steps", "<i4"),
+                         ("status", "<i4")])
 
 
 def _vp(t):
@@ -377,6 +380,58 @@ class SesBatch:
         """alpha, eta_over_rho: float64 CUDA tensors of one value per instance."""
         check(load().ses_batch_step(self.num, _vp(self.pts), _vp(alpha), _vp(eta_over_rho), _vp(self.ws),
                                     self.ws.numel(), _stream(stream), _vp(out)), "ses_batch_step")
+
+    def _host_tables(self):
+        return self.offsets.ctypes.data, self.n.ctypes.data, self.d.ctypes.data
+
+    def autotune(self, eps=1e-3, mode="practical", stream=None, **kw):
+        """Times the batched launch for each tile size that fits the workspace
+        (native autotuner) and re-initialises the batch with the fastest.
+        Returns (tile_rows, ms per launch)."""
+        o = _options(eps, mode, kw.get("max_iters", 1_000_000), 1, kw.get("max_steps", 200), kw.get("eta"),
+                     kw.get("delta", 1e-4), kw.get("patience", 10))
+        lib = load()
+        need = ctypes.c_size_t()
+        check(lib.ses_batch_workspace_size(self.num, self.n.ctypes.data, self.d.ctypes.data, 512,
+                                           ctypes.byref(need)), "ses_batch_workspace_size")
+        if need.value > self.ws.numel():
+            self.ws = torch.zeros(need.value, dtype=torch.uint8, device=self.pts.device)
+        tr, ms = ctypes.c_int32(), ctypes.c_float()
+        offs, n, d = self._host_tables()
+        check(lib.ses_batch_autotune(self.num, _vp(self.pts), self.pts.numel(), offs, n, d, ctypes.byref(o),
+                                     _vp(self.ws), self.ws.numel(), _stream(stream), ctypes.byref(tr),
+                                     ctypes.byref(ms)), "ses_batch_autotune")
+        self.tile_rows = tr.value
+        self.init(stream)
+        return tr.value, ms.value
+
+    def solve(self, eps=1e-3, mode="practical", max_iters=1_000_000, max_steps=200, eta=None, delta=1e-4,
+              patience=10, launches_per_poll=32, max_launches=10_000_000, stream=None):
+        """The search of Sec. 3 for every instance, on the device. Returns
+        (reports: structured numpy array of pdscp_report, centres: list of
+        float32 arrays, launches run)."""
+        o = _options(eps, mode, max_iters, 1, max_steps, eta, delta, patience)
+        lib = load()
+        offs, n, d = self._host_tables()
+        check(lib.ses_batch_solve_init(self.num, _vp(self.pts), self.pts.numel(), offs, n, d, self.tile_rows,
+                                       ctypes.byref(o), _vp(self.ws), self.ws.numel(), _stream(stream)),
+              "ses_batch_solve_init")
+        launches, done = ctypes.c_int64(), ctypes.c_int32()
+        check(lib.ses_batch_solve_run(self.num, _vp(self.pts), _vp(self.ws), self.ws.numel(), launches_per_poll,
+                                      max_launches, _stream(stream), ctypes.byref(launches), ctypes.byref(done)),
+              "ses_batch_solve_run")
+        return self.solve_read(eps, stream) + (launches.value,)
+
+    def solve_read(self, eps, stream=None):
+        reps = torch.zeros((self.num, ctypes.sizeof(_ffi.Report)), dtype=torch.uint8, device=self.pts.device)
+        cen = torch.empty(int(self.d.sum()), dtype=torch.float32, device=self.pts.device)
+        check(load().ses_batch_solve_read(self.num, _vp(self.ws), float(eps), _vp(reps), _vp(cen), _stream(stream)),
+              "ses_batch_solve_read")
+        torch.cuda.synchronize()
+        rec = np.frombuffer(reps.cpu().numpy().tobytes(), dtype=REPORT_DTYPE)
+        cut = np.concatenate([[0], np.cumsum(self.d)])
+        ch = cen.cpu().numpy()
+        return rec, [ch[cut[i]:cut[i + 1]] for i in range(self.num)]
 
     def read(self, stream=None):
         """(means, bests): lists of float32 numpy arrays, one per instance."""

@@ -20,7 +20,7 @@ pdscp_status err(pdscp_status s, const char* fmt, long long a = 0, long long b =
 
 struct BatchLayout {
   int64_t ntiles;
-  size_t inst_off, instcnt_off, tile_off, partial_off, state_off, total;
+  size_t inst_off, instcnt_off, tile_off, partial_off, state_off, search_off, total;
 };
 
 pdscp_status batch_layout(int num, const int64_t* n, const int32_t* d, int tile_rows, BatchLayout* L,
@@ -70,7 +70,104 @@ pdscp_status batch_layout(int num, const int64_t* n, const int32_t* d, int tile_
     t0 += nt;
     moff += d[i];
   }
-  L->total = so;
+  L->search_off = r256(so);
+  L->total = L->search_off + r256((size_t)num * sizeof(BatchSearch));
+  return PDSCP_OK;
+}
+
+// Tables, header and fresh states of a batch (shared by the plain and the
+// search entry points). Synchronises the stream (the host tables are local).
+pdscp_status batch_setup(int32_t num, const float* pts_dev, int64_t pts_len, const int64_t* offset_host,
+                         const int64_t* n_host, const int32_t* d_host, int32_t tile_rows, void* ws_dev,
+                         size_t ws_bytes, cudaStream_t s, BatchLayout* Lout) {
+  if (!pts_dev || !offset_host || !ws_dev || !n_host || !d_host)
+    return err(PDSCP_ERR_INVALID_ARG, "batch: null pointer argument");
+  if (((uintptr_t)pts_dev % 4) != 0 || ((uintptr_t)ws_dev % 256) != 0)
+    return err(PDSCP_ERR_INVALID_ARG, "batch: points must be 4-byte and workspace 256-byte aligned");
+  for (int i = 0; i < num; ++i) {
+    if (offset_host[i] < 0) return err(PDSCP_ERR_INVALID_ARG, "batch: negative offset for instance %lld", i);
+    if (n_host[i] < 0 || d_host[i] < 0 || offset_host[i] + n_host[i] * (int64_t)d_host[i] > pts_len)
+      return err(PDSCP_ERR_INVALID_ARG, "batch: instance %lld extends past the %lld points' floats", i, pts_len);
+  }
+  BatchLayout L;
+  std::vector<BatchInst> insts;
+  std::vector<BatchTile> tiles;
+  insts.reserve(num);
+  pdscp_status st = batch_layout(num, n_host, d_host, tile_rows, &L, &insts, &tiles, offset_host);
+  if (st != PDSCP_OK) return st;
+  if (ws_bytes < L.total) return err(PDSCP_ERR_WORKSPACE, "batch: workspace %lld < %lld bytes", (long long)ws_bytes,
+                                     (long long)L.total);
+  // 16-byte loads need each instance's rows to start on a 16-byte boundary
+  for (auto& in : insts)
+    if (in.shape <= 4 && (((uintptr_t)(pts_dev + in.pt_off)) % 16) != 0) in.shape = batch_shape(in.d, false);
+  unsigned char* ws = reinterpret_cast<unsigned char*>(ws_dev);
+  BatchHeader bh{num, L.ntiles, (int64_t)L.inst_off, (int64_t)L.instcnt_off, (int64_t)L.tile_off,
+                 (int64_t)L.partial_off, (int64_t)L.search_off, 0};
+  cudaError_t e = cudaMemsetAsync(ws, 0, 1024, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ws + 256, &bh, sizeof(bh), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ws + L.inst_off, insts.data(), insts.size() * sizeof(BatchInst), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ws + L.tile_off, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.search_off, 0, (size_t)num * sizeof(BatchSearch), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host tables go out of scope
+  if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: table upload failed (%lld)", (long long)e);
+  ses_batch_init_kernel<<<num, 64, 0, s>>>(pts_dev, reinterpret_cast<const BatchInst*>(ws + L.inst_off), ws,
+                                            reinterpret_cast<unsigned int*>(ws + L.instcnt_off));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: init launch failed (%lld)", (long long)e);
+  if (Lout) *Lout = L;
+  return PDSCP_OK;
+}
+
+cudaError_t launch_batch(const float* pts, const double* alpha, const double* eor, unsigned char* ws,
+                         pdscp_step_out* out, BatchSearch* search, cudaStream_t s) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ses_batch_kernel, kBatchBlock, 0) != cudaSuccess || occ < 1)
+    occ = 1;
+  const int grid = device_sm_count() * occ;
+  BatchParams p{pts, alpha, eor, ws, out, search};
+  ses_batch_kernel<<<grid, kBatchBlock, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+pdscp_status solve_opts(const pdscp_options* o, BatchSolveOpts* b) {
+  if (!o) return err(PDSCP_ERR_INVALID_ARG, "batch: options pointer is null");
+  if (!(o->eps > 0.0) || !(o->delta >= 0.0) || o->patience < 1 || o->max_iters < 1 || o->max_steps < 1 ||
+      (o->mode != PDSCP_MODE_PRACTICAL && o->mode != PDSCP_MODE_THEORY) || !(o->eta >= 0.0) || o->eta > 1.0)
+    return err(PDSCP_ERR_INVALID_ARG, "batch: invalid search options");
+  b->eps = o->eps;
+  b->delta = o->delta;
+  b->eta = o->eta;
+  b->max_iters = o->max_iters;
+  b->patience = o->patience;
+  b->rules = o->mode == PDSCP_MODE_PRACTICAL ? PDSCP_RULES_PRACTICAL : PDSCP_RULES_NONE;
+  b->max_steps = o->max_steps;
+  b->pad = 0;
+  return PDSCP_OK;
+}
+
+pdscp_status solve_setup(int32_t num, const float* pts_dev, int64_t pts_len, const int64_t* offset_host,
+                         const int64_t* n_host, const int32_t* d_host, int32_t tile_rows, const pdscp_options* o,
+                         void* ws_dev, size_t ws_bytes, cudaStream_t s) {
+  BatchSolveOpts bo;
+  pdscp_status st = solve_opts(o, &bo);
+  if (st != PDSCP_OK) return st;
+  st = batch_setup(num, pts_dev, pts_len, offset_host, n_host, d_host, tile_rows, ws_dev, ws_bytes, s, nullptr);
+  if (st != PDSCP_OK) return st;
+  cudaError_t e = cudaMemcpyAsync(reinterpret_cast<unsigned char*>(ws_dev) + kBatchOptsOff, &bo, sizeof(bo),
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: options upload failed (%lld)", (long long)e);
+  return PDSCP_OK;
+}
+
+pdscp_status read_header(const void* ws_dev, cudaStream_t s, BatchHeader* bh) {
+  cudaError_t e = cudaMemcpyAsync(bh, reinterpret_cast<const unsigned char*>(ws_dev) + 256, sizeof(*bh),
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: header read failed (%lld)", (long long)e);
+  if (bh->search_off <= 0) return err(PDSCP_ERR_INVALID_ARG, "batch: workspace was not set up by ses_batch_*init");
   return PDSCP_OK;
 }
 
@@ -94,43 +191,8 @@ pdscp_status ses_batch_workspace_size(int32_t num, const int64_t* n_host, const 
 pdscp_status ses_batch_init(int32_t num, const float* pts_dev, int64_t pts_len, const int64_t* offset_host,
                             const int64_t* n_host, const int32_t* d_host, int32_t tile_rows, void* ws_dev,
                             size_t ws_bytes, pdscp_stream stream) {
-  if (!pts_dev || !offset_host || !ws_dev || !n_host || !d_host)
-    return err(PDSCP_ERR_INVALID_ARG, "batch: null pointer argument");
-  if (((uintptr_t)pts_dev % 4) != 0 || ((uintptr_t)ws_dev % 256) != 0)
-    return err(PDSCP_ERR_INVALID_ARG, "batch: points must be 4-byte and workspace 256-byte aligned");
-  for (int i = 0; i < num; ++i) {
-    if (offset_host[i] < 0) return err(PDSCP_ERR_INVALID_ARG, "batch: negative offset for instance %lld", i);
-    if (n_host[i] < 0 || d_host[i] < 0 || offset_host[i] + n_host[i] * (int64_t)d_host[i] > pts_len)
-      return err(PDSCP_ERR_INVALID_ARG, "batch: instance %lld extends past the %lld points' floats", i, pts_len);
-  }
-  BatchLayout L;
-  std::vector<BatchInst> insts;
-  std::vector<BatchTile> tiles;
-  insts.reserve(num);
-  pdscp_status st = batch_layout(num, n_host, d_host, tile_rows, &L, &insts, &tiles, offset_host);
-  if (st != PDSCP_OK) return st;
-  if (ws_bytes < L.total) return err(PDSCP_ERR_WORKSPACE, "batch: workspace %lld < %lld bytes", (long long)ws_bytes,
-                                     (long long)L.total);
-  // 16-byte loads need each instance's rows to start on a 16-byte boundary
-  for (auto& in : insts)
-    if (in.shape <= 4 && (((uintptr_t)(pts_dev + in.pt_off)) % 16) != 0) in.shape = batch_shape(in.d, false);
-  unsigned char* ws = reinterpret_cast<unsigned char*>(ws_dev);
-  cudaStream_t s = (cudaStream_t)stream;
-  BatchHeader bh{num, L.ntiles, (int64_t)L.inst_off, (int64_t)L.instcnt_off, (int64_t)L.tile_off,
-                 (int64_t)L.partial_off};
-  cudaError_t e = cudaMemsetAsync(ws, 0, 256, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(ws + 256, &bh, sizeof(bh), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(ws + L.inst_off, insts.data(), insts.size() * sizeof(BatchInst), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(ws + L.tile_off, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host tables go out of scope
-  if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: table upload failed (%lld)", (long long)e);
-  ses_batch_init_kernel<<<num, 64, 0, s>>>(pts_dev, reinterpret_cast<const BatchInst*>(ws + L.inst_off), ws,
-                                            reinterpret_cast<unsigned int*>(ws + L.instcnt_off));
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: init launch failed (%lld)", (long long)e);
-  return PDSCP_OK;
+  return batch_setup(num, pts_dev, pts_len, offset_host, n_host, d_host, tile_rows, ws_dev, ws_bytes,
+                     (cudaStream_t)stream, nullptr);
 }
 
 pdscp_status ses_batch_step(int32_t num, const float* pts_dev, const double* alpha_dev,
@@ -139,14 +201,124 @@ pdscp_status ses_batch_step(int32_t num, const float* pts_dev, const double* alp
   if (num < 1 || !pts_dev || !alpha_dev || !eta_over_rho_dev || !ws_dev)
     return err(PDSCP_ERR_INVALID_ARG, "batch: bad argument to ses_batch_step");
   if (ws_bytes < 1024) return err(PDSCP_ERR_WORKSPACE, "batch: workspace too small");
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ses_batch_kernel, kBatchBlock, 0) != cudaSuccess || occ < 1)
-    occ = 1;
-  const int grid = device_sm_count() * occ;
-  BatchParams p{pts_dev, alpha_dev, eta_over_rho_dev, reinterpret_cast<unsigned char*>(ws_dev), out_dev};
-  ses_batch_kernel<<<grid, kBatchBlock, 0, (cudaStream_t)stream>>>(p);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_batch(pts_dev, alpha_dev, eta_over_rho_dev, reinterpret_cast<unsigned char*>(ws_dev),
+                               out_dev, nullptr, (cudaStream_t)stream);
   if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: step launch failed (%lld)", (long long)e);
+  return PDSCP_OK;
+}
+
+pdscp_status ses_batch_solve_init(int32_t num, const float* pts_dev, int64_t pts_len, const int64_t* offset_host,
+                                  const int64_t* n_host, const int32_t* d_host, int32_t tile_rows,
+                                  const pdscp_options* opts, void* ws_dev, size_t ws_bytes, pdscp_stream stream) {
+  return solve_setup(num, pts_dev, pts_len, offset_host, n_host, d_host, tile_rows, opts, ws_dev, ws_bytes,
+                     (cudaStream_t)stream);
+}
+
+pdscp_status ses_batch_solve_run(int32_t num, const float* pts_dev, void* ws_dev, size_t ws_bytes,
+                                 int32_t launches_per_poll, int64_t max_launches, pdscp_stream stream,
+                                 int64_t* launches_host, int32_t* done_host) {
+  if (num < 1 || !pts_dev || !ws_dev || launches_per_poll < 1 || max_launches < 1)
+    return err(PDSCP_ERR_INVALID_ARG, "batch: bad argument to ses_batch_solve_run");
+  if (ws_bytes < 1024) return err(PDSCP_ERR_WORKSPACE, "batch: workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* ws = reinterpret_cast<unsigned char*>(ws_dev);
+  BatchHeader bh;
+  pdscp_status st = read_header(ws_dev, s, &bh);
+  if (st != PDSCP_OK) return st;
+  BatchSearch* search = reinterpret_cast<BatchSearch*>(ws + bh.search_off);
+  const unsigned int* done = reinterpret_cast<const unsigned int*>(ws) + 2;
+  // a CUDA graph of launches_per_poll iterations, captured on a private stream
+  // (the legacy default stream cannot be captured) and replayed on `stream`
+  cudaStream_t cs = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int k = 0; k < launches_per_poll && e == cudaSuccess; ++k)
+      e = launch_batch(pts_dev, nullptr, nullptr, ws, nullptr, search, cs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  int64_t launches = 0;
+  unsigned int done_h = 0;
+  while (e == cudaSuccess && launches < max_launches) {
+    e = cudaGraphLaunch(exec, s);
+    launches += launches_per_poll;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&done_h, done, sizeof(done_h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (done_h >= (unsigned int)num) break;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (cs) cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: search launches failed (%lld)", (long long)e);
+  if (launches_host) *launches_host = launches;
+  if (done_host) *done_host = (int32_t)done_h;
+  return PDSCP_OK;
+}
+
+pdscp_status ses_batch_solve_read(int32_t num, const void* ws_dev, double eps, pdscp_report* reports_dev,
+                                  float* centers_dev, pdscp_stream stream) {
+  if (num < 1 || !ws_dev) return err(PDSCP_ERR_INVALID_ARG, "batch: bad argument to ses_batch_solve_read");
+  cudaStream_t s = (cudaStream_t)stream;
+  BatchHeader bh;
+  pdscp_status st = read_header(ws_dev, s, &bh);
+  if (st != PDSCP_OK) return st;
+  const unsigned char* ws = reinterpret_cast<const unsigned char*>(ws_dev);
+  ses_batch_solve_read_kernel<<<num, 64, 0, s>>>(reinterpret_cast<const BatchInst*>(ws + bh.inst_off),
+                                                 reinterpret_cast<const BatchSearch*>(ws + bh.search_off), eps,
+                                                 reports_dev, centers_dev);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: read launch failed (%lld)", (long long)e);
+  return PDSCP_OK;
+}
+
+pdscp_status ses_batch_autotune(int32_t num, const float* pts_dev, int64_t pts_len, const int64_t* offset_host,
+                                const int64_t* n_host, const int32_t* d_host, const pdscp_options* opts,
+                                void* ws_dev, size_t ws_bytes, pdscp_stream stream, int32_t* tile_rows_host,
+                                float* ms_per_launch_host) {
+  if (!tile_rows_host) return err(PDSCP_ERR_INVALID_ARG, "batch: null output pointer");
+  static const int32_t cand[] = {512, 1024, 2048, 4096, 8192, 16384, 32768};
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: event create failed (%lld)", (long long)e);
+  int32_t best = 0;
+  float best_ms = INFINITY;
+  pdscp_status st = PDSCP_OK;
+  for (int32_t tr : cand) {
+    BatchLayout L;
+    if (batch_layout(num, n_host, d_host, tr, &L, nullptr, nullptr, nullptr) != PDSCP_OK || L.total > ws_bytes) continue;
+    st = solve_setup(num, pts_dev, pts_len, offset_host, n_host, d_host, tr, opts, ws_dev, ws_bytes, s);
+    if (st != PDSCP_OK) break;
+    BatchHeader bh;
+    if ((st = read_header(ws_dev, s, &bh)) != PDSCP_OK) break;
+    unsigned char* ws = reinterpret_cast<unsigned char*>(ws_dev);
+    BatchSearch* search = reinterpret_cast<BatchSearch*>(ws + bh.search_off);
+    // the bounds pass and one iteration untimed, then four timed iterations
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_batch(pts_dev, nullptr, nullptr, ws, nullptr, search, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = launch_batch(pts_dev, nullptr, nullptr, ws, nullptr, search, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) break;
+    if (ms / 4.f < best_ms) {
+      best_ms = ms / 4.f;
+      best = tr;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: autotune launches failed (%lld)", (long long)e);
+  if (st != PDSCP_OK) return st;
+  if (best == 0) return err(PDSCP_ERR_WORKSPACE, "batch: workspace too small for every tile size");
+  *tile_rows_host = best;
+  if (ms_per_launch_host) *ms_per_launch_host = best_ms;
   return PDSCP_OK;
 }
 

@@ -41,14 +41,43 @@ struct BatchTile {
 struct BatchHeader {
   int64_t num, ntiles;
   int64_t inst_off, instcnt_off, tile_off, partial_off;
+  int64_t search_off;
+  int64_t pad;
 };
+
+// Device-side search of Sec. 3 for every instance of a batch (the rules of
+// ses_solve, run by the CTA that finishes an instance's iteration), in phases:
+constexpr int kPhaseBounds = 0;  // evaluation pass at v_1: f(v_1) = D of Sec. 4.1
+constexpr int kPhaseFtp = 1;     // an alpha-FTP is running
+constexpr int kPhaseFinal = 2;   // evaluation pass at the mean the FTP ended with
+constexpr int kPhaseDone = 3;
+
+struct BatchSearch {
+  double D, rho, logr;        // Sec. 4.1 constants of the instance
+  double L, U, lb, ub;        // search range and certificates
+  double alpha, eps_i, eta_over_rho;
+  int64_t T, cap, total;      // theorem count of this FTP, its iteration cap, iterations so far
+  int32_t steps, phase, status, pad;
+  float center[kBatchMaxD];   // the centre achieving ub
+};
+static_assert(sizeof(BatchSearch) == 376, "search record layout");
+
+struct BatchSolveOpts {
+  double eps, delta, eta;     // eta <= 0: eta_i = sqrt(ln r / T_i) (Theorem 2)
+  int64_t max_iters;          // per instance
+  int32_t patience, rules, max_steps, pad;
+};
+
+// The search options live in the workspace at this offset (after the header).
+constexpr size_t kBatchOptsOff = 512;
 
 struct BatchParams {
   const float* pts;
-  const double* alpha;         // per instance
-  const double* eta_over_rho;  // per instance
+  const double* alpha;         // per instance (plain iterations)
+  const double* eta_over_rho;  // per instance (plain iterations)
   unsigned char* ws;           // workspace base
   pdscp_step_out* out;         // per instance, may be null
+  BatchSearch* search;         // non-null: device-side search; alpha, eta/rho come from here
 };
 
 // Load/lane layouts, chosen on the host per instance:
@@ -158,6 +187,135 @@ __device__ void batch_tile(const float* pts, int d, int64_t r0, int64_t r1, cons
   }
 }
 
+// One warp, after the instance's finish: advances the instance's search
+// (the decisions of ses_solve: Sec. 3's update of [L, U] from the FTP's
+// outcome, Sec. 5's early exits, the primal lower bound of Eq.
+// primal_construction as a certificate) and starts its next alpha-FTP.
+__device__ void batch_search_update(BatchSearch* sr, void* state, const float* v1, int d, int64_t n,
+                                    const BatchSolveOpts& o, unsigned int* done_counter) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  StateHdr* hdr = reinterpret_cast<StateHdr*>(state);
+  const StateHdr h = *hdr;  // written by lane 0 of this warp before the __syncwarp
+  BatchSearch r = *sr;
+  bool end_ftp = false, start_ftp = false, done = false;
+  if (h.status != PDSCP_OK) {
+    r.status = h.status;
+    done = true;
+  } else if (r.phase == kPhaseBounds) {
+    r.D = h.hint;  // max_{i>=2} |v_1 - v_i| from the evaluation pass at v_1
+    if (!(r.D > 0.0)) {
+      r.lb = r.ub = r.L = r.U = 0.0;
+      done = true;
+    } else {
+      r.rho = 3.0 * r.D / kSqrt2;
+      r.logr = log(2.0 * (double)(n - 1));
+      r.L = r.D / 2.0;
+      r.U = r.D;
+      r.lb = 0.0;
+      r.ub = INFINITY;
+      start_ftp = true;
+    }
+  } else if (r.phase == kPhaseFinal) {
+    end_ftp = true;
+  } else if (h.stopped) {
+    end_ftp = true;
+  } else if (h.t >= r.cap) {
+    r.phase = kPhaseFinal;  // the next launch evaluates f at the final mean
+  }
+  if (end_ftp) {
+    const int64_t iters = h.t;
+    const int oc = h.stopped ? h.outcome : PDSCP_OUT_RUNNING;
+    r.total += iters;
+    const bool better = h.best_f < r.ub;
+    if (better) r.ub = h.best_f;
+    for (int j = lane; j < d; j += 32)
+      if (better) r.center[j] = state_best(state, d)[j];
+    if (h.lb_best > r.lb) r.lb = h.lb_best;
+    if (oc == PDSCP_OUT_SEPARATED) {
+      r.L = fmax(r.L, r.alpha);
+    } else if (iters >= r.T || oc == PDSCP_OUT_STALLED || oc == PDSCP_OUT_BEAT_ALPHA) {
+      r.U = fmin(fmin(r.U, (1.0 + r.eps_i) * r.alpha), r.ub);
+    }
+    r.L = fmax(r.L, r.lb);
+    r.steps += 1;
+    if (oc == PDSCP_OUT_RUNNING && iters < r.T) {
+      done = true;  // the iteration budget ended this FTP
+    } else if (!(r.U > (1.0 + o.eps) * r.L && r.ub > (1.0 + o.eps) * r.lb && r.total < o.max_iters &&
+                 r.steps < o.max_steps)) {
+      done = true;
+    } else {
+      start_ftp = true;
+    }
+  }
+  if (start_ftp) {
+    r.alpha = r.L + (r.U - r.L) / 3.0;
+    r.eps_i = (r.U - r.L) / (3.0 * r.alpha);
+    const double Tf = ceil(36.0 * r.D * r.D * r.logr / (r.eps_i * r.eps_i * r.alpha * r.alpha));
+    r.T = Tf > 4.0e18 ? (int64_t)4e18 : (int64_t)Tf;
+    const double eta = o.eta > 0.0 ? o.eta : sqrt(r.logr / (double)r.T);
+    r.eta_over_rho = eta / r.rho;
+    const int64_t left = o.max_iters - r.total;
+    r.cap = r.T < left ? r.T : left;
+    r.phase = kPhaseFtp;
+    // a fresh alpha-FTP: t = 0, mean = v_1 (as mwu_state_init)
+    const int dp = dpad4(d);
+    double* mean = state_mean(state);
+    float* mean32 = state_mean32(state, d);
+    float* best = state_best(state, d);
+    for (int j = lane; j < dp; j += 32) {
+      const double v = j < d ? (double)v1[j] : 0.0;
+      mean[j] = v;
+      mean32[j] = (float)v;
+      best[j] = (float)v;
+    }
+    if (lane == 0) {
+      StateHdr z;
+      memset(&z, 0, sizeof(z));
+      z.rules = o.rules;
+      z.patience = o.patience;
+      z.delta = o.delta;
+      z.f_prev = -1.0;
+      z.best_f = INFINITY;
+      z.ub_best = INFINITY;
+      *hdr = z;
+    }
+  }
+  if (done) {
+    if (!(r.ub < INFINITY) || !(r.D > 0.0)) {  // no FTP produced a centre: v_1 with radius D encloses every point
+      r.ub = r.D;
+      for (int j = lane; j < d; j += 32) r.center[j] = v1[j];
+    }
+    r.phase = kPhaseDone;
+    if (lane == 0) {
+      hdr->stopped = 1;  // the instance's tiles are skipped from now on
+      atomicAdd(done_counter, 1u);
+    }
+  }
+  __syncwarp();
+  // scalars by lane 0; each lane already wrote its own centre entries
+  if (lane == 0) {
+    BatchSearch* dst = sr;
+    dst->D = r.D;
+    dst->rho = r.rho;
+    dst->logr = r.logr;
+    dst->L = r.L;
+    dst->U = r.U;
+    dst->lb = r.lb;
+    dst->ub = r.ub;
+    dst->alpha = r.alpha;
+    dst->eps_i = r.eps_i;
+    dst->eta_over_rho = r.eta_over_rho;
+    dst->T = r.T;
+    dst->cap = r.cap;
+    dst->total = r.total;
+    dst->steps = r.steps;
+    dst->phase = r.phase;
+    dst->status = r.status;
+  }
+  for (int j = lane; j < d; j += 32) sr->center[j] = r.center[j];
+}
+
 __global__ void __launch_bounds__(kBatchBlock) ses_batch_kernel(BatchParams p) {
   __shared__ float sG[kBatchWarps * kBatchMaxD];
   __shared__ float s_sc[kBatchWarps][3];
@@ -189,11 +347,19 @@ __global__ void __launch_bounds__(kBatchBlock) ses_batch_kernel(BatchParams p) {
     const StateHdr* hdr = reinterpret_cast<const StateHdr*>(state);
     const int d = in.d;
     const float* pts = p.pts + in.pt_off;
-    const bool stopped = hdr->stopped != 0;
-    if (!stopped) {
-      const float kr = (float)((double)hdr->t * p.eta_over_rho[tl.inst] / kSqrt2);
+    if (hdr->stopped != 0) {  // a stopped FTP (or a finished search) is left as is
+      __syncthreads();
+      continue;
+    }
+    const BatchSearch* sr = p.search ? p.search + tl.inst : nullptr;
+    const int phase = sr ? sr->phase : kPhaseFtp;
+    const bool eval = phase == kPhaseBounds || phase == kPhaseFinal;
+    const double alpha_d = sr ? sr->alpha : p.alpha[tl.inst];
+    const double eor_d = sr ? sr->eta_over_rho : p.eta_over_rho[tl.inst];
+    {
+      const float kr = eval ? 0.f : (float)((double)hdr->t * eor_d / kSqrt2);
       const float H = (float)(hdr->hint + hdr->move);
-      const float alpha = (float)p.alpha[tl.inst];
+      const float alpha = (float)alpha_d;
       const float* mean32 = state_mean32(state, d);
       if (tid < d) s_ub[tid] = mean32[tid];
       __syncthreads();
@@ -240,7 +406,7 @@ __global__ void __launch_bounds__(kBatchBlock) ses_batch_kernel(BatchParams p) {
     if (s_flag) {
       // this CTA completed the instance: reduce its rows and finish it
       if (tid == 0) inst_counters[tl.inst] = 0u;
-      if (!stopped) {
+      {
         constexpr int HW = (int)(sizeof(StateHdr) / 8);
         if (tid < HW) s_hdr[tid] = reinterpret_cast<const double*>(hdr)[tid];
         const double* mean = state_mean(state);
@@ -252,9 +418,14 @@ __global__ void __launch_bounds__(kBatchBlock) ses_batch_kernel(BatchParams p) {
         // rows of this instance: stride kBatchStride, the first st columns used
         reduce_rows(partials + (size_t)in.tile0 * kBatchStride, 0, in.ntiles, st, raw, s_scr, opof, false,
                     kBatchStride);
-        if (tid < 32)
-          ses_finish_warp(raw, s_mean, s_v1, *reinterpret_cast<const StateHdr*>(s_hdr), state, d,
-                          p.alpha[tl.inst], 0.0, p.eta_over_rho[tl.inst], 0, p.out ? p.out + tl.inst : nullptr);
+        if (tid < 32) {
+          ses_finish_warp(raw, s_mean, s_v1, *reinterpret_cast<const StateHdr*>(s_hdr), state, d, alpha_d, 0.0,
+                          eor_d, eval ? 1 : 0, p.out ? p.out + tl.inst : nullptr);
+          if (p.search)
+            batch_search_update(p.search + tl.inst, state, pts, d, in.n,
+                                *reinterpret_cast<const BatchSolveOpts*>(p.ws + kBatchOptsOff),
+                                reinterpret_cast<unsigned int*>(p.ws) + 2);
+        }
       }
     }
     __syncthreads();
@@ -307,6 +478,29 @@ __global__ void ses_batch_read_kernel(const BatchInst* inst, unsigned char* ws, 
   for (int j = threadIdx.x; j < in.d; j += blockDim.x) {
     if (mean_out) mean_out[in.mean_off + j] = state_mean32(state, in.d)[j];
     if (best_out) best_out[in.mean_off + j] = state_best(state, in.d)[j];
+  }
+}
+
+// Per-instance search results: reports and centres (packed at inst.mean_off).
+__global__ void ses_batch_solve_read_kernel(const BatchInst* inst, const BatchSearch* search, double eps,
+                                            pdscp_report* rep, float* center_out) {
+  const BatchInst in = inst[blockIdx.x];
+  const BatchSearch& r = search[blockIdx.x];
+  for (int j = threadIdx.x; j < in.d; j += blockDim.x)
+    if (center_out) center_out[in.mean_off + j] = r.center[j];
+  if (threadIdx.x == 0 && rep) {
+    pdscp_report o;
+    o.value = r.ub;
+    o.lower_bound = r.lb;
+    o.upper_bound = r.ub;
+    o.D = r.D;
+    o.search_L = r.L;
+    o.search_U = r.U;
+    o.iters = r.total;
+    o.search_steps = r.steps;
+    const bool conv = r.phase == kPhaseDone && (r.U <= (1.0 + eps) * r.L || r.ub <= (1.0 + eps) * r.lb);
+    o.status = r.status != PDSCP_OK ? r.status : (conv ? PDSCP_OK : PDSCP_ERR_NOT_CONVERGED);
+    rep[blockIdx.x] = o;
   }
 }
 

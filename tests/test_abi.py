@@ -124,3 +124,20 @@ def test_shard_validation_without_gpu(lib):
     assert st == 1 and b"D > 0" in lib.pdscp_last_error()
     st = lib.mwu_shard_init(_ffi.SES, None, _ffi.F32, 4, 0, 1e-4, 10, fake, fake, 1 << 30, None)
     assert st == 1 and b"v_1" in lib.pdscp_last_error()
+
+
+def test_batch_search_validation_without_gpu(lib):
+    n = (ctypes.c_int64 * 2)(100, 50)
+    d = (ctypes.c_int32 * 2)(8, 8)
+    offs = (ctypes.c_int64 * 2)(0, 800)
+    fake = ctypes.c_void_p(1 << 20)
+    bad = _ffi.Options(0.0, 1e-4, 10, 0, 1000, 1, 10, 0.0)  # eps = 0
+    st = lib.ses_batch_solve_init(2, fake, 1200, offs, n, d, 512, ctypes.byref(bad), fake, 1 << 30, None)
+    assert st == 1 and b"options" in lib.pdscp_last_error()
+    bad = _ffi.Options(1e-3, 1e-4, 10, 7, 1000, 1, 10, 0.0)  # unknown mode
+    assert lib.ses_batch_solve_init(2, fake, 1200, offs, n, d, 512, ctypes.byref(bad), fake, 1 << 30, None) == 1
+    launches, done = ctypes.c_int64(), ctypes.c_int32()
+    assert lib.ses_batch_solve_run(2, fake, fake, 1 << 30, 0, 10, None, ctypes.byref(launches),
+                                   ctypes.byref(done)) == 1
+    tr = ctypes.c_int32()
+    assert lib.ses_batch_autotune(2, fake, 1200, offs, n, d, None, fake, 1 << 30, None, None, None) == 1
