@@ -297,6 +297,8 @@ def run_ours(args):
         result["variants"] = variants(dev, flush)
         result["variants"]["batched_ses_4096"] = batched_variant(dev)
         result["variants"]["ses_backward_n1e5_d64_T2000"] = backward_variant(dev)
+        result["variants"]["ses_multi_candidate_n1e6_d32"] = multi_variant(dev, flush)
+        result["variants"]["batched_ses_4096_search"] = batched_solve_variant(dev)
         result["time_to_eps"] = time_to_eps(pts)
     if world > 1:
         dist.barrier()
@@ -416,15 +418,53 @@ def variants(dev, flush):
     return out
 
 
-def batched_variant(dev, K=10, W=3):
-    """Per-iteration time of the batched SES workload: 4096 instances, n log-uniform
-    in [100, 1e5], d in {2,3,8,16,32,64}, N(0, I) points times a per-instance
-    U[0.1, 10] scale (sizes from the seeded generator, points from a seeded
-    device RNG); one launch advances every instance by one iteration. The input
-    (about 5 GB) is far larger than L2, so no flush is needed between steps."""
+def multi_variant(dev, flush, K=50):
+    """Multi-candidate pass (ses_multi_step) on the default workload: k alpha-FTPs
+    (alpha_j = (1 + 0.05 j) D, never separating) advanced by one pass over the
+    1,000,000 x 32 FP32 points, k in {1, 2, 4, 8}, timed as the main line (L2
+    flushed between steps, CUDA events around each step). Bytes per pass are
+    those of one iteration; per point the arithmetic grows k-fold."""
     import torch
-    from paper_2405_09157_gb300 import api, datagen
-    n, d, scale = datagen.batched_ses_sizes(4096, seed=0)
+    from paper_2405_09157_gb300 import _ffi, api, datagen
+    peak, _ = peaks()
+    V32 = datagen.ses_gaussian(N_POINTS, DIM, SEED)
+    pts = torch.from_numpy(V32).to(dev)
+    D = float(api.bounds(_ffi.SES, pts).item())
+    eor = 0.01 / (3 * D / math.sqrt(2))
+    res = {}
+    for k in (1, 2, 4, 8):
+        m = api.MultiMWU(pts, k)
+        a = torch.tensor([(1.0 + 0.05 * j) * D for j in range(k)], dtype=torch.float64, device=dev)
+        e = torch.full((k,), eor, dtype=torch.float64, device=dev)
+        out = api.new_steps(k, dev)
+        s0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        s1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        for i in range(K + 5):
+            flush()
+            if i >= 5:
+                s0[i - 5].record()
+            m.step(a, e, out=out)
+            if i >= 5:
+                s1[i - 5].record()
+        torch.cuda.synchronize()
+        rec = api.decode_steps(out)
+        if not np.all(rec["t"] == K + 5):
+            raise RuntimeError("a multi-candidate step did not advance every candidate")
+        ms = sum(x.elapsed_time(y) for x, y in zip(s0, s1)) / K
+        b = N_POINTS * DIM * 4
+        res[f"k{k}"] = {"ms_per_pass": ms, "candidate_iters_per_s": k * 1e3 / ms, "GBps": b / ms / 1e6,
+                        "frac_hbm": b / ms / 1e6 / peak}
+    return res
+
+
+def batched_inputs(dev, num=4096):
+    """The batched SES workload on the device: sizes from the seeded generator
+    (n log-uniform in [100, 1e5], d in {2,3,8,16,32,64}, scale U[0.1, 10]),
+    N(0, I) points from a seeded device RNG times the instance's scale, each
+    instance starting on a 16-byte boundary."""
+    import torch
+    from paper_2405_09157_gb300 import datagen
+    n, d, scale = datagen.batched_ses_sizes(num, seed=0)
     sizes = n * d
     offs = np.zeros(len(n), dtype=np.int64)
     pos = 0
@@ -440,6 +480,43 @@ def batched_variant(dev, K=10, W=3):
         elem_scale[offs[i]:offs[i] + sizes[i]] = float(scale[i])
     pts.mul_(elem_scale)
     del elem_scale
+    return pts, offs, n, d, scale
+
+
+def batched_solve_variant(dev, eps=1e-3, max_iters=20_000):
+    """Time to solve the batched SES workload: every instance runs the search
+    of Sec. 3 on the device (practical rules of Sec. 5, eps = 1e-3, at most
+    max_iters MWU iterations per instance), after the native autotuner picked
+    the tile size. Wall time of the whole search (CUDA events around
+    ses_batch_solve_run), launches, and how many instances closed their
+    range."""
+    import torch
+    from paper_2405_09157_gb300 import api
+    pts, offs, n, d, _ = batched_inputs(dev)
+    batch = api.SesBatch(pts, offs, n, d, tile_rows=4096)
+    tr, ms_launch = batch.autotune(eps=eps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps, _, launches = batch.solve(eps=eps, max_iters=max_iters, launches_per_poll=64)
+    sec = time.perf_counter() - t0
+    conv = int(np.sum(reps["status"] == 0))
+    gap = reps["upper_bound"] / np.maximum(reps["lower_bound"], 1e-300) - 1.0
+    return {"workload": f"{len(n)} SES instances, eps={eps}, practical rules, <= {max_iters} iterations each",
+            "seconds": sec, "launches": int(launches), "tile_rows": int(tr), "ms_per_launch_autotune": ms_launch,
+            "instances_converged": conv, "instances": int(len(n)), "iters_total": int(reps["iters"].sum()),
+            "certificate_gap_median": float(np.median(gap)), "certificate_gap_max": float(np.max(gap))}
+
+
+def batched_variant(dev, K=10, W=3):
+    """Per-iteration time of the batched SES workload: 4096 instances, n log-uniform
+    in [100, 1e5], d in {2,3,8,16,32,64}, N(0, I) points times a per-instance
+    U[0.1, 10] scale (sizes from the seeded generator, points from a seeded
+    device RNG); one launch advances every instance by one iteration. The input
+    (about 5 GB) is far larger than L2, so no flush is needed between steps."""
+    import torch
+    from paper_2405_09157_gb300 import api
+    pts, offs, n, d, scale = batched_inputs(dev)
+    sizes = n * d
     batch = api.SesBatch(pts, offs, n, d, tile_rows=4096)
     bound = 2.0 * scale * (np.sqrt(d) + 6.0)  # >= OPT with room: the ORACLE never separates
     a = torch.tensor(bound, dtype=torch.float64, device=dev)

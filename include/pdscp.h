@@ -383,6 +383,28 @@ pdscp_status mwu_shard_finish(int32_t problem, const float* rows_dev, int32_t ra
                               pdscp_step_out* out_dev);
 
 /*
+ * Multi-candidate SES iteration: one streaming pass over the points advances
+ * k in {1, 2, 4, 8} independent alpha-FTPs of the same instance (Sec. 3 with
+ * the SES data of Sec. 4.1), each with its own alpha_j, eta_j/rho and state:
+ * the candidates of a k-ary search over alpha share every byte read. Float32
+ * points, d <= 64. Per candidate the result is that of mwu_step with the same
+ * alpha_j, eta_j/rho and state (up to the order of the FP32 partial sums).
+ *   ses_multi_state_stride: bytes between consecutive candidate states in
+ *     states_dev (a multiple of 256); each state is started with
+ *     mwu_state_init (PDSCP_SES, the same points) at states_dev + j * stride.
+ *   ses_multi_workspace_size: bytes of ws_dev for (d, k); ws_dev must be
+ *     zero-filled before its first use (the kernels leave their counters at 0).
+ *   ses_multi_step: alpha_dev, eta_over_rho_dev: k doubles (device); out_dev:
+ *     k records or NULL. A stopped candidate keeps its state. Asynchronous.
+ */
+pdscp_status ses_multi_state_stride(int32_t d, size_t* bytes_host);
+pdscp_status ses_multi_workspace_size(int32_t d, int32_t k, size_t* bytes_host);
+pdscp_status ses_multi_step(const float* pts_dev, const float* radii_dev, int64_t n, int32_t d,
+                            int32_t k, const double* alpha_dev, const double* eta_over_rho_dev,
+                            void* states_dev, void* ws_dev, size_t ws_bytes, pdscp_stream stream,
+                            pdscp_step_out* out_dev);
+
+/*
  * Reverse-mode sweep through T unrolled iterations of the SES alpha-FTP at
  * fixed alpha and eta/rho (Sec. 3, Eq. implement, ORACLE Eq. ses_oracle): the
  * gradient of L = seed * f(ubar^T), f(c) = max_i ||c - v_i|| + gamma_i the

@@ -82,6 +82,9 @@ SIGNATURES = {
                                   c_i32, c_vp, c_vp, c_sz, c_vp, c_vp]),
     "mwu_shard_finish": (c_i32, [c_i32, c_vp, c_i32, c_vp, c_i32, c_vp, c_i32, c_dbl, c_dbl, c_dbl, c_i32,
                                  c_vp, c_vp, c_vp]),
+    "ses_multi_state_stride": (c_i32, [c_i32, ctypes.POINTER(c_sz)]),
+    "ses_multi_workspace_size": (c_i32, [c_i32, c_i32, ctypes.POINTER(c_sz)]),
+    "ses_multi_step": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp, c_vp]),
     "mwu_backward_workspace_size": (c_i32, [c_i32, c_i64, c_i32, c_i64, ctypes.POINTER(c_sz)]),
     "mwu_backward": (c_i32, [c_i32, c_vp, c_i32, c_vp, c_vp, c_i64, c_i32, c_dbl, c_dbl, c_dbl, c_i64, c_vp,
                              c_vp, c_sz, c_vp, c_vp, c_vp]),

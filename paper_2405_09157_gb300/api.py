@@ -130,6 +130,43 @@ def state_set(problem, pts, t, mean, state, ws, radii=None, labels=None, D=0.0, 
                                float(D), _vp(state), _vp(ws), ws.numel(), _stream(stream)), "mwu_state_set")
 
 
+# --- multi-candidate iteration (SES) -----------------------------------------
+
+class MultiMWU:
+    """k alpha-FTPs of one SES instance (float32 points, d <= 64) advanced by
+    one pass over the points per iteration, each with its own alpha and
+    eta/rho (k in {1, 2, 4, 8})."""
+
+    def __init__(self, pts, k, radii=None, rules=_ffi.RULES_NONE, delta=1e-4, patience=10, stream=None):
+        n, d, dt = _points(pts)
+        if dt != F32:
+            raise TypeError("multi-candidate iterations take float32 points")
+        lib = load()
+        stride, size = ctypes.c_size_t(), ctypes.c_size_t()
+        check(lib.ses_multi_state_stride(d, ctypes.byref(stride)), "ses_multi_state_stride")
+        check(lib.ses_multi_workspace_size(d, k, ctypes.byref(size)), "ses_multi_workspace_size")
+        self.pts, self.k, self.d, self.radii = pts, k, d, radii
+        self.stride = stride.value
+        self.states = torch.zeros(k * self.stride, dtype=torch.uint8, device=pts.device)
+        self.ws = torch.zeros(size.value, dtype=torch.uint8, device=pts.device)
+        init_ws = workspace(SES, n, d, pts.device)
+        for j in range(k):
+            state_init(SES, pts, self.state(j), init_ws, rules, delta, patience, stream)
+
+    def state(self, j):
+        return self.states[j * self.stride:(j + 1) * self.stride]
+
+    def step(self, alpha, eta_over_rho, out=None, stream=None):
+        """alpha, eta_over_rho: k float64 CUDA tensors; out: k records or None."""
+        n = self.pts.shape[0]
+        check(load().ses_multi_step(_vp(self.pts), _vp(self.radii), n, self.d, self.k, _vp(alpha),
+                                    _vp(eta_over_rho), _vp(self.states), _vp(self.ws), self.ws.numel(),
+                                    _stream(stream), _vp(out)), "ses_multi_step")
+
+    def read(self, j, stream=None):
+        return state_read(SES, self.d, self.state(j), stream, self.pts.device)
+
+
 # --- reverse sweep (SES) ----------------------------------------------------
 
 def backward_workspace_size(n, d, T):

@@ -141,3 +141,17 @@ def test_batch_search_validation_without_gpu(lib):
                                    ctypes.byref(done)) == 1
     tr = ctypes.c_int32()
     assert lib.ses_batch_autotune(2, fake, 1200, offs, n, d, None, fake, 1 << 30, None, None, None) == 1
+
+
+def test_multi_validation_without_gpu(lib):
+    size = ctypes.c_size_t()
+    assert lib.ses_multi_workspace_size(32, 3, ctypes.byref(size)) == 7
+    assert lib.ses_multi_workspace_size(65, 2, ctypes.byref(size)) == 7
+    assert lib.ses_multi_workspace_size(64, 8, ctypes.byref(size)) == 0 and size.value > 0
+    assert lib.ses_multi_state_stride(32, ctypes.byref(size)) == 0 and size.value % 256 == 0
+    fake = ctypes.c_void_p(1 << 20)
+    assert lib.ses_multi_step(fake, None, 1, 4, 2, fake, fake, fake, fake, 1 << 30, None, None) == 1
+    st = lib.ses_multi_step(fake, None, 10, 4, 2, fake, fake, ctypes.c_void_p((1 << 20) + 16), fake, 1 << 30,
+                            None, None)
+    assert st == 1 and b"misaligned" in lib.pdscp_last_error()
+    assert lib.ses_multi_step(fake, None, 10, 4, 2, fake, fake, fake, fake, 64, None, None) == 8
