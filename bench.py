@@ -322,13 +322,16 @@ class L2Flush:
         self.sink = self.half.sum()
 
 
+KERNEL_FILES = ("common.cuh", "dispatch.cuh", "ses_kernel.cuh", "kern_ses.cu")
+
+
 def kernel_rev():
-    """Hash of the kernel sources: a stored ncu traffic figure is used only
-    for the kernel revision it was measured on."""
+    """Hash of the sources of the SES iteration kernel: a stored ncu traffic
+    figure is used only for the kernel revision it was measured on."""
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2405_09157_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in KERNEL_FILES:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]

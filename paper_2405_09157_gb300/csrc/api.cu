@@ -47,18 +47,19 @@ constexpr int kRing = 4096;  // step records kept by the solves between polls
 size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t partials, grows, state, ring, dval, total;
+  size_t partials, grows, sink, state, ring, dval, total;
 };
 
 // Workspace: [counters][per-CTA partial rows (float)][per-group rows (double)]
-//            [solve state][step ring][D]
+//            [warm-up sink][solve state][step ring][D]
 Layout layout(int problem, int d) {
   Layout L;
   const int st = problem == PDSCP_SES ? ses_partial_stride(d) : svm_partial_stride(d);
   const size_t rows = (size_t)device_sm_count() * kMaxBlocksPerSM;
   L.partials = kHeadBytes;
   L.grows = L.partials + round256(rows * (size_t)st * sizeof(float));
-  L.state = L.grows + round256((size_t)kMaxGroups * st * sizeof(float2));
+  L.sink = L.grows + round256((size_t)kMaxGroups * st * sizeof(float2));
+  L.state = L.sink + round256(warm_sink_bytes(d));
   L.ring = L.state + round256(state_bytes(d));
   L.dval = L.ring + round256((size_t)kRing * sizeof(pdscp_step_out));
   L.total = L.dval + 256;
@@ -143,10 +144,11 @@ pdscp_status do_step(int problem, const void* pts, int dtype, const float* radii
   cudaError_t e;
   if (problem == PDSCP_SES) {
     SesParams p{pts, radii, n, d, eval_only, alpha, eta_over_rho, state, partials, grows, counter, 0, out, 1, nullptr,
-                tape};
+                tape, reinterpret_cast<unsigned char*>(ws) + L.sink};
     e = launch_ses(p, dtype, vec, stream);
   } else {
-    SvmParams p{pts, labels, n, d, eval_only, alpha, eta_over_rho, D, state, partials, grows, counter, 0, out, nullptr};
+    SvmParams p{pts, labels, n, d, eval_only, alpha, eta_over_rho, D, state, partials, grows, counter, 0, out, nullptr,
+                reinterpret_cast<unsigned char*>(ws) + L.sink};
     e = launch_svm(p, dtype, vec, stream);
   }
   if (e != cudaSuccess) return cuda_fail(e, "mwu_step launch");
@@ -411,10 +413,11 @@ pdscp_status mwu_shard_partial(int32_t problem, const void* pts, int32_t dtype, 
   cudaError_t e;
   if (problem == PDSCP_SES) {
     SesParams p{pts, radii, n, d, eval_only, alpha, eta_over_rho, st_rw, partials, grows, counter, 0, nullptr,
-                holds_first ? 1 : 0, row, nullptr};
+                holds_first ? 1 : 0, row, nullptr, nullptr};
     e = launch_ses(p, dtype, vec, (cudaStream_t)stream);
   } else {
-    SvmParams p{pts, labels, n, d, eval_only, alpha, eta_over_rho, D, st_rw, partials, grows, counter, 0, nullptr, row};
+    SvmParams p{pts, labels, n, d, eval_only, alpha, eta_over_rho, D, st_rw, partials, grows, counter, 0, nullptr, row,
+                nullptr};
     e = launch_svm(p, dtype, vec, (cudaStream_t)stream);
   }
   if (e != cudaSuccess) return cuda_fail(e, "mwu_shard_partial launch");

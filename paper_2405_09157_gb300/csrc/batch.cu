@@ -120,14 +120,18 @@ pdscp_status batch_setup(int32_t num, const float* pts_dev, int64_t pts_len, con
   return PDSCP_OK;
 }
 
+// One iteration of every instance; with a search, then every instance's search step.
 cudaError_t launch_batch(const float* pts, const double* alpha, const double* eor, unsigned char* ws,
-                         pdscp_step_out* out, BatchSearch* search, cudaStream_t s) {
+                         pdscp_step_out* out, BatchSearch* search, cudaStream_t s, int num = 0) {
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ses_batch_kernel, kBatchBlock, 0) != cudaSuccess || occ < 1)
     occ = 1;
   const int grid = device_sm_count() * occ;
   BatchParams p{pts, alpha, eor, ws, out, search};
   ses_batch_kernel<<<grid, kBatchBlock, 0, s>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !search) return e;
+  ses_batch_search_kernel<<<(num + 7) / 8, 256, 0, s>>>(pts, ws, num);
   return cudaGetLastError();
 }
 
@@ -236,7 +240,7 @@ pdscp_status ses_batch_solve_run(int32_t num, const float* pts_dev, void* ws_dev
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     for (int k = 0; k < launches_per_poll && e == cudaSuccess; ++k)
-      e = launch_batch(pts_dev, nullptr, nullptr, ws, nullptr, search, cs);
+      e = launch_batch(pts_dev, nullptr, nullptr, ws, nullptr, search, cs, num);
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
     if (e == cudaSuccess) e = e2;
   }
@@ -299,9 +303,9 @@ pdscp_status ses_batch_autotune(int32_t num, const float* pts_dev, int64_t pts_l
     unsigned char* ws = reinterpret_cast<unsigned char*>(ws_dev);
     BatchSearch* search = reinterpret_cast<BatchSearch*>(ws + bh.search_off);
     // the bounds pass and one iteration untimed, then four timed iterations
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_batch(pts_dev, nullptr, nullptr, ws, nullptr, search, s);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_batch(pts_dev, nullptr, nullptr, ws, nullptr, search, s, num);
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = launch_batch(pts_dev, nullptr, nullptr, ws, nullptr, search, s);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = launch_batch(pts_dev, nullptr, nullptr, ws, nullptr, search, s, num);
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.f;

@@ -191,8 +191,12 @@ __device__ void batch_tile(const float* pts, int d, int64_t r0, int64_t r1, cons
 // (the decisions of ses_solve: Sec. 3's update of [L, U] from the FTP's
 // outcome, Sec. 5's early exits, the primal lower bound of Eq.
 // primal_construction as a certificate) and starts its next alpha-FTP.
-__device__ void batch_search_update(BatchSearch* sr, void* state, const float* v1, int d, int64_t n,
-                                    const BatchSolveOpts& o, unsigned int* done_counter) {
+// Runs in its own kernel after each iteration launch (ses_batch_search_kernel):
+// called from the streaming kernel, its FP64 bookkeeping would raise that
+// kernel's register count and lower its occupancy.
+static __device__ __forceinline__ void batch_search_update(BatchSearch* sr, void* state, const float* v1, int d,
+                                                        int64_t n, const BatchSolveOpts& o,
+                                                        unsigned int* done_counter) {
   const int lane = threadIdx.x & 31;
   __syncwarp();
   StateHdr* hdr = reinterpret_cast<StateHdr*>(state);
@@ -421,10 +425,7 @@ __global__ void __launch_bounds__(kBatchBlock) ses_batch_kernel(BatchParams p) {
         if (tid < 32) {
           ses_finish_warp(raw, s_mean, s_v1, *reinterpret_cast<const StateHdr*>(s_hdr), state, d, alpha_d, 0.0,
                           eor_d, eval ? 1 : 0, p.out ? p.out + tl.inst : nullptr);
-          if (p.search)
-            batch_search_update(p.search + tl.inst, state, pts, d, in.n,
-                                *reinterpret_cast<const BatchSolveOpts*>(p.ws + kBatchOptsOff),
-                                reinterpret_cast<unsigned int*>(p.ws) + 2);
+
         }
       }
     }
@@ -440,6 +441,20 @@ __global__ void __launch_bounds__(kBatchBlock) ses_batch_kernel(BatchParams p) {
       __threadfence();
     }
   }
+}
+
+// The search step of every instance still searching, one warp per instance,
+// after the launch that ran the instance's iteration (or evaluation pass).
+__global__ void __launch_bounds__(256) ses_batch_search_kernel(const float* pts, unsigned char* ws, int num) {
+  const int inst = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (inst >= num) return;
+  const BatchHeader* bh = reinterpret_cast<const BatchHeader*>(ws + 256);
+  BatchSearch* sr = reinterpret_cast<BatchSearch*>(ws + bh->search_off) + inst;
+  if (sr->phase == kPhaseDone) return;
+  const BatchInst in = reinterpret_cast<const BatchInst*>(ws + bh->inst_off)[inst];
+  batch_search_update(sr, ws + in.state_off, pts + in.pt_off, in.d, in.n,
+                      *reinterpret_cast<const BatchSolveOpts*>(ws + kBatchOptsOff),
+                      reinterpret_cast<unsigned int*>(ws) + 2);
 }
 
 // Fresh alpha-FTP states for every instance (t = 0, mean = v_1); one CTA per instance.

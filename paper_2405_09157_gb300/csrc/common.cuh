@@ -74,6 +74,32 @@ __host__ __device__ inline int ses_partial_stride(int d) { return 4 + dpad4(d); 
 // One entry of the forward tape a reverse sweep reads (floats): S, |g|, k/sqrt2,
 // the exponent shift, then the mean the pass read (dp) and g (dp).
 __host__ __device__ inline int ses_tape_stride(int d) { return 4 + 2 * dpad4(d); }
+
+// Sink of the warm-up run of a finish (a scratch state, step record and tape
+// entry that the run writes instead of the real ones): its size and parts.
+__host__ __device__ inline size_t warm_sink_bytes(int d) {
+  return ((state_bytes(d) + 255) & ~(size_t)255) + 256 + (size_t)ses_tape_stride(d) * sizeof(float);
+}
+__device__ __forceinline__ pdscp_step_out* warm_sink_out(unsigned char* sink, int d) {
+  return reinterpret_cast<pdscp_step_out*>(sink + ((state_bytes(d) + 255) & ~(size_t)255));
+}
+__device__ __forceinline__ float* warm_sink_tape(unsigned char* sink, int d) {
+  return reinterpret_cast<float*>(sink + ((state_bytes(d) + 255) & ~(size_t)255) + 256);
+}
+
+// Warp split of a pass: with warm-up warps (the last warp of each CTA, when a
+// sink is given), the other warps take their share of the points.
+struct WarpSplit {
+  bool warm;
+  int64_t gw, nwarps;
+  __device__ WarpSplit(const void* sink, int nw, int warp) {
+    const bool on = sink != nullptr && nw > 1;
+    warm = on && warp == nw - 1;
+    const int nws = on ? nw - 1 : nw;
+    nwarps = (int64_t)gridDim.x * nws;
+    gw = (int64_t)blockIdx.x * nws + warp;
+  }
+};
 __host__ __device__ inline int svm_partial_stride(int d) { return 4 + 2 * dpad4(d); }
 
 // ---------------------------------------------------------------------------

@@ -48,7 +48,20 @@ struct SesParams {
   int64_t first;         // first row of the pass: 1 when row 0 is v_1 (the easy cone), else 0
   float2* row_out;       // non-null: a shard's pass; write the column totals here, no finish
   float* tape;           // non-null: the finish records entry t (ses_tape_stride floats) for a reverse sweep
+  unsigned char* sink;   // non-null: one warp warms the finish's code path early, writing here (warm_sink_bytes)
 };
+
+// The finish runs once per launch, in one warp, after every other warp is
+// done; its instructions are then cold (a flushed or streamed-over L2 holds
+// none of them) and fetching them from HBM costs more than its arithmetic.
+// The last warp of every CTA streams no points and instead runs the same
+// code at the start of the launch, on whatever shared memory holds, writing
+// only to the sink: whichever CTA finishes then finds the code in its SM's
+// instruction cache.
+template <typename T>
+__device__ void ses_finish_warm(const SesParams& p, unsigned char* smem_raw);
+
+
 
 template <typename T>
 __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw);
@@ -89,8 +102,10 @@ __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
   float S = 0.f, W = 0.f, maxd = -INFINITY;
 
   const T* pts = reinterpret_cast<const T*>(p.pts);
-  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
-  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
+  const WarpSplit ws(p.sink, kWarps, warp);
+  if (ws.warm) ses_finish_warm<T>(p, smem_raw);
+  const int64_t nwarps = ws.nwarps;
+  const int64_t gw = ws.warm ? (p.n + nwarps * (PPW * U)) : ws.gw;  // the warm-up warp streams nothing
   for (int64_t base = gw * (PPW * U); base < p.n; base += nwarps * (PPW * U)) {
     float x[U][NCH][VW];
 #pragma unroll
@@ -334,6 +349,18 @@ static __device__ __noinline__ void ses_finish_warp(const float2* raw, const dou
 }
 
 template <typename T>
+__device__ __noinline__ void ses_finish_warm(const SesParams& p, unsigned char* smem_raw) {
+  const int d = p.d;
+  const float2* raw = reinterpret_cast<const float2*>(smem_raw);
+  const double* s_mean = reinterpret_cast<const double*>(smem_raw) + ses_partial_stride(d);
+  const double* s_v1 = s_mean + dpad4(d);
+  StateHdr h;
+  memset(&h, 0, sizeof(h));
+  ses_finish_warp(raw, s_mean, s_v1, h, p.sink, d, p.alpha, 0.0, p.eta_over_rho, p.eval_only,
+                  warm_sink_out(p.sink, d), p.tape ? warm_sink_tape(p.sink, d) : nullptr);
+}
+
+template <typename T>
 __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw) {
   __shared__ float2 s_scr[kMaxBlock];
   __shared__ __align__(16) double s_hdr[sizeof(StateHdr) / 8];
@@ -413,13 +440,15 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
   const bool owner = (gl % GS::SHARE) == 0;
   const bool has_chunk = gl < nch;
   const T* pts = reinterpret_cast<const T*>(p.pts);
-  const int64_t nwarps = (int64_t)gridDim.x * NW;
-  const int64_t gw = (int64_t)blockIdx.x * NW + warp;
+  const WarpSplit wsp(p.sink, NW, warp);
+  if (wsp.warm) ses_finish_warm<T>(p, smem_raw);
+  const int64_t nwarps = wsp.nwarps;
+  const int64_t gw = wsp.gw;
   constexpr int ROUND = PPW * NI;
   // each warp streams one contiguous range of points, equal up to 8 points
   // (balanced bytes per warp; starts on 8-point boundaries)
   auto split = [&](int64_t w) { return w >= nwarps ? p.n : ((w * p.n / nwarps) & ~(int64_t)7); };
-  const int64_t lo = split(gw), hi = split(gw + 1);
+  const int64_t lo = wsp.warm ? p.n : split(gw), hi = wsp.warm ? p.n : split(gw + 1);
   // the first round's point loads do not depend on the state: issue them first
   float x[NI][VW];
   auto load_round = [&](int64_t base) {

@@ -42,7 +42,11 @@ struct SvmParams {
   int single;            // completion stages all partial rows in shared memory (single_level)
   pdscp_step_out* out;
   float2* row_out;       // non-null: a shard's pass; write the column totals here, no finish
+  unsigned char* sink;   // non-null: warm-up warps run the finish's code early, writing here
 };
+
+// Warm-up of the finish's code path in every CTA (see ses_finish_warm).
+static __device__ __noinline__ void svm_finish_warm(const SvmParams& p, unsigned char* smem_raw);
 
 template <typename T>
 __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw);
@@ -81,8 +85,10 @@ __global__ void __launch_bounds__(kBlock) svm_iter_kernel(SvmParams p) {
   float SP = 0.f, SQ = 0.f, minP = INFINITY, maxQ = -INFINITY;
 
   const T* pts = reinterpret_cast<const T*>(p.pts);
-  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
-  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
+  const WarpSplit ws(p.sink, kWarps, warp);
+  if (ws.warm) svm_finish_warm(p, smem_raw);
+  const int64_t nwarps = ws.nwarps;
+  const int64_t gw = ws.warm ? (p.n + nwarps * (PPW * U)) : ws.gw;  // the warm-up warp streams nothing
   for (int64_t base = gw * (PPW * U); base < p.n; base += nwarps * (PPW * U)) {
     float x[U][NCH][VW];
 #pragma unroll
@@ -326,6 +332,15 @@ static __device__ __noinline__ void svm_finish_warp(const float2* raw, const dou
   }
 }
 
+static __device__ __noinline__ void svm_finish_warm(const SvmParams& p, unsigned char* smem_raw) {
+  const int d = p.d;
+  const float2* raw = reinterpret_cast<const float2*>(smem_raw);
+  const double* s_mean = reinterpret_cast<const double*>(smem_raw) + svm_partial_stride(d);
+  StateHdr h;
+  memset(&h, 0, sizeof(h));
+  svm_finish_warp(raw, s_mean, h, p.sink, d, p.alpha, p.D, p.eta_over_rho, p.eval_only, warm_sink_out(p.sink, d));
+}
+
 // O(d) finish of one SVM iteration. Every CTA calls it after writing its
 // partial row [S_P, S_Q, minP, maxQ, Z_P (dp), Z_Q (dp)]; the completion
 // elects one CTA, which reduces the rows and hands the totals to warp 0.
@@ -390,13 +405,15 @@ __global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
   const bool owner = (gl % GS::SHARE) == 0;
   const bool has_chunk = gl < nch;
   const T* pts = reinterpret_cast<const T*>(p.pts);
-  const int64_t nwarps = (int64_t)gridDim.x * NW;
-  const int64_t gw = (int64_t)blockIdx.x * NW + warp;
+  const WarpSplit wsp(p.sink, NW, warp);
+  if (wsp.warm) svm_finish_warm(p, smem_raw);
+  const int64_t nwarps = wsp.nwarps;
+  const int64_t gw = wsp.gw;
   constexpr int ROUND = PPW * NI;
   // each warp streams one contiguous range of points, equal up to 8 points
   // (balanced bytes per warp; starts on 8-point boundaries)
   auto split = [&](int64_t w) { return w >= nwarps ? p.n : ((w * p.n / nwarps) & ~(int64_t)7); };
-  const int64_t lo = split(gw), hi = split(gw + 1);
+  const int64_t lo = wsp.warm ? p.n : split(gw), hi = wsp.warm ? p.n : split(gw + 1);
   // the first round's point loads do not depend on the state: issue them first
   float x[NI][VW];
   auto load_round = [&](int64_t base) {
