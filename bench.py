@@ -583,9 +583,39 @@ def backward_variant(dev, n=100_000, d=64, T=2000):
     fwd = e0.elapsed_time(e1)
     rev = (total - fwd) / T
     b = 12 * n * d
-    return {"workload": f"SES n={n} d={d} T={T} fp32, alpha = D", "ms_total": total, "ms_forward": fwd,
-            "ms_per_reverse_step": rev, "GBps_reverse": b / rev / 1e6,
-            "note": "points and gradient (51 MB) are L2-resident across passes: GB/s is not an HBM figure"}
+    res = {"workload": f"SES n={n} d={d} T={T} fp32, alpha = D", "ms_total": total, "ms_forward": fwd,
+           "ms_per_reverse_step": rev, "GBps_reverse": b / rev / 1e6,
+           "note": "points and gradient (51 MB) are L2-resident across passes: GB/s is not an HBM figure"}
+    # SVM: the margin of the minimisation alpha-FTP, two clusters as the SVM workload (n/2 per class)
+    X32, y = datagen.svm_clusters(n // 2, n // 2, d, seed=0)
+    X = torch.from_numpy(X32).to(dev)
+    lab = torch.from_numpy(y).to(dev)
+    Dv = float(api.bounds(_ffi.SVM, X).item())
+    eor = 0.5 / (2.0 * Dv)
+    alpha = 0.05 * Dv  # below OPT: the ORACLE never separates
+    ws = torch.empty(api.backward_workspace_size(n, d, T, _ffi.SVM), dtype=torch.uint8, device=dev)
+    api.mwu_backward(X, alpha, eor, T, ws=ws, out=out, problem=_ffi.SVM, labels=lab, D=Dv)  # warm-up
+    torch.cuda.synchronize()
+    e0.record()
+    api.mwu_backward(X, alpha, eor, T, ws=ws, out=out, problem=_ffi.SVM, labels=lab, D=Dv)
+    e1.record()
+    torch.cuda.synchronize()
+    total = e0.elapsed_time(e1)
+    rec = api.decode_steps(out)[0]
+    if not (rec["t"] == T and rec["status"] == 0):
+        raise RuntimeError("the SVM reverse sweep did not run every iteration")
+    m = api.MWU(_ffi.SVM, X, labels=lab)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(T):
+        m.step(alpha, eor, D=Dv)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd = e0.elapsed_time(e1)
+    rev = (total - fwd) / T
+    res["svm"] = {"workload": f"SVM n={n} d={d} T={T} fp32, alpha = 0.05 D", "ms_total": total, "ms_forward": fwd,
+                  "ms_per_reverse_step": rev, "GBps_reverse": (12 * n * d + n) / rev / 1e6}
+    return res
 
 
 def time_to_eps(pts):

@@ -405,28 +405,35 @@ pdscp_status ses_multi_step(const float* pts_dev, const float* radii_dev, int64_
                             pdscp_step_out* out_dev);
 
 /*
- * Reverse-mode sweep through T unrolled iterations of the SES alpha-FTP at
- * fixed alpha and eta/rho (Sec. 3, Eq. implement, ORACLE Eq. ses_oracle): the
- * gradient of L = seed * f(ubar^T), f(c) = max_i ||c - v_i|| + gamma_i the
- * radius of Sec. 5, with respect to the points. The sweep first runs the T
- * forward iterations from t = 0 (as mwu_state_init + T mwu_step calls with
- * rules PDSCP_RULES_NONE), recording O(d) values per iteration (the mean, g,
- * the normaliser, |g|, the exponent scale and shift) in the workspace, then
- * one streaming pass per iteration in reverse order, each adding that
- * iteration's dL/dv_i to grad_dev and summing the adjoint of the mean.
- * If the ORACLE separates at step t_f < T, the sweep differentiates the t_f
- * iterations taken. f is a maximum: the row attaining it (smallest index on
- * ties) receives the subgradient; radii are constants.
- *   problem: PDSCP_SES (SVM returns PDSCP_ERR_NOT_IMPLEMENTED); dtype:
- *     PDSCP_F32 (BF16 returns PDSCP_ERR_NOT_IMPLEMENTED); labels_dev, D: unused.
+ * Reverse-mode sweep through T unrolled iterations of the alpha-FTP at fixed
+ * alpha and eta/rho (Sec. 3, Eq. implement / min_implement, ORACLE Eq.
+ * ses_oracle / svm_oracle): the gradient, with respect to the points, of
+ *   SES: L = seed * f(ubar^T), f(c) = max_i ||c - v_i|| + gamma_i (the radius of Sec. 5);
+ *   SVM: L = seed * f(wbar^T), f(w) = max{(min_P x^T w - max_Q x^T w)/||w||, 0} (the margin of Sec. 5).
+ * The sweep first runs the T forward iterations from t = 0 (as mwu_state_init
+ * + T mwu_step calls with rules PDSCP_RULES_NONE), recording O(d) values per
+ * iteration in the workspace (SES: the mean, g, the normaliser, |g|, the
+ * exponent scale and shift; SVM: the mean, z, the normaliser, |z|, k, the
+ * shift, s1bar, s2bar), then one streaming pass per iteration in reverse
+ * order, each adding that iteration's dL/dx_i to grad_dev and summing the
+ * adjoint of the mean. If the ORACLE separates at step t_f < T, the sweep
+ * differentiates the t_f iterations taken. f is a maximum (SES) or a margin
+ * between a minimum and a maximum (SVM): the rows attaining them (smallest
+ * index on ties) receive the subgradient; a clipped SVM margin has gradient 0.
+ * Radii, D and alpha are constants; for SVM, s_1 and s_2 are piecewise
+ * constant in the points and pass no gradient.
+ *   problem: PDSCP_SES or PDSCP_SVM; dtype: PDSCP_F32 (BF16 returns
+ *     PDSCP_ERR_NOT_IMPLEMENTED); radii_dev (SES, may be NULL), labels_dev and
+ *     D (SVM) as for mwu_step.
  *   seed_dev: dL/df, one device double (NULL: 1).
  *   ws_dev: mwu_backward_workspace_size bytes (256-byte aligned); on return
  *     it holds the forward's final state and tape (caller-owned).
  *   grad_dev: n x d float32, row-major, overwritten (16-byte alignment with
  *     d % 4 == 0 takes the vector path).
- *   out_dev (may be NULL): one pdscp_step_out: objective = upper_bound =
- *     f(ubar^T), t = iterations taken, oracle_value/lower_bound/outcome of
- *     the forward, k = the index of the row attaining f.
+ *   out_dev (may be NULL): one pdscp_step_out: objective = f at the final
+ *     mean, t = iterations taken, oracle_value/outcome of the forward,
+ *     k = the index of the row attaining f (SES) or the minimum over P (SVM;
+ *     -1 when the margin is clipped).
  * Asynchronous on `stream` (2T + 3 launches); errors as mwu_step.
  */
 pdscp_status mwu_backward_workspace_size(int32_t problem, int64_t n, int32_t d, int64_t T,

@@ -169,25 +169,27 @@ class MultiMWU:
 
 # --- reverse sweep (SES) ----------------------------------------------------
 
-def backward_workspace_size(n, d, T):
+def backward_workspace_size(n, d, T, problem=SES):
     out = ctypes.c_size_t()
-    check(load().mwu_backward_workspace_size(SES, n, d, T, ctypes.byref(out)), "mwu_backward_workspace_size")
+    check(load().mwu_backward_workspace_size(problem, n, d, T, ctypes.byref(out)), "mwu_backward_workspace_size")
     return out.value
 
 
-def mwu_backward(pts, alpha, eta_over_rho, T, radii=None, seed=None, ws=None, out=None, stream=None):
-    """Gradient of seed * f(ubar^T) (SES radius after T alpha-FTP iterations
-    from t = 0 at fixed alpha, eta/rho) with respect to the float32 points.
-    seed: one-element float64 CUDA tensor or None (1). Returns (grad, ws)."""
+def mwu_backward(pts, alpha, eta_over_rho, T, radii=None, seed=None, ws=None, out=None, stream=None,
+                 problem=SES, labels=None, D=0.0):
+    """Gradient of seed * f at the final mean after T alpha-FTP iterations
+    from t = 0 at fixed alpha, eta/rho (SES: the radius; SVM: the margin, with
+    labels and D) with respect to the float32 points. seed: one-element
+    float64 CUDA tensor or None (1). Returns (grad, ws)."""
     n, d, dt = _points(pts)
     if ws is None:
-        ws = torch.empty(backward_workspace_size(n, d, T), dtype=torch.uint8, device=pts.device)
+        ws = torch.empty(backward_workspace_size(n, d, T, problem), dtype=torch.uint8, device=pts.device)
     grad = torch.empty((n, d), dtype=torch.float32, device=pts.device)
     if seed is not None:
         seed = seed.to(device=pts.device, dtype=torch.float64).contiguous()
-    check(load().mwu_backward(SES, _vp(pts), dt, _vp(radii), None, n, d, float(alpha), float(eta_over_rho), 0.0,
-                              int(T), _vp(seed), _vp(ws), ws.numel(), _stream(stream), _vp(grad), _vp(out)),
-          "mwu_backward")
+    check(load().mwu_backward(problem, _vp(pts), dt, _vp(radii), _vp(labels), n, d, float(alpha),
+                              float(eta_over_rho), float(D), int(T), _vp(seed), _vp(ws), ws.numel(),
+                              _stream(stream), _vp(grad), _vp(out)), "mwu_backward")
     return grad, ws
 
 
@@ -218,6 +220,36 @@ class SesUnrolledRadius(torch.autograd.Function):
 def ses_unrolled_radius(pts, alpha, eta_over_rho, T, radii=None):
     """Differentiable SES radius after T alpha-FTP iterations (float64 0-dim tensor)."""
     return SesUnrolledRadius.apply(pts, alpha, eta_over_rho, T, radii)
+
+
+class SvmUnrolledMargin(torch.autograd.Function):
+    """f(wbar^T) of the SVM alpha-FTP (the margin of Sec. 5) as a differentiable
+    function of the points: forward = T mwu_step iterations and one evaluation
+    pass; backward = mwu_backward seeded with the incoming gradient."""
+
+    @staticmethod
+    def forward(ctx, pts, labels, alpha, eta_over_rho, T, D):
+        m = MWU(SVM, pts.detach(), labels=labels)
+        for _ in range(T):
+            m.step(alpha, eta_over_rho, D=D)
+        rec = new_steps(1, pts.device)
+        m.step(alpha, eta_over_rho, out=rec, D=D, eval_only=True)
+        ctx.save_for_backward(pts)
+        ctx.args = (labels, alpha, eta_over_rho, T, D)
+        return rec.view(torch.float64)[0, 1].clone()  # the record's objective: the margin at the final mean
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (pts,) = ctx.saved_tensors
+        labels, alpha, eta_over_rho, T, D = ctx.args
+        grad, _ = mwu_backward(pts.detach(), alpha, eta_over_rho, T, seed=grad_out.reshape(1), problem=SVM,
+                               labels=labels, D=D)
+        return grad, None, None, None, None, None
+
+
+def svm_unrolled_margin(pts, labels, alpha, eta_over_rho, T, D):
+    """Differentiable SVM margin after T alpha-FTP iterations (float64 0-dim tensor)."""
+    return SvmUnrolledMargin.apply(pts, labels, alpha, eta_over_rho, T, D)
 
 
 # --- row-sharded iteration -------------------------------------------------

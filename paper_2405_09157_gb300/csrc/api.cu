@@ -23,6 +23,8 @@ cudaError_t launch_ses_merge(const SesMergeParams& m, int dtype, cudaStream_t st
 cudaError_t launch_svm_merge(const SvmMergeParams& m, cudaStream_t stream);
 cudaError_t launch_ses_bwd_seed(const BwdParams& p, bool vec, cudaStream_t stream);
 cudaError_t launch_ses_bwd_step(const BwdParams& p, bool vec, cudaStream_t stream);
+cudaError_t launch_svm_bwd_seed(const BwdParams& p, bool vec, cudaStream_t stream);
+cudaError_t launch_svm_bwd_step(const BwdParams& p, bool vec, cudaStream_t stream);
 
 namespace {
 
@@ -71,16 +73,16 @@ Layout layout(int problem, int d) {
 struct BwdLayout {
   size_t state, tape, bw, cval, cidx, total;
 };
-BwdLayout bwd_layout(int d, int64_t T) {
-  const Layout L = layout(PDSCP_SES, d);
+BwdLayout bwd_layout(int problem, int d, int64_t T) {
+  const Layout L = layout(problem, d);
   const size_t rows = (size_t)device_sm_count() * kMaxBlocksPerSM;
   BwdLayout B;
   B.state = L.state;
   B.tape = B.state + round256(state_bytes(d));
-  B.bw = B.tape + round256((size_t)T * ses_tape_stride(d) * sizeof(float));
+  B.bw = B.tape + round256((size_t)T * svm_tape_stride(d) * sizeof(float));  // the larger of the two entries
   B.cval = B.bw + round256(bwd_scratch_bytes(d));
-  B.cidx = B.cval + round256(rows * sizeof(float));
-  B.total = B.cidx + round256(rows * sizeof(long long));
+  B.cidx = B.cval + round256(2 * rows * sizeof(float));  // SVM: two candidates per CTA
+  B.total = B.cidx + round256(2 * rows * sizeof(long long));
   return B;
 }
 
@@ -148,7 +150,7 @@ pdscp_status do_step(int problem, const void* pts, int dtype, const float* radii
     e = launch_ses(p, dtype, vec, stream);
   } else {
     SvmParams p{pts, labels, n, d, eval_only, alpha, eta_over_rho, D, state, partials, grows, counter, 0, out, nullptr,
-                reinterpret_cast<unsigned char*>(ws) + L.sink};
+                reinterpret_cast<unsigned char*>(ws) + L.sink, tape};
     e = launch_svm(p, dtype, vec, stream);
   }
   if (e != cudaSuccess) return cuda_fail(e, "mwu_step launch");
@@ -417,7 +419,7 @@ pdscp_status mwu_shard_partial(int32_t problem, const void* pts, int32_t dtype, 
     e = launch_ses(p, dtype, vec, (cudaStream_t)stream);
   } else {
     SvmParams p{pts, labels, n, d, eval_only, alpha, eta_over_rho, D, st_rw, partials, grows, counter, 0, nullptr, row,
-                nullptr};
+                nullptr, nullptr};
     e = launch_svm(p, dtype, vec, (cudaStream_t)stream);
   }
   if (e != cudaSuccess) return cuda_fail(e, "mwu_shard_partial launch");
@@ -454,11 +456,11 @@ pdscp_status mwu_shard_finish(int32_t problem, const float* rows, int32_t ranks,
 // --- reverse sweep (SES) -------------------------------------------------------
 
 pdscp_status mwu_backward_workspace_size(int32_t problem, int64_t n, int32_t d, int64_t T, size_t* bytes) {
-  if (problem != PDSCP_SES) return fail(PDSCP_ERR_NOT_IMPLEMENTED, "the reverse sweep is built for SES only");
+  if (problem != PDSCP_SES && problem != PDSCP_SVM) return fail(PDSCP_ERR_INVALID_ARG, "unknown problem %d", problem);
   if (d < 1 || d > PDSCP_MAX_D) return fail(PDSCP_ERR_NOT_IMPLEMENTED, "d=%d outside [1, %d]", d, PDSCP_MAX_D);
   if (n < 2 || T < 1) return fail(PDSCP_ERR_INVALID_ARG, "need n >= 2 and T >= 1");
   if (!bytes) return fail(PDSCP_ERR_INVALID_ARG, "bytes pointer is null");
-  *bytes = bwd_layout(d, T).total;
+  *bytes = bwd_layout(problem, d, T).total;
   return PDSCP_OK;
 }
 
@@ -466,11 +468,8 @@ pdscp_status mwu_backward(int32_t problem, const void* pts, int32_t dtype, const
                           int64_t n, int32_t d, double alpha, double eta_over_rho, double D, int64_t T,
                           const double* seed, void* ws, size_t ws_bytes, pdscp_stream stream, float* grad,
                           pdscp_step_out* out) {
-  (void)labels;
-  (void)D;
   pdscp_status st = check_common(problem, pts, dtype, n, d);
   if (st != PDSCP_OK) return st;
-  if (problem != PDSCP_SES) return fail(PDSCP_ERR_NOT_IMPLEMENTED, "the reverse sweep is built for SES only");
   if (dtype != PDSCP_F32) return fail(PDSCP_ERR_NOT_IMPLEMENTED, "the reverse sweep takes float32 points");
   if (T < 1) return fail(PDSCP_ERR_INVALID_ARG, "T must be >= 1");
   if (!ws || !grad) return fail(PDSCP_ERR_INVALID_ARG, "workspace or gradient pointer is null");
@@ -480,26 +479,33 @@ pdscp_status mwu_backward(int32_t problem, const void* pts, int32_t dtype, const
   if (seed && !aligned(seed, 8)) return fail(PDSCP_ERR_INVALID_ARG, "seed pointer not 8-byte aligned");
   if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(PDSCP_ERR_INVALID_ARG, "alpha must be finite and > 0");
   if (!(eta_over_rho >= 0.0) || !std::isfinite(eta_over_rho)) return fail(PDSCP_ERR_INVALID_ARG, "eta/rho must be finite and >= 0");
-  const BwdLayout B = bwd_layout(d, T);
+  if (problem == PDSCP_SVM) {
+    if (!labels) return fail(PDSCP_ERR_INVALID_ARG, "SVM needs labels");
+    if (!(D > 0.0) || !std::isfinite(D)) return fail(PDSCP_ERR_INVALID_ARG, "SVM needs D > 0 (the largest point norm)");
+  }
+  const BwdLayout B = bwd_layout(problem, d, T);
   if (ws_bytes < B.total) return fail(PDSCP_ERR_WORKSPACE, "workspace too small for the reverse sweep");
   cudaStream_t s = (cudaStream_t)stream;
   char* w = reinterpret_cast<char*>(ws);
   void* state = w + B.state;
   float* tape = reinterpret_cast<float*>(w + B.tape);
   unsigned int* counter = reinterpret_cast<unsigned int*>(ws);
-  cudaError_t e = launch_state_init(PDSCP_SES, pts, dtype, d, PDSCP_RULES_NONE, 1e-4, 10, state, counter, s);
+  cudaError_t e = launch_state_init(problem, pts, dtype, d, PDSCP_RULES_NONE, 1e-4, 10, state, counter, s);
   if (e != cudaSuccess) return cuda_fail(e, "state init launch");
   e = cudaMemsetAsync(grad, 0, (size_t)n * d * sizeof(float), s);
   if (e != cudaSuccess) return cuda_fail(e, "gradient clear");
   // forward, recording the tape (a stopped alpha-FTP leaves the later launches idle)
+  const float* rad = problem == PDSCP_SES ? radii : nullptr;
+  const int8_t* lab = problem == PDSCP_SVM ? labels : nullptr;
   for (int64_t t = 0; t < T; ++t) {
-    st = do_step(PDSCP_SES, pts, dtype, radii, nullptr, n, d, alpha, eta_over_rho, 0.0, 0, state, ws, s, nullptr, tape);
+    st = do_step(problem, pts, dtype, rad, lab, n, d, alpha, eta_over_rho, D, 0, state, ws, s, nullptr, tape);
     if (st != PDSCP_OK) return st;
   }
-  const Layout L = layout(PDSCP_SES, d);
+  const Layout L = layout(problem, d);
   BwdParams bp{};
   bp.pts = reinterpret_cast<const float*>(pts);
-  bp.radii = radii;
+  bp.radii = rad;
+  bp.labels = lab;
   bp.n = n;
   bp.d = d;
   bp.alpha = alpha;
@@ -517,12 +523,22 @@ pdscp_status mwu_backward(int32_t problem, const void* pts, int32_t dtype, const
   bp.seed = seed;
   bp.out = out;
   const bool vec = use_vec(pts, dtype, d) && aligned(grad, 16);
-  e = launch_ses_bwd_seed(bp, vec, s);
-  if (e != cudaSuccess) return cuda_fail(e, "reverse-sweep seed launch");
-  for (int64_t k = T - 1; k >= 1; --k) {
-    bp.s = k;
-    e = launch_ses_bwd_step(bp, vec, s);
-    if (e != cudaSuccess) return cuda_fail(e, "reverse-step launch");
+  if (problem == PDSCP_SES) {
+    e = launch_ses_bwd_seed(bp, vec, s);
+    if (e != cudaSuccess) return cuda_fail(e, "reverse-sweep seed launch");
+    for (int64_t k = T - 1; k >= 1; --k) {  // step 0 only hands dL/dubar^1 to v_1 (done by step 1's bookkeeping)
+      bp.s = k;
+      e = launch_ses_bwd_step(bp, vec, s);
+      if (e != cudaSuccess) return cuda_fail(e, "reverse-step launch");
+    }
+  } else {
+    e = launch_svm_bwd_seed(bp, vec, s);
+    if (e != cudaSuccess) return cuda_fail(e, "reverse-sweep seed launch");
+    for (int64_t k = T - 1; k >= 0; --k) {
+      bp.s = k;
+      e = launch_svm_bwd_step(bp, vec, s);
+      if (e != cudaSuccess) return cuda_fail(e, "reverse-step launch");
+    }
   }
   return PDSCP_OK;
 }

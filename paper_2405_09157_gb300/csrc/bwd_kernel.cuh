@@ -61,6 +61,7 @@ struct BwdParams {
   int ncand;
   const double* seed;    // dL/df (may be null: 1)
   pdscp_step_out* out;   // seed: f at ubar^T and the steps taken (may be null)
+  const int8_t* labels;  // SVM: +1 (P) / -1 (Q) per row
 };
 
 __device__ __forceinline__ double* bwd_B(unsigned char* bw) { return reinterpret_cast<double*>(bw); }
@@ -405,6 +406,338 @@ __global__ void __launch_bounds__(32) ses_bwd_seed_kernel(BwdParams p) {
   }
   const float rad = (float)(p.alpha - (p.radii ? (double)__ldg(p.radii) : 0.0));
   bwd_prologue(T - 1, p.tape, d, rad, p.bw, p.grad);
+}
+
+// ---------------------------------------------------------------------------
+// SVM (Sec. 4.2, the minimisation variant of Sec. 3): gradient of
+//   L = f(wbar^T) = (min_P x^T wbar - max_Q x^T wbar)/|wbar|   (0 when clipped)
+// Forward step t (wbar = wbar^t, k = eta t/rho, Hm the tape's shift):
+//   m_i = y_i x_i^T wbar - sbar_c(i), pt_i = e^{-k (m_i - Hm)}, S = sum pt_i,
+//   z = sum_i y_i pt_i x_i / S, w = z/|z|, wbar^{t+1} = (t wbar + w)/(t+1).
+//   s_1, s_2 are piecewise constant in the points: nothing flows through them.
+// Reverse step t, given B = dL/dwbar^{t+1}: B' = B/(t+1),
+//   zbar = (B' - what (what . B'))/|z|, zeta = zbar/S, Sbar = -(zbar . z)/S;
+//   dL/dx_i += pt_i y_i zeta + beta_i wbar, beta_i = -k pt_i (x_i . zeta + y_i Sbar),
+//   dL/dwbar^t = t/(t+1) B + sum_i beta_i x_i.
+// Step t = 0 is a full reverse step here (uniform weights; w depends on the
+// points); wbar^0 = 0 receives nothing.
+
+// Bookkeeping of SVM reverse step s (one warp), given B = dL/dwbar^{s+1}:
+// zeta (in the Gbar slot) and Sbar of step s from the tape.
+static __device__ void svm_bwd_prologue(int64_t s, const float* tape, int d, unsigned char* bw) {
+  const int lane = threadIdx.x & 31;
+  const int dp = dpad4(d);
+  const double* B = bwd_B(bw);
+  float* zeta = bwd_Gbar(bw, d);
+  const float inv = (float)(1.0 / (double)(s + 1));
+  const float* ent = tape + (size_t)s * svm_tape_stride(d);
+  const float S = ent[0], nz = ent[1];
+  const float* z = ent + 8 + dp;
+  if (!(nz > 0.f)) {  // w = 0 at this step: nothing flows to the points
+    for (int j = lane; j < d; j += 32) zeta[j] = 0.f;
+    if (lane == 0) *bwd_Sbar(bw, d) = 0.f;
+    return;
+  }
+  const float rnz = 1.0f / nz;
+  float dot1 = 0.f;
+  for (int j = lane; j < d; j += 32) dot1 = fmaf(z[j] * rnz, (float)B[j] * inv, dot1);
+  dot1 = warp_sum(dot1);
+  const float rS = 1.0f / S;
+  float dot2 = 0.f;
+  for (int j = lane; j < d; j += 32) {
+    const float zb = ((float)B[j] * inv - z[j] * rnz * dot1) * rnz;
+    dot2 = fmaf(zb, z[j], dot2);
+    zeta[j] = zb * rS;
+  }
+  dot2 = warp_sum(dot2);
+  if (lane == 0) *bwd_Sbar(bw, d) = -dot2 * rS;
+}
+
+template <int VW, int LPP, int NCH, int U>
+__global__ void __launch_bounds__(kBlock) svm_bwd_step_kernel(BwdParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float2 s_scr[kMaxBlock];
+  __shared__ bool s_flag;
+  const StateHdr* hdr = reinterpret_cast<const StateHdr*>(p.state);
+  if (p.s >= hdr->t) return;  // the forward stopped before step s
+
+  const int d = p.d;
+  const int dp = dpad4(d);
+  const int nch = (d + VW - 1) / VW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / LPP, gl = lane % LPP;
+  constexpr int PPW = 32 / LPP;
+  const float* ent = p.tape + (size_t)p.s * svm_tape_stride(d);
+  const float k = ent[2], Hm = ent[3], s1 = ent[4], s2 = ent[5];
+  const float* wbar = ent + 8;
+  const float* zeta = bwd_Gbar(p.bw, d);
+  const float Sbar = *bwd_Sbar(p.bw, d);
+
+  float wb[NCH][VW], zt[NCH][VW], acc[NCH][VW];
+#pragma unroll
+  for (int j = 0; j < NCH; ++j) {
+    const int c = gl + j * LPP;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      wb[j][e] = (c < nch) ? wbar[c * VW + e] : 0.f;
+      zt[j][e] = (c < nch) ? zeta[c * VW + e] : 0.f;
+      acc[j][e] = 0.f;
+    }
+  }
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
+  for (int64_t base = gw * (PPW * U); base < p.n; base += nwarps * (PPW * U)) {
+    float x[U][NCH][VW];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * PPW + grp;
+#pragma unroll
+      for (int j = 0; j < NCH; ++j) {
+        const int c = gl + j * LPP;
+        if (i < p.n && c < nch) {
+          Chunk<float, VW>::load(p.pts + i * d, c, x[u][j]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VW; ++e) x[u][j][e] = 0.f;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * PPW + grp;
+      float pw = 0.f, pz = 0.f;
+#pragma unroll
+      for (int j = 0; j < NCH; ++j)
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          pw = fmaf(x[u][j][e], wb[j][e], pw);
+          pz = fmaf(x[u][j][e], zt[j][e], pz);
+        }
+      const float dw = group_sum<LPP>(pw);
+      const float dz = group_sum<LPP>(pz);
+      const bool row = i < p.n;
+      float py = 0.f, beta = 0.f;
+      if (row) {
+        const bool pos = __ldg(p.labels + i) > 0;
+        const float margin = pos ? dw - s1 : -dw - s2;
+        const float pt = expf(-k * (margin - Hm));
+        const float y = pos ? 1.f : -1.f;
+        py = pt * y;
+        beta = -k * pt * (dz + y * Sbar);
+      }
+#pragma unroll
+      for (int j = 0; j < NCH; ++j) {
+        const int ch = gl + j * LPP;
+        float dd[VW];
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          dd[e] = fmaf(py, zt[j][e], beta * wb[j][e]);
+          acc[j][e] = fmaf(beta, x[u][j][e], acc[j][e]);
+        }
+        if (row && ch < nch) {
+          float* gp = p.grad + i * d + ch * VW;
+          if constexpr (VW == 4) {
+            float4 v = *reinterpret_cast<float4*>(gp);
+            v.x += dd[0]; v.y += dd[1]; v.z += dd[2]; v.w += dd[3];
+            *reinterpret_cast<float4*>(gp) = v;
+          } else {
+#pragma unroll
+            for (int e = 0; e < VW; ++e) gp[e] += dd[e];
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = LPP; o < 32; o <<= 1)
+#pragma unroll
+    for (int j = 0; j < NCH; ++j)
+#pragma unroll
+      for (int e = 0; e < VW; ++e) acc[j][e] += __shfl_xor_sync(0xffffffffu, acc[j][e], o);
+  float* sA = reinterpret_cast<float*>(smem_raw);  // [kWarps][dp]
+  if (grp == 0) {
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) {
+      const int c = gl + j * LPP;
+      if (c < nch)
+#pragma unroll
+        for (int e = 0; e < VW; ++e) sA[warp * dp + c * VW + e] = acc[j][e];
+    }
+  }
+  __syncthreads();
+  const int st = ses_partial_stride(d);  // [0, 0, 0, 0, sum_i beta_i x_i]
+  float* prow = p.partials + (size_t)blockIdx.x * st;
+  for (int j = threadIdx.x; j < dp; j += kBlock) {
+    float sum = 0.f;
+    if (j < d)
+      for (int w = 0; w < kWarps; ++w) sum += sA[w * dp + j];
+    prow[4 + j] = sum;
+  }
+  if (threadIdx.x < 4) prow[threadIdx.x] = 0.f;
+
+  auto opof = [](int) { return 0; };
+  if (!arrive_pass(p.partials, st, p.grows, p.counter, s_scr, &s_flag, opof, p.single)) return;
+  float2* raw = reinterpret_cast<float2*>(smem_raw);
+  float* stage = reinterpret_cast<float*>(raw + st);
+  final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single);
+  if (threadIdx.x >= 32) return;
+  double* B = bwd_B(p.bw);
+  const double keep = (double)p.s / (double)(p.s + 1);
+  for (int j = lane; j < d; j += 32) B[j] = keep * B[j] + ((double)raw[4 + j].x + (double)raw[4 + j].y);
+  __syncwarp();
+  if (p.s >= 1) svm_bwd_prologue(p.s - 1, p.tape, d, p.bw);
+}
+
+// min over P and max over Q of x_i^T wbar^T: two candidates (value, smallest
+// index) per CTA, at [2 b] (P) and [2 b + 1] (Q).
+template <int VW, int LPP, int NCH, int U>
+__global__ void __launch_bounds__(kBlock) svm_bwd_argmax_kernel(BwdParams p) {
+  __shared__ float s_val[kWarps][2];
+  __shared__ long long s_idx[kWarps][2];
+  const int d = p.d;
+  const int nch = (d + VW - 1) / VW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / LPP, gl = lane % LPP;
+  constexpr int PPW = 32 / LPP;
+  const float* mean32 = state_mean32(const_cast<void*>(p.state), d);
+  float wb[NCH][VW];
+#pragma unroll
+  for (int j = 0; j < NCH; ++j) {
+    const int c = gl + j * LPP;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) wb[j][e] = (c < nch) ? mean32[c * VW + e] : 0.f;
+  }
+  // track -x.w over P (so both are maxima) and x.w over Q
+  float best[2] = {-INFINITY, -INFINITY};
+  long long bidx[2] = {0x7fffffffffffffffLL, 0x7fffffffffffffffLL};
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
+  for (int64_t base = gw * (PPW * U); base < p.n; base += nwarps * (PPW * U)) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * PPW + grp;
+      float part = 0.f;
+#pragma unroll
+      for (int j = 0; j < NCH; ++j) {
+        const int c = gl + j * LPP;
+        float x[VW];
+        if (i < p.n && c < nch) {
+          Chunk<float, VW>::load(p.pts + i * d, c, x);
+#pragma unroll
+          for (int e = 0; e < VW; ++e) part = fmaf(x[e], wb[j][e], part);
+        }
+      }
+      const float dot = group_sum<LPP>(part);
+      if (i < p.n) {
+        const int cls = __ldg(p.labels + i) > 0 ? 0 : 1;
+        const float v = cls == 0 ? -dot : dot;
+        if (v > best[cls] || (v == best[cls] && i < bidx[cls])) {
+          best[cls] = v;
+          bidx[cls] = i;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, best[c], o);
+      const long long oi = __shfl_xor_sync(0xffffffffu, bidx[c], o);
+      if (ov > best[c] || (ov == best[c] && oi < bidx[c])) {
+        best[c] = ov;
+        bidx[c] = oi;
+      }
+    }
+    if (lane == 0) {
+      s_val[warp][c] = best[c];
+      s_idx[warp][c] = bidx[c];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    const int c = threadIdx.x;
+    float bv = s_val[0][c];
+    long long bi = s_idx[0][c];
+    for (int w = 1; w < kWarps; ++w)
+      if (s_val[w][c] > bv || (s_val[w][c] == bv && s_idx[w][c] < bi)) {
+        bv = s_val[w][c];
+        bi = s_idx[w][c];
+      }
+    p.cand_val[2 * blockIdx.x + c] = bv;
+    p.cand_idx[2 * blockIdx.x + c] = bi;
+  }
+}
+
+// One warp: picks the rows attaining min_P and max_Q, seeds B = dL/dwbar^T and
+// those rows of grad, then the bookkeeping of step T-1.
+template <int kUnused = 0>  // a template so that only the launching unit instantiates it
+__global__ void __launch_bounds__(32) svm_bwd_seed_kernel(BwdParams p) {
+  const int lane = threadIdx.x;
+  const int d = p.d;
+  float bv[2] = {-INFINITY, -INFINITY};
+  long long bi[2] = {0x7fffffffffffffffLL, 0x7fffffffffffffffLL};
+  for (int k = lane; k < p.ncand; k += 32)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float v = p.cand_val[2 * k + c];
+      const long long i = p.cand_idx[2 * k + c];
+      if (v > bv[c] || (v == bv[c] && i < bi[c])) {
+        bv[c] = v;
+        bi[c] = i;
+      }
+    }
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, bv[c], o);
+      const long long oi = __shfl_xor_sync(0xffffffffu, bi[c], o);
+      if (ov > bv[c] || (ov == bv[c] && oi < bi[c])) {
+        bv[c] = ov;
+        bi[c] = oi;
+      }
+    }
+  const StateHdr* hdr = reinterpret_cast<const StateHdr*>(p.state);
+  const int64_t T = hdr->t;
+  const float* wb = state_mean32(const_cast<void*>(p.state), d);
+  float n2 = 0.f;
+  for (int j = lane; j < d; j += 32) n2 = fmaf(wb[j], wb[j], n2);
+  n2 = warp_sum(n2);
+  const bool have = n2 > 0.f && bi[0] != 0x7fffffffffffffffLL && bi[1] != 0x7fffffffffffffffLL;
+  const float rn = have ? 1.0f / sqrtf(n2) : 0.f;
+  const float L = have ? (-bv[0] - bv[1]) * rn : 0.f;  // (min_P x.w - max_Q x.w)/|w|
+  const bool live = have && L > 0.f;                    // a clipped margin has gradient 0
+  const double sd = p.seed ? *p.seed : 1.0;
+  double* B = bwd_B(p.bw);
+  const float* xP = p.pts + (live ? bi[0] : 0) * d;
+  const float* xQ = p.pts + (live ? bi[1] : 0) * d;
+  for (int j = lane; j < d; j += 32) {
+    if (live) {
+      const float dir = wb[j] * rn;
+      B[j] = sd * (double)((xP[j] - xQ[j]) * rn - L * dir * rn);
+      p.grad[bi[0] * d + j] += (float)(sd * dir);
+      p.grad[bi[1] * d + j] -= (float)(sd * dir);
+    } else {
+      B[j] = 0.0;
+    }
+  }
+  __syncwarp();
+  if (lane == 0 && p.out) {
+    pdscp_step_out o;
+    o.oracle_value = hdr->last_value;
+    o.objective = live ? (double)L : 0.0;
+    o.lower_bound = o.objective;
+    o.upper_bound = hdr->ub_best;
+    o.t = T;
+    o.failed = hdr->outcome == PDSCP_OUT_SEPARATED ? 1 : 0;
+    o.stopped = hdr->stopped;
+    o.status = hdr->status;
+    o.outcome = hdr->outcome;
+    o.k = live ? (double)bi[0] : -1.0;  // the row of P attaining the margin
+    *p.out = o;
+  }
+  if (T >= 1) svm_bwd_prologue(T - 1, p.tape, d, p.bw);
 }
 
 }  // namespace pdscp

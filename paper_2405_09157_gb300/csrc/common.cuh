@@ -74,11 +74,14 @@ __host__ __device__ inline int ses_partial_stride(int d) { return 4 + dpad4(d); 
 // One entry of the forward tape a reverse sweep reads (floats): S, |g|, k/sqrt2,
 // the exponent shift, then the mean the pass read (dp) and g (dp).
 __host__ __device__ inline int ses_tape_stride(int d) { return 4 + 2 * dpad4(d); }
+// SVM tape entry (floats): S, |z|, k, the shift, s1bar, s2bar, 0, 0, then the
+// mean the pass read (dp) and z (dp).
+__host__ __device__ inline int svm_tape_stride(int d) { return 8 + 2 * dpad4(d); }
 
 // Sink of the warm-up run of a finish (a scratch state, step record and tape
 // entry that the run writes instead of the real ones): its size and parts.
 __host__ __device__ inline size_t warm_sink_bytes(int d) {
-  return ((state_bytes(d) + 255) & ~(size_t)255) + 256 + (size_t)ses_tape_stride(d) * sizeof(float);
+  return ((state_bytes(d) + 255) & ~(size_t)255) + 256 + (size_t)svm_tape_stride(d) * sizeof(float);
 }
 __device__ __forceinline__ pdscp_step_out* warm_sink_out(unsigned char* sink, int d) {
   return reinterpret_cast<pdscp_step_out*>(sink + ((state_bytes(d) + 255) & ~(size_t)255));

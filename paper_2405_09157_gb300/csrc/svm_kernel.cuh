@@ -43,6 +43,7 @@ struct SvmParams {
   pdscp_step_out* out;
   float2* row_out;       // non-null: a shard's pass; write the column totals here, no finish
   unsigned char* sink;   // non-null: warm-up warps run the finish's code early, writing here
+  float* tape;           // non-null: the finish records entry t (svm_tape_stride floats) for a reverse sweep
 };
 
 // Warm-up of the finish's code path in every CTA (see ses_finish_warm).
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(kBlock) svm_iter_kernel(SvmParams p) {
 // ses_finish_warp).
 static __device__ __noinline__ void svm_finish_warp(const float2* raw, const double* s_mean, const StateHdr& h,
                                              void* state, int d, double alpha_d, double D_d, double eta_over_rho,
-                                             int eval_only, pdscp_step_out* out) {
+                                             int eval_only, pdscp_step_out* out, float* tape = nullptr) {
   const int lane = threadIdx.x & 31;
   const int dp = dpad4(d);
   StateHdr* hdr = reinterpret_cast<StateHdr*>(state);
@@ -289,6 +290,24 @@ static __device__ __noinline__ void svm_finish_warp(const float2* raw, const dou
       mean32[j] = (float)nm;
     }
   }
+  if (tape && advance) {
+    // what the pass used (same expressions as the pass kernels) and what it produced
+    float* ent = tape + (size_t)t * svm_tape_stride(d);
+    for (int j = lane; j < d; j += 32) {
+      ent[8 + j] = (float)s_mean[j];
+      ent[8 + dp + j] = (tot(4 + j) - tot(4 + dp + j)) * rS;
+    }
+    if (lane == 0) {
+      ent[0] = S;
+      ent[1] = nz;
+      ent[2] = (float)((double)t * eta_over_rho);
+      ent[3] = (float)(h.hint - h.move);
+      ent[4] = (float)h.s1bar;
+      ent[5] = (float)h.s2bar;
+      ent[6] = 0.f;
+      ent[7] = 0.f;
+    }
+  }
   if (lane == 0) {
     if (!eval_only && (double)UB < h.ub_best) hdr->ub_best = (double)UB;
     if (streak != h.streak) hdr->streak = streak;
@@ -338,7 +357,8 @@ static __device__ __noinline__ void svm_finish_warm(const SvmParams& p, unsigned
   const double* s_mean = reinterpret_cast<const double*>(smem_raw) + svm_partial_stride(d);
   StateHdr h;
   memset(&h, 0, sizeof(h));
-  svm_finish_warp(raw, s_mean, h, p.sink, d, p.alpha, p.D, p.eta_over_rho, p.eval_only, warm_sink_out(p.sink, d));
+  svm_finish_warp(raw, s_mean, h, p.sink, d, p.alpha, p.D, p.eta_over_rho, p.eval_only, warm_sink_out(p.sink, d),
+                  p.tape ? warm_sink_tape(p.sink, d) : nullptr);
 }
 
 // O(d) finish of one SVM iteration. Every CTA calls it after writing its
@@ -377,7 +397,7 @@ __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
   // The O(d) math runs in warp 0 alone (see ses_finish).
   if (tid >= 32) return;
   svm_finish_warp(raw, s_mean, *reinterpret_cast<const StateHdr*>(s_hdr), p.state, d, p.alpha, p.D,
-                  p.eta_over_rho, p.eval_only, p.out);
+                  p.eta_over_rho, p.eval_only, p.out, p.tape);
 }
 
 }  // namespace pdscp

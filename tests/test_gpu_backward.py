@@ -111,3 +111,83 @@ def test_full_size_invariances(n, d, T):
     # rotation equivariance: sum_i v_i grad_i^T is symmetric
     Mv = V.T @ got
     assert np.max(np.abs(Mv - Mv.T)) <= 1e-4 * np.abs(V).max() * tot.sum() + 1e-6
+
+
+# --- SVM: margin of the minimisation alpha-FTP -------------------------------
+
+from oracle import svm as osvm  # noqa: E402
+from oracle import svm_grad  # noqa: E402
+
+
+def _svm_case(n1, n2, d, seed):
+    X32, y = datagen.svm_clusters(n1, n2, d, mu_norm=3.0, band=0.5, seed=seed)
+    X = X32.astype(np.float64)
+    D = osvm.svm_D(X)
+    return X32, y, X, D, osvm.svm_width(D)
+
+
+def _svm_gpu(X32, y, alpha, eor, T, D, seed=None):
+    pts = torch.from_numpy(X32).cuda()
+    lab = torch.from_numpy(y).cuda()
+    out = api.new_steps(1)
+    grad, _ = api.mwu_backward(pts, alpha, eor, T, seed=seed, out=out, problem=_ffi.SVM, labels=lab, D=D)
+    torch.cuda.synchronize()
+    return grad.cpu().numpy().astype(np.float64), api.decode_steps(out)[0]
+
+
+@pytest.mark.parametrize("n1,n2,d,T", [(60, 50, 3, 10), (700, 900, 8, 15), (2000, 1500, 32, 12),
+                                       (3000, 3000, 64, 8), (500, 400, 5, 6), (1, 1, 4, 5)])
+def test_svm_backward_matches_oracle(n1, n2, d, T):
+    X32, y, X, D, rho = _svm_case(n1, n2, d, 31)
+    alpha, eta = 0.2 * D, 0.5
+    L, want, steps = svm_grad.svm_unrolled_margin_grad(X, y, alpha, eta / rho, D, T)
+    got, rec = _svm_gpu(X32, y, alpha, eta / rho, T, D)
+    assert rec["status"] == 0 and rec["t"] == steps == T
+    assert abs(rec["objective"] - L) <= RTOL * D
+    scale = max(np.max(np.abs(want)), 1.0)
+    err = np.max(np.abs(got - want))
+    assert err <= GRAD_RTOL * scale, (err / scale, np.unravel_index(np.argmax(np.abs(got - want)), want.shape))
+
+
+def test_svm_one_iteration_closed_form_and_seed():
+    X32, y, X, D, rho = _svm_case(300, 200, 6, 9)
+    n = X.shape[0]
+    seed = torch.tensor([2.0], dtype=torch.float64, device="cuda")
+    got, rec = _svm_gpu(X32, y, 0.1 * D, 0.5 / rho, 1, D, seed=seed)
+    z = (X[y > 0].sum(axis=0) - X[y < 0].sum(axis=0)) / n
+    w = z / np.linalg.norm(z)
+    s = X @ w
+    iP = np.flatnonzero(y > 0)[np.argmin(s[y > 0])]
+    iQ = np.flatnonzero(y < 0)[np.argmax(s[y < 0])]
+    proj = (np.eye(6) - np.outer(w, w)) @ (X[iP] - X[iQ]) / np.linalg.norm(z)
+    want = np.outer(y.astype(np.float64) / n, proj)
+    want[iP] += w
+    want[iQ] -= w
+    assert int(rec["k"]) == iP and abs(rec["objective"] - (s[iP] - s[iQ])) <= RTOL * D
+    assert np.max(np.abs(got - 2.0 * want)) <= 1e-5
+
+
+def test_svm_autograd_function_matches_the_sweep():
+    X32, y, X, D, rho = _svm_case(1500, 1200, 16, 12)
+    eor, T = 0.5 / rho, 10
+    pts = torch.from_numpy(X32).cuda().requires_grad_(True)
+    lab = torch.from_numpy(y).cuda()
+    f = api.svm_unrolled_margin(pts, lab, 0.2 * D, eor, T, D)
+    (1.5 * f).backward()
+    direct, _ = api.mwu_backward(pts.detach(), 0.2 * D, eor, T, problem=_ffi.SVM, labels=lab, D=D)
+    torch.cuda.synchronize()
+    assert torch.allclose(pts.grad, 1.5 * direct, rtol=1e-6, atol=1e-7)
+    L, _, _ = svm_grad.svm_unrolled_margin_grad(X, y, 0.2 * D, eor, D, T)
+    assert abs(float(f) - L) <= RTOL * D
+
+
+def test_svm_full_size_rotation_identity():
+    # the margin and the whole alpha-FTP are rotation equivariant, so sum_i x_i grad_i^T is symmetric
+    # alpha = 0.05 D (about 0.55) stays below OPT >= 1 (the band 0.5 on both sides of the Bayes
+    # hyperplane), so the ORACLE never separates and all 500 iterations are differentiated
+    X32, y, X, D, rho = _svm_case(50_000, 50_000, 64, 0)
+    got, rec = _svm_gpu(X32, y, 0.05 * D, 0.5 / rho, 500, D)
+    assert rec["status"] == 0 and rec["t"] == 500 and rec["objective"] > 0 and np.all(np.isfinite(got))
+    M = X.T @ got
+    tot = np.abs(got).sum()
+    assert np.max(np.abs(M - M.T)) <= 1e-4 * np.abs(X).max() * tot + 1e-6

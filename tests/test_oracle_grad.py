@@ -1,9 +1,12 @@
-"""Pins for the FP64 gradient oracle of the unrolled SES alpha-FTP (oracle/ses_grad.py).
+"""Pins for the FP64 gradient oracles of the unrolled alpha-FTPs
+(oracle/ses_grad.py, oracle/svm_grad.py).
 
-Checked against: the independent numpy forward of oracle/ses.py (value and
-central finite differences), the closed form at T = 1 (ubar^1 = v_1), and the
-closed form for two points, where every ORACLE answer lies on the segment
-v_1 v_2 and ubar^T = v_1 + alpha (T-1)/T (v_2 - v_1)/|v_2 - v_1|.
+SES: the independent numpy forward of oracle/ses.py (value and central finite
+differences), the closed form at T = 1 (ubar^1 = v_1), and the closed form for
+two points, where every ORACLE answer lies on the segment v_1 v_2 and
+ubar^T = v_1 + alpha (T-1)/T (v_2 - v_1)/|v_2 - v_1|.
+SVM: the numpy forward of oracle/svm.py (value and central finite differences)
+and the closed form at T = 1 (wbar^1 = z/|z| from uniform weights).
 """
 
 import numpy as np
@@ -99,3 +102,74 @@ def test_two_points_closed_form(T, rel):
     else:
         want = np.zeros_like(V)
     assert np.allclose(grad, want, rtol=0, atol=1e-12)
+
+
+# --- SVM: margin of the minimisation alpha-FTP (oracle/svm_grad.py) ----------
+
+from oracle import svm as osvm  # noqa: E402
+from oracle import svm_grad  # noqa: E402
+
+
+def svm_numpy_forward(X, y, alpha, eta, rho, D, T):
+    wbar, s1, s2 = np.zeros(X.shape[1]), 0.0, 0.0
+    for t in range(T):
+        rec = osvm.svm_step(X, y, wbar, s1, s2, t, alpha, eta, rho, D)
+        if rec["failed"]:
+            break
+        wbar, s1, s2 = rec["wbar_next"], rec["s1bar_next"], rec["s2bar_next"]
+    return osvm.svm_margin(X, y, wbar)
+
+
+def _svm_case(n1, n2, d, seed):
+    X, y = datagen.svm_clusters(n1, n2, d, mu_norm=3.0, band=0.5, seed=seed)
+    X = X.astype(np.float64)
+    D = osvm.svm_D(X)
+    return X, y, D, osvm.svm_width(D)
+
+
+def test_svm_value_matches_numpy_forward():
+    X, y, D, rho = _svm_case(15, 12, 3, 1)
+    for T in (1, 3, 10, 30):
+        L, grad, steps = svm_grad.svm_unrolled_margin_grad(X, y, 0.2 * D, 0.5 / rho, D, T)
+        assert steps == T and np.all(np.isfinite(grad))
+        assert abs(L - svm_numpy_forward(X, y, 0.2 * D, 0.5, rho, D, T)) <= 1e-12 * D
+
+
+@pytest.mark.parametrize("n1,n2,d,T,seed", [(10, 9, 2, 6, 2), (8, 12, 4, 15, 3), (14, 11, 3, 25, 4)])
+def test_svm_gradient_matches_central_differences(n1, n2, d, T, seed):
+    X, y, D, rho = _svm_case(n1, n2, d, seed)
+    alpha, eta = 0.2 * D, 0.5
+    L, grad, steps = svm_grad.svm_unrolled_margin_grad(X, y, alpha, eta / rho, D, T)
+    assert steps == T and L > 0
+    h = 1e-6
+    fd = np.zeros_like(X)
+    for i in range(X.shape[0]):
+        for j in range(d):
+            Xp, Xm = X.copy(), X.copy()
+            Xp[i, j] += h
+            Xm[i, j] -= h
+            fd[i, j] = (svm_numpy_forward(Xp, y, alpha, eta, rho, D, T) -
+                        svm_numpy_forward(Xm, y, alpha, eta, rho, D, T)) / (2 * h)
+    scale = np.max(np.abs(grad))
+    assert np.max(np.abs(fd - grad)) <= 1e-6 * scale, np.max(np.abs(fd - grad)) / scale
+    # beyond the two rows attaining the margin, the sweep reaches the other points through z
+    assert np.count_nonzero(np.abs(grad) > 1e-3 * scale) > 2 * d
+
+
+def test_svm_one_iteration_closed_form():
+    # T = 1: wbar^1 = w^0 = z/|z| with z = (sum_P x - sum_Q x)/n (p^1 = e/r), |wbar^1| = 1, so
+    # L = x_iP.w - x_iQ.w and dL/dx_i = [i = iP] w - [i = iQ] w + (y_i/n)(I - w w^T)(x_iP - x_iQ)/|z|
+    X, y, D, rho = _svm_case(9, 11, 3, 5)
+    n = X.shape[0]
+    L, grad, _ = svm_grad.svm_unrolled_margin_grad(X, y, 0.1 * D, 0.5 / rho, D, 1)
+    z = (X[y > 0].sum(axis=0) - X[y < 0].sum(axis=0)) / n
+    w = z / np.linalg.norm(z)
+    s = X @ w
+    iP = np.flatnonzero(y > 0)[np.argmin(s[y > 0])]
+    iQ = np.flatnonzero(y < 0)[np.argmax(s[y < 0])]
+    assert abs(L - (s[iP] - s[iQ])) <= 1e-13 * D
+    proj = (np.eye(3) - np.outer(w, w)) @ (X[iP] - X[iQ]) / np.linalg.norm(z)
+    want = np.outer(y.astype(np.float64) / n, proj)
+    want[iP] += w
+    want[iQ] -= w
+    assert np.allclose(grad, want, rtol=0, atol=1e-13)
