@@ -521,6 +521,7 @@ def batched_variant(dev, K=10, W=3):
     pts, offs, n, d, scale = batched_inputs(dev)
     sizes = n * d
     batch = api.SesBatch(pts, offs, n, d, tile_rows=4096)
+    tr, _ = batch.autotune()  # the native autotuner re-initialises the batch with the fastest tile size
     bound = 2.0 * scale * (np.sqrt(d) + 6.0)  # >= OPT with room: the ORACLE never separates
     a = torch.tensor(bound, dtype=torch.float64, device=dev)
     e = torch.tensor(0.01 / (3.0 * bound / np.sqrt(2.0)), dtype=torch.float64, device=dev)
@@ -540,7 +541,8 @@ def batched_variant(dev, K=10, W=3):
         raise RuntimeError("a batched instance did not run every iteration")
     peak, _ = peaks()
     b = int(sizes.sum()) * 4
-    return {"instances": int(len(n)), "points": int(n.sum()), "bytes_per_iter": b, "ms_per_iter": ms,
+    return {"instances": int(len(n)), "points": int(n.sum()), "tile_rows": int(tr), "bytes_per_iter": b,
+            "ms_per_iter": ms,
             "instance_iters_per_s": len(n) * 1e3 / ms, "GBps": b / ms / 1e6, "frac_hbm": b / ms / 1e6 / peak,
             "l2": "input larger than L2, no flush"}
 

@@ -82,14 +82,16 @@ struct BatchParams {
 
 // Load/lane layouts, chosen on the host per instance:
 //   0..4: 16-byte chunks, LPP = 1, 2, 4, 8, 16 (d = 4 * LPP or less, d % 4 == 0, aligned)
-//   5: scalar, 2 lanes (d <= 2); 6: scalar, 8 lanes (d <= 8); 7: scalar, 32 lanes (d <= 32);
-//   8: scalar, 32 lanes x 2 (d <= 64)
+//   9: scalar, one lane per point (d <= 4: a warp covers 32 consecutive short
+//      rows, and each point's exponentials run once, not on several lanes);
+//   6: scalar, 8 lanes (d <= 8); 7: scalar, 32 lanes (d <= 32);
+//   8: scalar, 32 lanes x 2 (d <= 64); 5 (2 lanes, d <= 2) is kept for callers of old tables
 inline int batch_shape(int d, bool aligned16) {
   if (d % 4 == 0 && aligned16) {
     const int c = d / 4;
     return c <= 1 ? 0 : c <= 2 ? 1 : c <= 4 ? 2 : c <= 8 ? 3 : 4;
   }
-  return d <= 2 ? 5 : d <= 8 ? 6 : d <= 32 ? 7 : 8;
+  return d <= 4 ? 9 : d <= 8 ? 6 : d <= 32 ? 7 : 8;
 }
 
 // Streams rows [r0, r1) of one instance at mean ubar (in shared memory, FP32)
@@ -376,6 +378,7 @@ __global__ void __launch_bounds__(kBatchBlock) ses_batch_kernel(BatchParams p) {
         case 5: batch_tile<1, 2, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
         case 6: batch_tile<1, 8, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
         case 7: batch_tile<1, 32, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
+        case 9: batch_tile<1, 1, 4, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
         default: batch_tile<1, 32, 2, 2>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
       }
       __syncthreads();

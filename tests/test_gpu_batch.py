@@ -109,16 +109,19 @@ def test_batch_search_brackets_the_optimum():
             # the FP64 oracle's search with the same rules (instances small
             # enough for it to finish in seconds). The Sec. 5 rules take a
             # stalled FTP as an affirmative answer, so [L, U] may end below
-            # OPT on some instances (the oracle does the same); the returned
-            # radius is compared with the oracle's, not with OPT.
+            # OPT on some instances (the oracle does the same), and which FTP
+            # stalls where depends on rounding near the delta threshold, so
+            # the two searches may end on different balls: both are actual
+            # enclosing balls, and the device's may not be worse than the
+            # oracle's by more than 2 eps.
             ref = oses.ses_solve(V, eps=eps, max_iters=200_000)
-            assert abs(r["upper_bound"] - ref["radius"]) <= 2 * eps * ref["radius"], (k, r, ref["radius"])
+            assert r["upper_bound"] <= ref["radius"] * (1 + 2 * eps), (k, r, ref["radius"])
             assert r["lower_bound"] <= ref["upper_bound"] * (1 + 1e-5)
             assert ref["lower_bound"] <= r["upper_bound"] * (1 + 1e-5)
         elif r["D"] > 0:
             # larger instances: the single-instance GPU search, same rules
             _, one = api.ses_solve(torch.from_numpy(arrays[k]).cuda(), eps=eps, max_iters=200_000)
-            assert abs(r["upper_bound"] - one["value"]) <= 2 * eps * one["value"], (k, r, one)
+            assert r["upper_bound"] <= one["value"] * (1 + 2 * eps), (k, r, one)
             assert r["lower_bound"] <= one["upper_bound"] * (1 + 1e-5)
             assert one["lower_bound"] <= r["upper_bound"] * (1 + 1e-5)
 
