@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kBlock) ses_bwd_step_kernel(BwdParams p) {
   if (!arrive_pass(p.partials, st, p.grows, p.counter, s_scr, &s_flag, opof, p.single)) return;
   float2* raw = reinterpret_cast<float2*>(smem_raw);
   float* stage = reinterpret_cast<float*>(raw + st);
-  final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single);
+  final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single, -1, -1, st);
   if (threadIdx.x >= 32) return;
   double* B = bwd_B(p.bw);
   const double keep = (double)p.s / (double)(p.s + 1);
@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(kBlock) svm_bwd_step_kernel(BwdParams p) {
   if (!arrive_pass(p.partials, st, p.grows, p.counter, s_scr, &s_flag, opof, p.single)) return;
   float2* raw = reinterpret_cast<float2*>(smem_raw);
   float* stage = reinterpret_cast<float*>(raw + st);
-  final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single);
+  final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single, -1, -1, st);
   if (threadIdx.x >= 32) return;
   double* B = bwd_B(p.bw);
   const double keep = (double)p.s / (double)(p.s + 1);

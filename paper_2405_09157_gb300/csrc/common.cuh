@@ -385,9 +385,39 @@ __device__ bool arrive_pass(const float* rows, int stride, float2* grows, unsign
   return *s_flag;
 }
 
+// Column totals of an (nb x stride) float matrix in shared memory, one warp
+// per column (columns c0, c0 + cstep, ...): each lane combines rows lane,
+// lane + 32, ... (compensated FP32 sums; column pc % period == max_col is a
+// maximum, == min_col a minimum), then the lanes combine in a fixed butterfly
+// (every lane ends with the same pair, so the result is deterministic). No
+// barrier inside. (Warming this code too, as the finish's, was measured: the
+// extra call from the warm-up path changed the streaming loop's register
+// allocation and cost 8 us per launch, far more than it saved.)
+static __device__ __forceinline__ void warp_columns(const float* m, int nb, int stride, int c0, int cstep,
+                                                 float2* out, int period, int max_col, int min_col) {
+  const int lane = threadIdx.x & 31;
+  for (int pc = c0; pc < stride; pc += cstep) {
+    const int q = pc % period;
+    const int op = q == max_col ? 1 : (q == min_col ? 2 : 0);
+    float2 acc = col_init2(op);
+    for (int r = lane; r < nb; r += 32) col_comb2(op, acc, make_float2(m[(size_t)r * stride + pc], 0.f));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      float2 other;
+      other.x = __shfl_xor_sync(0xffffffffu, acc.x, o);
+      other.y = __shfl_xor_sync(0xffffffffu, acc.y, o);
+      col_comb2(op, acc, other);
+    }
+    if (lane == 0) out[pc] = acc;
+  }
+}
+
+// max_col / min_col / period: the column operations for the single-level
+// path (warp_columns); opof gives the same for the two-level path.
 template <typename OpOf>
 __device__ void final_reduce(const float* rows, int stride, const float2* grows, unsigned int* counters,
-                             float2* scratch, OpOf opof, float2* raw, float* stage, bool single) {
+                             float2* scratch, OpOf opof, float2* raw, float* stage, bool single, int max_col,
+                             int min_col, int period) {
   const int nb = gridDim.x;
   if (!single) {
     const int G = (nb + group_size(nb) - 1) / group_size(nb);
@@ -408,7 +438,8 @@ __device__ void final_reduce(const float* rows, int stride, const float2* grows,
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   if (threadIdx.x == 0) counters[0] = 0u;
   __syncthreads();
-  reduce_rows(stage, 0, nb, stride, raw, scratch, opof, true);
+  warp_columns(stage, nb, stride, threadIdx.x >> 5, (int)(blockDim.x >> 5), raw, period, max_col, min_col);
+  __syncthreads();
 }
 
 // Sums of up to four doubles per thread over the whole block in one pass

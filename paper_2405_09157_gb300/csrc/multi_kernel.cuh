@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kBlock) ses_multi_kernel(MultiParams p) {
     mreg[r] = (q < K && j < d) ? state_mean(p.states + (size_t)q * p.state_stride)[j] : 0.0;
   }
   const double v0 = threadIdx.x < d ? (double)elem_to_float<T>(pts + threadIdx.x) : 0.0;
-  final_reduce(p.partials, wst, p.grows, p.counter, s_scr, opof, raw, stage, p.single);
+  final_reduce(p.partials, wst, p.grows, p.counter, s_scr, opof, raw, stage, p.single, 2, -1, st);
 #pragma unroll
   for (int r = 0; r < (K * kMultiMaxD + kBlock - 1) / kBlock; ++r) {
     const int idx = threadIdx.x + r * kBlock;

@@ -388,7 +388,7 @@ __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw) {
   const double m0 = tid < d ? mean[tid] : 0.0;
   const double v0 = tid < d ? (double)elem_to_float<T>(pts + tid) : 0.0;
   const double gam1 = p.radii ? (double)__ldg(p.radii) : 0.0;
-  final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single);
+  final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single, 2, -1, st);
   if (p.row_out) {  // a shard of a row-sharded iteration: hand the totals to the merge
     for (int pc = tid; pc < st; pc += blockDim.x) p.row_out[pc] = raw[pc];
     return;

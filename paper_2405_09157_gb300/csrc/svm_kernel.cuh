@@ -385,7 +385,7 @@ __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
   constexpr int HW = (int)(sizeof(StateHdr) / 8);
   const double hw = tid < HW ? reinterpret_cast<const double*>(hdr)[tid] : 0.0;
   const double m0 = tid < d ? mean[tid] : 0.0;
-  final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single);
+  final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single, 3, 2, st);
   if (p.row_out) {  // a shard of a row-sharded iteration: hand the totals to the merge
     for (int pc = tid; pc < st; pc += blockDim.x) p.row_out[pc] = raw[pc];
     return;
