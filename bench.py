@@ -62,7 +62,8 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+        import tempfile
+        self.path = os.path.join(os.environ.get("PDSCP_CLOCKS_DIR", tempfile.gettempdir()), f"clocks_gpu{index}.csv")
 
     def start(self):
         try:

@@ -13,7 +13,7 @@ means points, gamma = 0). Row 0 is v_1, the constraint kept as the easy set C
 ("the first one", Sec. 4.1); rows 1..n-1 form the product cone
 K = prod_{i>=2} Q^{d+1} of rank r = 2(n-1).
 
-Readings of the paper taken here (each is listed in the design doc):
+Readings of the paper taken here (the GPU path takes the same ones):
   * gamma-bar, the running mean of the oracle's gamma outputs, equals alpha
     inside one alpha-FTP because the ORACLE always returns gamma = alpha.
   * When g = sum_i w_i = 0 (always at t = 0, where p^1 = e/r) the ORACLE's

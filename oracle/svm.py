@@ -14,7 +14,7 @@ P = rows with y = +1, Q = rows with y = -1 (Sec. 4.2). Component i of
 K = R^n_+ belongs to row i; the order of components in a product cone does
 not matter (Sec. 2.1).
 
-Readings of the paper taken here (each is listed in the design doc):
+Readings of the paper taken here (the GPU path takes the same ones):
   * f^t (Sec. 5) prints the letters of the two sets swapped; it is read as
     (min over P of x^T wbar - max over Q of x^T wbar)/||wbar||, clipped at 0,
     which is the margin of the hyperplane with normal wbar (Eq. SVM).

@@ -423,8 +423,7 @@ __global__ void __launch_bounds__(kBatchBlock) ses_batch_kernel(BatchParams p) {
         }
         const int st = 4 + dpad4(d);
         // rows of this instance: stride kBatchStride, the first st columns used
-        reduce_rows(partials + (size_t)in.tile0 * kBatchStride, 0, in.ntiles, st, raw, s_scr, opof, false,
-                    kBatchStride);
+        reduce_rows(partials + (size_t)in.tile0 * kBatchStride, 0, in.ntiles, st, raw, s_scr, opof, kBatchStride);
         if (tid < 32) {
           ses_finish_warp(raw, s_mean, s_v1, *reinterpret_cast<const StateHdr*>(s_hdr), state, d, alpha_d, 0.0,
                           eor_d, eval ? 1 : 0, p.out ? p.out + tl.inst : nullptr);

@@ -228,15 +228,13 @@ __device__ __forceinline__ float2 as_pair(float2 v) { return v; }
 // R * stride <= blockDim) so each thread issues few loads, all independent;
 // the R partial results are combined in a fixed order (deterministic).
 // opof(pc) gives the operation of column pc. `scratch` holds blockDim
-// float2. Ends with a barrier; every thread must call it.
-template <typename TIn>
-__device__ __forceinline__ TIn load_row_elem(const TIn* p, bool shared_src) {
-  return shared_src ? *p : __ldcg(p);
-}
+// float2. `ld` (> 0) is the row pitch when it differs from stride. The rows
+// are read through L2 (other CTAs wrote them). Ends with a barrier; every
+// thread must call it.
 
 template <typename TIn, typename OpOf>
 __device__ void reduce_rows(const TIn* m, int r0, int r1, int stride, float2* out, float2* scratch, OpOf opof,
-                            bool shared_src = false, int ld = 0) {
+                            int ld = 0) {
   const size_t pitch = ld > 0 ? (size_t)ld : (size_t)stride;  // row pitch; the first `stride` columns are reduced
   const int nt = blockDim.x;
   int R = 1;
@@ -246,7 +244,7 @@ __device__ void reduce_rows(const TIn* m, int r0, int r1, int stride, float2* ou
       const int op = opof(pc);
       float2 acc = col_init2(op);
 #pragma unroll 8
-      for (int r = r0; r < r1; ++r) col_comb2(op, acc, as_pair(load_row_elem(m + (size_t)r * pitch + pc, shared_src)));
+      for (int r = r0; r < r1; ++r) col_comb2(op, acc, as_pair(__ldcg(m + (size_t)r * pitch + pc)));
       out[pc] = acc;
     }
     __syncthreads();
@@ -258,7 +256,7 @@ __device__ void reduce_rows(const TIn* m, int r0, int r1, int stride, float2* ou
     const int op = opof(pc);
     float2 acc = col_init2(op);
 #pragma unroll 8
-    for (int r = r0 + q; r < r1; r += R) col_comb2(op, acc, as_pair(load_row_elem(m + (size_t)r * pitch + pc, shared_src)));
+    for (int r = r0 + q; r < r1; r += R) col_comb2(op, acc, as_pair(__ldcg(m + (size_t)r * pitch + pc)));
     scratch[q * stride + pc] = acc;
   }
   __syncthreads();

@@ -1,6 +1,7 @@
 // SES iteration kernel: one streaming pass over the points per MWU iteration
 // (Sec. 4.1 with the update of Eq. implement and the ORACLE of Eq. ses_oracle),
-// finished in FP64 by the last CTA to complete.
+// finished by the last CTA to complete (compensated FP32 column totals, an
+// FP32 O(d) finish in one warp, the running mean kept in FP64).
 //
 // Per cone i >= 2 the exponent is X_i = -k (ubar - v_i; alpha - gamma_i) with
 // k = eta t / rho. Its SOC spectrum (Sec. 2.1) is
@@ -205,9 +206,6 @@ __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
   ses_finish<T>(p, smem_raw);
 }
 
-// O(d) finish of one SES iteration. Every CTA calls it after writing its
-// partial row [S, Wt, maxd, 0, G'_1..G'_d]; the two-level completion elects
-// one CTA, which reduces the group rows in FP64 and does the rest.
 // The O(d) finish of one SES iteration from the column totals: run by one
 // warp (lane = threadIdx.x & 31). raw: [S, Wt, maxd, 0, G'_1..G'_d] as
 // compensated pairs; s_mean, s_v1: the mean read by the pass and v_1 (FP64,

@@ -1,7 +1,8 @@
 // SVM iteration kernel: one streaming pass over the labelled points per MWU
 // iteration of the minimisation variant (Sec. 3, Eq. min_implement) for the
-// data of Eq. (svm_dual_scp), K = R^n_+ (Sec. 4.2), finished in FP64 by the
-// last CTA to complete.
+// data of Eq. (svm_dual_scp), K = R^n_+ (Sec. 4.2), finished by the last CTA
+// to complete (compensated FP32 column totals, an FP32 O(d) finish in one
+// warp, the running means kept in FP64).
 //
 // Point i (label y_i = +1 for P, -1 for Q) has margin
 //   m_i = y_i x_i^T wbar - sbar_{class i}      (c - sum_j a_j ybar_j, Sec. 4.2)
