@@ -358,6 +358,10 @@ __device__ __noinline__ void ses_finish_warm(const SesParams& p, unsigned char* 
                   warm_sink_out(p.sink, d), p.tape ? warm_sink_tape(p.sink, d) : nullptr);
 }
 
+// Completion of one SES iteration. Every CTA calls it after writing its
+// partial row [S, Wt, maxd, 0, G'_1..G'_d]; the last CTA to arrive reduces
+// the rows and hands the totals to warp 0 (ses_finish_warp), or, for a shard
+// of a row-sharded iteration, writes them to row_out.
 template <typename T>
 __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw) {
   __shared__ float2 s_scr[kMaxBlock];
