@@ -322,6 +322,98 @@ static __device__ __forceinline__ void batch_search_update(BatchSearch* sr, void
   for (int j = lane; j < d; j += 32) sr->center[j] = r.center[j];
 }
 
+// batch_tile for 16-byte chunk rows (d = 4 VW.. up to 64 floats): each warp
+// streams one contiguous part of the tile, NI points per lane per round (all
+// loads of a round in flight together), and each point's scalar work runs
+// once, on the lane that owns it after a reduce-scatter of the partial
+// squared distances (GroupScatter), as in ses_iter_t_kernel.
+template <int VW, int LPP, int NI>
+__device__ void batch_tile_t(const float* pts, int d, int64_t r0, int64_t r1, const float* s_ub, float kr,
+                             float H, float alpha, float* sG, float (*s_sc)[3]) {
+  using GS = GroupScatter<LPP, NI>;
+  const int nch = d / VW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / LPP, gl = lane % LPP;
+  constexpr int PPW = 32 / LPP;
+  constexpr int ROUND = PPW * NI;
+  const bool owner = (gl % GS::SHARE) == 0;
+  const bool has_chunk = gl < nch;
+  const int64_t len = r1 - r0;
+  const int64_t lo = r0 + (int64_t)warp * len / kBatchWarps, hi = r0 + (int64_t)(warp + 1) * len / kBatchWarps;
+  float ub[VW], G[VW];
+#pragma unroll
+  for (int e = 0; e < VW; ++e) {
+    ub[e] = has_chunk ? s_ub[gl * VW + e] : 0.f;
+    G[e] = 0.f;
+  }
+  float S = 0.f, W = 0.f, maxd = -INFINITY;
+  for (int64_t base = lo; base < hi; base += ROUND) {
+    float x[NI][VW];
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const int64_t i = base + r * PPW + grp;
+      if (i < hi && has_chunk) {
+        Chunk<float, VW>::load(pts + i * d, gl, x[r]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) x[r][e] = 0.f;
+      }
+    }
+    float part[NI];
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      float a = 0.f;
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        x[r][e] -= ub[e];
+        a = fmaf(x[r][e], x[r][e], a);
+      }
+      part[r] = has_chunk ? a : 0.f;
+    }
+    GS::run(part, gl);
+    float c[GS::OWN];
+#pragma unroll
+    for (int k = 0; k < GS::OWN; ++k) {
+      const int64_t i = base + GS::owned(gl, k) * PPW + grp;
+      c[k] = 0.f;
+      if (i >= 1 && i < hi) {  // instance row 0 is v_1, the easy cone
+        const float dist = sqrtf(part[k]);
+        const float E1 = expf(kr * (dist - H));
+        const float em = -expm1f(-2.f * kr * dist);
+        const float dif = E1 * em;
+        const float sum = E1 * (2.f - em);
+        c[k] = dist > 0.f ? dif / dist : 2.f * kr * E1;
+        if (owner) {
+          S += sum;
+          W += alpha * sum - dist * dif;
+          maxd = fmaxf(maxd, dist);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const float cr = __shfl_sync(0xffffffffu, c[r % GS::OWN], grp * LPP + GS::src_lane(r));
+#pragma unroll
+      for (int e = 0; e < VW; ++e) G[e] = fmaf(cr, x[r][e], G[e]);
+    }
+  }
+#pragma unroll
+  for (int o = LPP; o < 32; o <<= 1)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) G[e] += __shfl_xor_sync(0xffffffffu, G[e], o);
+  S = warp_sum(S);
+  W = warp_sum(W);
+  maxd = warp_max(maxd);
+  if (grp == 0 && has_chunk)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) sG[warp * kBatchMaxD + gl * VW + e] = G[e];
+  if (lane == 0) {
+    s_sc[warp][0] = S;
+    s_sc[warp][1] = W;
+    s_sc[warp][2] = maxd;
+  }
+}
+
 __global__ void __launch_bounds__(kBatchBlock) ses_batch_kernel(BatchParams p) {
   __shared__ float sG[kBatchWarps * kBatchMaxD];
   __shared__ float s_sc[kBatchWarps][3];
@@ -370,11 +462,11 @@ __global__ void __launch_bounds__(kBatchBlock) ses_batch_kernel(BatchParams p) {
       if (tid < d) s_ub[tid] = mean32[tid];
       __syncthreads();
       switch (in.shape) {
-        case 0: batch_tile<4, 1, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
-        case 1: batch_tile<4, 2, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
-        case 2: batch_tile<4, 4, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
-        case 3: batch_tile<4, 8, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
-        case 4: batch_tile<4, 16, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
+        case 0: batch_tile_t<4, 1, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
+        case 1: batch_tile_t<4, 2, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
+        case 2: batch_tile_t<4, 4, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
+        case 3: batch_tile_t<4, 8, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
+        case 4: batch_tile_t<4, 16, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
         case 5: batch_tile<1, 2, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
         case 6: batch_tile<1, 8, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
         case 7: batch_tile<1, 32, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
