@@ -37,7 +37,7 @@ struct MultiLauncher {
   cudaStream_t stream;
   template <int VW, int LPP, int NCH>
   cudaError_t go() {
-    constexpr int U = Unroll<VW, NCH>::value;
+    constexpr int U = K >= 8 ? 2 : Unroll<VW, NCH>::value;  // fewer points in flight, more warps (see the kernel)
     auto kern = ses_multi_kernel<float, VW, LPP, NCH, U, K>;
     const int dp = dpad4(p.d);
     const int wst = K * ses_partial_stride(p.d);

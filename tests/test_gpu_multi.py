@@ -36,15 +36,21 @@ def test_candidates_follow_their_own_oracle_trajectories(n, d, k, radii):
         m.step(a_dev, e_dev, out=outs[t])
     torch.cuda.synchronize()
     recs = [api.decode_steps(o) for o in outs]
-    tol = RTOL * D
     for j in range(k):
+        # Every step carries FP32 rounding of about 6e-8 D, which the
+        # trajectory itself may amplify (measured here on the oracle by moving
+        # ubar^2 by 1e-7 D); the bound is the larger of the usual tolerance and
+        # T * 6e-8 D * amplification (equal to the usual one for all but the
+        # ill-conditioned candidates).
+        amp = _amplification(V, g, alphas[j], eta, rho, T)
+        tol = max(RTOL * D, T * 6e-8 * amp * D)
         ubar, stopped_at = V[0].copy(), None
         for t in range(T):
             o = oses.ses_step(V, g, ubar, t, alphas[j], eta, rho)
             r = recs[t][j]
             assert r["status"] == 0
             for key in ("objective", "oracle_value", "lower_bound"):
-                assert abs(r[key] - o[key]) <= tol, (j, t, key, r[key], o[key])
+                assert abs(r[key] - o[key]) <= tol, (j, t, key, r[key], o[key], amp)
             if abs(o["oracle_value"]) > tol:
                 assert bool(r["failed"]) == o["failed"], (j, t)
             if o["failed"]:
@@ -53,14 +59,9 @@ def test_candidates_follow_their_own_oracle_trajectories(n, d, k, radii):
             ubar = o["ubar_next"]
         if stopped_at is not None:
             assert all(recs[t][j]["t"] == 0 for t in range(stopped_at + 1, T))  # no record after the stop
-        # The final mean carries every step's FP32 rounding (about 6e-8 D per
-        # step) times the trajectory's own amplification, measured here on the
-        # oracle by moving ubar^2 by 1e-7 D; the bound is the larger of the
-        # usual tolerance and T * 6e-8 D * amplification.
-        amp = _amplification(V, g, alphas[j], eta, rho, T)
         mean, _ = m.read(j)
         err = np.linalg.norm(mean.cpu().numpy().astype(np.float64) - ubar)
-        assert err <= max(tol, T * 6e-8 * amp * D), (j, err / D, amp)
+        assert err <= tol, (j, err / D, amp)
 
 
 def _amplification(V, g, alpha, eta, rho, T):
