@@ -261,6 +261,150 @@ __global__ void __launch_bounds__(kBlock) ses_bwd_step_kernel(BwdParams p) {
   bwd_prologue(p.s - 1, p.tape, d, rad, p.bw, p.grad);
 }
 
+// ses_bwd_step_kernel for rows of 16-byte chunks (at most 32 per row): NI
+// points per lane per round, their gradient rows loaded with them, and the
+// scalar work of each point (its exponentials, c_i, beta_i) done once, on the
+// lane that owns it after a reduce-scatter of the two partial dot products.
+template <int VW, int LPP, int NI>
+__global__ void __launch_bounds__(kBlock) ses_bwd_step_t_kernel(BwdParams p) {
+  using GS = GroupScatter<LPP, NI>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float2 s_scr[kMaxBlock];
+  __shared__ bool s_flag;
+  const StateHdr* hdr = reinterpret_cast<const StateHdr*>(p.state);
+  if (p.s >= hdr->t) return;  // the forward stopped before step s
+
+  const int d = p.d;
+  const int dp = dpad4(d);
+  const int nch = d / VW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / LPP, gl = lane % LPP;
+  constexpr int PPW = 32 / LPP;
+  constexpr int ROUND = PPW * NI;
+  const bool owner = (gl % GS::SHARE) == 0;
+  const bool has_chunk = gl < nch;
+  const float* ent = p.tape + (size_t)p.s * ses_tape_stride(d);
+  const float kr = ent[2], H = ent[3];
+  const float* ubar = ent + 4;
+  const float* Gbar = bwd_Gbar(p.bw, d);
+  const float Sbar = *bwd_Sbar(p.bw, d);
+  float ub[VW], gb[VW], acc[VW];
+#pragma unroll
+  for (int e = 0; e < VW; ++e) {
+    ub[e] = has_chunk ? ubar[gl * VW + e] : 0.f;
+    gb[e] = has_chunk ? Gbar[gl * VW + e] : 0.f;
+    acc[e] = 0.f;
+  }
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
+  for (int64_t base = gw * ROUND; base < p.n; base += nwarps * ROUND) {
+    float x[NI][VW], gr[NI][VW];
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const int64_t i = base + r * PPW + grp;
+      if (i < p.n && has_chunk) {
+        Chunk<float, VW>::load(p.pts + i * d, gl, x[r]);
+        const float4 g4 = *reinterpret_cast<const float4*>(p.grad + i * d + gl * VW);
+        gr[r][0] = g4.x; gr[r][1] = g4.y; gr[r][2] = g4.z; gr[r][3] = g4.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          x[r][e] = 0.f;
+          gr[r][e] = 0.f;
+        }
+      }
+    }
+    float p2[NI], pd[NI];
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      float a = 0.f, b = 0.f;
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        x[r][e] -= ub[e];  // delta_i = v_i - ubar
+        a = fmaf(x[r][e], x[r][e], a);
+        b = fmaf(gb[e], x[r][e], b);
+      }
+      p2[r] = has_chunk ? a : 0.f;
+      pd[r] = has_chunk ? b : 0.f;
+    }
+    GS::run(p2, gl);
+    GS::run(pd, gl);
+    float cown[GS::OWN], bown[GS::OWN];
+#pragma unroll
+    for (int k = 0; k < GS::OWN; ++k) {
+      const int64_t i = base + GS::owned(gl, k) * PPW + grp;
+      cown[k] = 0.f;
+      bown[k] = 0.f;
+      if (i >= 1 && i < p.n) {
+        const float dist = sqrtf(p2[k]);
+        const float gam = p.radii ? __ldg(p.radii + i) : 0.f;
+        const float E1 = expf(kr * ((dist + gam) - H));
+        const float em = -expm1f(-2.f * kr * dist);
+        const float dif = E1 * em;
+        const float sum = E1 * (2.f - em);
+        if (dist > 0.f) {
+          const float rd = 1.0f / dist;
+          const float c = dif * rd;
+          cown[k] = c;
+          bown[k] = (pd[k] * (kr * sum - c) * rd + Sbar * kr * dif) * rd;
+        } else {
+          cown[k] = 2.f * kr * E1;
+        }
+      }
+    }
+    (void)owner;
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const int src = grp * LPP + GS::src_lane(r);
+      const float cr = __shfl_sync(0xffffffffu, cown[r % GS::OWN], src);
+      const float br = __shfl_sync(0xffffffffu, bown[r % GS::OWN], src);
+      const int64_t i = base + r * PPW + grp;
+      float dd[VW];
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        dd[e] = fmaf(cr, gb[e], br * x[r][e]);
+        acc[e] += dd[e];
+      }
+      if (i >= 1 && i < p.n && has_chunk) {
+        float4 v;
+        v.x = gr[r][0] + dd[0]; v.y = gr[r][1] + dd[1]; v.z = gr[r][2] + dd[2]; v.w = gr[r][3] + dd[3];
+        *reinterpret_cast<float4*>(p.grad + i * d + gl * VW) = v;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = LPP; o < 32; o <<= 1)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+  float* sA = reinterpret_cast<float*>(smem_raw);  // [kWarps][dp]
+  if (grp == 0 && has_chunk)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) sA[warp * dp + gl * VW + e] = acc[e];
+  __syncthreads();
+  const int st = ses_partial_stride(d);
+  float* prow = p.partials + (size_t)blockIdx.x * st;
+  for (int j = threadIdx.x; j < dp; j += kBlock) {
+    float sum = 0.f;
+    if (j < d)
+      for (int w = 0; w < kWarps; ++w) sum += sA[w * dp + j];
+    prow[4 + j] = sum;
+  }
+  if (threadIdx.x < 4) prow[threadIdx.x] = 0.f;
+
+  auto opof = [](int) { return 0; };
+  if (!arrive_pass(p.partials, st, p.grows, p.counter, s_scr, &s_flag, opof, p.single)) return;
+  float2* raw = reinterpret_cast<float2*>(smem_raw);
+  float* stage = reinterpret_cast<float*>(raw + st);
+  final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single, -1, -1, st);
+  if (threadIdx.x >= 32) return;
+  double* B = bwd_B(p.bw);
+  const double keep = (double)p.s / (double)(p.s + 1);
+  for (int j = lane; j < d; j += 32) B[j] = keep * B[j] - ((double)raw[4 + j].x + (double)raw[4 + j].y);
+  __syncwarp();
+  const float rad = (float)(p.alpha - (p.radii ? (double)__ldg(p.radii) : 0.0));
+  bwd_prologue(p.s - 1, p.tape, d, rad, p.bw, p.grad);
+}
+
 // argmax_i dist(ubar^T, v_i) + gamma_i over every row (v_1 included): one
 // candidate (value, smallest index) per CTA.
 template <int VW, int LPP, int NCH, int U>
@@ -564,6 +708,138 @@ __global__ void __launch_bounds__(kBlock) svm_bwd_step_kernel(BwdParams p) {
         for (int e = 0; e < VW; ++e) sA[warp * dp + c * VW + e] = acc[j][e];
     }
   }
+  __syncthreads();
+  const int st = ses_partial_stride(d);  // [0, 0, 0, 0, sum_i beta_i x_i]
+  float* prow = p.partials + (size_t)blockIdx.x * st;
+  for (int j = threadIdx.x; j < dp; j += kBlock) {
+    float sum = 0.f;
+    if (j < d)
+      for (int w = 0; w < kWarps; ++w) sum += sA[w * dp + j];
+    prow[4 + j] = sum;
+  }
+  if (threadIdx.x < 4) prow[threadIdx.x] = 0.f;
+
+  auto opof = [](int) { return 0; };
+  if (!arrive_pass(p.partials, st, p.grows, p.counter, s_scr, &s_flag, opof, p.single)) return;
+  float2* raw = reinterpret_cast<float2*>(smem_raw);
+  float* stage = reinterpret_cast<float*>(raw + st);
+  final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single, -1, -1, st);
+  if (threadIdx.x >= 32) return;
+  double* B = bwd_B(p.bw);
+  const double keep = (double)p.s / (double)(p.s + 1);
+  for (int j = lane; j < d; j += 32) B[j] = keep * B[j] + ((double)raw[4 + j].x + (double)raw[4 + j].y);
+  __syncwarp();
+  if (p.s >= 1) svm_bwd_prologue(p.s - 1, p.tape, d, p.bw);
+}
+
+// svm_bwd_step_kernel for rows of 16-byte chunks (at most 32 per row), in
+// the form of ses_bwd_step_t_kernel: NI points per lane per round with their
+// gradient rows, the scalar work once per point after a reduce-scatter of
+// the two partial dot products.
+template <int VW, int LPP, int NI>
+__global__ void __launch_bounds__(kBlock) svm_bwd_step_t_kernel(BwdParams p) {
+  using GS = GroupScatter<LPP, NI>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float2 s_scr[kMaxBlock];
+  __shared__ bool s_flag;
+  const StateHdr* hdr = reinterpret_cast<const StateHdr*>(p.state);
+  if (p.s >= hdr->t) return;  // the forward stopped before step s
+
+  const int d = p.d;
+  const int dp = dpad4(d);
+  const int nch = d / VW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / LPP, gl = lane % LPP;
+  constexpr int PPW = 32 / LPP;
+  constexpr int ROUND = PPW * NI;
+  const bool has_chunk = gl < nch;
+  const float* ent = p.tape + (size_t)p.s * svm_tape_stride(d);
+  const float k = ent[2], Hm = ent[3], s1 = ent[4], s2 = ent[5];
+  const float* wbar = ent + 8;
+  const float* zeta = bwd_Gbar(p.bw, d);
+  const float Sbar = *bwd_Sbar(p.bw, d);
+  float wb[VW], zt[VW], acc[VW];
+#pragma unroll
+  for (int e = 0; e < VW; ++e) {
+    wb[e] = has_chunk ? wbar[gl * VW + e] : 0.f;
+    zt[e] = has_chunk ? zeta[gl * VW + e] : 0.f;
+    acc[e] = 0.f;
+  }
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
+  for (int64_t base = gw * ROUND; base < p.n; base += nwarps * ROUND) {
+    float x[NI][VW], gr[NI][VW];
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const int64_t i = base + r * PPW + grp;
+      if (i < p.n && has_chunk) {
+        Chunk<float, VW>::load(p.pts + i * d, gl, x[r]);
+        const float4 g4 = *reinterpret_cast<const float4*>(p.grad + i * d + gl * VW);
+        gr[r][0] = g4.x; gr[r][1] = g4.y; gr[r][2] = g4.z; gr[r][3] = g4.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          x[r][e] = 0.f;
+          gr[r][e] = 0.f;
+        }
+      }
+    }
+    float pw[NI], pz[NI];
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      float a = 0.f, b = 0.f;
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        a = fmaf(x[r][e], wb[e], a);
+        b = fmaf(x[r][e], zt[e], b);
+      }
+      pw[r] = a;
+      pz[r] = b;
+    }
+    GS::run(pw, gl);
+    GS::run(pz, gl);
+    float yown[GS::OWN], bown[GS::OWN];  // pt_i y_i and beta_i of the owned points
+#pragma unroll
+    for (int kk = 0; kk < GS::OWN; ++kk) {
+      const int64_t i = base + GS::owned(gl, kk) * PPW + grp;
+      yown[kk] = 0.f;
+      bown[kk] = 0.f;
+      if (i < p.n) {
+        const bool pos = __ldg(p.labels + i) > 0;
+        const float margin = pos ? pw[kk] - s1 : -pw[kk] - s2;
+        const float pt = expf(-k * (margin - Hm));
+        const float y = pos ? 1.f : -1.f;
+        yown[kk] = pt * y;
+        bown[kk] = -k * pt * (pz[kk] + y * Sbar);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const int src = grp * LPP + GS::src_lane(r);
+      const float py = __shfl_sync(0xffffffffu, yown[r % GS::OWN], src);
+      const float br = __shfl_sync(0xffffffffu, bown[r % GS::OWN], src);
+      const int64_t i = base + r * PPW + grp;
+      float dd[VW];
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        dd[e] = fmaf(py, zt[e], br * wb[e]);
+        acc[e] = fmaf(br, x[r][e], acc[e]);
+      }
+      if (i < p.n && has_chunk) {
+        float4 v;
+        v.x = gr[r][0] + dd[0]; v.y = gr[r][1] + dd[1]; v.z = gr[r][2] + dd[2]; v.w = gr[r][3] + dd[3];
+        *reinterpret_cast<float4*>(p.grad + i * d + gl * VW) = v;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = LPP; o < 32; o <<= 1)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+  float* sA = reinterpret_cast<float*>(smem_raw);  // [kWarps][dp]
+  if (grp == 0 && has_chunk)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) sA[warp * dp + gl * VW + e] = acc[e];
   __syncthreads();
   const int st = ses_partial_stride(d);  // [0, 0, 0, 0, sum_i beta_i x_i]
   float* prow = p.partials + (size_t)blockIdx.x * st;

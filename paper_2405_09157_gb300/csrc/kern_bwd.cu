@@ -10,14 +10,21 @@ struct BwdStepLauncher {
   cudaStream_t stream;
   template <int VW, int LPP, int NCH>
   cudaError_t go() {
-    constexpr int U = Unroll<VW, NCH>::value;
-    auto kern = ses_bwd_step_kernel<VW, LPP, NCH, U>;
+    if constexpr (VW > 1 && NCH == 1) {  // 16-byte chunk rows: the reduce-scatter form
+      constexpr int NI = RoundSize<VW, LPP>::value < 8 ? RoundSize<VW, LPP>::value : 8;
+      return run(ses_bwd_step_t_kernel<VW, LPP, NI>, (32 / LPP) * NI * kWarps);
+    } else {
+      constexpr int U = Unroll<VW, NCH>::value;
+      return run(ses_bwd_step_kernel<VW, LPP, NCH, U>, (32 / LPP) * U * kWarps);
+    }
+  }
+  template <typename Kern>
+  cudaError_t run(Kern kern, int per_step) {
     const int dp = dpad4(p.d);
     const int st = ses_partial_stride(p.d);
     const size_t pass_smem = (size_t)kWarps * dp * sizeof(float);
     const size_t fin_base = (size_t)st * sizeof(float2);
     size_t smem = pass_smem > fin_base ? pass_smem : fin_base;
-    const int per_step = (32 / LPP) * U * kWarps;
     int grid = pass_grid(kern, smem, p.n, per_step);
     BwdParams q = p;
     q.single = single_level(grid, st, kStageBytesManyCta) ? 1 : 0;
@@ -54,14 +61,22 @@ struct SvmBwdStepLauncher {
   cudaStream_t stream;
   template <int VW, int LPP, int NCH>
   cudaError_t go() {
-    constexpr int U = Unroll<VW, NCH>::value;
-    auto kern = svm_bwd_step_kernel<VW, LPP, NCH, U>;
+    if constexpr (VW > 1 && NCH == 1) {  // 16-byte chunk rows: the reduce-scatter form
+      constexpr int NI = RoundSize<VW, LPP>::value < 8 ? RoundSize<VW, LPP>::value : 8;
+      return run(svm_bwd_step_t_kernel<VW, LPP, NI>, (32 / LPP) * NI * kWarps);
+    } else {
+      constexpr int U = Unroll<VW, NCH>::value;
+      return run(svm_bwd_step_kernel<VW, LPP, NCH, U>, (32 / LPP) * U * kWarps);
+    }
+  }
+  template <typename Kern>
+  cudaError_t run(Kern kern, int per_step) {
     const int dp = dpad4(p.d);
     const int st = ses_partial_stride(p.d);
     const size_t pass_smem = (size_t)kWarps * dp * sizeof(float);
     const size_t fin_base = (size_t)st * sizeof(float2);
     size_t smem = pass_smem > fin_base ? pass_smem : fin_base;
-    int grid = pass_grid(kern, smem, p.n, (32 / LPP) * U * kWarps);
+    int grid = pass_grid(kern, smem, p.n, per_step);
     BwdParams q = p;
     q.single = single_level(grid, st, kStageBytesManyCta) ? 1 : 0;
     if (q.single) {
