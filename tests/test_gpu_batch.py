@@ -153,3 +153,44 @@ def test_batch_autotune_and_budget():
         assert reps[k]["status"] == 5 and reps[k]["iters"] <= 50
         f = oses.ses_objective(a.astype(np.float64), None, centres[k].astype(np.float64))
         assert f <= reps[k]["upper_bound"] * (1 + 1e-5)
+
+
+def test_batch_full_workload_sampled_instances():
+    """The 4096-instance workload in the benchmarked launch configuration
+    (tile size from the autotuner): three iterations of every instance, then
+    eight sampled instances (the largest of each d and two random ones)
+    against their own FP64 oracle trajectories on the same points."""
+    import bench
+    dev = torch.device("cuda")
+    pts, offs, n, d, scale = bench.batched_inputs(dev)
+    batch = api.SesBatch(pts, offs, n, d, tile_rows=4096)
+    batch.autotune()
+    alpha = 2.0 * scale * (np.sqrt(d) + 6.0)
+    eor = 0.01 / (3.0 * alpha / np.sqrt(2.0))
+    a_dev = torch.tensor(alpha, dtype=torch.float64, device=dev)
+    e_dev = torch.tensor(eor, dtype=torch.float64, device=dev)
+    T = 3
+    outs = [api.new_steps(len(n), dev) for _ in range(T)]
+    for t in range(T):
+        batch.step(a_dev, e_dev, out=outs[t])
+    torch.cuda.synchronize()
+    recs = [api.decode_steps(o) for o in outs]
+    means, _ = batch.read()
+    rng = np.random.default_rng(0)
+    picks = [int(np.flatnonzero(d == dd)[np.argmax(n[d == dd])]) for dd in (2, 3, 8, 16, 32, 64)]
+    picks += [int(x) for x in rng.choice(len(n), 2, replace=False)]
+    for k in picks:
+        V = pts[offs[k]:offs[k] + n[k] * d[k]].view(int(n[k]), int(d[k])).cpu().numpy().astype(np.float64)
+        D = oses.ses_D(V)
+        rho = oses.ses_width(D)
+        eta = eor[k] * rho  # the same eta/rho
+        ubar = V[0].copy()
+        tol = RTOL * D
+        for t in range(T):
+            o = oses.ses_step(V, None, ubar, t, alpha[k], eta, rho)
+            r = recs[t][k]
+            assert r["status"] == 0 and r["t"] == t + 1, (k, t)
+            for key in ("objective", "oracle_value", "lower_bound"):
+                assert abs(r[key] - o[key]) <= tol, (k, int(n[k]), int(d[k]), t, key, r[key], o[key])
+            ubar = o["ubar_next"]
+        assert np.linalg.norm(means[k].astype(np.float64) - ubar) <= tol, k

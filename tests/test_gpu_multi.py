@@ -103,3 +103,30 @@ def test_candidates_match_single_candidate_steps():
         assert rm[j]["t"] == rs[j]["t"]
         for key in ("objective", "oracle_value", "lower_bound"):
             assert abs(rm[j][key] - rs[j][key]) <= 2 * RTOL * D, (j, key)
+
+
+def test_full_size_k8_against_oracle():
+    """The benchmarked multi-candidate configuration (n = 1e6, d = 32, k = 8):
+    three iterations of every candidate against the FP64 oracle."""
+    V32 = datagen.ses_gaussian(1_000_000, 32, seed=0)
+    V = V32.astype(np.float64)
+    D = oses.ses_D(V)
+    rho = oses.ses_width(D)
+    k, T, eta = 8, 3, 0.5
+    alphas = np.array([(0.7 + 0.05 * j) * D for j in range(k)])
+    m = api.MultiMWU(torch.from_numpy(V32).cuda(), k)
+    a_dev = torch.tensor(alphas, dtype=torch.float64, device="cuda")
+    e_dev = torch.full((k,), eta / rho, dtype=torch.float64, device="cuda")
+    outs = [api.new_steps(k) for _ in range(T)]
+    for t in range(T):
+        m.step(a_dev, e_dev, out=outs[t])
+    torch.cuda.synchronize()
+    recs = [api.decode_steps(o) for o in outs]
+    tol = RTOL * D
+    for j in range(k):
+        ubar = V[0].copy()
+        for t in range(T):
+            o = oses.ses_step(V, None, ubar, t, alphas[j], eta, rho)
+            for key in ("objective", "oracle_value", "lower_bound"):
+                assert abs(recs[t][j][key] - o[key]) <= tol, (j, t, key)
+            ubar = o["ubar_next"]
