@@ -414,12 +414,14 @@ pdscp_status mwu_shard_partial(int32_t problem, const void* pts, int32_t dtype, 
   float2* row = reinterpret_cast<float2*>(row_out);
   cudaError_t e;
   if (problem == PDSCP_SES) {
+    // the same warp split as mwu_step (its warm-up warps streaming nothing), so that one shard reproduces
+    // the unsharded iteration bit for bit
     SesParams p{pts, radii, n, d, eval_only, alpha, eta_over_rho, st_rw, partials, grows, counter, 0, nullptr,
-                holds_first ? 1 : 0, row, nullptr, nullptr};
+                holds_first ? 1 : 0, row, nullptr, reinterpret_cast<unsigned char*>(ws) + L.sink};
     e = launch_ses(p, dtype, vec, (cudaStream_t)stream);
   } else {
     SvmParams p{pts, labels, n, d, eval_only, alpha, eta_over_rho, D, st_rw, partials, grows, counter, 0, nullptr, row,
-                nullptr, nullptr};
+                reinterpret_cast<unsigned char*>(ws) + L.sink, nullptr};
     e = launch_svm(p, dtype, vec, (cudaStream_t)stream);
   }
   if (e != cudaSuccess) return cuda_fail(e, "mwu_shard_partial launch");

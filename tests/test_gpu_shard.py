@@ -178,3 +178,23 @@ def test_svm_sharded_trajectory_matches_oracle(G, dtype):
     mean, _ = sh.read()
     assert np.linalg.norm(mean[:16] - wbar) <= RTOL
     assert abs(mean[16] - s1) <= tol and abs(mean[17] - s2) <= tol
+
+
+def test_sharded_mwu_single_rank_is_bit_identical_to_mwu_step():
+    """ShardedMWU on one rank (no process group): the shard pass writes its
+    totals and the merge finishes from them, exactly as the fused kernel."""
+    V32 = datagen.ses_gaussian(200_000, 32, seed=2)
+    pts = _cuda(V32)
+    D = oses.ses_D(V32.astype(np.float64))
+    rho = oses.ses_width(D)
+    sh = api.ShardedMWU(_ffi.SES, pts, pts[0].contiguous(), 0, 1)
+    one = api.MWU(_ffi.SES, pts)
+    out_s, out_1 = api.new_steps(30), api.new_steps(30)
+    for t in range(30):
+        sh.step(0.9 * D, 0.5 / rho, out=out_s[t])
+        one.step(0.9 * D, 0.5 / rho, out=out_1[t])
+    torch.cuda.synchronize()
+    assert torch.equal(out_s, out_1)
+    ms, _ = sh.read()
+    m1, _ = one.read()
+    assert torch.equal(ms, m1)
