@@ -414,7 +414,10 @@ __device__ void batch_tile_t(const float* pts, int d, int64_t r0, int64_t r1, co
   }
 }
 
-__global__ void __launch_bounds__(kBatchBlock) ses_batch_kernel(BatchParams p) {
+// Three CTAs per SM: left free, the compiler gave this kernel 111 registers
+// (two CTAs per SM); bounded, it needs 78 with no spill, and the extra warps
+// raise the batched iteration from 4.9 to 5.9 TB/s.
+__global__ void __launch_bounds__(kBatchBlock, 3) ses_batch_kernel(BatchParams p) {
   __shared__ float sG[kBatchWarps * kBatchMaxD];
   __shared__ float s_sc[kBatchWarps][3];
   __shared__ float s_ub[kBatchMaxD];
