@@ -38,13 +38,13 @@ struct MultiParams {
   pdscp_step_out* out;          // k records, may be null
 };
 
-// At least two CTAs per SM from K = 4 on: with one (the register count of K
-// means and K weighted sums per lane), the pass has 2 warps per scheduler
-// and stalls on instruction latency. K = 8 also keeps 2 points in flight per
-// lane group instead of 4 to fit (measured at n = 1e6, d = 32: K = 8 132 ->
-// 118 us per pass).
+// CTAs per SM: at least two from K = 4 on (with one, the register count of K
+// means and K weighted sums per lane leaves 2 warps per scheduler and the
+// pass stalls on instruction latency; K = 8 also keeps 2 points in flight
+// per lane group instead of 4 to fit), three below (no spill either way).
+// Measured at n = 1e6, d = 32: K = 8 132 -> 118 us per pass, K = 2 67 -> 64 us.
 template <typename T, int VW, int LPP, int NCH, int U, int K>
-__global__ void __launch_bounds__(kBlock, (K >= 4 ? 2 : 1)) ses_multi_kernel(MultiParams p) {
+__global__ void __launch_bounds__(kBlock, (K >= 4 ? 2 : 3)) ses_multi_kernel(MultiParams p) {
   using GS = GroupScatter<LPP, K>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float s_sc[kWarps][K][3];
