@@ -90,4 +90,4 @@ def ses_unrolled_radius_grad(V, gamma, alpha, eta_over_rho, T):
     Vt = torch.tensor(np.asarray(V, dtype=np.float64), requires_grad=True)
     L, _, steps = ses_unrolled_radius(Vt, gamma, alpha, eta_over_rho, T)
     L.backward()
-    return float(L), Vt.grad.numpy().copy(), steps
+    return float(L.detach()), Vt.grad.numpy().copy(), steps
