@@ -33,10 +33,14 @@ OUT_FEASIBLE = "feasible"        # T iterations without separation (Theorem 2)
 OUT_BELOW_ALPHA = "below_alpha"  # f^t < alpha: affirmative early exit (Sec. 5)
 OUT_STALLED = "stalled"          # |f^t - f^{t-1}|/f^{t-1} < delta, patience times (Sec. 5)
 OUT_FIXED = "fixed"              # FIXED_ITERS mode ran its T iterations
+OUT_CERTIFIED = "certified"      # CERTIFIED mode: the certificates closed at a poll
 
 MODE_PRACTICAL = "practical"
 MODE_THEORY = "theory"
 MODE_FIXED = "fixed"
+MODE_CERTIFIED = "certified"
+OUT_STUCK = "stuck"              # CERTIFIED mode: the certificate gap stopped shrinking (eta is halved)
+CERT_FIRST_CHECK = 1024          # CERTIFIED: first progress check of an alpha-FTP (then at 2x, 4x, ...)
 
 
 def _prep(V, gamma):
@@ -164,13 +168,75 @@ def ses_objective(V, gamma, c):
     return float(np.max(np.sqrt(np.sum((V - np.asarray(c)[None, :]) ** 2, axis=1)) + gm))
 
 
-def ses_step(V, gamma, ubar, t, alpha, eta, rho):
+def ses_qp_weights(V, gamma, ubar, P, k):
+    """kappa_i >= 0 with w_i = kappa_i (v_i - ubar), i >= 2: the coefficient of
+    each point in the ORACLE's g = sum_i w_i (Eq. ses_oracle).
+
+    The vector part of exp(X_i) points along x_i = k (v_i - ubar) (Sec. 2.1:
+    exp keeps the eigenvectors), so kappa_i = w_i . (v_i - ubar) / dist_i^2.
+    Where v_i sits at the mean (dist_i = 0) w_i vanishes; kappa_i is then its
+    limit k s_i / sqrt2 as dist_i -> 0 (lambda_1 - lambda_2 = sqrt2 k dist_i).
+    """
+    V, gm = _prep(V, gamma)
+    R = V[1:] - np.asarray(ubar, dtype=np.float64)[None, :]
+    dist2 = np.sum(R * R, axis=1)
+    w, s = P[:, :-1], P[:, -1]
+    kap = np.empty(R.shape[0])
+    pos = dist2 > 0.0
+    kap[pos] = np.sum(w[pos] * R[pos], axis=1) / dist2[pos]
+    kap[~pos] = k * s[~pos] / SQRT2
+    return kap
+
+
+def ses_qp_moments(V, kap):
+    """(A, B) of the weights mu = kappa / sum kappa over the points i >= 2,
+    taken about v_1: A = sum_i mu_i |v_i - v_1|^2, B = sum_i mu_i (v_i - v_1).
+
+    The QP of Sec. 5 (Eq. ses_qp) maximises, over the simplex, -(y^T y -
+    sum_i x_i v_i^T v_i) with y = sum_i x_i v_i, whose optimum is OPT^2 for
+    points; every simplex x therefore gives OPT^2 >= A - |B|^2 (the value is
+    unchanged by the shift to v_1). None when sum kappa = 0 (t = 0: k = 0).
+    """
+    V = np.asarray(V, dtype=np.float64)
+    tot = float(np.sum(kap))
+    if not tot > 0.0:
+        return None
+    mu = kap / tot
+    Z = V[1:] - V[0][None, :]
+    return float(mu @ np.sum(Z * Z, axis=1)), mu @ Z
+
+
+def ses_dual_update(avg, t, moments):
+    """Running average of the QP moments over an alpha-FTP, iterate t weighted
+    by t (so the early, nearly uniform weights fade): avg = {"A", "B", "wsum"}.
+    Returns the lower bound sqrt(max(Abar - |Bbar|^2, 0)) (0 before any update).
+    The averaged weights are again a point of the simplex, so the bound holds.
+    """
+    if moments is not None and t >= 1:
+        A, B = moments
+        avg["wsum"] += float(t)
+        r = float(t) / avg["wsum"]
+        avg["A"] += r * (A - avg["A"])
+        avg["B"] = avg["B"] + r * (B - avg["B"])
+    if avg["wsum"] == 0.0:
+        return 0.0
+    return math.sqrt(max(avg["A"] - float(avg["B"] @ avg["B"]), 0.0))
+
+
+def ses_dual_state(d):
+    return {"A": 0.0, "B": np.zeros(d), "wsum": 0.0}
+
+
+def ses_step(V, gamma, ubar, t, alpha, eta, rho, avg=None):
     """One iteration of the alpha-FTP (Sec. 3, Theorem 2) for SES.
 
     ``t`` oracle calls have completed and ``ubar`` is the mean of their u's (any
     value when t = 0). Computes p^{t+1} (Eq. implement with k = eta t/rho), the
     ORACLE answer, the primal lower bound and f at ubar. If the ORACLE succeeds
-    the mean is advanced to ubar^{t+1}. Returns a dict record.
+    the mean is advanced to ubar^{t+1}. ``avg`` (points only; from
+    :func:`ses_dual_state`) is advanced by this iteration's QP moments and
+    rec["dual_bound"] is the averaged QP lower bound (0 for spheres). Returns a
+    dict record.
     """
     V, gm = _prep(V, gamma)
     k = eta * t / rho
@@ -185,7 +251,10 @@ def ses_step(V, gamma, ubar, t, alpha, eta, rho):
         "u": u,
         "g": g,
         "failed": value < 0.0,
+        "dual_bound": 0.0,
     }
+    if avg is not None and not np.any(gm):
+        rec["dual_bound"] = ses_dual_update(avg, t, ses_qp_moments(V, ses_qp_weights(V, gm, ubar, P, k)))
     if value >= 0.0:
         rec["ubar_next"] = np.asarray(ubar, dtype=np.float64) + (u - ubar) / (t + 1)
     else:
@@ -195,7 +264,7 @@ def ses_step(V, gamma, ubar, t, alpha, eta, rho):
 
 # ------------------------------------------------------------ the alpha-FTP
 def ses_ftp(V, gamma, alpha, eta, rho, T, mode=MODE_FIXED, delta=1e-4, patience=10,
-            keep_trace=False):
+            keep_trace=False, cert=None):
     """alpha-feasibility test of Theorem 2 for SES, run for at most T iterations.
 
     Modes: FIXED runs exactly T iterations unless the ORACLE separates;
@@ -203,35 +272,44 @@ def ses_ftp(V, gamma, alpha, eta, rho, T, mode=MODE_FIXED, delta=1e-4, patience=
     when T is the theorem's count); PRACTICAL adds the two rules of Sec. 5:
     stop with an affirmative answer as soon as f^t < alpha, and stop when
     |f^t - f^{t-1}|/f^{t-1} < delta for ``patience`` consecutive iterations
-    (the ratio is skipped when f^{t-1} = 0).
+    (the ratio is skipped when f^{t-1} = 0). CERTIFIED keeps the first rule
+    only (f^t < alpha proves OPT < alpha) and, every cert["poll_every"]
+    completed iterations, stops once the certificates close:
+    min(cert["ub"], f_best) <= (1 + cert["eps"]) max(cert["lb"], lb_best),
+    or as STUCK when, at the first poll with t >= 1024, 2048, 4096, ..., the
+    FTP's own gap f_best / lb_best - 1 has not halved since the previous such
+    poll (the first check compares with infinity, so it never stops there).
     Returns a dict with the outcome, the iteration count, the final mean, the
-    best enclosing ball seen (c_best, f_best), the best primal lower bound and,
-    if asked, the per-iteration records.
+    best enclosing ball seen (c_best, f_best), the best lower bound (primal
+    construction or, for points, the averaged QP bound) and, if asked, the
+    per-iteration records.
     """
     V, gm = _prep(V, gamma)
     ubar = V[0].copy()
     f_best, c_best = math.inf, ubar.copy()
     lb_best = 0.0
+    avg = ses_dual_state(V.shape[1])
     trace = []
     f_prev, streak = None, 0
     outcome = OUT_FIXED if mode == MODE_FIXED else OUT_FEASIBLE
+    last_gap, next_check = math.inf, CERT_FIRST_CHECK
     t = 0
     while t < T:
-        rec = ses_step(V, gm, ubar, t, alpha, eta, rho)
+        rec = ses_step(V, gm, ubar, t, alpha, eta, rho, avg=avg)
         if keep_trace:
             trace.append(rec)
         if t > 0 and rec["objective"] < f_best:
             f_best, c_best = rec["objective"], ubar.copy()
-        lb_best = max(lb_best, rec["lower_bound"])
+        lb_best = max(lb_best, rec["lower_bound"], rec["dual_bound"])
         if rec["failed"]:
             outcome = OUT_SEPARATED
             break
-        if mode == MODE_PRACTICAL and t > 0:
+        if mode in (MODE_PRACTICAL, MODE_CERTIFIED) and t > 0:
             f = rec["objective"]
             if f < alpha:
                 outcome = OUT_BELOW_ALPHA
                 break
-            if f_prev is not None and f_prev > 0.0:
+            if mode == MODE_PRACTICAL and f_prev is not None and f_prev > 0.0:
                 streak = streak + 1 if abs(f - f_prev) / f_prev < delta else 0
                 if streak >= patience:
                     outcome = OUT_STALLED
@@ -239,6 +317,16 @@ def ses_ftp(V, gamma, alpha, eta, rho, T, mode=MODE_FIXED, delta=1e-4, patience=
             f_prev = f
         ubar = rec["ubar_next"]
         t += 1
+        if mode == MODE_CERTIFIED and t % cert["poll_every"] == 0:
+            if min(cert["ub"], f_best) <= (1.0 + cert["eps"]) * max(cert["lb"], lb_best):
+                outcome = OUT_CERTIFIED
+                break
+            if t >= next_check:  # progress test: this FTP's own gap must halve while t doubles
+                gap = f_best / lb_best - 1.0 if lb_best > 0.0 else math.inf
+                if gap > 0.5 * last_gap:
+                    outcome = OUT_STUCK
+                    break
+                last_gap, next_check = gap, 2 * next_check
     f_end = ses_objective(V, gm, ubar)
     if t > 0 and f_end < f_best:
         f_best, c_best = f_end, ubar.copy()
@@ -248,7 +336,7 @@ def ses_ftp(V, gamma, alpha, eta, rho, T, mode=MODE_FIXED, delta=1e-4, patience=
 
 # ------------------------------------------------- feasibility -> optimisation
 def ses_solve(V, gamma=None, eps=1e-2, mode=MODE_PRACTICAL, max_iters=10**7,
-              delta=1e-4, patience=10, max_steps=200, eta=None):
+              delta=1e-4, patience=10, max_steps=200, eta=None, poll_every=256):
     """(1+eps)-approximate SES by the search of Sec. 3 over alpha in [D/2, D].
 
     Step i: alpha_i = L + (U-L)/3, eps_i = (U-L)/(3 alpha_i), T_i and eta_i from
@@ -267,7 +355,18 @@ def ses_solve(V, gamma=None, eps=1e-2, mode=MODE_PRACTICAL, max_iters=10**7,
     ``eta`` None uses eta_i = sqrt(ln r / T_i) of Theorem 2 in every step; a
     number fixes the step size (Theorem 1 allows any eta in (0, 1]; the
     guarantee of Theorem 2 then no longer applies, the certificates still do).
+
+    CERTIFIED mode draws only proven conclusions: separation gives L = alpha_i,
+    f^t < alpha_i gives U = f^t; nothing is concluded from a stall or from T_i.
+    Each alpha-FTP runs until one of those, or until the certificates close at
+    a poll (every ``poll_every`` iterations), and the loop ends only when
+    ub <= (1+eps) max(lb, L) or the budget is spent. Its step size is eta
+    (default 1, the largest Theorem 1 allows). The search range (L, U) is then
+    a certificate too and lower_bound reports max(lb, L).
     """
+    if mode == MODE_CERTIFIED:
+        return _ses_solve_certified(V, gamma, eps, max_iters, max_steps, 1.0 if eta is None else float(eta),
+                                    poll_every)
     V, gm = _prep(V, gamma)
     n = V.shape[0]
     D = ses_D(V, gm)
@@ -300,4 +399,38 @@ def ses_solve(V, gamma=None, eps=1e-2, mode=MODE_PRACTICAL, max_iters=10**7,
         if res["outcome"] not in (OUT_SEPARATED, OUT_STALLED, OUT_BELOW_ALPHA) and res["iters"] < T:
             break  # iteration budget exhausted inside the step
     return {"radius": ub, "center": center, "lower_bound": lb, "upper_bound": ub,
+            "iters": total, "steps": steps, "L": L, "U": U}
+
+
+def _ses_solve_certified(V, gamma, eps, max_iters, max_steps, eta, poll_every):
+    V, gm = _prep(V, gamma)
+    n = V.shape[0]
+    D = ses_D(V, gm)
+    rho = ses_width(D)
+    L, U = D / 2.0, D
+    lb, ub, center = 0.0, ses_objective(V, gm, V[0]), V[0].copy()
+    total, steps = 0, []
+    if D == 0.0:
+        return {"radius": ub, "center": center, "lower_bound": ub, "upper_bound": ub,
+                "iters": 0, "steps": steps, "L": 0.0, "U": 0.0}
+    while ub > (1.0 + eps) * max(lb, L) and total < max_iters and len(steps) < max_steps:
+        alpha = L + (U - L) / 3.0
+        cert = {"lb": max(lb, L), "ub": ub, "eps": eps, "poll_every": poll_every}
+        res = ses_ftp(V, gm, alpha, eta, rho, max_iters - total, mode=MODE_CERTIFIED, cert=cert)
+        total += res["iters"]
+        eta_used = eta
+        if res["outcome"] == OUT_STUCK:
+            eta *= 0.5  # smaller steps resolve alpha closer to OPT
+        if res["f_best"] < ub:
+            ub, center = res["f_best"], res["c_best"]
+        lb = max(lb, res["lb_best"])
+        if res["outcome"] == OUT_SEPARATED:
+            L = max(L, alpha)
+        U = min(U, ub)
+        L = max(L, lb)
+        steps.append({"alpha": alpha, "eta": eta_used, "outcome": res["outcome"], "iters": res["iters"],
+                      "L": L, "U": U})
+        if res["outcome"] not in (OUT_SEPARATED, OUT_BELOW_ALPHA, OUT_CERTIFIED, OUT_STUCK):
+            break  # iteration budget exhausted inside the step
+    return {"radius": ub, "center": center, "lower_bound": max(lb, L), "upper_bound": ub,
             "iters": total, "steps": steps, "L": L, "U": U}

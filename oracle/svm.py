@@ -38,10 +38,14 @@ OUT_FEASIBLE = "feasible"        # T iterations without separation
 OUT_ABOVE_ALPHA = "above_alpha"  # margin f^t > alpha: affirmative early exit (Sec. 5)
 OUT_STALLED = "stalled"
 OUT_FIXED = "fixed"
+OUT_CERTIFIED = "certified"      # CERTIFIED mode: the certificates closed at a poll
 
 MODE_PRACTICAL = "practical"
 MODE_THEORY = "theory"
 MODE_FIXED = "fixed"
+MODE_CERTIFIED = "certified"
+OUT_STUCK = "stuck"              # CERTIFIED mode: the certificate gap stopped shrinking (eta is halved)
+CERT_FIRST_CHECK = 1024          # CERTIFIED: first progress check of an alpha-FTP (then at 2x, 4x, ...)
 
 SVM_R = 2.0  # Sec. 4.2
 
@@ -121,14 +125,36 @@ def svm_program_value(X, y, p, w, s1, s2):
     return float(slack @ p)
 
 
-def svm_pd_value(X, y, p):
-    """Claim 8: (mu/Tr mu; gamma/Tr gamma) is PD-feasible; returns its PD objective
-    ||P mu/Tr mu - Q gamma/Tr gamma||, an upper bound on OPT (Eq. PD)."""
+def svm_pd_vector(X, y, p):
+    """P mu/Tr mu - Q gamma/Tr gamma for the weights p (Claim 8)."""
     X, y = _prep(X, y)
     mu = np.where(y > 0, p, 0.0)
     ga = np.where(y < 0, p, 0.0)
-    diff = X.T @ mu / np.sum(mu) - X.T @ ga / np.sum(ga)
+    return X.T @ mu / np.sum(mu) - X.T @ ga / np.sum(ga)
+
+
+def svm_pd_value(X, y, p):
+    """Claim 8: (mu/Tr mu; gamma/Tr gamma) is PD-feasible; returns its PD objective
+    ||P mu/Tr mu - Q gamma/Tr gamma||, an upper bound on OPT (Eq. PD)."""
+    diff = svm_pd_vector(X, y, p)
     return math.sqrt(float(diff @ diff))
+
+
+def svm_dual_state(d):
+    return {"z": np.zeros(d), "wsum": 0.0}
+
+
+def svm_dual_update(avg, t, z):
+    """Running average of the Claim 8 vectors over an alpha-FTP, iterate t
+    weighted by t: zbar is P mubar - Q gammabar for the averaged class-normalised
+    weights (each a point of its simplex), so |zbar| is again a PD-feasible
+    value, an upper bound on OPT. Returns |zbar| (inf before any update)."""
+    if t >= 1 and np.all(np.isfinite(z)):
+        avg["wsum"] += float(t)
+        avg["z"] = avg["z"] + (float(t) / avg["wsum"]) * (z - avg["z"])
+    if avg["wsum"] == 0.0:
+        return math.inf
+    return math.sqrt(float(avg["z"] @ avg["z"]))
 
 
 def svm_margin(X, y, wbar):
@@ -142,24 +168,30 @@ def svm_margin(X, y, wbar):
     return max((float(np.min(s[y > 0])) - float(np.max(s[y < 0]))) / nw, 0.0)
 
 
-def svm_step(X, y, wbar, s1bar, s2bar, t, alpha, eta, rho, D):
+def svm_step(X, y, wbar, s1bar, s2bar, t, alpha, eta, rho, D, avg=None):
     """One iteration of the minimisation alpha-FTP (Sec. 3, Theorem 3) for SVM.
 
     Computes p^{t+1} (k = eta t/rho), the ORACLE answer, the Claim 8 upper
     bound and the margin f at wbar; advances the means when the ORACLE succeeds.
+    ``avg`` (from :func:`svm_dual_state`) is advanced by this iteration's Claim 8
+    vector and rec["dual_bound"] is the averaged upper bound (inf without it).
     """
     X, y = _prep(X, y)
     k = eta * t / rho
     p = svm_weights(X, y, wbar, s1bar, s2bar, k)
     w, s1, s2, value, z, tr_mu, tr_ga = svm_oracle(X, y, p, alpha, D)
+    pd = svm_pd_vector(X, y, p)
     rec = {
         "t": t, "k": k,
         "objective": svm_margin(X, y, wbar),
         "oracle_value": value,
-        "upper_bound": svm_pd_value(X, y, p),
+        "upper_bound": math.sqrt(float(pd @ pd)),
         "w": w, "s1": s1, "s2": s2, "z": z, "tr_mu": tr_mu, "tr_gamma": tr_ga,
         "failed": value < 0.0,
+        "dual_bound": math.inf,
     }
+    if avg is not None:
+        rec["dual_bound"] = svm_dual_update(avg, t, pd)
     wbar = np.asarray(wbar, dtype=np.float64)
     if value >= 0.0:
         rec["wbar_next"] = wbar + (w - wbar) / (t + 1)
@@ -171,37 +203,46 @@ def svm_step(X, y, wbar, s1bar, s2bar, t, alpha, eta, rho, D):
 
 
 def svm_ftp(X, y, alpha, eta, rho, T, D, mode=MODE_FIXED, delta=1e-4, patience=10,
-            keep_trace=False):
+            keep_trace=False, cert=None):
     """Minimisation alpha-FTP of Theorem 3 for SVM, at most T iterations.
 
     Same modes as the SES test. PRACTICAL stops affirmatively once the margin
-    f^t exceeds alpha and on the delta/patience rule of Sec. 5.
+    f^t exceeds alpha and on the delta/patience rule of Sec. 5. CERTIFIED keeps
+    the first rule only (f^t > alpha proves OPT > alpha) and, every
+    cert["poll_every"] completed iterations, stops once
+    min(cert["ub"], ub_best) <= (1 + cert["eps"]) max(cert["lb"], f_best),
+    or as STUCK when, at the first poll with t >= 1024, 2048, 4096, ..., the
+    FTP's own gap ub_best / f_best - 1 has not halved since the previous such
+    poll. ub_best is the best of the per-iteration and the averaged Claim 8
+    values.
     """
     X, y = _prep(X, y)
     d = X.shape[1]
     wbar, s1bar, s2bar = np.zeros(d), 0.0, 0.0
     f_best, w_best = 0.0, np.zeros(d)
     ub_best = math.inf
+    avg = svm_dual_state(d)
     trace = []
     f_prev, streak = None, 0
     outcome = OUT_FIXED if mode == MODE_FIXED else OUT_FEASIBLE
+    last_gap, next_check = math.inf, CERT_FIRST_CHECK
     t = 0
     while t < T:
-        rec = svm_step(X, y, wbar, s1bar, s2bar, t, alpha, eta, rho, D)
+        rec = svm_step(X, y, wbar, s1bar, s2bar, t, alpha, eta, rho, D, avg=avg)
         if keep_trace:
             trace.append(rec)
         if rec["objective"] > f_best:
             f_best, w_best = rec["objective"], wbar.copy()
-        ub_best = min(ub_best, rec["upper_bound"])
+        ub_best = min(ub_best, rec["upper_bound"], rec["dual_bound"])
         if rec["failed"]:
             outcome = OUT_SEPARATED
             break
-        if mode == MODE_PRACTICAL and t > 0:
+        if mode in (MODE_PRACTICAL, MODE_CERTIFIED) and t > 0:
             f = rec["objective"]
             if f > alpha:
                 outcome = OUT_ABOVE_ALPHA
                 break
-            if f_prev is not None and f_prev > 0.0:
+            if mode == MODE_PRACTICAL and f_prev is not None and f_prev > 0.0:
                 streak = streak + 1 if abs(f - f_prev) / f_prev < delta else 0
                 if streak >= patience:
                     outcome = OUT_STALLED
@@ -209,6 +250,16 @@ def svm_ftp(X, y, alpha, eta, rho, T, D, mode=MODE_FIXED, delta=1e-4, patience=1
             f_prev = f
         wbar, s1bar, s2bar = rec["wbar_next"], rec["s1bar_next"], rec["s2bar_next"]
         t += 1
+        if mode == MODE_CERTIFIED and t % cert["poll_every"] == 0:
+            if min(cert["ub"], ub_best) <= (1.0 + cert["eps"]) * max(cert["lb"], f_best):
+                outcome = OUT_CERTIFIED
+                break
+            if t >= next_check:  # progress test: this FTP's own gap must halve while t doubles
+                gap = ub_best / f_best - 1.0 if f_best > 0.0 else math.inf
+                if gap > 0.5 * last_gap:
+                    outcome = OUT_STUCK
+                    break
+                last_gap, next_check = gap, 2 * next_check
     f_end = svm_margin(X, y, wbar)
     if f_end > f_best:
         f_best, w_best = f_end, wbar.copy()
@@ -217,14 +268,23 @@ def svm_ftp(X, y, alpha, eta, rho, T, D, mode=MODE_FIXED, delta=1e-4, patience=1
 
 
 def svm_solve(X, y, eps=1e-2, mode=MODE_PRACTICAL, max_iters=10**7, delta=1e-4,
-              patience=10, max_steps=200, eta=None):
+              patience=10, max_steps=200, eta=None, poll_every=256):
     """(1-eps)-approximate max margin by the search over alpha in (0, 2D] (Sec. 4.2).
 
     Certificates: lb = best margin f of an actual separating direction, ub =
     best Claim 8 PD value; the loop ends when U <= (1+eps) L, when
     ub <= (1+eps) lb, or when ``max_iters`` iterations have run. ``eta`` as in
     the SES search: None for Theorem 3's eta_i, a number to fix it.
+
+    CERTIFIED mode (as for SES): separation gives U = alpha_i, f^t > alpha_i
+    gives L = f^t, nothing else is concluded; each alpha-FTP runs until one of
+    those or until the certificates close at a poll, and the loop ends when
+    min(ub, U) <= (1+eps) lb or the budget is spent; eta defaults to 1 and
+    upper_bound reports min(ub, U).
     """
+    if mode == MODE_CERTIFIED:
+        return _svm_solve_certified(X, y, eps, max_iters, max_steps, 1.0 if eta is None else float(eta),
+                                    poll_every)
     X, y = _prep(X, y)
     n = X.shape[0]
     D = svm_D(X)
@@ -254,4 +314,34 @@ def svm_solve(X, y, eps=1e-2, mode=MODE_PRACTICAL, max_iters=10**7, delta=1e-4,
         if res["outcome"] not in (OUT_SEPARATED, OUT_STALLED, OUT_ABOVE_ALPHA) and res["iters"] < T:
             break
     return {"margin": lb, "w": w_best, "lower_bound": lb, "upper_bound": ub,
+            "iters": total, "steps": steps, "L": L, "U": U}
+
+
+def _svm_solve_certified(X, y, eps, max_iters, max_steps, eta, poll_every):
+    X, y = _prep(X, y)
+    D = svm_D(X)
+    rho = svm_width(D)
+    L, U = 0.0, 2.0 * D
+    lb, ub, w_best = 0.0, math.inf, np.zeros(X.shape[1])
+    total, steps = 0, []
+    while min(ub, U) > (1.0 + eps) * lb and total < max_iters and len(steps) < max_steps:
+        alpha = U - (U - L) / 3.0
+        cert = {"lb": lb, "ub": min(ub, U), "eps": eps, "poll_every": poll_every}
+        res = svm_ftp(X, y, alpha, eta, rho, max_iters - total, D, mode=MODE_CERTIFIED, cert=cert)
+        total += res["iters"]
+        eta_used = eta
+        if res["outcome"] == OUT_STUCK:
+            eta *= 0.5
+        if res["f_best"] > lb:
+            lb, w_best = res["f_best"], res["w_best"]
+        ub = min(ub, res["ub_best"])
+        if res["outcome"] == OUT_SEPARATED:
+            U = min(U, alpha)
+        U = min(U, ub)
+        L = max(L, lb)
+        steps.append({"alpha": alpha, "eta": eta_used, "outcome": res["outcome"], "iters": res["iters"],
+                      "L": L, "U": U})
+        if res["outcome"] not in (OUT_SEPARATED, OUT_ABOVE_ALPHA, OUT_CERTIFIED, OUT_STUCK):
+            break
+    return {"margin": lb, "w": w_best, "lower_bound": lb, "upper_bound": min(ub, U),
             "iters": total, "steps": steps, "L": L, "U": U}
