@@ -40,7 +40,9 @@ MODE_THEORY = "theory"
 MODE_FIXED = "fixed"
 MODE_CERTIFIED = "certified"
 OUT_STUCK = "stuck"              # CERTIFIED mode: the certificate gap stopped shrinking (eta is halved)
-CERT_FIRST_CHECK = 1024          # CERTIFIED: first progress check of an alpha-FTP (then at 2x, 4x, ...)
+CERT_FIRST_CHECK = 1024          # CERTIFIED: first progress check of an alpha-FTP at eta = 1 (then 2x, 4x, ...)
+CERT_SHRINK = 0.8                # CERTIFIED: the FTP's own gap must shrink by this factor while t doubles
+CERT_MIN_ETA = 1.0 / 64.0        # CERTIFIED: eta is not halved below this (no progress test there)
 
 
 def _prep(V, gamma):
@@ -276,9 +278,10 @@ def ses_ftp(V, gamma, alpha, eta, rho, T, mode=MODE_FIXED, delta=1e-4, patience=
     only (f^t < alpha proves OPT < alpha) and, every cert["poll_every"]
     completed iterations, stops once the certificates close:
     min(cert["ub"], f_best) <= (1 + cert["eps"]) max(cert["lb"], lb_best),
-    or as STUCK when, at the first poll with t >= 1024, 2048, 4096, ..., the
-    FTP's own gap f_best / lb_best - 1 has not halved since the previous such
-    poll (the first check compares with infinity, so it never stops there).
+    or as STUCK when, at the first poll with t >= c, 2c, 4c, ... (c = 1024/eta),
+    the FTP's own gap f_best / lb_best - 1 has not shrunk by the factor 0.8
+    since the previous such poll (the first check compares with infinity, so it
+    never stops there; no check once eta <= 1/64).
     Returns a dict with the outcome, the iteration count, the final mean, the
     best enclosing ball seen (c_best, f_best), the best lower bound (primal
     construction or, for points, the averaged QP bound) and, if asked, the
@@ -292,7 +295,8 @@ def ses_ftp(V, gamma, alpha, eta, rho, T, mode=MODE_FIXED, delta=1e-4, patience=
     trace = []
     f_prev, streak = None, 0
     outcome = OUT_FIXED if mode == MODE_FIXED else OUT_FEASIBLE
-    last_gap, next_check = math.inf, CERT_FIRST_CHECK
+    last_gap = math.inf
+    next_check = math.ceil(CERT_FIRST_CHECK / eta) if mode == MODE_CERTIFIED and eta > CERT_MIN_ETA else math.inf
     t = 0
     while t < T:
         rec = ses_step(V, gm, ubar, t, alpha, eta, rho, avg=avg)
@@ -323,7 +327,7 @@ def ses_ftp(V, gamma, alpha, eta, rho, T, mode=MODE_FIXED, delta=1e-4, patience=
                 break
             if t >= next_check:  # progress test: this FTP's own gap must halve while t doubles
                 gap = f_best / lb_best - 1.0 if lb_best > 0.0 else math.inf
-                if gap > 0.5 * last_gap:
+                if gap > CERT_SHRINK * last_gap:
                     outcome = OUT_STUCK
                     break
                 last_gap, next_check = gap, 2 * next_check

@@ -45,7 +45,9 @@ MODE_THEORY = "theory"
 MODE_FIXED = "fixed"
 MODE_CERTIFIED = "certified"
 OUT_STUCK = "stuck"              # CERTIFIED mode: the certificate gap stopped shrinking (eta is halved)
-CERT_FIRST_CHECK = 1024          # CERTIFIED: first progress check of an alpha-FTP (then at 2x, 4x, ...)
+CERT_FIRST_CHECK = 1024          # CERTIFIED: first progress check of an alpha-FTP at eta = 1 (then 2x, 4x, ...)
+CERT_SHRINK = 0.8                # CERTIFIED: the FTP's own gap must shrink by this factor while t doubles
+CERT_MIN_ETA = 1.0 / 64.0        # CERTIFIED: eta is not halved below this (no progress test there)
 
 SVM_R = 2.0  # Sec. 4.2
 
@@ -211,10 +213,10 @@ def svm_ftp(X, y, alpha, eta, rho, T, D, mode=MODE_FIXED, delta=1e-4, patience=1
     the first rule only (f^t > alpha proves OPT > alpha) and, every
     cert["poll_every"] completed iterations, stops once
     min(cert["ub"], ub_best) <= (1 + cert["eps"]) max(cert["lb"], f_best),
-    or as STUCK when, at the first poll with t >= 1024, 2048, 4096, ..., the
-    FTP's own gap ub_best / f_best - 1 has not halved since the previous such
-    poll. ub_best is the best of the per-iteration and the averaged Claim 8
-    values.
+    or as STUCK when, at the first poll with t >= c, 2c, 4c, ... (c = 1024/eta),
+    the FTP's own gap ub_best / f_best - 1 has not shrunk by the factor 0.8
+    since the previous such poll (no check once eta <= 1/64). ub_best is the
+    best of the per-iteration and the averaged Claim 8 values.
     """
     X, y = _prep(X, y)
     d = X.shape[1]
@@ -225,7 +227,8 @@ def svm_ftp(X, y, alpha, eta, rho, T, D, mode=MODE_FIXED, delta=1e-4, patience=1
     trace = []
     f_prev, streak = None, 0
     outcome = OUT_FIXED if mode == MODE_FIXED else OUT_FEASIBLE
-    last_gap, next_check = math.inf, CERT_FIRST_CHECK
+    last_gap = math.inf
+    next_check = math.ceil(CERT_FIRST_CHECK / eta) if mode == MODE_CERTIFIED and eta > CERT_MIN_ETA else math.inf
     t = 0
     while t < T:
         rec = svm_step(X, y, wbar, s1bar, s2bar, t, alpha, eta, rho, D, avg=avg)
@@ -256,7 +259,7 @@ def svm_ftp(X, y, alpha, eta, rho, T, D, mode=MODE_FIXED, delta=1e-4, patience=1
                 break
             if t >= next_check:  # progress test: this FTP's own gap must halve while t doubles
                 gap = ub_best / f_best - 1.0 if f_best > 0.0 else math.inf
-                if gap > 0.5 * last_gap:
+                if gap > CERT_SHRINK * last_gap:
                     outcome = OUT_STUCK
                     break
                 last_gap, next_check = gap, 2 * next_check
