@@ -321,6 +321,7 @@ def run_ours(args):
         result["variants"]["ses_multi_candidate_n1e6_d32"] = multi_variant(dev, flush)
         result["variants"]["batched_ses_4096_search"] = batched_solve_variant(dev)
         result["time_to_eps"] = time_to_eps(pts)
+        result["variants"]["svm_time_to_eps_n1e6_d128"] = svm_time_to_eps(dev)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -642,18 +643,51 @@ def backward_variant(dev, n=100_000, d=64, T=2000):
 
 
 def time_to_eps(pts):
-    """ses_solve at eps = 1e-3 (paper's practical rules, Theorem 2 step size)
-    within a 200,000-iteration budget: wall time and the certificate reached."""
+    """Time to a certified (1+eps) ball at eps = 1e-3: ses_solve in CERTIFIED
+    mode (only proven conclusions; ends when the radius of an actual
+    enclosing ball is within 1 + eps of a lower bound), then the same solve
+    under the paper's practical rules of Sec. 5 (a stalled alpha-FTP read as
+    affirmative), whose search range can close while its certificates stay
+    wide. Wall time of the whole solve, bounds pass and polls included."""
     import torch
     from paper_2405_09157_gb300 import api
+    out = {}
+    for mode, budget in (("certified", 200_000), ("practical", 200_000)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, rep = api.ses_solve(pts, eps=1e-3, mode=mode, max_iters=budget, poll_every=256)
+        el = time.perf_counter() - t0
+        out[mode] = {"seconds": el, "iters": rep["iters"], "search_steps": rep["search_steps"],
+                     "radius": rep["value"], "lower_bound": rep["lower_bound"],
+                     "gap": rep["value"] / rep["lower_bound"] - 1 if rep["lower_bound"] > 0 else None,
+                     "search_range": [rep["search_L"], rep["search_U"]], "status": rep["status"],
+                     "budget_iters": budget}
+    res = dict(out["certified"])
+    res["eps"] = 1e-3
+    res["mode"] = "certified (eta starts at 1)"
+    res["practical_rules"] = out["practical"]
+    res["note"] = ("gap = radius of the returned ball / certified lower bound - 1 (<= eps: done); "
+                   "status 5 = budget spent")
+    return res
+
+
+def svm_time_to_eps(dev):
+    """svm_solve in CERTIFIED mode on the n = 1e6, d = 128 SVM workload at
+    eps = 1e-3 within 30,000 iterations: wall time and the certificates
+    reached (the margin of an actual direction, the best Claim 8 value)."""
+    import torch
+    from paper_2405_09157_gb300 import api, datagen
+    X32, y = datagen.svm_clusters(500_000, 500_000, 128, seed=0)
+    X = torch.from_numpy(X32).to(dev)
+    lab = torch.from_numpy(y).to(dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    _, rep = api.ses_solve(pts, eps=1e-3, max_iters=200_000, poll_every=512)
+    _, rep = api.svm_solve(X, lab, eps=1e-3, mode="certified", max_iters=30_000, poll_every=256)
     el = time.perf_counter() - t0
-    return {"seconds": el, "iters": rep["iters"], "radius": rep["value"], "lower_bound": rep["lower_bound"],
-            "gap": rep["value"] / rep["lower_bound"] - 1 if rep["lower_bound"] > 0 else None,
-            "search_range": [rep["search_L"], rep["search_U"]], "status": rep["status"],
-            "note": "certificate gap = radius / primal lower bound - 1; status 5 = budget spent"}
+    return {"workload": "SVM n=1e6 (5e5 + 5e5) d=128 fp32, eps = 1e-3, certified", "seconds": el,
+            "iters": rep["iters"], "margin": rep["value"], "upper_bound": rep["upper_bound"],
+            "gap": rep["upper_bound"] / rep["value"] - 1 if rep["value"] > 0 else None,
+            "status": rep["status"], "budget_iters": 30_000}
 
 
 def main():

@@ -61,13 +61,14 @@ typedef enum pdscp_status {
 /* solve modes */
 #define PDSCP_MODE_PRACTICAL 0  /* Sec. 5 rules inside each alpha-FTP */
 #define PDSCP_MODE_THEORY 1     /* T_i iterations of Theorem 2/3 per FTP */
+#define PDSCP_MODE_CERTIFIED 2  /* proven conclusions only; ends on the certificates (see ses_solve) */
 
 /* Largest supported dimension d. */
 #define PDSCP_MAX_D 1024
 
 /*
  * Per-step record written on the device by mwu_step (Sec. 3 alpha-FTP
- * iteration t -> t+1; Sec. 5 objective). 64 bytes.
+ * iteration t -> t+1; Sec. 5 objective). 72 bytes.
  *   oracle_value  value of the ORACLE program at p^{t+1}: Eq. (ses_oracle) /
  *                 Eq. (svm_oracle). Negative = separated.
  *   objective     f at the mean read by this step (ubar^t or wbar^t), Sec. 5:
@@ -80,6 +81,20 @@ typedef enum pdscp_status {
  *                 for SVM).
  *   stopped       1 if the alpha-FTP has ended (separation or a rule).
  *   status        pdscp_status of the device computation.
+ *   outcome       PDSCP_OUT_* of the alpha-FTP after the step.
+ *   k             eta t / rho used by the step.
+ *   dual_bound    certificate from the dual weights averaged over the
+ *                 alpha-FTP so far (iterate t weighted by t, t >= 1). SES
+ *                 (points; 0 for spheres or before the first update): lower
+ *                 bound sqrt(Abar - |Bbar|^2) from the QP of Sec. 5 (Eq.
+ *                 ses_qp), where mu_i = c_i / sum_j c_j are the weights of the
+ *                 points in the ORACLE's g (w_i = c_i (v_i - ubar) / (sqrt2 S)),
+ *                 A = sum mu_i |v_i - v_1|^2 and B = sum mu_i (v_i - v_1): any
+ *                 simplex weights give OPT^2 >= A - |B|^2. SVM: upper bound
+ *                 |zbar|, zbar the average of the Claim 8 vectors
+ *                 P mu/Tr mu - Q gamma/Tr gamma (inf before the first update).
+ *                 Both enter the state's best bounds (lower_bound /
+ *                 upper_bound of the solves).
  */
 typedef struct pdscp_step_out {
   double oracle_value;
@@ -92,6 +107,7 @@ typedef struct pdscp_step_out {
   int32_t status;
   int32_t outcome;
   double k;
+  double dual_bound;
 } pdscp_step_out;
 
 /* Outcome codes in pdscp_step_out.outcome / pdscp_state header. */
@@ -246,9 +262,21 @@ pdscp_status mwu_state_read(int32_t problem, int32_t d, const void* state_dev,
  * host polling every opts->poll_every iterations (this synchronises the
  * stream). Writes the best centre (d floats) to center_dev and fills
  * *report_host: radius of an actual enclosing ball (upper bound), the best
- * primal lower bound of Eq. (primal_construction), the search range.
+ * lower bound (Eq. (primal_construction) or, for points, the averaged QP
+ * bound of pdscp_step_out.dual_bound), the search range.
  * Returns PDSCP_ERR_NOT_CONVERGED (with a valid report) when opts->max_iters
  * ran out before the range or the certificate gap closed.
+ * Modes: PRACTICAL runs the Sec. 5 rules in each alpha-FTP and reads a stall
+ * as the affirmative answer (U moves), so the range may close below OPT while
+ * the certificates stay wide; THEORY runs T_i iterations of Theorem 2.
+ * CERTIFIED draws only proven conclusions: separation gives L = alpha_i,
+ * f < alpha_i gives U = f; each FTP also ends at a poll where the
+ * certificates close (ub <= (1+eps) max(lb, L)) or, as stuck, at the first
+ * poll with t >= c, 2c, 4c, ... (c = 1024/eta) where the FTP's own gap (best
+ * f over its lower bound, minus 1) has not shrunk by the factor 0.8 since the
+ * previous such poll, after which eta is halved (not below 1/64, where the
+ * test stops); the solve ends only on the certificates (or the budget) and
+ * report.lower_bound is max(lb, L). eta 0 means 1 in this mode.
  */
 pdscp_status ses_solve(const void* pts_dev, int32_t dtype, const float* radii_dev,
                        int64_t n, int32_t d, const pdscp_options* opts,
@@ -259,7 +287,11 @@ pdscp_status ses_solve(const void* pts_dev, int32_t dtype, const float* radii_de
  * (1-eps)-approximate hard-margin SVM / (1+eps) polytope distance (Sec. 4.2)
  * by the minimisation search over alpha in (0, 2D]. Writes the best
  * direction w (d floats, unit norm) to w_dev and its margin and Claim 8
- * upper bound to *report_host. Synchronises like ses_solve.
+ * upper bound (per iteration or averaged, pdscp_step_out.dual_bound) to
+ * *report_host. Synchronises like ses_solve. Modes as in ses_solve, with the
+ * roles mirrored: in CERTIFIED mode separation gives U = alpha_i, a margin
+ * f > alpha_i gives L = f, the FTP's own gap is its Claim 8 bound over its
+ * best margin, and report.upper_bound is min(ub, U).
  */
 pdscp_status svm_solve(const void* X_dev, int32_t dtype, const int8_t* labels_dev,
                        int64_t n, int32_t d, const pdscp_options* opts,

@@ -18,7 +18,7 @@ STATUS_NAMES = {
 SES, SVM = 0, 1
 F32, BF16 = 0, 1
 RULES_NONE, RULES_PRACTICAL = 0, 1
-MODE_PRACTICAL, MODE_THEORY = 0, 1
+MODE_PRACTICAL, MODE_THEORY, MODE_CERTIFIED = 0, 1, 2
 OUT_RUNNING, OUT_SEPARATED, OUT_BEAT_ALPHA, OUT_STALLED = 0, 1, 2, 3
 MAX_D = 1024
 
@@ -26,10 +26,10 @@ c_i32, c_i64, c_dbl, c_sz, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_doubl
 
 
 class StepOut(ctypes.Structure):
-    """pdscp_step_out (64 bytes)."""
+    """pdscp_step_out (72 bytes)."""
     _fields_ = [("oracle_value", c_dbl), ("objective", c_dbl), ("lower_bound", c_dbl),
                 ("upper_bound", c_dbl), ("t", c_i64), ("failed", c_i32), ("stopped", c_i32),
-                ("status", c_i32), ("outcome", c_i32), ("k", c_dbl)]
+                ("status", c_i32), ("outcome", c_i32), ("k", c_dbl), ("dual_bound", c_dbl)]
 
 
 class Options(ctypes.Structure):
@@ -45,7 +45,7 @@ class Report(ctypes.Structure):
                 ("search_steps", c_i32), ("status", c_i32)]
 
 
-assert ctypes.sizeof(StepOut) == 64
+assert ctypes.sizeof(StepOut) == 72
 
 # name -> (restype, argtypes); every entry point declared in include/pdscp.h
 SIGNATURES = {

@@ -14,8 +14,8 @@ from ._ffi import BF16, F32, SES, SVM, check, load
 
 STEP_DTYPE = np.dtype([("oracle_value", "<f8"), ("objective", "<f8"), ("lower_bound", "<f8"),
                        ("upper_bound", "<f8"), ("t", "<i8"), ("failed", "<i4"), ("stopped", "<i4"),
-                       ("status", "<i4"), ("outcome", "<i4"), ("k", "<f8")])
-STEP_BYTES = 64
+                       ("status", "<i4"), ("outcome", "<i4"), ("k", "<f8"), ("dual_bound", "<f8")])
+STEP_BYTES = 72
 REPORT_DTYPE = np.dtype([("value", "<f8"), ("lower_bound", "<f8"), ("upper_bound", "<f8"), ("D", "<f8"),
                          ("search_L", "<f8"), ("search_U", "<f8"), ("iters", "<i8"), ("search_steps", "<i4"),
                          ("status", "<i4")])
@@ -365,7 +365,7 @@ class MWU:
 
 
 def _options(eps, mode, max_iters, poll_every, max_steps, eta, delta, patience):
-    m = {"practical": _ffi.MODE_PRACTICAL, "theory": _ffi.MODE_THEORY}[mode]
+    m = {"practical": _ffi.MODE_PRACTICAL, "theory": _ffi.MODE_THEORY, "certified": _ffi.MODE_CERTIFIED}[mode]
     return _ffi.Options(eps, delta, patience, m, max_iters, poll_every, max_steps, eta or 0.0)
 
 

@@ -555,14 +555,45 @@ namespace {
 struct FtpResult {
   StateHdr hdr;
   int64_t iters;
+  bool certified;  // stopped at a poll because the certificates closed
+  bool stuck;      // stopped at a poll because the FTP's own gap stopped shrinking
 };
+
+// CERTIFIED mode: first progress check of an alpha-FTP at eta = 1 (1024/eta in
+// general; then 2x, 4x, ...), the factor the FTP's own gap must shrink by
+// while t doubles, and the eta below which it is not halved any more.
+constexpr double kCertFirstCheck = 1024.0;
+constexpr double kCertShrink = 0.8;
+constexpr double kCertMinEta = 1.0 / 64.0;
+
+// Certificate test of the CERTIFIED mode, made at every poll: the best bounds
+// known before this alpha-FTP (lb, ub) combined with the FTP's own (SES: the
+// smallest f and the best lower bound; SVM: the largest margin and the best
+// Claim 8 value) close to within a factor 1 + eps.
+struct CertCheck {
+  bool on;
+  double lb, ub, eps, eta;
+};
+bool cert_closed(int problem, const CertCheck& c, const StateHdr& h) {
+  if (!c.on) return false;
+  const double lo = problem == PDSCP_SES ? std::max(c.lb, h.lb_best) : std::max(c.lb, h.best_f);
+  const double hi = problem == PDSCP_SES ? std::min(c.ub, h.best_f) : std::min(c.ub, h.ub_best);
+  return hi <= (1.0 + c.eps) * lo;
+}
+// The FTP's own certificate gap (upper over lower bound, minus 1; inf before a
+// lower bound exists), the measure of its progress.
+double own_gap(int problem, const StateHdr& h) {
+  if (problem == PDSCP_SES) return h.lb_best > 0.0 ? h.best_f / h.lb_best - 1.0 : INFINITY;
+  return h.best_f > 0.0 ? h.ub_best / h.best_f - 1.0 : INFINITY;
+}
 
 pdscp_status check_opts(const pdscp_options* o) {
   if (!o) return fail(PDSCP_ERR_INVALID_ARG, "options pointer is null");
   if (!(o->eps > 0.0) || !std::isfinite(o->eps)) return fail(PDSCP_ERR_INVALID_ARG, "eps must be > 0");
   if (!(o->delta >= 0.0)) return fail(PDSCP_ERR_INVALID_ARG, "delta must be >= 0");
   if (o->patience < 1) return fail(PDSCP_ERR_INVALID_ARG, "patience must be >= 1");
-  if (o->mode != PDSCP_MODE_PRACTICAL && o->mode != PDSCP_MODE_THEORY) return fail(PDSCP_ERR_INVALID_ARG, "unknown mode");
+  if (o->mode != PDSCP_MODE_PRACTICAL && o->mode != PDSCP_MODE_THEORY && o->mode != PDSCP_MODE_CERTIFIED)
+    return fail(PDSCP_ERR_INVALID_ARG, "unknown mode");
   if (o->max_iters < 1) return fail(PDSCP_ERR_INVALID_ARG, "max_iters must be >= 1");
   if (o->poll_every < 1 || o->poll_every > kRing) return fail(PDSCP_ERR_INVALID_ARG, "poll_every outside [1, %d]", kRing);
   if (o->max_steps < 1) return fail(PDSCP_ERR_INVALID_ARG, "max_steps must be >= 1");
@@ -573,18 +604,27 @@ pdscp_status check_opts(const pdscp_options* o) {
 // Runs one alpha-FTP on the device: T (capped by budget) iterations, polling
 // the state every poll_every launches; evaluates f at the final mean when the
 // loop ended without a stop (as the oracle's end-of-FTP evaluation does).
+// cert.on (CERTIFIED mode): the stall rule is off (delta = 0); the FTP also
+// ends at the first poll where the certificates close, or, as stuck, at the
+// first poll with t >= c, 2c, 4c, ... (c = 1024/eta; none once eta <= 1/64)
+// where its own gap has not shrunk by the factor 0.8 since the previous one.
 pdscp_status run_ftp(int problem, const void* pts, int dtype, const float* radii, const int8_t* labels, int64_t n,
                      int d, double alpha, double eta_over_rho, double D, int rules, const pdscp_options* o,
-                     int64_t budget, void* ws, size_t ws_bytes, cudaStream_t s, FtpResult* res) {
+                     int64_t budget, void* ws, size_t ws_bytes, cudaStream_t s, FtpResult* res,
+                     const CertCheck& cert = CertCheck{false, 0.0, 0.0, 0.0, 1.0}) {
   const Layout L = layout(problem, d);
   void* state = reinterpret_cast<char*>(ws) + L.state;
   pdscp_step_out* ring = reinterpret_cast<pdscp_step_out*>(reinterpret_cast<char*>(ws) + L.ring);
-  pdscp_status st = mwu_state_init(problem, pts, dtype, n, d, rules, o->delta, o->patience, state, ws, ws_bytes,
-                                   (pdscp_stream)s);
+  res->certified = false;
+  pdscp_status st = mwu_state_init(problem, pts, dtype, n, d, rules, cert.on ? 0.0 : o->delta, o->patience, state,
+                                   ws, ws_bytes, (pdscp_stream)s);
   if (st != PDSCP_OK) return st;
   int64_t ran = 0;
   StateHdr h;
   bool stopped = false;
+  res->stuck = false;
+  double last_gap = INFINITY;
+  double next_check = (cert.on && cert.eta > kCertMinEta) ? std::ceil(kCertFirstCheck / cert.eta) : INFINITY;
   while (ran < budget) {
     const int64_t chunk = std::min<int64_t>(o->poll_every, budget - ran);
     for (int64_t j = 0; j < chunk; ++j) {
@@ -599,6 +639,19 @@ pdscp_status run_ftp(int problem, const void* pts, int dtype, const float* radii
     if (h.stopped) {
       stopped = true;
       break;
+    }
+    if (cert_closed(problem, cert, h)) {
+      res->certified = true;
+      break;
+    }
+    if (cert.on && (double)h.t >= next_check) {
+      const double gap = own_gap(problem, h);
+      if (gap > kCertShrink * last_gap) {
+        res->stuck = true;
+        break;
+      }
+      last_gap = gap;
+      next_check *= 2;
     }
   }
   if (!stopped) {
@@ -672,8 +725,38 @@ pdscp_status ses_solve(const void* pts, int32_t dtype, const float* radii, int64
   int steps = 0;
   bool have_center = false;
   const double eps = o->eps;
-  const int rules = o->mode == PDSCP_MODE_PRACTICAL ? PDSCP_RULES_PRACTICAL : PDSCP_RULES_NONE;
-  while (Up > (1.0 + eps) * Lo && ub > (1.0 + eps) * lb && total < o->max_iters && steps < o->max_steps) {
+  const bool certified = o->mode == PDSCP_MODE_CERTIFIED;
+  const int rules = o->mode == PDSCP_MODE_THEORY ? PDSCP_RULES_NONE : PDSCP_RULES_PRACTICAL;
+  // CERTIFIED: only proven conclusions move the range (separation: OPT > alpha;
+  // f < alpha: OPT < alpha), every FTP also ends when the certificates close,
+  // and the loop ends on ub <= (1+eps) max(lb, L); eta defaults to 1.
+  double eta_c = o->eta > 0.0 ? o->eta : 1.0;
+  while (certified && ub > (1.0 + eps) * std::max(lb, Lo) && total < o->max_iters && steps < o->max_steps) {
+    const double alpha = Lo + (Up - Lo) / 3.0;
+    const double eta = eta_c;
+    FtpResult r;
+    const CertCheck c{true, std::max(lb, Lo), ub, eps, eta};
+    if ((st = run_ftp(PDSCP_SES, pts, dtype, radii, nullptr, n, d, alpha, eta / rho, 0.0, rules, o, o->max_iters - total,
+                      ws, ws_bytes, s, &r, c)) != PDSCP_OK)
+      return st;
+    total += r.iters;
+    if (r.hdr.best_f < ub) {
+      ub = r.hdr.best_f;
+      if ((st = mwu_state_read(PDSCP_SES, d, reinterpret_cast<char*>(ws) + L.state, nullptr, center, stream)) != PDSCP_OK)
+        return st;
+      have_center = true;
+    }
+    if (r.hdr.lb_best > lb) lb = r.hdr.lb_best;
+    const int oc = r.hdr.stopped ? r.hdr.outcome : PDSCP_OUT_RUNNING;
+    if (oc == PDSCP_OUT_SEPARATED) Lo = std::max(Lo, alpha);
+    if (r.stuck) eta_c *= 0.5;  // smaller steps resolve alpha closer to OPT
+    Up = std::min(Up, ub);
+    Lo = std::max(Lo, lb);
+    ++steps;
+    if (oc == PDSCP_OUT_RUNNING && !r.certified && !r.stuck) break;  // budget spent inside the step
+  }
+  while (!certified && Up > (1.0 + eps) * Lo && ub > (1.0 + eps) * lb && total < o->max_iters &&
+         steps < o->max_steps) {
     const double alpha = Lo + (Up - Lo) / 3.0;
     const double eps_i = (Up - Lo) / (3.0 * alpha);
     const int64_t T = theorem_T(36.0, D, logr, eps_i, alpha);
@@ -708,6 +791,7 @@ pdscp_status ses_solve(const void* pts, int32_t dtype, const float* radii, int64
   (void)gam1;
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "ses_solve final sync");
+  if (certified) lb = std::max(lb, Lo);  // a separation is a proof too
   rep->value = ub;
   rep->lower_bound = lb;
   rep->upper_bound = ub;
@@ -715,7 +799,7 @@ pdscp_status ses_solve(const void* pts, int32_t dtype, const float* radii, int64
   rep->search_U = Up;
   rep->iters = total;
   rep->search_steps = steps;
-  const bool done = Up <= (1.0 + eps) * Lo || ub <= (1.0 + eps) * lb;
+  const bool done = certified ? ub <= (1.0 + eps) * lb : (Up <= (1.0 + eps) * Lo || ub <= (1.0 + eps) * lb);
   rep->status = done ? PDSCP_OK : PDSCP_ERR_NOT_CONVERGED;
   if (!done) fail(PDSCP_ERR_NOT_CONVERGED, "iteration budget spent (range [%g, %g], certificate [%g, %g])", Lo, Up, lb, ub);
   return (pdscp_status)rep->status;
@@ -751,8 +835,37 @@ pdscp_status svm_solve(const void* X, int32_t dtype, const int8_t* labels, int64
   int steps = 0;
   bool have_w = false;
   const double eps = o->eps;
-  const int rules = o->mode == PDSCP_MODE_PRACTICAL ? PDSCP_RULES_PRACTICAL : PDSCP_RULES_NONE;
-  while (Up > (1.0 + eps) * Lo && ub > (1.0 + eps) * lb && total < o->max_iters && steps < o->max_steps) {
+  const bool certified = o->mode == PDSCP_MODE_CERTIFIED;
+  const int rules = o->mode == PDSCP_MODE_THEORY ? PDSCP_RULES_NONE : PDSCP_RULES_PRACTICAL;
+  // CERTIFIED (as in ses_solve): separation gives U = alpha, f > alpha gives
+  // L = f; the loop ends on min(ub, U) <= (1+eps) lb.
+  double eta_c = o->eta > 0.0 ? o->eta : 1.0;
+  while (certified && std::min(ub, Up) > (1.0 + eps) * lb && total < o->max_iters && steps < o->max_steps) {
+    const double alpha = Up - (Up - Lo) / 3.0;
+    const double eta = eta_c;
+    FtpResult r;
+    const CertCheck c{true, lb, std::min(ub, Up), eps, eta};
+    if ((st = run_ftp(PDSCP_SVM, X, dtype, nullptr, labels, n, d, alpha, eta / rho, D, rules, o, o->max_iters - total,
+                      ws, ws_bytes, s, &r, c)) != PDSCP_OK)
+      return st;
+    total += r.iters;
+    if (r.hdr.best_f > lb) {
+      lb = r.hdr.best_f;
+      if ((st = mwu_state_read(PDSCP_SVM, d, reinterpret_cast<char*>(ws) + L.state, nullptr, w_out, stream)) != PDSCP_OK)
+        return st;
+      have_w = true;
+    }
+    if (r.hdr.ub_best < ub) ub = r.hdr.ub_best;
+    const int oc = r.hdr.stopped ? r.hdr.outcome : PDSCP_OUT_RUNNING;
+    if (oc == PDSCP_OUT_SEPARATED) Up = std::min(Up, alpha);
+    if (r.stuck) eta_c *= 0.5;
+    Up = std::min(Up, ub);
+    Lo = std::max(Lo, lb);
+    ++steps;
+    if (oc == PDSCP_OUT_RUNNING && !r.certified && !r.stuck) break;
+  }
+  while (!certified && Up > (1.0 + eps) * Lo && ub > (1.0 + eps) * lb && total < o->max_iters &&
+         steps < o->max_steps) {
     const double alpha = Up - (Up - Lo) / 3.0;
     const double eps_i = (Up - Lo) / (3.0 * alpha);
     const int64_t T = theorem_T(64.0, D, logr, eps_i, alpha);
@@ -787,6 +900,7 @@ pdscp_status svm_solve(const void* X, int32_t dtype, const int8_t* labels, int64
   }
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "svm_solve final sync");
+  if (certified) ub = std::min(ub, Up);  // a separation is a proof too
   rep->value = lb;
   rep->lower_bound = lb;
   rep->upper_bound = ub;
@@ -794,7 +908,7 @@ pdscp_status svm_solve(const void* X, int32_t dtype, const int8_t* labels, int64
   rep->search_U = Up;
   rep->iters = total;
   rep->search_steps = steps;
-  const bool done = Up <= (1.0 + eps) * Lo || ub <= (1.0 + eps) * lb;
+  const bool done = certified ? ub <= (1.0 + eps) * lb : (Up <= (1.0 + eps) * Lo || ub <= (1.0 + eps) * lb);
   rep->status = done ? PDSCP_OK : PDSCP_ERR_NOT_CONVERGED;
   if (!done) fail(PDSCP_ERR_NOT_CONVERGED, "iteration budget spent (range [%g, %g], certificate [%g, %g])", Lo, Up, lb, ub);
   return (pdscp_status)rep->status;

@@ -274,6 +274,7 @@ static __device__ __forceinline__ void batch_search_update(BatchSearch* sr, void
       mean[j] = v;
       mean32[j] = (float)v;
       best[j] = (float)v;
+      state_dual(state, d)[j] = 0.0;
     }
     if (lane == 0) {
       StateHdr z;
@@ -569,6 +570,7 @@ __global__ void ses_batch_init_kernel(const float* pts, const BatchInst* inst, u
     mean[j] = v;
     mean32[j] = (float)v;
     best[j] = (float)v;
+    state_dual(state, d)[j] = 0.0;
   }
   if (threadIdx.x == 0) {
     StateHdr h;

@@ -109,12 +109,14 @@ __global__ void state_init_kernel(const T* pts, int d, int problem, int rules, d
   double* mean = state_mean(state);
   float* mean32 = state_mean32(state, d);
   float* best = state_best(state, d);
+  double* dual = state_dual(state, d);
   const int dp = dpad4(d);
   for (int j = threadIdx.x; j < dp; j += blockDim.x) {
     const double v = (problem == PDSCP_SES && j < d) ? (double)elem_to_float<T>(pts + j) : 0.0;
     mean[j] = v;
     mean32[j] = (float)v;
     best[j] = (float)v;
+    dual[j] = 0.0;
   }
   if (threadIdx.x == 0) {
     StateHdr h;
@@ -135,8 +137,8 @@ __global__ void state_init_kernel(const T* pts, int d, int problem, int rules, d
     h.s1bar = 0.0;
     h.s2bar = 0.0;
     h.last_value = 0.0;
-    h.reserved[0] = 0.0;
-    h.reserved[1] = 0.0;
+    h.dual_A = 0.0;
+    h.dual_w = 0.0;
     *hdr = h;
   }
   if (counter)
@@ -152,12 +154,14 @@ __global__ void state_set_kernel(int d, int problem, int64_t t, const double* me
   double* mean = state_mean(state);
   float* mean32 = state_mean32(state, d);
   float* best = state_best(state, d);
+  double* dual = state_dual(state, d);
   const int dp = dpad4(d);
   for (int j = threadIdx.x; j < dp; j += blockDim.x) {
     const double v = j < d ? mean_in[j] : 0.0;
     mean[j] = v;
     mean32[j] = (float)v;
     best[j] = (float)v;
+    dual[j] = 0.0;
   }
   if (threadIdx.x == 0) {
     StateHdr h;
@@ -178,8 +182,8 @@ __global__ void state_set_kernel(int d, int problem, int64_t t, const double* me
     h.s1bar = problem == PDSCP_SVM ? mean_in[d] : 0.0;
     h.s2bar = problem == PDSCP_SVM ? mean_in[d + 1] : 0.0;
     h.last_value = 0.0;
-    h.reserved[0] = 0.0;
-    h.reserved[1] = 0.0;
+    h.dual_A = 0.0;
+    h.dual_w = 0.0;
     *hdr = h;
   }
   if (counter)

@@ -542,6 +542,7 @@ __global__ void __launch_bounds__(32) ses_bwd_seed_kernel(BwdParams p) {
     o.status = hdr->status;
     o.outcome = hdr->outcome;
     o.k = (double)bi;  // the row that attains f
+    o.dual_bound = 0.0;
     *p.out = o;
   }
   if (T == 0) {  // ubar^0 = v_1
@@ -1011,6 +1012,7 @@ __global__ void __launch_bounds__(32) svm_bwd_seed_kernel(BwdParams p) {
     o.status = hdr->status;
     o.outcome = hdr->outcome;
     o.k = live ? (double)bi[0] : -1.0;  // the row of P attaining the margin
+    o.dual_bound = INFINITY;
     *p.out = o;
   }
   if (T >= 1) svm_bwd_prologue(T - 1, p.tape, d, p.bw);

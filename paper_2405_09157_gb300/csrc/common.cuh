@@ -27,7 +27,9 @@ constexpr int kMaxGroups = 64;        // group rows reserved in the workspace
 
 // ---------------------------------------------------------------------------
 // Device state of one alpha-FTP. 128-byte header, then the running mean in
-// FP64 (master copy), its FP32 copy read by the point pass, and the best point.
+// FP64 (master copy), its FP32 copy read by the point pass, the best point,
+// and the running average of the dual weights' d-vector (FP64: SES B-bar of
+// the QP bound, SVM z-bar of the Claim 8 bound).
 // ---------------------------------------------------------------------------
 struct StateHdr {
   int64_t t;        // completed ORACLE calls
@@ -48,16 +50,28 @@ struct StateHdr {
   double s1bar;     // SVM running means of s_1, s_2
   double s2bar;
   double last_value;
-  double reserved[2];
+  double dual_A;    // SES: running average A-bar of the QP bound
+  double dual_w;    // sum of the averaging weights so far (iterate t has weight t)
 };
 static_assert(sizeof(StateHdr) == 128, "state header must be 128 bytes");
 
 __host__ __device__ inline int dpad4(int d) { return (d + 3) & ~3; }
 
+#ifdef __CUDACC__
+// 8-byte global -> shared copy that holds no register while in flight (both
+// addresses 8-byte aligned); completed by cp_async_wait_all() of the same thread.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned int)__cvta_generic_to_shared(smem_dst)),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+#endif
+
 __host__ __device__ inline size_t state_bytes(int d) {
-  // header | double mean[dp] | float mean32[dp] | float best[dp]
+  // header | double mean[dp] | float mean32[dp] | float best[dp] | double dual[dp]
   const int dp = dpad4(d);
-  return sizeof(StateHdr) + (size_t)dp * 8 + (size_t)dp * 4 * 2;
+  return sizeof(StateHdr) + (size_t)dp * 8 * 2 + (size_t)dp * 4 * 2;
 }
 __host__ __device__ inline double* state_mean(void* s) {
   return reinterpret_cast<double*>(reinterpret_cast<char*>(s) + sizeof(StateHdr));
@@ -67,6 +81,9 @@ __host__ __device__ inline float* state_mean32(void* s, int d) {
 }
 __host__ __device__ inline float* state_best(void* s, int d) {
   return state_mean32(s, d) + dpad4(d);
+}
+__host__ __device__ inline double* state_dual(void* s, int d) {
+  return reinterpret_cast<double*>(state_best(s, d) + dpad4(d));
 }
 
 // Per-CTA partial row width (floats).

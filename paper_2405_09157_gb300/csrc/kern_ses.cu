@@ -17,7 +17,7 @@ struct SesLauncher {
     const int dp = dpad4(p.d);
     const int st = ses_partial_stride(p.d);
     const size_t pass_smem = (size_t)(block / 32) * 1 * dp * sizeof(float);
-    const size_t fin_base = (size_t)(st + 2 * dp) * sizeof(double);
+    const size_t fin_base = (size_t)(st + 3 * dp) * sizeof(double);  // totals | mean | v_1 | Bbar
     size_t smem = pass_smem > fin_base ? pass_smem : fin_base;
     int grid = pass_grid(kern, smem, p.n, (32 / lpp) * points_per_lane_step * (block / 32), block);
     SesParams q = p;
@@ -61,7 +61,7 @@ cudaError_t launch_ses(const SesParams& p, int dtype, bool vec, cudaStream_t str
 }
 
 cudaError_t launch_ses_merge(const SesMergeParams& m, int dtype, cudaStream_t stream) {
-  const size_t smem = (size_t)(ses_partial_stride(m.d) + 2 * dpad4(m.d)) * sizeof(double);
+  const size_t smem = (size_t)(ses_partial_stride(m.d) + 3 * dpad4(m.d)) * sizeof(double);
   if (dtype == PDSCP_F32) ses_merge_kernel<float><<<1, kMergeBlock, smem, stream>>>(m);
   else ses_merge_kernel<__nv_bfloat16><<<1, kMergeBlock, smem, stream>>>(m);
   return cudaGetLastError();

@@ -17,7 +17,7 @@ struct SvmLauncher {
     const int dp = dpad4(p.d);
     const int st = svm_partial_stride(p.d);
     const size_t pass_smem = (size_t)(block / 32) * 2 * dp * sizeof(float);
-    const size_t fin_base = (size_t)(st + 1 * dp) * sizeof(double);
+    const size_t fin_base = (size_t)(st + 2 * dp) * sizeof(double);  // totals | mean | zbar
     size_t smem = pass_smem > fin_base ? pass_smem : fin_base;
     int grid = pass_grid(kern, smem, p.n, (32 / lpp) * points_per_lane_step * (block / 32), block);
     SvmParams q = p;
@@ -61,7 +61,7 @@ cudaError_t launch_svm(const SvmParams& p, int dtype, bool vec, cudaStream_t str
 }
 
 cudaError_t launch_svm_merge(const SvmMergeParams& m, cudaStream_t stream) {
-  const size_t smem = (size_t)(svm_partial_stride(m.d) + dpad4(m.d)) * sizeof(double);
+  const size_t smem = (size_t)(svm_partial_stride(m.d) + 2 * dpad4(m.d)) * sizeof(double);
   svm_merge_kernel<0><<<1, kSvmMergeBlock, smem, stream>>>(m);
   return cudaGetLastError();
 }

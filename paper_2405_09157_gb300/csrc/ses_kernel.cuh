@@ -72,7 +72,7 @@ __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw);
 template <typename T, int VW, int LPP, int NCH, int U>
 __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ float s_sc[kWarps][3];
+  __shared__ float s_sc[kWarps][4];
 
   StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
   if (hdr->stopped && !p.eval_only) return;
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
       G[j][e] = 0.f;
     }
   }
-  float S = 0.f, W = 0.f, maxd = -INFINITY;
+  float S = 0.f, W = 0.f, Cs = 0.f, maxd = -INFINITY;
 
   const T* pts = reinterpret_cast<const T*>(p.pts);
   const WarpSplit ws(p.sink, kWarps, warp);
@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
         if (gl == 0) {
           S += sum;
           W += a * sum - dist * dif;
+          Cs += c;
           maxd = fmaxf(maxd, dist + gam);
         }
       }
@@ -167,6 +168,7 @@ __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
 #pragma unroll
       for (int e = 0; e < VW; ++e) G[j][e] += __shfl_xor_sync(0xffffffffu, G[j][e], o);
   S = warp_sum(S);
+  Cs = warp_sum(Cs);
   W = warp_sum(W);
   maxd = warp_max(maxd);
   float* sG = reinterpret_cast<float*>(smem_raw);  // [kWarps][dp]
@@ -183,6 +185,7 @@ __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
     s_sc[warp][0] = S;
     s_sc[warp][1] = W;
     s_sc[warp][2] = maxd;
+    s_sc[warp][3] = Cs;
   }
   __syncthreads();
   float* prow = p.partials + (size_t)blockIdx.x * ses_partial_stride(d);
@@ -192,29 +195,33 @@ __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
     prow[4 + j] = s;
   }
   if (threadIdx.x == 0) {
-    float s0 = 0.f, s1 = 0.f, m = -INFINITY;
+    float s0 = 0.f, s1 = 0.f, s3 = 0.f, m = -INFINITY;
     for (int w = 0; w < kWarps; ++w) {
       s0 += s_sc[w][0];
       s1 += s_sc[w][1];
+      s3 += s_sc[w][3];
       m = fmaxf(m, s_sc[w][2]);
     }
     prow[0] = s0;
     prow[1] = s1;
     prow[2] = m;
-    prow[3] = 0.f;
+    prow[3] = p.radii ? NAN : s3;  // the QP bound holds for points only
   }
   ses_finish<T>(p, smem_raw);
 }
 
 // The O(d) finish of one SES iteration from the column totals: run by one
-// warp (lane = threadIdx.x & 31). raw: [S, Wt, maxd, 0, G'_1..G'_d] as
-// compensated pairs; s_mean, s_v1: the mean read by the pass and v_1 (FP64,
-// shared memory); h: a copy of the state header. Writes the state and the
-// step record (out, may be null).
+// warp (lane = threadIdx.x & 31). raw: [S, Wt, maxd, Cc, G'_1..G'_d] as
+// compensated pairs (Cc = sum of the ORACLE coefficients c_i); s_mean, s_v1:
+// the mean read by the pass and v_1 (FP64, shared memory); h: a copy of the
+// state header. Writes the state and the step record (out, may be null).
+// s_dual (may be null: no averaged bound): the state's Bbar, read beforehand
+// into shared memory; with it the averaged QP lower bound is advanced (points:
+// a pass over spheres leaves Cc = NaN, which switches the update off).
 static __device__ __noinline__ void ses_finish_warp(const float2* raw, const double* s_mean, const double* s_v1,
                                              const StateHdr& h, void* state, int d, double alpha_d, double gam1,
                                              double eta_over_rho, int eval_only, pdscp_step_out* out,
-                                             float* tape = nullptr) {
+                                             float* tape = nullptr, const double* s_dual = nullptr) {
   const int lane = threadIdx.x & 31;
   StateHdr* hdr = reinterpret_cast<StateHdr*>(state);
   double* mean = state_mean(state);
@@ -231,17 +238,43 @@ static __device__ __noinline__ void ses_finish_warp(const float2* raw, const dou
   const float alpha = (float)alpha_in;
   const float gam1f = (float)gam1;
   const float inv = 1.0f / ((float)kSqrt2 * S);  // g = G' / (sqrt2 S)
-  // A = |g|^2, B = g . (v_1 - ubar), C = |ubar - v_1|^2
-  float acc[3] = {0.f, 0.f, 0.f};
+  const int64_t t = h.t;
+  // Averaged QP bound (Eq. ses_qp; points): the weights mu_i = c_i / Cc of this
+  // pass give, about v_1, A_t = sum mu_i |v_i - v_1|^2 and B_t = sum mu_i (v_i -
+  // v_1) = G'/Cc - (v_1 - ubar); both are averaged over the alpha-FTP with
+  // iterate t weighted by t, and OPT^2 >= Abar - |Bbar|^2.
+  const float Cc = tot(3);
+  const bool qp = s_dual != nullptr;
+  const bool qpu = qp && !eval_only && t >= 1 && Cc > 0.f && isfinite(Cc);
+  const double wsum = h.dual_w + (qpu ? (double)t : 0.0);
+  const double rw = qpu ? (double)t / wsum : 0.0;
+  const float rCc = qpu ? 1.0f / Cc : 0.f;
+  double* bbar = state_dual(state, d);
+  // A = |g|^2, B = g . (v_1 - ubar), C = |ubar - v_1|^2, |Bbar|^2
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
   for (int j = lane; j < d; j += 32) {
-    const float g = tot(4 + j) * inv;
+    const float gp = tot(4 + j);
+    const float g = gp * inv;
     const float dv = (float)(s_v1[j] - s_mean[j]);
     acc[0] = fmaf(g, g, acc[0]);
     acc[1] = fmaf(g, dv, acc[1]);
     acc[2] = fmaf(dv, dv, acc[2]);
+    if (qp) {
+      double b = s_dual[j];
+      if (qpu) {
+        b += rw * (double)(fmaf(gp, rCc, -dv) - (float)b);
+        bbar[j] = b;
+      }
+      acc[3] = fmaf((float)b, (float)b, acc[3]);
+    }
   }
-  warp_sum_kf<3>(acc);
+  warp_sum_kf<4>(acc);
   const float A = acc[0], B = acc[1], C = acc[2];
+  // A_t = (sum c_i dist_i^2 - 2 G'.(v_1 - ubar)) / Cc + |v_1 - ubar|^2, with
+  // sum c_i dist_i^2 = alpha S - Wt for points
+  const double Abar = qpu ? h.dual_A + rw * ((double)((alpha_d * S - Wt - 2.f * (float)kSqrt2 * S * B) * rCc + C) - h.dual_A)
+                          : h.dual_A;
+  const float LBq = (qp && wsum > 0.0) ? sqrtf(fmaxf((float)Abar - acc[3], 0.f)) : 0.f;
   const float rad = alpha - gam1f;
   const float rng = A > 0.f ? 1.0f / sqrtf(A) : 0.f;
   const float ng = A * rng;                 // ||g||
@@ -251,7 +284,6 @@ static __device__ __noinline__ void ses_finish_warp(const float2* raw, const dou
   const float f = fmaxf(maxd, sqrtf(C) + gam1f);                             // f at the mean read (Sec. 5)
   const double fd = (double)f;
 
-  const int64_t t = h.t;
   int status = PDSCP_OK;
   if (!(S > 0.f) || !isfinite(S) || !isfinite(V) || !isfinite(f)) status = PDSCP_ERR_NUMERIC;
   bool stop = false, failed = false;
@@ -312,7 +344,12 @@ static __device__ __noinline__ void ses_finish_warp(const float2* raw, const dou
     }
   }
   if (lane == 0) {
-    if (!eval_only && (double)LB > h.lb_best) hdr->lb_best = (double)LB;
+    const double lbn = (double)fmaxf(LB, LBq);
+    if (!eval_only && lbn > h.lb_best) hdr->lb_best = lbn;
+    if (qpu) {
+      hdr->dual_A = Abar;
+      hdr->dual_w = wsum;
+    }
     if (streak != h.streak) hdr->streak = streak;
     if (set_fprev) hdr->f_prev = fd;
     if (better) hdr->best_f = fd;
@@ -340,6 +377,7 @@ static __device__ __noinline__ void ses_finish_warp(const float2* raw, const dou
       o.status = status;
       o.outcome = outcome;
       o.k = (double)t * eta_over_rho;
+      o.dual_bound = (double)LBq;
       *out = o;
     }
   }
@@ -355,11 +393,11 @@ __device__ __noinline__ void ses_finish_warm(const SesParams& p, unsigned char* 
   StateHdr h;
   memset(&h, 0, sizeof(h));
   ses_finish_warp(raw, s_mean, s_v1, h, p.sink, d, p.alpha, 0.0, p.eta_over_rho, p.eval_only,
-                  warm_sink_out(p.sink, d), p.tape ? warm_sink_tape(p.sink, d) : nullptr);
+                  warm_sink_out(p.sink, d), p.tape ? warm_sink_tape(p.sink, d) : nullptr, s_v1 + dpad4(d));
 }
 
 // Completion of one SES iteration. Every CTA calls it after writing its
-// partial row [S, Wt, maxd, 0, G'_1..G'_d]; the last CTA to arrive reduces
+// partial row [S, Wt, maxd, Cc, G'_1..G'_d]; the last CTA to arrive reduces
 // the rows and hands the totals to warp 0 (ses_finish_warp), or, for a shard
 // of a row-sharded iteration, writes them to row_out.
 template <typename T>
@@ -379,39 +417,40 @@ __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw) {
   const T* pts = reinterpret_cast<const T*>(p.pts);
   const int tid = threadIdx.x;
   const int dp = dpad4(d);
-  // dynamic shared memory: column totals as (s, c) pairs | mean | v_1 | staged partial rows
+  // dynamic shared memory: column totals as (s, c) pairs | mean | v_1 | Bbar | staged partial rows
   float2* raw = reinterpret_cast<float2*>(smem_raw);
   double* s_mean = reinterpret_cast<double*>(smem_raw) + st;
   double* s_v1 = s_mean + dp;
-  float* stage = reinterpret_cast<float*>(s_v1 + dp);
-  // loads the finish needs, issued before the reduction so their latency overlaps it
+  double* s_dual = s_v1 + dp;
+  float* stage = reinterpret_cast<float*>(s_dual + dp);
+  const double* dual = state_dual(p.state, d);
+  // what the finish reads, fetched before the reduction so that its latency
+  // overlaps it: the FP64 header, mean and Bbar straight into shared memory
+  // (cp.async: no register is held across the reduction), v_1 into a register
   constexpr int HW = (int)(sizeof(StateHdr) / 8);
-  const double hw = tid < HW ? reinterpret_cast<const double*>(hdr)[tid] : 0.0;
-  const double m0 = tid < d ? mean[tid] : 0.0;
-  const double v0 = tid < d ? (double)elem_to_float<T>(pts + tid) : 0.0;
-  const double gam1 = p.radii ? (double)__ldg(p.radii) : 0.0;
+  if (tid < HW) cp_async8(s_hdr + tid, reinterpret_cast<const double*>(hdr) + tid);
+  for (int j = tid; j < d; j += blockDim.x) {
+    cp_async8(s_mean + j, mean + j);
+    cp_async8(s_dual + j, dual + j);
+  }
+  const float v0 = tid < d ? elem_to_float<T>(pts + tid) : 0.f;
+  const float gam1 = p.radii ? __ldg(p.radii) : 0.f;
   final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single, 2, -1, st);
+  cp_async_wait_all();
   if (p.row_out) {  // a shard of a row-sharded iteration: hand the totals to the merge
     for (int pc = tid; pc < st; pc += blockDim.x) p.row_out[pc] = raw[pc];
     return;
   }
-  if (tid < HW) s_hdr[tid] = hw;
-  if (tid < d) {
-    s_mean[tid] = m0;
-    s_v1[tid] = v0;
-  }
-  for (int j = tid + blockDim.x; j < d; j += blockDim.x) {
-    s_mean[j] = mean[j];
-    s_v1[j] = (double)elem_to_float<T>(pts + j);
-  }
+  if (tid < d) s_v1[tid] = (double)v0;
+  for (int j = tid + blockDim.x; j < d; j += blockDim.x) s_v1[j] = (double)elem_to_float<T>(pts + j);
   __syncthreads();
   // The O(d) math runs in warp 0 alone: FP64 work is slow on this GPU and
   // would only contend across warps; no block barrier follows.
   if (tid >= 32) return;
   const int lane = tid;
   (void)lane;
-  ses_finish_warp(raw, s_mean, s_v1, *reinterpret_cast<const StateHdr*>(s_hdr), p.state, d, p.alpha, gam1,
-                  p.eta_over_rho, p.eval_only, p.out, p.tape);
+  ses_finish_warp(raw, s_mean, s_v1, *reinterpret_cast<const StateHdr*>(s_hdr), p.state, d, p.alpha, (double)gam1,
+                  p.eta_over_rho, p.eval_only, p.out, p.tape, s_dual);
 }
 
 }  // namespace pdscp
@@ -431,7 +470,10 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
   using GS = GroupScatter<LPP, NI>;
   constexpr int NW = BLOCK / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ float s_sc[NW][3];
+  __shared__ float s_sc[NW][4];
+  // per-lane sum of the ORACLE coefficients (kept in shared memory: one more
+  // register across the streaming loop costs more than the shared access)
+  __shared__ float s_cs[BLOCK];
 
   const int d = p.d;
   const int dp = dpad4(d);
@@ -482,6 +524,7 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
     G[e] = 0.f;
   }
   float S = 0.f, W = 0.f, maxd = -INFINITY;
+  s_cs[threadIdx.x] = 0.f;
 
   for (int64_t base = lo; base < hi; base += ROUND) {
     if (base != lo) load_round(base);
@@ -514,6 +557,7 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
         if (owner) {
           S += sum;
           W += a * sum - dist * dif;
+          s_cs[threadIdx.x] += c[k];
           maxd = fmaxf(maxd, dist + gam);
         }
       }
@@ -531,6 +575,7 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
 #pragma unroll
     for (int e = 0; e < VW; ++e) G[e] += __shfl_xor_sync(0xffffffffu, G[e], o);
   S = warp_sum(S);
+  const float Cs = warp_sum(s_cs[threadIdx.x]);
   W = warp_sum(W);
   maxd = warp_max(maxd);
   float* sG = reinterpret_cast<float*>(smem_raw);
@@ -541,6 +586,7 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
     s_sc[warp][0] = S;
     s_sc[warp][1] = W;
     s_sc[warp][2] = maxd;
+    s_sc[warp][3] = Cs;
   }
   __syncthreads();
   float* prow = p.partials + (size_t)blockIdx.x * ses_partial_stride(d);
@@ -550,16 +596,17 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
     prow[4 + j] = s;
   }
   if (threadIdx.x == 0) {
-    float s0 = 0.f, s1 = 0.f, m = -INFINITY;
+    float s0 = 0.f, s1 = 0.f, s3 = 0.f, m = -INFINITY;
     for (int w = 0; w < NW; ++w) {
       s0 += s_sc[w][0];
       s1 += s_sc[w][1];
+      s3 += s_sc[w][3];
       m = fmaxf(m, s_sc[w][2]);
     }
     prow[0] = s0;
     prow[1] = s1;
     prow[2] = m;
-    prow[3] = 0.f;
+    prow[3] = p.radii ? NAN : s3;  // the QP bound holds for points only
   }
   ses_finish<T>(p, smem_raw);
 }
@@ -597,10 +644,12 @@ __global__ void __launch_bounds__(kMergeBlock) ses_merge_kernel(SesMergeParams m
   if (hdr->stopped && !m.eval_only) return;  // as the pass kernels: a stopped FTP is left as is
   const int d = m.d, dp = dpad4(d), st = ses_partial_stride(d);
   const int tid = threadIdx.x;
-  // dynamic shared memory: column totals (s, c) | mean | v_1
+  // dynamic shared memory: column totals (s, c) | mean | v_1 | Bbar
   float2* raw = reinterpret_cast<float2*>(smem_raw);
   double* s_mean = reinterpret_cast<double*>(smem_raw) + st;
   double* s_v1 = s_mean + dp;
+  double* s_dual = s_v1 + dp;
+  const double* dual = state_dual(m.state, d);
   constexpr int HW = (int)(sizeof(StateHdr) / 8);
   if (tid < HW) s_hdr[tid] = reinterpret_cast<const double*>(hdr)[tid];
   const double* mean = state_mean(m.state);
@@ -608,13 +657,14 @@ __global__ void __launch_bounds__(kMergeBlock) ses_merge_kernel(SesMergeParams m
   for (int j = tid; j < d; j += blockDim.x) {
     s_mean[j] = mean[j];
     s_v1[j] = (double)elem_to_float<T>(v1 + j);
+    s_dual[j] = dual[j];
   }
   auto opof = [](int pc) { return pc == 2 ? 1 : 0; };
   reduce_rows(m.rows, 0, m.ranks, st, raw, s_scr, opof);  // ends with a barrier
   if (tid >= 32) return;
   const double gam1 = m.radius1 ? (double)__ldg(m.radius1) : 0.0;
   ses_finish_warp(raw, s_mean, s_v1, *reinterpret_cast<const StateHdr*>(s_hdr), m.state, d, m.alpha, gam1,
-                  m.eta_over_rho, m.eval_only, m.out);
+                  m.eta_over_rho, m.eval_only, m.out, nullptr, s_dual);
 }
 
 }  // namespace pdscp

@@ -206,9 +206,12 @@ __global__ void __launch_bounds__(kBlock) svm_iter_kernel(SvmParams p) {
 // shared memory); h: a copy of the state header. Writes the state and the
 // step record (out, may be null). FP32 math, FP64 running means (as in
 // ses_finish_warp).
+// s_dual (may be null: no averaged bound): the state's zbar, read beforehand
+// into shared memory; with it the averaged Claim 8 upper bound is advanced.
 static __device__ __noinline__ void svm_finish_warp(const float2* raw, const double* s_mean, const StateHdr& h,
                                              void* state, int d, double alpha_d, double D_d, double eta_over_rho,
-                                             int eval_only, pdscp_step_out* out, float* tape = nullptr) {
+                                             int eval_only, pdscp_step_out* out, float* tape = nullptr,
+                                             const double* s_dual = nullptr) {
   const int lane = threadIdx.x & 31;
   const int dp = dpad4(d);
   StateHdr* hdr = reinterpret_cast<StateHdr*>(state);
@@ -223,8 +226,17 @@ static __device__ __noinline__ void svm_finish_warp(const float2* raw, const dou
   const float trmu = SP * rS, trga = SQ * rS;
   const float alpha = (float)alpha_d, D = (float)D_d;
   const double s1b = h.s1bar, s2b = h.s2bar;
-  // |z|^2, Claim 8 |P mu/Tr mu - Q gamma/Tr gamma|^2, |wbar|^2, z . wbar
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  const int64_t t = h.t;
+  // Averaged Claim 8 bound: zbar, the average over the alpha-FTP of the vectors
+  // P mu/Tr mu - Q gamma/Tr gamma (iterate t weighted by t), is again such a
+  // vector for the averaged class-normalised weights, so OPT <= |zbar|.
+  const bool qp = s_dual != nullptr;
+  const bool qpu = qp && !eval_only && t >= 1 && SP > 0.f && SQ > 0.f;
+  const double wsum = h.dual_w + (qpu ? (double)t : 0.0);
+  const double rw = qpu ? (double)t / wsum : 0.0;
+  double* zbar = state_dual(state, d);
+  // |z|^2, Claim 8 |P mu/Tr mu - Q gamma/Tr gamma|^2, |wbar|^2, z . wbar, |zbar|^2
+  float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   for (int j = lane; j < d; j += 32) {
     const float zp = tot(4 + j), zq = tot(4 + dp + j);
     const float z = (zp - zq) * rS;
@@ -234,8 +246,17 @@ static __device__ __noinline__ void svm_finish_warp(const float2* raw, const dou
     acc[1] = fmaf(df, df, acc[1]);
     acc[2] = fmaf(m, m, acc[2]);
     acc[3] = fmaf(z, m, acc[3]);
+    if (qp) {
+      double b = s_dual[j];
+      if (qpu) {
+        b += rw * (double)(df - (float)b);
+        zbar[j] = b;
+      }
+      acc[4] = fmaf((float)b, (float)b, acc[4]);
+    }
   }
-  warp_sum_kf<4>(acc);
+  warp_sum_kf<5>(acc);
+  const float UBq = (qp && wsum > 0.0) ? sqrtf(acc[4]) : INFINITY;
   const float rnz = acc[0] > 0.f ? 1.0f / sqrtf(acc[0]) : 0.f;
   const float nz = acc[0] * rnz;
   const float s1 = (trmu <= trga) ? D : alpha - D;
@@ -247,7 +268,6 @@ static __device__ __noinline__ void svm_finish_warp(const float2* raw, const dou
   const float wscale = rS * rnz;                                        // w = (Z_P - Z_Q) wscale
   const double fd = (double)f;
 
-  const int64_t t = h.t;
   int status = PDSCP_OK;
   if (!(S > 0.f) || !isfinite(S) || !isfinite(V)) status = PDSCP_ERR_NUMERIC;
   bool stop = false, failed = false;
@@ -310,7 +330,9 @@ static __device__ __noinline__ void svm_finish_warp(const float2* raw, const dou
     }
   }
   if (lane == 0) {
-    if (!eval_only && (double)UB < h.ub_best) hdr->ub_best = (double)UB;
+    const double ubn = (double)fminf(UB, UBq);
+    if (!eval_only && ubn < h.ub_best) hdr->ub_best = ubn;
+    if (qpu) hdr->dual_w = wsum;
     if (streak != h.streak) hdr->streak = streak;
     if (set_fprev) hdr->f_prev = fd;
     if (better) hdr->best_f = fd;
@@ -347,6 +369,7 @@ static __device__ __noinline__ void svm_finish_warp(const float2* raw, const dou
       o.status = status;
       o.outcome = outcome;
       o.k = (double)t * eta_over_rho;
+      o.dual_bound = (double)UBq;
       *out = o;
     }
   }
@@ -359,7 +382,7 @@ static __device__ __noinline__ void svm_finish_warm(const SvmParams& p, unsigned
   StateHdr h;
   memset(&h, 0, sizeof(h));
   svm_finish_warp(raw, s_mean, h, p.sink, d, p.alpha, p.D, p.eta_over_rho, p.eval_only, warm_sink_out(p.sink, d),
-                  p.tape ? warm_sink_tape(p.sink, d) : nullptr);
+                  p.tape ? warm_sink_tape(p.sink, d) : nullptr, s_mean + dpad4(d));
 }
 
 // O(d) finish of one SVM iteration. Every CTA calls it after writing its
@@ -379,26 +402,31 @@ __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
   StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
   double* mean = state_mean(p.state);
   const int tid = threadIdx.x;
-  // dynamic shared memory: column totals as (s, c) pairs | mean | staged partial rows
+  // dynamic shared memory: column totals as (s, c) pairs | mean | zbar | staged partial rows
   float2* raw = reinterpret_cast<float2*>(smem_raw);
   double* s_mean = reinterpret_cast<double*>(smem_raw) + st;
-  float* stage = reinterpret_cast<float*>(s_mean + dp);
+  double* s_dual = s_mean + dp;
+  float* stage = reinterpret_cast<float*>(s_dual + dp);
+  const double* dual = state_dual(p.state, d);
+  // the FP64 header, mean and zbar go straight into shared memory before the
+  // reduction (cp.async: their latency overlaps it, no register is held)
   constexpr int HW = (int)(sizeof(StateHdr) / 8);
-  const double hw = tid < HW ? reinterpret_cast<const double*>(hdr)[tid] : 0.0;
-  const double m0 = tid < d ? mean[tid] : 0.0;
+  if (tid < HW) cp_async8(s_hdr + tid, reinterpret_cast<const double*>(hdr) + tid);
+  for (int j = tid; j < d; j += blockDim.x) {
+    cp_async8(s_mean + j, mean + j);
+    cp_async8(s_dual + j, dual + j);
+  }
   final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single, 3, 2, st);
+  cp_async_wait_all();
   if (p.row_out) {  // a shard of a row-sharded iteration: hand the totals to the merge
     for (int pc = tid; pc < st; pc += blockDim.x) p.row_out[pc] = raw[pc];
     return;
   }
-  if (tid < HW) s_hdr[tid] = hw;
-  if (tid < d) s_mean[tid] = m0;
-  for (int j = tid + blockDim.x; j < d; j += blockDim.x) s_mean[j] = mean[j];
   __syncthreads();
   // The O(d) math runs in warp 0 alone (see ses_finish).
   if (tid >= 32) return;
   svm_finish_warp(raw, s_mean, *reinterpret_cast<const StateHdr*>(s_hdr), p.state, d, p.alpha, p.D,
-                  p.eta_over_rho, p.eval_only, p.out, p.tape);
+                  p.eta_over_rho, p.eval_only, p.out, p.tape, s_dual);
 }
 
 }  // namespace pdscp
@@ -596,15 +624,20 @@ __global__ void __launch_bounds__(kSvmMergeBlock) svm_merge_kernel(SvmMergeParam
   const int tid = threadIdx.x;
   float2* raw = reinterpret_cast<float2*>(smem_raw);
   double* s_mean = reinterpret_cast<double*>(smem_raw) + st;
+  double* s_dual = s_mean + dpad4(d);
   constexpr int HW = (int)(sizeof(StateHdr) / 8);
   if (tid < HW) s_hdr[tid] = reinterpret_cast<const double*>(hdr)[tid];
   const double* mean = state_mean(m.state);
-  for (int j = tid; j < d; j += blockDim.x) s_mean[j] = mean[j];
+  const double* dual = state_dual(m.state, d);
+  for (int j = tid; j < d; j += blockDim.x) {
+    s_mean[j] = mean[j];
+    s_dual[j] = dual[j];
+  }
   auto opof = [](int pc) { return pc == 2 ? 2 : (pc == 3 ? 1 : 0); };
   reduce_rows(m.rows, 0, m.ranks, st, raw, s_scr, opof);  // ends with a barrier
   if (tid >= 32) return;
   svm_finish_warp(raw, s_mean, *reinterpret_cast<const StateHdr*>(s_hdr), m.state, d, m.alpha, m.D,
-                  m.eta_over_rho, m.eval_only, m.out);
+                  m.eta_over_rho, m.eval_only, m.out, nullptr, s_dual);
 }
 
 }  // namespace pdscp

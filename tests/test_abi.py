@@ -38,7 +38,8 @@ def test_version_and_sizes(lib):
     assert lib.pdscp_version() >= 100
     out = ctypes.c_size_t()
     assert lib.pdscp_state_size(_ffi.SES, 32, ctypes.byref(out)) == 0
-    assert out.value == 128 + 32 * 8 + 2 * 32 * 4
+    # header | FP64 mean | FP32 mean | FP32 best point | FP64 averaged dual vector
+    assert out.value == 128 + 32 * 8 + 2 * 32 * 4 + 32 * 8
     assert lib.pdscp_workspace_size(_ffi.SVM, 1000, 128, ctypes.byref(out)) == 0 and out.value > 0
     assert lib.pdscp_workspace_size(_ffi.SES, 10, 0, ctypes.byref(out)) == 7
 

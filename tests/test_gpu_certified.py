@@ -1,0 +1,102 @@
+"""CERTIFIED solves (ses_solve / svm_solve, mode "certified") on the GPU
+against exact optima and the FP64 oracle's certified search.
+
+Both searches draw only proven conclusions, so each one's report brackets
+OPT; the GPU's trajectory differs from the oracle's by FP32 rounding (and
+its decisions may fall one poll apart), so the two are compared through
+what they certify: both brackets contain the exact optimum where one is
+known, both close to within eps, and both radii (margins) lie within the
+other's certified range.
+"""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import exact, ses as oses, svm as osvm
+from paper_2405_09157_gb300 import api, datagen
+
+pytestmark = pytest.mark.gpu
+FP = 1e-5  # FP32 slack on a certified value (relative)
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_ses_certified_brackets_welzl():
+    V32 = datagen.ses_uniform(1000, 2, seed=0)
+    V = V32.astype(np.float64)
+    _, opt = exact.mec_2d(V)
+    center, rep = api.ses_solve(_cuda(V32), eps=1e-3, mode="certified", max_iters=100_000, poll_every=64)
+    assert rep["status"] == 0
+    assert rep["lower_bound"] <= opt * (1 + FP) and rep["value"] >= opt * (1 - FP)
+    assert rep["value"] <= (1 + 1e-3) * rep["lower_bound"]
+    c = center.cpu().numpy().astype(np.float64)
+    assert oses.ses_objective(V, None, c) <= rep["value"] * (1 + FP)
+
+
+@pytest.mark.parametrize("n,d", [(2000, 8), (3000, 32)])
+def test_ses_certified_matches_oracle(n, d):
+    V32 = datagen.ses_gaussian(n, d, seed=1)
+    V = V32.astype(np.float64)
+    ref = oses.ses_solve(V, eps=1e-3, mode="certified", max_iters=100_000, poll_every=64)
+    center, rep = api.ses_solve(_cuda(V32), eps=1e-3, mode="certified", max_iters=100_000, poll_every=64)
+    assert rep["status"] == 0 and ref["radius"] <= (1 + 1e-3) * ref["lower_bound"]
+    assert rep["value"] <= (1 + 1e-3) * rep["lower_bound"]
+    # each certified interval contains the other's ball radius and lower bound
+    assert rep["lower_bound"] <= ref["radius"] * (1 + FP) and ref["lower_bound"] <= rep["value"] * (1 + FP)
+    assert abs(rep["value"] - ref["radius"]) <= 1e-3 * ref["radius"]
+    c = center.cpu().numpy().astype(np.float64)
+    assert oses.ses_objective(V, None, c) <= rep["value"] * (1 + FP)
+    # the GPU's iteration count is the oracle's up to the decisions FP32 moves by a poll or a step
+    assert rep["iters"] <= 3 * ref["iters"] + 4096
+
+
+def test_ses_certified_spheres_use_primal_bound_only():
+    V32 = datagen.ses_gaussian(1500, 4, seed=3)
+    g32 = (0.2 * np.random.default_rng(3).random(1500)).astype(np.float32)
+    center, rep = api.ses_solve(_cuda(V32), radii=_cuda(g32), eps=1e-2, mode="certified", max_iters=60_000,
+                                poll_every=64)
+    V, g = V32.astype(np.float64), g32.astype(np.float64)
+    c = center.cpu().numpy().astype(np.float64)
+    assert oses.ses_objective(V, g, c) <= rep["value"] * (1 + FP)
+    assert rep["lower_bound"] <= rep["value"]
+    ref = oses.ses_solve(V, g, eps=1e-2, mode="certified", max_iters=60_000, poll_every=64)
+    assert rep["lower_bound"] <= ref["radius"] * (1 + FP) and ref["lower_bound"] <= rep["value"] * (1 + FP)
+
+
+def test_svm_certified_brackets_bruteforce():
+    X32, y = datagen.svm_clusters(5, 5, 2, band=0.5, seed=7)
+    X = X32.astype(np.float64)
+    opt, _, _ = exact.pd_bruteforce(X[y > 0], X[y < 0])
+    w, rep = api.svm_solve(_cuda(X32), _cuda(y), eps=1e-3, mode="certified", max_iters=100_000, poll_every=64)
+    assert rep["status"] == 0
+    assert rep["lower_bound"] <= opt * (1 + FP) and rep["upper_bound"] >= opt * (1 - FP)
+    assert rep["upper_bound"] <= (1 + 1e-3) * rep["lower_bound"]
+    wn = w.cpu().numpy().astype(np.float64)
+    assert math.isclose(exact.svm_margin_of(X[y > 0], X[y < 0], wn), rep["value"], rel_tol=1e-4)
+
+
+def test_svm_certified_matches_oracle():
+    X32, y = datagen.svm_clusters(300, 300, 16, seed=1)
+    X = X32.astype(np.float64)
+    ref = osvm.svm_solve(X, y, eps=1e-2, mode="certified", max_iters=60_000, poll_every=64)
+    w, rep = api.svm_solve(_cuda(X32), _cuda(y), eps=1e-2, mode="certified", max_iters=60_000, poll_every=64)
+    assert rep["status"] == 0 and ref["upper_bound"] <= (1 + 1e-2) * ref["lower_bound"]
+    assert rep["upper_bound"] <= (1 + 1e-2) * rep["lower_bound"]
+    assert rep["lower_bound"] <= ref["upper_bound"] * (1 + FP) and ref["lower_bound"] <= rep["upper_bound"] * (1 + FP)
+
+
+def test_ses_certified_full_size():
+    # the benchmarked workload: n = 1e6, d = 32, N(0, I), eps = 1e-3
+    V32 = datagen.ses_gaussian(1_000_000, 32, seed=0)
+    center, rep = api.ses_solve(_cuda(V32), eps=1e-3, mode="certified", max_iters=200_000, poll_every=256)
+    assert rep["status"] == 0
+    assert rep["value"] <= (1 + 1e-3) * rep["lower_bound"]
+    # the centre's radius, recomputed in FP64 over all points, is the reported one
+    c = center.cpu().numpy().astype(np.float64)
+    r = float(np.sqrt(np.max(np.sum((V32.astype(np.float64) - c) ** 2, axis=1))))
+    assert abs(r - rep["value"]) <= FP * r

@@ -52,13 +52,24 @@ def gpu_ses_traj(V32, g32, alpha, eta_over_rho, T, dtype=torch.float32, rules=_f
 def oracle_ses_traj(V, g, alpha, eta, rho, T):
     ubar = V[0].copy()
     recs = []
+    avg = oses.ses_dual_state(V.shape[1])
     for t in range(T):
-        rec = oses.ses_step(V, g, ubar, t, alpha, eta, rho)
+        rec = oses.ses_step(V, g, ubar, t, alpha, eta, rho, avg=avg)
         recs.append(rec)
         if rec["failed"]:
             break
         ubar = rec["ubar_next"]
     return recs, ubar
+
+
+def dual_tol(D, lb):
+    """Tolerance for the averaged QP bound sqrt(Abar - |Bbar|^2): the FP32
+    moments carry an error of about eta2 = 1e-6 D^2 (a few ulp of D^2, the
+    scale of |v_i - v_1|^2), which moves the square root by at most
+    min(sqrt(eta2), eta2/lb); that is within RTOL D once lb >= D/10 and
+    grows only where the averaged weights sit on nearly one point (lb -> 0)."""
+    eta2 = 1e-6 * D * D
+    return max(RTOL * D, min(math.sqrt(eta2), eta2 / max(lb, 1e-300)))
 
 
 def compare_ses(gr, orr, gmean, omean, D):
@@ -70,6 +81,8 @@ def compare_ses(gr, orr, gmean, omean, D):
         assert abs(g["objective"] - o["objective"]) <= tol, (t, g["objective"], o["objective"])
         assert abs(g["oracle_value"] - o["oracle_value"]) <= tol, (t, g["oracle_value"], o["oracle_value"])
         assert abs(g["lower_bound"] - o["lower_bound"]) <= tol, (t, g["lower_bound"], o["lower_bound"])
+        assert abs(g["dual_bound"] - o["dual_bound"]) <= dual_tol(D, o["dual_bound"]), (t, g["dual_bound"],
+                                                                                        o["dual_bound"])
         if abs(o["oracle_value"]) > tol:
             assert bool(g["failed"]) == o["failed"], t
     assert np.linalg.norm(gmean - omean) <= tol, (gmean[:4], omean[:4])
@@ -131,12 +144,15 @@ def forced_ses(n, d, seed, kDs, rel_alpha=0.8, radii=False, dtype=torch.float32,
         m.step(alpha, eta / rho, out=out[j])
         mean, _ = m.read()
         torch.cuda.synchronize()
-        o = oses.ses_step(V, g, ubar, t, alpha, eta, rho)
+        # a checkpoint restarts the averaged bound: this step's weights alone
+        o = oses.ses_step(V, g, ubar, t, alpha, eta, rho, avg=oses.ses_dual_state(d))
         r = api.decode_steps(out[j])[0]
         tol = RTOL * D
         assert r["status"] == 0 and r["t"] == (t + 1 if not o["failed"] else t)
         for key in ("objective", "oracle_value", "lower_bound"):
             assert abs(r[key] - o[key]) <= tol, (kD, key, r[key], o[key])
+        assert abs(r["dual_bound"] - o["dual_bound"]) <= dual_tol(D, o["dual_bound"]), (kD, r["dual_bound"],
+                                                                                         o["dual_bound"])
         assert np.linalg.norm(mean.cpu().numpy().astype(np.float64) - o["ubar_next"]) <= tol, kD
 
 
@@ -253,13 +269,18 @@ def run_svm_case(n1, n2, d, seed=0, T=100, eta=0.5, rel_alpha=0.5, dtype=torch.f
     gr, gmean = gpu_svm_traj(X32, y, alpha, eta / rho, D, T, dtype)
     wbar, s1, s2 = np.zeros(d), 0.0, 0.0
     tol = RTOL * D
+    avg = osvm.svm_dual_state(d)
     for t in range(T):
-        o = osvm.svm_step(X, y, wbar, s1, s2, t, alpha, eta, rho, D)
+        o = osvm.svm_step(X, y, wbar, s1, s2, t, alpha, eta, rho, D, avg=avg)
         g = gr[t]
         assert g["status"] == 0
         assert abs(g["objective"] - o["objective"]) <= tol, (t, g["objective"], o["objective"])
         assert abs(g["oracle_value"] - o["oracle_value"]) <= tol, (t, g["oracle_value"], o["oracle_value"])
         assert abs(g["upper_bound"] - o["upper_bound"]) <= tol, (t, g["upper_bound"], o["upper_bound"])
+        if t == 0:
+            assert math.isinf(g["dual_bound"]) and math.isinf(o["dual_bound"])
+        else:
+            assert abs(g["dual_bound"] - o["dual_bound"]) <= tol, (t, g["dual_bound"], o["dual_bound"])
         if abs(o["oracle_value"]) > tol:
             assert bool(g["failed"]) == o["failed"]
         if o["failed"]:
@@ -287,11 +308,11 @@ def forced_svm(n1, n2, d, seed, kDs, dtype=torch.float32, eta=0.5, rel_alpha=0.5
         m.step(alpha, eta / rho, out=out[j], D=D)
         mean, _ = m.read()
         torch.cuda.synchronize()
-        o = osvm.svm_step(X, y, w, s1, s2, t, alpha, eta, rho, D)
+        o = osvm.svm_step(X, y, w, s1, s2, t, alpha, eta, rho, D, avg=osvm.svm_dual_state(d))
         r = api.decode_steps(out[j])[0]
         tol = RTOL * D
         assert r["status"] == 0
-        for key in ("objective", "oracle_value", "upper_bound"):
+        for key in ("objective", "oracle_value", "upper_bound", "dual_bound"):
             assert abs(r[key] - o[key]) <= tol, (kD, key, r[key], o[key])
         mm = mean.cpu().numpy().astype(np.float64)
         assert np.linalg.norm(mm[:d] - o["wbar_next"]) <= RTOL
