@@ -331,21 +331,25 @@ pdscp_status ses_batch_read(int32_t num, const void* ws_dev, float* mean_dev, fl
 /*
  * Batched search: every instance runs the whole search of Sec. 3 (alpha in
  * [D/2, D], alpha_i = L + (U-L)/3, eps_i and T_i of Theorem 2 with the Sec.
- * 4.1 constants, the Sec. 5 rules when opts->mode is PDSCP_MODE_PRACTICAL),
+ * 4.1 constants, the Sec. 5 rules when opts->mode is PDSCP_MODE_PRACTICAL;
+ * PDSCP_MODE_CERTIFIED as in ses_solve, its certificate and progress tests
+ * made every opts->poll_every iterations of an instance's FTP),
  * with the decisions of ses_solve, on the device: the CTA that finishes an
  * instance's iteration also updates its search and starts its next
  * alpha-FTP. An instance's first launch is an evaluation pass at v_1 (which
  * gives D); a finished instance's tiles are skipped.
  *   ses_batch_solve_init: as ses_batch_init, plus the search records and
- *     options (opts->poll_every is not used; opts->max_iters counts MWU
- *     iterations per instance). Synchronises the stream.
+ *     options (opts->poll_every is used by the CERTIFIED mode only;
+ *     opts->max_iters counts MWU iterations per instance). Synchronises the
+ *     stream.
  *   ses_batch_solve_run: replays a CUDA graph of launches_per_poll launches
  *     on `stream` until every instance is done or max_launches launches ran
  *     (host polls a device counter after each replay); reports the launches
  *     run and the instances done (host pointers, may be NULL).
  *   ses_batch_solve_read: one pdscp_report per instance (value = upper_bound
- *     = radius of the returned centre, lower_bound = best primal bound of Eq.
- *     primal_construction, search_L/U, iters, search_steps, status: OK when
+ *     = radius of the returned centre, lower_bound = best lower bound (Eq.
+ *     primal_construction, the averaged QP bound; CERTIFIED: also the search's
+ *     L), search_L/U, iters, search_steps, status: OK when
  *     U <= (1+eps) L or ub <= (1+eps) lb, PDSCP_ERR_NOT_CONVERGED otherwise)
  *     to reports_dev and the centres, packed as in ses_batch_read, to
  *     centers_dev (either may be NULL).

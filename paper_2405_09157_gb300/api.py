@@ -475,11 +475,12 @@ class SesBatch:
         return tr.value, ms.value
 
     def solve(self, eps=1e-3, mode="practical", max_iters=1_000_000, max_steps=200, eta=None, delta=1e-4,
-              patience=10, launches_per_poll=32, max_launches=10_000_000, stream=None):
+              patience=10, launches_per_poll=32, max_launches=10_000_000, poll_every=256, stream=None):
         """The search of Sec. 3 for every instance, on the device. Returns
         (reports: structured numpy array of pdscp_report, centres: list of
-        float32 arrays, launches run)."""
-        o = _options(eps, mode, max_iters, 1, max_steps, eta, delta, patience)
+        float32 arrays, launches run). poll_every: iterations between the
+        certificate tests of mode "certified"."""
+        o = _options(eps, mode, max_iters, poll_every, max_steps, eta, delta, patience)
         lib = load()
         offs, n, d = self._host_tables()
         check(lib.ses_batch_solve_init(self.num, _vp(self.pts), self.pts.numel(), offs, n, d, self.tile_rows,

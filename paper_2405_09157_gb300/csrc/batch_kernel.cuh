@@ -57,16 +57,27 @@ struct BatchSearch {
   double L, U, lb, ub;        // search range and certificates
   double alpha, eps_i, eta_over_rho;
   int64_t T, cap, total;      // theorem count of this FTP, its iteration cap, iterations so far
-  int32_t steps, phase, status, pad;
+  int32_t steps, phase, status, why;  // why: how a CERTIFIED FTP ended (kWhy*)
+  double eta_c;               // CERTIFIED: the current step size
+  double last_gap, next_check;  // CERTIFIED: progress test of the running FTP
   float center[kBatchMaxD];   // the centre achieving ub
 };
-static_assert(sizeof(BatchSearch) == 376, "search record layout");
+static_assert(sizeof(BatchSearch) == 400, "search record layout");
 
 struct BatchSolveOpts {
-  double eps, delta, eta;     // eta <= 0: eta_i = sqrt(ln r / T_i) (Theorem 2)
+  double eps, delta, eta;     // eta <= 0: eta_i = sqrt(ln r / T_i) (Theorem 2); CERTIFIED: 1
   int64_t max_iters;          // per instance
-  int32_t patience, rules, max_steps, pad;
+  int32_t patience, rules, max_steps, mode;  // mode: PDSCP_MODE_*
+  int32_t poll, pad;          // CERTIFIED: iterations between certificate tests
 };
+
+// How a CERTIFIED alpha-FTP ended besides the device's own stop (ses_solve's rules).
+constexpr int kWhyBudget = 0;  // its iteration cap
+constexpr int kWhyClosed = 1;  // the certificates closed at a poll
+constexpr int kWhyStuck = 2;   // its own gap stopped shrinking: eta is halved
+constexpr double kCertFirstCheck = 1024.0;  // first progress test at eta = 1 (1024/eta in general)
+constexpr double kCertShrink = 0.8;         // the FTP's own gap must shrink by this while t doubles
+constexpr double kCertMinEta = 1.0 / 64.0;  // eta is not halved below this
 
 // The search options live in the workspace at this offset (after the header).
 constexpr size_t kBatchOptsOff = 512;
@@ -99,7 +110,7 @@ inline int batch_shape(int d, bool aligned16) {
 // arithmetic as ses_iter_kernel (rows 0 of the instance, v_1, excluded).
 template <int VW, int LPP, int NCH, int U>
 __device__ void batch_tile(const float* pts, int d, int64_t r0, int64_t r1, const float* s_ub, float kr, float H,
-                           float alpha, float* sG, float (*s_sc)[3]) {
+                           float alpha, float* sG, float (*s_sc)[4], float* s_cs) {
   const int nch = (d + VW - 1) / VW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = lane / LPP, gl = lane % LPP;
@@ -115,6 +126,7 @@ __device__ void batch_tile(const float* pts, int d, int64_t r0, int64_t r1, cons
     }
   }
   float S = 0.f, W = 0.f, maxd = -INFINITY;
+  s_cs[threadIdx.x] = 0.f;  // per-lane sum of the ORACLE coefficients (shared: no register in the loop)
   for (int64_t base = r0 + (int64_t)warp * (PPW * U); base < r1; base += (int64_t)kBatchWarps * (PPW * U)) {
     float x[U][NCH][VW];
 #pragma unroll
@@ -155,6 +167,7 @@ __device__ void batch_tile(const float* pts, int d, int64_t r0, int64_t r1, cons
         if (gl == 0) {
           S += sum;
           W += alpha * sum - dist * dif;
+          s_cs[threadIdx.x] += c;
           maxd = fmaxf(maxd, dist);
         }
       }
@@ -171,6 +184,7 @@ __device__ void batch_tile(const float* pts, int d, int64_t r0, int64_t r1, cons
 #pragma unroll
       for (int e = 0; e < VW; ++e) G[j][e] += __shfl_xor_sync(0xffffffffu, G[j][e], o);
   S = warp_sum(S);
+  const float Cs = warp_sum(s_cs[threadIdx.x]);
   W = warp_sum(W);
   maxd = warp_max(maxd);
   if (grp == 0) {
@@ -186,13 +200,16 @@ __device__ void batch_tile(const float* pts, int d, int64_t r0, int64_t r1, cons
     s_sc[warp][0] = S;
     s_sc[warp][1] = W;
     s_sc[warp][2] = maxd;
+    s_sc[warp][3] = Cs;
   }
 }
 
 // One warp, after the instance's finish: advances the instance's search
 // (the decisions of ses_solve: Sec. 3's update of [L, U] from the FTP's
-// outcome, Sec. 5's early exits, the primal lower bound of Eq.
-// primal_construction as a certificate) and starts its next alpha-FTP.
+// outcome, Sec. 5's early exits, the lower bounds of Eq. primal_construction
+// and of the averaged QP weights as certificates; in CERTIFIED mode only
+// proven conclusions, polls every o.poll iterations) and starts its next
+// alpha-FTP.
 // Runs in its own kernel after each iteration launch (ses_batch_search_kernel):
 // called from the streaming kernel, its FP64 bookkeeping would raise that
 // kernel's register count and lower its occupancy.
@@ -204,6 +221,7 @@ static __device__ __forceinline__ void batch_search_update(BatchSearch* sr, void
   StateHdr* hdr = reinterpret_cast<StateHdr*>(state);
   const StateHdr h = *hdr;  // written by lane 0 of this warp before the __syncwarp
   BatchSearch r = *sr;
+  const bool cert = o.mode == PDSCP_MODE_CERTIFIED;
   bool end_ftp = false, start_ftp = false, done = false;
   if (h.status != PDSCP_OK) {
     r.status = h.status;
@@ -220,6 +238,7 @@ static __device__ __forceinline__ void batch_search_update(BatchSearch* sr, void
       r.U = r.D;
       r.lb = 0.0;
       r.ub = INFINITY;
+      r.eta_c = o.eta > 0.0 ? o.eta : 1.0;
       start_ftp = true;
     }
   } else if (r.phase == kPhaseFinal) {
@@ -228,6 +247,21 @@ static __device__ __forceinline__ void batch_search_update(BatchSearch* sr, void
     end_ftp = true;
   } else if (h.t >= r.cap) {
     r.phase = kPhaseFinal;  // the next launch evaluates f at the final mean
+  } else if (cert && h.t % o.poll == 0) {
+    // a poll: the certificates closed, or the FTP's own gap stopped shrinking
+    if (fmin(r.ub, h.best_f) <= (1.0 + o.eps) * fmax(fmax(r.lb, r.L), h.lb_best)) {
+      r.why = kWhyClosed;
+      r.phase = kPhaseFinal;
+    } else if ((double)h.t >= r.next_check) {
+      const double gap = h.lb_best > 0.0 ? h.best_f / h.lb_best - 1.0 : INFINITY;
+      if (gap > kCertShrink * r.last_gap) {
+        r.why = kWhyStuck;
+        r.phase = kPhaseFinal;
+      } else {
+        r.last_gap = gap;
+        r.next_check *= 2.0;
+      }
+    }
   }
   if (end_ftp) {
     const int64_t iters = h.t;
@@ -238,20 +272,36 @@ static __device__ __forceinline__ void batch_search_update(BatchSearch* sr, void
     for (int j = lane; j < d; j += 32)
       if (better) r.center[j] = state_best(state, d)[j];
     if (h.lb_best > r.lb) r.lb = h.lb_best;
-    if (oc == PDSCP_OUT_SEPARATED) {
-      r.L = fmax(r.L, r.alpha);
-    } else if (iters >= r.T || oc == PDSCP_OUT_STALLED || oc == PDSCP_OUT_BEAT_ALPHA) {
-      r.U = fmin(fmin(r.U, (1.0 + r.eps_i) * r.alpha), r.ub);
-    }
-    r.L = fmax(r.L, r.lb);
-    r.steps += 1;
-    if (oc == PDSCP_OUT_RUNNING && iters < r.T) {
-      done = true;  // the iteration budget ended this FTP
-    } else if (!(r.U > (1.0 + o.eps) * r.L && r.ub > (1.0 + o.eps) * r.lb && r.total < o.max_iters &&
-                 r.steps < o.max_steps)) {
-      done = true;
+    if (cert) {
+      if (oc == PDSCP_OUT_SEPARATED) r.L = fmax(r.L, r.alpha);
+      if (oc == PDSCP_OUT_RUNNING && r.why == kWhyStuck) r.eta_c *= 0.5;
+      r.U = fmin(r.U, r.ub);
+      r.L = fmax(r.L, r.lb);
+      r.steps += 1;
+      if (oc == PDSCP_OUT_RUNNING && r.why == kWhyBudget) {
+        done = true;  // the iteration budget ended this FTP
+      } else if (!(r.ub > (1.0 + o.eps) * fmax(r.lb, r.L) && r.total < o.max_iters && r.steps < o.max_steps)) {
+        done = true;
+      } else {
+        start_ftp = true;
+      }
+      if (done) r.lb = fmax(r.lb, r.L);  // a separation is a proof too
     } else {
-      start_ftp = true;
+      if (oc == PDSCP_OUT_SEPARATED) {
+        r.L = fmax(r.L, r.alpha);
+      } else if (iters >= r.T || oc == PDSCP_OUT_STALLED || oc == PDSCP_OUT_BEAT_ALPHA) {
+        r.U = fmin(fmin(r.U, (1.0 + r.eps_i) * r.alpha), r.ub);
+      }
+      r.L = fmax(r.L, r.lb);
+      r.steps += 1;
+      if (oc == PDSCP_OUT_RUNNING && iters < r.T) {
+        done = true;  // the iteration budget ended this FTP
+      } else if (!(r.U > (1.0 + o.eps) * r.L && r.ub > (1.0 + o.eps) * r.lb && r.total < o.max_iters &&
+                   r.steps < o.max_steps)) {
+        done = true;
+      } else {
+        start_ftp = true;
+      }
     }
   }
   if (start_ftp) {
@@ -259,10 +309,14 @@ static __device__ __forceinline__ void batch_search_update(BatchSearch* sr, void
     r.eps_i = (r.U - r.L) / (3.0 * r.alpha);
     const double Tf = ceil(36.0 * r.D * r.D * r.logr / (r.eps_i * r.eps_i * r.alpha * r.alpha));
     r.T = Tf > 4.0e18 ? (int64_t)4e18 : (int64_t)Tf;
-    const double eta = o.eta > 0.0 ? o.eta : sqrt(r.logr / (double)r.T);
+    const double eta = cert ? r.eta_c : (o.eta > 0.0 ? o.eta : sqrt(r.logr / (double)r.T));
     r.eta_over_rho = eta / r.rho;
     const int64_t left = o.max_iters - r.total;
+    if (cert) r.T = left;  // no theorem count: the FTP runs until a proof, the certificates or the budget
     r.cap = r.T < left ? r.T : left;
+    r.why = kWhyBudget;
+    r.last_gap = INFINITY;
+    r.next_check = (cert && eta > kCertMinEta) ? ceil(kCertFirstCheck / eta) : INFINITY;
     r.phase = kPhaseFtp;
     // a fresh alpha-FTP: t = 0, mean = v_1 (as mwu_state_init)
     const int dp = dpad4(d);
@@ -319,6 +373,10 @@ static __device__ __forceinline__ void batch_search_update(BatchSearch* sr, void
     dst->steps = r.steps;
     dst->phase = r.phase;
     dst->status = r.status;
+    dst->why = r.why;
+    dst->eta_c = r.eta_c;
+    dst->last_gap = r.last_gap;
+    dst->next_check = r.next_check;
   }
   for (int j = lane; j < d; j += 32) sr->center[j] = r.center[j];
 }
@@ -330,7 +388,7 @@ static __device__ __forceinline__ void batch_search_update(BatchSearch* sr, void
 // squared distances (GroupScatter), as in ses_iter_t_kernel.
 template <int VW, int LPP, int NI>
 __device__ void batch_tile_t(const float* pts, int d, int64_t r0, int64_t r1, const float* s_ub, float kr,
-                             float H, float alpha, float* sG, float (*s_sc)[3]) {
+                             float H, float alpha, float* sG, float (*s_sc)[4], float* s_cs) {
   using GS = GroupScatter<LPP, NI>;
   const int nch = d / VW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -348,6 +406,7 @@ __device__ void batch_tile_t(const float* pts, int d, int64_t r0, int64_t r1, co
     G[e] = 0.f;
   }
   float S = 0.f, W = 0.f, maxd = -INFINITY;
+  s_cs[threadIdx.x] = 0.f;  // per-lane sum of the ORACLE coefficients (shared: no register in the loop)
   for (int64_t base = lo; base < hi; base += ROUND) {
     float x[NI][VW];
 #pragma unroll
@@ -387,6 +446,7 @@ __device__ void batch_tile_t(const float* pts, int d, int64_t r0, int64_t r1, co
         if (owner) {
           S += sum;
           W += alpha * sum - dist * dif;
+          s_cs[threadIdx.x] += c[k];
           maxd = fmaxf(maxd, dist);
         }
       }
@@ -403,6 +463,7 @@ __device__ void batch_tile_t(const float* pts, int d, int64_t r0, int64_t r1, co
 #pragma unroll
     for (int e = 0; e < VW; ++e) G[e] += __shfl_xor_sync(0xffffffffu, G[e], o);
   S = warp_sum(S);
+  const float Cs = warp_sum(s_cs[threadIdx.x]);
   W = warp_sum(W);
   maxd = warp_max(maxd);
   if (grp == 0 && has_chunk)
@@ -412,6 +473,7 @@ __device__ void batch_tile_t(const float* pts, int d, int64_t r0, int64_t r1, co
     s_sc[warp][0] = S;
     s_sc[warp][1] = W;
     s_sc[warp][2] = maxd;
+    s_sc[warp][3] = Cs;
   }
 }
 
@@ -420,11 +482,13 @@ __device__ void batch_tile_t(const float* pts, int d, int64_t r0, int64_t r1, co
 // raise the batched iteration from 4.9 to 5.9 TB/s.
 __global__ void __launch_bounds__(kBatchBlock, 3) ses_batch_kernel(BatchParams p) {
   __shared__ float sG[kBatchWarps * kBatchMaxD];
-  __shared__ float s_sc[kBatchWarps][3];
+  __shared__ float s_sc[kBatchWarps][4];
+  __shared__ float s_cs[kBatchBlock];
   __shared__ float s_ub[kBatchMaxD];
   __shared__ float2 raw[kBatchStride];
   __shared__ double s_mean[kBatchMaxD];
   __shared__ double s_v1[kBatchMaxD];
+  __shared__ double s_dual[kBatchMaxD];
   __shared__ float2 s_scr[kBatchBlock];
   __shared__ __align__(16) double s_hdr[sizeof(StateHdr) / 8];
   __shared__ long long s_tile;
@@ -466,16 +530,16 @@ __global__ void __launch_bounds__(kBatchBlock, 3) ses_batch_kernel(BatchParams p
       if (tid < d) s_ub[tid] = mean32[tid];
       __syncthreads();
       switch (in.shape) {
-        case 0: batch_tile_t<4, 1, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
-        case 1: batch_tile_t<4, 2, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
-        case 2: batch_tile_t<4, 4, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
-        case 3: batch_tile_t<4, 8, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
-        case 4: batch_tile_t<4, 16, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
-        case 5: batch_tile<1, 2, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
-        case 6: batch_tile<1, 8, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
-        case 7: batch_tile<1, 32, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
-        case 9: batch_tile<1, 1, 4, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
-        default: batch_tile<1, 32, 2, 2>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc); break;
+        case 0: batch_tile_t<4, 1, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
+        case 1: batch_tile_t<4, 2, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
+        case 2: batch_tile_t<4, 4, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
+        case 3: batch_tile_t<4, 8, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
+        case 4: batch_tile_t<4, 16, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
+        case 5: batch_tile<1, 2, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
+        case 6: batch_tile<1, 8, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
+        case 7: batch_tile<1, 32, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
+        case 9: batch_tile<1, 1, 4, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
+        default: batch_tile<1, 32, 2, 2>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
       }
       __syncthreads();
       float* prow = partials + (size_t)tile * kBatchStride;
@@ -485,16 +549,17 @@ __global__ void __launch_bounds__(kBatchBlock, 3) ses_batch_kernel(BatchParams p
         prow[4 + j] = s;
       }
       if (tid == 0) {
-        float s0 = 0.f, s1 = 0.f, m = -INFINITY;
+        float s0 = 0.f, s1 = 0.f, s3 = 0.f, m = -INFINITY;
         for (int w = 0; w < kBatchWarps; ++w) {
           s0 += s_sc[w][0];
           s1 += s_sc[w][1];
+          s3 += s_sc[w][3];
           m = fmaxf(m, s_sc[w][2]);
         }
         prow[0] = s0;
         prow[1] = s1;
         prow[2] = m;
-        prow[3] = 0.f;
+        prow[3] = s3;
       }
     }
     // arrival of this tile at its instance
@@ -516,13 +581,14 @@ __global__ void __launch_bounds__(kBatchBlock, 3) ses_batch_kernel(BatchParams p
         if (tid < d) {
           s_mean[tid] = mean[tid];
           s_v1[tid] = (double)pts[tid];
+          s_dual[tid] = state_dual(state, d)[tid];
         }
         const int st = 4 + dpad4(d);
         // rows of this instance: stride kBatchStride, the first st columns used
         reduce_rows(partials + (size_t)in.tile0 * kBatchStride, 0, in.ntiles, st, raw, s_scr, opof, kBatchStride);
         if (tid < 32) {
           ses_finish_warp(raw, s_mean, s_v1, *reinterpret_cast<const StateHdr*>(s_hdr), state, d, alpha_d, 0.0,
-                          eor_d, eval ? 1 : 0, p.out ? p.out + tl.inst : nullptr);
+                          eor_d, eval ? 1 : 0, p.out ? p.out + tl.inst : nullptr, nullptr, s_dual);
 
         }
       }

@@ -126,6 +126,38 @@ def test_batch_search_brackets_the_optimum():
             assert one["lower_bound"] <= r["upper_bound"] * (1 + 1e-5)
 
 
+def test_batch_certified_search_brackets_the_optimum():
+    """CERTIFIED mode on the device: every instance ends with a ball within
+    1 + eps of its certified lower bound, both bracketing the exact optimum
+    where one is known and the oracle's certified search on small instances,
+    and the batched search agrees with ses_solve's certified mode."""
+    eps = 1e-3
+    arrays, opts = _instances()
+    pts, offs, n, d = api.pack_instances(arrays)
+    batch = api.SesBatch(pts, offs, n, d, tile_rows=1024)
+    reps, centres, _ = batch.solve(eps=eps, mode="certified", max_iters=200_000, poll_every=64,
+                                   launches_per_poll=16)
+    for k, a in enumerate(arrays):
+        V = a.astype(np.float64)
+        r = reps[k]
+        assert r["status"] == 0, (k, r)
+        f = oses.ses_objective(V, None, centres[k].astype(np.float64))
+        assert f <= r["upper_bound"] * (1 + 1e-5) + 1e-6, (k, f, r["upper_bound"])
+        assert r["upper_bound"] <= (1 + eps) * r["lower_bound"] * (1 + 1e-5) + 1e-7, (k, r)
+        if opts[k] is not None:
+            assert r["lower_bound"] <= opts[k] * (1 + 1e-5) + 1e-7, (k, r["lower_bound"], opts[k])
+            assert r["upper_bound"] >= opts[k] * (1 - 1e-5), (k, r["upper_bound"], opts[k])
+        if r["D"] > 0 and n[k] * d[k] <= 4000:
+            ref = oses.ses_solve(V, eps=eps, mode="certified", max_iters=200_000, poll_every=64)
+            assert r["lower_bound"] <= ref["radius"] * (1 + 1e-5) and ref["lower_bound"] <= r["upper_bound"] * (1 + 1e-5)
+        elif r["D"] > 0:
+            _, one = api.ses_solve(torch.from_numpy(a).cuda(), eps=eps, mode="certified", max_iters=200_000,
+                                   poll_every=64)
+            assert one["status"] == 0
+            assert r["lower_bound"] <= one["upper_bound"] * (1 + 1e-5)
+            assert one["lower_bound"] <= r["upper_bound"] * (1 + 1e-5)
+
+
 def test_batch_search_matches_single_instance_solves():
     eps = 1e-2
     arrays = [datagen.ses_gaussian(n, dd, seed=500 + n) for n, dd in [(4000, 8), (1500, 32), (999, 3)]]
