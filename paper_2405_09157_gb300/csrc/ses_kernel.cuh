@@ -508,6 +508,19 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
       }
   };
   load_round(lo);
+  // BF16 rows: a round holds twice the points of an FP32 round, and its loads
+  // wait for the previous round's arithmetic; lane 0 of each warp asks L2
+  // for the next round ahead of its loads (measured at n = 1e6, d = 32:
+  // 32.8 -> 30.7 us; no gain for FP32, so not done there)
+  auto prefetch_round = [&](int64_t b) {
+    if constexpr (sizeof(T) == 2) {
+      if (lane == 0 && b < hi) {
+        const int64_t m = hi - b < ROUND ? hi - b : ROUND;
+        const unsigned int bytes = (unsigned int)(m * d * (int64_t)sizeof(T));  // whole 16-byte chunks
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(pts + b * d), "r"(bytes) : "memory");
+      }
+    }
+  };
 
   StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
   if (hdr->stopped && !p.eval_only) return;
@@ -527,6 +540,7 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
   s_cs[threadIdx.x] = 0.f;
 
   for (int64_t base = lo; base < hi; base += ROUND) {
+    prefetch_round(base + ROUND);
     if (base != lo) load_round(base);
     float part[NI];
 #pragma unroll

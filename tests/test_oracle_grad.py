@@ -173,3 +173,40 @@ def test_svm_one_iteration_closed_form():
     want[iP] += w
     want[iQ] -= w
     assert np.allclose(grad, want, rtol=0, atol=1e-13)
+
+
+# --- the unrolled gradient against the envelope-theorem gradient -------------
+
+
+def _envelope_gradient(V, c, r):
+    """dr*/dv_i = mu_i (v_i - c*)/r* with mu the optimal dual weights on the
+    support (points at distance r* from c*; c* = sum mu_i v_i, sum mu_i = 1,
+    mu >= 0, solved by non-negative least squares)."""
+    from scipy.optimize import nnls
+    dist = np.linalg.norm(V - c, axis=1)
+    S = np.flatnonzero(np.abs(dist - r) <= 1e-9 * r)
+    A = np.vstack([(V[S] - c).T, np.ones(len(S))])
+    mu, res = nnls(A, np.concatenate([np.zeros(V.shape[1]), [1.0]]))
+    assert res <= 1e-9
+    G = np.zeros_like(V)
+    G[S] = mu[:, None] * (V[S] - c) / r
+    return G
+
+
+def test_unrolled_gradient_is_not_the_envelope_gradient():
+    # The unrolled gradient is the derivative of the T-step computation, not of the optimal radius r*:
+    # near the equilibrium g -> 0 and u = v_1 + alpha g/|g| turns with O(1/|g|) sensitivity, so the
+    # derivative of ubar^T grows quickly with T. Measured on a 40-point planar instance at alpha = 1.02 r*:
+    # relative distance to the envelope gradient ~1.9 for T <= 10, then > 10 by T = 20 and > 100 by T = 50.
+    from oracle import exact
+    V = datagen.ses_gaussian(40, 2, 1).astype(np.float64)
+    c, r = exact.mec_2d(V)
+    Ge = _envelope_gradient(V, c, r)
+    assert np.allclose(Ge.sum(axis=0), 0.0, atol=1e-12)  # translation invariance of r*
+    rho = oses.ses_width(oses.ses_D(V))
+    errs = {}
+    for T in (5, 20, 50):
+        _, G, steps = ses_grad.ses_unrolled_radius_grad(V, None, 1.02 * r, 0.5 / rho, T)
+        assert steps == T and np.allclose(G.sum(axis=0), 0.0, atol=1e-9 * np.abs(G).max())
+        errs[T] = np.linalg.norm(G - Ge) / np.linalg.norm(Ge)
+    assert 1.0 < errs[5] < 3.0 and errs[20] > 10.0 and errs[50] > 100.0, errs
