@@ -375,7 +375,16 @@ def _report(r):
 
 def ses_solve(pts, radii=None, eps=1e-3, mode="practical", max_iters=1_000_000, poll_every=256,
               max_steps=200, eta=None, delta=1e-4, patience=10, ws=None, stream=None, raise_on_budget=False):
-    """(1+eps)-approximate smallest enclosing sphere; returns (centre tensor, report dict)."""
+    """(1+eps)-approximate smallest enclosing sphere; returns (centre tensor, report dict).
+
+    mode: "practical" (the Sec. 5 rules; a stalled alpha-FTP is read as the
+    affirmative answer, so the search range can close while the certificates
+    stay wide), "theory" (T_i iterations of Theorem 2 per FTP) or "certified"
+    (only proven conclusions; ends when the ball's radius is within 1 + eps of
+    a certified lower bound; eta defaults to 1 and is halved when an FTP's own
+    certificate gap stops shrinking). The report holds the radius of an actual
+    enclosing ball ("value" = "upper_bound"), the best lower bound, the search
+    range, iterations and status (5 = budget spent, with valid bounds)."""
     n, d, dt = _points(pts)
     ws = workspace(SES, n, d, pts.device) if ws is None else ws
     center = torch.empty(d, dtype=torch.float32, device=pts.device)
@@ -390,7 +399,12 @@ def ses_solve(pts, radii=None, eps=1e-3, mode="practical", max_iters=1_000_000, 
 
 def svm_solve(X, labels, eps=1e-3, mode="practical", max_iters=1_000_000, poll_every=256, max_steps=200,
               eta=None, delta=1e-4, patience=10, ws=None, stream=None, raise_on_budget=False):
-    """(1-eps)-approximate hard-margin SVM; returns (best mean direction wbar, report dict)."""
+    """(1-eps)-approximate hard-margin SVM; returns (best mean direction wbar, report dict).
+
+    mode as in ses_solve, roles mirrored: "value" = "lower_bound" is the margin
+    of the returned direction, "upper_bound" the best Claim 8 value (per
+    iteration or averaged); "certified" ends when upper_bound <= (1 + eps)
+    lower_bound."""
     n, d, dt = _points(X)
     if labels.dtype != torch.int8 or not labels.is_cuda or labels.numel() != n:
         raise ValueError("labels must be an int8 CUDA tensor of n entries in {+1, -1}")
