@@ -139,7 +139,7 @@ pdscp_status solve_opts(const pdscp_options* o, BatchSolveOpts* b) {
   if (!o) return err(PDSCP_ERR_INVALID_ARG, "batch: options pointer is null");
   if (!(o->eps > 0.0) || !(o->delta >= 0.0) || o->patience < 1 || o->max_iters < 1 || o->max_steps < 1 ||
       (o->mode != PDSCP_MODE_PRACTICAL && o->mode != PDSCP_MODE_THEORY && o->mode != PDSCP_MODE_CERTIFIED) ||
-      !(o->eta >= 0.0) || o->eta > 1.0 || o->poll_every < 1)
+      !(o->eta >= 0.0) || o->eta > 1.0 || (o->mode == PDSCP_MODE_CERTIFIED && o->poll_every < 1))
     return err(PDSCP_ERR_INVALID_ARG, "batch: invalid search options");
   const bool cert = o->mode == PDSCP_MODE_CERTIFIED;
   b->eps = o->eps;
@@ -150,7 +150,7 @@ pdscp_status solve_opts(const pdscp_options* o, BatchSolveOpts* b) {
   b->rules = o->mode == PDSCP_MODE_THEORY ? PDSCP_RULES_NONE : PDSCP_RULES_PRACTICAL;
   b->max_steps = o->max_steps;
   b->mode = o->mode;
-  b->poll = o->poll_every;
+  b->poll = cert ? o->poll_every : 1;
   b->pad = 0;
   return PDSCP_OK;
 }

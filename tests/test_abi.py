@@ -72,6 +72,17 @@ def test_argument_validation_without_gpu(lib):
     opts = _ffi.Options(1e-3, 1e-4, 10, 0, 1000, 0, 10, 0.0)
     st = lib.svm_solve(fake, _ffi.F32, fake, 10, 4, ctypes.byref(opts), fake, 1 << 30, None, fake, ctypes.byref(rep))
     assert st == 1 and b"poll_every" in lib.pdscp_last_error()
+    # the certified mode is a known mode (the call then fails on the too-small workspace, before any launch);
+    # an unknown one and an eta outside (0, 1] are rejected
+    opts = _ffi.Options(1e-3, 0.0, 10, _ffi.MODE_CERTIFIED, 1000, 64, 10, 0.0)
+    st = lib.ses_solve(fake, _ffi.F32, None, 10, 4, ctypes.byref(opts), fake, 16, None, fake, ctypes.byref(rep))
+    assert st == 8
+    opts = _ffi.Options(1e-3, 0.0, 10, 3, 1000, 64, 10, 0.0)
+    st = lib.ses_solve(fake, _ffi.F32, None, 10, 4, ctypes.byref(opts), fake, 1 << 30, None, fake, ctypes.byref(rep))
+    assert st == 1 and b"mode" in lib.pdscp_last_error()
+    opts = _ffi.Options(1e-3, 0.0, 10, _ffi.MODE_CERTIFIED, 1000, 64, 10, 1.5)
+    st = lib.svm_solve(fake, _ffi.F32, fake, 10, 4, ctypes.byref(opts), fake, 1 << 30, None, fake, ctypes.byref(rep))
+    assert st == 1 and b"eta" in lib.pdscp_last_error()
     bwd = lambda problem, dtype, T, ws_bytes: lib.mwu_backward(problem, fake, dtype, None, None, 10, 4, 1.0, 0.1,
                                                                0.0, T, None, fake, ws_bytes, None, fake, None)
     assert bwd(_ffi.SVM, _ffi.F32, 5, 1 << 30) == 1 and b"labels" in lib.pdscp_last_error()
@@ -136,6 +147,8 @@ def test_batch_search_validation_without_gpu(lib):
     st = lib.ses_batch_solve_init(2, fake, 1200, offs, n, d, 512, ctypes.byref(bad), fake, 1 << 30, None)
     assert st == 1 and b"options" in lib.pdscp_last_error()
     bad = _ffi.Options(1e-3, 1e-4, 10, 7, 1000, 1, 10, 0.0)  # unknown mode
+    assert lib.ses_batch_solve_init(2, fake, 1200, offs, n, d, 512, ctypes.byref(bad), fake, 1 << 30, None) == 1
+    bad = _ffi.Options(1e-3, 0.0, 10, _ffi.MODE_CERTIFIED, 1000, 0, 10, 0.0)  # certified needs a poll interval
     assert lib.ses_batch_solve_init(2, fake, 1200, offs, n, d, 512, ctypes.byref(bad), fake, 1 << 30, None) == 1
     launches, done = ctypes.c_int64(), ctypes.c_int32()
     assert lib.ses_batch_solve_run(2, fake, fake, 1 << 30, 0, 10, None, ctypes.byref(launches),
