@@ -100,3 +100,24 @@ def test_ses_certified_full_size():
     c = center.cpu().numpy().astype(np.float64)
     r = float(np.sqrt(np.max(np.sum((V32.astype(np.float64) - c) ** 2, axis=1))))
     assert abs(r - rep["value"]) <= FP * r
+
+
+@pytest.mark.parametrize("name", ["two points", "d = 1", "duplicates", "collinear"])
+def test_ses_certified_degenerate_inputs(name):
+    rng = np.random.default_rng(5)
+    V = {"two points": np.array([[0.0, 0.0], [3.0, 4.0]]),
+         "d = 1": rng.standard_normal((50, 1)),
+         "duplicates": np.repeat(rng.standard_normal((5, 2)), 10, axis=0),
+         "collinear": np.outer(np.linspace(-1, 2, 40), [1.0, 2.0, -1.0])}[name].astype(np.float32)
+    V64 = V.astype(np.float64)
+    if V.shape[1] == 2:
+        opt = exact.mec_2d(V64)[1]
+    elif V.shape[1] == 1:
+        opt = 0.5 * float(V64.max() - V64.min())
+    else:
+        opt = 0.5 * float(np.max(np.linalg.norm(V64[:, None, :] - V64[None, :, :], axis=2)))  # collinear: half the diameter
+    center, rep = api.ses_solve(_cuda(V), eps=1e-3, mode="certified", max_iters=100_000, poll_every=64)
+    assert rep["status"] == 0
+    assert rep["lower_bound"] <= opt * (1 + FP) <= rep["value"] * (1 + FP) + 1e-6
+    assert rep["value"] <= (1 + 1e-3) * rep["lower_bound"] * (1 + FP)
+    assert oses.ses_objective(V64, None, center.cpu().numpy().astype(np.float64)) <= rep["value"] * (1 + FP)
