@@ -17,8 +17,8 @@
 
 namespace pdscp {
 
-cudaError_t launch_ses(const SesParams& p, int dtype, bool vec, cudaStream_t stream);
-cudaError_t launch_svm(const SvmParams& p, int dtype, bool vec, cudaStream_t stream);
+cudaError_t launch_ses(const SesParams& p, int dtype, bool vec, cudaStream_t stream, bool pdl = false);
+cudaError_t launch_svm(const SvmParams& p, int dtype, bool vec, cudaStream_t stream, bool pdl = false);
 cudaError_t launch_ses_merge(const SesMergeParams& m, int dtype, cudaStream_t stream);
 cudaError_t launch_svm_merge(const SvmMergeParams& m, cudaStream_t stream);
 cudaError_t launch_ses_bwd_seed(const BwdParams& p, bool vec, cudaStream_t stream);
@@ -137,7 +137,8 @@ cudaError_t launch_state_init(int problem, const void* pts, int dtype, int d, in
 
 pdscp_status do_step(int problem, const void* pts, int dtype, const float* radii, const int8_t* labels,
                      int64_t n, int d, double alpha, double eta_over_rho, double D, int eval_only,
-                     void* state, void* ws, cudaStream_t stream, pdscp_step_out* out, float* tape = nullptr) {
+                     void* state, void* ws, cudaStream_t stream, pdscp_step_out* out, float* tape = nullptr,
+                     bool pdl = false) {
   const Layout L = layout(problem, d);
   const bool vec = use_vec(pts, dtype, d);
   unsigned int* counter = reinterpret_cast<unsigned int*>(ws);
@@ -147,11 +148,11 @@ pdscp_status do_step(int problem, const void* pts, int dtype, const float* radii
   if (problem == PDSCP_SES) {
     SesParams p{pts, radii, n, d, eval_only, alpha, eta_over_rho, state, partials, grows, counter, 0, out, 1, nullptr,
                 tape, reinterpret_cast<unsigned char*>(ws) + L.sink};
-    e = launch_ses(p, dtype, vec, stream);
+    e = launch_ses(p, dtype, vec, stream, pdl);
   } else {
     SvmParams p{pts, labels, n, d, eval_only, alpha, eta_over_rho, D, state, partials, grows, counter, 0, out, nullptr,
                 reinterpret_cast<unsigned char*>(ws) + L.sink, tape};
-    e = launch_svm(p, dtype, vec, stream);
+    e = launch_svm(p, dtype, vec, stream, pdl);
   }
   if (e != cudaSuccess) return cuda_fail(e, "mwu_step launch");
   return PDSCP_OK;
@@ -500,7 +501,7 @@ pdscp_status mwu_backward(int32_t problem, const void* pts, int32_t dtype, const
   const float* rad = problem == PDSCP_SES ? radii : nullptr;
   const int8_t* lab = problem == PDSCP_SVM ? labels : nullptr;
   for (int64_t t = 0; t < T; ++t) {
-    st = do_step(problem, pts, dtype, rad, lab, n, d, alpha, eta_over_rho, D, 0, state, ws, s, nullptr, tape);
+    st = do_step(problem, pts, dtype, rad, lab, n, d, alpha, eta_over_rho, D, 0, state, ws, s, nullptr, tape, true);
     if (st != PDSCP_OK) return st;
   }
   const Layout L = layout(problem, d);
@@ -628,7 +629,9 @@ pdscp_status run_ftp(int problem, const void* pts, int dtype, const float* radii
   while (ran < budget) {
     const int64_t chunk = std::min<int64_t>(o->poll_every, budget - ran);
     for (int64_t j = 0; j < chunk; ++j) {
-      st = do_step(problem, pts, dtype, radii, labels, n, d, alpha, eta_over_rho, D, 0, state, ws, s, ring + j);
+      // consecutive iterations of the solve overlap by programmatic dependent launch
+      st = do_step(problem, pts, dtype, radii, labels, n, d, alpha, eta_over_rho, D, 0, state, ws, s, ring + j, nullptr,
+                   true);
       if (st != PDSCP_OK) return st;
     }
     ran += chunk;

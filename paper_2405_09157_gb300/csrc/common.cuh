@@ -66,6 +66,13 @@ __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
                : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// Programmatic dependent launch: a pass kernel lets the next launch in the
+// stream start early (pdl_trigger) and, in that next launch, waits for the
+// previous grid's completion and memory (pdl_wait) before it reads anything
+// the previous grid writes. Both are no-ops for a launch without the
+// attribute. The wait is a hardware dependency, not a spin loop.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 #endif
 
 __host__ __device__ inline size_t state_bytes(int d) {

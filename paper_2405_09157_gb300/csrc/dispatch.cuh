@@ -6,6 +6,28 @@
 
 namespace pdscp {
 
+// Launch of a pass kernel; pdl: with programmatic stream serialization, so
+// that it may start while the previous launch in the stream finishes (the
+// kernel waits for that launch in pdl_wait before it reads its results).
+template <typename Kern, typename P>
+cudaError_t launch_pass(Kern kern, int grid, int block, size_t smem, cudaStream_t stream, bool pdl, const P& q) {
+  if (!pdl) {
+    kern<<<grid, block, smem, stream>>>(q);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned int)grid);
+  cfg.blockDim = dim3((unsigned int)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, q);
+}
+
 // Launch configuration of one kernel instance on the current device.
 struct LaunchCfg {
   int grid;

@@ -9,6 +9,7 @@ template <typename T>
 struct SesLauncher {
   const SesParams& p;
   cudaStream_t stream;
+  bool pdl;
   // Dynamic shared memory: the per-warp partial sums of the pass, or in the
   // finishing CTA the column totals, the mean and v_1 and (single-level
   // completion) every partial row, whichever is larger.
@@ -37,8 +38,7 @@ struct SesLauncher {
       cudaError_t e = allow_smem(kern, smem);
       if (e != cudaSuccess) return e;
     }
-    kern<<<grid, block, smem, stream>>>(q);
-    return cudaGetLastError();
+    return launch_pass(kern, grid, block, smem, stream, pdl, q);
   }
   template <int VW, int LPP, int NCH>
   cudaError_t go() {
@@ -55,9 +55,9 @@ struct SesLauncher {
 };
 }  // namespace
 
-cudaError_t launch_ses(const SesParams& p, int dtype, bool vec, cudaStream_t stream) {
-  if (dtype == PDSCP_F32) return dispatch_shape<4>(p.d, vec, SesLauncher<float>{p, stream});
-  return dispatch_shape<8>(p.d, vec, SesLauncher<__nv_bfloat16>{p, stream});
+cudaError_t launch_ses(const SesParams& p, int dtype, bool vec, cudaStream_t stream, bool pdl) {
+  if (dtype == PDSCP_F32) return dispatch_shape<4>(p.d, vec, SesLauncher<float>{p, stream, pdl});
+  return dispatch_shape<8>(p.d, vec, SesLauncher<__nv_bfloat16>{p, stream, pdl});
 }
 
 cudaError_t launch_ses_merge(const SesMergeParams& m, int dtype, cudaStream_t stream) {

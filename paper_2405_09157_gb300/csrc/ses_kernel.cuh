@@ -74,6 +74,8 @@ __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float s_sc[kWarps][4];
 
+  pdl_trigger();
+  pdl_wait();  // the state below is the previous launch's output
   StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
   if (hdr->stopped && !p.eval_only) return;
 
@@ -484,6 +486,7 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
   const bool owner = (gl % GS::SHARE) == 0;
   const bool has_chunk = gl < nch;
   const T* pts = reinterpret_cast<const T*>(p.pts);
+  pdl_trigger();
   const WarpSplit wsp(p.sink, NW, warp);
   if (wsp.warm) ses_finish_warm<T>(p, smem_raw);
   const int64_t nwarps = wsp.nwarps;
@@ -522,6 +525,9 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
     }
   };
 
+  // the first round's loads are in flight; everything below depends on the
+  // previous launch (state, partial rows, counters)
+  pdl_wait();
   StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
   if (hdr->stopped && !p.eval_only) return;
 

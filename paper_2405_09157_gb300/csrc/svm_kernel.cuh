@@ -58,6 +58,8 @@ __global__ void __launch_bounds__(kBlock) svm_iter_kernel(SvmParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float s_sc[kWarps][4];
 
+  pdl_trigger();
+  pdl_wait();  // the state below is the previous launch's output
   StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
   if (hdr->stopped && !p.eval_only) return;
 
@@ -454,6 +456,7 @@ __global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
   const bool owner = (gl % GS::SHARE) == 0;
   const bool has_chunk = gl < nch;
   const T* pts = reinterpret_cast<const T*>(p.pts);
+  pdl_trigger();
   const WarpSplit wsp(p.sink, NW, warp);
   if (wsp.warm) svm_finish_warm(p, smem_raw);
   const int64_t nwarps = wsp.nwarps;
@@ -491,6 +494,9 @@ __global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
     }
   };
 
+  // the first round's loads are in flight; everything below depends on the
+  // previous launch (state, partial rows, counters)
+  pdl_wait();
   StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
   if (hdr->stopped && !p.eval_only) return;
 
