@@ -22,9 +22,9 @@ cudaError_t launch_svm(const SvmParams& p, int dtype, bool vec, cudaStream_t str
 cudaError_t launch_ses_merge(const SesMergeParams& m, int dtype, cudaStream_t stream);
 cudaError_t launch_svm_merge(const SvmMergeParams& m, cudaStream_t stream);
 cudaError_t launch_ses_bwd_seed(const BwdParams& p, bool vec, cudaStream_t stream);
-cudaError_t launch_ses_bwd_step(const BwdParams& p, bool vec, cudaStream_t stream);
+cudaError_t launch_ses_bwd_step(const BwdParams& p, bool vec, cudaStream_t stream, bool pdl);
 cudaError_t launch_svm_bwd_seed(const BwdParams& p, bool vec, cudaStream_t stream);
-cudaError_t launch_svm_bwd_step(const BwdParams& p, bool vec, cudaStream_t stream);
+cudaError_t launch_svm_bwd_step(const BwdParams& p, bool vec, cudaStream_t stream, bool pdl);
 
 namespace {
 
@@ -531,7 +531,7 @@ pdscp_status mwu_backward(int32_t problem, const void* pts, int32_t dtype, const
     if (e != cudaSuccess) return cuda_fail(e, "reverse-sweep seed launch");
     for (int64_t k = T - 1; k >= 1; --k) {  // step 0 only hands dL/dubar^1 to v_1 (done by step 1's bookkeeping)
       bp.s = k;
-      e = launch_ses_bwd_step(bp, vec, s);
+      e = launch_ses_bwd_step(bp, vec, s, true);  // consecutive reverse steps overlap (dependent launch)
       if (e != cudaSuccess) return cuda_fail(e, "reverse-step launch");
     }
   } else {
@@ -539,7 +539,7 @@ pdscp_status mwu_backward(int32_t problem, const void* pts, int32_t dtype, const
     if (e != cudaSuccess) return cuda_fail(e, "reverse-sweep seed launch");
     for (int64_t k = T - 1; k >= 0; --k) {
       bp.s = k;
-      e = launch_svm_bwd_step(bp, vec, s);
+      e = launch_svm_bwd_step(bp, vec, s, true);
       if (e != cudaSuccess) return cuda_fail(e, "reverse-step launch");
     }
   }

@@ -118,6 +118,8 @@ static __device__ void bwd_prologue(int64_t s, const float* tape, int d, float r
 // B <- s/(s+1) B - sum_i dL/ddelta_i and the bookkeeping of step s - 1.
 template <int VW, int LPP, int NCH, int U>
 __global__ void __launch_bounds__(kBlock) ses_bwd_step_kernel(BwdParams p) {
+  pdl_trigger();
+  pdl_wait();  // Gbar, Sbar and the gradient rows are the previous reverse step's output
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float2 s_scr[kMaxBlock];
   __shared__ bool s_flag;
@@ -271,6 +273,8 @@ __global__ void __launch_bounds__(kBlock) ses_bwd_step_t_kernel(BwdParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float2 s_scr[kMaxBlock];
   __shared__ bool s_flag;
+  pdl_trigger();
+  // the forward's state and tape were complete before the sweep began
   const StateHdr* hdr = reinterpret_cast<const StateHdr*>(p.state);
   if (p.s >= hdr->t) return;  // the forward stopped before step s
 
@@ -286,6 +290,24 @@ __global__ void __launch_bounds__(kBlock) ses_bwd_step_t_kernel(BwdParams p) {
   const float* ent = p.tape + (size_t)p.s * ses_tape_stride(d);
   const float kr = ent[2], H = ent[3];
   const float* ubar = ent + 4;
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
+  float x[NI][VW], gr[NI][VW];
+  auto load_points = [&](int64_t base) {
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const int64_t i = base + r * PPW + grp;
+      if (i < p.n && has_chunk) {
+        Chunk<float, VW>::load(p.pts + i * d, gl, x[r]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) x[r][e] = 0.f;
+      }
+    }
+  };
+  // the first round's points do not depend on the previous reverse step
+  load_points(gw * ROUND);
+  pdl_wait();  // Gbar, Sbar and the gradient rows are the previous step's output
   const float* Gbar = bwd_Gbar(p.bw, d);
   const float Sbar = *bwd_Sbar(p.bw, d);
   float ub[VW], gb[VW], acc[VW];
@@ -295,23 +317,17 @@ __global__ void __launch_bounds__(kBlock) ses_bwd_step_t_kernel(BwdParams p) {
     gb[e] = has_chunk ? Gbar[gl * VW + e] : 0.f;
     acc[e] = 0.f;
   }
-  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
-  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
   for (int64_t base = gw * ROUND; base < p.n; base += nwarps * ROUND) {
-    float x[NI][VW], gr[NI][VW];
+    if (base != gw * ROUND) load_points(base);
 #pragma unroll
     for (int r = 0; r < NI; ++r) {
       const int64_t i = base + r * PPW + grp;
       if (i < p.n && has_chunk) {
-        Chunk<float, VW>::load(p.pts + i * d, gl, x[r]);
         const float4 g4 = *reinterpret_cast<const float4*>(p.grad + i * d + gl * VW);
         gr[r][0] = g4.x; gr[r][1] = g4.y; gr[r][2] = g4.z; gr[r][3] = g4.w;
       } else {
 #pragma unroll
-        for (int e = 0; e < VW; ++e) {
-          x[r][e] = 0.f;
-          gr[r][e] = 0.f;
-        }
+        for (int e = 0; e < VW; ++e) gr[r][e] = 0.f;
       }
     }
     float p2[NI], pd[NI];
@@ -600,6 +616,8 @@ static __device__ void svm_bwd_prologue(int64_t s, const float* tape, int d, uns
 
 template <int VW, int LPP, int NCH, int U>
 __global__ void __launch_bounds__(kBlock) svm_bwd_step_kernel(BwdParams p) {
+  pdl_trigger();
+  pdl_wait();  // the adjoint scratch and the gradient rows are the previous reverse step's output
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float2 s_scr[kMaxBlock];
   __shared__ bool s_flag;
@@ -739,6 +757,8 @@ __global__ void __launch_bounds__(kBlock) svm_bwd_step_kernel(BwdParams p) {
 // the two partial dot products.
 template <int VW, int LPP, int NI>
 __global__ void __launch_bounds__(kBlock) svm_bwd_step_t_kernel(BwdParams p) {
+  pdl_trigger();
+  pdl_wait();  // the adjoint scratch and the gradient rows are the previous reverse step's output
   using GS = GroupScatter<LPP, NI>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float2 s_scr[kMaxBlock];

@@ -8,6 +8,7 @@ namespace {
 struct BwdStepLauncher {
   const BwdParams& p;
   cudaStream_t stream;
+  bool pdl;
   template <int VW, int LPP, int NCH>
   cudaError_t go() {
     if constexpr (VW > 1 && NCH == 1) {  // 16-byte chunk rows: the reduce-scatter form
@@ -36,8 +37,7 @@ struct BwdStepLauncher {
       cudaError_t e = allow_smem(kern, smem);
       if (e != cudaSuccess) return e;
     }
-    kern<<<grid, kBlock, smem, stream>>>(q);
-    return cudaGetLastError();
+    return launch_pass(kern, grid, kBlock, smem, stream, pdl, q);
   }
 };
 
@@ -59,6 +59,7 @@ struct BwdArgmaxLauncher {
 struct SvmBwdStepLauncher {
   const BwdParams& p;
   cudaStream_t stream;
+  bool pdl;
   template <int VW, int LPP, int NCH>
   cudaError_t go() {
     if constexpr (VW > 1 && NCH == 1) {  // 16-byte chunk rows: the reduce-scatter form
@@ -85,8 +86,7 @@ struct SvmBwdStepLauncher {
     }
     cudaError_t e = allow_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kBlock, smem, stream>>>(q);
-    return cudaGetLastError();
+    return launch_pass(kern, grid, kBlock, smem, stream, pdl, q);
   }
 };
 
@@ -119,8 +119,8 @@ cudaError_t launch_svm_bwd_seed(const BwdParams& p, bool vec, cudaStream_t strea
 }
 
 // SVM reverse step p.s (>= 0).
-cudaError_t launch_svm_bwd_step(const BwdParams& p, bool vec, cudaStream_t stream) {
-  return dispatch_shape<4>(p.d, vec, SvmBwdStepLauncher{p, stream});
+cudaError_t launch_svm_bwd_step(const BwdParams& p, bool vec, cudaStream_t stream, bool pdl) {
+  return dispatch_shape<4>(p.d, vec, SvmBwdStepLauncher{p, stream, pdl});
 }
 
 // The argmax pass and the seed (B = dL/dubar^T, step T-1's bookkeeping).
@@ -135,8 +135,8 @@ cudaError_t launch_ses_bwd_seed(const BwdParams& p, bool vec, cudaStream_t strea
 }
 
 // Reverse step p.s (>= 1).
-cudaError_t launch_ses_bwd_step(const BwdParams& p, bool vec, cudaStream_t stream) {
-  return dispatch_shape<4>(p.d, vec, BwdStepLauncher{p, stream});
+cudaError_t launch_ses_bwd_step(const BwdParams& p, bool vec, cudaStream_t stream, bool pdl) {
+  return dispatch_shape<4>(p.d, vec, BwdStepLauncher{p, stream, pdl});
 }
 
 }  // namespace pdscp
