@@ -446,6 +446,19 @@ def variants(dev, flush):
     b = 4 * N_POINTS * DIM * 4
     out["ses_n4e6_d32_f32"] = {"ms_per_iter": ms, "iters_per_s": 1e3 / ms, "GBps": b / ms / 1e6,
                               "frac_hbm": b / ms / 1e6 / peak, "note": "512 MB of points, 4x L2: streamed from HBM"}
+    # the same iterations back to back (mwu_run: dependent-launch overlap); the input exceeds L2, so no flush
+    K = 50
+    m.run(D, 0.01 / (3 * D / math.sqrt(2)), 3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    m.run(D, 0.01 / (3 * D / math.sqrt(2)), K)
+    e1.record()
+    torch.cuda.synchronize()
+    msr = e0.elapsed_time(e1) / K
+    out["ses_n4e6_d32_f32"]["run_back_to_back"] = {"ms_per_iter": msr, "iters_per_s": 1e3 / msr,
+                                                   "GBps": b / msr / 1e6, "frac_hbm": b / msr / 1e6 / peak,
+                                                   "iterations": K}
     del V4, m
     X32, y = datagen.svm_clusters(500_000, 500_000, 128, seed=0)
     X = torch.from_numpy(X32).to(dev)

@@ -248,6 +248,22 @@ pdscp_status mwu_step_noalloc(int32_t problem, const void* pts_dev, int32_t dtyp
                               pdscp_stream stream, pdscp_step_out* out_dev);
 
 /*
+ * k iterations of mwu_step (same arguments and meaning, eval_only = 0) enqueued
+ * back to back on `stream`, consecutive launches overlapping by programmatic
+ * dependent launch: each launch's CTAs issue their first point loads while
+ * the previous launch finishes and wait for it (a hardware dependency)
+ * before reading the state. The results are those of k mwu_step calls, bit
+ * for bit. out_dev (may be NULL) receives k pdscp_step_out, one per
+ * iteration (an iteration after the alpha-FTP stopped writes nothing). k = 0
+ * does nothing. Asynchronous; no host sync.
+ */
+pdscp_status mwu_run(int32_t problem, const void* pts_dev, int32_t dtype,
+                     const float* radii_dev, const int8_t* labels_dev,
+                     int64_t n, int32_t d, double alpha, double eta_over_rho,
+                     double D, int64_t k, void* state_dev, void* ws_dev,
+                     size_t ws_bytes, pdscp_stream stream, pdscp_step_out* out_dev);
+
+/*
  * Read the running mean (SES: ubar, d floats; SVM: wbar then s1bar, s2bar:
  * d+2 floats) and the best point seen (SES: centre with the smallest f; SVM:
  * direction with the largest margin; d floats) of a state into device

@@ -57,6 +57,8 @@ SIGNATURES = {
     "mwu_state_init": (c_i32, [c_i32, c_vp, c_i32, c_i64, c_i32, c_i32, c_dbl, c_i32, c_vp, c_vp, c_sz, c_vp]),
     "mwu_step": (c_i32, [c_i32, c_vp, c_i32, c_vp, c_vp, c_i64, c_i32, c_dbl, c_dbl, c_dbl, c_i32,
                          c_vp, c_vp, c_sz, c_vp, c_vp]),
+    "mwu_run": (c_i32, [c_i32, c_vp, c_i32, c_vp, c_vp, c_i64, c_i32, c_dbl, c_dbl, c_dbl, c_i64, c_vp, c_vp, c_sz,
+                        c_vp, c_vp]),
     "mwu_step_noalloc": (c_i32, [c_i32, c_vp, c_i32, c_vp, c_vp, c_i64, c_i32, c_dbl, c_dbl, c_dbl, c_i32,
                                  c_vp, c_vp, c_vp]),
     "mwu_state_read": (c_i32, [c_i32, c_i32, c_vp, c_vp, c_vp, c_vp]),

@@ -101,6 +101,15 @@ def mwu_step(problem, pts, alpha, eta_over_rho, state, ws, out=None, D=0.0, radi
                           ws.numel(), _stream(stream), _vp(out)), "mwu_step")
 
 
+def mwu_run(problem, pts, alpha, eta_over_rho, k, state, ws, out=None, D=0.0, radii=None, labels=None, stream=None):
+    """k alpha-FTP iterations enqueued back to back, consecutive launches
+    overlapping (no host sync); out: k records or None. Bit-identical to k
+    mwu_step calls."""
+    n, d, dt = _points(pts)
+    check(load().mwu_run(problem, _vp(pts), dt, _vp(radii), _vp(labels), n, d, float(alpha), float(eta_over_rho),
+                         float(D), int(k), _vp(state), _vp(ws), ws.numel(), _stream(stream), _vp(out)), "mwu_run")
+
+
 def mwu_step_noalloc(problem, pts, alpha, eta_over_rho, state, out=None, D=0.0, radii=None, labels=None,
                      eval_only=False, stream=None):
     """mwu_step for callers that cannot allocate device memory: the scratch is
@@ -356,6 +365,10 @@ class MWU:
     def step(self, alpha, eta_over_rho, out=None, D=0.0, eval_only=False, stream=None):
         mwu_step(self.problem, self.pts, alpha, eta_over_rho, self.state, self.ws, out, D, self.radii,
                  self.labels, eval_only, stream)
+
+    def run(self, alpha, eta_over_rho, k, out=None, D=0.0, stream=None):
+        mwu_run(self.problem, self.pts, alpha, eta_over_rho, k, self.state, self.ws, out, D, self.radii, self.labels,
+                stream)
 
     def set(self, t, mean, D=0.0, stream=None):
         state_set(self.problem, self.pts, t, mean, self.state, self.ws, self.radii, self.labels, D, stream)

@@ -256,6 +256,30 @@ pdscp_status mwu_step(int32_t problem, const void* pts, int32_t dtype, const flo
                  eval_only, state, ws, (cudaStream_t)stream, out);
 }
 
+pdscp_status mwu_run(int32_t problem, const void* pts, int32_t dtype, const float* radii, const int8_t* labels,
+                     int64_t n, int32_t d, double alpha, double eta_over_rho, double D, int64_t k, void* state, void* ws,
+                     size_t ws_bytes, pdscp_stream stream, pdscp_step_out* out) {
+  if (k < 0) return fail(PDSCP_ERR_INVALID_ARG, "mwu_run: k = %lld < 0", (long long)k);
+  pdscp_status st = check_common(problem, pts, dtype, n, d);
+  if (st != PDSCP_OK) return st;
+  if (!state || !ws) return fail(PDSCP_ERR_INVALID_ARG, "state or workspace pointer is null");
+  if (!aligned(state, 16) || !aligned(ws, 16)) return fail(PDSCP_ERR_INVALID_ARG, "state/workspace not 16-byte aligned");
+  if (out && !aligned(out, 8)) return fail(PDSCP_ERR_INVALID_ARG, "out pointer not 8-byte aligned");
+  if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(PDSCP_ERR_INVALID_ARG, "alpha must be finite and > 0");
+  if (!(eta_over_rho >= 0.0) || !std::isfinite(eta_over_rho)) return fail(PDSCP_ERR_INVALID_ARG, "eta/rho must be finite and >= 0");
+  if (problem == PDSCP_SVM) {
+    if (!labels) return fail(PDSCP_ERR_INVALID_ARG, "SVM needs labels");
+    if (!(D > 0.0) || !std::isfinite(D)) return fail(PDSCP_ERR_INVALID_ARG, "SVM needs D > 0 (the largest point norm)");
+  }
+  if (ws_bytes < layout(problem, d).state) return fail(PDSCP_ERR_WORKSPACE, "workspace too small");
+  for (int64_t j = 0; j < k; ++j) {
+    st = do_step(problem, pts, dtype, problem == PDSCP_SES ? radii : nullptr, labels, n, d, alpha, eta_over_rho, D, 0,
+                 state, ws, (cudaStream_t)stream, out ? out + j : nullptr, nullptr, true);
+    if (st != PDSCP_OK) return st;
+  }
+  return PDSCP_OK;
+}
+
 pdscp_status mwu_state_read(int32_t problem, int32_t d, const void* state, float* mean_dev, float* best_dev,
                             pdscp_stream stream) {
   if (problem != PDSCP_SES && problem != PDSCP_SVM) return fail(PDSCP_ERR_INVALID_ARG, "unknown problem %d", problem);

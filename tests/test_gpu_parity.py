@@ -390,3 +390,37 @@ def test_svm_solve_against_bruteforce():
     wn = w.cpu().numpy().astype(np.float64)
     assert math.isclose(exact.svm_margin_of(X[y > 0], X[y < 0], wn), rep["value"], rel_tol=1e-4)
     assert rep["value"] >= 0.97 * opt
+
+
+@pytest.mark.parametrize("problem,n,d,dtype", [("ses", 5000, 32, torch.float32), ("ses", 3001, 5, torch.float32),
+                                               ("ses", 4099, 32, torch.bfloat16), ("svm", 3000, 64, torch.float32)])
+def test_mwu_run_equals_single_steps_bit_for_bit(problem, n, d, dtype):
+    # k iterations launched back to back with dependent-launch overlap give the records and means of k
+    # separate mwu_step calls exactly: the overlap changes when a launch starts, not what it computes
+    k = 12
+    if problem == "ses":
+        V32 = datagen.ses_gaussian(n, d, seed=n)
+        pts = _cuda(V32).to(dtype)
+        D = oses.ses_D(V32.astype(np.float64))
+        args = dict(alpha=0.8 * D, eta_over_rho=0.5 / oses.ses_width(D))
+        make = lambda: api.MWU(_ffi.SES, pts)
+        extra = {}
+    else:
+        X32, y = datagen.svm_clusters(n // 2, n - n // 2, d, seed=3)
+        pts = _cuda(X32).to(dtype)
+        D = osvm.svm_D(X32.astype(np.float64))
+        args = dict(alpha=0.3 * D, eta_over_rho=0.5 / osvm.svm_width(D))
+        lab = _cuda(y)
+        make = lambda: api.MWU(_ffi.SVM, pts, labels=lab)
+        extra = {"D": D}
+    a, b = make(), make()
+    out_a, out_b = api.new_steps(k), api.new_steps(k)
+    for t in range(k):
+        a.step(args["alpha"], args["eta_over_rho"], out=out_a[t], **extra)
+    b.run(args["alpha"], args["eta_over_rho"], k, out=out_b, **extra)
+    torch.cuda.synchronize()
+    assert torch.equal(out_a, out_b)
+    ma, ba = a.read()
+    mb, bb = b.read()
+    assert torch.equal(ma, mb) and torch.equal(ba, bb)
+    assert api.decode_steps(out_b)[-1]["t"] == k
