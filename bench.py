@@ -20,6 +20,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -153,7 +154,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_POINTS, "d": DIM, "parallelism": "replicas"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{rows} of {N_POINTS} rows per step, scaled by rows/n"},
+                         "sample": f"{rows} of {N_POINTS} rows per step, scaled by rows/n", "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -390,11 +391,27 @@ def e2e_host(args, V32, alpha, eor, dev):
             "d2h_bytes_per_step": api.STEP_BYTES, "ms_per_step": ms, "steps": K}
 
 
+def host_cpu():
+    """The host's processor model and logical CPU count (for the CPU baseline's context)."""
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu": model, "arch": platform.machine()}
+
+
 def cpu_baseline(V32, alpha, eta, rho):
     V64 = V32.astype(np.float64)
     rate, steps, el = oracle_rate(V64, alpha, eta, rho, budget_s=15.0)
     return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} oracle iterations over all {V32.shape[0]} points ({el:.1f} s), FP64 numpy, 1 thread"}
+            "sample": f"{steps} oracle iterations over all {V32.shape[0]} points ({el:.1f} s), FP64 numpy, 1 thread",
+            "host": host_cpu()}
 
 
 def _time_steps(m, alpha, eor, D, flush, K=50):
