@@ -496,19 +496,32 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
   // (balanced bytes per warp; starts on 8-point boundaries)
   auto split = [&](int64_t w) { return w >= nwarps ? p.n : ((w * p.n / nwarps) & ~(int64_t)7); };
   const int64_t lo = wsp.warm ? p.n : split(gw), hi = wsp.warm ? p.n : split(gw + 1);
-  // the first round's point loads do not depend on the state: issue them first
-  float x[NI][VW];
+  // the first round's point loads do not depend on the state: issue them first.
+  // BF16 rows stay packed (16 bytes = 4 registers per chunk) and are widened
+  // where they are used, which halves the registers a round needs.
+  constexpr bool kPacked = sizeof(T) == 2;
+  float x[kPacked ? 1 : NI][kPacked ? 1 : VW];
+  uint4 xr[kPacked ? NI : 1];
   auto load_round = [&](int64_t base) {
 #pragma unroll
     for (int r = 0; r < NI; ++r) {
         const int64_t i = base + r * PPW + grp;
-        if (i < hi && has_chunk) {
+        if constexpr (kPacked) {
+          xr[r] = (i < hi && has_chunk) ? __ldg(reinterpret_cast<const uint4*>(pts + i * d) + gl) : make_uint4(0u, 0u, 0u, 0u);
+        } else if (i < hi && has_chunk) {
           Chunk<T, VW>::load(pts + i * d, gl, x[r]);
         } else {
 #pragma unroll
           for (int e = 0; e < VW; ++e) x[r][e] = 0.f;
         }
       }
+  };
+  // element e of round slot r as FP32 (bf16 -> fp32 is a 16-bit left shift of the bit pattern)
+  auto xval = [&](int r, int e) -> float {
+    const uint4& v = xr[r];
+    const int j = e >> 1;
+    const uint32_t w = j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+    return __uint_as_float((e & 1) ? (w & 0xffff0000u) : (w << 16));
   };
   load_round(lo);
   // BF16 rows: a round holds twice the points of an FP32 round, and its loads
@@ -554,8 +567,13 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
       float a = 0.f;
 #pragma unroll
       for (int e = 0; e < VW; ++e) {
-        x[r][e] -= ub[e];
-        a = fmaf(x[r][e], x[r][e], a);
+        if constexpr (kPacked) {
+          const float xe = xval(r, e) - ub[e];
+          a = fmaf(xe, xe, a);
+        } else {
+          x[r][e] -= ub[e];
+          a = fmaf(x[r][e], x[r][e], a);
+        }
       }
       part[r] = has_chunk ? a : 0.f;
     }
@@ -586,7 +604,13 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
     for (int r = 0; r < NI; ++r) {
       const float cr = __shfl_sync(0xffffffffu, c[r % GS::OWN], grp * LPP + GS::src_lane(r));
 #pragma unroll
-      for (int e = 0; e < VW; ++e) G[e] = fmaf(cr, x[r][e], G[e]);
+      for (int e = 0; e < VW; ++e) {
+        if constexpr (kPacked) {
+          G[e] = fmaf(cr, xval(r, e) - ub[e], G[e]);
+        } else {
+          G[e] = fmaf(cr, x[r][e], G[e]);
+        }
+      }
     }
   }
 
