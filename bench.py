@@ -394,12 +394,17 @@ def e2e_host(args, V32, alpha, eor, dev):
 def host_cpu():
     """The host's processor model and logical CPU count (for the CPU baseline's context)."""
     model = platform.processor() or platform.machine()
+    parts = {"0xd4f": "Arm Neoverse-V2 (NVIDIA Grace)", "0xd40": "Arm Neoverse-V1", "0xd0c": "Arm Neoverse-N1"}
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
                 key = line.split(":")[0].strip().lower()
                 if key in ("model name", "cpu model", "hardware"):
                     model = line.split(":", 1)[1].strip()
+                    break
+                if key == "cpu part":
+                    part = line.split(":", 1)[1].strip().lower()
+                    model = parts.get(part, f"Arm CPU part {part}")
                     break
     except OSError:
         pass
