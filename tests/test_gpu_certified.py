@@ -121,3 +121,18 @@ def test_ses_certified_degenerate_inputs(name):
     assert rep["lower_bound"] <= opt * (1 + FP) <= rep["value"] * (1 + FP) + 1e-6
     assert rep["value"] <= (1 + 1e-3) * rep["lower_bound"] * (1 + FP)
     assert oses.ses_objective(V64, None, center.cpu().numpy().astype(np.float64)) <= rep["value"] * (1 + FP)
+
+
+def test_svm_certified_not_separable():
+    # both classes from one distribution: OPT = 0. No direction has a positive margin, so the search
+    # spends its budget (status 5) with margin 0 and a Claim 8 bound that shrinks towards 0 (the oracle
+    # reaches 0.017 on this set within the same budget)
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((200, 3)).astype(np.float32)
+    y = np.where(np.arange(200) < 100, 1, -1).astype(np.int8)
+    w, rep = api.svm_solve(_cuda(X), _cuda(y), eps=1e-2, mode="certified", max_iters=20_000, poll_every=64)
+    assert rep["status"] == 5
+    assert rep["value"] == 0.0 and rep["lower_bound"] == 0.0
+    assert 0.0 <= rep["upper_bound"] < 0.1
+    ref = osvm.svm_solve(X.astype(np.float64), y, eps=1e-2, mode="certified", max_iters=20_000, poll_every=64)
+    assert ref["margin"] == 0.0 and ref["upper_bound"] < 0.1
