@@ -148,12 +148,14 @@ def svm_dual_state(d):
 
 def svm_dual_update(avg, t, z):
     """Running average of the Claim 8 vectors over an alpha-FTP, iterate t
-    weighted by t: zbar is P mubar - Q gammabar for the averaged class-normalised
-    weights (each a point of its simplex), so |zbar| is again a PD-feasible
-    value, an upper bound on OPT. Returns |zbar| (inf before any update)."""
+    weighted by t^2 (as the SES bound): zbar is P mubar - Q gammabar for the
+    averaged class-normalised weights (each a point of its simplex), so |zbar|
+    is again a PD-feasible value, an upper bound on OPT. Returns |zbar| (inf
+    before any update)."""
     if t >= 1 and np.all(np.isfinite(z)):
-        avg["wsum"] += float(t)
-        avg["z"] = avg["z"] + (float(t) / avg["wsum"]) * (z - avg["z"])
+        w = float(t) * float(t)
+        avg["wsum"] += w
+        avg["z"] = avg["z"] + (w / avg["wsum"]) * (z - avg["z"])
     if avg["wsum"] == 0.0:
         return math.inf
     return math.sqrt(float(avg["z"] @ avg["z"]))

@@ -62,8 +62,8 @@ def test_averaged_bound_is_the_qp_value_of_the_averaged_weights(n, d, seed):
     for (t, P, ubar, k), rec in zip(weights, recs):
         kap = oses.ses_qp_weights(V, None, ubar, P, k)
         if t >= 1 and kap.sum() > 0:
-            num += t * kap / kap.sum()
-            den += t
+            num += t * t * kap / kap.sum()
+            den += t * t
             mu = num / den
             y = mu @ V[1:]
             qp = float(y @ y) - float(mu @ np.sum(V[1:] * V[1:], axis=1))  # Eq. ses_qp objective at x = mu
@@ -160,9 +160,9 @@ def test_svm_averaged_bound_is_the_pd_value_of_the_averaged_weights():
             assert math.isinf(rec["dual_bound"])
             continue
         mu, ga = p[y > 0], p[y < 0]
-        mu_acc += t * mu / mu.sum()
-        ga_acc += t * ga / ga.sum()
-        den += t
+        mu_acc += t * t * mu / mu.sum()
+        ga_acc += t * t * ga / ga.sum()
+        den += t * t
         diff = P.T @ (mu_acc / den) - Q.T @ (ga_acc / den)
         assert rec["dual_bound"] == pytest.approx(float(np.linalg.norm(diff)), rel=1e-12)
 
