@@ -84,7 +84,7 @@ typedef enum pdscp_status {
  *   outcome       PDSCP_OUT_* of the alpha-FTP after the step.
  *   k             eta t / rho used by the step.
  *   dual_bound    certificate from the dual weights averaged over the
- *                 alpha-FTP so far (iterate t weighted by t, t >= 1). SES
+ *                 alpha-FTP so far (iterate t weighted by t^2, t >= 1). SES
  *                 (points; 0 for spheres or before the first update): lower
  *                 bound sqrt(Abar - |Bbar|^2) from the QP of Sec. 5 (Eq.
  *                 ses_qp), where mu_i = c_i / sum_j c_j are the weights of the

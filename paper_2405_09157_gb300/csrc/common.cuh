@@ -51,7 +51,7 @@ struct StateHdr {
   double s2bar;
   double last_value;
   double dual_A;    // SES: running average A-bar of the QP bound
-  double dual_w;    // sum of the averaging weights so far (iterate t has weight t)
+  double dual_w;    // sum of the averaging weights so far (iterate t has weight t^2)
 };
 static_assert(sizeof(StateHdr) == 128, "state header must be 128 bytes");
 

@@ -244,12 +244,13 @@ static __device__ __noinline__ void ses_finish_warp(const float2* raw, const dou
   // Averaged QP bound (Eq. ses_qp; points): the weights mu_i = c_i / Cc of this
   // pass give, about v_1, A_t = sum mu_i |v_i - v_1|^2 and B_t = sum mu_i (v_i -
   // v_1) = G'/Cc - (v_1 - ubar); both are averaged over the alpha-FTP with
-  // iterate t weighted by t, and OPT^2 >= Abar - |Bbar|^2.
+  // iterate t weighted by t^2, and OPT^2 >= Abar - |Bbar|^2.
   const float Cc = tot(3);
   const bool qp = s_dual != nullptr;
   const bool qpu = qp && !eval_only && t >= 1 && Cc > 0.f && isfinite(Cc);
-  const double wsum = h.dual_w + (qpu ? (double)t : 0.0);
-  const double rw = qpu ? (double)t / wsum : 0.0;
+  const double wt = (double)t * (double)t;
+  const double wsum = h.dual_w + (qpu ? wt : 0.0);
+  const double rw = qpu ? wt / wsum : 0.0;
   const float rCc = qpu ? 1.0f / Cc : 0.f;
   double* bbar = state_dual(state, d);
   // A = |g|^2, B = g . (v_1 - ubar), C = |ubar - v_1|^2, |Bbar|^2

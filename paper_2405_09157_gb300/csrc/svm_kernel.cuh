@@ -230,12 +230,13 @@ static __device__ __noinline__ void svm_finish_warp(const float2* raw, const dou
   const double s1b = h.s1bar, s2b = h.s2bar;
   const int64_t t = h.t;
   // Averaged Claim 8 bound: zbar, the average over the alpha-FTP of the vectors
-  // P mu/Tr mu - Q gamma/Tr gamma (iterate t weighted by t), is again such a
+  // P mu/Tr mu - Q gamma/Tr gamma (iterate t weighted by t^2), is again such a
   // vector for the averaged class-normalised weights, so OPT <= |zbar|.
   const bool qp = s_dual != nullptr;
   const bool qpu = qp && !eval_only && t >= 1 && SP > 0.f && SQ > 0.f;
-  const double wsum = h.dual_w + (qpu ? (double)t : 0.0);
-  const double rw = qpu ? (double)t / wsum : 0.0;
+  const double wt = (double)t * (double)t;
+  const double wsum = h.dual_w + (qpu ? wt : 0.0);
+  const double rw = qpu ? wt / wsum : 0.0;
   double* zbar = state_dual(state, d);
   // |z|^2, Claim 8 |P mu/Tr mu - Q gamma/Tr gamma|^2, |wbar|^2, z . wbar, |zbar|^2
   float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
