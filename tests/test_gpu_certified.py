@@ -136,3 +136,15 @@ def test_svm_certified_not_separable():
     assert 0.0 <= rep["upper_bound"] < 0.1
     ref = osvm.svm_solve(X.astype(np.float64), y, eps=1e-2, mode="certified", max_iters=20_000, poll_every=64)
     assert ref["margin"] == 0.0 and ref["upper_bound"] < 0.1
+
+
+def test_ses_certified_bf16_points():
+    # BF16-stored points: a certified ball of the BF16-rounded point set (the oracle gets the same values)
+    V32 = datagen.ses_gaussian(3000, 16, seed=4)
+    pb = _cuda(V32).to(torch.bfloat16)
+    V = pb.to(torch.float32).cpu().numpy().astype(np.float64)
+    center, rep = api.ses_solve(pb, eps=1e-3, mode="certified", max_iters=100_000, poll_every=64)
+    ref = oses.ses_solve(V, eps=1e-3, mode="certified", max_iters=100_000, poll_every=64)
+    assert rep["status"] == 0 and rep["value"] <= (1 + 1e-3) * rep["lower_bound"]
+    assert rep["lower_bound"] <= ref["radius"] * (1 + FP) and ref["lower_bound"] <= rep["value"] * (1 + FP)
+    assert oses.ses_objective(V, None, center.cpu().numpy().astype(np.float64)) <= rep["value"] * (1 + FP)
