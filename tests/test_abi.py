@@ -65,6 +65,15 @@ def test_argument_validation_without_gpu(lib):
     assert st == 1 and b"aligned" in lib.pdscp_last_error()
     st = lib.mwu_step(_ffi.SES, fake, _ffi.F32, None, None, 10, 4, 1.0, 0.1, 0.0, 0, fake, fake, 16, None, None)
     assert st == 8
+    # mwu_run: the same checks, plus k >= 0; k = 0 with valid arguments enqueues nothing
+    st = lib.mwu_run(_ffi.SES, fake, _ffi.F32, None, None, 10, 4, 1.0, 0.1, 0.0, -1, fake, fake, 1 << 30, None, None)
+    assert st == 1 and b"k =" in lib.pdscp_last_error()
+    st = lib.mwu_run(_ffi.SVM, fake, _ffi.F32, None, None, 10, 4, 1.0, 0.1, 1.0, 5, fake, fake, 1 << 30, None, None)
+    assert st == 1 and b"labels" in lib.pdscp_last_error()
+    st = lib.mwu_run(_ffi.SES, fake, _ffi.F32, None, None, 10, 4, 1.0, 0.1, 0.0, 5, fake, fake, 16, None, None)
+    assert st == 8
+    assert lib.mwu_run(_ffi.SES, fake, _ffi.F32, None, None, 10, 4, 1.0, 0.1, 0.0, 0, fake, fake, 1 << 30, None,
+                       None) == 0
     opts = _ffi.Options(0.0, 1e-4, 10, 0, 1000, 16, 10, 0.0)
     rep = _ffi.Report()
     st = lib.ses_solve(fake, _ffi.F32, None, 10, 4, ctypes.byref(opts), fake, 1 << 30, None, fake, ctypes.byref(rep))
