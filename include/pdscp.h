@@ -474,14 +474,15 @@ pdscp_status ses_multi_step(const float* pts_dev, const float* radii_dev, int64_
  * index on ties) receive the subgradient; a clipped SVM margin has gradient 0.
  * Radii, D and alpha are constants; for SVM, s_1 and s_2 are piecewise
  * constant in the points and pass no gradient.
- *   problem: PDSCP_SES or PDSCP_SVM; dtype: PDSCP_F32 (BF16 returns
- *     PDSCP_ERR_NOT_IMPLEMENTED); radii_dev (SES, may be NULL), labels_dev and
- *     D (SVM) as for mwu_step.
+ *   problem: PDSCP_SES or PDSCP_SVM; dtype: PDSCP_F32 or PDSCP_BF16 (bfloat16
+ *     rows are widened to float32 on load: the result is the gradient at the
+ *     bfloat16 values, in float32); radii_dev (SES, may be NULL), labels_dev
+ *     and D (SVM) as for mwu_step.
  *   seed_dev: dL/df, one device double (NULL: 1).
  *   ws_dev: mwu_backward_workspace_size bytes (256-byte aligned); on return
  *     it holds the forward's final state and tape (caller-owned).
- *   grad_dev: n x d float32, row-major, overwritten (16-byte alignment with
- *     d % 4 == 0 takes the vector path).
+ *   grad_dev: n x d float32, row-major, overwritten (d % 4 == 0 with grad_dev
+ *     16-byte aligned and pts_dev aligned to 4 elements takes the vector path).
  *   out_dev (may be NULL): one pdscp_step_out: objective = f at the final
  *     mean, t = iterations taken, oracle_value/outcome of the forward,
  *     k = the index of the row attaining f (SES) or the minimum over P (SVM;

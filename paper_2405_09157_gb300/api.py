@@ -188,7 +188,8 @@ def mwu_backward(pts, alpha, eta_over_rho, T, radii=None, seed=None, ws=None, ou
                  problem=SES, labels=None, D=0.0):
     """Gradient of seed * f at the final mean after T alpha-FTP iterations
     from t = 0 at fixed alpha, eta/rho (SES: the radius; SVM: the margin, with
-    labels and D) with respect to the float32 points. seed: one-element
+    labels and D) with respect to the points (float32, or bfloat16 widened on
+    load; the gradient is float32 either way). seed: one-element
     float64 CUDA tensor or None (1). Returns (grad, ws)."""
     n, d, dt = _points(pts)
     if ws is None:

@@ -21,10 +21,10 @@ cudaError_t launch_ses(const SesParams& p, int dtype, bool vec, cudaStream_t str
 cudaError_t launch_svm(const SvmParams& p, int dtype, bool vec, cudaStream_t stream, bool pdl = false);
 cudaError_t launch_ses_merge(const SesMergeParams& m, int dtype, cudaStream_t stream);
 cudaError_t launch_svm_merge(const SvmMergeParams& m, cudaStream_t stream);
-cudaError_t launch_ses_bwd_seed(const BwdParams& p, bool vec, cudaStream_t stream);
-cudaError_t launch_ses_bwd_step(const BwdParams& p, bool vec, cudaStream_t stream, bool pdl);
-cudaError_t launch_svm_bwd_seed(const BwdParams& p, bool vec, cudaStream_t stream);
-cudaError_t launch_svm_bwd_step(const BwdParams& p, bool vec, cudaStream_t stream, bool pdl);
+cudaError_t launch_ses_bwd_seed(const BwdParams& p, bool bf16, bool vec, cudaStream_t stream);
+cudaError_t launch_ses_bwd_step(const BwdParams& p, bool bf16, bool vec, cudaStream_t stream, bool pdl);
+cudaError_t launch_svm_bwd_seed(const BwdParams& p, bool bf16, bool vec, cudaStream_t stream);
+cudaError_t launch_svm_bwd_step(const BwdParams& p, bool bf16, bool vec, cudaStream_t stream, bool pdl);
 
 namespace {
 
@@ -497,7 +497,6 @@ pdscp_status mwu_backward(int32_t problem, const void* pts, int32_t dtype, const
                           pdscp_step_out* out) {
   pdscp_status st = check_common(problem, pts, dtype, n, d);
   if (st != PDSCP_OK) return st;
-  if (dtype != PDSCP_F32) return fail(PDSCP_ERR_NOT_IMPLEMENTED, "the reverse sweep takes float32 points");
   if (T < 1) return fail(PDSCP_ERR_INVALID_ARG, "T must be >= 1");
   if (!ws || !grad) return fail(PDSCP_ERR_INVALID_ARG, "workspace or gradient pointer is null");
   if (!aligned(ws, 256)) return fail(PDSCP_ERR_INVALID_ARG, "workspace not 256-byte aligned");
@@ -530,7 +529,7 @@ pdscp_status mwu_backward(int32_t problem, const void* pts, int32_t dtype, const
   }
   const Layout L = layout(problem, d);
   BwdParams bp{};
-  bp.pts = reinterpret_cast<const float*>(pts);
+  bp.pts = pts;
   bp.radii = rad;
   bp.labels = lab;
   bp.n = n;
@@ -549,21 +548,23 @@ pdscp_status mwu_backward(int32_t problem, const void* pts, int32_t dtype, const
   bp.ncand = device_sm_count() * kMaxBlocksPerSM;
   bp.seed = seed;
   bp.out = out;
-  const bool vec = use_vec(pts, dtype, d) && aligned(grad, 16);
+  // the reverse passes read 4-element chunks of either point type next to float4 gradient chunks
+  const bool bf16 = dtype == PDSCP_BF16;
+  const bool vec = d % 4 == 0 && aligned(pts, 4 * elem_size(dtype)) && aligned(grad, 16);
   if (problem == PDSCP_SES) {
-    e = launch_ses_bwd_seed(bp, vec, s);
+    e = launch_ses_bwd_seed(bp, bf16, vec, s);
     if (e != cudaSuccess) return cuda_fail(e, "reverse-sweep seed launch");
     for (int64_t k = T - 1; k >= 1; --k) {  // step 0 only hands dL/dubar^1 to v_1 (done by step 1's bookkeeping)
       bp.s = k;
-      e = launch_ses_bwd_step(bp, vec, s, true);  // consecutive reverse steps overlap (dependent launch)
+      e = launch_ses_bwd_step(bp, bf16, vec, s, true);  // consecutive reverse steps overlap (dependent launch)
       if (e != cudaSuccess) return cuda_fail(e, "reverse-step launch");
     }
   } else {
-    e = launch_svm_bwd_seed(bp, vec, s);
+    e = launch_svm_bwd_seed(bp, bf16, vec, s);
     if (e != cudaSuccess) return cuda_fail(e, "reverse-sweep seed launch");
     for (int64_t k = T - 1; k >= 0; --k) {
       bp.s = k;
-      e = launch_svm_bwd_step(bp, vec, s, true);
+      e = launch_svm_bwd_step(bp, bf16, vec, s, true);
       if (e != cudaSuccess) return cuda_fail(e, "reverse-step launch");
     }
   }

@@ -41,7 +41,7 @@ __host__ __device__ inline size_t bwd_scratch_bytes(int d) {
 }
 
 struct BwdParams {
-  const float* pts;
+  const void* pts;     // n x d rows of the kernels' point type T (float or bfloat16)
   const float* radii;  // may be null
   int64_t n;
   int d;
@@ -62,6 +62,25 @@ struct BwdParams {
   const double* seed;    // dL/df (may be null: 1)
   pdscp_step_out* out;   // seed: f at ubar^T and the steps taken (may be null)
   const int8_t* labels;  // SVM: +1 (P) / -1 (Q) per row
+};
+
+// Row i of the points, as the kernels' point type T.
+template <typename T>
+__device__ __forceinline__ const T* bwd_row(const BwdParams& p, int64_t i) {
+  return static_cast<const T*>(p.pts) + i * p.d;
+}
+
+// Four bfloat16 values (8 bytes) widened to float: the reverse sweep keeps the
+// float32 chunk width of its gradient rows (VW = 4) for bfloat16 points.
+template <>
+struct Chunk<__nv_bfloat16, 4> {
+  static __device__ __forceinline__ void load(const __nv_bfloat16* row, int c, float* o) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(row) + c);
+    o[0] = __uint_as_float(v.x << 16);
+    o[1] = __uint_as_float(v.x & 0xffff0000u);
+    o[2] = __uint_as_float(v.y << 16);
+    o[3] = __uint_as_float(v.y & 0xffff0000u);
+  }
 };
 
 __device__ __forceinline__ double* bwd_B(unsigned char* bw) { return reinterpret_cast<double*>(bw); }
@@ -116,7 +135,7 @@ static __device__ void bwd_prologue(int64_t s, const float* tape, int d, float r
 
 // One reverse step s >= 1: a streaming pass over the cones, then (last CTA)
 // B <- s/(s+1) B - sum_i dL/ddelta_i and the bookkeeping of step s - 1.
-template <int VW, int LPP, int NCH, int U>
+template <typename T, int VW, int LPP, int NCH, int U>
 __global__ void __launch_bounds__(kBlock) ses_bwd_step_kernel(BwdParams p) {
   pdl_trigger();
   pdl_wait();  // Gbar, Sbar and the gradient rows are the previous reverse step's output
@@ -160,7 +179,7 @@ __global__ void __launch_bounds__(kBlock) ses_bwd_step_kernel(BwdParams p) {
       for (int j = 0; j < NCH; ++j) {
         const int c = gl + j * LPP;
         if (i < p.n && c < nch) {
-          Chunk<float, VW>::load(p.pts + i * d, c, x[u][j]);
+          Chunk<T, VW>::load(bwd_row<T>(p, i), c, x[u][j]);
         } else {
 #pragma unroll
           for (int e = 0; e < VW; ++e) x[u][j][e] = 0.f;
@@ -267,7 +286,7 @@ __global__ void __launch_bounds__(kBlock) ses_bwd_step_kernel(BwdParams p) {
 // points per lane per round, their gradient rows loaded with them, and the
 // scalar work of each point (its exponentials, c_i, beta_i) done once, on the
 // lane that owns it after a reduce-scatter of the two partial dot products.
-template <int VW, int LPP, int NI>
+template <typename T, int VW, int LPP, int NI>
 __global__ void __launch_bounds__(kBlock) ses_bwd_step_t_kernel(BwdParams p) {
   using GS = GroupScatter<LPP, NI>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -298,7 +317,7 @@ __global__ void __launch_bounds__(kBlock) ses_bwd_step_t_kernel(BwdParams p) {
     for (int r = 0; r < NI; ++r) {
       const int64_t i = base + r * PPW + grp;
       if (i < p.n && has_chunk) {
-        Chunk<float, VW>::load(p.pts + i * d, gl, x[r]);
+        Chunk<T, VW>::load(bwd_row<T>(p, i), gl, x[r]);
       } else {
 #pragma unroll
         for (int e = 0; e < VW; ++e) x[r][e] = 0.f;
@@ -423,7 +442,7 @@ __global__ void __launch_bounds__(kBlock) ses_bwd_step_t_kernel(BwdParams p) {
 
 // argmax_i dist(ubar^T, v_i) + gamma_i over every row (v_1 included): one
 // candidate (value, smallest index) per CTA.
-template <int VW, int LPP, int NCH, int U>
+template <typename T, int VW, int LPP, int NCH, int U>
 __global__ void __launch_bounds__(kBlock) ses_bwd_argmax_kernel(BwdParams p) {
   __shared__ float s_val[kWarps];
   __shared__ long long s_idx[kWarps];
@@ -454,7 +473,7 @@ __global__ void __launch_bounds__(kBlock) ses_bwd_argmax_kernel(BwdParams p) {
         const int c = gl + j * LPP;
         float x[VW];
         if (i < p.n && c < nch) {
-          Chunk<float, VW>::load(p.pts + i * d, c, x);
+          Chunk<T, VW>::load(bwd_row<T>(p, i), c, x);
 #pragma unroll
           for (int e = 0; e < VW; ++e) {
             const float dl = x[e] - ub[j][e];
@@ -501,7 +520,7 @@ __global__ void __launch_bounds__(kBlock) ses_bwd_argmax_kernel(BwdParams p) {
 
 // One CTA: picks i* from the candidates, seeds B = dL/dubar^T = seed (ubar^T -
 // v_i*)/|ubar^T - v_i*| and row i* of grad, then the bookkeeping of step T-1.
-template <int kUnused = 0>  // a template so that only the launching unit instantiates it
+template <typename PT>  // the point type; a template, so only the launching units instantiate it
 __global__ void __launch_bounds__(32) ses_bwd_seed_kernel(BwdParams p) {
   const int lane = threadIdx.x;
   const int d = p.d;
@@ -527,11 +546,11 @@ __global__ void __launch_bounds__(32) ses_bwd_seed_kernel(BwdParams p) {
   const StateHdr* hdr = reinterpret_cast<const StateHdr*>(p.state);
   const int64_t T = hdr->t;
   const float* mean32 = state_mean32(const_cast<void*>(p.state), d);
-  const float* row = p.pts + bi * d;
+  const PT* row = bwd_row<PT>(p, bi);
   // the direction in FP32 from the values the argmax pass compared
   float n2 = 0.f;
   for (int j = lane; j < d; j += 32) {
-    const float dl = mean32[j] - row[j];
+    const float dl = mean32[j] - elem_to_float(row + j);
     n2 = fmaf(dl, dl, n2);
   }
   n2 = warp_sum(n2);
@@ -540,7 +559,7 @@ __global__ void __launch_bounds__(32) ses_bwd_seed_kernel(BwdParams p) {
   double* B = bwd_B(p.bw);
   double* V1 = bwd_V1(p.bw, d);
   for (int j = lane; j < d; j += 32) {
-    const double dir = (double)((mean32[j] - row[j]) * rn);
+    const double dir = (double)((mean32[j] - elem_to_float(row + j)) * rn);
     B[j] = sd * dir;
     V1[j] = 0.0;
     p.grad[bi * d + j] -= (float)(sd * dir);
@@ -614,7 +633,7 @@ static __device__ void svm_bwd_prologue(int64_t s, const float* tape, int d, uns
   if (lane == 0) *bwd_Sbar(bw, d) = -dot2 * rS;
 }
 
-template <int VW, int LPP, int NCH, int U>
+template <typename T, int VW, int LPP, int NCH, int U>
 __global__ void __launch_bounds__(kBlock) svm_bwd_step_kernel(BwdParams p) {
   pdl_trigger();
   pdl_wait();  // the adjoint scratch and the gradient rows are the previous reverse step's output
@@ -658,7 +677,7 @@ __global__ void __launch_bounds__(kBlock) svm_bwd_step_kernel(BwdParams p) {
       for (int j = 0; j < NCH; ++j) {
         const int c = gl + j * LPP;
         if (i < p.n && c < nch) {
-          Chunk<float, VW>::load(p.pts + i * d, c, x[u][j]);
+          Chunk<T, VW>::load(bwd_row<T>(p, i), c, x[u][j]);
         } else {
 #pragma unroll
           for (int e = 0; e < VW; ++e) x[u][j][e] = 0.f;
@@ -755,7 +774,7 @@ __global__ void __launch_bounds__(kBlock) svm_bwd_step_kernel(BwdParams p) {
 // the form of ses_bwd_step_t_kernel: NI points per lane per round with their
 // gradient rows, the scalar work once per point after a reduce-scatter of
 // the two partial dot products.
-template <int VW, int LPP, int NI>
+template <typename T, int VW, int LPP, int NI>
 __global__ void __launch_bounds__(kBlock) svm_bwd_step_t_kernel(BwdParams p) {
   pdl_trigger();
   pdl_wait();  // the adjoint scratch and the gradient rows are the previous reverse step's output
@@ -794,7 +813,7 @@ __global__ void __launch_bounds__(kBlock) svm_bwd_step_t_kernel(BwdParams p) {
     for (int r = 0; r < NI; ++r) {
       const int64_t i = base + r * PPW + grp;
       if (i < p.n && has_chunk) {
-        Chunk<float, VW>::load(p.pts + i * d, gl, x[r]);
+        Chunk<T, VW>::load(bwd_row<T>(p, i), gl, x[r]);
         const float4 g4 = *reinterpret_cast<const float4*>(p.grad + i * d + gl * VW);
         gr[r][0] = g4.x; gr[r][1] = g4.y; gr[r][2] = g4.z; gr[r][3] = g4.w;
       } else {
@@ -887,7 +906,7 @@ __global__ void __launch_bounds__(kBlock) svm_bwd_step_t_kernel(BwdParams p) {
 
 // min over P and max over Q of x_i^T wbar^T: two candidates (value, smallest
 // index) per CTA, at [2 b] (P) and [2 b + 1] (Q).
-template <int VW, int LPP, int NCH, int U>
+template <typename T, int VW, int LPP, int NCH, int U>
 __global__ void __launch_bounds__(kBlock) svm_bwd_argmax_kernel(BwdParams p) {
   __shared__ float s_val[kWarps][2];
   __shared__ long long s_idx[kWarps][2];
@@ -919,7 +938,7 @@ __global__ void __launch_bounds__(kBlock) svm_bwd_argmax_kernel(BwdParams p) {
         const int c = gl + j * LPP;
         float x[VW];
         if (i < p.n && c < nch) {
-          Chunk<float, VW>::load(p.pts + i * d, c, x);
+          Chunk<T, VW>::load(bwd_row<T>(p, i), c, x);
 #pragma unroll
           for (int e = 0; e < VW; ++e) part = fmaf(x[e], wb[j][e], part);
         }
@@ -968,7 +987,7 @@ __global__ void __launch_bounds__(kBlock) svm_bwd_argmax_kernel(BwdParams p) {
 
 // One warp: picks the rows attaining min_P and max_Q, seeds B = dL/dwbar^T and
 // those rows of grad, then the bookkeeping of step T-1.
-template <int kUnused = 0>  // a template so that only the launching unit instantiates it
+template <typename PT>  // the point type; a template, so only the launching units instantiate it
 __global__ void __launch_bounds__(32) svm_bwd_seed_kernel(BwdParams p) {
   const int lane = threadIdx.x;
   const int d = p.d;
@@ -1007,12 +1026,12 @@ __global__ void __launch_bounds__(32) svm_bwd_seed_kernel(BwdParams p) {
   const bool live = have && L > 0.f;                    // a clipped margin has gradient 0
   const double sd = p.seed ? *p.seed : 1.0;
   double* B = bwd_B(p.bw);
-  const float* xP = p.pts + (live ? bi[0] : 0) * d;
-  const float* xQ = p.pts + (live ? bi[1] : 0) * d;
+  const PT* xP = bwd_row<PT>(p, live ? bi[0] : 0);
+  const PT* xQ = bwd_row<PT>(p, live ? bi[1] : 0);
   for (int j = lane; j < d; j += 32) {
     if (live) {
       const float dir = wb[j] * rn;
-      B[j] = sd * (double)((xP[j] - xQ[j]) * rn - L * dir * rn);
+      B[j] = sd * (double)((elem_to_float(xP + j) - elem_to_float(xQ + j)) * rn - L * dir * rn);
       p.grad[bi[0] * d + j] += (float)(sd * dir);
       p.grad[bi[1] * d + j] -= (float)(sd * dir);
     } else {

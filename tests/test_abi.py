@@ -95,7 +95,8 @@ def test_argument_validation_without_gpu(lib):
     bwd = lambda problem, dtype, T, ws_bytes: lib.mwu_backward(problem, fake, dtype, None, None, 10, 4, 1.0, 0.1,
                                                                0.0, T, None, fake, ws_bytes, None, fake, None)
     assert bwd(_ffi.SVM, _ffi.F32, 5, 1 << 30) == 1 and b"labels" in lib.pdscp_last_error()
-    assert bwd(_ffi.SES, _ffi.BF16, 5, 1 << 30) == 7 and b"float32" in lib.pdscp_last_error()
+    assert bwd(_ffi.SES, 3, 5, 1 << 30) == 1 and b"dtype" in lib.pdscp_last_error()
+    assert bwd(_ffi.SES, _ffi.BF16, 5, 1024) == 8  # bfloat16 points pass the checks up to the workspace size
     assert bwd(_ffi.SES, _ffi.F32, 0, 1 << 30) == 1
     assert bwd(_ffi.SES, _ffi.F32, 5, 1024) == 8
     size = ctypes.c_size_t()

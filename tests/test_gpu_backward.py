@@ -191,3 +191,72 @@ def test_svm_full_size_rotation_identity():
     M = X.T @ got
     tot = np.abs(got).sum()
     assert np.max(np.abs(M - M.T)) <= 1e-4 * np.abs(X).max() * tot + 1e-6
+
+
+# --- bfloat16 points --------------------------------------------------------
+# The sweep reads BF16 rows and widens them to FP32 on load; the gradient is the
+# one of the BF16-rounded point set, so the oracle runs on those values (exact
+# in FP64) and the tolerance is the FP32 one above.
+
+
+def _bf16(a32):
+    """(bf16 CUDA tensor, its values as float64 numpy)."""
+    pb = torch.from_numpy(a32).cuda().to(torch.bfloat16)
+    return pb, pb.float().cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("n,d,T,radii", [(3000, 32, 12, False), (2000, 8, 15, True), (1001, 5, 6, True),
+                                         (4099, 16, 10, False), (20000, 64, 8, False), (300, 3, 10, False)])
+def test_backward_bf16_points_match_oracle(n, d, T, radii):
+    V32, g32, _, g, _, _, _ = _case(n, d, 23, radii)
+    pb, V = _bf16(V32)
+    D = oses.ses_D(V, g)
+    alpha, rho, eta = 0.9 * D, oses.ses_width(D), 0.5
+    L, want, steps = ses_grad.ses_unrolled_radius_grad(V, g, alpha, eta / rho, T)
+    out = api.new_steps(1)
+    radii_t = None if g32 is None else torch.from_numpy(g32).cuda()
+    grad, _ = api.mwu_backward(pb, alpha, eta / rho, T, radii=radii_t, out=out)
+    torch.cuda.synchronize()
+    rec = api.decode_steps(out)[0]
+    assert grad.dtype == torch.float32 and grad.shape == (n, d)
+    assert rec["status"] == 0 and rec["t"] == steps == T
+    assert abs(rec["objective"] - L) <= RTOL * D
+    got = grad.cpu().numpy().astype(np.float64)
+    scale = max(np.max(np.abs(want)), 1.0)
+    assert np.max(np.abs(got - want)) <= GRAD_RTOL * scale
+
+
+def test_backward_bf16_rows_not_8_byte_aligned():
+    # a view starting 2 elements (4 bytes) into its buffer takes the per-element path
+    n, d, T = 1500, 8, 10
+    V32, _, _, _, _, _, _ = _case(n, d, 24, False)
+    buf = torch.zeros(n * d + 2, dtype=torch.bfloat16, device="cuda")
+    buf[2:] = torch.from_numpy(V32).cuda().reshape(-1).to(torch.bfloat16)
+    pb = buf[2:].view(n, d)
+    assert pb.data_ptr() % 8 == 4
+    V = pb.float().cpu().numpy().astype(np.float64)
+    D = oses.ses_D(V)
+    alpha, rho, eta = 0.9 * D, oses.ses_width(D), 0.5
+    L, want, _ = ses_grad.ses_unrolled_radius_grad(V, None, alpha, eta / rho, T)
+    grad, _ = api.mwu_backward(pb, alpha, eta / rho, T)
+    got = grad.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - want)) <= GRAD_RTOL * max(np.max(np.abs(want)), 1.0)
+
+
+@pytest.mark.parametrize("n1,n2,d,T", [(700, 900, 8, 15), (2000, 1500, 32, 12), (500, 400, 5, 6)])
+def test_svm_backward_bf16_points_match_oracle(n1, n2, d, T):
+    X32, y = datagen.svm_clusters(n1, n2, d, mu_norm=3.0, band=0.5, seed=33)
+    pb, X = _bf16(X32)
+    D = osvm.svm_D(X)
+    rho, alpha, eta = osvm.svm_width(D), 0.2 * D, 0.5
+    L, want, steps = svm_grad.svm_unrolled_margin_grad(X, y, alpha, eta / rho, D, T)
+    out = api.new_steps(1)
+    grad, _ = api.mwu_backward(pb, alpha, eta / rho, T, out=out, problem=_ffi.SVM,
+                               labels=torch.from_numpy(y).cuda(), D=D)
+    torch.cuda.synchronize()
+    rec = api.decode_steps(out)[0]
+    assert rec["status"] == 0 and rec["t"] == steps == T
+    assert abs(rec["objective"] - L) <= RTOL * D
+    got = grad.cpu().numpy().astype(np.float64)
+    scale = max(np.max(np.abs(want)), 1.0)
+    assert np.max(np.abs(got - want)) <= GRAD_RTOL * scale
