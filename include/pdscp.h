@@ -317,28 +317,35 @@ pdscp_status svm_solve(const void* X_dev, int32_t dtype, const int8_t* labels_de
 /*
  * Batched SES (many independent instances, one launch per iteration for all).
  * Instance i has n_i >= 2 points of dimension 1 <= d_i <= 64, stored row-major
- * in one float32 buffer of pts_len floats starting at element offset_i
- * (16-byte aligned starts enable 16-byte loads when d_i % 4 == 0). Each
+ * in one buffer of pts_len elements of type dtype (PDSCP_F32 or PDSCP_BF16;
+ * bfloat16 rows are widened to float32 on load, the arithmetic is that of
+ * float32 rows), starting at element offset_i (a start aligned to 4 elements
+ * enables 16-byte (float32) or 8-byte (bfloat16) loads when d_i % 4 == 0;
+ * pts_dev must be aligned to its element). Each
  * instance runs its own alpha-FTP (Sec. 3 with the SES data of Sec. 4.1)
  * with its own state, kept in the workspace. Rows are cut into tiles of
  * tile_rows (>= 32); a persistent grid takes tiles from a counter and the
  * CTA that completes an instance's last tile finishes that instance.
  *   ses_batch_workspace_size: bytes of the workspace (host sizes).
  *   ses_batch_init: builds the tile tables (host -> workspace, synchronises
- *     the stream) and starts every instance's alpha-FTP (t = 0, mean = v_1).
+ *     the stream), records dtype and starts every instance's alpha-FTP (t = 0,
+ *     mean = v_1). An unknown dtype, an instance past pts_len or a misaligned
+ *     pointer returns PDSCP_ERR_INVALID_ARG before any device work.
  *   ses_batch_step: one MWU iteration of every instance (asynchronous);
- *     alpha_dev and eta_over_rho_dev hold one double per instance; out_dev
- *     (may be NULL) receives one pdscp_step_out per instance.
+ *     pts_dev and dtype must be those given to ses_batch_init (not checked
+ *     against the workspace: the call does not synchronise); alpha_dev and
+ *     eta_over_rho_dev hold one double per instance; out_dev (may be NULL)
+ *     receives one pdscp_step_out per instance.
  *   ses_batch_read: each instance's running mean and best centre, packed one
  *     after another (instance i's d_i values after those of instances < i).
  */
 pdscp_status ses_batch_workspace_size(int32_t num, const int64_t* n_host, const int32_t* d_host,
                                       int32_t tile_rows, size_t* bytes_host);
-pdscp_status ses_batch_init(int32_t num, const float* pts_dev, int64_t pts_len,
+pdscp_status ses_batch_init(int32_t num, const void* pts_dev, int32_t dtype, int64_t pts_len,
                             const int64_t* offset_host, const int64_t* n_host,
                             const int32_t* d_host, int32_t tile_rows, void* ws_dev,
                             size_t ws_bytes, pdscp_stream stream);
-pdscp_status ses_batch_step(int32_t num, const float* pts_dev, const double* alpha_dev,
+pdscp_status ses_batch_step(int32_t num, const void* pts_dev, int32_t dtype, const double* alpha_dev,
                             const double* eta_over_rho_dev, void* ws_dev, size_t ws_bytes,
                             pdscp_stream stream, pdscp_step_out* out_dev);
 pdscp_status ses_batch_read(int32_t num, const void* ws_dev, float* mean_dev, float* best_dev,
@@ -358,7 +365,8 @@ pdscp_status ses_batch_read(int32_t num, const void* ws_dev, float* mean_dev, fl
  *     options (opts->poll_every is used by the CERTIFIED mode only;
  *     opts->max_iters counts MWU iterations per instance). Synchronises the
  *     stream.
- *   ses_batch_solve_run: replays a CUDA graph of launches_per_poll launches
+ *   ses_batch_solve_run: (pts_dev as given to ses_batch_solve_init, whose
+ *     dtype the workspace records) replays a CUDA graph of launches_per_poll launches
  *     on `stream` until every instance is done or max_launches launches ran
  *     (host polls a device counter after each replay); reports the launches
  *     run and the instances done (host pointers, may be NULL).
@@ -374,18 +382,18 @@ pdscp_status ses_batch_read(int32_t num, const void* ws_dev, float* mean_dev, fl
  *     the fastest; leaves the workspace set up for the last candidate tried,
  *     so ses_batch_solve_init must follow.
  */
-pdscp_status ses_batch_solve_init(int32_t num, const float* pts_dev, int64_t pts_len,
+pdscp_status ses_batch_solve_init(int32_t num, const void* pts_dev, int32_t dtype, int64_t pts_len,
                                   const int64_t* offset_host, const int64_t* n_host,
                                   const int32_t* d_host, int32_t tile_rows,
                                   const pdscp_options* opts, void* ws_dev, size_t ws_bytes,
                                   pdscp_stream stream);
-pdscp_status ses_batch_solve_run(int32_t num, const float* pts_dev, void* ws_dev, size_t ws_bytes,
+pdscp_status ses_batch_solve_run(int32_t num, const void* pts_dev, void* ws_dev, size_t ws_bytes,
                                  int32_t launches_per_poll, int64_t max_launches,
                                  pdscp_stream stream, int64_t* launches_host, int32_t* done_host);
 pdscp_status ses_batch_solve_read(int32_t num, const void* ws_dev, double eps,
                                   pdscp_report* reports_dev, float* centers_dev,
                                   pdscp_stream stream);
-pdscp_status ses_batch_autotune(int32_t num, const float* pts_dev, int64_t pts_len,
+pdscp_status ses_batch_autotune(int32_t num, const void* pts_dev, int32_t dtype, int64_t pts_len,
                                 const int64_t* offset_host, const int64_t* n_host,
                                 const int32_t* d_host, const pdscp_options* opts, void* ws_dev,
                                 size_t ws_bytes, pdscp_stream stream, int32_t* tile_rows_host,

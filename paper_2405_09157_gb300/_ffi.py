@@ -69,14 +69,14 @@ SIGNATURES = {
     "svm_solve": (c_i32, [c_vp, c_i32, c_vp, c_i64, c_i32, ctypes.POINTER(Options), c_vp, c_sz, c_vp,
                           c_vp, ctypes.POINTER(Report)]),
     "ses_batch_workspace_size": (c_i32, [c_i32, c_vp, c_vp, c_i32, ctypes.POINTER(c_sz)]),
-    "ses_batch_init": (c_i32, [c_i32, c_vp, c_i64, c_vp, c_vp, c_vp, c_i32, c_vp, c_sz, c_vp]),
-    "ses_batch_step": (c_i32, [c_i32, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp, c_vp]),
+    "ses_batch_init": (c_i32, [c_i32, c_vp, c_i32, c_i64, c_vp, c_vp, c_vp, c_i32, c_vp, c_sz, c_vp]),
+    "ses_batch_step": (c_i32, [c_i32, c_vp, c_i32, c_vp, c_vp, c_vp, c_sz, c_vp, c_vp]),
     "ses_batch_read": (c_i32, [c_i32, c_vp, c_vp, c_vp, c_vp]),
-    "ses_batch_solve_init": (c_i32, [c_i32, c_vp, c_i64, c_vp, c_vp, c_vp, c_i32, c_vp, c_vp, c_sz, c_vp]),
+    "ses_batch_solve_init": (c_i32, [c_i32, c_vp, c_i32, c_i64, c_vp, c_vp, c_vp, c_i32, c_vp, c_vp, c_sz, c_vp]),
     "ses_batch_solve_run": (c_i32, [c_i32, c_vp, c_vp, c_sz, c_i32, c_i64, c_vp, ctypes.POINTER(c_i64),
                                     ctypes.POINTER(c_i32)]),
     "ses_batch_solve_read": (c_i32, [c_i32, c_vp, c_dbl, c_vp, c_vp, c_vp]),
-    "ses_batch_autotune": (c_i32, [c_i32, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp,
+    "ses_batch_autotune": (c_i32, [c_i32, c_vp, c_i32, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp,
                                    ctypes.POINTER(c_i32), ctypes.POINTER(ctypes.c_float)]),
     "mwu_shard_row_width": (c_i32, [c_i32, c_i32, ctypes.POINTER(c_i32)]),
     "mwu_shard_init": (c_i32, [c_i32, c_vp, c_i32, c_i32, c_i32, c_dbl, c_i32, c_vp, c_vp, c_sz, c_vp]),

@@ -434,10 +434,11 @@ def svm_solve(X, labels, eps=1e-3, mode="practical", max_iters=1_000_000, poll_e
 
 
 # ------------------------------------------------------------------ batched SES
-def pack_instances(arrays, device="cuda"):
-    """Pack float32 (n_i, d_i) arrays into one device buffer, each instance
-    starting on a 16-byte boundary. Returns (pts, offsets, n, d) where offsets,
-    n (int64) and d (int32) are numpy arrays."""
+def pack_instances(arrays, device="cuda", dtype=torch.float32):
+    """Pack (n_i, d_i) arrays into one device buffer of dtype (torch.float32 or
+    torch.bfloat16, rounded on the device), each instance starting on a
+    4-element boundary. Returns (pts, offsets, n, d) where offsets, n (int64)
+    and d (int32) are numpy arrays."""
     n = np.array([a.shape[0] for a in arrays], dtype=np.int64)
     d = np.array([a.shape[1] for a in arrays], dtype=np.int32)
     offs = np.zeros(len(arrays), dtype=np.int64)
@@ -449,14 +450,16 @@ def pack_instances(arrays, device="cuda"):
     host = np.zeros(max(pos, 4), dtype=np.float32)
     for i, a in enumerate(arrays):
         host[offs[i]:offs[i] + a.size] = np.ascontiguousarray(a, dtype=np.float32).reshape(-1)
-    return torch.from_numpy(host).to(device), offs, n, d
+    return torch.from_numpy(host).to(device).to(dtype), offs, n, d
 
 
 class SesBatch:
     """Many independent SES alpha-FTPs advanced together, one launch per iteration."""
 
     def __init__(self, pts, offsets, n, d, tile_rows=4096, stream=None):
+        """pts: the packed 1-D float32 or bfloat16 CUDA buffer of pack_instances."""
         self.pts, self.num = pts, len(n)
+        self.dt = dtype_code(pts)
         self.offsets = np.ascontiguousarray(offsets, dtype=np.int64)
         self.n = np.ascontiguousarray(n, dtype=np.int64)
         self.d = np.ascontiguousarray(d, dtype=np.int32)
@@ -469,13 +472,13 @@ class SesBatch:
         self.init(stream)
 
     def init(self, stream=None):
-        check(load().ses_batch_init(self.num, _vp(self.pts), self.pts.numel(), self.offsets.ctypes.data,
+        check(load().ses_batch_init(self.num, _vp(self.pts), self.dt, self.pts.numel(), self.offsets.ctypes.data,
                                     self.n.ctypes.data, self.d.ctypes.data, self.tile_rows, _vp(self.ws),
                                     self.ws.numel(), _stream(stream)), "ses_batch_init")
 
     def step(self, alpha, eta_over_rho, out=None, stream=None):
         """alpha, eta_over_rho: float64 CUDA tensors of one value per instance."""
-        check(load().ses_batch_step(self.num, _vp(self.pts), _vp(alpha), _vp(eta_over_rho), _vp(self.ws),
+        check(load().ses_batch_step(self.num, _vp(self.pts), self.dt, _vp(alpha), _vp(eta_over_rho), _vp(self.ws),
                                     self.ws.numel(), _stream(stream), _vp(out)), "ses_batch_step")
 
     def _host_tables(self):
@@ -495,7 +498,7 @@ class SesBatch:
             self.ws = torch.zeros(need.value, dtype=torch.uint8, device=self.pts.device)
         tr, ms = ctypes.c_int32(), ctypes.c_float()
         offs, n, d = self._host_tables()
-        check(lib.ses_batch_autotune(self.num, _vp(self.pts), self.pts.numel(), offs, n, d, ctypes.byref(o),
+        check(lib.ses_batch_autotune(self.num, _vp(self.pts), self.dt, self.pts.numel(), offs, n, d, ctypes.byref(o),
                                      _vp(self.ws), self.ws.numel(), _stream(stream), ctypes.byref(tr),
                                      ctypes.byref(ms)), "ses_batch_autotune")
         self.tile_rows = tr.value
@@ -511,7 +514,7 @@ class SesBatch:
         o = _options(eps, mode, max_iters, poll_every, max_steps, eta, delta, patience)
         lib = load()
         offs, n, d = self._host_tables()
-        check(lib.ses_batch_solve_init(self.num, _vp(self.pts), self.pts.numel(), offs, n, d, self.tile_rows,
+        check(lib.ses_batch_solve_init(self.num, _vp(self.pts), self.dt, self.pts.numel(), offs, n, d, self.tile_rows,
                                        ctypes.byref(o), _vp(self.ws), self.ws.numel(), _stream(stream)),
               "ses_batch_solve_init")
         launches, done = ctypes.c_int64(), ctypes.c_int32()

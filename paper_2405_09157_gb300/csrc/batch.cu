@@ -1,5 +1,6 @@
 // Host side of the batched SES iteration (batch_kernel.cuh): workspace
-// layout, per-instance tables and states, one-iteration launches.
+// layout, per-instance tables and states, one-iteration launches, for
+// float32 or bfloat16 points (one instantiation of the kernels per type).
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -77,17 +78,21 @@ pdscp_status batch_layout(int num, const int64_t* n, const int32_t* d, int tile_
 
 // Tables, header and fresh states of a batch (shared by the plain and the
 // search entry points). Synchronises the stream (the host tables are local).
-pdscp_status batch_setup(int32_t num, const float* pts_dev, int64_t pts_len, const int64_t* offset_host,
+size_t batch_elem(int dtype) { return dtype == PDSCP_BF16 ? 2 : 4; }
+
+pdscp_status batch_setup(int32_t num, const void* pts_dev, int32_t dtype, int64_t pts_len, const int64_t* offset_host,
                          const int64_t* n_host, const int32_t* d_host, int32_t tile_rows, void* ws_dev,
                          size_t ws_bytes, cudaStream_t s, BatchLayout* Lout) {
   if (!pts_dev || !offset_host || !ws_dev || !n_host || !d_host)
     return err(PDSCP_ERR_INVALID_ARG, "batch: null pointer argument");
-  if (((uintptr_t)pts_dev % 4) != 0 || ((uintptr_t)ws_dev % 256) != 0)
-    return err(PDSCP_ERR_INVALID_ARG, "batch: points must be 4-byte and workspace 256-byte aligned");
+  if (dtype != PDSCP_F32 && dtype != PDSCP_BF16) return err(PDSCP_ERR_INVALID_ARG, "batch: unknown dtype %lld", dtype);
+  const size_t es = batch_elem(dtype);
+  if (((uintptr_t)pts_dev % es) != 0 || ((uintptr_t)ws_dev % 256) != 0)
+    return err(PDSCP_ERR_INVALID_ARG, "batch: points must be aligned to their element and workspace to 256 bytes");
   for (int i = 0; i < num; ++i) {
     if (offset_host[i] < 0) return err(PDSCP_ERR_INVALID_ARG, "batch: negative offset for instance %lld", i);
     if (n_host[i] < 0 || d_host[i] < 0 || offset_host[i] + n_host[i] * (int64_t)d_host[i] > pts_len)
-      return err(PDSCP_ERR_INVALID_ARG, "batch: instance %lld extends past the %lld points' floats", i, pts_len);
+      return err(PDSCP_ERR_INVALID_ARG, "batch: instance %lld extends past the %lld point elements", i, pts_len);
   }
   BatchLayout L;
   std::vector<BatchInst> insts;
@@ -97,12 +102,14 @@ pdscp_status batch_setup(int32_t num, const float* pts_dev, int64_t pts_len, con
   if (st != PDSCP_OK) return st;
   if (ws_bytes < L.total) return err(PDSCP_ERR_WORKSPACE, "batch: workspace %lld < %lld bytes", (long long)ws_bytes,
                                      (long long)L.total);
-  // 16-byte loads need each instance's rows to start on a 16-byte boundary
+  // chunk loads (16 bytes for float32, 8 for bfloat16) need each instance's rows to start on a
+  // 4-element boundary of the address space
   for (auto& in : insts)
-    if (in.shape <= 4 && (((uintptr_t)(pts_dev + in.pt_off)) % 16) != 0) in.shape = batch_shape(in.d, false);
+    if (in.shape <= 4 && ((uintptr_t)pts_dev + (uintptr_t)in.pt_off * es) % (4 * es) != 0)
+      in.shape = batch_shape(in.d, false);
   unsigned char* ws = reinterpret_cast<unsigned char*>(ws_dev);
   BatchHeader bh{num, L.ntiles, (int64_t)L.inst_off, (int64_t)L.instcnt_off, (int64_t)L.tile_off,
-                 (int64_t)L.partial_off, (int64_t)L.search_off, 0};
+                 (int64_t)L.partial_off, (int64_t)L.search_off, dtype, 0};
   cudaError_t e = cudaMemsetAsync(ws, 0, 1024, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ws + 256, &bh, sizeof(bh), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
@@ -112,8 +119,12 @@ pdscp_status batch_setup(int32_t num, const float* pts_dev, int64_t pts_len, con
   if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.search_off, 0, (size_t)num * sizeof(BatchSearch), s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host tables go out of scope
   if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: table upload failed (%lld)", (long long)e);
-  ses_batch_init_kernel<<<num, 64, 0, s>>>(pts_dev, reinterpret_cast<const BatchInst*>(ws + L.inst_off), ws,
-                                            reinterpret_cast<unsigned int*>(ws + L.instcnt_off));
+  const BatchInst* inst_dev = reinterpret_cast<const BatchInst*>(ws + L.inst_off);
+  unsigned int* cnt_dev = reinterpret_cast<unsigned int*>(ws + L.instcnt_off);
+  if (dtype == PDSCP_BF16)
+    ses_batch_init_kernel<<<num, 64, 0, s>>>(static_cast<const __nv_bfloat16*>(pts_dev), inst_dev, ws, cnt_dev);
+  else
+    ses_batch_init_kernel<<<num, 64, 0, s>>>(static_cast<const float*>(pts_dev), inst_dev, ws, cnt_dev);
   e = cudaGetLastError();
   if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: init launch failed (%lld)", (long long)e);
   if (Lout) *Lout = L;
@@ -121,18 +132,26 @@ pdscp_status batch_setup(int32_t num, const float* pts_dev, int64_t pts_len, con
 }
 
 // One iteration of every instance; with a search, then every instance's search step.
-cudaError_t launch_batch(const float* pts, const double* alpha, const double* eor, unsigned char* ws,
-                         pdscp_step_out* out, BatchSearch* search, cudaStream_t s, int num = 0) {
+template <typename T>
+cudaError_t launch_batch_t(const T* pts, const double* alpha, const double* eor, unsigned char* ws,
+                           pdscp_step_out* out, BatchSearch* search, cudaStream_t s, int num) {
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ses_batch_kernel, kBatchBlock, 0) != cudaSuccess || occ < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ses_batch_kernel<T>, kBatchBlock, 0) != cudaSuccess ||
+      occ < 1)
     occ = 1;
   const int grid = device_sm_count() * occ;
   BatchParams p{pts, alpha, eor, ws, out, search};
-  ses_batch_kernel<<<grid, kBatchBlock, 0, s>>>(p);
+  ses_batch_kernel<T><<<grid, kBatchBlock, 0, s>>>(p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !search) return e;
-  ses_batch_search_kernel<<<(num + 7) / 8, 256, 0, s>>>(pts, ws, num);
+  ses_batch_search_kernel<T><<<(num + 7) / 8, 256, 0, s>>>(pts, ws, num);
   return cudaGetLastError();
+}
+cudaError_t launch_batch(const void* pts, int32_t dtype, const double* alpha, const double* eor, unsigned char* ws,
+                         pdscp_step_out* out, BatchSearch* search, cudaStream_t s, int num = 0) {
+  if (dtype == PDSCP_BF16)
+    return launch_batch_t(static_cast<const __nv_bfloat16*>(pts), alpha, eor, ws, out, search, s, num);
+  return launch_batch_t(static_cast<const float*>(pts), alpha, eor, ws, out, search, s, num);
 }
 
 pdscp_status solve_opts(const pdscp_options* o, BatchSolveOpts* b) {
@@ -155,13 +174,14 @@ pdscp_status solve_opts(const pdscp_options* o, BatchSolveOpts* b) {
   return PDSCP_OK;
 }
 
-pdscp_status solve_setup(int32_t num, const float* pts_dev, int64_t pts_len, const int64_t* offset_host,
+pdscp_status solve_setup(int32_t num, const void* pts_dev, int32_t dtype, int64_t pts_len, const int64_t* offset_host,
                          const int64_t* n_host, const int32_t* d_host, int32_t tile_rows, const pdscp_options* o,
                          void* ws_dev, size_t ws_bytes, cudaStream_t s) {
   BatchSolveOpts bo;
   pdscp_status st = solve_opts(o, &bo);
   if (st != PDSCP_OK) return st;
-  st = batch_setup(num, pts_dev, pts_len, offset_host, n_host, d_host, tile_rows, ws_dev, ws_bytes, s, nullptr);
+  st = batch_setup(num, pts_dev, dtype, pts_len, offset_host, n_host, d_host, tile_rows, ws_dev, ws_bytes, s,
+                   nullptr);
   if (st != PDSCP_OK) return st;
   cudaError_t e = cudaMemcpyAsync(reinterpret_cast<unsigned char*>(ws_dev) + kBatchOptsOff, &bo, sizeof(bo),
                                   cudaMemcpyHostToDevice, s);
@@ -196,33 +216,35 @@ pdscp_status ses_batch_workspace_size(int32_t num, const int64_t* n_host, const 
   return PDSCP_OK;
 }
 
-pdscp_status ses_batch_init(int32_t num, const float* pts_dev, int64_t pts_len, const int64_t* offset_host,
-                            const int64_t* n_host, const int32_t* d_host, int32_t tile_rows, void* ws_dev,
-                            size_t ws_bytes, pdscp_stream stream) {
-  return batch_setup(num, pts_dev, pts_len, offset_host, n_host, d_host, tile_rows, ws_dev, ws_bytes,
+pdscp_status ses_batch_init(int32_t num, const void* pts_dev, int32_t dtype, int64_t pts_len,
+                            const int64_t* offset_host, const int64_t* n_host, const int32_t* d_host,
+                            int32_t tile_rows, void* ws_dev, size_t ws_bytes, pdscp_stream stream) {
+  return batch_setup(num, pts_dev, dtype, pts_len, offset_host, n_host, d_host, tile_rows, ws_dev, ws_bytes,
                      (cudaStream_t)stream, nullptr);
 }
 
-pdscp_status ses_batch_step(int32_t num, const float* pts_dev, const double* alpha_dev,
+pdscp_status ses_batch_step(int32_t num, const void* pts_dev, int32_t dtype, const double* alpha_dev,
                             const double* eta_over_rho_dev, void* ws_dev, size_t ws_bytes, pdscp_stream stream,
                             pdscp_step_out* out_dev) {
   if (num < 1 || !pts_dev || !alpha_dev || !eta_over_rho_dev || !ws_dev)
     return err(PDSCP_ERR_INVALID_ARG, "batch: bad argument to ses_batch_step");
+  if (dtype != PDSCP_F32 && dtype != PDSCP_BF16) return err(PDSCP_ERR_INVALID_ARG, "batch: unknown dtype %lld", dtype);
   if (ws_bytes < 1024) return err(PDSCP_ERR_WORKSPACE, "batch: workspace too small");
-  cudaError_t e = launch_batch(pts_dev, alpha_dev, eta_over_rho_dev, reinterpret_cast<unsigned char*>(ws_dev),
+  cudaError_t e = launch_batch(pts_dev, dtype, alpha_dev, eta_over_rho_dev, reinterpret_cast<unsigned char*>(ws_dev),
                                out_dev, nullptr, (cudaStream_t)stream);
   if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: step launch failed (%lld)", (long long)e);
   return PDSCP_OK;
 }
 
-pdscp_status ses_batch_solve_init(int32_t num, const float* pts_dev, int64_t pts_len, const int64_t* offset_host,
-                                  const int64_t* n_host, const int32_t* d_host, int32_t tile_rows,
-                                  const pdscp_options* opts, void* ws_dev, size_t ws_bytes, pdscp_stream stream) {
-  return solve_setup(num, pts_dev, pts_len, offset_host, n_host, d_host, tile_rows, opts, ws_dev, ws_bytes,
+pdscp_status ses_batch_solve_init(int32_t num, const void* pts_dev, int32_t dtype, int64_t pts_len,
+                                  const int64_t* offset_host, const int64_t* n_host, const int32_t* d_host,
+                                  int32_t tile_rows, const pdscp_options* opts, void* ws_dev, size_t ws_bytes,
+                                  pdscp_stream stream) {
+  return solve_setup(num, pts_dev, dtype, pts_len, offset_host, n_host, d_host, tile_rows, opts, ws_dev, ws_bytes,
                      (cudaStream_t)stream);
 }
 
-pdscp_status ses_batch_solve_run(int32_t num, const float* pts_dev, void* ws_dev, size_t ws_bytes,
+pdscp_status ses_batch_solve_run(int32_t num, const void* pts_dev, void* ws_dev, size_t ws_bytes,
                                  int32_t launches_per_poll, int64_t max_launches, pdscp_stream stream,
                                  int64_t* launches_host, int32_t* done_host) {
   if (num < 1 || !pts_dev || !ws_dev || launches_per_poll < 1 || max_launches < 1)
@@ -233,6 +255,7 @@ pdscp_status ses_batch_solve_run(int32_t num, const float* pts_dev, void* ws_dev
   BatchHeader bh;
   pdscp_status st = read_header(ws_dev, s, &bh);
   if (st != PDSCP_OK) return st;
+  const int32_t dtype = bh.dtype;  // the point type given to ses_batch_solve_init
   BatchSearch* search = reinterpret_cast<BatchSearch*>(ws + bh.search_off);
   const unsigned int* done = reinterpret_cast<const unsigned int*>(ws) + 2;
   // a CUDA graph of launches_per_poll iterations, captured on a private stream
@@ -244,7 +267,7 @@ pdscp_status ses_batch_solve_run(int32_t num, const float* pts_dev, void* ws_dev
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     for (int k = 0; k < launches_per_poll && e == cudaSuccess; ++k)
-      e = launch_batch(pts_dev, nullptr, nullptr, ws, nullptr, search, cs, num);
+      e = launch_batch(pts_dev, dtype, nullptr, nullptr, ws, nullptr, search, cs, num);
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
     if (e == cudaSuccess) e = e2;
   }
@@ -283,7 +306,8 @@ pdscp_status ses_batch_solve_read(int32_t num, const void* ws_dev, double eps, p
   return PDSCP_OK;
 }
 
-pdscp_status ses_batch_autotune(int32_t num, const float* pts_dev, int64_t pts_len, const int64_t* offset_host,
+pdscp_status ses_batch_autotune(int32_t num, const void* pts_dev, int32_t dtype, int64_t pts_len,
+                                const int64_t* offset_host,
                                 const int64_t* n_host, const int32_t* d_host, const pdscp_options* opts,
                                 void* ws_dev, size_t ws_bytes, pdscp_stream stream, int32_t* tile_rows_host,
                                 float* ms_per_launch_host) {
@@ -300,16 +324,16 @@ pdscp_status ses_batch_autotune(int32_t num, const float* pts_dev, int64_t pts_l
   for (int32_t tr : cand) {
     BatchLayout L;
     if (batch_layout(num, n_host, d_host, tr, &L, nullptr, nullptr, nullptr) != PDSCP_OK || L.total > ws_bytes) continue;
-    st = solve_setup(num, pts_dev, pts_len, offset_host, n_host, d_host, tr, opts, ws_dev, ws_bytes, s);
+    st = solve_setup(num, pts_dev, dtype, pts_len, offset_host, n_host, d_host, tr, opts, ws_dev, ws_bytes, s);
     if (st != PDSCP_OK) break;
     BatchHeader bh;
     if ((st = read_header(ws_dev, s, &bh)) != PDSCP_OK) break;
     unsigned char* ws = reinterpret_cast<unsigned char*>(ws_dev);
     BatchSearch* search = reinterpret_cast<BatchSearch*>(ws + bh.search_off);
     // the bounds pass and one iteration untimed, then four timed iterations
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_batch(pts_dev, nullptr, nullptr, ws, nullptr, search, s, num);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_batch(pts_dev, dtype, nullptr, nullptr, ws, nullptr, search, s, num);
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = launch_batch(pts_dev, nullptr, nullptr, ws, nullptr, search, s, num);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = launch_batch(pts_dev, dtype, nullptr, nullptr, ws, nullptr, search, s, num);
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.f;

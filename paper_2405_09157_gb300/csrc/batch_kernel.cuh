@@ -1,13 +1,15 @@
 // Batched SES iteration: one launch runs one MWU iteration (Sec. 4.1 with
 // Eq. implement and Eq. ses_oracle, as in ses_kernel.cuh) for every instance
 // of a batch of independent SES problems of uneven size n_i and dimension
-// d_i <= 64. The instances' points are packed in one float32 buffer; each
+// d_i <= 64. The instances' points are packed in one float32 or bfloat16
+// buffer (the kernels' point type T; bfloat16 rows are widened on load); each
 // instance is cut into tiles of consecutive rows. A persistent grid takes
 // tiles from a global counter; the CTA that completes an instance's last
 // tile reduces that instance's partial rows and runs its O(d) finish while
 // the other CTAs keep streaming. No CTA waits on another.
 #pragma once
 
+#include "bf16_chunk4.cuh"
 #include "ses_kernel.cuh"
 
 namespace pdscp {
@@ -42,7 +44,8 @@ struct BatchHeader {
   int64_t num, ntiles;
   int64_t inst_off, instcnt_off, tile_off, partial_off;
   int64_t search_off;
-  int64_t pad;
+  int32_t dtype;  // PDSCP_F32 or PDSCP_BF16: the point type of ses_batch_*init
+  int32_t pad;
 };
 
 // Device-side search of Sec. 3 for every instance of a batch (the rules of
@@ -83,7 +86,7 @@ constexpr double kCertMinEta = 1.0 / 64.0;  // eta is not halved below this
 constexpr size_t kBatchOptsOff = 512;
 
 struct BatchParams {
-  const float* pts;
+  const void* pts;             // packed rows of the kernels' point type T
   const double* alpha;         // per instance (plain iterations)
   const double* eta_over_rho;  // per instance (plain iterations)
   unsigned char* ws;           // workspace base
@@ -92,13 +95,14 @@ struct BatchParams {
 };
 
 // Load/lane layouts, chosen on the host per instance:
-//   0..4: 16-byte chunks, LPP = 1, 2, 4, 8, 16 (d = 4 * LPP or less, d % 4 == 0, aligned)
+//   0..4: 4-element chunks, LPP = 1, 2, 4, 8, 16 (d = 4 * LPP or less, d % 4 == 0, rows aligned
+//        to 4 elements: one 16-byte load per chunk for float32, one 8-byte load for bfloat16)
 //   9: scalar, one lane per point (d <= 4: a warp covers 32 consecutive short
 //      rows, and each point's exponentials run once, not on several lanes);
 //   6: scalar, 8 lanes (d <= 8); 7: scalar, 32 lanes (d <= 32);
 //   8: scalar, 32 lanes x 2 (d <= 64); 5 (2 lanes, d <= 2) is kept for callers of old tables
-inline int batch_shape(int d, bool aligned16) {
-  if (d % 4 == 0 && aligned16) {
+inline int batch_shape(int d, bool aligned4) {
+  if (d % 4 == 0 && aligned4) {
     const int c = d / 4;
     return c <= 1 ? 0 : c <= 2 ? 1 : c <= 4 ? 2 : c <= 8 ? 3 : 4;
   }
@@ -108,8 +112,8 @@ inline int batch_shape(int d, bool aligned16) {
 // Streams rows [r0, r1) of one instance at mean ubar (in shared memory, FP32)
 // and leaves the CTA's totals in sG/s_sc (per warp). Same per-point
 // arithmetic as ses_iter_kernel (rows 0 of the instance, v_1, excluded).
-template <int VW, int LPP, int NCH, int U>
-__device__ void batch_tile(const float* pts, int d, int64_t r0, int64_t r1, const float* s_ub, float kr, float H,
+template <typename T, int VW, int LPP, int NCH, int U>
+__device__ void batch_tile(const T* pts, int d, int64_t r0, int64_t r1, const float* s_ub, float kr, float H,
                            float alpha, float* sG, float (*s_sc)[4], float* s_cs) {
   const int nch = (d + VW - 1) / VW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -132,12 +136,12 @@ __device__ void batch_tile(const float* pts, int d, int64_t r0, int64_t r1, cons
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t i = base + u * PPW + grp;
-      const float* row = pts + i * d;
+      const T* row = pts + i * d;
 #pragma unroll
       for (int j = 0; j < NCH; ++j) {
         const int c = gl + j * LPP;
         if (i < r1 && c < nch) {
-          Chunk<float, VW>::load(row, c, x[u][j]);
+          Chunk<T, VW>::load(row, c, x[u][j]);
         } else {
 #pragma unroll
           for (int e = 0; e < VW; ++e) x[u][j][e] = 0.f;
@@ -213,7 +217,8 @@ __device__ void batch_tile(const float* pts, int d, int64_t r0, int64_t r1, cons
 // Runs in its own kernel after each iteration launch (ses_batch_search_kernel):
 // called from the streaming kernel, its FP64 bookkeeping would raise that
 // kernel's register count and lower its occupancy.
-static __device__ __forceinline__ void batch_search_update(BatchSearch* sr, void* state, const float* v1, int d,
+template <typename T>
+static __device__ __forceinline__ void batch_search_update(BatchSearch* sr, void* state, const T* v1, int d,
                                                         int64_t n, const BatchSolveOpts& o,
                                                         unsigned int* done_counter) {
   const int lane = threadIdx.x & 31;
@@ -324,7 +329,7 @@ static __device__ __forceinline__ void batch_search_update(BatchSearch* sr, void
     float* mean32 = state_mean32(state, d);
     float* best = state_best(state, d);
     for (int j = lane; j < dp; j += 32) {
-      const double v = j < d ? (double)v1[j] : 0.0;
+      const double v = j < d ? (double)elem_to_float(v1 + j) : 0.0;
       mean[j] = v;
       mean32[j] = (float)v;
       best[j] = (float)v;
@@ -345,7 +350,7 @@ static __device__ __forceinline__ void batch_search_update(BatchSearch* sr, void
   if (done) {
     if (!(r.ub < INFINITY) || !(r.D > 0.0)) {  // no FTP produced a centre: v_1 with radius D encloses every point
       r.ub = r.D;
-      for (int j = lane; j < d; j += 32) r.center[j] = v1[j];
+      for (int j = lane; j < d; j += 32) r.center[j] = elem_to_float(v1 + j);
     }
     r.phase = kPhaseDone;
     if (lane == 0) {
@@ -381,13 +386,13 @@ static __device__ __forceinline__ void batch_search_update(BatchSearch* sr, void
   for (int j = lane; j < d; j += 32) sr->center[j] = r.center[j];
 }
 
-// batch_tile for 16-byte chunk rows (d = 4 VW.. up to 64 floats): each warp
+// batch_tile for rows of 4-element chunks (d = 4 .. 64, d % 4 == 0): each warp
 // streams one contiguous part of the tile, NI points per lane per round (all
 // loads of a round in flight together), and each point's scalar work runs
 // once, on the lane that owns it after a reduce-scatter of the partial
 // squared distances (GroupScatter), as in ses_iter_t_kernel.
-template <int VW, int LPP, int NI>
-__device__ void batch_tile_t(const float* pts, int d, int64_t r0, int64_t r1, const float* s_ub, float kr,
+template <typename T, int VW, int LPP, int NI>
+__device__ void batch_tile_t(const T* pts, int d, int64_t r0, int64_t r1, const float* s_ub, float kr,
                              float H, float alpha, float* sG, float (*s_sc)[4], float* s_cs) {
   using GS = GroupScatter<LPP, NI>;
   const int nch = d / VW;
@@ -413,7 +418,7 @@ __device__ void batch_tile_t(const float* pts, int d, int64_t r0, int64_t r1, co
     for (int r = 0; r < NI; ++r) {
       const int64_t i = base + r * PPW + grp;
       if (i < hi && has_chunk) {
-        Chunk<float, VW>::load(pts + i * d, gl, x[r]);
+        Chunk<T, VW>::load(pts + i * d, gl, x[r]);
       } else {
 #pragma unroll
         for (int e = 0; e < VW; ++e) x[r][e] = 0.f;
@@ -480,6 +485,7 @@ __device__ void batch_tile_t(const float* pts, int d, int64_t r0, int64_t r1, co
 // Three CTAs per SM: left free, the compiler gave this kernel 111 registers
 // (two CTAs per SM); bounded, it needs 78 with no spill, and the extra warps
 // raise the batched iteration from 4.9 to 5.9 TB/s.
+template <typename T>
 __global__ void __launch_bounds__(kBatchBlock, 3) ses_batch_kernel(BatchParams p) {
   __shared__ float sG[kBatchWarps * kBatchMaxD];
   __shared__ float s_sc[kBatchWarps][4];
@@ -512,7 +518,7 @@ __global__ void __launch_bounds__(kBatchBlock, 3) ses_batch_kernel(BatchParams p
     void* state = p.ws + in.state_off;
     const StateHdr* hdr = reinterpret_cast<const StateHdr*>(state);
     const int d = in.d;
-    const float* pts = p.pts + in.pt_off;
+    const T* pts = static_cast<const T*>(p.pts) + in.pt_off;
     if (hdr->stopped != 0) {  // a stopped FTP (or a finished search) is left as is
       __syncthreads();
       continue;
@@ -530,16 +536,16 @@ __global__ void __launch_bounds__(kBatchBlock, 3) ses_batch_kernel(BatchParams p
       if (tid < d) s_ub[tid] = mean32[tid];
       __syncthreads();
       switch (in.shape) {
-        case 0: batch_tile_t<4, 1, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
-        case 1: batch_tile_t<4, 2, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
-        case 2: batch_tile_t<4, 4, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
-        case 3: batch_tile_t<4, 8, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
-        case 4: batch_tile_t<4, 16, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
-        case 5: batch_tile<1, 2, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
-        case 6: batch_tile<1, 8, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
-        case 7: batch_tile<1, 32, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
-        case 9: batch_tile<1, 1, 4, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
-        default: batch_tile<1, 32, 2, 2>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
+        case 0: batch_tile_t<T, 4, 1, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
+        case 1: batch_tile_t<T, 4, 2, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
+        case 2: batch_tile_t<T, 4, 4, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
+        case 3: batch_tile_t<T, 4, 8, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
+        case 4: batch_tile_t<T, 4, 16, 8>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
+        case 5: batch_tile<T, 1, 2, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
+        case 6: batch_tile<T, 1, 8, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
+        case 7: batch_tile<T, 1, 32, 1, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
+        case 9: batch_tile<T, 1, 1, 4, 4>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
+        default: batch_tile<T, 1, 32, 2, 2>(pts, d, tl.r0, tl.r1, s_ub, kr, H, alpha, sG, s_sc, s_cs); break;
       }
       __syncthreads();
       float* prow = partials + (size_t)tile * kBatchStride;
@@ -580,7 +586,7 @@ __global__ void __launch_bounds__(kBatchBlock, 3) ses_batch_kernel(BatchParams p
         const double* mean = state_mean(state);
         if (tid < d) {
           s_mean[tid] = mean[tid];
-          s_v1[tid] = (double)pts[tid];
+          s_v1[tid] = (double)elem_to_float(pts + tid);
           s_dual[tid] = state_dual(state, d)[tid];
         }
         const int st = 4 + dpad4(d);
@@ -609,7 +615,8 @@ __global__ void __launch_bounds__(kBatchBlock, 3) ses_batch_kernel(BatchParams p
 
 // The search step of every instance still searching, one warp per instance,
 // after the launch that ran the instance's iteration (or evaluation pass).
-__global__ void __launch_bounds__(256) ses_batch_search_kernel(const float* pts, unsigned char* ws, int num) {
+template <typename T>
+__global__ void __launch_bounds__(256) ses_batch_search_kernel(const T* pts, unsigned char* ws, int num) {
   const int inst = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (inst >= num) return;
   const BatchHeader* bh = reinterpret_cast<const BatchHeader*>(ws + 256);
@@ -622,7 +629,8 @@ __global__ void __launch_bounds__(256) ses_batch_search_kernel(const float* pts,
 }
 
 // Fresh alpha-FTP states for every instance (t = 0, mean = v_1); one CTA per instance.
-__global__ void ses_batch_init_kernel(const float* pts, const BatchInst* inst, unsigned char* ws,
+template <typename T>
+__global__ void ses_batch_init_kernel(const T* pts, const BatchInst* inst, unsigned char* ws,
                                       unsigned int* inst_counters) {
   const BatchInst in = inst[blockIdx.x];
   void* state = ws + in.state_off;
@@ -632,7 +640,7 @@ __global__ void ses_batch_init_kernel(const float* pts, const BatchInst* inst, u
   float* mean32 = state_mean32(state, d);
   float* best = state_best(state, d);
   for (int j = threadIdx.x; j < dp; j += blockDim.x) {
-    const double v = j < d ? (double)pts[in.pt_off + j] : 0.0;
+    const double v = j < d ? (double)elem_to_float(pts + in.pt_off + j) : 0.0;
     mean[j] = v;
     mean32[j] = (float)v;
     best[j] = (float)v;

@@ -30,7 +30,7 @@
 // not take (it stopped early) are skipped on the device.
 #pragma once
 
-#include "common.cuh"
+#include "bf16_chunk4.cuh"
 
 namespace pdscp {
 
@@ -69,19 +69,6 @@ template <typename T>
 __device__ __forceinline__ const T* bwd_row(const BwdParams& p, int64_t i) {
   return static_cast<const T*>(p.pts) + i * p.d;
 }
-
-// Four bfloat16 values (8 bytes) widened to float: the reverse sweep keeps the
-// float32 chunk width of its gradient rows (VW = 4) for bfloat16 points.
-template <>
-struct Chunk<__nv_bfloat16, 4> {
-  static __device__ __forceinline__ void load(const __nv_bfloat16* row, int c, float* o) {
-    const uint2 v = __ldg(reinterpret_cast<const uint2*>(row) + c);
-    o[0] = __uint_as_float(v.x << 16);
-    o[1] = __uint_as_float(v.x & 0xffff0000u);
-    o[2] = __uint_as_float(v.y << 16);
-    o[3] = __uint_as_float(v.y & 0xffff0000u);
-  }
-};
 
 __device__ __forceinline__ double* bwd_B(unsigned char* bw) { return reinterpret_cast<double*>(bw); }
 __device__ __forceinline__ double* bwd_V1(unsigned char* bw, int d) {

@@ -119,8 +119,17 @@ def test_batch_validation_without_gpu(lib):
     assert lib.ses_batch_workspace_size(2, n, d, 4096, ctypes.byref(size)) == 0 and size.value > 0
     offs = (ctypes.c_int64 * 2)(0, 800)
     fake = ctypes.c_void_p(1 << 20)
-    st = lib.ses_batch_init(2, fake, 1000, offs, n, d, 4096, fake, 1 << 30, None)  # 800 + 400 > 1000
+    st = lib.ses_batch_init(2, fake, _ffi.F32, 1000, offs, n, d, 4096, fake, 1 << 30, None)  # 800 + 400 > 1000
     assert st == 1 and b"extends past" in lib.pdscp_last_error()
+    st = lib.ses_batch_init(2, fake, _ffi.BF16, 1000, offs, n, d, 4096, fake, 1 << 30, None)  # lengths in elements
+    assert st == 1 and b"extends past" in lib.pdscp_last_error()
+    st = lib.ses_batch_init(2, fake, 5, 2000, offs, n, d, 4096, fake, 1 << 30, None)
+    assert st == 1 and b"dtype" in lib.pdscp_last_error()
+    odd = ctypes.c_void_p((1 << 20) + 1)  # not aligned to a bfloat16 element
+    st = lib.ses_batch_init(2, odd, _ffi.BF16, 2000, offs, n, d, 4096, fake, 1 << 30, None)
+    assert st == 1 and b"aligned" in lib.pdscp_last_error()
+    alpha = ctypes.c_void_p(1 << 21)
+    assert lib.ses_batch_step(2, fake, 9, alpha, alpha, fake, 1 << 30, None, None) == 1
 
 
 def test_shard_validation_without_gpu(lib):
@@ -154,17 +163,17 @@ def test_batch_search_validation_without_gpu(lib):
     offs = (ctypes.c_int64 * 2)(0, 800)
     fake = ctypes.c_void_p(1 << 20)
     bad = _ffi.Options(0.0, 1e-4, 10, 0, 1000, 1, 10, 0.0)  # eps = 0
-    st = lib.ses_batch_solve_init(2, fake, 1200, offs, n, d, 512, ctypes.byref(bad), fake, 1 << 30, None)
+    st = lib.ses_batch_solve_init(2, fake, _ffi.F32, 1200, offs, n, d, 512, ctypes.byref(bad), fake, 1 << 30, None)
     assert st == 1 and b"options" in lib.pdscp_last_error()
     bad = _ffi.Options(1e-3, 1e-4, 10, 7, 1000, 1, 10, 0.0)  # unknown mode
-    assert lib.ses_batch_solve_init(2, fake, 1200, offs, n, d, 512, ctypes.byref(bad), fake, 1 << 30, None) == 1
+    assert lib.ses_batch_solve_init(2, fake, _ffi.F32, 1200, offs, n, d, 512, ctypes.byref(bad), fake, 1 << 30, None) == 1
     bad = _ffi.Options(1e-3, 0.0, 10, _ffi.MODE_CERTIFIED, 1000, 0, 10, 0.0)  # certified needs a poll interval
-    assert lib.ses_batch_solve_init(2, fake, 1200, offs, n, d, 512, ctypes.byref(bad), fake, 1 << 30, None) == 1
+    assert lib.ses_batch_solve_init(2, fake, _ffi.F32, 1200, offs, n, d, 512, ctypes.byref(bad), fake, 1 << 30, None) == 1
     launches, done = ctypes.c_int64(), ctypes.c_int32()
     assert lib.ses_batch_solve_run(2, fake, fake, 1 << 30, 0, 10, None, ctypes.byref(launches),
                                    ctypes.byref(done)) == 1
     tr = ctypes.c_int32()
-    assert lib.ses_batch_autotune(2, fake, 1200, offs, n, d, None, fake, 1 << 30, None, None, None) == 1
+    assert lib.ses_batch_autotune(2, fake, _ffi.F32, 1200, offs, n, d, None, fake, 1 << 30, None, None, None) == 1
 
 
 def test_multi_validation_without_gpu(lib):

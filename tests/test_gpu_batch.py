@@ -226,3 +226,87 @@ def test_batch_full_workload_sampled_instances():
                 assert abs(r[key] - o[key]) <= tol, (k, int(n[k]), int(d[k]), t, key, r[key], o[key])
             ubar = o["ubar_next"]
         assert np.linalg.norm(means[k].astype(np.float64) - ubar) <= tol, k
+
+
+# --- bfloat16 batches ---------------------------------------------------------
+# Rows are stored in bfloat16 and widened on load; each instance is compared with
+# the oracle run on its bfloat16-rounded values (exact in FP64), at the FP32
+# tolerance above.
+
+
+def _rounded(pts, off, n, d):
+    return pts[off:off + n * d].float().view(n, d).cpu().numpy().astype(np.float64)
+
+
+def _check_trajectories(batch, pts, offs, n, d, shapes, T=20, eta=0.5):
+    V = [_rounded(pts, int(offs[k]), int(n[k]), int(d[k])) for k in range(len(shapes))]
+    D = np.array([oses.ses_D(v) for v in V])
+    rho = np.array([oses.ses_width(x) for x in D])
+    alpha = 0.8 * D
+    a_dev = torch.tensor(alpha, dtype=torch.float64, device="cuda")
+    e_dev = torch.tensor(eta / rho, dtype=torch.float64, device="cuda")
+    outs = [api.new_steps(len(shapes)) for _ in range(T)]
+    for t in range(T):
+        batch.step(a_dev, e_dev, out=outs[t])
+    torch.cuda.synchronize()
+    recs = [api.decode_steps(o) for o in outs]
+    means, _ = batch.read()
+    for k in range(len(shapes)):
+        ubar = V[k][0].copy()
+        tol = RTOL * D[k]
+        for t in range(T):
+            o = oses.ses_step(V[k], None, ubar, t, alpha[k], eta, rho[k])
+            r = recs[t][k]
+            assert r["status"] == 0, (k, t)
+            for key in ("objective", "oracle_value", "lower_bound"):
+                assert abs(r[key] - o[key]) <= tol, (k, shapes[k], t, key, r[key], o[key])
+            if abs(o["oracle_value"]) > tol:
+                assert bool(r["failed"]) == o["failed"], (k, t)
+            if o["failed"]:
+                break
+            ubar = o["ubar_next"]
+        assert np.linalg.norm(means[k].astype(np.float64) - ubar) <= tol, (k, shapes[k])
+
+
+def test_batch_bf16_trajectories_match_oracle_per_instance():
+    arrays = [datagen.ses_gaussian(n, d, seed=700 + k, scale=1.0 + k) for k, (n, d) in enumerate(SHAPES)]
+    pts, offs, n, d = api.pack_instances(arrays, dtype=torch.bfloat16)
+    assert pts.dtype == torch.bfloat16
+    batch = api.SesBatch(pts, offs, n, d, tile_rows=512)
+    _check_trajectories(batch, pts, offs, n, d, SHAPES)
+
+
+def test_batch_bf16_rows_off_the_chunk_boundary():
+    # instances starting 2 elements (4 bytes) past an 8-byte boundary take the per-element layouts
+    shapes = [(3000, 32), (777, 16), (1000, 4)]
+    arrays = [datagen.ses_gaussian(nn, dd, seed=800 + k) for k, (nn, dd) in enumerate(shapes)]
+    offs = np.array([2, 2 + 3000 * 32 + 4, 2 + 3000 * 32 + 4 + 777 * 16 + 4], dtype=np.int64)
+    total = int(offs[-1] + 1000 * 4)
+    host = np.zeros(total, dtype=np.float32)
+    for k, a in enumerate(arrays):
+        host[offs[k]:offs[k] + a.size] = a.reshape(-1)
+    pts = torch.from_numpy(host).cuda().to(torch.bfloat16)
+    n = np.array([s[0] for s in shapes], dtype=np.int64)
+    d = np.array([s[1] for s in shapes], dtype=np.int32)
+    batch = api.SesBatch(pts, offs, n, d, tile_rows=256)
+    _check_trajectories(batch, pts, offs, n, d, shapes, T=12)
+
+
+def test_batch_bf16_certified_search_matches_single_instance_solves():
+    eps = 1e-3
+    arrays = [datagen.ses_gaussian(nn, dd, seed=900 + nn) for nn, dd in [(4000, 8), (1500, 32), (999, 3), (20000, 16)]]
+    pts, offs, n, d = api.pack_instances(arrays, dtype=torch.bfloat16)
+    batch = api.SesBatch(pts, offs, n, d, tile_rows=1024)
+    reps, centres, _ = batch.solve(eps=eps, mode="certified", max_iters=200_000, poll_every=64,
+                                   launches_per_poll=16)
+    for k in range(len(arrays)):
+        V = _rounded(pts, int(offs[k]), int(n[k]), int(d[k]))
+        r = reps[k]
+        assert r["status"] == 0, (k, r)
+        assert r["upper_bound"] <= (1 + eps) * r["lower_bound"] * (1 + 1e-5)
+        assert oses.ses_objective(V, None, centres[k].astype(np.float64)) <= r["upper_bound"] * (1 + 1e-5)
+        row = pts[int(offs[k]):int(offs[k]) + int(n[k]) * int(d[k])].view(int(n[k]), int(d[k]))
+        _, one = api.ses_solve(row, eps=eps, mode="certified", max_iters=200_000, poll_every=64)
+        assert one["status"] == 0
+        assert r["lower_bound"] <= one["upper_bound"] * (1 + 1e-5)
+        assert one["lower_bound"] <= r["upper_bound"] * (1 + 1e-5)
