@@ -188,3 +188,24 @@ def test_multi_validation_without_gpu(lib):
                             None, None)
     assert st == 1 and b"misaligned" in lib.pdscp_last_error()
     assert lib.ses_multi_step(fake, None, 10, 4, 2, fake, fake, fake, fake, 64, None, None) == 8
+
+
+def test_pack_instances_layout_without_gpu():
+    # host logic of the batch binding: every instance starts on a 4-element boundary (16 bytes for
+    # float32, 8 for bfloat16, the chunk loads of the batched pass), rows are stored in order, and the
+    # bfloat16 buffer holds the rounded values
+    import numpy as np
+    import torch
+
+    from paper_2405_09157_gb300 import api
+    rng = np.random.default_rng(0)
+    arrays = [rng.standard_normal((n, d)).astype(np.float32) for n, d in [(3, 5), (7, 4), (2, 1), (5, 3)]]
+    for dt in (torch.float32, torch.bfloat16):
+        pts, offs, n, d = api.pack_instances(arrays, device="cpu", dtype=dt)
+        assert pts.dtype == dt and pts.dim() == 1
+        assert list(n) == [3, 7, 2, 5] and list(d) == [5, 4, 1, 3]
+        assert np.all(offs % 4 == 0) and np.all(np.diff(offs) >= (n * d)[:-1])
+        for k, a in enumerate(arrays):
+            got = pts[offs[k]:offs[k] + a.size].float().view(a.shape)
+            want = torch.from_numpy(a).to(dt).float()
+            assert torch.equal(got, want)
