@@ -22,7 +22,14 @@ REPORT_DTYPE = np.dtype([("value", "<f8"), ("lower_bound", "<f8"), ("upper_bound
 
 
 def _vp(t):
-    return None if t is None else ctypes.c_void_p(t.data_ptr())
+    """Device pointer of a CUDA tensor (None passes NULL). Every pointer this
+    binding hands to the library is dereferenced by a kernel, so a host tensor
+    is rejected here rather than read by the GPU."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"expected a CUDA tensor, got one on {t.device}")
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def _stream(stream=None):

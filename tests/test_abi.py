@@ -209,3 +209,16 @@ def test_pack_instances_layout_without_gpu():
             got = pts[offs[k]:offs[k] + a.size].float().view(a.shape)
             want = torch.from_numpy(a).to(dt).float()
             assert torch.equal(got, want)
+
+
+def test_binding_rejects_host_tensors_without_gpu():
+    # a host pointer never reaches a kernel: the binding refuses CPU tensors before the call
+    import pytest
+    import torch
+
+    from paper_2405_09157_gb300 import api
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        api._vp(torch.zeros(4))
+    assert api._vp(None) is None
+    with pytest.raises(ValueError, match="CUDA"):
+        api.bounds(api.SES, torch.zeros(8, 2))
