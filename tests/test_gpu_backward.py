@@ -96,7 +96,7 @@ def test_autograd_function_matches_the_sweep():
     torch.cuda.synchronize()
     assert torch.allclose(pts.grad, 3.0 * direct, rtol=1e-6, atol=1e-7)
     L, _, _ = ses_grad.ses_unrolled_radius_grad(V, None, alpha, eor, T)
-    assert abs(float(f) - L) <= RTOL * D
+    assert abs(float(f.detach()) - L) <= RTOL * D
 
 
 @pytest.mark.parametrize("n,d,T", [(100_000, 64, 2000), (200_000, 32, 300)])
@@ -178,7 +178,7 @@ def test_svm_autograd_function_matches_the_sweep():
     torch.cuda.synchronize()
     assert torch.allclose(pts.grad, 1.5 * direct, rtol=1e-6, atol=1e-7)
     L, _, _ = svm_grad.svm_unrolled_margin_grad(X, y, 0.2 * D, eor, D, T)
-    assert abs(float(f) - L) <= RTOL * D
+    assert abs(float(f.detach()) - L) <= RTOL * D
 
 
 def test_svm_full_size_rotation_identity():
