@@ -5,6 +5,7 @@ method runs in the library's CUDA kernels. Names follow include/pdscp.h.
 """
 
 import ctypes
+import functools
 
 import numpy as np
 import torch
@@ -51,12 +52,39 @@ def _points(pts):
     return pts.shape[0], pts.shape[1], dtype_code(pts)
 
 
+def _rows(t, n, dtype, name):
+    """Checks an optional per-row argument (radii, labels, per-instance or
+    per-candidate values): contiguous, of `dtype`, at least n entries."""
+    if t is not None and (t.dtype != dtype or not t.is_contiguous() or t.numel() < n):
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of at least {n} entries")
+
+
+def _bytes(t, nbytes, name):
+    """Checks an optional caller-owned buffer: contiguous and at least nbytes long."""
+    if t is not None and (not t.is_contiguous() or t.numel() * t.element_size() < nbytes):
+        raise ValueError(f"{name} must be a contiguous buffer of at least {nbytes} bytes")
+
+
+def _state(problem, d, state):
+    _bytes(state, state_size(problem, d), "state")
+
+
+def _records(out, k=1):
+    _bytes(out, k * STEP_BYTES, "out (step records)")
+
+
+def _per_row(problem, n, radii, labels):
+    _rows(radii, n, torch.float32, "radii")
+    _rows(labels, n, torch.int8, "labels")
+
+
 def workspace_size(problem, n, d):
     out = ctypes.c_size_t()
     check(load().pdscp_workspace_size(problem, n, d, ctypes.byref(out)), "pdscp_workspace_size")
     return out.value
 
 
+@functools.lru_cache(maxsize=None)
 def state_size(problem, d):
     out = ctypes.c_size_t()
     check(load().pdscp_state_size(problem, d, ctypes.byref(out)), "pdscp_state_size")
@@ -86,6 +114,7 @@ def decode_steps(buf):
 def bounds(problem, pts, radii=None, ws=None, stream=None):
     """D of Sec. 4.1 (SES) or Lemma 6 (SVM) as a (1,) float64 CUDA tensor."""
     n, d, dt = _points(pts)
+    _rows(radii, n, torch.float32, "radii")
     ws = workspace(problem, n, d, pts.device) if ws is None else ws
     out = torch.empty(1, dtype=torch.float64, device=pts.device)
     check(load().pdscp_bounds(problem, _vp(pts), dt, _vp(radii), n, d, _vp(ws), ws.numel(),
@@ -95,6 +124,7 @@ def bounds(problem, pts, radii=None, ws=None, stream=None):
 
 def state_init(problem, pts, state, ws, rules=_ffi.RULES_NONE, delta=1e-4, patience=10, stream=None):
     n, d, dt = _points(pts)
+    _state(problem, d, state)
     check(load().mwu_state_init(problem, _vp(pts), dt, n, d, rules, delta, patience, _vp(state),
                                 _vp(ws), ws.numel(), _stream(stream)), "mwu_state_init")
 
@@ -103,6 +133,9 @@ def mwu_step(problem, pts, alpha, eta_over_rho, state, ws, out=None, D=0.0, radi
              eval_only=False, stream=None):
     """One alpha-FTP iteration on the device (no host sync)."""
     n, d, dt = _points(pts)
+    _state(problem, d, state)
+    _per_row(problem, n, radii, labels)
+    _records(out)
     check(load().mwu_step(problem, _vp(pts), dt, _vp(radii), _vp(labels), n, d, float(alpha),
                           float(eta_over_rho), float(D), int(bool(eval_only)), _vp(state), _vp(ws),
                           ws.numel(), _stream(stream), _vp(out)), "mwu_step")
@@ -113,6 +146,9 @@ def mwu_run(problem, pts, alpha, eta_over_rho, k, state, ws, out=None, D=0.0, ra
     overlapping (no host sync); out: k records or None. Bit-identical to k
     mwu_step calls."""
     n, d, dt = _points(pts)
+    _state(problem, d, state)
+    _per_row(problem, n, radii, labels)
+    _records(out, int(k))
     check(load().mwu_run(problem, _vp(pts), dt, _vp(radii), _vp(labels), n, d, float(alpha), float(eta_over_rho),
                          float(D), int(k), _vp(state), _vp(ws), ws.numel(), _stream(stream), _vp(out)), "mwu_run")
 
@@ -123,6 +159,9 @@ def mwu_step_noalloc(problem, pts, alpha, eta_over_rho, state, out=None, D=0.0, 
     the library's built-in 2 MiB array (shared by all calls on a device, so
     calls must not overlap on the GPU)."""
     n, d, dt = _points(pts)
+    _state(problem, d, state)
+    _per_row(problem, n, radii, labels)
+    _records(out)
     check(load().mwu_step_noalloc(problem, _vp(pts), dt, _vp(radii), _vp(labels), n, d, float(alpha),
                                   float(eta_over_rho), float(D), int(bool(eval_only)), _vp(state),
                                   _stream(stream), _vp(out)), "mwu_step_noalloc")
@@ -131,6 +170,7 @@ def mwu_step_noalloc(problem, pts, alpha, eta_over_rho, state, out=None, D=0.0, 
 def state_read(problem, d, state, stream=None, device="cuda"):
     """(mean, best) float32 tensors of a state: SES (ubar, best centre); SVM
     ((wbar, s1bar, s2bar), best direction)."""
+    _state(problem, d, state)
     m = torch.empty(d + (2 if problem == SVM else 0), dtype=torch.float32, device=device)
     b = torch.empty(d, dtype=torch.float32, device=device)
     check(load().mwu_state_read(problem, d, _vp(state), _vp(m), _vp(b), _stream(stream)), "mwu_state_read")
@@ -141,7 +181,10 @@ def state_set(problem, pts, t, mean, state, ws, radii=None, labels=None, D=0.0, 
     """Resume from a checkpoint: t and the running mean (float64 CUDA tensor;
     SVM: wbar then s1bar, s2bar)."""
     n, d, dt = _points(pts)
+    _state(problem, d, state)
+    _per_row(problem, n, radii, labels)
     mean = mean.to(device=pts.device, dtype=torch.float64).contiguous()
+    _rows(mean, d + (2 if problem == SVM else 0), torch.float64, "mean")
     check(load().mwu_state_set(problem, _vp(pts), dt, _vp(radii), _vp(labels), n, d, int(t), _vp(mean),
                                float(D), _vp(state), _vp(ws), ws.numel(), _stream(stream)), "mwu_state_set")
 
@@ -157,6 +200,7 @@ class MultiMWU:
         n, d, dt = _points(pts)
         if dt != F32:
             raise TypeError("multi-candidate iterations take float32 points")
+        _rows(radii, n, torch.float32, "radii")
         lib = load()
         stride, size = ctypes.c_size_t(), ctypes.c_size_t()
         check(lib.ses_multi_state_stride(d, ctypes.byref(stride)), "ses_multi_state_stride")
@@ -175,6 +219,9 @@ class MultiMWU:
     def step(self, alpha, eta_over_rho, out=None, stream=None):
         """alpha, eta_over_rho: k float64 CUDA tensors; out: k records or None."""
         n = self.pts.shape[0]
+        _rows(alpha, self.k, torch.float64, "alpha")
+        _rows(eta_over_rho, self.k, torch.float64, "eta_over_rho")
+        _records(out, self.k)
         check(load().ses_multi_step(_vp(self.pts), _vp(self.radii), n, self.d, self.k, _vp(alpha),
                                     _vp(eta_over_rho), _vp(self.states), _vp(self.ws), self.ws.numel(),
                                     _stream(stream), _vp(out)), "ses_multi_step")
@@ -199,6 +246,8 @@ def mwu_backward(pts, alpha, eta_over_rho, T, radii=None, seed=None, ws=None, ou
     load; the gradient is float32 either way). seed: one-element
     float64 CUDA tensor or None (1). Returns (grad, ws)."""
     n, d, dt = _points(pts)
+    _per_row(problem, n, radii, labels)
+    _records(out)
     if ws is None:
         ws = torch.empty(backward_workspace_size(n, d, T, problem), dtype=torch.uint8, device=pts.device)
     grad = torch.empty((n, d), dtype=torch.float32, device=pts.device)
@@ -301,6 +350,8 @@ def exchange_rows(row, world, group=None):
 
 def shard_init(problem, first, d, state, ws, dtype=F32, rules=_ffi.RULES_NONE, delta=1e-4, patience=10,
                stream=None):
+    _state(problem, d, state)
+    _rows(first, d, torch.bfloat16 if dtype == BF16 else torch.float32, "first")
     check(load().mwu_shard_init(problem, _vp(first), dtype, d, rules, delta, patience, _vp(state), _vp(ws),
                                 ws.numel(), _stream(stream)), "mwu_shard_init")
 
@@ -310,6 +361,9 @@ def shard_partial(problem, pts, holds_first, alpha, eta_over_rho, state, ws, row
     """One pass over this shard; writes its column totals to `row` (float32
     CUDA tensor of 2 * shard_row_width floats)."""
     n, d, dt = _points(pts)
+    _state(problem, d, state)
+    _per_row(problem, n, radii, labels)
+    _rows(row, 2 * shard_row_width(problem, d), torch.float32, "row")
     check(load().mwu_shard_partial(problem, _vp(pts), dt, _vp(radii), _vp(labels), n, d, int(bool(holds_first)),
                                    float(alpha), float(eta_over_rho), float(D), int(bool(eval_only)), _vp(state),
                                    _vp(ws), ws.numel(), _stream(stream), _vp(row)), "mwu_shard_partial")
@@ -319,6 +373,11 @@ def shard_finish(problem, rows, d, alpha, eta_over_rho, state, first=None, first
                  eval_only=False, out=None, stream=None):
     """Reduces the shards' rows ((ranks, 2 * width) float32, rank order) and
     finishes the iteration on this replica of the state."""
+    _state(problem, d, state)
+    _rows(rows, rows.shape[0] * 2 * shard_row_width(problem, d), torch.float32, "rows")
+    _rows(first, d, torch.bfloat16 if dtype == BF16 else torch.float32, "first")
+    _rows(first_radius, 1, torch.float32, "first_radius")
+    _records(out)
     check(load().mwu_shard_finish(problem, _vp(rows), rows.shape[0], _vp(first), dtype, _vp(first_radius), d,
                                   float(alpha), float(eta_over_rho), float(D), int(bool(eval_only)), _vp(state),
                                   _stream(stream), _vp(out)), "mwu_shard_finish")
@@ -407,6 +466,7 @@ def ses_solve(pts, radii=None, eps=1e-3, mode="practical", max_iters=1_000_000, 
     enclosing ball ("value" = "upper_bound"), the best lower bound, the search
     range, iterations and status (5 = budget spent, with valid bounds)."""
     n, d, dt = _points(pts)
+    _rows(radii, n, torch.float32, "radii")
     ws = workspace(SES, n, d, pts.device) if ws is None else ws
     center = torch.empty(d, dtype=torch.float32, device=pts.device)
     opts = _options(eps, mode, max_iters, poll_every, max_steps, eta, delta, patience)
@@ -427,8 +487,9 @@ def svm_solve(X, labels, eps=1e-3, mode="practical", max_iters=1_000_000, poll_e
     iteration or averaged); "certified" ends when upper_bound <= (1 + eps)
     lower_bound."""
     n, d, dt = _points(X)
-    if labels.dtype != torch.int8 or not labels.is_cuda or labels.numel() != n:
+    if labels is None or labels.numel() != n:
         raise ValueError("labels must be an int8 CUDA tensor of n entries in {+1, -1}")
+    _rows(labels, n, torch.int8, "labels")
     ws = workspace(SVM, n, d, X.device) if ws is None else ws
     w = torch.empty(d, dtype=torch.float32, device=X.device)
     opts = _options(eps, mode, max_iters, poll_every, max_steps, eta, delta, patience)
@@ -485,6 +546,9 @@ class SesBatch:
 
     def step(self, alpha, eta_over_rho, out=None, stream=None):
         """alpha, eta_over_rho: float64 CUDA tensors of one value per instance."""
+        _rows(alpha, self.num, torch.float64, "alpha")
+        _rows(eta_over_rho, self.num, torch.float64, "eta_over_rho")
+        _records(out, self.num)
         check(load().ses_batch_step(self.num, _vp(self.pts), self.dt, _vp(alpha), _vp(eta_over_rho), _vp(self.ws),
                                     self.ws.numel(), _stream(stream), _vp(out)), "ses_batch_step")
 
