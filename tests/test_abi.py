@@ -222,3 +222,35 @@ def test_binding_rejects_host_tensors_without_gpu():
     assert api._vp(None) is None
     with pytest.raises(ValueError, match="CUDA"):
         api.bounds(api.SES, torch.zeros(8, 2))
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    # a C99 program (no C++) includes the header with every warning on, links the library and calls it
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "use.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "pdscp.h"\n'
+        "int main(void) {\n"
+        "  size_t b = 0;\n"
+        "  pdscp_status st = pdscp_state_size(PDSCP_SES, 32, &b);\n"
+        '  printf("%d %zu\\n", (int)st, b);\n'
+        "  st = mwu_step(7, NULL, PDSCP_F32, NULL, NULL, 10, 4, 1.0, 0.1, 0.0, 0, NULL, NULL, 0, NULL, NULL);\n"
+        '  printf("%d %s\\n", (int)st, pdscp_last_error());\n'
+        "  return 0;\n}\n")
+    libdir = os.path.dirname(build.LIB)
+    exe = tmp_path / "use"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.dirname(HEADER),
+                        str(src), "-L", libdir, "-lpdscp", f"-Wl,-rpath,{libdir}", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    first, second = out.stdout.splitlines()
+    size = ctypes.c_size_t()
+    assert lib.pdscp_state_size(_ffi.SES, 32, ctypes.byref(size)) == 0
+    assert first == f"0 {size.value}"
+    assert second.startswith("1 ") and "problem" in second
