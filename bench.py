@@ -105,6 +105,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+L2_NOTE = "flushed between timed steps (512 MB write, then 256 MB read) outside the events"
+
+
+def ses_params(V32):
+    """The benchmark iteration's parameters, computed the same way in both
+    arms from the float32 points: D = max_i ||v_1 - v_i|| (Sec. 4.1, points),
+    rho = 3D/sqrt2, alpha = D (an upper bound on OPT: the ORACLE never
+    separates) and the Theorem 2 step size of the first search step
+    (alpha_1 = 2D/3, eps_1 = 1/4). Returns (D, rho, alpha, eta, T1)."""
+    V = V32.astype(np.float64)
+    D = float(np.max(np.linalg.norm(V[1:] - V[0], axis=1)))
+    rho = 3.0 * D / math.sqrt(2.0)
+    eta, T1 = theorem_eta_ses(D, V.shape[0], 2.0 * D / 3.0, 0.25)
+    return D, rho, D, eta, T1
+
+
+def arm_config(alpha, eta, eor, T1, world):
+    """The benchmark configuration, identical in both arms: the SES workload at
+    alpha = D with the first search step's Theorem 2 step size, one replica
+    per rank."""
+    return {"workload": WORKLOAD, "n": N_POINTS, "d": DIM, "alpha": alpha, "eta": eta, "eta_over_rho": eor,
+            "theorem_T1": T1, "l2": L2_NOTE, "parallelism": "replicas" if world > 1 else "single"}
+
+
 # ------------------------------------------------------------- oracle timing
 def oracle_rate(V64, alpha, eta, rho, budget_s, max_steps=None):
     """Iterations per second of the FP64 oracle on the rows of V64, timed on
@@ -127,11 +151,9 @@ def run_reference(args):
         return
     from paper_2405_09157_gb300 import datagen
     from oracle import ses as oses
-    V = datagen.ses_gaussian(N_POINTS, DIM, SEED).astype(np.float64)
-    D = oses.ses_D(V)
-    rho = oses.ses_width(D)
-    alpha = 2.0 * D / 3.0
-    eta, _ = theorem_eta_ses(D, N_POINTS, alpha, 0.25)
+    V32 = datagen.ses_gaussian(N_POINTS, DIM, SEED)
+    D, rho, alpha, eta, T1 = ses_params(V32)  # the GPU arm's iteration
+    V = V32.astype(np.float64)
     # size each step's row sample so the whole K+W run stays within ~2 minutes
     probe_rows = 100_000
     r_probe, _, _ = oracle_rate(V[:probe_rows], alpha, eta, rho, 1.0, max_steps=3)
@@ -152,9 +174,12 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_POINTS, "d": DIM, "parallelism": "replicas"},
+        "data": "synthetic", "config": arm_config(alpha, eta, eta / rho, T1, args.gpus),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{rows} of {N_POINTS} rows per step, scaled by rows/n", "host": host_cpu()},
+                         "sample": (f"each step: one FP64 oracle iteration over the first {rows} of the {N_POINTS} "
+                                    f"rows (1 thread); iterations per second extrapolated to all rows by the "
+                                    f"factor rows/n = {rows / N_POINTS:.4g} (the iteration is linear in n)"),
+                         "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -210,11 +235,8 @@ def run_ours(args):
         V32 = datagen.ses_gaussian(n, d, SEED + rank)
         pts = torch.from_numpy(V32).to(dev).to(tdt)
         m = api.MWU(_ffi.SES, pts)
-        D = float(api.bounds(_ffi.SES, pts).item())
     if args.problem == "ses":
-        rho = 3.0 * D / math.sqrt(2.0)
-        eta, T1 = theorem_eta_ses(D, n, 2.0 * D / 3.0, 0.25)
-        alpha = D  # >= OPT: the ORACLE never separates
+        D, rho, alpha, eta, T1 = ses_params(V32)
         alg_bytes = n * d * ebytes
         label_D = 0.0
     else:
@@ -297,12 +319,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "strong" if shard else "weak",
         "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-        "config": {"workload": WORKLOAD if default_workload else
-                   f"{args.problem.upper()} n={n} d={d} {args.dtype} (non-default case)",
-                   "n": n, "d": d, "alpha": alpha, "eta": eta,
-                   "eta_over_rho": eor, "theorem_T1": T1,
-                   "l2": "flushed between timed steps (512 MB write, then 256 MB read) outside the events",
-                   "parallelism": ("rows" if shard else "replicas") if world > 1 else "single"},
+        "config": (arm_config(alpha, eta, eor, T1, world) if default_workload else
+                   {"workload": f"{args.problem.upper()} n={n} d={d} {args.dtype} (non-default case)",
+                    "n": n, "d": d, "alpha": alpha, "eta": eta, "eta_over_rho": eor, "theorem_T1": T1,
+                    "l2": L2_NOTE, "parallelism": ("rows" if shard else "replicas") if world > 1 else "single"}),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
@@ -439,7 +459,35 @@ def cpu_baseline(V32, alpha, eta, rho):
     rate, steps, el = oracle_rate(V64, alpha, eta, rho, budget_s=15.0)
     return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{steps} oracle iterations over all {V32.shape[0]} points ({el:.1f} s), FP64 numpy, 1 thread",
-            "host": host_cpu()}
+            "host": host_cpu(), "all_cores": oracle_all_cores()}
+
+
+def oracle_all_cores(budget_s=10.0):
+    """The same oracle iterations with numpy's thread pools opened to every
+    host core (the thread counts must be set before numpy loads, so this runs
+    in a child process). The oracle is numpy elementwise work and reductions,
+    which run on one thread whatever the setting; only its BLAS products can
+    use more. Returns the rate and the thread count offered."""
+    cores = os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS=str(cores), OPENBLAS_NUM_THREADS=str(cores),
+               MKL_NUM_THREADS=str(cores))
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-rate-child", str(budget_s)],
+                           env=env, capture_output=True, text=True, timeout=120 + 3 * budget_s)
+        v = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:  # reported, never fatal for the line
+        return {"error": f"{type(e).__name__}: {e}"[:200], "cores": cores}
+    return {"value": v["rate"], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{v['steps']} oracle iterations over all {N_POINTS} points ({v['seconds']:.1f} s), "
+                      f"numpy thread pools set to {cores} threads"}
+
+
+def oracle_rate_child(budget_s):
+    from paper_2405_09157_gb300 import datagen
+    V32 = datagen.ses_gaussian(N_POINTS, DIM, SEED)
+    D, rho, alpha, eta, _ = ses_params(V32)
+    rate, steps, el = oracle_rate(V32.astype(np.float64), alpha, eta, rho, budget_s=budget_s)
+    print(json.dumps({"rate": rate, "steps": steps, "seconds": el}))
 
 
 def _time_steps(m, alpha, eor, D, flush, K=50):
@@ -789,7 +837,11 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--shard", default="replicas", choices=["replicas", "rows"],
                     help="N > 1: independent replicas (default) or one instance with its rows split over the GPUs")
+    ap.add_argument("--oracle-rate-child", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_rate_child is not None:
+        oracle_rate_child(args.oracle_rate_child)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -163,7 +163,7 @@ pdscp_status pdscp_state_size(int32_t problem, int32_t d, size_t* bytes_host);
  *   SES: D = max_{i>=2} ||v_1 - v_i|| + gamma_1 + gamma_i  (OPT in [D/2, D])
  *   SVM: D = max_i ||x_i||                                  (s_1, s_2 <= D)
  * radii_dev (SES, may be NULL = all zero) holds n float radii.
- * Asynchronous. Requires n >= 2 (SES) or n >= 1 (SVM), 1 <= d <= PDSCP_MAX_D.
+ * Asynchronous. Requires n >= 2, 1 <= d <= PDSCP_MAX_D.
  */
 pdscp_status pdscp_bounds(int32_t problem, const void* pts_dev, int32_t dtype,
                           const float* radii_dev, int64_t n, int32_t d,
@@ -232,10 +232,13 @@ pdscp_status mwu_state_set(int32_t problem, const void* pts_dev, int32_t dtype,
  * ws_dev/ws_bytes: the per-CTA partial sums and completion counters live in a
  * 2 MiB array built into the library, which every GPU that loads the library
  * reserves until the process exits. Problems whose scratch does not fit
- * (roughly d > 384 for SES and d > 190 for SVM on a 152-SM GPU) are rejected
- * with PDSCP_ERR_WORKSPACE and a message; use mwu_step for them.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (d > 380 for SES and d > 192 for SVM on a 152-SM GPU) are rejected with
+ * PDSCP_ERR_WORKSPACE and a message; use mwu_step for them.
+ * Every call looks up the array's address on the current device
+ * (cudaGetSymbolAddress, host-side; nothing is cached, so a device reset
+ * leaves no stale address); the first call on a device may load the
+ * library's device code there, so make that first call before any stream
+ * capture.
  * Each call clears the counters on `stream` (cudaMemsetAsync) and allocates
  * nothing. All calls on a device share the one array: calls that overlap on
  * the GPU (different streams, or several threads) race and give wrong

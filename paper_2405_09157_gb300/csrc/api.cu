@@ -6,7 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
+#include <atomic>
 #include <string>
 
 #include "bounds_kernel.cuh"
@@ -167,15 +167,17 @@ pdscp_status report_error(pdscp_status s, const char* msg) {
 }
 
 int device_sm_count() {
-  static int cached[64] = {0};
+  // per-device cache, read and written by any host thread (relaxed atomics:
+  // every thread that fills an entry stores the same value)
+  static std::atomic<int> cached[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-  if (cached[dev] == 0) {
-    int v = 0;
+  int v = cached[dev].load(std::memory_order_relaxed);
+  if (v == 0) {
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
-    cached[dev] = v;
+    cached[dev].store(v, std::memory_order_relaxed);
   }
-  return cached[dev];
+  return v;
 }
 
 }  // namespace pdscp
@@ -326,25 +328,18 @@ namespace {
 constexpr size_t kStaticScratchBytes = 2u << 20;  // 2 MiB
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-std::mutex g_scratch_mu;
-void* g_scratch_addr[64] = {nullptr};
-
-// Device address of g_static_scratch on the current device. The name is
-// only a host-side stand-in for the array, so its address is looked up once
-// per device, with that device current, through cudaGetSymbolAddress.
+// Device address of g_static_scratch on the current device. In host code
+// the array's name is only a stand-in, so the address is looked up with the
+// device current through cudaGetSymbolAddress. The lookup is host-side work
+// (no device call once the library's device code is loaded on the device)
+// and is repeated on every call rather than cached: a cached address would
+// go stale after cudaDeviceReset or when the device's primary context is
+// destroyed and created again.
 pdscp_status static_scratch(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "mwu_step_noalloc: cudaGetDevice");
-  if (dev < 0 || dev >= 64) return fail(PDSCP_ERR_INVALID_ARG, "mwu_step_noalloc: device index %d unsupported", dev);
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || !p) return cuda_fail(e, "mwu_step_noalloc: cudaGetSymbolAddress");
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess || !p) return cuda_fail(e, "mwu_step_noalloc: cudaGetSymbolAddress");
+  *out = p;
   return PDSCP_OK;
 }
 

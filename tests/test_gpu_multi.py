@@ -1,7 +1,16 @@
 """Multi-candidate SES iteration (ses_multi_step) against the FP64 oracle:
 every candidate's trajectory is that of an independent alpha-FTP with its own
-alpha (tolerance as in test_gpu_parity.py), including candidates whose ORACLE
-separates (they stop and keep their state while the others continue)."""
+alpha (tolerance as in test_gpu_parity.py, 1e-5 relative to D), including
+candidates whose ORACLE separates (they stop and keep their state while the
+others continue), and single steps of every candidate from a checkpoint.
+
+Trajectories are compared at the flat tolerance only on well-conditioned
+candidates: each step carries FP32 rounding of about 6e-8 D, which the
+alpha-FTP's dynamics may amplify (measured on the oracle by moving ubar^2 by
+1e-7 D); every candidate here is asserted to amplify it at most AMP_MAX = 8
+times, so T * 6e-8 D * AMP_MAX <= 1e-5 D over the T = 20 steps."""
+
+import math
 
 import numpy as np
 import pytest
@@ -12,12 +21,17 @@ from paper_2405_09157_gb300 import api, datagen
 
 pytestmark = pytest.mark.gpu
 RTOL = 1e-5
+AMP_MAX = 8.0
 
 
-@pytest.mark.parametrize("n,d,k,radii", [(3001, 32, 2, False), (2000, 5, 4, False), (1500, 64, 8, False),
-                                         (999, 2, 8, True), (4000, 8, 4, True), (5003, 16, 1, False),
-                                         (2, 3, 2, False)])
-def test_candidates_follow_their_own_oracle_trajectories(n, d, k, radii):
+# base: the first candidate's alpha / D (candidate j runs base + 0.1 j); the
+# 999-point case starts at 0.42 because at 0.45 its seventh candidate
+# (alpha = 1.05 D with radii) amplifies rounding 91 times over 20 steps
+@pytest.mark.parametrize("n,d,k,radii,base", [(3001, 32, 2, False, 0.45), (2000, 5, 4, False, 0.45),
+                                              (1500, 64, 8, False, 0.45), (999, 2, 8, True, 0.42),
+                                              (4000, 8, 4, True, 0.45), (5003, 16, 1, False, 0.45),
+                                              (2, 3, 2, False, 0.45)])
+def test_candidates_follow_their_own_oracle_trajectories(n, d, k, radii, base):
     V32 = datagen.ses_gaussian(n, d, seed=n + k)
     g32 = (0.1 * np.random.default_rng(n).random(n)).astype(np.float32) if radii else None
     V = V32.astype(np.float64)
@@ -25,7 +39,10 @@ def test_candidates_follow_their_own_oracle_trajectories(n, d, k, radii):
     D = oses.ses_D(V, g)
     rho = oses.ses_width(D)
     eta, T = 1.0, 20
-    alphas = np.array([(0.45 + 0.1 * j) * D for j in range(k)])
+    alphas = np.array([(base + 0.1 * j) * D for j in range(k)])
+    amps = [_amplification(V, g, a, eta, rho, T) for a in alphas]
+    assert max(amps) <= AMP_MAX, amps  # only well-conditioned candidates are compared
+    tol = RTOL * D
     pts = torch.from_numpy(V32).cuda()
     rad = None if g32 is None else torch.from_numpy(g32).cuda()
     m = api.MultiMWU(pts, k, radii=rad)
@@ -37,13 +54,7 @@ def test_candidates_follow_their_own_oracle_trajectories(n, d, k, radii):
     torch.cuda.synchronize()
     recs = [api.decode_steps(o) for o in outs]
     for j in range(k):
-        # Every step carries FP32 rounding of about 6e-8 D, which the
-        # trajectory itself may amplify (measured here on the oracle by moving
-        # ubar^2 by 1e-7 D); the bound is the larger of the usual tolerance and
-        # T * 6e-8 D * amplification (equal to the usual one for all but the
-        # ill-conditioned candidates).
-        amp = _amplification(V, g, alphas[j], eta, rho, T)
-        tol = max(RTOL * D, T * 6e-8 * amp * D)
+        amp = amps[j]
         ubar, stopped_at = V[0].copy(), None
         for t in range(T):
             o = oses.ses_step(V, g, ubar, t, alphas[j], eta, rho)
@@ -130,3 +141,48 @@ def test_full_size_k8_against_oracle():
             for key in ("objective", "oracle_value", "lower_bound"):
                 assert abs(recs[t][j][key] - o[key]) <= tol, (j, t, key)
             ubar = o["ubar_next"]
+
+
+@pytest.mark.parametrize("n,d,k,radii", [(20000, 32, 8, False), (5000, 16, 4, True), (3001, 64, 2, False),
+                                         (1500, 3, 8, False)])
+def test_candidates_single_steps_from_checkpoints(n, d, k, radii):
+    """One multi-candidate pass from a checkpoint (t_j, ubar_j) set in every
+    candidate's state (mwu_state_set, as the single-step parity tests do for
+    mwu_step), at k D from 1 to 64 and alphas on both sides of OPT, against
+    the oracle's step from the same checkpoint at the flat 1e-5 D."""
+    V32 = datagen.ses_gaussian(n, d, seed=n + d + k)
+    g32 = (0.2 * np.random.default_rng(n).random(n)).astype(np.float32) if radii else None
+    V = V32.astype(np.float64)
+    g = None if g32 is None else g32.astype(np.float64)
+    D = oses.ses_D(V, g)
+    rho = oses.ses_width(D)
+    eta = 0.5
+    tol = RTOL * D
+    pts = torch.from_numpy(V32).cuda()
+    rad = None if g32 is None else torch.from_numpy(g32).cuda()
+    m = api.MultiMWU(pts, k, radii=rad)
+    ws = api.workspace(api.SES, n, d)
+    rng = np.random.default_rng(n + 1)
+    kDs = np.geomspace(1.0, 64.0, k)
+    alphas = np.linspace(0.5, 1.1, k) * D
+    ck = []
+    for j in range(k):
+        t = max(1, int(round(kDs[j] * rho / (eta * D))))
+        ubar = V.mean(axis=0) + 0.3 * D / math.sqrt(d) * rng.standard_normal(d)
+        api.state_set(api.SES, pts, t, torch.from_numpy(ubar), m.state(j), ws, radii=rad)
+        ck.append((t, ubar))
+    out = api.new_steps(k)
+    m.step(torch.tensor(alphas, dtype=torch.float64, device="cuda"),
+           torch.full((k,), eta / rho, dtype=torch.float64, device="cuda"), out=out)
+    recs = api.decode_steps(out)
+    for j, (t, ubar) in enumerate(ck):
+        o = oses.ses_step(V, g, ubar, t, alphas[j], eta, rho)
+        r = recs[j]
+        assert r["status"] == 0
+        for key in ("objective", "oracle_value", "lower_bound"):
+            assert abs(r[key] - o[key]) <= tol, (j, key, r[key], o[key])
+        if abs(o["oracle_value"]) > tol:
+            assert bool(r["failed"]) == o["failed"], j
+            assert r["t"] == (t if o["failed"] else t + 1)
+        mean, _ = m.read(j)
+        assert np.linalg.norm(mean.cpu().numpy().astype(np.float64) - o["ubar_next"]) <= tol, j

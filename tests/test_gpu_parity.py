@@ -1,7 +1,9 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
-Tolerance. The kernels compute per point in FP32 and finish each iteration
-in FP64. A per-point weight e^{x} carries a relative error of about
+Tolerance. The kernels compute per point in FP32, reduce the per-CTA
+partial sums in compensated FP32 (FP64-grade totals), run the O(d) finish of
+each iteration in FP32 from those totals and keep the running mean in FP64.
+A per-point weight e^{x} carries a relative error of about
 k D 2^-24 from its FP32 argument (k = eta t / rho, D the problem scale);
 with k D <= 64 (every case below) that is <= 4e-6, and the ORACLE value, f,
 the bounds and the next running mean, being weighted averages, inherit it.

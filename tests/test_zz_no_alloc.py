@@ -1,7 +1,12 @@
 """mwu_step_noalloc: the step for callers that cannot allocate device memory
-(the scratch is the library's built-in array) must give the same results as
-mwu_step with a caller workspace, on consecutive calls. This file is named so
-that pytest collects it last."""
+(code inside a host program that owns all GPU memory through its own pool, or
+that must avoid the implicit synchronisation an allocation can cause) takes
+its scratch from an array built into the library. It runs the same kernel with
+the same fixed-order reductions as mwu_step with a caller workspace, so on
+consecutive calls its records, running means and whole states must equal
+mwu_step's bit for bit (a tolerance would let a scratch-layout fault that
+shifts the results slightly pass). This file is named so that pytest collects
+it last."""
 
 import ctypes
 
@@ -12,7 +17,6 @@ import torch
 from paper_2405_09157_gb300 import _ffi, api, datagen
 
 pytestmark = pytest.mark.gpu
-RTOL = 1e-5  # the tolerance of the other GPU parity tests, relative to the problem scale D
 
 
 def _vp(t):
@@ -37,26 +41,29 @@ def _run_pair(problem, pts, alpha, eor, D=0.0, labels=None, steps=2):
     a, b = api.decode_steps(out_ref), api.decode_steps(out_na)
     mean_ref, _ = ref.read()
     mean_na, _ = api.state_read(problem, d, state)
+    assert torch.equal(ref.state.cpu(), state.cpu())  # header, FP64 and FP32 means, best point, dual vector
     return a, b, mean_ref.cpu().numpy(), mean_na.cpu().numpy()
+
+
+def _assert_identical(a, b, ma, mb):
+    for key in a.dtype.names:  # every field of every record, NaN-free by the status check
+        assert np.array_equal(a[key], b[key]), key
+    assert np.array_equal(ma, mb)
 
 
 def test_noalloc_step_matches_workspace_step_ses_and_svm():
     V = torch.from_numpy(datagen.ses_gaussian(4099, 32, seed=21)).cuda()
     D = float(api.bounds(_ffi.SES, V).item())
     a, b, ma, mb = _run_pair(_ffi.SES, V, 0.8 * D, 0.5 / (3 * D / np.sqrt(2)))
-    for key in ("oracle_value", "objective", "lower_bound", "upper_bound"):
-        assert np.all(np.abs(a[key] - b[key]) <= RTOL * D), key
-    assert np.array_equal(a["t"], b["t"]) and np.all(b["status"] == 0) and b["t"][-1] == 2
-    assert np.linalg.norm(ma - mb) <= RTOL * D
+    assert np.all(b["status"] == 0) and b["t"][-1] == 2
+    _assert_identical(a, b, ma, mb)
 
     X, y = datagen.svm_clusters(1500, 1200, 64, seed=22)
     X, y = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
     D = float(api.bounds(_ffi.SVM, X).item())
     a, b, ma, mb = _run_pair(_ffi.SVM, X, 0.3 * D, 0.5 / (2 * D), D=D, labels=y)
-    for key in ("oracle_value", "objective", "upper_bound"):
-        assert np.all(np.abs(a[key] - b[key]) <= RTOL * D), key
     assert np.all(b["status"] == 0) and b["t"][-1] == 2
-    assert np.linalg.norm(ma - mb) <= RTOL * D
+    _assert_identical(a, b, ma, mb)
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch():
