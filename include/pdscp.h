@@ -232,7 +232,7 @@ pdscp_status mwu_state_set(int32_t problem, const void* pts_dev, int32_t dtype,
  * ws_dev/ws_bytes: the per-CTA partial sums and completion counters live in a
  * 2 MiB array built into the library, which every GPU that loads the library
  * reserves until the process exits. Problems whose scratch does not fit
- * (d > 380 for SES and d > 192 for SVM on a 152-SM GPU) are rejected with
+ * (d > 380 for SES and d > 188 for SVM on a 152-SM GPU) are rejected with
  * PDSCP_ERR_WORKSPACE and a message; use mwu_step for them.
  * Every call looks up the array's address on the current device
  * (cudaGetSymbolAddress, host-side; nothing is cached, so a device reset

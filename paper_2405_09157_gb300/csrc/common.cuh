@@ -22,7 +22,13 @@ constexpr int kMaxBlocksPerSM = 8;    // upper bound used to size the workspace
 // two-level completion.
 constexpr size_t kStageBytesOneCta = 96 * 1024;
 constexpr size_t kStageBytesManyCta = 48 * 1024;
-constexpr size_t kHeadBytes = 1024;   // workspace: completion counters (top + per group)
+// Workspace head (zeroed by mwu_state_init and left zeroed by every pass):
+// [0, 1 KB) completion counters (top + per group) | [kFxFlagOff] overflow flag
+// of the fixed-point completion | [kFxOff, kHeadBytes) its column accumulators.
+constexpr size_t kHeadBytes = 16384;
+constexpr size_t kFxFlagOff = 1024;
+constexpr size_t kFxOff = 2048;
+constexpr int kFxMaxCols = (int)((kHeadBytes - kFxOff) / 16);  // two 64-bit words per column
 constexpr int kMaxGroups = 64;        // group rows reserved in the workspace
 
 // ---------------------------------------------------------------------------
@@ -405,6 +411,176 @@ __device__ bool arrive_pass(const float* rows, int stride, float2* grows, unsign
   }
   __syncthreads();
   return *s_flag;
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-point completion. Every CTA adds its partial row into per-column
+// 64-bit integer accumulators in the workspace head (atomics, while the other
+// CTAs still stream), so the finishing CTA reads one total per column instead
+// of reducing every CTA's row. Integer addition is associative: the totals do
+// not depend on the order in which CTAs arrive, and a run stays bit for bit
+// reproducible. A column sum uses a scale 2^e fixed before the pass from a
+// bound B on the column's absolute sum (identical in every CTA): a CTA's value
+// v becomes X = v 2^e (exact in FP64), split into hi = floor(X) (signed) and
+// lo = the next 32 bits of the fraction; with B 2^e < 2^51 the hi words of
+// up to 2048 CTAs cannot overflow, and the total is exact to 2^-(e+32). A
+// maximum (minimum) column takes an atomic maximum of an order-preserving
+// integer image of v (of -v). A value outside its bound (or NaN) sets the
+// overflow flag instead; the finishing CTA then reduces the CTAs' FP32 rows,
+// which every CTA also writes, as before.
+// ---------------------------------------------------------------------------
+constexpr int kFxMaxBanks = 1;  // copies of the accumulators (see fx_cols)
+struct FxCols {
+  // bank b, column pc: acc[2 (b stride + pc)] = sum of hi (two's complement), acc[2 (b stride + pc) + 1] = sum of lo
+  unsigned long long* acc;
+  unsigned int* bad;
+  int stride, banks;
+};
+// CTAs push into `banks` copies of the accumulators (CTA b into copy b mod
+// banks; the finishing CTA adds the copies), so that fewer CTAs contend for
+// one address: as many copies as the head holds, a power of two <= kFxMaxBanks.
+__device__ __forceinline__ FxCols fx_cols(unsigned int* counter, int stride) {
+  char* h = reinterpret_cast<char*>(counter);
+  const int room = (int)((kHeadBytes - kFxOff) / (16 * (size_t)stride));
+  int banks = 1;
+  while (2 * banks <= room && 2 * banks <= kFxMaxBanks) banks *= 2;
+  return FxCols{reinterpret_cast<unsigned long long*>(h + kFxOff), reinterpret_cast<unsigned int*>(h + kFxFlagOff),
+                stride, banks};
+}
+// Scale exponent for a column whose absolute sum is at most `bound`.
+__device__ __forceinline__ int fx_exp(double bound) {
+  return 50 - ilogb(fmax(bound, 1e-30));
+}
+// Adds this CTA's value v of column pc (op 0 sum with scale 2^e, 1 max, 2 min).
+// The split of X = v 2^e into hi and lo is integer work on the FP32 fields of
+// v (FP64 arithmetic is slow on this GPU and would sit on every CTA's arrival):
+// v = m 2^x with an integer m < 2^24, so |X| 2^32 = m 2^(x + e + 32) is a shift
+// of m, truncated at 2^-32 (deterministic; a sign is applied to the 96-bit
+// integer). rel: the column divides or is divided by, so a nonzero value must
+// keep 30 bits of relative precision (|X| >= 1/4); a smaller one, a value of
+// 2^52 or more, an Inf or a NaN sets the overflow flag instead.
+static __device__ __noinline__ void fx_push(FxCols f, int pc, int op, int e, float v, bool rel = false) {
+  unsigned long long* a = f.acc + 2 * ((blockIdx.x & (f.banks - 1)) * f.stride + pc);
+  if (op == 0) {
+    const unsigned int bits = __float_as_uint(v);
+    const int be = (int)((bits >> 23) & 0xffu);
+    if (be == 0xff) {  // Inf or NaN
+      atomicOr(f.bad, 1u);
+      return;
+    }
+    const unsigned long long m = be ? ((bits & 0x7fffffu) | 0x800000u) : (bits & 0x7fffffu);
+    if (m == 0ull) return;                         // +-0 adds nothing
+    const int sh = (be ? be - 150 : -149) + e;     // X = m 2^sh
+    const int top = sh + 64 - __clzll((long long)m);  // bit length of m 2^sh; |X| < 2^top
+    if (top > 52 || (rel && top < -1)) {
+      atomicOr(f.bad, 1u);
+      return;
+    }
+    unsigned long long hiw, low;  // |X| 2^32 = hiw 2^32 + low, low < 2^32
+    const int s = sh + 32;
+    if (s >= 32) {
+      hiw = m << (s - 32);
+      low = 0ull;
+    } else if (s >= 0) {
+      const unsigned long long w = m << s;  // < 2^56
+      hiw = w >> 32;
+      low = w & 0xffffffffull;
+    } else {
+      hiw = 0ull;
+      low = s > -64 ? (m >> (-s)) : 0ull;
+    }
+    if (bits >> 31) {  // negate the 96-bit integer: (-hiw - [low != 0]) 2^32 + (2^32 - low)
+      hiw = (unsigned long long)(-(long long)hiw) - (low != 0ull ? 1ull : 0ull);
+      low = low != 0ull ? 4294967296ull - low : 0ull;
+    }
+    atomicAdd(a, hiw);
+    if (low != 0ull) atomicAdd(a + 1, low);
+  } else {
+    const float u = op == 1 ? v : -v;
+    if (u != u) {
+      atomicOr(f.bad, 1u);
+      return;
+    }
+    unsigned int b = __float_as_uint(u);
+    b = (b & 0x80000000u) ? ~b : (b | 0x80000000u);  // larger float -> larger unsigned
+    atomicMax(a, (unsigned long long)b);
+  }
+}
+// Total of column pc as a compensated pair (s, c), s + c = total; resets the
+// column's accumulators for the next launch.
+__device__ __forceinline__ float2 fx_take(FxCols f, int pc, int op, int e) {
+  unsigned long long hb[kFxMaxBanks], lb[kFxMaxBanks];
+#pragma unroll
+  for (int b = 0; b < kFxMaxBanks; ++b) {  // every load first, then the sums
+    if (b < f.banks) {
+      unsigned long long* a = f.acc + 2 * (b * f.stride + pc);
+      hb[b] = __ldcg(a);
+      lb[b] = __ldcg(a + 1);
+    }
+  }
+  unsigned long long h = 0ull, l = 0ull;
+#pragma unroll
+  for (int b = 0; b < kFxMaxBanks; ++b) {
+    if (b < f.banks) {
+      unsigned long long* a = f.acc + 2 * (b * f.stride + pc);
+      a[0] = 0ull;
+      a[1] = 0ull;
+      if (op == 0) {
+        h += hb[b];  // two's complement: the wrapping sum is the signed sum
+        l += lb[b];
+      } else {
+        h = hb[b] > h ? hb[b] : h;
+      }
+    }
+  }
+  if (op == 0) {
+    const double T = ldexp((double)(long long)h + (double)l * (1.0 / 4294967296.0), -e);
+    const float s = (float)T;
+    return make_float2(s, (float)(T - (double)s));
+  }
+  if (h == 0ull) return col_init2(op);  // no CTA pushed a value
+  unsigned int b = (unsigned int)h;
+  b = (b & 0x80000000u) ? (b & 0x7fffffffu) : ~b;
+  const float u = __uint_as_float(b);
+  return make_float2(op == 1 ? u : -u, 0.f);
+}
+
+// Arrival of a CTA for the fixed-point completion (after its pushes and its
+// row): one device-scope fence and atomic per CTA, as arrive_pass. Returns
+// true in the finishing CTA.
+__device__ __forceinline__ bool fx_arrive(unsigned int* counters, bool* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int prev = atomicAdd(&counters[0], 1u);
+    __threadfence();
+    *s_flag = (prev == (unsigned int)(gridDim.x - 1));
+  }
+  __syncthreads();
+  return *s_flag;
+}
+
+// In the finishing CTA: the column totals into raw[0..stride) (pairs), every
+// accumulator and the counter reset. exp_of(pc) / opof(pc) give each column's
+// scale and operation. When a CTA set the overflow flag, the FP32 rows (rows x
+// stride) of all CTAs are reduced instead (compensated, fixed order). Ends
+// with a barrier.
+template <typename ExpOf, typename OpOf>
+__device__ void fx_finish(unsigned int* counters, const float* rows, int stride, float2* raw, float2* scratch,
+                          ExpOf exp_of, OpOf opof) {
+  const FxCols f = fx_cols(counters, stride);
+  const bool bad = __ldcg(f.bad) != 0u;
+  __syncthreads();  // every thread has read the flag before thread 0 clears it
+  for (int pc = threadIdx.x; pc < stride; pc += blockDim.x) {
+    const float2 v = fx_take(f, pc, opof(pc), exp_of(pc));
+    if (!bad) raw[pc] = v;
+  }
+  if (threadIdx.x == 0) {
+    counters[0] = 0u;
+    *f.bad = 0u;
+  }
+  __syncthreads();
+  if (bad) reduce_rows(rows, 0, (int)gridDim.x, stride, raw, scratch, opof);  // ends with a barrier
 }
 
 // Column totals of an (nb x stride) float matrix in shared memory, one warp

@@ -22,7 +22,14 @@ struct SesLauncher {
     size_t smem = pass_smem > fin_base ? pass_smem : fin_base;
     int grid = pass_grid(kern, smem, p.n, (32 / lpp) * points_per_lane_step * (block / 32), block);
     SesParams q = p;
+    // Rows that fit the staging area complete by one staged reduction in the
+    // last CTA; wider rows that fit the workspace head's accumulators complete
+    // through them (fixed point), the rest in two levels. Measured on GB300:
+    // the staged reduction beats the accumulators for SES rows at d = 32
+    // (35.5 against 37.5 us per iteration, n = 1e6), the accumulators beat
+    // the two-level reduction for SVM rows at d = 128 (95.6 against 102.7 us).
     q.single = single_level(grid, st, block >= 512 ? kStageBytesOneCta : kStageBytesManyCta) ? 1 : 0;
+    q.fx = (!q.single && st <= kFxMaxCols) ? 1 : 0;
     if (q.single) {
       const size_t fin = fin_base + (size_t)grid * st * sizeof(float);
       if (fin > smem) smem = fin;

@@ -50,7 +50,30 @@ struct SesParams {
   float2* row_out;       // non-null: a shard's pass; write the column totals here, no finish
   float* tape;           // non-null: the finish records entry t (ses_tape_stride floats) for a reverse sweep
   unsigned char* sink;   // non-null: one warp warms the finish's code path early, writing here (warm_sink_bytes)
+  int fx;                // completion through the fixed-point column accumulators (fx_push / fx_finish)
 };
+
+// Scale exponents of the fixed-point completion for the SES columns [S, Wt,
+// maxd, Cc, G'_1..G'_d], from bounds on their absolute sums over the n points
+// that hold for every pass (H = hint + move bounds dist_i + gamma_i; shifted
+// exponentials E1 <= 1): S = sum E1 (2 - em) <= 2n; |G'_j| <= sum c_i dist_i
+// <= sum (E1 - E2) <= n; c_i <= 2 (k/sqrt2) E1 gives Cc <= 2 (k/sqrt2) n;
+// |a_i (E1 + E2) - dist_i (E1 - E2)| <= 2 (|alpha| + H) + H. Each bound is
+// doubled for the FP32 rounding of the terms. A pass whose terms break a
+// bound (an evaluation pass over spheres with radii far above alpha, NaN or
+// Inf inputs) falls back to the row reduction (fx_finish).
+struct SesFxExp {
+  int eS, eW, eC, eG;
+  __device__ int operator()(int pc) const { return pc == 0 ? eS : (pc == 1 ? eW : (pc == 3 ? eC : eG)); }
+};
+__device__ __forceinline__ SesFxExp ses_fx_exp(int64_t n, float kr, float H, float alpha) {
+  const double nn = (double)n;
+  return SesFxExp{fx_exp(4.0 * nn), fx_exp(nn * (4.0 * fabs((double)alpha) + 6.0 * fabs((double)H) + 4.0)),
+                  fx_exp(4.0 * nn * (double)kr + 1.0), fx_exp(2.0 * nn + 1.0)};
+}
+__device__ __forceinline__ int ses_col_op(int pc) { return pc == 2 ? 1 : 0; }  // maxd is a max, the rest sums
+// S and Cc divide (g = G'/(sqrt2 S), mu_i = c_i/Cc): they need relative precision
+__device__ __forceinline__ bool ses_col_rel(int pc) { return pc == 0 || pc == 3; }
 
 // The finish runs once per launch, in one warp, after every other warp is
 // done; its instructions are then cold (a flushed or streamed-over L2 holds
@@ -65,7 +88,16 @@ __device__ void ses_finish_warm(const SesParams& p, unsigned char* smem_raw);
 
 
 template <typename T>
-__device__ void ses_finish(const SesParams& p, unsigned char* smem_raw);
+__device__ void ses_finish(const SesParams& p, unsigned char* smem_raw, const SesFxExp& fe);
+
+// This CTA's partial row: the FP32 row (always written: the fallback of the
+// fixed-point completion and the row-reduction paths read it) and, with
+// p.fx, its fixed-point pushes. Column pc's value v is written by one thread.
+__device__ __forceinline__ void ses_emit(const SesParams& p, float* prow, const SesFxExp& fe, int pc, float v) {
+  prow[pc] = v;
+  if (p.fx && !(pc == 3 && p.radii))
+    fx_push(fx_cols(p.counter, ses_partial_stride(p.d)), pc, ses_col_op(pc), fe(pc), v, ses_col_rel(pc));
+}
 
 // T: element type of the points; VW: elements per chunk; LPP: lanes per point
 // (power of two); NCH: chunks per lane; U: points in flight per lane group.
@@ -190,11 +222,12 @@ __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
     s_sc[warp][3] = Cs;
   }
   __syncthreads();
+  const SesFxExp fe = ses_fx_exp(p.n, kr, H, alpha);
   float* prow = p.partials + (size_t)blockIdx.x * ses_partial_stride(d);
   for (int j = threadIdx.x; j < d; j += kBlock) {
     float s = 0.f;
     for (int w = 0; w < kWarps; ++w) s += sG[w * dp + j];
-    prow[4 + j] = s;
+    ses_emit(p, prow, fe, 4 + j, s);
   }
   if (threadIdx.x == 0) {
     float s0 = 0.f, s1 = 0.f, s3 = 0.f, m = -INFINITY;
@@ -204,12 +237,12 @@ __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
       s3 += s_sc[w][3];
       m = fmaxf(m, s_sc[w][2]);
     }
-    prow[0] = s0;
-    prow[1] = s1;
-    prow[2] = m;
-    prow[3] = p.radii ? NAN : s3;  // the QP bound holds for points only
+    ses_emit(p, prow, fe, 0, s0);
+    ses_emit(p, prow, fe, 1, s1);
+    ses_emit(p, prow, fe, 2, m);
+    ses_emit(p, prow, fe, 3, p.radii ? NAN : s3);  // the QP bound holds for points only
   }
-  ses_finish<T>(p, smem_raw);
+  ses_finish<T>(p, smem_raw, fe);
 }
 
 // The O(d) finish of one SES iteration from the column totals: run by one
@@ -404,14 +437,16 @@ __device__ __noinline__ void ses_finish_warm(const SesParams& p, unsigned char* 
 // the rows and hands the totals to warp 0 (ses_finish_warp), or, for a shard
 // of a row-sharded iteration, writes them to row_out.
 template <typename T>
-__device__ void ses_finish(const SesParams& p, unsigned char* smem_raw) {
+__device__ void ses_finish(const SesParams& p, unsigned char* smem_raw, const SesFxExp& fe) {
   __shared__ float2 s_scr[kMaxBlock];
   __shared__ __align__(16) double s_hdr[sizeof(StateHdr) / 8];
   __shared__ bool s_flag;
   const int d = p.d;
   const int st = ses_partial_stride(d);
-  auto opof = [](int pc) { return pc == 2 ? 1 : 0; };  // maxd is a max, the rest sums
-  if (!arrive_pass(p.partials, st, p.grows, p.counter, s_scr, &s_flag, opof, p.single)) return;
+  auto opof = [](int pc) { return ses_col_op(pc); };
+  if (p.fx ? !fx_arrive(p.counter, &s_flag)
+           : !arrive_pass(p.partials, st, p.grows, p.counter, s_scr, &s_flag, opof, p.single))
+    return;
 
   StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
   double* mean = state_mean(p.state);
@@ -438,9 +473,15 @@ __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw) {
   }
   const float v0 = tid < d ? elem_to_float<T>(pts + tid) : 0.f;
   const float gam1 = p.radii ? __ldg(p.radii) : 0.f;
-  final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single, 2, -1, st);
+  if (p.fx) {
+    fx_finish(p.counter, p.partials, st, raw, s_scr, fe, opof);
+    if (p.radii && tid == 0) raw[3] = make_float2(NAN, 0.f);  // no QP bound for spheres (not pushed)
+  } else {
+    final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single, 2, -1, st);
+  }
   cp_async_wait_all();
   if (p.row_out) {  // a shard of a row-sharded iteration: hand the totals to the merge
+    __syncthreads();
     for (int pc = tid; pc < st; pc += blockDim.x) p.row_out[pc] = raw[pc];
     return;
   }
@@ -549,6 +590,10 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
   const float H = (float)(hdr->hint + hdr->move);
   const float alpha = (float)p.alpha;
   const float* mean32 = state_mean32(p.state, d);
+  // the completion's scale exponents, kept in shared memory across the
+  // streaming loop rather than in registers
+  __shared__ SesFxExp s_fe;
+  if (threadIdx.x == 0) s_fe = ses_fx_exp(p.n, kr, H, alpha);
 
   float ub[VW], G[VW];
 #pragma unroll
@@ -634,11 +679,12 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
     s_sc[warp][3] = Cs;
   }
   __syncthreads();
+  const SesFxExp fe = s_fe;
   float* prow = p.partials + (size_t)blockIdx.x * ses_partial_stride(d);
   for (int j = threadIdx.x; j < d; j += BLOCK) {
     float s = 0.f;
     for (int w = 0; w < NW; ++w) s += sG[w * dp + j];
-    prow[4 + j] = s;
+    ses_emit(p, prow, fe, 4 + j, s);
   }
   if (threadIdx.x == 0) {
     float s0 = 0.f, s1 = 0.f, s3 = 0.f, m = -INFINITY;
@@ -648,12 +694,12 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
       s3 += s_sc[w][3];
       m = fmaxf(m, s_sc[w][2]);
     }
-    prow[0] = s0;
-    prow[1] = s1;
-    prow[2] = m;
-    prow[3] = p.radii ? NAN : s3;  // the QP bound holds for points only
+    ses_emit(p, prow, fe, 0, s0);
+    ses_emit(p, prow, fe, 1, s1);
+    ses_emit(p, prow, fe, 2, m);
+    ses_emit(p, prow, fe, 3, p.radii ? NAN : s3);  // the QP bound holds for points only
   }
-  ses_finish<T>(p, smem_raw);
+  ses_finish<T>(p, smem_raw, fe);
 }
 
 }  // namespace pdscp

@@ -45,13 +45,36 @@ struct SvmParams {
   float2* row_out;       // non-null: a shard's pass; write the column totals here, no finish
   unsigned char* sink;   // non-null: warm-up warps run the finish's code early, writing here
   float* tape;           // non-null: the finish records entry t (svm_tape_stride floats) for a reverse sweep
+  int fx;                // completion through the fixed-point column accumulators (fx_push / fx_finish)
 };
+
+// Scale exponents of the fixed-point completion for the SVM columns [S_P, S_Q,
+// minP, maxQ, Z_P (dp), Z_Q (dp)]: every shifted exponential is <= 1, so
+// S_P, S_Q <= n and |Z_.j| <= n D (D the largest point norm); bounds doubled
+// for rounding. A pass that breaks them (a D below the true largest norm,
+// NaN or Inf inputs) falls back to the row reduction.
+struct SvmFxExp {
+  int eS, eZ;
+  __device__ int operator()(int pc) const { return pc < 2 ? eS : eZ; }
+};
+__device__ __forceinline__ SvmFxExp svm_fx_exp(int64_t n, double D) {
+  const double nn = (double)n;
+  return SvmFxExp{fx_exp(2.0 * nn), fx_exp(2.0 * nn * fabs(D) + 1.0)};
+}
+__device__ __forceinline__ int svm_col_op(int pc) { return pc == 2 ? 2 : (pc == 3 ? 1 : 0); }  // minP min, maxQ max
+// S_P and S_Q divide (Tr mu = S_P/S, the Claim 8 vector Z_P/S_P - Z_Q/S_Q): one
+// class's sum can be exponentially smaller than the bound, then the rows are reduced
+__device__ __forceinline__ bool svm_col_rel(int pc) { return pc < 2; }
+__device__ __forceinline__ void svm_emit(const SvmParams& p, float* prow, const SvmFxExp& fe, int pc, float v) {
+  prow[pc] = v;
+  if (p.fx) fx_push(fx_cols(p.counter, svm_partial_stride(p.d)), pc, svm_col_op(pc), fe(pc), v, svm_col_rel(pc));
+}
 
 // Warm-up of the finish's code path in every CTA (see ses_finish_warm).
 static __device__ __noinline__ void svm_finish_warm(const SvmParams& p, unsigned char* smem_raw);
 
 template <typename T>
-__device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw);
+__device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw, const SvmFxExp& fe);
 
 template <typename T, int VW, int LPP, int NCH, int U>
 __global__ void __launch_bounds__(kBlock) svm_iter_kernel(SvmParams p) {
@@ -176,6 +199,7 @@ __global__ void __launch_bounds__(kBlock) svm_iter_kernel(SvmParams p) {
     s_sc[warp][3] = maxQ;
   }
   __syncthreads();
+  const SvmFxExp fe = svm_fx_exp(p.n, p.D);
   float* prow = p.partials + (size_t)blockIdx.x * svm_partial_stride(d);
   for (int j = threadIdx.x; j < d; j += kBlock) {
     float a = 0.f, b = 0.f;
@@ -183,8 +207,8 @@ __global__ void __launch_bounds__(kBlock) svm_iter_kernel(SvmParams p) {
       a += sZ[w * 2 * dp + j];
       b += sZ[w * 2 * dp + dp + j];
     }
-    prow[4 + j] = a;
-    prow[4 + dp + j] = b;
+    svm_emit(p, prow, fe, 4 + j, a);
+    svm_emit(p, prow, fe, 4 + dp + j, b);
   }
   if (threadIdx.x == 0) {
     float a = 0.f, b = 0.f, mn = INFINITY, mx = -INFINITY;
@@ -194,12 +218,12 @@ __global__ void __launch_bounds__(kBlock) svm_iter_kernel(SvmParams p) {
       mn = fminf(mn, s_sc[w][2]);
       mx = fmaxf(mx, s_sc[w][3]);
     }
-    prow[0] = a;
-    prow[1] = b;
-    prow[2] = mn;
-    prow[3] = mx;
+    svm_emit(p, prow, fe, 0, a);
+    svm_emit(p, prow, fe, 1, b);
+    svm_emit(p, prow, fe, 2, mn);
+    svm_emit(p, prow, fe, 3, mx);
   }
-  svm_finish<T>(p, smem_raw);
+  svm_finish<T>(p, smem_raw, fe);
 }
 
 // The O(d) finish of one SVM iteration from the column totals: run by one
@@ -392,15 +416,17 @@ static __device__ __noinline__ void svm_finish_warm(const SvmParams& p, unsigned
 // partial row [S_P, S_Q, minP, maxQ, Z_P (dp), Z_Q (dp)]; the completion
 // elects one CTA, which reduces the rows and hands the totals to warp 0.
 template <typename T>
-__device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
+__device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw, const SvmFxExp& fe) {
   __shared__ float2 s_scr[kMaxBlock];
   __shared__ __align__(16) double s_hdr[sizeof(StateHdr) / 8];
   __shared__ bool s_flag;
   const int d = p.d;
   const int dp = dpad4(d);
   const int st = svm_partial_stride(d);
-  auto opof = [](int pc) { return pc == 2 ? 2 : (pc == 3 ? 1 : 0); };  // minP min, maxQ max
-  if (!arrive_pass(p.partials, st, p.grows, p.counter, s_scr, &s_flag, opof, p.single)) return;
+  auto opof = [](int pc) { return svm_col_op(pc); };
+  if (p.fx ? !fx_arrive(p.counter, &s_flag)
+           : !arrive_pass(p.partials, st, p.grows, p.counter, s_scr, &s_flag, opof, p.single))
+    return;
 
   StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
   double* mean = state_mean(p.state);
@@ -419,7 +445,10 @@ __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw) {
     cp_async8(s_mean + j, mean + j);
     cp_async8(s_dual + j, dual + j);
   }
-  final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single, 3, 2, st);
+  if (p.fx)
+    fx_finish(p.counter, p.partials, st, raw, s_scr, fe, opof);
+  else
+    final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single, 3, 2, st);
   cp_async_wait_all();
   if (p.row_out) {  // a shard of a row-sharded iteration: hand the totals to the merge
     for (int pc = tid; pc < st; pc += blockDim.x) p.row_out[pc] = raw[pc];
@@ -586,6 +615,7 @@ __global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
     s_sc[warp][3] = maxQ;
   }
   __syncthreads();
+  const SvmFxExp fe = svm_fx_exp(p.n, p.D);
   float* prow = p.partials + (size_t)blockIdx.x * svm_partial_stride(d);
   for (int j = threadIdx.x; j < d; j += BLOCK) {
     float a = 0.f, b = 0.f;
@@ -593,8 +623,8 @@ __global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
       a += sZ[w * 2 * dp + j];
       b += sZ[w * 2 * dp + dp + j];
     }
-    prow[4 + j] = a;
-    prow[4 + dp + j] = b;
+    svm_emit(p, prow, fe, 4 + j, a);
+    svm_emit(p, prow, fe, 4 + dp + j, b);
   }
   if (threadIdx.x == 0) {
     float a = 0.f, b = 0.f, mn = INFINITY, mx = -INFINITY;
@@ -604,12 +634,12 @@ __global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
       mn = fminf(mn, s_sc[w][2]);
       mx = fmaxf(mx, s_sc[w][3]);
     }
-    prow[0] = a;
-    prow[1] = b;
-    prow[2] = mn;
-    prow[3] = mx;
+    svm_emit(p, prow, fe, 0, a);
+    svm_emit(p, prow, fe, 1, b);
+    svm_emit(p, prow, fe, 2, mn);
+    svm_emit(p, prow, fe, 3, mx);
   }
-  svm_finish<T>(p, smem_raw);
+  svm_finish<T>(p, smem_raw, fe);
 }
 
 }  // namespace pdscp

@@ -186,8 +186,12 @@ def test_ses_single_steps_large_grids(n, d, dtype):
     forced_ses(n, d, seed=d, kDs=[10.0, 64.0], dtype=dtype)
 
 
-@pytest.mark.parametrize("d,dtype", [(64, torch.float32), (32, torch.bfloat16)])
+@pytest.mark.parametrize("d,dtype", [(64, torch.float32), (32, torch.bfloat16), (128, torch.float32),
+                                     (128, torch.bfloat16)])
 def test_svm_single_steps_large_grids(d, dtype):
+    # d = 128: rows too wide to stage complete through the fixed-point column
+    # accumulators; at k D = 64 from a random direction one class's weight sum
+    # falls far below its bound and the completion falls back to the rows
     forced_svm(50_000, 50_000, d, seed=d, kDs=[10.0, 64.0], dtype=dtype)
 
 
@@ -238,6 +242,25 @@ def test_ses_duplicates_and_two_points():
     gr, gmean = gpu_ses_traj(two, None, 1.01, 1.0 / oses.ses_width(2.0), 50)
     assert np.allclose(gmean, [49 / 50 * 1.01, 0, 0], atol=1e-6)
     assert np.all(gr["failed"] == 0) and gr["t"][-1] == 50
+
+
+def test_ses_completion_fallback_on_large_radii():
+    """The fixed-point column totals assume |Wt| <= 2 n (2 |alpha| + 3 H + 2)
+    with H bounding dist_i + gamma_i; at t = 0 (H = 0) over spheres whose
+    radii far exceed alpha, Wt = sum 2 (alpha - gamma_i) breaks that bound and
+    the finishing CTA falls back to reducing the CTAs' FP32 rows. The steps
+    must still match the oracle (the first one through the fallback)."""
+    rng = np.random.default_rng(41)
+    V32 = (10.0 * rng.standard_normal((5000, 4))).astype(np.float32)
+    g32 = rng.uniform(0.0, 40.0, 5000).astype(np.float32)
+    V, g = V32.astype(np.float64), g32.astype(np.float64)
+    D = oses.ses_D(V, g)
+    rho = oses.ses_width(D)
+    alpha = 0.02 * D
+    assert 2.0 * np.sum(g[1:] - alpha) > 2.0 * 5000 * (2.0 * alpha + 2.0)  # beyond the bound at t = 0
+    gr, gmean = gpu_ses_traj(V32, g32, alpha, 0.5 / rho, 5)
+    orr, omean = oracle_ses_traj(V, g, alpha, 0.5, rho, 5)
+    compare_ses(gr, orr, gmean, omean, D)
 
 
 def test_ses_full_size_trajectory():
