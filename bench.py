@@ -1,16 +1,20 @@
 """Benchmark of the MWU hot path on one GB300 (or N replicas under torchrun).
 
-A step is one MWU iteration of the alpha-FTP (one mwu_step launch: the SOC
-exponential of every cone, the trace normaliser, the weighted n x d reduction,
-the closed-form ORACLE and the running-mean update) over the SES workload
-n = 1,000,000 points i.i.d. N(0, I_32), float32, seed 0, at alpha = D (an
-upper bound on OPT, so the ORACLE never separates and every step does the
-full work) with the step size Theorem 2 gives the first search step. The
-input (128 MB) is smaller than L2, so L2 is flushed between timed steps by
-writing a 512 MB buffer and then reading 256 MB of it (the lines left in L2
-are clean, so the timed step pays for no write-back of the flush); each step
-is timed with CUDA events on the launching stream and the flush is outside the
-events.
+A step is one MWU iteration of the alpha-FTP (one launch of the iteration
+kernel: the SOC exponential of every cone, the trace normaliser, the weighted
+n x d reduction, the closed-form ORACLE and the running-mean update) over the
+SES workload n = 1,000,000 points i.i.d. N(0, I_32), float32, seed 0, at
+alpha = D (an upper bound on OPT, so the ORACLE never separates and every step
+does the full work) with the step size Theorem 2 gives the first search step.
+
+The steps run as a solve runs them: launched back to back (mwu_run, one
+iteration per call, consecutive launches overlapping by programmatic dependent
+launch), the K timed steps bracketed by one pair of CUDA events. The input
+(128 MB) is smaller than L2, so the steps rotate over 4 copies of the point
+set (512 MB): between two uses of a copy 384 MB of other points stream through
+the 126 MB L2, and no step finds its points there. The same iteration launched
+alone after an L2 flush, each launch between its own events, is reported
+beside it (variants.ses_single_launch_l2_flushed).
 
 Prints one JSON line. `--impl reference` times the FP64 oracle (the CPU
 reference of this method) on the host cores instead.
@@ -105,7 +109,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-L2_NOTE = "flushed between timed steps (512 MB write, then 256 MB read) outside the events"
+L2_FLUSH_NOTE = "flushed between timed steps (512 MB write, then 256 MB read) outside the events"
+L2_NOTE = ("inputs larger than L2: 4 copies of the 128 MB point set (512 MB) used in rotation, so no step finds "
+           "its points in L2; the K steps are launched back to back (dependent-launch overlap, as the solves run "
+           "them) and timed together with CUDA events")
+
+
+def rotation_note(R, nbytes):
+    return (f"inputs larger than L2: {R} copies of the {nbytes / 1e6:.0f} MB point set ({R * nbytes / 1e6:.0f} MB) "
+            "used in rotation, so no step finds its points in L2; the K steps are launched back to back "
+            "(dependent-launch overlap, as the solves run them) and timed together with CUDA events")
 
 
 def ses_params(V32):
@@ -258,37 +271,60 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     out = api.new_steps(1, dev)
 
-    def step():
-        if shard:
+    if shard:
+        # one instance over the ranks: each step is a pass, an all-gather and a
+        # finish, timed alone after an L2 flush
+        def step(i):
+            flush()
+            starts[i].record(stream)
             m.step(alpha, eor, out=out[0])
-        else:
-            m.step(alpha, eor, out=out[0], D=label_D)
+            ends[i].record(stream)
+        l2_note = L2_FLUSH_NOTE
+    else:
+        # R copies of the points, used in rotation: between two uses of a copy
+        # at least 3 L2 sizes of other points stream through L2, so no step
+        # finds its points there; the steps are launched back to back with the
+        # dependent-launch overlap of the solves (mwu_run, one iteration each)
+        R = max(2, math.ceil(4 * l2 / (n * d * ebytes)))
+        copies = [m.pts] + [m.pts.clone() for _ in range(R - 1)]
+        lab = m.labels
+
+        def step(i):
+            api.mwu_run(m.problem, copies[i % R], alpha, eor, 1, m.state, m.ws, out=out[0], D=label_D,
+                        labels=lab)
+        l2_note = rotation_note(R, n * d * ebytes)
 
     clocks = ClockSampler(local)
     clocks.start()
-    for _ in range(args.warmup):
-        flush()
-        step()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for i in range(args.warmup):
+        if shard:
+            step(i % args.steps)
+        else:
+            step(i)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     w0 = time.perf_counter()
-    for i in range(args.steps):
-        flush()
-        starts[i].record(stream)
-        step()
-        ends[i].record(stream)
+    if shard:
+        for i in range(args.steps):
+            step(i)
+    else:
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(args.steps):
+            step(args.warmup + i)
+        t1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     wall = time.perf_counter() - w0
     clk = clocks.stop()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms_per_step, value = aggregate_timing(sum(step_ms), args.steps, world, dev)
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) if shard else t0.elapsed_time(t1)
+    ms_per_step, value = aggregate_timing(total_ms, args.steps, world, dev)
     if shard:  # one instance over all ranks: its iterations per second, not the ranks' sum
         value = 1e3 / ms_per_step
     rec = api.decode_steps(out)[0]
@@ -322,12 +358,12 @@ def run_ours(args):
         "config": (arm_config(alpha, eta, eor, T1, world) if default_workload else
                    {"workload": f"{args.problem.upper()} n={n} d={d} {args.dtype} (non-default case)",
                     "n": n, "d": d, "alpha": alpha, "eta": eta, "eta_over_rho": eor, "theorem_T1": T1,
-                    "l2": L2_NOTE, "parallelism": ("rows" if shard else "replicas") if world > 1 else "single"}),
+                    "l2": l2_note, "parallelism": ("rows" if shard else "replicas") if world > 1 else "single"}),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
                      "alg_bytes_per_launch": alg_bytes},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (2 if shard else 1),
         "clocks": clk,
         "wall_ms_per_step_incl_flush": 1e3 * wall / args.steps,
         "last_step": {"t": int(rec["t"]), "oracle_value": float(rec["oracle_value"]),
@@ -337,6 +373,7 @@ def run_ours(args):
         result["e2e"] = e2e_host(args, V32, alpha, eor, dev)
         result["cpu_baseline"] = cpu_baseline(V32, alpha, eta, rho)
         result["variants"] = variants(dev, flush)
+        result["variants"]["ses_single_launch_l2_flushed"] = single_launch_variant(m, alpha, eor, flush, alg_bytes)
         result["variants"]["batched_ses_4096"] = batched_variant(dev)
         result["variants"]["ses_backward_n1e5_d64_T2000"] = backward_variant(dev)
         result["variants"]["ses_multi_candidate_n1e6_d32"] = multi_variant(dev, flush)
@@ -348,6 +385,16 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(result))
+
+
+def single_launch_variant(m, alpha, eor, flush, alg_bytes, K=300):
+    """The same iteration as one mwu_step launch timed alone (CUDA events
+    around it) after an L2 flush: the launch and event overhead of a lone
+    kernel (about 5 us on this GPU for an empty one) is inside this figure."""
+    ms = _time_steps(m, alpha, eor, 0.0, flush, K=K)
+    peak, _ = peaks()
+    return {"ms_per_step": ms, "iters_per_s": 1e3 / ms, "frac_hbm": alg_bytes / (ms * 1e-3) / 1e9 / peak,
+            "timing": "one mwu_step per step, L2 flushed before it, CUDA events around the launch", "steps": K}
 
 
 class L2Flush:

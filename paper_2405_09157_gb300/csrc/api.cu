@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <atomic>
 #include <string>
@@ -164,6 +165,14 @@ pdscp_status do_step(int problem, const void* pts, int dtype, const float* radii
 pdscp_status report_error(pdscp_status s, const char* msg) {
   g_err = msg;
   return s;
+}
+
+unsigned int wait_limit() {
+  const char* v = getenv("PDSCP_WAIT_LIMIT");
+  if (!v || !*v) return kWaitLimit;
+  char* end = nullptr;
+  const unsigned long x = strtoul(v, &end, 10);
+  return (end && *end == '\0' && x <= 0xffffffffUL) ? (unsigned int)x : kWaitLimit;
 }
 
 int device_sm_count() {

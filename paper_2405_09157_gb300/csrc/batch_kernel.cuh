@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(kBatchBlock, 3) ses_batch_kernel(BatchParams p
     const double alpha_d = sr ? sr->alpha : p.alpha[tl.inst];
     const double eor_d = sr ? sr->eta_over_rho : p.eta_over_rho[tl.inst];
     {
-      const float kr = eval ? 0.f : (float)((double)hdr->t * eor_d / kSqrt2);
+      const float kr = eval ? 0.f : ses_kr(hdr->t, eor_d);
       const float H = (float)(hdr->hint + hdr->move);
       const float alpha = (float)alpha_d;
       const float* mean32 = state_mean32(state, d);

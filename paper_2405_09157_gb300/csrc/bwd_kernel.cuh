@@ -126,7 +126,7 @@ template <typename T, int VW, int LPP, int NCH, int U>
 __global__ void __launch_bounds__(kBlock) ses_bwd_step_kernel(BwdParams p) {
   pdl_trigger();
   pdl_wait();  // Gbar, Sbar and the gradient rows are the previous reverse step's output
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ float2 s_scr[kMaxBlock];
   __shared__ bool s_flag;
   const StateHdr* hdr = reinterpret_cast<const StateHdr*>(p.state);
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kBlock) ses_bwd_step_kernel(BwdParams p) {
 template <typename T, int VW, int LPP, int NI>
 __global__ void __launch_bounds__(kBlock) ses_bwd_step_t_kernel(BwdParams p) {
   using GS = GroupScatter<LPP, NI>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ float2 s_scr[kMaxBlock];
   __shared__ bool s_flag;
   pdl_trigger();
@@ -624,7 +624,7 @@ template <typename T, int VW, int LPP, int NCH, int U>
 __global__ void __launch_bounds__(kBlock) svm_bwd_step_kernel(BwdParams p) {
   pdl_trigger();
   pdl_wait();  // the adjoint scratch and the gradient rows are the previous reverse step's output
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ float2 s_scr[kMaxBlock];
   __shared__ bool s_flag;
   const StateHdr* hdr = reinterpret_cast<const StateHdr*>(p.state);
@@ -766,7 +766,7 @@ __global__ void __launch_bounds__(kBlock) svm_bwd_step_t_kernel(BwdParams p) {
   pdl_trigger();
   pdl_wait();  // the adjoint scratch and the gradient rows are the previous reverse step's output
   using GS = GroupScatter<LPP, NI>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ float2 s_scr[kMaxBlock];
   __shared__ bool s_flag;
   const StateHdr* hdr = reinterpret_cast<const StateHdr*>(p.state);

@@ -63,6 +63,15 @@ static_assert(sizeof(StateHdr) == 128, "state header must be 128 bytes");
 
 __host__ __device__ inline int dpad4(int d) { return (d + 3) & ~3; }
 
+// k / sqrt2 = eta t / (rho sqrt2) of an SES pass, in FP32 (the pass kernels,
+// the tape of the reverse sweep and the multi-candidate and batched passes use
+// this one expression). Multiplies by 1/sqrt2 rather than dividing by sqrt2:
+// FP64 division takes hundreds of cycles on this GPU, on every CTA's start.
+constexpr double kRsqrt2 = 0.70710678118654752440;
+__host__ __device__ inline float ses_kr(int64_t t, double eta_over_rho) {
+  return (float)((double)t * eta_over_rho * kRsqrt2);
+}
+
 #ifdef __CUDACC__
 // 8-byte global -> shared copy that holds no register while in flight (both
 // addresses 8-byte aligned); completed by cp_async_wait_all() of the same thread.
@@ -72,6 +81,67 @@ __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
                : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// ---------------------------------------------------------------------------
+// One-dimensional bulk copies (TMA, cp.async.bulk) global -> shared, completed
+// on an mbarrier. Used by the staged pass kernels: each warp keeps a ring of
+// slots in shared memory and copies its next rounds of points into it while it
+// computes the current one. Addresses and sizes must be multiples of 16 bytes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned int smem_u32(const void* p) {
+  return (unsigned int)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// Makes initialised mbarriers visible to the async proxy (the bulk copies).
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// Orders this thread's earlier shared-memory accesses before later bulk copies
+// into the same memory (a slot is refilled only after its data was read).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// Copies `bytes` from global `src` to shared `dst`; the copy's completion
+// flips the phase of `bar`, which expects exactly these bytes (one arrival).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned int bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// Waits for the phase with parity `parity` of `bar` to complete, trying at
+// most `limit` times (each try may suspend the thread for a short,
+// hardware-chosen time). Returns false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned int parity, unsigned int limit) {
+  for (unsigned int it = 0; it < limit; ++it) {
+    unsigned int done;
+    asm volatile(
+        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Default try limit of the staged kernels' waits (each try may suspend the
+// thread for a hardware-chosen time; a copy of 4 KB completes within a few
+// microseconds, so only a copy that never completes reaches the limit).
+constexpr unsigned int kWaitLimit = 1u << 20;
+// Workspace head word in which a staged pass records a wait that gave up
+// (read and cleared by the finishing CTA, which then reports PDSCP_ERR_TIMEOUT).
+constexpr size_t kTimeoutFlagOff = kFxFlagOff + 4;
+
+// Device-scope acquire-release fence: the release half orders this CTA's
+// earlier writes (made visible to this thread by the CTA barrier before it)
+// before a following completion atomic, the acquire half orders the atomic
+// before later reads of the other CTAs' writes. It is the weaker form of
+// __threadfence(), which is sequentially consistent and costs more.
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;\n" ::: "memory"); }
 // Programmatic dependent launch: a pass kernel lets the next launch in the
 // stream start early (pdl_trigger) and, in that next launch, waits for the
 // previous grid's completion and memory (pdl_wait) before it reads anything
@@ -339,9 +409,9 @@ __device__ bool arrive_two_level(const float* rows, int stride, float2* grows, u
   // cumulative over the writes the barrier ordered before it.
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
+    fence_acq_rel_gpu();
     const unsigned int prev = atomicAdd(&counters[1 + g], 1u);
-    __threadfence();
+    fence_acq_rel_gpu();
     *s_flag = (prev == (unsigned int)(r1 - r0 - 1));
   }
   __syncthreads();
@@ -350,9 +420,9 @@ __device__ bool arrive_two_level(const float* rows, int stride, float2* grows, u
   const int G = (nb + gs - 1) / gs;
   if (threadIdx.x == 0) {
     counters[1 + g] = 0u;
-    __threadfence();
+    fence_acq_rel_gpu();
     const unsigned int prev = atomicAdd(&counters[0], 1u);
-    __threadfence();
+    fence_acq_rel_gpu();
     *s_flag = (prev == (unsigned int)(G - 1));
   }
   __syncthreads();
@@ -404,9 +474,9 @@ __device__ bool arrive_pass(const float* rows, int stride, float2* grows, unsign
   if (!single) return arrive_two_level(rows, stride, grows, counters, scratch, s_flag, opof);
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
+    fence_acq_rel_gpu();
     const unsigned int prev = atomicAdd(&counters[0], 1u);
-    __threadfence();
+    fence_acq_rel_gpu();
     *s_flag = (prev == (unsigned int)(gridDim.x - 1));
   }
   __syncthreads();
@@ -551,9 +621,9 @@ __device__ __forceinline__ float2 fx_take(FxCols f, int pc, int op, int e) {
 __device__ __forceinline__ bool fx_arrive(unsigned int* counters, bool* s_flag) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
+    fence_acq_rel_gpu();
     const unsigned int prev = atomicAdd(&counters[0], 1u);
-    __threadfence();
+    fence_acq_rel_gpu();
     *s_flag = (prev == (unsigned int)(gridDim.x - 1));
   }
   __syncthreads();
@@ -590,7 +660,9 @@ __device__ void fx_finish(unsigned int* counters, const float* rows, int stride,
 // (every lane ends with the same pair, so the result is deterministic). No
 // barrier inside. (Warming this code too, as the finish's, was measured: the
 // extra call from the warm-up path changed the streaming loop's register
-// allocation and cost 8 us per launch, far more than it saved.)
+// allocation and cost 8 us per launch, far more than it saved; as a
+// non-inlined function called from both places it adds spills in the pass
+// kernels.)
 static __device__ __forceinline__ void warp_columns(const float* m, int nb, int stride, int c0, int cstep,
                                                  float2* out, int period, int max_col, int min_col) {
   const int lane = threadIdx.x & 31;

@@ -79,6 +79,22 @@ struct PassBlock {
   static constexpr int value = (VW * NI <= 32) ? 768 : 512;
 };
 
+// Staged pass kernels: rounds of kRoundPoints 16-byte chunks per lane (4 KB
+// per warp), and as many slots per warp as fit 192 KB of shared memory beside
+// the kernels' static shared memory (768 threads: 2, 512 threads: 3).
+template <int BLOCK>
+struct StagedSlots {
+  static constexpr int kRoundPoints = 8;
+  static constexpr int value = BLOCK >= 768 ? 2 : 3;
+  static constexpr size_t slot_bytes(int chunk_bytes, int ni) { return (size_t)32 * ni * chunk_bytes; }
+  static_assert((size_t)(BLOCK / 32) * value * 32 * kRoundPoints * 16 <= 192 * 1024, "ring exceeds 192 KB");
+};
+
+// Try limit of the staged kernels' waits for their bulk copies: kWaitLimit,
+// or PDSCP_WAIT_LIMIT from the environment (read at each launch; a small
+// value lets a test make the wait give up and check the reported status).
+unsigned int wait_limit();
+
 // Points in flight per lane group, by the number of floats a lane holds.
 template <int VW, int NCH>
 struct Unroll {

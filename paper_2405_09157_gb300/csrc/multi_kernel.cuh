@@ -46,7 +46,7 @@ struct MultiParams {
 template <typename T, int VW, int LPP, int NCH, int U, int K>
 __global__ void __launch_bounds__(kBlock, (K >= 4 ? 2 : 3)) ses_multi_kernel(MultiParams p) {
   using GS = GroupScatter<LPP, K>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ float s_sc[kWarps][K][3];
   __shared__ float2 s_scr[kBlock];
   __shared__ __align__(16) double s_hdr[K][sizeof(StateHdr) / 8];
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kBlock, (K >= 4 ? 2 : 3)) ses_multi_kernel(Mul
     const int q = threadIdx.x;
     const StateHdr* hdr = reinterpret_cast<const StateHdr*>(p.states + (size_t)q * p.state_stride);
     s_live[q] = hdr->stopped == 0;
-    s_kr[q] = (float)((double)hdr->t * p.eta_over_rho[q] / kSqrt2);
+    s_kr[q] = ses_kr(hdr->t, p.eta_over_rho[q]);
     s_H[q] = (float)(hdr->hint + hdr->move);
     s_alpha[q] = (float)p.alpha[q];
   }

@@ -51,6 +51,7 @@ struct SesParams {
   float* tape;           // non-null: the finish records entry t (ses_tape_stride floats) for a reverse sweep
   unsigned char* sink;   // non-null: one warp warms the finish's code path early, writing here (warm_sink_bytes)
   int fx;                // completion through the fixed-point column accumulators (fx_push / fx_finish)
+  unsigned int wait_limit;  // staged kernels: tries per wait for a bulk copy before giving up (kWaitLimit)
 };
 
 // Scale exponents of the fixed-point completion for the SES columns [S, Wt,
@@ -103,7 +104,7 @@ __device__ __forceinline__ void ses_emit(const SesParams& p, float* prow, const 
 // (power of two); NCH: chunks per lane; U: points in flight per lane group.
 template <typename T, int VW, int LPP, int NCH, int U>
 __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ float s_sc[kWarps][4];
 
   pdl_trigger();
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
   constexpr int PPW = 32 / LPP;
 
   // k/sqrt2; an evaluation pass needs only distances, so it uses k = 0
-  const float kr = p.eval_only ? 0.f : (float)((double)hdr->t * p.eta_over_rho / kSqrt2);
+  const float kr = p.eval_only ? 0.f : ses_kr(hdr->t, p.eta_over_rho);
   const float H = (float)(hdr->hint + hdr->move);
   const float alpha = (float)p.alpha;
   const float* mean32 = state_mean32(p.state, d);
@@ -256,7 +257,8 @@ __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
 static __device__ __noinline__ void ses_finish_warp(const float2* raw, const double* s_mean, const double* s_v1,
                                              const StateHdr& h, void* state, int d, double alpha_d, double gam1,
                                              double eta_over_rho, int eval_only, pdscp_step_out* out,
-                                             float* tape = nullptr, const double* s_dual = nullptr) {
+                                             float* tape = nullptr, const double* s_dual = nullptr,
+                                             int forced_status = PDSCP_OK) {
   const int lane = threadIdx.x & 31;
   StateHdr* hdr = reinterpret_cast<StateHdr*>(state);
   double* mean = state_mean(state);
@@ -283,7 +285,7 @@ static __device__ __noinline__ void ses_finish_warp(const float2* raw, const dou
   const bool qpu = qp && !eval_only && t >= 1 && Cc > 0.f && isfinite(Cc);
   const double wt = (double)t * (double)t;
   const double wsum = h.dual_w + (qpu ? wt : 0.0);
-  const double rw = qpu ? wt / wsum : 0.0;
+  const double rw = qpu ? wt * recip_d(wsum) : 0.0;  // Newton-refined reciprocal: FP64 divide is slow here
   const float rCc = qpu ? 1.0f / Cc : 0.f;
   double* bbar = state_dual(state, d);
   // A = |g|^2, B = g . (v_1 - ubar), C = |ubar - v_1|^2, |Bbar|^2
@@ -322,6 +324,7 @@ static __device__ __noinline__ void ses_finish_warp(const float2* raw, const dou
 
   int status = PDSCP_OK;
   if (!(S > 0.f) || !isfinite(S) || !isfinite(V) || !isfinite(f)) status = PDSCP_ERR_NUMERIC;
+  if (forced_status != PDSCP_OK) status = forced_status;  // a staged pass whose copy wait gave up
   bool stop = false, failed = false;
   int outcome = PDSCP_OUT_RUNNING;
   const bool better = (t > 0 && fd < h.best_f);
@@ -341,7 +344,7 @@ static __device__ __noinline__ void ses_finish_warp(const float2* raw, const dou
       } else {
         const double fp = h.f_prev;
         if (fp > 0.0) {
-          streak = (fabs(fd - fp) / fp < h.delta) ? streak + 1 : 0;
+          streak = (fabs(fd - fp) < h.delta * fp) ? streak + 1 : 0;  // |df|/f < delta, f > 0 (no FP64 divide)
           if (streak >= h.patience) {
             stop = true;
             outcome = PDSCP_OUT_STALLED;
@@ -375,7 +378,7 @@ static __device__ __noinline__ void ses_finish_warp(const float2* raw, const dou
     if (lane == 0) {
       ent[0] = S;
       ent[1] = ng;
-      ent[2] = (float)((double)t * eta_over_rho / kSqrt2);
+      ent[2] = ses_kr(t, eta_over_rho);
       ent[3] = (float)(h.hint + h.move);
     }
   }
@@ -482,7 +485,12 @@ __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw, const Se
   cp_async_wait_all();
   if (p.row_out) {  // a shard of a row-sharded iteration: hand the totals to the merge
     __syncthreads();
-    for (int pc = tid; pc < st; pc += blockDim.x) p.row_out[pc] = raw[pc];
+    unsigned int* tmo = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(p.counter) + kTimeoutFlagOff);
+    const bool timed_out = __ldcg(tmo) != 0u;
+    __syncthreads();
+    for (int pc = tid; pc < st; pc += blockDim.x)  // a timed-out pass hands on S = NaN: the merge reports it
+      p.row_out[pc] = (timed_out && pc == 0) ? make_float2(NAN, 0.f) : raw[pc];
+    if (timed_out && tid == 0) *tmo = 0u;
     return;
   }
   if (tid < d) s_v1[tid] = (double)v0;
@@ -491,10 +499,11 @@ __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw, const Se
   // The O(d) math runs in warp 0 alone: FP64 work is slow on this GPU and
   // would only contend across warps; no block barrier follows.
   if (tid >= 32) return;
-  const int lane = tid;
-  (void)lane;
+  unsigned int* tmo = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(p.counter) + kTimeoutFlagOff);
+  const bool timed_out = __ldcg(tmo) != 0u;
+  if (timed_out && tid == 0) *tmo = 0u;
   ses_finish_warp(raw, s_mean, s_v1, *reinterpret_cast<const StateHdr*>(s_hdr), p.state, d, p.alpha, (double)gam1,
-                  p.eta_over_rho, p.eval_only, p.out, p.tape, s_dual);
+                  p.eta_over_rho, p.eval_only, p.out, p.tape, s_dual, timed_out ? PDSCP_ERR_TIMEOUT : PDSCP_OK);
 }
 
 }  // namespace pdscp
@@ -509,12 +518,24 @@ namespace pdscp {
 // The weighted sums G' are then accumulated from the broadcast
 // coefficients. Same arithmetic per point as ses_iter_kernel; only the order
 // of the FP32 partial sums differs.
-template <typename T, int VW, int LPP, int NI, int BLOCK>
+//
+// S = 0: every lane loads its chunks of a round straight into registers, the
+// next round's loads issued after the current round's arithmetic. S >= 2:
+// staged rounds. Each streaming warp owns a ring of S slots of shared memory
+// (4 KB each, one round) and S mbarriers; lane 0 fills a slot with one bulk
+// copy (cp.async.bulk) of the round's contiguous rows, and the copies of the
+// next S - 1 rounds are in flight while the warp computes the current one
+// from shared memory (bytes in flight no longer bounded by registers). A
+// wait that gives up after p.wait_limit tries records a timeout, drains the
+// copies still in flight and leaves the loop; the finishing CTA reports
+// PDSCP_ERR_TIMEOUT.
+template <typename T, int VW, int LPP, int NI, int BLOCK, int NS>
 __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
   using GS = GroupScatter<LPP, NI>;
   constexpr int NW = BLOCK / 32;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ float s_sc[NW][4];
+  __shared__ uint64_t s_bar[NS > 0 ? NW * NS : 1];
   // per-lane sum of the ORACLE coefficients (kept in shared memory: one more
   // register across the streaming loop costs more than the shared access)
   __shared__ float s_cs[BLOCK];
@@ -565,13 +586,64 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
     const uint32_t w = j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
     return __uint_as_float((e & 1) ? (w & 0xffff0000u) : (w << 16));
   };
-  load_round(lo);
-  // BF16 rows: a round holds twice the points of an FP32 round, and its loads
-  // wait for the previous round's arithmetic; lane 0 of each warp asks L2
-  // for the next round ahead of its loads (measured at n = 1e6, d = 32:
-  // 32.8 -> 30.7 us; no gain for FP32, so not done there)
+  // staged rounds: slot k of this warp's ring, one round of contiguous rows
+  constexpr int SLOT = 32 * NI * VW * (int)sizeof(T);  // >= ROUND * d * sizeof(T)
+  unsigned char* ring = smem_raw + (size_t)warp * (NS > 0 ? NS : 1) * SLOT;
+  uint64_t* bar = s_bar + (NS > 0 ? warp * NS : 0);
+  auto issue = [&](int k, int64_t b) {  // lane 0: round starting at row b into slot k
+    const int64_t m = hi - b < ROUND ? hi - b : ROUND;
+    bulk_load(ring + k * SLOT, pts + b * d, (unsigned int)(m * d * (int64_t)sizeof(T)), bar + k);
+  };
+  if constexpr (NS > 0) {
+    if (lane == 0 && lo < hi) {
+#pragma unroll
+      for (int k = 0; k < NS; ++k) mbar_init(bar + k, 1);
+      mbar_init_fence();
+#pragma unroll
+      for (int k = 0; k < NS; ++k)
+        if (lo + k * ROUND < hi) issue(k, lo + k * ROUND);
+    }
+    __syncwarp();
+  } else {
+    load_round(lo);
+  }
+  // the round at base, slot k, from shared memory into the round's registers
+  auto read_round = [&](int64_t base, int k) {
+    const unsigned char* sl = ring + k * SLOT;
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const int64_t i = base + r * PPW + grp;
+      const uint4 v = (i < hi && has_chunk)
+                          ? *reinterpret_cast<const uint4*>(sl + ((size_t)(r * PPW + grp) * d) * sizeof(T) + gl * 16)
+                          : make_uint4(0u, 0u, 0u, 0u);
+      if constexpr (kPacked) {
+        xr[r] = v;
+      } else {
+        x[r][0] = __uint_as_float(v.x);
+        x[r][1] = __uint_as_float(v.y);
+        x[r][2] = __uint_as_float(v.z);
+        x[r][3] = __uint_as_float(v.w);
+      }
+    }
+  };
+  // waits (at least kWaitLimit tries each) for the copies of rounds r0 ..
+  // r0 + NS - 1 that were issued, before the ring's memory is reused or the
+  // CTA exits
+  auto drain = [&](int r0) {
+    if constexpr (NS > 0) {
+      const unsigned int lim = p.wait_limit > kWaitLimit ? p.wait_limit : kWaitLimit;
+#pragma unroll
+      for (int j = 0; j < NS; ++j)
+        if (lo + (int64_t)(r0 + j) * ROUND < hi) mbar_wait(bar + (r0 + j) % NS, (unsigned int)((r0 + j) / NS) & 1u, lim);
+    }
+  };
+  bool timed_out = false;
+  // BF16 rows (register rounds): a round holds twice the points of an FP32
+  // round, and its loads wait for the previous round's arithmetic; lane 0 of
+  // each warp asks L2 for the next round ahead of its loads (measured at n =
+  // 1e6, d = 32: 32.8 -> 30.7 us; no gain for FP32, so not done there)
   auto prefetch_round = [&](int64_t b) {
-    if constexpr (sizeof(T) == 2) {
+    if constexpr (sizeof(T) == 2 && NS == 0) {
       if (lane == 0 && b < hi) {
         const int64_t m = hi - b < ROUND ? hi - b : ROUND;
         const unsigned int bytes = (unsigned int)(m * d * (int64_t)sizeof(T));  // whole 16-byte chunks
@@ -584,9 +656,12 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
   // previous launch (state, partial rows, counters)
   pdl_wait();
   StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
-  if (hdr->stopped && !p.eval_only) return;
+  if (hdr->stopped && !p.eval_only) {
+    drain(0);  // staged: the first rounds' copies are in flight
+    return;
+  }
 
-  const float kr = p.eval_only ? 0.f : (float)((double)hdr->t * p.eta_over_rho / kSqrt2);
+  const float kr = p.eval_only ? 0.f : ses_kr(hdr->t, p.eta_over_rho);
   const float H = (float)(hdr->hint + hdr->move);
   const float alpha = (float)p.alpha;
   const float* mean32 = state_mean32(p.state, d);
@@ -604,9 +679,19 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
   float S = 0.f, W = 0.f, maxd = -INFINITY;
   s_cs[threadIdx.x] = 0.f;
 
-  for (int64_t base = lo; base < hi; base += ROUND) {
-    prefetch_round(base + ROUND);
-    if (base != lo) load_round(base);
+  int rnd = 0;
+  for (int64_t base = lo; base < hi; base += ROUND, ++rnd) {
+    const int k = NS > 0 ? rnd % (NS > 0 ? NS : 1) : 0;
+    if constexpr (NS > 0) {
+      if (!mbar_wait(bar + k, (unsigned int)(rnd / (NS > 0 ? NS : 1)) & 1u, p.wait_limit)) {
+        timed_out = true;
+        break;
+      }
+      read_round(base, k);
+    } else {
+      prefetch_round(base + ROUND);
+      if (base != lo) load_round(base);
+    }
     float part[NI];
 #pragma unroll
     for (int r = 0; r < NI; ++r) {
@@ -658,6 +743,24 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
         }
       }
     }
+    if constexpr (NS > 0) {
+      // every lane has read slot k (its values were used above): refill it
+      // with the round S ahead
+      __syncwarp();
+      if (lane == 0 && base + NS * ROUND < hi) {
+        fence_proxy_async_smem();
+        issue(k, base + NS * ROUND);
+      }
+    }
+  }
+  if constexpr (NS > 0) {
+    if (timed_out) {
+      // drain: wait (again at most wait_limit tries, at least the default)
+      // for every copy still in flight before the ring is reused or the
+      // CTA exits, then report the timeout
+      drain(rnd);
+      if (lane == 0) atomicOr(reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(p.counter) + kTimeoutFlagOff), 1u);
+    }
   }
 
 #pragma unroll
@@ -668,6 +771,7 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
   const float Cs = warp_sum(s_cs[threadIdx.x]);
   W = warp_sum(W);
   maxd = warp_max(maxd);
+  if constexpr (NS > 0) __syncthreads();  // every warp is done with its ring before the shared memory is reused
   float* sG = reinterpret_cast<float*>(smem_raw);
   if (grp == 0 && has_chunk)
 #pragma unroll
@@ -728,7 +832,7 @@ constexpr int kMergeBlock = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(kMergeBlock) ses_merge_kernel(SesMergeParams m) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ float2 s_scr[kMergeBlock];
   __shared__ __align__(16) double s_hdr[sizeof(StateHdr) / 8];
   const StateHdr* hdr = reinterpret_cast<const StateHdr*>(m.state);

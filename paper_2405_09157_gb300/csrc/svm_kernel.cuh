@@ -78,7 +78,7 @@ __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw, const Sv
 
 template <typename T, int VW, int LPP, int NCH, int U>
 __global__ void __launch_bounds__(kBlock) svm_iter_kernel(SvmParams p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ float s_sc[kWarps][4];
 
   pdl_trigger();
@@ -260,7 +260,7 @@ static __device__ __noinline__ void svm_finish_warp(const float2* raw, const dou
   const bool qpu = qp && !eval_only && t >= 1 && SP > 0.f && SQ > 0.f;
   const double wt = (double)t * (double)t;
   const double wsum = h.dual_w + (qpu ? wt : 0.0);
-  const double rw = qpu ? wt / wsum : 0.0;
+  const double rw = qpu ? wt * recip_d(wsum) : 0.0;  // Newton-refined reciprocal: FP64 divide is slow here
   double* zbar = state_dual(state, d);
   // |z|^2, Claim 8 |P mu/Tr mu - Q gamma/Tr gamma|^2, |wbar|^2, z . wbar, |zbar|^2
   float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -316,7 +316,7 @@ static __device__ __noinline__ void svm_finish_warp(const float2* raw, const dou
       } else {
         const double fp = h.f_prev;
         if (fp > 0.0) {
-          streak = (fabs(fd - fp) / fp < h.delta) ? streak + 1 : 0;
+          streak = (fabs(fd - fp) < h.delta * fp) ? streak + 1 : 0;  // |df|/f < delta, f > 0 (no FP64 divide)
           if (streak >= h.patience) {
             stop = true;
             outcome = PDSCP_OUT_STALLED;
@@ -474,7 +474,7 @@ template <typename T, int VW, int LPP, int NI, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
   using GS = GroupScatter<LPP, NI>;
   constexpr int NW = BLOCK / 32;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ float s_sc[NW][4];
 
   const int d = p.d;
@@ -665,7 +665,7 @@ constexpr int kSvmMergeBlock = 256;
 
 template <int kUnused = 0>  // a template so that only the launching unit instantiates it
 __global__ void __launch_bounds__(kSvmMergeBlock) svm_merge_kernel(SvmMergeParams m) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ float2 s_scr[kSvmMergeBlock];
   __shared__ __align__(16) double s_hdr[sizeof(StateHdr) / 8];
   const StateHdr* hdr = reinterpret_cast<const StateHdr*>(m.state);
