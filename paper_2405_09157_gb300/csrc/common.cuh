@@ -142,6 +142,15 @@ constexpr size_t kTimeoutFlagOff = kFxFlagOff + 4;
 // before later reads of the other CTAs' writes. It is the weaker form of
 // __threadfence(), which is sequentially consistent and costs more.
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;\n" ::: "memory"); }
+// Arrival on a completion counter in one instruction: an acquire-release
+// atomic add (the release half orders this thread's earlier writes, and those
+// the CTA barrier before it made visible to it, before the add; the acquire
+// half orders the add before this thread's later reads). Returns the old value.
+__device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int* a, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;\n" : "=r"(old) : "l"(a), "r"(v) : "memory");
+  return old;
+}
 // Programmatic dependent launch: a pass kernel lets the next launch in the
 // stream start early (pdl_trigger) and, in that next launch, waits for the
 // previous grid's completion and memory (pdl_wait) before it reads anything
@@ -473,12 +482,7 @@ __device__ bool arrive_pass(const float* rows, int stride, float2* grows, unsign
                             bool* s_flag, OpOf opof, bool single) {
   if (!single) return arrive_two_level(rows, stride, grows, counters, scratch, s_flag, opof);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    fence_acq_rel_gpu();
-    const unsigned int prev = atomicAdd(&counters[0], 1u);
-    fence_acq_rel_gpu();
-    *s_flag = (prev == (unsigned int)(gridDim.x - 1));
-  }
+  if (threadIdx.x == 0) *s_flag = (atom_add_acq_rel_gpu(&counters[0], 1u) == (unsigned int)(gridDim.x - 1));
   __syncthreads();
   return *s_flag;
 }
@@ -620,12 +624,7 @@ __device__ __forceinline__ float2 fx_take(FxCols f, int pc, int op, int e) {
 // true in the finishing CTA.
 __device__ __forceinline__ bool fx_arrive(unsigned int* counters, bool* s_flag) {
   __syncthreads();
-  if (threadIdx.x == 0) {
-    fence_acq_rel_gpu();
-    const unsigned int prev = atomicAdd(&counters[0], 1u);
-    fence_acq_rel_gpu();
-    *s_flag = (prev == (unsigned int)(gridDim.x - 1));
-  }
+  if (threadIdx.x == 0) *s_flag = (atom_add_acq_rel_gpu(&counters[0], 1u) == (unsigned int)(gridDim.x - 1));
   __syncthreads();
   return *s_flag;
 }

@@ -14,14 +14,16 @@ struct SvmLauncher {
   // finishing CTA the column totals, the mean and (single-level
   // completion) every partial row, whichever is larger.
   template <typename Kern>
-  cudaError_t launch(Kern kern, int points_per_lane_step, int lpp, int block) {
+  cudaError_t launch(Kern kern, int points_per_lane_step, int lpp, int block, size_t ring_bytes = 0) {
     const int dp = dpad4(p.d);
     const int st = svm_partial_stride(p.d);
-    const size_t pass_smem = (size_t)(block / 32) * 2 * dp * sizeof(float);
+    size_t pass_smem = (size_t)(block / 32) * 2 * dp * sizeof(float);
+    if (ring_bytes > pass_smem) pass_smem = ring_bytes;
     const size_t fin_base = (size_t)(st + 2 * dp) * sizeof(double);  // totals | mean | zbar
     size_t smem = pass_smem > fin_base ? pass_smem : fin_base;
     int grid = pass_grid(kern, smem, p.n, (32 / lpp) * points_per_lane_step * (block / 32), block);
     SvmParams q = p;
+    q.wait_limit = wait_limit();
     // Rows that fit the staging area complete by one staged reduction in the
     // last CTA; wider rows that fit the workspace head's accumulators complete
     // through them (fixed point), the rest in two levels. Measured on GB300:
@@ -51,9 +53,22 @@ struct SvmLauncher {
   cudaError_t go() {
     if constexpr (VW > 1 && NCH == 1) {
       // vector rows of at most 32 chunks: the reduce-scatter form
-      constexpr int NI = RoundSize<VW, LPP>::value;
-      constexpr int B = PassBlock<VW, NI>::value;
-      return launch(svm_iter_t_kernel<T, VW, LPP, NI, B>, NI, LPP, B);
+      if constexpr (sizeof(T) == 2) {
+        // bfloat16 rows: staged rounds of 8 points per lane group (4 KB per
+        // slot), 512 threads (measured at n = 1e6, d = 128: 69.5 -> 56.4 us)
+        constexpr int NI = StagedSlots<768>::kRoundPoints;
+        constexpr int B = 512;
+        constexpr int NS = StagedSlots<B>::value;
+        return launch(svm_iter_t_kernel<T, VW, LPP, NI, B, NS>, NI, LPP, B,
+                      (size_t)(B / 32) * NS * StagedSlots<B>::slot_bytes(VW * (int)sizeof(T), NI));
+      } else {
+        // float32 rows: rounds loaded into registers (staged at 512 threads
+        // measured 91.6 against 88.3 us at n = 1e6, d = 128; at 768 threads
+        // the staged kernel spills)
+        constexpr int NI = RoundSize<VW, LPP>::value;
+        constexpr int B = PassBlock<VW, NI>::value;
+        return launch(svm_iter_t_kernel<T, VW, LPP, NI, B, 0>, NI, LPP, B);
+      }
     } else {
       constexpr int U = Unroll<VW, NCH>::value;
       return launch(svm_iter_kernel<T, VW, LPP, NCH, U>, U, LPP, kBlock);

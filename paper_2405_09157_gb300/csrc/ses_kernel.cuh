@@ -258,18 +258,24 @@ static __device__ __noinline__ void ses_finish_warp(const float2* raw, const dou
                                              const StateHdr& h, void* state, int d, double alpha_d, double gam1,
                                              double eta_over_rho, int eval_only, pdscp_step_out* out,
                                              float* tape = nullptr, const double* s_dual = nullptr,
-                                             int forced_status = PDSCP_OK) {
+                                             int forced_status = PDSCP_OK, int role = 0) {
   const int lane = threadIdx.x & 31;
   StateHdr* hdr = reinterpret_cast<StateHdr*>(state);
   double* mean = state_mean(state);
   float* mean32 = state_mean32(state, d);
   float* best = state_best(state, d);
   const double alpha_in = alpha_d;
+  // role 0: the whole finish in this warp; role 1: all but the averaged QP
+  // bound; role 2: only the averaged QP bound (Bbar, Abar, its lower bound,
+  // lb_best, dual_A, dual_w and the record's dual_bound), run by a second warp
+  // at the same time as role 1 (its FP64 chains are the longest of the finish).
+  const bool main_part = role != 2;
   // The finish works in FP32 (FP64 is slow here and its dependent chains
   // dominated this step): its inputs are compensated sums accurate to ~1e-7,
   // and its results feed tolerances of 1e-5. FP64 is kept for the running
-  // mean, which accumulates over the whole alpha-FTP, and for the Sec. 5
-  // ratio test, which decides an integer as the oracle does.
+  // mean, which accumulates over the whole alpha-FTP, for the averaged QP
+  // bound's running averages, and for the Sec. 5 ratio test, which decides an
+  // integer as the oracle does.
   auto tot = [&](int pc) { return raw[pc].x + raw[pc].y; };
   const float S = tot(0), Wt = tot(1), maxd = raw[2].x;
   const float alpha = (float)alpha_in;
@@ -281,10 +287,10 @@ static __device__ __noinline__ void ses_finish_warp(const float2* raw, const dou
   // v_1) = G'/Cc - (v_1 - ubar); both are averaged over the alpha-FTP with
   // iterate t weighted by t^2, and OPT^2 >= Abar - |Bbar|^2.
   const float Cc = tot(3);
-  const bool qp = s_dual != nullptr;
+  const bool qp = s_dual != nullptr && role != 1;
   const bool qpu = qp && !eval_only && t >= 1 && Cc > 0.f && isfinite(Cc);
-  const double wt = (double)t * (double)t;
-  const double wsum = h.dual_w + (qpu ? wt : 0.0);
+  const double wt = qpu ? (double)t * (double)t : 0.0;
+  const double wsum = h.dual_w + wt;
   const double rw = qpu ? wt * recip_d(wsum) : 0.0;  // Newton-refined reciprocal: FP64 divide is slow here
   const float rCc = qpu ? 1.0f / Cc : 0.f;
   double* bbar = state_dual(state, d);
@@ -308,17 +314,29 @@ static __device__ __noinline__ void ses_finish_warp(const float2* raw, const dou
   }
   warp_sum_kf<4>(acc);
   const float A = acc[0], B = acc[1], C = acc[2];
-  // A_t = (sum c_i dist_i^2 - 2 G'.(v_1 - ubar)) / Cc + |v_1 - ubar|^2, with
-  // sum c_i dist_i^2 = alpha S - Wt for points
-  const double Abar = qpu ? h.dual_A + rw * ((double)((alpha_d * S - Wt - 2.f * (float)kSqrt2 * S * B) * rCc + C) - h.dual_A)
-                          : h.dual_A;
-  const float LBq = (qp && wsum > 0.0) ? sqrtf(fmaxf((float)Abar - acc[3], 0.f)) : 0.f;
   const float rad = alpha - gam1f;
   const float rng = A > 0.f ? 1.0f / sqrtf(A) : 0.f;
   const float ng = A * rng;                 // ||g||
   const float step = rad * rng;             // u = v_1 + step g  (u = v_1 when g = 0)
   const float V = B + step * A + Wt * inv;  // g.(u - ubar) + Wt/(sqrt2 S): Eq. (ses_oracle) value
   const float LB = fmaxf(gam1f, alpha - V / (ng + (float)(1.0 / kSqrt2)));  // Eq. (primal_construction)
+  if (role != 1) {
+    // A_t = (sum c_i dist_i^2 - 2 G'.(v_1 - ubar)) / Cc + |v_1 - ubar|^2, with
+    // sum c_i dist_i^2 = alpha S - Wt for points
+    const double Abar = qpu ? h.dual_A + rw * ((double)((alpha_d * S - Wt - 2.f * (float)kSqrt2 * S * B) * rCc + C) - h.dual_A)
+                            : h.dual_A;
+    const float LBq = (qp && wsum > 0.0) ? sqrtf(fmaxf((float)Abar - acc[3], 0.f)) : 0.f;
+    if (lane == 0) {
+      const double lbn = (double)fmaxf(LB, LBq);
+      if (!eval_only && lbn > h.lb_best) hdr->lb_best = lbn;
+      if (qpu) {
+        hdr->dual_A = Abar;
+        hdr->dual_w = wsum;
+      }
+      if (out) out->dual_bound = (double)LBq;
+    }
+  }
+  if (!main_part) return;
   const float f = fmaxf(maxd, sqrtf(C) + gam1f);                             // f at the mean read (Sec. 5)
   const double fd = (double)f;
 
@@ -383,12 +401,6 @@ static __device__ __noinline__ void ses_finish_warp(const float2* raw, const dou
     }
   }
   if (lane == 0) {
-    const double lbn = (double)fmaxf(LB, LBq);
-    if (!eval_only && lbn > h.lb_best) hdr->lb_best = lbn;
-    if (qpu) {
-      hdr->dual_A = Abar;
-      hdr->dual_w = wsum;
-    }
     if (streak != h.streak) hdr->streak = streak;
     if (set_fprev) hdr->f_prev = fd;
     if (better) hdr->best_f = fd;
@@ -404,23 +416,19 @@ static __device__ __noinline__ void ses_finish_warp(const float2* raw, const dou
     }
     if (status != PDSCP_OK) hdr->status = status;
     hdr->last_value = (double)V;
-    if (out) {
-      pdscp_step_out o;
-      o.oracle_value = (double)V;
-      o.objective = fd;
-      o.lower_bound = (double)LB;
-      o.upper_bound = fd;
-      o.t = tn;
-      o.failed = failed ? 1 : 0;
-      o.stopped = (stop || h.stopped) ? 1 : 0;
-      o.status = status;
-      o.outcome = outcome;
-      o.k = (double)t * eta_over_rho;
-      o.dual_bound = (double)LBq;
-      *out = o;
+    if (out) {  // field by field: in role 1 the dual_bound is written by the other warp
+      out->oracle_value = (double)V;
+      out->objective = fd;
+      out->lower_bound = (double)LB;
+      out->upper_bound = fd;
+      out->t = tn;
+      out->failed = failed ? 1 : 0;
+      out->stopped = (stop || h.stopped) ? 1 : 0;
+      out->status = status;
+      out->outcome = outcome;
+      out->k = (double)t * eta_over_rho;
     }
   }
-
 }
 
 template <typename T>
@@ -476,6 +484,10 @@ __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw, const Se
   }
   const float v0 = tid < d ? elem_to_float<T>(pts + tid) : 0.f;
   const float gam1 = p.radii ? __ldg(p.radii) : 0.f;
+  // a staged pass whose copy wait gave up (read before the reduction, so that
+  // the load's latency overlaps it; cleared once every thread has read it)
+  unsigned int* tmo = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(p.counter) + kTimeoutFlagOff);
+  const bool timed_out = __ldcg(tmo) != 0u;
   if (p.fx) {
     fx_finish(p.counter, p.partials, st, raw, s_scr, fe, opof);
     if (p.radii && tid == 0) raw[3] = make_float2(NAN, 0.f);  // no QP bound for spheres (not pushed)
@@ -485,9 +497,6 @@ __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw, const Se
   cp_async_wait_all();
   if (p.row_out) {  // a shard of a row-sharded iteration: hand the totals to the merge
     __syncthreads();
-    unsigned int* tmo = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(p.counter) + kTimeoutFlagOff);
-    const bool timed_out = __ldcg(tmo) != 0u;
-    __syncthreads();
     for (int pc = tid; pc < st; pc += blockDim.x)  // a timed-out pass hands on S = NaN: the merge reports it
       p.row_out[pc] = (timed_out && pc == 0) ? make_float2(NAN, 0.f) : raw[pc];
     if (timed_out && tid == 0) *tmo = 0u;
@@ -496,14 +505,19 @@ __device__ void ses_finish(const SesParams& p, unsigned char* smem_raw, const Se
   if (tid < d) s_v1[tid] = (double)v0;
   for (int j = tid + blockDim.x; j < d; j += blockDim.x) s_v1[j] = (double)elem_to_float<T>(pts + j);
   __syncthreads();
-  // The O(d) math runs in warp 0 alone: FP64 work is slow on this GPU and
-  // would only contend across warps; no block barrier follows.
-  if (tid >= 32) return;
-  unsigned int* tmo = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(p.counter) + kTimeoutFlagOff);
-  const bool timed_out = __ldcg(tmo) != 0u;
   if (timed_out && tid == 0) *tmo = 0u;
+  // The O(d) math runs in one warp (FP64 work is slow on this GPU and would
+  // only contend across warps; no block barrier follows): the last warp,
+  // which as the warm-up warp ran the finish's code at the start of the
+  // launch, so its scheduler's instruction cache holds that code. The
+  // averaged QP bound, whose FP64 chains are the finish's longest, runs at
+  // the same time in the warp before it.
+  const int nw = (int)(blockDim.x >> 5), w = (int)(tid >> 5);
+  const bool split = nw >= 2;
+  if (w != nw - 1 && !(split && w == nw - 2)) return;
   ses_finish_warp(raw, s_mean, s_v1, *reinterpret_cast<const StateHdr*>(s_hdr), p.state, d, p.alpha, (double)gam1,
-                  p.eta_over_rho, p.eval_only, p.out, p.tape, s_dual, timed_out ? PDSCP_ERR_TIMEOUT : PDSCP_OK);
+                  p.eta_over_rho, p.eval_only, p.out, p.tape, s_dual, timed_out ? PDSCP_ERR_TIMEOUT : PDSCP_OK,
+                  split ? (w == nw - 1 ? 1 : 2) : 0);
 }
 
 }  // namespace pdscp
@@ -595,12 +609,17 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
     bulk_load(ring + k * SLOT, pts + b * d, (unsigned int)(m * d * (int64_t)sizeof(T)), bar + k);
   };
   if constexpr (NS > 0) {
+    // NS - 1 rounds are issued before the wait for the previous launch: the
+    // copies of every CTA of this launch that starts early flood the memory
+    // system while the previous launch's finishing CTA reads its partial
+    // rows (measured at n = 1e6, d = 32: its staged reduction took 5.1 us with
+    // 2 rounds ahead, 3.4 us with 1; the iteration 1.3 us less with 1)
     if (lane == 0 && lo < hi) {
 #pragma unroll
       for (int k = 0; k < NS; ++k) mbar_init(bar + k, 1);
       mbar_init_fence();
 #pragma unroll
-      for (int k = 0; k < NS; ++k)
+      for (int k = 0; k < NS - 1; ++k)
         if (lo + k * ROUND < hi) issue(k, lo + k * ROUND);
     }
     __syncwarp();
@@ -655,6 +674,9 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
   // the first round's loads are in flight; everything below depends on the
   // previous launch (state, partial rows, counters)
   pdl_wait();
+  if constexpr (NS > 0) {
+    if (lane == 0 && lo + (NS - 1) * ROUND < hi) issue(NS - 1, lo + (NS - 1) * ROUND);
+  }
   StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
   if (hdr->stopped && !p.eval_only) {
     drain(0);  // staged: the first rounds' copies are in flight

@@ -46,6 +46,7 @@ struct SvmParams {
   unsigned char* sink;   // non-null: warm-up warps run the finish's code early, writing here
   float* tape;           // non-null: the finish records entry t (svm_tape_stride floats) for a reverse sweep
   int fx;                // completion through the fixed-point column accumulators (fx_push / fx_finish)
+  unsigned int wait_limit;  // staged kernels: tries per wait for a bulk copy before giving up (kWaitLimit)
 };
 
 // Scale exponents of the fixed-point completion for the SVM columns [S_P, S_Q,
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(kBlock) svm_iter_kernel(SvmParams p) {
 static __device__ __noinline__ void svm_finish_warp(const float2* raw, const double* s_mean, const StateHdr& h,
                                              void* state, int d, double alpha_d, double D_d, double eta_over_rho,
                                              int eval_only, pdscp_step_out* out, float* tape = nullptr,
-                                             const double* s_dual = nullptr) {
+                                             const double* s_dual = nullptr, int forced_status = PDSCP_OK) {
   const int lane = threadIdx.x & 31;
   const int dp = dpad4(d);
   StateHdr* hdr = reinterpret_cast<StateHdr*>(state);
@@ -297,6 +298,7 @@ static __device__ __noinline__ void svm_finish_warp(const float2* raw, const dou
 
   int status = PDSCP_OK;
   if (!(S > 0.f) || !isfinite(S) || !isfinite(V)) status = PDSCP_ERR_NUMERIC;
+  if (forced_status != PDSCP_OK) status = forced_status;  // a staged pass whose copy wait gave up
   bool stop = false, failed = false;
   int outcome = PDSCP_OUT_RUNNING;
   const bool better = fd > h.best_f;
@@ -450,15 +452,19 @@ __device__ void svm_finish(const SvmParams& p, unsigned char* smem_raw, const Sv
   else
     final_reduce(p.partials, st, p.grows, p.counter, s_scr, opof, raw, stage, p.single, 3, 2, st);
   cp_async_wait_all();
+  unsigned int* tmo = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(p.counter) + kTimeoutFlagOff);
+  const bool timed_out = __ldcg(tmo) != 0u;
+  __syncthreads();
+  if (timed_out && tid == 0) *tmo = 0u;
   if (p.row_out) {  // a shard of a row-sharded iteration: hand the totals to the merge
-    for (int pc = tid; pc < st; pc += blockDim.x) p.row_out[pc] = raw[pc];
+    for (int pc = tid; pc < st; pc += blockDim.x)  // a timed-out pass hands on S_P = NaN: the merge reports it
+      p.row_out[pc] = (timed_out && pc == 0) ? make_float2(NAN, 0.f) : raw[pc];
     return;
   }
-  __syncthreads();
-  // The O(d) math runs in warp 0 alone (see ses_finish).
-  if (tid >= 32) return;
+  // The O(d) math runs in the last warp alone (see ses_finish).
+  if ((int)(tid >> 5) != (int)(blockDim.x >> 5) - 1) return;
   svm_finish_warp(raw, s_mean, *reinterpret_cast<const StateHdr*>(s_hdr), p.state, d, p.alpha, p.D,
-                  p.eta_over_rho, p.eval_only, p.out, p.tape, s_dual);
+                  p.eta_over_rho, p.eval_only, p.out, p.tape, s_dual, timed_out ? PDSCP_ERR_TIMEOUT : PDSCP_OK);
 }
 
 }  // namespace pdscp
@@ -470,12 +476,17 @@ namespace pdscp {
 // reduce-scattered so that one lane per point forms the margin, the label
 // test and the exponential; the signed weight y_i e^{...} is broadcast back
 // for the per-class weighted sums Z_P, Z_Q.
-template <typename T, int VW, int LPP, int NI, int BLOCK>
+//
+// NS = 0: rounds loaded into registers; NS >= 2: rounds staged through a
+// per-warp ring of NS shared-memory slots filled by bulk copies, bounded waits
+// (as ses_iter_t_kernel).
+template <typename T, int VW, int LPP, int NI, int BLOCK, int NS>
 __global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
   using GS = GroupScatter<LPP, NI>;
   constexpr int NW = BLOCK / 32;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ float s_sc[NW][4];
+  __shared__ uint64_t s_bar[NS > 0 ? NW * NS : 1];
 
   const int d = p.d;
   const int dp = dpad4(d);
@@ -510,12 +521,62 @@ __global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
         }
       }
   };
-  load_round(lo);
-  // BF16 rows: lane 0 of each warp asks L2 for the next round ahead of its
-  // loads, as in ses_iter_t_kernel (measured at n = 1e6, d = 128: 86.6 ->
-  // 71.7 us; FP32 is 2.5 us slower with it, so not done there)
+  constexpr int SLOT = 32 * NI * VW * (int)sizeof(T);  // >= ROUND * d * sizeof(T)
+  unsigned char* ring = smem_raw + (size_t)warp * (NS > 0 ? NS : 1) * SLOT;
+  uint64_t* bar = s_bar + (NS > 0 ? warp * NS : 0);
+  auto issue = [&](int kk, int64_t b) {  // lane 0: round starting at row b into slot kk
+    const int64_t m = hi - b < ROUND ? hi - b : ROUND;
+    bulk_load(ring + kk * SLOT, pts + b * d, (unsigned int)(m * d * (int64_t)sizeof(T)), bar + kk);
+  };
+  if constexpr (NS > 0) {
+    // NS - 1 rounds before the wait for the previous launch, as in ses_iter_t_kernel
+    if (lane == 0 && lo < hi) {
+#pragma unroll
+      for (int kk = 0; kk < NS; ++kk) mbar_init(bar + kk, 1);
+      mbar_init_fence();
+#pragma unroll
+      for (int kk = 0; kk < NS - 1; ++kk)
+        if (lo + kk * ROUND < hi) issue(kk, lo + kk * ROUND);
+    }
+    __syncwarp();
+  } else {
+    load_round(lo);
+  }
+  auto read_round = [&](int64_t base, int kk) {
+    const unsigned char* sl = ring + kk * SLOT;
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const int64_t i = base + r * PPW + grp;
+      const uint4 v = (i < hi && has_chunk)
+                          ? *reinterpret_cast<const uint4*>(sl + ((size_t)(r * PPW + grp) * d) * sizeof(T) + gl * 16)
+                          : make_uint4(0u, 0u, 0u, 0u);
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+      if constexpr (sizeof(T) == 2) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {  // bf16 -> fp32 is a 16-bit left shift of the bit pattern
+          x[r][2 * j] = __uint_as_float(w[j] << 16);
+          x[r][2 * j + 1] = __uint_as_float(w[j] & 0xffff0000u);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[r][j] = __uint_as_float(w[j]);
+      }
+    }
+  };
+  auto drain = [&](int r0) {
+    if constexpr (NS > 0) {
+      const unsigned int lim = p.wait_limit > kWaitLimit ? p.wait_limit : kWaitLimit;
+#pragma unroll
+      for (int j = 0; j < NS; ++j)
+        if (lo + (int64_t)(r0 + j) * ROUND < hi) mbar_wait(bar + (r0 + j) % NS, (unsigned int)((r0 + j) / NS) & 1u, lim);
+    }
+  };
+  bool timed_out = false;
+  // BF16 rows (register rounds): lane 0 of each warp asks L2 for the next
+  // round ahead of its loads, as in ses_iter_t_kernel (measured at n = 1e6,
+  // d = 128: 86.6 -> 71.7 us; FP32 is 2.5 us slower with it, so not done there)
   auto prefetch_round = [&](int64_t b) {
-    if constexpr (sizeof(T) == 2) {
+    if constexpr (sizeof(T) == 2 && NS == 0) {
       if (lane == 0 && b < hi) {
         const int64_t m = hi - b < ROUND ? hi - b : ROUND;
         const unsigned int bytes = (unsigned int)(m * d * (int64_t)sizeof(T));  // whole 16-byte chunks
@@ -527,8 +588,14 @@ __global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
   // the first round's loads are in flight; everything below depends on the
   // previous launch (state, partial rows, counters)
   pdl_wait();
+  if constexpr (NS > 0) {
+    if (lane == 0 && lo + (NS - 1) * ROUND < hi) issue(NS - 1, lo + (NS - 1) * ROUND);
+  }
   StateHdr* hdr = reinterpret_cast<StateHdr*>(p.state);
-  if (hdr->stopped && !p.eval_only) return;
+  if (hdr->stopped && !p.eval_only) {
+    drain(0);
+    return;
+  }
 
   const float k = p.eval_only ? 0.f : (float)((double)hdr->t * p.eta_over_rho);
   const float Hm = (float)(hdr->hint - hdr->move);
@@ -544,9 +611,19 @@ __global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
   }
   float SP = 0.f, SQ = 0.f, minP = INFINITY, maxQ = -INFINITY;
 
-  for (int64_t base = lo; base < hi; base += ROUND) {
-    prefetch_round(base + ROUND);
-    if (base != lo) load_round(base);
+  int rnd = 0;
+  for (int64_t base = lo; base < hi; base += ROUND, ++rnd) {
+    const int ks = NS > 0 ? rnd % (NS > 0 ? NS : 1) : 0;
+    if constexpr (NS > 0) {
+      if (!mbar_wait(bar + ks, (unsigned int)(rnd / (NS > 0 ? NS : 1)) & 1u, p.wait_limit)) {
+        timed_out = true;
+        break;
+      }
+      read_round(base, ks);
+    } else {
+      prefetch_round(base + ROUND);
+      if (base != lo) load_round(base);
+    }
     float part[NI];
 #pragma unroll
     for (int r = 0; r < NI; ++r) {
@@ -588,6 +665,20 @@ __global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
         ZQ[e] = fmaf(qq, x[r][e], ZQ[e]);
       }
     }
+    if constexpr (NS > 0) {
+      __syncwarp();  // every lane has read slot ks: refill it with the round NS ahead
+      if (lane == 0 && base + NS * ROUND < hi) {
+        fence_proxy_async_smem();
+        issue(ks, base + NS * ROUND);
+      }
+    }
+  }
+  if constexpr (NS > 0) {
+    if (timed_out) {
+      drain(rnd);
+      if (lane == 0) atomicOr(reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(p.counter) + kTimeoutFlagOff), 1u);
+    }
+    __syncthreads();  // every warp is done with its ring before the shared memory is reused
   }
 
 #pragma unroll

@@ -51,3 +51,23 @@ def test_wait_limit_reports_timeout_then_normal_steps(monkeypatch, dtype):
     assert r["status"] == 0 and r["t"] == 1
     for key in ("objective", "oracle_value", "lower_bound"):
         assert abs(r[key] - o[key]) <= RTOL * D, key
+
+
+def test_svm_wait_limit_reports_timeout(monkeypatch):
+    X32, y = datagen.svm_clusters(60_000, 60_000, 64, seed=52)
+    D = float(np.max(np.linalg.norm(X32.astype(np.float64), axis=1)))
+    X = torch.from_numpy(X32).cuda().to(torch.bfloat16)  # bfloat16 rows of 16-byte chunks: the staged kernel
+    lab = torch.from_numpy(y).cuda()
+    out = api.new_steps(2)
+    m = api.MWU(_ffi.SVM, X, labels=lab)
+    monkeypatch.setenv("PDSCP_WAIT_LIMIT", "0")
+    m.step(0.3 * D, 0.5 / (2 * D), out=out[0], D=D)
+    torch.cuda.synchronize()
+    monkeypatch.delenv("PDSCP_WAIT_LIMIT")
+    r = api.decode_steps(out[0])[0]
+    assert r["status"] == TIMEOUT and r["stopped"] == 1
+    assert _hdr_status(m.state)[1:] == (1, TIMEOUT)
+    m2 = api.MWU(_ffi.SVM, X, labels=lab)
+    m2.step(0.3 * D, 0.5 / (2 * D), out=out[1], D=D)
+    torch.cuda.synchronize()
+    assert api.decode_steps(out[1])[0]["status"] == 0
