@@ -103,14 +103,26 @@ __device__ __forceinline__ void mbar_init_fence() {
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
+// L2 policy for data read once per pass: its lines are the first evicted, so
+// a pass streaming more than L2 holds does not push out the lines the rest of
+// the launch needs (the kernel's code, the state, the partial rows).
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+  return pol;
+}
 // Copies `bytes` from global `src` to shared `dst`; the copy's completion
 // flips the phase of `bar`, which expects exactly these bytes (one arrival).
+// The source lines are read with the L2 evict-first policy (made here, at
+// each copy: one instruction, and no register held across the caller's loop).
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned int bytes, uint64_t* bar) {
+  const uint64_t pol = l2_evict_first_policy();
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
 }
 // Waits for the phase with parity `parity` of `bar` to complete, trying at
 // most `limit` times (each try may suspend the thread for a short,
@@ -652,37 +664,44 @@ __device__ void fx_finish(unsigned int* counters, const float* rows, int stride,
   if (bad) reduce_rows(rows, 0, (int)gridDim.x, stride, raw, scratch, opof);  // ends with a barrier
 }
 
-// Column totals of an (nb x stride) float matrix in shared memory, one warp
-// per column (columns c0, c0 + cstep, ...): each lane combines rows lane,
-// lane + 32, ... (compensated FP32 sums; column pc % period == max_col is a
-// maximum, == min_col a minimum), then the lanes combine in a fixed butterfly
-// (every lane ends with the same pair, so the result is deterministic). No
-// barrier inside. (Warming this code too, as the finish's, was measured: the
-// extra call from the warm-up path changed the streaming loop's register
-// allocation and cost 8 us per launch, far more than it saved; as a
-// non-inlined function called from both places it adds spills in the pass
-// kernels.)
-static __device__ __forceinline__ void warp_columns(const float* m, int nb, int stride, int c0, int cstep,
-                                                 float2* out, int period, int max_col, int min_col) {
-  const int lane = threadIdx.x & 31;
-  for (int pc = c0; pc < stride; pc += cstep) {
-    const int q = pc % period;
+// Column totals of an (nb x stride) float matrix in shared memory, L lanes
+// per column (L a power of two dividing 32), every CTA thread on some column:
+// each lane combines rows li, li + L, ... of its column (compensated FP32
+// sums; column pc % period == max_col is a maximum, == min_col a minimum),
+// then the L lanes combine in a fixed butterfly and lane 0 of the group
+// writes the pair (a fixed order: the result is deterministic). Every warp
+// runs the same number of passes (columns past `stride` take dummy values),
+// so the shuffles never diverge. No barrier inside. With 16 lanes a CTA of
+// 768 threads covers the 36 columns of a SES row at d = 32 in one pass,
+// where one warp per column left half the warps two columns in a row.
+// (Running this code in the warm-up warps as well, as a shared non-inlined
+// function, did not shorten the reduction: measured 1.41 against 1.47 us.)
+template <int L>
+static __device__ __forceinline__ void group_columns(const float* m, int nb, int stride, float2* out, int period,
+                                                     int max_col, int min_col) {
+  const int li = threadIdx.x % L, g = threadIdx.x / L, ng = blockDim.x / L;
+  const int passes = (stride + ng - 1) / ng;
+  for (int k = 0; k < passes; ++k) {
+    const int pc = g + k * ng;
+    const bool on = pc < stride;
+    const int q = on ? pc % period : -3;
     const int op = q == max_col ? 1 : (q == min_col ? 2 : 0);
     float2 acc = col_init2(op);
-    for (int r = lane; r < nb; r += 32) col_comb2(op, acc, make_float2(m[(size_t)r * stride + pc], 0.f));
+    if (on)
+      for (int r = li; r < nb; r += L) col_comb2(op, acc, make_float2(m[(size_t)r * stride + pc], 0.f));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = L / 2; o > 0; o >>= 1) {
       float2 other;
       other.x = __shfl_xor_sync(0xffffffffu, acc.x, o);
       other.y = __shfl_xor_sync(0xffffffffu, acc.y, o);
       col_comb2(op, acc, other);
     }
-    if (lane == 0) out[pc] = acc;
+    if (on && li == 0) out[pc] = acc;
   }
 }
 
 // max_col / min_col / period: the column operations for the single-level
-// path (warp_columns); opof gives the same for the two-level path.
+// path (group_columns); opof gives the same for the two-level path.
 template <typename OpOf>
 __device__ void final_reduce(const float* rows, int stride, const float2* grows, unsigned int* counters,
                              float2* scratch, OpOf opof, float2* raw, float* stage, bool single, int max_col,
@@ -707,7 +726,7 @@ __device__ void final_reduce(const float* rows, int stride, const float2* grows,
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   if (threadIdx.x == 0) counters[0] = 0u;
   __syncthreads();
-  warp_columns(stage, nb, stride, threadIdx.x >> 5, (int)(blockDim.x >> 5), raw, period, max_col, min_col);
+  group_columns<16>(stage, nb, stride, raw, period, max_col, min_col);
   __syncthreads();
 }
 

@@ -84,7 +84,7 @@ __device__ __forceinline__ bool ses_col_rel(int pc) { return pc == 0 || pc == 3;
 // only to the sink: whichever CTA finishes then finds the code in its SM's
 // instruction cache.
 template <typename T>
-__device__ void ses_finish_warm(const SesParams& p, unsigned char* smem_raw);
+__device__ __noinline__ void ses_finish_warm(const SesParams& p, unsigned char* scratch, size_t scratch_bytes);
 
 
 
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kBlock) ses_iter_kernel(SesParams p) {
 
   const T* pts = reinterpret_cast<const T*>(p.pts);
   const WarpSplit ws(p.sink, kWarps, warp);
-  if (ws.warm) ses_finish_warm<T>(p, smem_raw);
+  if (ws.warm) ses_finish_warm<T>(p, smem_raw, (size_t)(ses_partial_stride(p.d) + 3 * dpad4(p.d)) * sizeof(double));
   const int64_t nwarps = ws.nwarps;
   const int64_t gw = ws.warm ? (p.n + nwarps * (PPW * U)) : ws.gw;  // the warm-up warp streams nothing
   for (int64_t base = gw * (PPW * U); base < p.n; base += nwarps * (PPW * U)) {
@@ -312,7 +312,15 @@ static __device__ __noinline__ void ses_finish_warp(const float2* raw, const dou
       acc[3] = fmaf((float)b, (float)b, acc[3]);
     }
   }
-  warp_sum_kf<4>(acc);
+  if (qp) {
+    warp_sum_kf<4>(acc);
+  } else {  // no averaged bound in this warp: three sums
+    float a3[3] = {acc[0], acc[1], acc[2]};
+    warp_sum_kf<3>(a3);
+    acc[0] = a3[0];
+    acc[1] = a3[1];
+    acc[2] = a3[2];
+  }
   const float A = acc[0], B = acc[1], C = acc[2];
   const float rad = alpha - gam1f;
   const float rng = A > 0.f ? 1.0f / sqrtf(A) : 0.f;
@@ -431,9 +439,15 @@ static __device__ __noinline__ void ses_finish_warp(const float2* raw, const dou
   }
 }
 
+// scratch (scratch_bytes long): shared memory the finish's code reads
+// (garbage; other warps may be writing there), never writes.
 template <typename T>
-__device__ __noinline__ void ses_finish_warm(const SesParams& p, unsigned char* smem_raw) {
+__device__ __noinline__ void ses_finish_warm(const SesParams& p, unsigned char* scratch, size_t scratch_bytes) {
   const int d = p.d;
+  const int st = ses_partial_stride(d);
+  // totals, mean, v_1 and Bbar
+  if ((size_t)(st + 3 * dpad4(d)) * sizeof(double) > scratch_bytes) return;
+  unsigned char* smem_raw = scratch;
   const float2* raw = reinterpret_cast<const float2*>(smem_raw);
   const double* s_mean = reinterpret_cast<const double*>(smem_raw) + ses_partial_stride(d);
   const double* s_v1 = s_mean + dpad4(d);
@@ -565,7 +579,8 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
   const T* pts = reinterpret_cast<const T*>(p.pts);
   pdl_trigger();
   const WarpSplit wsp(p.sink, NW, warp);
-  if (wsp.warm) ses_finish_warm<T>(p, smem_raw);
+  constexpr int SLOT = 32 * NI * VW * (int)sizeof(T);  // >= ROUND * d * sizeof(T)
+  if (wsp.warm) ses_finish_warm<T>(p, smem_raw, (size_t)(ses_partial_stride(p.d) + 3 * dpad4(p.d)) * sizeof(double));
   const int64_t nwarps = wsp.nwarps;
   const int64_t gw = wsp.gw;
   constexpr int ROUND = PPW * NI;
@@ -601,7 +616,6 @@ __global__ void __launch_bounds__(BLOCK, 1) ses_iter_t_kernel(SesParams p) {
     return __uint_as_float((e & 1) ? (w & 0xffff0000u) : (w << 16));
   };
   // staged rounds: slot k of this warp's ring, one round of contiguous rows
-  constexpr int SLOT = 32 * NI * VW * (int)sizeof(T);  // >= ROUND * d * sizeof(T)
   unsigned char* ring = smem_raw + (size_t)warp * (NS > 0 ? NS : 1) * SLOT;
   uint64_t* bar = s_bar + (NS > 0 ? warp * NS : 0);
   auto issue = [&](int k, int64_t b) {  // lane 0: round starting at row b into slot k
