@@ -44,12 +44,16 @@ MODE_PRACTICAL = "practical"
 MODE_THEORY = "theory"
 MODE_FIXED = "fixed"
 MODE_CERTIFIED = "certified"
+MODE_CORESET = "coreset"         # CERTIFIED with the core-set certificates of reading 25
 OUT_STUCK = "stuck"              # CERTIFIED mode: the certificate gap stopped shrinking (eta is halved)
 CERT_FIRST_CHECK = 1024          # CERTIFIED: first progress check of an alpha-FTP at eta = 1 (then 2x, 4x, ...)
 CERT_SHRINK = 0.8                # CERTIFIED: the FTP's own gap must shrink by this factor while t doubles
 CERT_MIN_ETA = 1.0 / 64.0        # CERTIFIED: eta is not halved below this (no progress test there)
 
 SVM_R = 2.0  # Sec. 4.2
+CORESET_K = 512        # points per class in a core set (reading 25)
+CORESET_FIRST = 256    # first core-set check after this many iterations of the search, then every doubling
+CORESET_ROUNDS = 4     # active-set rounds of one check
 
 
 def _prep(X, y):
@@ -172,6 +176,53 @@ def svm_margin(X, y, wbar):
     return max((float(np.min(s[y > 0])) - float(np.max(s[y < 0]))) / nw, 0.0)
 
 
+def svm_coreset_pick(X, y, w, K):
+    """The core set picked by a direction w (reading 25): in each class the K
+    points (all, if fewer) with the smallest y_i x_i^T w, the points nearest
+    the hyperplane with normal w, which are also the points the MWU weighs
+    most in that class (the class-normalised weights fall with y_i x_i^T w).
+    Returns a boolean mask over the rows."""
+    X, y = _prep(X, y)
+    s = y * (X @ np.asarray(w, dtype=np.float64))
+    pick = np.zeros(X.shape[0], dtype=bool)
+    for cls in (y > 0, y < 0):
+        idx = np.nonzero(cls)[0]
+        pick[idx[np.argsort(s[idx], kind="stable")[:K]]] = True
+    return pick
+
+
+def svm_coreset_bounds(X, y, w, eps, K=CORESET_K, rounds=CORESET_ROUNDS):
+    """Certificates from core sets (reading 25): restricting Eq. (PD) to a
+    subset of each class can only raise its minimum, so the exact polytope
+    distance of a core set C (the points svm_coreset_pick takes from w) is an
+    upper bound on OPT; the direction z_C of that solution is a separating
+    direction of all the points only if no point outside C lies closer, and
+    its margin over all the points (Sec. 5's f) is a lower bound on OPT. Each
+    round adds the core set picked by z_C to C (an active set) until the
+    bounds are within 1 + eps or `rounds` rounds have run. The core-set
+    problem is solved by exact.pd_mdm to a gap of eps/10 of its value.
+    Returns (lb, ub, w_lb): the margin of the best direction found, the
+    smallest core-set distance, that direction."""
+    from .exact import pd_mdm
+    X, y = _prep(X, y)
+    C = np.zeros(X.shape[0], dtype=bool)
+    lb, ub, w_lb = 0.0, math.inf, None
+    w = np.asarray(w, dtype=np.float64)
+    for _ in range(rounds):
+        C |= svm_coreset_pick(X, y, w, K)
+        P, Q = X[C & (y > 0)], X[C & (y < 0)]
+        dist, mu, ga, _, _ = pd_mdm(P, Q, tol=eps / 10.0)
+        z = P.T @ mu - Q.T @ ga
+        ub = min(ub, dist)
+        m = svm_margin(X, y, z)
+        if m > lb:
+            lb, w_lb = m, z / math.sqrt(float(z @ z))
+        if ub <= (1.0 + eps) * lb:
+            break
+        w = z
+    return lb, ub, w_lb
+
+
 def svm_step(X, y, wbar, s1bar, s2bar, t, alpha, eta, rho, D, avg=None):
     """One iteration of the minimisation alpha-FTP (Sec. 3, Theorem 3) for SVM.
 
@@ -219,6 +270,12 @@ def svm_ftp(X, y, alpha, eta, rho, T, D, mode=MODE_FIXED, delta=1e-4, patience=1
     the FTP's own gap ub_best / f_best - 1 has not shrunk by the factor 0.8
     since the previous such poll (no check once eta <= 1/64). ub_best is the
     best of the per-iteration and the averaged Claim 8 values.
+
+    With cert["coreset"] (mode "coreset" of the search: reading 25), a poll at
+    which the search's iteration count cert["coreset"]["base"] + t has reached
+    cert["coreset"]["next"] also runs svm_coreset_bounds from the FTP's best
+    direction (wbar when no direction separates yet), folds its bounds into
+    f_best / w_best and ub_best, and doubles "next", before the test above.
     """
     X, y = _prep(X, y)
     d = X.shape[1]
@@ -256,6 +313,13 @@ def svm_ftp(X, y, alpha, eta, rho, T, D, mode=MODE_FIXED, delta=1e-4, patience=1
         wbar, s1bar, s2bar = rec["wbar_next"], rec["s1bar_next"], rec["s2bar_next"]
         t += 1
         if mode == MODE_CERTIFIED and t % cert["poll_every"] == 0:
+            cs = cert.get("coreset")
+            if cs is not None and cs["base"] + t >= cs["next"]:
+                lb_c, ub_c, w_c = svm_coreset_bounds(X, y, w_best if f_best > 0.0 else wbar, cert["eps"])
+                if lb_c > f_best:
+                    f_best, w_best = lb_c, w_c
+                ub_best = min(ub_best, ub_c)
+                cs["next"] *= 2
             if min(cert["ub"], ub_best) <= (1.0 + cert["eps"]) * max(cert["lb"], f_best):
                 outcome = OUT_CERTIFIED
                 break
@@ -286,10 +350,14 @@ def svm_solve(X, y, eps=1e-2, mode=MODE_PRACTICAL, max_iters=10**7, delta=1e-4,
     those or until the certificates close at a poll, and the loop ends when
     min(ub, U) <= (1+eps) lb or the budget is spent; eta defaults to 1 and
     upper_bound reports min(ub, U).
+
+    CORESET mode is CERTIFIED with the core-set certificates of reading 25:
+    at the polls where the search's iteration count first reaches 256, 512,
+    1024, ..., svm_coreset_bounds runs from the running FTP's best direction.
     """
-    if mode == MODE_CERTIFIED:
+    if mode in (MODE_CERTIFIED, MODE_CORESET):
         return _svm_solve_certified(X, y, eps, max_iters, max_steps, 1.0 if eta is None else float(eta),
-                                    poll_every)
+                                    poll_every, coreset=mode == MODE_CORESET)
     X, y = _prep(X, y)
     n = X.shape[0]
     D = svm_D(X)
@@ -322,16 +390,20 @@ def svm_solve(X, y, eps=1e-2, mode=MODE_PRACTICAL, max_iters=10**7, delta=1e-4,
             "iters": total, "steps": steps, "L": L, "U": U}
 
 
-def _svm_solve_certified(X, y, eps, max_iters, max_steps, eta, poll_every):
+def _svm_solve_certified(X, y, eps, max_iters, max_steps, eta, poll_every, coreset=False):
     X, y = _prep(X, y)
     D = svm_D(X)
     rho = svm_width(D)
     L, U = 0.0, 2.0 * D
     lb, ub, w_best = 0.0, math.inf, np.zeros(X.shape[1])
     total, steps = 0, []
+    cs = {"next": CORESET_FIRST, "base": 0} if coreset else None
     while min(ub, U) > (1.0 + eps) * lb and total < max_iters and len(steps) < max_steps:
         alpha = U - (U - L) / 3.0
         cert = {"lb": lb, "ub": min(ub, U), "eps": eps, "poll_every": poll_every}
+        if cs is not None:
+            cs["base"] = total
+            cert["coreset"] = cs
         res = svm_ftp(X, y, alpha, eta, rho, max_iters - total, D, mode=MODE_CERTIFIED, cert=cert)
         total += res["iters"]
         eta_used = eta

@@ -141,3 +141,52 @@ def test_solve_brackets_exact_polytope_distance():
         assert res["upper_bound"] >= opt * (1 - 1e-9)
         assert math.isclose(exact.svm_margin_of(P, Q, res["w"]), res["margin"], rel_tol=1e-9)
     assert res["margin"] >= 0.98 * opt
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_mdm_matches_bruteforce_polytope_distance(seed):
+    rng = np.random.default_rng(100 + seed)
+    d = int(rng.integers(2, 5))
+    P = rng.standard_normal((int(rng.integers(1, 7)), d)) + 1.5
+    Q = rng.standard_normal((int(rng.integers(1, 7)), d)) - 1.5
+    opt, _, _ = exact.pd_bruteforce(P, Q)
+    dist, mu, ga, gap, _ = exact.pd_mdm(P, Q, tol=1e-14)
+    assert abs(dist - opt) <= 1e-9 * max(opt, 1.0)
+    assert np.all(mu >= 0) and np.all(ga >= 0) and abs(mu.sum() - 1) < 1e-12 and abs(ga.sum() - 1) < 1e-12
+    z = P.T @ mu - Q.T @ ga
+    assert abs(math.sqrt(float(z @ z)) - dist) <= 1e-12 * max(dist, 1.0)
+    # the direction's margin never exceeds the distance (weak duality, Sec. 4.2)
+    assert exact.svm_margin_of(P, Q, z) <= dist * (1 + 1e-12)
+
+
+def test_coreset_bounds_bracket_the_optimum():
+    X, y = _inst(7, 6, 3, 8)
+    P, Q = X[y > 0], X[y < 0]
+    opt, _, _ = exact.pd_bruteforce(P, Q)
+    w0 = P.mean(axis=0) - Q.mean(axis=0)
+    # a core set holding every point: the bounds are the optimum itself
+    lb, ub, w = svm.svm_coreset_bounds(X, y, w0, eps=1e-9, K=100, rounds=1)
+    assert abs(ub - opt) <= 1e-8 * opt and abs(lb - opt) <= 1e-6 * opt
+    assert math.isclose(exact.svm_margin_of(P, Q, w), lb, rel_tol=1e-9)
+    # core sets of two points per class from a poor direction: still bounds
+    lb, ub, w = svm.svm_coreset_bounds(X, y, np.array([1.0, 0.0, 0.0]), eps=1e-3, K=2)
+    assert lb <= opt * (1 + 1e-9) <= ub * (1 + 2e-9)
+
+
+def test_coreset_pick_takes_the_points_nearest_the_hyperplane():
+    X = np.array([[3.0, 0], [1.0, 5], [2.0, -1], [-1.0, 0], [-4.0, 2], [-2.5, 1]])
+    y = np.array([1, 1, 1, -1, -1, -1], dtype=np.int8)
+    pick = svm.svm_coreset_pick(X, y, np.array([1.0, 0.0]), 2)
+    # y x^T w: P 3, 1, 2 -> 1, 2; Q 1, 4, 2.5 -> 1, 2.5
+    assert pick.tolist() == [False, True, True, True, False, True]
+
+
+def test_coreset_search_certifies_and_brackets():
+    for (n1, n2, d, seed) in [(6, 6, 2, 7), (5, 7, 3, 9)]:
+        X, y = _inst(n1, n2, d, seed)
+        P, Q = X[y > 0], X[y < 0]
+        opt, _, _ = exact.pd_bruteforce(P, Q)
+        res = svm.svm_solve(X, y, eps=1e-3, mode=svm.MODE_CORESET, max_iters=20000)
+        assert res["lower_bound"] <= opt * (1 + 1e-9) and res["upper_bound"] >= opt * (1 - 1e-9)
+        assert res["upper_bound"] <= (1 + 1e-3) * res["lower_bound"]
+        assert math.isclose(exact.svm_margin_of(P, Q, res["w"]), res["margin"], rel_tol=1e-9)
