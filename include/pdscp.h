@@ -62,6 +62,7 @@ typedef enum pdscp_status {
 #define PDSCP_MODE_PRACTICAL 0  /* Sec. 5 rules inside each alpha-FTP */
 #define PDSCP_MODE_THEORY 1     /* T_i iterations of Theorem 2/3 per FTP */
 #define PDSCP_MODE_CERTIFIED 2  /* proven conclusions only; ends on the certificates (see ses_solve) */
+#define PDSCP_MODE_CORESET 3    /* SVM: CERTIFIED plus core-set certificates (see svm_solve); SES: CERTIFIED */
 
 /* Largest supported dimension d. */
 #define PDSCP_MAX_D 1024
@@ -144,6 +145,24 @@ int32_t pdscp_version(void);
 
 /* Message describing the last failing call on this thread ("" if none). */
 const char* pdscp_last_error(void);
+
+/*
+ * Exact polytope distance (Eq. PD, Sec. 4.2) of two small point sets on the
+ * host: min ||P^T mu - Q^T gamma|| over mu, gamma in the simplices, P_host
+ * nP x d and Q_host nQ x d row-major doubles (caller-owned). The solver of the
+ * core-set certificates of svm_solve (PDSCP_MODE_CORESET): a primal
+ * active-set method (the affine least-distance problem on the support solved
+ * exactly, the most violating point added, points whose weight reaches zero
+ * dropped) until z.z - (min_i p_i.z - max_j q_j.z) <= tol z.z or max_iter
+ * additions. Writes the weights (mu_host: nP, gamma_host: nQ, in the
+ * simplices) and *dist_host = ||P^T mu - Q^T gamma||, an upper bound on the
+ * distance whatever the convergence. Synchronous, host only, no device work.
+ * PDSCP_ERR_INVALID_ARG for null pointers, empty sets, d < 1, tol < 0 or
+ * max_iter < 1.
+ */
+pdscp_status pdscp_polytope_distance(const double* P_host, int32_t nP, const double* Q_host, int32_t nQ,
+                                     int32_t d, double tol, int32_t max_iter, double* mu_host,
+                                     double* gamma_host, double* dist_host);
 
 /*
  * Bytes of device workspace needed by pdscp_bounds / mwu_step / the solves for
@@ -311,6 +330,17 @@ pdscp_status ses_solve(const void* pts_dev, int32_t dtype, const float* radii_de
  * roles mirrored: in CERTIFIED mode separation gives U = alpha_i, a margin
  * f > alpha_i gives L = f, the FTP's own gap is its Claim 8 bound over its
  * best margin, and report.upper_bound is min(ub, U).
+ * PDSCP_MODE_CORESET is CERTIFIED plus core-set certificates (not in the
+ * paper; built on Eq. PD): at the polls where the search's iteration count
+ * first reaches 256, 512, 1024, ..., the 512 points of each class nearest
+ * the hyperplane of the running FTP's best direction form a core set whose
+ * exact polytope distance (solved on the host, pdscp_polytope_distance) is
+ * an upper bound on OPT, and whose solution direction, projected on every
+ * point on the device, gives a margin, a lower bound; up to four rounds add
+ * the core set of each new direction. The bounds join the FTP's own; the
+ * returned direction is the one of the best margin. The workspace then also
+ * holds the projections of the n points and the core set's rows (see
+ * pdscp_workspace_size, which counts them for SVM).
  */
 pdscp_status svm_solve(const void* X_dev, int32_t dtype, const int8_t* labels_dev,
                        int64_t n, int32_t d, const pdscp_options* opts,

@@ -18,7 +18,7 @@ STATUS_NAMES = {
 SES, SVM = 0, 1
 F32, BF16 = 0, 1
 RULES_NONE, RULES_PRACTICAL = 0, 1
-MODE_PRACTICAL, MODE_THEORY, MODE_CERTIFIED = 0, 1, 2
+MODE_PRACTICAL, MODE_THEORY, MODE_CERTIFIED, MODE_CORESET = 0, 1, 2, 3
 OUT_RUNNING, OUT_SEPARATED, OUT_BEAT_ALPHA, OUT_STALLED = 0, 1, 2, 3
 MAX_D = 1024
 
@@ -50,6 +50,7 @@ assert ctypes.sizeof(StepOut) == 72
 # name -> (restype, argtypes); every entry point declared in include/pdscp.h
 SIGNATURES = {
     "pdscp_version": (c_i32, []),
+    "pdscp_polytope_distance": (c_i32, [c_vp, c_i32, c_vp, c_i32, c_i32, c_dbl, c_i32, c_vp, c_vp, c_vp]),
     "pdscp_last_error": (ctypes.c_char_p, []),
     "pdscp_workspace_size": (c_i32, [c_i32, c_i64, c_i32, ctypes.POINTER(c_sz)]),
     "pdscp_state_size": (c_i32, [c_i32, c_i32, ctypes.POINTER(c_sz)]),

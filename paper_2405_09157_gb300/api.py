@@ -445,7 +445,8 @@ class MWU:
 
 
 def _options(eps, mode, max_iters, poll_every, max_steps, eta, delta, patience):
-    m = {"practical": _ffi.MODE_PRACTICAL, "theory": _ffi.MODE_THEORY, "certified": _ffi.MODE_CERTIFIED}[mode]
+    m = {"practical": _ffi.MODE_PRACTICAL, "theory": _ffi.MODE_THEORY, "certified": _ffi.MODE_CERTIFIED,
+         "coreset": _ffi.MODE_CORESET}[mode]
     return _ffi.Options(eps, delta, patience, m, max_iters, poll_every, max_steps, eta or 0.0)
 
 
@@ -485,7 +486,9 @@ def svm_solve(X, labels, eps=1e-3, mode="practical", max_iters=1_000_000, poll_e
     mode as in ses_solve, roles mirrored: "value" = "lower_bound" is the margin
     of the returned direction, "upper_bound" the best Claim 8 value (per
     iteration or averaged); "certified" ends when upper_bound <= (1 + eps)
-    lower_bound."""
+    lower_bound; "coreset" is "certified" plus the core-set certificates
+    (exact polytope distance of the 512 points per class nearest the best
+    hyperplane, checked at 256, 512, 1024, ... iterations of the search)."""
     n, d, dt = _points(X)
     if labels is None or labels.numel() != n:
         raise ValueError("labels must be an int8 CUDA tensor of n entries in {+1, -1}")
@@ -499,6 +502,27 @@ def svm_solve(X, labels, eps=1e-3, mode="practical", max_iters=1_000_000, poll_e
     if st != _ffi.PDSCP_OK and (raise_on_budget or st != 5):
         check(st, "svm_solve")
     return w, _report(rep)
+
+
+def polytope_distance(P, Q, tol=1e-9, max_iter=None):
+    """Exact polytope distance of two small point sets (Eq. PD), the host
+    solver of the core-set certificates: P (nP x d), Q (nQ x d) array-likes,
+    taken as float64. Returns (dist, mu, gamma) with mu, gamma the weights on
+    the two simplices."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    if P.ndim != 2 or Q.ndim != 2 or P.shape[1] != Q.shape[1]:
+        raise ValueError("P and Q must be 2-D with the same number of columns")
+    nP, d = P.shape
+    nQ = Q.shape[0]
+    mu = np.zeros(max(nP, 1))
+    ga = np.zeros(max(nQ, 1))
+    dist = ctypes.c_double(0.0)
+    it = 4 * (nP + nQ) + 64 if max_iter is None else int(max_iter)
+    st = load().pdscp_polytope_distance(P.ctypes.data, nP, Q.ctypes.data, nQ, d, float(tol), it,
+                                        mu.ctypes.data, ga.ctypes.data, ctypes.byref(dist))
+    check(st, "pdscp_polytope_distance")
+    return dist.value, mu[:nP], ga[:nQ]
 
 
 # ------------------------------------------------------------------ batched SES

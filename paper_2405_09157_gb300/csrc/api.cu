@@ -9,9 +9,11 @@
 #include <cstring>
 #include <atomic>
 #include <string>
+#include <vector>
 
 #include "bounds_kernel.cuh"
 #include "bwd_kernel.cuh"
+#include "coreset.cuh"
 #include "dispatch.cuh"
 #include "ses_kernel.cuh"
 #include "svm_kernel.cuh"
@@ -204,7 +206,8 @@ pdscp_status pdscp_workspace_size(int32_t problem, int64_t n, int32_t d, size_t*
   if (problem != PDSCP_SES && problem != PDSCP_SVM) return fail(PDSCP_ERR_INVALID_ARG, "unknown problem %d", problem);
   if (d < 1 || d > PDSCP_MAX_D) return fail(PDSCP_ERR_NOT_IMPLEMENTED, "d=%d outside [1, %d]", d, PDSCP_MAX_D);
   if (n < 1) return fail(PDSCP_ERR_INVALID_ARG, "n must be >= 1");
-  *bytes = layout(problem, d).total;
+  const size_t base = layout(problem, d).total;
+  *bytes = problem == PDSCP_SVM ? round256(base) + coreset_bytes(n, d) : base;
   return PDSCP_OK;
 }
 
@@ -617,12 +620,24 @@ double own_gap(int problem, const StateHdr& h) {
   return h.best_f > 0.0 ? h.ub_best / h.best_f - 1.0 : INFINITY;
 }
 
+// Core-set certificates of the certified SVM search (PDSCP_MODE_CORESET).
+// next: the search's iteration count of the next check (256, then doubling,
+// kept across FTPs); base: the search's count when this FTP began; lb, ub,
+// w: the best bounds this FTP's checks found (lb with its unit direction).
+struct CoresetHook {
+  int64_t next = kCoresetFirst, base = 0;
+  double lb = 0.0, ub = INFINITY;
+  std::vector<double> w;
+  void* ws = nullptr;  // coreset_bytes(n, d) bytes of the solve's workspace
+};
+
 pdscp_status check_opts(const pdscp_options* o) {
   if (!o) return fail(PDSCP_ERR_INVALID_ARG, "options pointer is null");
   if (!(o->eps > 0.0) || !std::isfinite(o->eps)) return fail(PDSCP_ERR_INVALID_ARG, "eps must be > 0");
   if (!(o->delta >= 0.0)) return fail(PDSCP_ERR_INVALID_ARG, "delta must be >= 0");
   if (o->patience < 1) return fail(PDSCP_ERR_INVALID_ARG, "patience must be >= 1");
-  if (o->mode != PDSCP_MODE_PRACTICAL && o->mode != PDSCP_MODE_THEORY && o->mode != PDSCP_MODE_CERTIFIED)
+  if (o->mode != PDSCP_MODE_PRACTICAL && o->mode != PDSCP_MODE_THEORY && o->mode != PDSCP_MODE_CERTIFIED &&
+      o->mode != PDSCP_MODE_CORESET)
     return fail(PDSCP_ERR_INVALID_ARG, "unknown mode");
   if (o->max_iters < 1) return fail(PDSCP_ERR_INVALID_ARG, "max_iters must be >= 1");
   if (o->poll_every < 1 || o->poll_every > kRing) return fail(PDSCP_ERR_INVALID_ARG, "poll_every outside [1, %d]", kRing);
@@ -641,7 +656,7 @@ pdscp_status check_opts(const pdscp_options* o) {
 pdscp_status run_ftp(int problem, const void* pts, int dtype, const float* radii, const int8_t* labels, int64_t n,
                      int d, double alpha, double eta_over_rho, double D, int rules, const pdscp_options* o,
                      int64_t budget, void* ws, size_t ws_bytes, cudaStream_t s, FtpResult* res,
-                     const CertCheck& cert = CertCheck{false, 0.0, 0.0, 0.0, 1.0}) {
+                     const CertCheck& cert = CertCheck{false, 0.0, 0.0, 0.0, 1.0}, CoresetHook* cs = nullptr) {
   const Layout L = layout(problem, d);
   void* state = reinterpret_cast<char*>(ws) + L.state;
   pdscp_step_out* ring = reinterpret_cast<pdscp_step_out*>(reinterpret_cast<char*>(ws) + L.ring);
@@ -672,12 +687,45 @@ pdscp_status run_ftp(int problem, const void* pts, int dtype, const float* radii
       stopped = true;
       break;
     }
-    if (cert_closed(problem, cert, h)) {
+    if (cs && cs->base + h.t >= cs->next) {
+      // the check starts from the FTP's best direction so far: a core-set
+      // direction of this FTP, else the device's best, else the mean
+      std::vector<double> w0(d);
+      if (cs->lb > 0.0 && cs->lb >= h.best_f) {
+        w0 = cs->w;
+      } else {
+        float* tmp = reinterpret_cast<float*>(cs->ws);
+        std::vector<float> wf(d);
+        st = mwu_state_read(problem, d, state, h.best_f > 0.0 ? nullptr : tmp, h.best_f > 0.0 ? tmp : nullptr,
+                            (pdscp_stream)s);
+        if (st != PDSCP_OK) return st;
+        e = cudaMemcpyAsync(wf.data(), tmp, (size_t)d * sizeof(float), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "core-set direction read");
+        for (int j = 0; j < d; ++j) w0[j] = wf[j];
+      }
+      double lbc = 0.0, ubc = INFINITY;
+      std::vector<double> wc;
+      st = svm_coreset_check(pts, dtype, labels, n, d, w0.data(), cert.eps, cs->ws, s, &lbc, &ubc, wc);
+      if (st != PDSCP_OK) return st;
+      if (lbc > cs->lb) {
+        cs->lb = lbc;
+        cs->w = wc;
+      }
+      cs->ub = std::min(cs->ub, ubc);
+      cs->next *= 2;
+    }
+    StateHdr hc = h;  // the core-set bounds join the FTP's own
+    if (cs) {
+      hc.best_f = std::max(hc.best_f, cs->lb);
+      hc.ub_best = std::min(hc.ub_best, cs->ub);
+    }
+    if (cert_closed(problem, cert, hc)) {
       res->certified = true;
       break;
     }
     if (cert.on && (double)h.t >= next_check) {
-      const double gap = own_gap(problem, h);
+      const double gap = own_gap(problem, hc);
       if (gap > kCertShrink * last_gap) {
         res->stuck = true;
         break;
@@ -757,7 +805,7 @@ pdscp_status ses_solve(const void* pts, int32_t dtype, const float* radii, int64
   int steps = 0;
   bool have_center = false;
   const double eps = o->eps;
-  const bool certified = o->mode == PDSCP_MODE_CERTIFIED;
+  const bool certified = o->mode == PDSCP_MODE_CERTIFIED || o->mode == PDSCP_MODE_CORESET;
   const int rules = o->mode == PDSCP_MODE_THEORY ? PDSCP_RULES_NONE : PDSCP_RULES_PRACTICAL;
   // CERTIFIED: only proven conclusions move the range (separation: OPT > alpha;
   // f < alpha: OPT < alpha), every FTP also ends when the certificates close,
@@ -846,9 +894,13 @@ pdscp_status svm_solve(const void* X, int32_t dtype, const int8_t* labels, int64
   if (!labels || !ws || !w_out || !rep) return fail(PDSCP_ERR_INVALID_ARG, "null labels/workspace/w/report pointer");
   if (!aligned(ws, 256)) return fail(PDSCP_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
   const Layout L = layout(PDSCP_SVM, d);
-  if (ws_bytes < L.total) return fail(PDSCP_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws_bytes, L.total);
+  const bool use_cs = o->mode == PDSCP_MODE_CORESET;
+  const size_t need = use_cs ? round256(L.total) + coreset_bytes(n, d) : L.total;
+  if (ws_bytes < need) return fail(PDSCP_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws_bytes, need);
   cudaStream_t s = (cudaStream_t)stream;
   memset(rep, 0, sizeof(*rep));
+  CoresetHook cs;
+  cs.ws = reinterpret_cast<char*>(ws) + round256(L.total);
   double* Ddev = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + L.dval);
   if ((st = mwu_state_init(PDSCP_SVM, X, dtype, n, d, 0, 0.0, 1, reinterpret_cast<char*>(ws) + L.state, ws, ws_bytes,
                            stream)) != PDSCP_OK)
@@ -867,7 +919,7 @@ pdscp_status svm_solve(const void* X, int32_t dtype, const int8_t* labels, int64
   int steps = 0;
   bool have_w = false;
   const double eps = o->eps;
-  const bool certified = o->mode == PDSCP_MODE_CERTIFIED;
+  const bool certified = o->mode == PDSCP_MODE_CERTIFIED || o->mode == PDSCP_MODE_CORESET;
   const int rules = o->mode == PDSCP_MODE_THEORY ? PDSCP_RULES_NONE : PDSCP_RULES_PRACTICAL;
   // CERTIFIED (as in ses_solve): separation gives U = alpha, f > alpha gives
   // L = f; the loop ends on min(ub, U) <= (1+eps) lb.
@@ -877,17 +929,28 @@ pdscp_status svm_solve(const void* X, int32_t dtype, const int8_t* labels, int64
     const double eta = eta_c;
     FtpResult r;
     const CertCheck c{true, lb, std::min(ub, Up), eps, eta};
+    cs.base = total;
+    cs.lb = 0.0;
+    cs.ub = INFINITY;
     if ((st = run_ftp(PDSCP_SVM, X, dtype, nullptr, labels, n, d, alpha, eta / rho, D, rules, o, o->max_iters - total,
-                      ws, ws_bytes, s, &r, c)) != PDSCP_OK)
+                      ws, ws_bytes, s, &r, c, use_cs ? &cs : nullptr)) != PDSCP_OK)
       return st;
     total += r.iters;
-    if (r.hdr.best_f > lb) {
+    if (cs.lb > lb && cs.lb > r.hdr.best_f) {  // a core-set direction has the best margin
+      lb = cs.lb;
+      std::vector<float> wf(cs.w.begin(), cs.w.end());
+      e = cudaMemcpyAsync(w_out, wf.data(), sizeof(float) * d, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // wf is pageable and about to go
+      if (e != cudaSuccess) return cuda_fail(e, "core-set direction write");
+      have_w = true;
+    } else if (r.hdr.best_f > lb) {
       lb = r.hdr.best_f;
       if ((st = mwu_state_read(PDSCP_SVM, d, reinterpret_cast<char*>(ws) + L.state, nullptr, w_out, stream)) != PDSCP_OK)
         return st;
       have_w = true;
     }
     if (r.hdr.ub_best < ub) ub = r.hdr.ub_best;
+    if (cs.ub < ub) ub = cs.ub;
     const int oc = r.hdr.stopped ? r.hdr.outcome : PDSCP_OUT_RUNNING;
     if (oc == PDSCP_OUT_SEPARATED) Up = std::min(Up, alpha);
     if (r.stuck) eta_c *= 0.5;

@@ -1,0 +1,538 @@
+// Core-set certificates for the certified SVM search (a reading beyond the
+// paper, built on Eq. (PD) and the core-set view of PD it cites in Sec. 4.2).
+//
+// Restricting Eq. (PD) to subsets of the two classes can only raise its
+// minimum, so the exact polytope distance of a core set is an upper bound on
+// OPT; the direction of that solution, evaluated on every point (the margin f
+// of Sec. 5), is a lower bound. The core set is read off the MWU: in each
+// class the K points nearest the hyperplane of the FTP's best direction w
+// (smallest y_i x_i^T w). This file holds
+//   * the exact solver of the small problem (host, FP64): a primal
+//     active-set method (exact affine least-distance solves on the support,
+//     the most violating point added, points leaving the support on the way
+//     to the affine optimum dropped), pd_active_set;
+//   * the device kernels that project every point on a direction, pick the
+//     core set by a threshold per class, and gather its rows;
+//   * svm_coreset_check, which the certified search of svm_solve calls.
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "coreset.cuh"
+#include "dispatch.cuh"
+
+namespace pdscp {
+
+// ---------------------------------------------------------------------------
+// Host solver: polytope distance min ||P^T mu - Q^T gamma|| over the two
+// simplices (Eq. PD), P: nP x d, Q: nQ x d row-major (FP64).
+// ---------------------------------------------------------------------------
+namespace {
+
+// Solves the (k + 2) x (k + 2) system M x = r in place by Gaussian
+// elimination with partial pivoting. Returns false if a pivot vanishes.
+bool solve_dense(std::vector<double>& M, std::vector<double>& r, int m) {
+  for (int c = 0; c < m; ++c) {
+    int piv = c;
+    double best = std::fabs(M[(size_t)c * m + c]);
+    for (int i = c + 1; i < m; ++i) {
+      const double v = std::fabs(M[(size_t)i * m + c]);
+      if (v > best) {
+        best = v;
+        piv = i;
+      }
+    }
+    if (!(best > 1e-300)) return false;
+    if (piv != c) {
+      for (int j = 0; j < m; ++j) std::swap(M[(size_t)c * m + j], M[(size_t)piv * m + j]);
+      std::swap(r[c], r[piv]);
+    }
+    const double inv = 1.0 / M[(size_t)c * m + c];
+    for (int i = c + 1; i < m; ++i) {
+      const double f = M[(size_t)i * m + c] * inv;
+      if (f == 0.0) continue;
+      for (int j = c; j < m; ++j) M[(size_t)i * m + j] -= f * M[(size_t)c * m + j];
+      r[i] -= f * r[c];
+    }
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    double acc = r[i];
+    for (int j = i + 1; j < m; ++j) acc -= M[(size_t)i * m + j] * r[j];
+    r[i] = acc / M[(size_t)i * m + i];
+  }
+  return true;
+}
+
+struct ActiveSet {
+  const double* P;
+  const double* Q;
+  int nP, nQ, d;
+  // candidate k: a_k = P[k] (class 0) for k < nP, a_k = -Q[k - nP] (class 1) otherwise
+  double dot_a(int k, const double* v) const {
+    const double* x = k < nP ? P + (size_t)k * d : Q + (size_t)(k - nP) * d;
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) s += x[j] * v[j];
+    return k < nP ? s : -s;
+  }
+  double dot_aa(int k, int l) const {
+    const double* x = k < nP ? P + (size_t)k * d : Q + (size_t)(k - nP) * d;
+    const double* u = l < nP ? P + (size_t)l * d : Q + (size_t)(l - nP) * d;
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) s += x[j] * u[j];
+    return ((k < nP) == (l < nP)) ? s : -s;
+  }
+  void axpy_a(int k, double c, double* z) const {
+    const double* x = k < nP ? P + (size_t)k * d : Q + (size_t)(k - nP) * d;
+    const double cc = k < nP ? c : -c;
+    for (int j = 0; j < d; ++j) z[j] += cc * x[j];
+  }
+};
+
+}  // namespace
+
+int pd_active_set(const double* P, int nP, const double* Q, int nQ, int d, double tol, int max_iter, double* mu,
+                  double* ga, double* z, double* gap_out) {
+  ActiveSet A{P, Q, nP, nQ, d};
+  const int m = nP + nQ;
+  std::vector<double> zc(d, 0.0), cen(d, 0.0);
+  for (int i = 0; i < nP; ++i)
+    for (int j = 0; j < d; ++j) cen[j] += P[(size_t)i * d + j] / nP;
+  for (int i = 0; i < nQ; ++i)
+    for (int j = 0; j < d; ++j) cen[j] -= Q[(size_t)i * d + j] / nQ;
+  // start: the pair nearest along the difference of the centroids
+  int s0 = 0, s1 = nP;
+  double b0 = INFINITY, b1 = INFINITY;
+  for (int k = 0; k < m; ++k) {
+    const double v = A.dot_a(k, cen.data());
+    if (k < nP && v < b0) b0 = v, s0 = k;
+    if (k >= nP && v < b1) b1 = v, s1 = k;
+  }
+  std::vector<int> S = {s0, s1};       // support (candidate indices)
+  std::vector<double> c = {1.0, 1.0};  // weights on the support
+  std::vector<double> G = {A.dot_aa(s0, s0), A.dot_aa(s0, s1), A.dot_aa(s1, s0), A.dot_aa(s1, s1)};
+  std::vector<char> in(m, 0);
+  in[s0] = in[s1] = 1;
+  auto rebuild_z = [&]() {
+    std::fill(zc.begin(), zc.end(), 0.0);
+    for (size_t i = 0; i < S.size(); ++i) A.axpy_a(S[i], c[i], zc.data());
+  };
+  auto remove_at = [&](size_t pos) {
+    const size_t k = S.size();
+    std::vector<double> G2;
+    G2.reserve((k - 1) * (k - 1));
+    for (size_t i = 0; i < k; ++i) {
+      if (i == pos) continue;
+      for (size_t j = 0; j < k; ++j)
+        if (j != pos) G2.push_back(G[i * k + j]);
+    }
+    G.swap(G2);
+    in[S[pos]] = 0;
+    S.erase(S.begin() + pos);
+    c.erase(c.begin() + pos);
+  };
+  rebuild_z();
+  double gap = INFINITY;
+  int it = 0;
+  for (; it < max_iter; ++it) {
+    // optimality: z.z = lam0 + lam1 with lam_c the weighted projection of
+    // class c; the margin of z times |z| is min_P a.z + min_Q a.z
+    double zz = 0.0;
+    for (int j = 0; j < d; ++j) zz += zc[j] * zc[j];
+    double lam[2] = {0.0, 0.0};
+    for (size_t i = 0; i < S.size(); ++i) lam[S[i] < nP ? 0 : 1] += c[i] * A.dot_a(S[i], zc.data());
+    double mn[2] = {INFINITY, INFINITY};
+    int arg[2] = {-1, -1};
+    for (int k = 0; k < m; ++k) {
+      const double v = A.dot_a(k, zc.data());
+      const int cl = k < nP ? 0 : 1;
+      if (v < mn[cl]) mn[cl] = v, arg[cl] = k;
+    }
+    gap = zz - (mn[0] + mn[1]);
+    if (gap <= tol * zz) break;
+    const int cl = (lam[0] - mn[0] >= lam[1] - mn[1]) ? 0 : 1;
+    const int add = arg[cl];
+    if (add < 0 || in[add]) break;  // no progress possible in this arithmetic
+    // add with weight 0
+    const size_t k = S.size();
+    std::vector<double> G2((k + 1) * (k + 1));
+    for (size_t i = 0; i < k; ++i)
+      for (size_t j = 0; j < k; ++j) G2[i * (k + 1) + j] = G[i * k + j];
+    for (size_t i = 0; i < k; ++i) G2[i * (k + 1) + k] = G2[k * (k + 1) + i] = A.dot_aa(S[i], add);
+    G2[k * (k + 1) + k] = A.dot_aa(add, add);
+    G.swap(G2);
+    S.push_back(add);
+    c.push_back(0.0);
+    in[add] = 1;
+    // minor cycles: move toward the affine optimum on the support, dropping
+    // points whose weight reaches zero on the way
+    bool stalled = false;
+    for (int minor = 0; minor < 4 * m + 8; ++minor) {
+      const int ks = (int)S.size(), ms = ks + 2;
+      std::vector<double> M((size_t)ms * ms, 0.0), r(ms, 0.0);
+      for (int i = 0; i < ks; ++i) {
+        for (int j = 0; j < ks; ++j) M[(size_t)i * ms + j] = G[(size_t)i * ks + j];
+        const int cl2 = S[i] < nP ? 0 : 1;
+        M[(size_t)i * ms + ks + cl2] = 1.0;
+        M[(size_t)(ks + cl2) * ms + i] = 1.0;
+      }
+      r[ks] = r[ks + 1] = 1.0;
+      if (!solve_dense(M, r, ms)) {
+        stalled = true;
+        break;
+      }
+      bool all_pos = true;
+      for (int i = 0; i < ks; ++i)
+        if (!(r[i] > 0.0)) all_pos = false;
+      if (all_pos) {
+        for (int i = 0; i < ks; ++i) c[i] = r[i];
+        break;
+      }
+      // largest step theta in [0, 1] keeping c + theta (r - c) >= 0
+      double theta = 1.0;
+      int hit = -1;
+      for (int i = 0; i < ks; ++i)
+        if (r[i] <= 0.0 && c[i] - r[i] > 0.0) {
+          const double th = c[i] / (c[i] - r[i]);
+          if (th < theta) theta = th, hit = i;
+        }
+      for (int i = 0; i < ks; ++i) c[i] += theta * (r[i] - c[i]);
+      if (hit >= 0) c[hit] = 0.0;
+      bool removed = false;
+      for (int i = ks - 1; i >= 0; --i) {
+        const int cl2 = S[i] < nP ? 0 : 1;
+        int others = 0;
+        for (int j = 0; j < ks; ++j)
+          if (j != i && (S[j] < nP ? 0 : 1) == cl2) ++others;
+        if (c[i] <= 0.0 && others > 0) {
+          remove_at((size_t)i);
+          removed = true;
+        }
+      }
+      if (!removed) {
+        stalled = true;
+        break;
+      }
+    }
+    rebuild_z();
+    if (stalled || !in[add]) break;  // the point just added left again: no progress in this arithmetic
+  }
+  // weights on the two simplices (clamped, renormalised) and the final z
+  double s0w = 0.0, s1w = 0.0;
+  for (size_t i = 0; i < S.size(); ++i) {
+    if (c[i] < 0.0) c[i] = 0.0;
+    (S[i] < nP ? s0w : s1w) += c[i];
+  }
+  std::fill(mu, mu + nP, 0.0);
+  std::fill(ga, ga + nQ, 0.0);
+  for (size_t i = 0; i < S.size(); ++i) {
+    if (S[i] < nP) mu[S[i]] = s0w > 0.0 ? c[i] / s0w : 0.0;
+    else ga[S[i] - nP] = s1w > 0.0 ? c[i] / s1w : 0.0;
+  }
+  std::fill(z, z + d, 0.0);
+  for (int i = 0; i < nP; ++i)
+    if (mu[i] > 0.0)
+      for (int j = 0; j < d; ++j) z[j] += mu[i] * P[(size_t)i * d + j];
+  for (int i = 0; i < nQ; ++i)
+    if (ga[i] > 0.0)
+      for (int j = 0; j < d; ++j) z[j] -= ga[i] * Q[(size_t)i * d + j];
+  if (gap_out) *gap_out = gap;
+  return it;
+}
+
+}  // namespace pdscp
+
+// ---------------------------------------------------------------------------
+// Device side: projections, the per-class threshold pick, row gathering.
+// ---------------------------------------------------------------------------
+namespace pdscp {
+
+namespace {
+
+// order-preserving images of floats as unsigned ints (atomic min / max)
+__device__ __forceinline__ unsigned int f2o(float v) {
+  const unsigned int b = __float_as_uint(v);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__host__ __device__ inline float o2f(unsigned int b) {
+  b = (b & 0x80000000u) ? (b & 0x7fffffffu) : ~b;
+  float f;
+  memcpy(&f, &b, sizeof(f));
+  return f;
+}
+
+// s_i = y_i x_i . w for every row, one warp per row (rows strided over the
+// grid); mm[0..3] = images of min_P s, max_P s, min_Q s, max_Q s.
+template <typename T>
+__global__ void __launch_bounds__(256) svm_project_kernel(const T* X, const int8_t* y, int64_t n, int d,
+                                                          const float* w, float* s, unsigned int* mm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float lo[2] = {INFINITY, INFINITY}, hi[2] = {-INFINITY, -INFINITY};
+  for (int64_t i = wid; i < n; i += nw) {
+    const T* row = X + i * d;
+    float acc = 0.f;
+    for (int j = lane; j < d; j += 32) acc = fmaf(elem_to_float<T>(row + j), __ldg(w + j), acc);
+    acc = warp_sum(acc);
+    const bool pos = __ldg(y + i) > 0;
+    const float v = pos ? acc : -acc;
+    if (lane == 0) s[i] = v;
+    const int c = pos ? 0 : 1;
+    lo[c] = fminf(lo[c], v);
+    hi[c] = fmaxf(hi[c], v);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (lo[c] <= hi[c]) {
+        atomicMin(mm + 2 * c, f2o(lo[c]));
+        atomicMax(mm + 2 * c + 1, f2o(hi[c]));
+      }
+    }
+  }
+}
+
+// cnt[c] = number of rows of class c (0: P, 1: Q) with s <= th[c]
+__global__ void __launch_bounds__(256) count_le_kernel(const float* s, const int8_t* y, int64_t n, float thP,
+                                                       float thQ, unsigned long long* cnt) {
+  unsigned int a = 0, b = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const bool pos = __ldg(y + i) > 0;
+    const float v = s[i];
+    if (pos) a += v <= thP ? 1u : 0u;
+    else b += v <= thQ ? 1u : 0u;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (a) atomicAdd(cnt, (unsigned long long)a);
+    if (b) atomicAdd(cnt + 1, (unsigned long long)b);
+  }
+}
+
+// the indices of rows with s <= th[c], appended per class (at most cap each;
+// pos[c] counts them all)
+__global__ void __launch_bounds__(256) select_le_kernel(const float* s, const int8_t* y, int64_t n, float thP,
+                                                        float thQ, int* idx, int cap, unsigned int* pos) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = __ldg(y + i) > 0 ? 0 : 1;
+    if (s[i] <= (c == 0 ? thP : thQ)) {
+      const unsigned int k = atomicAdd(pos + c, 1u);
+      if (k < (unsigned int)cap) idx[(size_t)c * cap + k] = (int)i;
+    }
+  }
+}
+
+// rows idx[0..k) of X as float32 into out (k x d)
+template <typename T>
+__global__ void __launch_bounds__(256) gather_rows_kernel(const T* X, const int* idx, int k, int d, float* out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)k * d;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / d), j = (int)(e % d);
+    out[e] = elem_to_float<T>(X + (int64_t)idx[r] * d + j);
+  }
+}
+
+size_t r256c(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct CsLayout {
+  size_t s, mm, cnt, pos, sel, gidx, rows, w, total;
+};
+CsLayout cs_layout(int64_t n, int d) {
+  CsLayout L;
+  const size_t cap = (size_t)2 * kCoresetK;  // selection cap per class (threshold overshoot)
+  const size_t kmax = (size_t)2 * kCoresetMaxPerClass;
+  L.s = 0;
+  L.mm = r256c((size_t)n * sizeof(float));
+  L.cnt = L.mm + 256;
+  L.pos = L.cnt + 256;
+  L.sel = L.pos + 256;
+  L.gidx = L.sel + r256c(2 * cap * sizeof(int));
+  L.rows = L.gidx + r256c(kmax * sizeof(int));
+  L.w = L.rows + r256c(kmax * (size_t)d * sizeof(float));
+  L.total = L.w + r256c((size_t)d * sizeof(float));
+  return L;
+}
+
+template <typename T>
+cudaError_t launch_project(const void* X, const int8_t* y, int64_t n, int d, const float* w, float* s,
+                           unsigned int* mm, cudaStream_t st) {
+  const unsigned int init[4] = {0xffffffffu, 0u, 0xffffffffu, 0u};
+  cudaError_t e = cudaMemcpyAsync(mm, init, sizeof(init), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  const int grid = device_sm_count() * 8;
+  svm_project_kernel<T><<<grid, 256, 0, st>>>(reinterpret_cast<const T*>(X), y, n, d, w, s, mm);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t coreset_bytes(int64_t n, int d) { return cs_layout(n, d).total; }
+
+pdscp_status svm_coreset_check(const void* X, int dtype, const int8_t* y, int64_t n, int d, const double* w0,
+                               double eps, void* ws, cudaStream_t st, double* lb, double* ub,
+                               std::vector<double>& w_lb) {
+  const CsLayout L = cs_layout(n, d);
+  char* base = reinterpret_cast<char*>(ws);
+  float* s = reinterpret_cast<float*>(base + L.s);
+  unsigned int* mm = reinterpret_cast<unsigned int*>(base + L.mm);
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(base + L.cnt);
+  unsigned int* pos = reinterpret_cast<unsigned int*>(base + L.pos);
+  int* sel = reinterpret_cast<int*>(base + L.sel);
+  int* gidx = reinterpret_cast<int*>(base + L.gidx);
+  float* rows = reinterpret_cast<float*>(base + L.rows);
+  float* wdev = reinterpret_cast<float*>(base + L.w);
+  const int cap = 2 * kCoresetK;
+  const int grid = device_sm_count() * 4;
+  std::vector<float> wf(d);
+  std::vector<double> w(w0, w0 + d);
+  std::vector<int> core[2];  // the core set, sorted row indices per class
+  *lb = 0.0;
+  *ub = INFINITY;
+  w_lb.assign(d, 0.0);
+  auto fail_cuda = [](cudaError_t, const char* what) { return report_error(PDSCP_ERR_CUDA, what); };
+  // projections of every point on w (unit norm taken by the caller's use of
+  // the margin: here only their order matters, and min_P s + min_Q s)
+  auto project = [&](const std::vector<double>& v, unsigned int* mm_host) -> cudaError_t {
+    double nv = 0.0;
+    for (int j = 0; j < d; ++j) nv += v[j] * v[j];
+    nv = nv > 0.0 ? 1.0 / std::sqrt(nv) : 0.0;
+    for (int j = 0; j < d; ++j) wf[j] = (float)(v[j] * nv);
+    cudaError_t e = cudaMemcpyAsync(wdev, wf.data(), (size_t)d * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = dtype == PDSCP_F32 ? launch_project<float>(X, y, n, d, wdev, s, mm, st)
+                             : launch_project<__nv_bfloat16>(X, y, n, d, wdev, s, mm, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mm_host, mm, 4 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+  };
+  unsigned int mmh[4];
+  cudaError_t e = project(w, mmh);
+  if (e != cudaSuccess) return fail_cuda(e, "coreset: projection");
+  std::vector<float> rowsh;
+  std::vector<double> Pd, Qd, mu, ga, z(d);
+  for (int round = 0; round < kCoresetRounds; ++round) {
+    // per class: a threshold taking between K and 2K points (bisection on
+    // its float value over [min, max] of the class), or every point of a
+    // class of at most K points
+    auto count = [&](const float* th2, unsigned long long* got) -> cudaError_t {
+      const unsigned long long z2[2] = {0ull, 0ull};
+      cudaError_t e2 = cudaMemcpyAsync(cnt, z2, sizeof(z2), cudaMemcpyHostToDevice, st);
+      if (e2 == cudaSuccess) count_le_kernel<<<grid, 256, 0, st>>>(s, y, n, th2[0], th2[1], cnt);
+      if (e2 == cudaSuccess) e2 = cudaGetLastError();
+      if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(got, cnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+      if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+      return e2;
+    };
+    float lo[2] = {o2f(mmh[0]), o2f(mmh[2])}, hi[2] = {o2f(mmh[1]), o2f(mmh[3])};
+    unsigned long long got[2];
+    if ((e = count(lo, got)) != cudaSuccess) return fail_cuda(e, "coreset: count");
+    // lo takes fewer than K points (else it is the threshold); hi takes all of the class
+    bool need[2];
+    for (int c = 0; c < 2; ++c) {
+      need[c] = got[c] < (unsigned long long)kCoresetK;
+      if (!need[c]) hi[c] = lo[c];
+    }
+    for (int itb = 0; itb < 40 && (need[0] || need[1]); ++itb) {
+      float mid[2];
+      for (int c = 0; c < 2; ++c) mid[c] = need[c] ? lo[c] + 0.5f * (hi[c] - lo[c]) : hi[c];
+      if ((e = count(mid, got)) != cudaSuccess) return fail_cuda(e, "coreset: count");
+      for (int c = 0; c < 2; ++c) {
+        if (!need[c]) continue;
+        if (!(mid[c] > lo[c] && mid[c] < hi[c])) {  // no float left between lo and hi
+          need[c] = false;
+          continue;
+        }
+        if (got[c] < (unsigned long long)kCoresetK) {
+          lo[c] = mid[c];
+        } else {
+          hi[c] = mid[c];
+          if (got[c] <= (unsigned long long)cap) need[c] = false;
+        }
+      }
+    }
+    const float th[2] = {hi[0], hi[1]};
+    unsigned int posh[2] = {0u, 0u};
+    e = cudaMemcpyAsync(pos, posh, sizeof(posh), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) select_le_kernel<<<grid, 256, 0, st>>>(s, y, n, th[0], th[1], sel, cap, pos);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(posh, pos, sizeof(posh), cudaMemcpyDeviceToHost, st);
+    std::vector<int> selh(2 * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(selh.data(), sel, selh.size() * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail_cuda(e, "coreset: select");
+    // merge the picked points into the core set (sorted: the set and so the
+    // solve do not depend on the order of the device's atomic appends)
+    for (int c = 0; c < 2; ++c) {
+      std::vector<int> got(selh.begin() + (size_t)c * cap, selh.begin() + (size_t)c * cap + std::min<unsigned int>(posh[c], cap));
+      std::sort(got.begin(), got.end());
+      std::vector<int> merged;
+      std::set_union(core[c].begin(), core[c].end(), got.begin(), got.end(), std::back_inserter(merged));
+      if ((int)merged.size() > kCoresetMaxPerClass) merged.resize(kCoresetMaxPerClass);  // keeps the sorted head
+      core[c].swap(merged);
+    }
+    const int nP = (int)core[0].size(), nQ = (int)core[1].size();
+    if (nP == 0 || nQ == 0) break;
+    std::vector<int> all(core[0]);
+    all.insert(all.end(), core[1].begin(), core[1].end());
+    const int k = nP + nQ;
+    rowsh.resize((size_t)k * d);
+    e = cudaMemcpyAsync(gidx, all.data(), (size_t)k * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+      if (dtype == PDSCP_F32)
+        gather_rows_kernel<float><<<grid, 256, 0, st>>>(reinterpret_cast<const float*>(X), gidx, k, d, rows);
+      else
+        gather_rows_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(X), gidx, k,
+                                                                d, rows);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rowsh.data(), rows, rowsh.size() * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail_cuda(e, "coreset: gather");
+    Pd.assign(rowsh.begin(), rowsh.begin() + (size_t)nP * d);
+    Qd.assign(rowsh.begin() + (size_t)nP * d, rowsh.end());
+    mu.assign(nP, 0.0);
+    ga.assign(nQ, 0.0);
+    double gap = 0.0;
+    pd_active_set(Pd.data(), nP, Qd.data(), nQ, d, eps / 10.0, 4 * (nP + nQ) + 64, mu.data(), ga.data(), z.data(),
+                  &gap);
+    double zz = 0.0;
+    for (int j = 0; j < d; ++j) zz += z[j] * z[j];
+    if (!(zz > 0.0)) break;
+    *ub = std::min(*ub, std::sqrt(zz));
+    // the solution's direction over every point: its margin
+    w.assign(z.begin(), z.end());
+    e = project(w, mmh);
+    if (e != cudaSuccess) return fail_cuda(e, "coreset: projection");
+    const double m = (double)o2f(mmh[0]) + (double)o2f(mmh[2]);  // min_P x.w - max_Q x.w, |w| = 1
+    if (m > *lb) {
+      *lb = m;
+      const double inv = 1.0 / std::sqrt(zz);
+      for (int j = 0; j < d; ++j) w_lb[j] = z[j] * inv;
+    }
+    if (*ub <= (1.0 + eps) * *lb) break;
+  }
+  return PDSCP_OK;
+}
+
+}  // namespace pdscp
+
+using namespace pdscp;
+
+extern "C" pdscp_status pdscp_polytope_distance(const double* P, int32_t nP, const double* Q, int32_t nQ, int32_t d,
+                                                double tol, int32_t max_iter, double* mu, double* gamma,
+                                                double* dist) {
+  if (!P || !Q || !mu || !gamma || !dist) return report_error(PDSCP_ERR_INVALID_ARG, "pdscp_polytope_distance: null pointer");
+  if (nP < 1 || nQ < 1 || d < 1) return report_error(PDSCP_ERR_INVALID_ARG, "pdscp_polytope_distance: empty set or d < 1");
+  if (!(tol >= 0.0) || max_iter < 1) return report_error(PDSCP_ERR_INVALID_ARG, "pdscp_polytope_distance: tol < 0 or max_iter < 1");
+  std::vector<double> z(d);
+  pd_active_set(P, nP, Q, nQ, d, tol, max_iter, mu, gamma, z.data(), nullptr);
+  double zz = 0.0;
+  for (int j = 0; j < d; ++j) zz += z[j] * z[j];
+  *dist = std::sqrt(zz);
+  return PDSCP_OK;
+}

@@ -1,0 +1,37 @@
+// Core-set certificates for the certified SVM search (see coreset.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/pdscp.h"
+
+namespace pdscp {
+
+constexpr int kCoresetK = 512;       // points per class picked by one direction
+constexpr int kCoresetRounds = 4;    // active-set rounds of one check
+constexpr int kCoresetMaxPerClass = 4 * kCoresetK;  // core-set size cap per class
+constexpr int64_t kCoresetFirst = 256;  // first check at this many iterations of the search, then every doubling
+
+// Exact polytope distance of two small point sets (host, FP64) by a primal
+// active-set method; returns the iterations run. mu (nP), ga (nQ): the
+// weights on the two simplices; z (d): P^T mu - Q^T ga; *gap: z.z minus
+// (min_i p_i.z - max_j q_j.z) at the end (>= 0; <= tol z.z when converged).
+int pd_active_set(const double* P, int nP, const double* Q, int nQ, int d, double tol, int max_iter, double* mu,
+                  double* ga, double* z, double* gap);
+
+// Bytes of workspace the core-set checks of svm_solve need for n points in d.
+size_t coreset_bytes(int64_t n, int d);
+
+// One core-set check (reading 25 of the design notes): from direction w0
+// (host, d doubles), core sets picked on the device, solved on the host.
+// Sets *lb (a margin of some direction over all points), *ub (a core-set
+// distance) and w_lb (that direction, unit norm). ws: coreset_bytes(n, d)
+// bytes of device memory, 256-byte aligned.
+pdscp_status svm_coreset_check(const void* X, int dtype, const int8_t* y, int64_t n, int d, const double* w0,
+                               double eps, void* ws, cudaStream_t s, double* lb, double* ub,
+                               std::vector<double>& w_lb);
+
+}  // namespace pdscp

@@ -86,9 +86,16 @@ def test_argument_validation_without_gpu(lib):
     opts = _ffi.Options(1e-3, 0.0, 10, _ffi.MODE_CERTIFIED, 1000, 64, 10, 0.0)
     st = lib.ses_solve(fake, _ffi.F32, None, 10, 4, ctypes.byref(opts), fake, 16, None, fake, ctypes.byref(rep))
     assert st == 8
-    opts = _ffi.Options(1e-3, 0.0, 10, 3, 1000, 64, 10, 0.0)
+    opts = _ffi.Options(1e-3, 0.0, 10, 4, 1000, 64, 10, 0.0)
     st = lib.ses_solve(fake, _ffi.F32, None, 10, 4, ctypes.byref(opts), fake, 1 << 30, None, fake, ctypes.byref(rep))
     assert st == 1 and b"mode" in lib.pdscp_last_error()
+    # the core-set mode needs the larger SVM workspace pdscp_workspace_size reports
+    size = ctypes.c_size_t()
+    assert lib.pdscp_workspace_size(_ffi.SVM, 10, 4, ctypes.byref(size)) == 0
+    opts = _ffi.Options(1e-3, 0.0, 10, _ffi.MODE_CORESET, 1000, 64, 10, 0.0)
+    st = lib.svm_solve(fake, _ffi.F32, fake, 10, 4, ctypes.byref(opts), fake, size.value - 256, None, fake,
+                       ctypes.byref(rep))
+    assert st == 8
     opts = _ffi.Options(1e-3, 0.0, 10, _ffi.MODE_CERTIFIED, 1000, 64, 10, 1.5)
     st = lib.svm_solve(fake, _ffi.F32, fake, 10, 4, ctypes.byref(opts), fake, 1 << 30, None, fake, ctypes.byref(rep))
     assert st == 1 and b"eta" in lib.pdscp_last_error()

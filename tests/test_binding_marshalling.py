@@ -93,6 +93,8 @@ def test_every_entry_point_marshals(fake):
     api.decode_steps(api.new_steps(2, cpu))
     api.ses_solve(pts, radii, mode="certified")
     api.svm_solve(pts, labels, mode="certified")
+    api.svm_solve(pts, labels, mode="coreset")
+    api.polytope_distance(np.ones((3, d)), -np.ones((2, d)))
     f = api.ses_unrolled_radius(pts.clone().requires_grad_(True), 1.0, 0.1, 3)
     f.backward()
     g = api.svm_unrolled_margin(pts.clone().requires_grad_(True), labels, 1.0, 0.1, 3, 2.0)
@@ -114,7 +116,8 @@ def test_every_entry_point_marshals(fake):
     # every entry point the binding reaches was called with its declared arity
     assert {"mwu_step", "mwu_run", "mwu_backward", "ses_solve", "svm_solve", "ses_multi_step", "mwu_shard_partial",
             "mwu_shard_finish", "ses_batch_init", "ses_batch_step", "ses_batch_autotune", "ses_batch_solve_init",
-            "ses_batch_solve_run", "ses_batch_solve_read", "mwu_step_noalloc", "mwu_state_set"} <= set(fake.calls)
+            "ses_batch_solve_run", "ses_batch_solve_read", "mwu_step_noalloc", "mwu_state_set",
+            "pdscp_polytope_distance"} <= set(fake.calls)
 
 
 def test_binding_rejects_bad_buffers(fake):

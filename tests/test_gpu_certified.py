@@ -148,3 +148,56 @@ def test_ses_certified_bf16_points():
     assert rep["status"] == 0 and rep["value"] <= (1 + 1e-3) * rep["lower_bound"]
     assert rep["lower_bound"] <= ref["radius"] * (1 + FP) and ref["lower_bound"] <= rep["value"] * (1 + FP)
     assert oses.ses_objective(V, None, center.cpu().numpy().astype(np.float64)) <= rep["value"] * (1 + FP)
+
+
+def _margin64(X, y, w):
+    return exact.svm_margin_of(X[y > 0], X[y < 0], w.cpu().numpy().astype(np.float64))
+
+
+def test_svm_coreset_matches_oracle_d128():
+    # core-set certificates (mode "coreset") at d = 128: both searches bracket the exact optimum
+    # (MDM on all 10,000 points) and close to eps = 1e-3
+    X32, y = datagen.svm_clusters(5000, 5000, 128, seed=2)
+    X = X32.astype(np.float64)
+    opt = exact.pd_mdm(X[y > 0], X[y < 0], tol=1e-10)[0]
+    ref = osvm.svm_solve(X, y, eps=1e-3, mode="coreset", max_iters=20_000, poll_every=64)
+    w, rep = api.svm_solve(_cuda(X32), _cuda(y), eps=1e-3, mode="coreset", max_iters=20_000, poll_every=64)
+    assert ref["upper_bound"] <= (1 + 1e-3) * ref["lower_bound"]
+    assert rep["status"] == 0 and rep["upper_bound"] <= (1 + 1e-3) * rep["lower_bound"]
+    assert rep["lower_bound"] <= opt * (1 + FP) and rep["upper_bound"] >= opt * (1 - FP)
+    assert ref["lower_bound"] <= opt * (1 + FP) and ref["upper_bound"] >= opt * (1 - FP)
+    assert math.isclose(_margin64(X, y, w), rep["value"], rel_tol=1e-4)
+    # the first check (256 iterations of the search) closes it in both
+    assert rep["iters"] <= 2 * 256 and ref["iters"] <= 2 * 256
+
+
+def test_svm_coreset_small_classes_take_every_point():
+    # classes of at most 512 points: the first core set is the whole set, its distance is OPT
+    X32, y = datagen.svm_clusters(300, 200, 16, seed=3)
+    X = X32.astype(np.float64)
+    opt = exact.pd_mdm(X[y > 0], X[y < 0], tol=1e-12)[0]
+    w, rep = api.svm_solve(_cuda(X32), _cuda(y), eps=1e-3, mode="coreset", max_iters=20_000, poll_every=64)
+    assert rep["status"] == 0
+    assert opt * (1 - 1e-9) <= rep["upper_bound"] <= opt * (1 + 1e-4)  # core-set solve to a gap of eps/10
+    assert rep["lower_bound"] <= opt * (1 + FP) and rep["lower_bound"] >= opt * (1 - 1e-3)
+    assert math.isclose(_margin64(X, y, w), rep["value"], rel_tol=1e-4)
+
+
+def test_svm_coreset_bf16_points():
+    # BF16-stored points: certificates of the BF16-rounded set
+    X32, y = datagen.svm_clusters(4000, 3000, 64, seed=4)
+    xb = _cuda(X32).to(torch.bfloat16)
+    X = xb.to(torch.float32).cpu().numpy().astype(np.float64)
+    opt = exact.pd_mdm(X[y > 0], X[y < 0], tol=1e-10)[0]
+    w, rep = api.svm_solve(xb, _cuda(y), eps=1e-3, mode="coreset", max_iters=20_000, poll_every=64)
+    assert rep["status"] == 0 and rep["upper_bound"] <= (1 + 1e-3) * rep["lower_bound"]
+    assert rep["lower_bound"] <= opt * (1 + FP) and rep["upper_bound"] >= opt * (1 - FP)
+    assert math.isclose(_margin64(X, y, w), rep["value"], rel_tol=1e-4)
+
+
+def test_svm_coreset_full_size():
+    # the benchmarked SVM workload: n1 = n2 = 5e5, d = 128, eps = 1e-3
+    X32, y = datagen.svm_clusters(500_000, 500_000, 128, seed=0)
+    w, rep = api.svm_solve(_cuda(X32), _cuda(y), eps=1e-3, mode="coreset", max_iters=200_000, poll_every=256)
+    assert rep["status"] == 0 and rep["upper_bound"] <= (1 + 1e-3) * rep["lower_bound"]
+    assert math.isclose(_margin64(X32.astype(np.float64), y, w), rep["value"], rel_tol=1e-4)
