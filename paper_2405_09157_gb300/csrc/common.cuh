@@ -724,6 +724,9 @@ __device__ void final_reduce(const float* rows, int stride, const float2* grows,
   }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  // the rows are in shared memory: the next launch of the stream may start
+  // now (a kernel that let it start earlier already has; then a no-op)
+  pdl_trigger();
   if (threadIdx.x == 0) counters[0] = 0u;
   __syncthreads();
   group_columns<16>(stage, nb, stride, raw, period, max_col, min_col);
