@@ -116,7 +116,9 @@ def svm_oracle(X, y, p, alpha, D):
     z = X.T @ mu - X.T @ ga
     nz = math.sqrt(float(z @ z))
     w = z / nz if nz > 0.0 else np.zeros_like(z)
-    tr_mu, tr_ga = float(np.sum(mu)), float(np.sum(ga))
+    # correctly rounded traces: two classes carrying equal weight (n1 = n2 at
+    # t = 0) tie exactly and take s_1 = D, not a choice left to rounding
+    tr_mu, tr_ga = math.fsum(mu), math.fsum(ga)
     s1 = D if tr_mu <= tr_ga else alpha - D
     s2 = alpha - s1
     value = float(z @ w) - tr_mu * s1 - tr_ga * s2
