@@ -410,10 +410,21 @@ pdscp_status ses_batch_read(int32_t num, const void* ws_dev, float* mean_dev, fl
  *     U <= (1+eps) L or ub <= (1+eps) lb, PDSCP_ERR_NOT_CONVERGED otherwise)
  *     to reports_dev and the centres, packed as in ses_batch_read, to
  *     centers_dev (either may be NULL).
- *   ses_batch_autotune: times the launch for tile_rows in {512, ..., 32768}
- *     (the candidates whose workspace fits ws_bytes) on this batch and returns
- *     the fastest; leaves the workspace set up for the last candidate tried,
- *     so ses_batch_solve_init must follow.
+ *   ses_batch_autotune: times the search launch on this batch for every
+ *     tile_rows in {512, ..., 32768} whose workspace fits ws_bytes, with 1, 2
+ *     and 3 CTAs per SM in the persistent grid and both lane-layout policies
+ *     (0: 4-element chunk loads for instances with d % 4 == 0 whose rows
+ *     start on a 4-element boundary, scalar layouts otherwise; 1: scalar
+ *     layouts only), and returns the fastest (tile_rows_host, and, where not
+ *     NULL, its time, CTAs per SM and layout); leaves the workspace set up
+ *     for the last candidate tried, so ses_batch_solve_init must follow.
+ *   ses_batch_set_launch: after ses_batch_init or ses_batch_solve_init,
+ *     records the CTAs per SM of ses_batch_solve_run's persistent grid
+ *     (0: as many as fit, else 1..3) and applies a layout policy (0 or 1)
+ *     to every instance (pts_dev as given to the init); ses_batch_step keeps
+ *     the grid of as many CTAs as fit. Synchronises the stream.
+ *     PDSCP_ERR_INVALID_ARG for values out of range or another batch's
+ *     instance count.
  */
 pdscp_status ses_batch_solve_init(int32_t num, const void* pts_dev, int32_t dtype, int64_t pts_len,
                                   const int64_t* offset_host, const int64_t* n_host,
@@ -430,7 +441,65 @@ pdscp_status ses_batch_autotune(int32_t num, const void* pts_dev, int32_t dtype,
                                 const int64_t* offset_host, const int64_t* n_host,
                                 const int32_t* d_host, const pdscp_options* opts, void* ws_dev,
                                 size_t ws_bytes, pdscp_stream stream, int32_t* tile_rows_host,
-                                float* ms_per_launch_host);
+                                float* ms_per_launch_host, int32_t* ctas_per_sm_host,
+                                int32_t* layout_host);
+pdscp_status ses_batch_set_launch(int32_t num, const void* pts_dev, void* ws_dev, int32_t ctas_per_sm,
+                                  int32_t layout, pdscp_stream stream);
+
+/*
+ * Batched SVM (many independent hard-margin SVM instances, one launch per
+ * iteration for all): instance i has n_i >= 2 points of dimension
+ * 1 <= d_i <= 64, stored as for the batched SES (offset_i, dtype, pts_len),
+ * and n_i int8 labels (+1: class P, -1: class Q, Sec. 4.2) starting at
+ * element label_offset_i of labels_dev (labels_len elements). Each instance
+ * runs its own minimisation alpha-FTP (Sec. 3, Eq. min_implement, the SVM
+ * data of Sec. 4.2) with its own state; the tiles, the persistent grid and
+ * the completion are those of the batched SES.
+ *   svm_batch_workspace_size: bytes of the workspace (host sizes).
+ *   svm_batch_init: builds the tables (host -> workspace), computes each
+ *     instance's D = max_i ||x_i|| on the device (FP64 norms of the stored
+ *     values) and starts every alpha-FTP (t = 0, means 0); synchronises the
+ *     stream. Bad pointers, an unknown dtype, or an instance past pts_len or
+ *     labels_len return PDSCP_ERR_INVALID_ARG before any device work.
+ *   svm_batch_step: one MWU iteration of every instance (asynchronous);
+ *     pts_dev, dtype and labels_dev must be those given to svm_batch_init;
+ *     alpha_dev and eta_over_rho_dev hold one double per instance; out_dev
+ *     (may be NULL) receives one pdscp_step_out per instance.
+ *   svm_batch_read: each instance's running mean wbar and best-margin
+ *     direction (packed as in ses_batch_read) and its D (one double each);
+ *     any output may be NULL.
+ *   svm_batch_solve_init / _run / _read: the search of svm_solve for every
+ *     instance on the device (alpha in (0, 2D], alpha_i = U - (U-L)/3; the
+ *     PRACTICAL and THEORY modes with T_i of Theorem 3 and the Sec. 5 rules,
+ *     CERTIFIED with the certificate and progress tests of svm_solve every
+ *     opts->poll_every iterations); the CUDA-graph replay and polling of
+ *     ses_batch_solve_run. The reports carry value = lower_bound = the margin
+ *     of the returned direction, upper_bound = the best Claim 8 value (with
+ *     CERTIFIED: min(ub, U)); the directions are packed as in ses_batch_read.
+ */
+pdscp_status svm_batch_workspace_size(int32_t num, const int64_t* n_host, const int32_t* d_host,
+                                      int32_t tile_rows, size_t* bytes_host);
+pdscp_status svm_batch_init(int32_t num, const void* pts_dev, int32_t dtype, int64_t pts_len,
+                            const int64_t* offset_host, const int64_t* n_host,
+                            const int32_t* d_host, const int8_t* labels_dev, int64_t labels_len,
+                            const int64_t* label_offset_host, int32_t tile_rows, void* ws_dev,
+                            size_t ws_bytes, pdscp_stream stream);
+pdscp_status svm_batch_step(int32_t num, const void* pts_dev, int32_t dtype, const int8_t* labels_dev,
+                            const double* alpha_dev, const double* eta_over_rho_dev, void* ws_dev,
+                            size_t ws_bytes, pdscp_stream stream, pdscp_step_out* out_dev);
+pdscp_status svm_batch_read(int32_t num, const void* ws_dev, float* mean_dev, float* best_dev,
+                            double* D_dev, pdscp_stream stream);
+pdscp_status svm_batch_solve_init(int32_t num, const void* pts_dev, int32_t dtype, int64_t pts_len,
+                                  const int64_t* offset_host, const int64_t* n_host,
+                                  const int32_t* d_host, const int8_t* labels_dev, int64_t labels_len,
+                                  const int64_t* label_offset_host, int32_t tile_rows,
+                                  const pdscp_options* opts, void* ws_dev, size_t ws_bytes,
+                                  pdscp_stream stream);
+pdscp_status svm_batch_solve_run(int32_t num, const void* pts_dev, const int8_t* labels_dev, void* ws_dev,
+                                 size_t ws_bytes, int32_t launches_per_poll, int64_t max_launches,
+                                 pdscp_stream stream, int64_t* launches_host, int32_t* done_host);
+pdscp_status svm_batch_solve_read(int32_t num, const void* ws_dev, double eps,
+                                  pdscp_report* reports_dev, float* w_dev, pdscp_stream stream);
 
 /*
  * Row-sharded iteration: the rows (cones) split across G GPUs, one shard per

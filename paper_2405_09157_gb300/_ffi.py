@@ -77,8 +77,20 @@ SIGNATURES = {
     "ses_batch_solve_run": (c_i32, [c_i32, c_vp, c_vp, c_sz, c_i32, c_i64, c_vp, ctypes.POINTER(c_i64),
                                     ctypes.POINTER(c_i32)]),
     "ses_batch_solve_read": (c_i32, [c_i32, c_vp, c_dbl, c_vp, c_vp, c_vp]),
+    "svm_batch_workspace_size": (c_i32, [c_i32, c_vp, c_vp, c_i32, ctypes.POINTER(c_sz)]),
+    "svm_batch_init": (c_i32, [c_i32, c_vp, c_i32, c_i64, c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, c_i32, c_vp, c_sz,
+                               c_vp]),
+    "svm_batch_step": (c_i32, [c_i32, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp, c_vp]),
+    "svm_batch_read": (c_i32, [c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "svm_batch_solve_init": (c_i32, [c_i32, c_vp, c_i32, c_i64, c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, c_i32, c_vp,
+                                     c_vp, c_sz, c_vp]),
+    "svm_batch_solve_run": (c_i32, [c_i32, c_vp, c_vp, c_vp, c_sz, c_i32, c_i64, c_vp, ctypes.POINTER(c_i64),
+                                    ctypes.POINTER(c_i32)]),
+    "svm_batch_solve_read": (c_i32, [c_i32, c_vp, c_dbl, c_vp, c_vp, c_vp]),
     "ses_batch_autotune": (c_i32, [c_i32, c_vp, c_i32, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp,
-                                   ctypes.POINTER(c_i32), ctypes.POINTER(ctypes.c_float)]),
+                                   ctypes.POINTER(c_i32), ctypes.POINTER(ctypes.c_float), ctypes.POINTER(c_i32),
+                                   ctypes.POINTER(c_i32)]),
+    "ses_batch_set_launch": (c_i32, [c_i32, c_vp, c_vp, c_i32, c_i32, c_vp]),
     "mwu_shard_row_width": (c_i32, [c_i32, c_i32, ctypes.POINTER(c_i32)]),
     "mwu_shard_init": (c_i32, [c_i32, c_vp, c_i32, c_i32, c_i32, c_dbl, c_i32, c_vp, c_vp, c_sz, c_vp]),
     "mwu_shard_partial": (c_i32, [c_i32, c_vp, c_i32, c_vp, c_vp, c_i64, c_i32, c_i32, c_dbl, c_dbl, c_dbl,

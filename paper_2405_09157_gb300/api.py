@@ -556,6 +556,7 @@ class SesBatch:
         self.n = np.ascontiguousarray(n, dtype=np.int64)
         self.d = np.ascontiguousarray(d, dtype=np.int32)
         self.tile_rows = int(tile_rows)
+        self.ctas_per_sm, self.layout = 0, 0  # launch settings (ses_batch_set_launch; set by autotune)
         lib = load()
         size = ctypes.c_size_t()
         check(lib.ses_batch_workspace_size(self.num, self.n.ctypes.data, self.d.ctypes.data, self.tile_rows,
@@ -567,6 +568,19 @@ class SesBatch:
         check(load().ses_batch_init(self.num, _vp(self.pts), self.dt, self.pts.numel(), self.offsets.ctypes.data,
                                     self.n.ctypes.data, self.d.ctypes.data, self.tile_rows, _vp(self.ws),
                                     self.ws.numel(), _stream(stream)), "ses_batch_init")
+        self._apply_launch(stream)
+
+    def _apply_launch(self, stream=None):
+        if self.ctas_per_sm or self.layout:
+            check(load().ses_batch_set_launch(self.num, _vp(self.pts), _vp(self.ws), self.ctas_per_sm, self.layout,
+                                              _stream(stream)), "ses_batch_set_launch")
+
+    def set_launch(self, ctas_per_sm=0, layout=0, stream=None):
+        """CTAs per SM of the search's persistent grid (0: as many as fit) and
+        the lane-layout policy (0: chunk loads where rows allow, 1: scalar)."""
+        self.ctas_per_sm, self.layout = int(ctas_per_sm), int(layout)
+        check(load().ses_batch_set_launch(self.num, _vp(self.pts), _vp(self.ws), self.ctas_per_sm, self.layout,
+                                          _stream(stream)), "ses_batch_set_launch")
 
     def step(self, alpha, eta_over_rho, out=None, stream=None):
         """alpha, eta_over_rho: float64 CUDA tensors of one value per instance."""
@@ -580,9 +594,10 @@ class SesBatch:
         return self.offsets.ctypes.data, self.n.ctypes.data, self.d.ctypes.data
 
     def autotune(self, eps=1e-3, mode="practical", stream=None, **kw):
-        """Times the batched launch for each tile size that fits the workspace
-        (native autotuner) and re-initialises the batch with the fastest.
-        Returns (tile_rows, ms per launch)."""
+        """Times the batched launch for each tile size that fits the workspace,
+        1 to 3 CTAs per SM and both lane-layout policies (native autotuner)
+        and re-initialises the batch with the fastest. Returns (tile_rows, ms
+        per launch); the CTAs per SM and the layout are kept for solve()."""
         o = _options(eps, mode, kw.get("max_iters", 1_000_000), 1, kw.get("max_steps", 200), kw.get("eta"),
                      kw.get("delta", 1e-4), kw.get("patience", 10))
         lib = load()
@@ -591,12 +606,13 @@ class SesBatch:
                                            ctypes.byref(need)), "ses_batch_workspace_size")
         if need.value > self.ws.numel():
             self.ws = torch.zeros(need.value, dtype=torch.uint8, device=self.pts.device)
-        tr, ms = ctypes.c_int32(), ctypes.c_float()
+        tr, ms, ctas, lay = ctypes.c_int32(), ctypes.c_float(), ctypes.c_int32(), ctypes.c_int32()
         offs, n, d = self._host_tables()
         check(lib.ses_batch_autotune(self.num, _vp(self.pts), self.dt, self.pts.numel(), offs, n, d, ctypes.byref(o),
                                      _vp(self.ws), self.ws.numel(), _stream(stream), ctypes.byref(tr),
-                                     ctypes.byref(ms)), "ses_batch_autotune")
+                                     ctypes.byref(ms), ctypes.byref(ctas), ctypes.byref(lay)), "ses_batch_autotune")
         self.tile_rows = tr.value
+        self.ctas_per_sm, self.layout = ctas.value, lay.value
         self.init(stream)
         return tr.value, ms.value
 
@@ -612,6 +628,7 @@ class SesBatch:
         check(lib.ses_batch_solve_init(self.num, _vp(self.pts), self.dt, self.pts.numel(), offs, n, d, self.tile_rows,
                                        ctypes.byref(o), _vp(self.ws), self.ws.numel(), _stream(stream)),
               "ses_batch_solve_init")
+        self._apply_launch(stream)
         launches, done = ctypes.c_int64(), ctypes.c_int32()
         check(lib.ses_batch_solve_run(self.num, _vp(self.pts), _vp(self.ws), self.ws.numel(), launches_per_poll,
                                       max_launches, _stream(stream), ctypes.byref(launches), ctypes.byref(done)),
@@ -639,3 +656,92 @@ class SesBatch:
         cut = np.concatenate([[0], np.cumsum(self.d)])
         mh, bh = m.cpu().numpy(), b.cpu().numpy()
         return [mh[cut[i]:cut[i + 1]] for i in range(self.num)], [bh[cut[i]:cut[i + 1]] for i in range(self.num)]
+
+
+# ------------------------------------------------------------------ batched SVM
+def pack_labels(labels, device="cuda"):
+    """Pack per-instance label arrays (+1 / -1) into one int8 device buffer,
+    one instance after another. Returns (labels tensor, label offsets int64)."""
+    n = np.array([len(y) for y in labels], dtype=np.int64)
+    offs = np.concatenate([[0], np.cumsum(n)[:-1]]).astype(np.int64)
+    host = np.concatenate([np.asarray(y, dtype=np.int8).reshape(-1) for y in labels]) if len(labels) else \
+        np.zeros(0, dtype=np.int8)
+    return torch.from_numpy(np.ascontiguousarray(host)).to(device), offs
+
+
+class SvmBatch:
+    """Many independent hard-margin SVM alpha-FTPs advanced together, one launch per iteration."""
+
+    def __init__(self, pts, offsets, n, d, labels, label_offsets, tile_rows=4096, stream=None):
+        """pts: the packed 1-D float32 or bfloat16 CUDA buffer of pack_instances;
+        labels, label_offsets: from pack_labels."""
+        self.pts, self.num = pts, len(n)
+        self.dt = dtype_code(pts)
+        self.offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        self.n = np.ascontiguousarray(n, dtype=np.int64)
+        self.d = np.ascontiguousarray(d, dtype=np.int32)
+        self.lab_offsets = np.ascontiguousarray(label_offsets, dtype=np.int64)
+        if labels is None or len(self.lab_offsets) != self.num:
+            raise ValueError("labels and one label offset per instance are required")
+        _rows(labels, int(np.max(self.lab_offsets + self.n)) if self.num else 0, torch.int8, "labels")
+        self.labels = labels
+        self.tile_rows = int(tile_rows)
+        size = ctypes.c_size_t()
+        check(load().svm_batch_workspace_size(self.num, self.n.ctypes.data, self.d.ctypes.data, self.tile_rows,
+                                              ctypes.byref(size)), "svm_batch_workspace_size")
+        self.ws = torch.zeros(size.value, dtype=torch.uint8, device=pts.device)
+        self.init(stream)
+
+    def _tables(self):
+        return (self.pts.numel(), self.offsets.ctypes.data, self.n.ctypes.data, self.d.ctypes.data,
+                _vp(self.labels), self.labels.numel(), self.lab_offsets.ctypes.data, self.tile_rows)
+
+    def init(self, stream=None):
+        check(load().svm_batch_init(self.num, _vp(self.pts), self.dt, *self._tables(), _vp(self.ws),
+                                    self.ws.numel(), _stream(stream)), "svm_batch_init")
+
+    def step(self, alpha, eta_over_rho, out=None, stream=None):
+        """alpha, eta_over_rho: float64 CUDA tensors of one value per instance."""
+        _rows(alpha, self.num, torch.float64, "alpha")
+        _rows(eta_over_rho, self.num, torch.float64, "eta_over_rho")
+        _records(out, self.num)
+        check(load().svm_batch_step(self.num, _vp(self.pts), self.dt, _vp(self.labels), _vp(alpha),
+                                    _vp(eta_over_rho), _vp(self.ws), self.ws.numel(), _stream(stream), _vp(out)),
+              "svm_batch_step")
+
+    def read(self, stream=None):
+        """(means, best directions, D): lists of float32 arrays per instance and a float64 array of D."""
+        tot = int(self.d.sum())
+        m = torch.empty(tot, dtype=torch.float32, device=self.pts.device)
+        b = torch.empty(tot, dtype=torch.float32, device=self.pts.device)
+        D = torch.empty(self.num, dtype=torch.float64, device=self.pts.device)
+        check(load().svm_batch_read(self.num, _vp(self.ws), _vp(m), _vp(b), _vp(D), _stream(stream)),
+              "svm_batch_read")
+        torch.cuda.synchronize()
+        cut = np.concatenate([[0], np.cumsum(self.d)])
+        mh, bh = m.cpu().numpy(), b.cpu().numpy()
+        return ([mh[cut[i]:cut[i + 1]] for i in range(self.num)], [bh[cut[i]:cut[i + 1]] for i in range(self.num)],
+                D.cpu().numpy())
+
+    def solve(self, eps=1e-3, mode="practical", max_iters=1_000_000, max_steps=200, eta=None, delta=1e-4,
+              patience=10, launches_per_poll=32, max_launches=10_000_000, poll_every=256, stream=None):
+        """The search of svm_solve for every instance, on the device. Returns
+        (reports: structured numpy array of pdscp_report, directions: list of
+        float32 arrays, launches run)."""
+        o = _options(eps, mode, max_iters, poll_every, max_steps, eta, delta, patience)
+        lib = load()
+        check(lib.svm_batch_solve_init(self.num, _vp(self.pts), self.dt, *self._tables(), ctypes.byref(o),
+                                       _vp(self.ws), self.ws.numel(), _stream(stream)), "svm_batch_solve_init")
+        launches, done = ctypes.c_int64(), ctypes.c_int32()
+        check(lib.svm_batch_solve_run(self.num, _vp(self.pts), _vp(self.labels), _vp(self.ws), self.ws.numel(),
+                                      launches_per_poll, max_launches, _stream(stream), ctypes.byref(launches),
+                                      ctypes.byref(done)), "svm_batch_solve_run")
+        reps = torch.zeros((self.num, ctypes.sizeof(_ffi.Report)), dtype=torch.uint8, device=self.pts.device)
+        w = torch.empty(int(self.d.sum()), dtype=torch.float32, device=self.pts.device)
+        check(lib.svm_batch_solve_read(self.num, _vp(self.ws), float(eps), _vp(reps), _vp(w), _stream(stream)),
+              "svm_batch_solve_read")
+        torch.cuda.synchronize()
+        rec = np.frombuffer(reps.cpu().numpy().tobytes(), dtype=REPORT_DTYPE)
+        cut = np.concatenate([[0], np.cumsum(self.d)])
+        wh = w.cpu().numpy()
+        return rec, [wh[cut[i]:cut[i + 1]] for i in range(self.num)], launches.value

@@ -1,85 +1,19 @@
 // Host side of the batched SES iteration (batch_kernel.cuh): workspace
 // layout, per-instance tables and states, one-iteration launches, for
 // float32 or bfloat16 points (one instantiation of the kernels per type).
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <vector>
 
-#include "batch_kernel.cuh"
-#include "dispatch.cuh"
+#include "batch_host.cuh"
 
 namespace pdscp {
 namespace {
-
-size_t r256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-pdscp_status err(pdscp_status s, const char* fmt, long long a = 0, long long b = 0) {
-  char buf[320];
-  snprintf(buf, sizeof(buf), fmt, a, b);
-  return report_error(s, buf);
-}
-
-struct BatchLayout {
-  int64_t ntiles;
-  size_t inst_off, instcnt_off, tile_off, partial_off, state_off, search_off, total;
-};
-
-pdscp_status batch_layout(int num, const int64_t* n, const int32_t* d, int tile_rows, BatchLayout* L,
-                          std::vector<BatchInst>* insts, std::vector<BatchTile>* tiles, const int64_t* offs) {
-  if (num < 1) return err(PDSCP_ERR_INVALID_ARG, "batch: num must be >= 1 (got %lld)", num);
-  if (!n || !d) return err(PDSCP_ERR_INVALID_ARG, "batch: null size arrays");
-  if (tile_rows < 32) return err(PDSCP_ERR_INVALID_ARG, "batch: tile_rows must be >= 32 (got %lld)", tile_rows);
-  int64_t T = 0;
-  for (int i = 0; i < num; ++i) {
-    if (n[i] < 2) return err(PDSCP_ERR_INVALID_ARG, "batch: instance %lld has n = %lld < 2", i, n[i]);
-    if (d[i] < 1 || d[i] > kBatchMaxD)
-      return err(PDSCP_ERR_NOT_IMPLEMENTED, "batch: instance %lld has d = %lld outside [1, 64]", i, d[i]);
-    T += (n[i] + tile_rows - 1) / tile_rows;
-  }
-  L->ntiles = T;
-  L->inst_off = 1024;
-  L->instcnt_off = L->inst_off + r256((size_t)num * sizeof(BatchInst));
-  L->tile_off = L->instcnt_off + r256((size_t)num * sizeof(unsigned int));
-  L->partial_off = L->tile_off + r256((size_t)T * sizeof(BatchTile));
-  L->state_off = L->partial_off + r256((size_t)T * kBatchStride * sizeof(float));
-  size_t so = L->state_off;
-  int64_t t0 = 0, moff = 0;
-  for (int i = 0; i < num; ++i) {
-    const int64_t nt = (n[i] + tile_rows - 1) / tile_rows;
-    if (insts) {
-      BatchInst in;
-      in.pt_off = offs ? offs[i] : 0;
-      in.n = n[i];
-      in.state_off = (int64_t)so;
-      in.tile0 = t0;
-      in.mean_off = moff;
-      in.ntiles = (int32_t)nt;
-      in.d = d[i];
-      in.shape = batch_shape(d[i], offs ? (offs[i] % 4 == 0) : false);
-      in.pad = 0;
-      insts->push_back(in);
-      for (int64_t k = 0; k < nt; ++k) {
-        BatchTile tl;
-        tl.inst = i;
-        tl.pad = 0;
-        tl.r0 = k * tile_rows;
-        tl.r1 = (k + 1) * tile_rows < n[i] ? (k + 1) * tile_rows : n[i];
-        tiles->push_back(tl);
-      }
-    }
-    so += r256(state_bytes(d[i]));
-    t0 += nt;
-    moff += d[i];
-  }
-  L->search_off = r256(so);
-  L->total = L->search_off + r256((size_t)num * sizeof(BatchSearch));
-  return PDSCP_OK;
-}
+using namespace batchhost;
 
 // Tables, header and fresh states of a batch (shared by the plain and the
 // search entry points). Synchronises the stream (the host tables are local).
-size_t batch_elem(int dtype) { return dtype == PDSCP_BF16 ? 2 : 4; }
-
 pdscp_status batch_setup(int32_t num, const void* pts_dev, int32_t dtype, int64_t pts_len, const int64_t* offset_host,
                          const int64_t* n_host, const int32_t* d_host, int32_t tile_rows, void* ws_dev,
                          size_t ws_bytes, cudaStream_t s, BatchLayout* Lout) {
@@ -134,12 +68,12 @@ pdscp_status batch_setup(int32_t num, const void* pts_dev, int32_t dtype, int64_
 // One iteration of every instance; with a search, then every instance's search step.
 template <typename T>
 cudaError_t launch_batch_t(const T* pts, const double* alpha, const double* eor, unsigned char* ws,
-                           pdscp_step_out* out, BatchSearch* search, cudaStream_t s, int num) {
+                           pdscp_step_out* out, BatchSearch* search, cudaStream_t s, int num, int ctas) {
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ses_batch_kernel<T>, kBatchBlock, 0) != cudaSuccess ||
       occ < 1)
     occ = 1;
-  const int grid = device_sm_count() * occ;
+  const int grid = device_sm_count() * (ctas > 0 && ctas < occ ? ctas : occ);
   BatchParams p{pts, alpha, eor, ws, out, search};
   ses_batch_kernel<T><<<grid, kBatchBlock, 0, s>>>(p);
   cudaError_t e = cudaGetLastError();
@@ -147,30 +81,28 @@ cudaError_t launch_batch_t(const T* pts, const double* alpha, const double* eor,
   ses_batch_search_kernel<T><<<(num + 7) / 8, 256, 0, s>>>(pts, ws, num);
   return cudaGetLastError();
 }
+// ctas: CTAs per SM of the persistent grid (0: as many as fit)
 cudaError_t launch_batch(const void* pts, int32_t dtype, const double* alpha, const double* eor, unsigned char* ws,
-                         pdscp_step_out* out, BatchSearch* search, cudaStream_t s, int num = 0) {
+                         pdscp_step_out* out, BatchSearch* search, cudaStream_t s, int num = 0, int ctas = 0) {
   if (dtype == PDSCP_BF16)
-    return launch_batch_t(static_cast<const __nv_bfloat16*>(pts), alpha, eor, ws, out, search, s, num);
-  return launch_batch_t(static_cast<const float*>(pts), alpha, eor, ws, out, search, s, num);
+    return launch_batch_t(static_cast<const __nv_bfloat16*>(pts), alpha, eor, ws, out, search, s, num, ctas);
+  return launch_batch_t(static_cast<const float*>(pts), alpha, eor, ws, out, search, s, num, ctas);
 }
 
-pdscp_status solve_opts(const pdscp_options* o, BatchSolveOpts* b) {
-  if (!o) return err(PDSCP_ERR_INVALID_ARG, "batch: options pointer is null");
-  if (!(o->eps > 0.0) || !(o->delta >= 0.0) || o->patience < 1 || o->max_iters < 1 || o->max_steps < 1 ||
-      (o->mode != PDSCP_MODE_PRACTICAL && o->mode != PDSCP_MODE_THEORY && o->mode != PDSCP_MODE_CERTIFIED) ||
-      !(o->eta >= 0.0) || o->eta > 1.0 || (o->mode == PDSCP_MODE_CERTIFIED && o->poll_every < 1))
-    return err(PDSCP_ERR_INVALID_ARG, "batch: invalid search options");
-  const bool cert = o->mode == PDSCP_MODE_CERTIFIED;
-  b->eps = o->eps;
-  b->delta = cert ? 0.0 : o->delta;  // CERTIFIED: no stall rule
-  b->eta = o->eta;
-  b->max_iters = o->max_iters;
-  b->patience = o->patience;
-  b->rules = o->mode == PDSCP_MODE_THEORY ? PDSCP_RULES_NONE : PDSCP_RULES_PRACTICAL;
-  b->max_steps = o->max_steps;
-  b->mode = o->mode;
-  b->poll = cert ? o->poll_every : 1;
-  b->pad = 0;
+// Records the grid of the search launches and rewrites the instances' lane
+// layouts (batch_layout_kernel) in a set-up workspace.
+pdscp_status set_launch(int32_t num, const void* pts_dev, void* ws_dev, const BatchHeader& bh, int ctas, int layout,
+                        cudaStream_t s) {
+  unsigned char* ws = reinterpret_cast<unsigned char*>(ws_dev);
+  cudaError_t e = cudaMemcpyAsync(ws + 256 + offsetof(BatchHeader, ctas_per_sm), &ctas, sizeof(int32_t),
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    batch_layout_kernel<<<(num + 127) / 128, 128, 0, s>>>(reinterpret_cast<BatchInst*>(ws + bh.inst_off), num,
+                                                          pts_dev, (int)batch_elem(bh.dtype), layout);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // `ctas` is a host local
+  if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: launch settings failed (%lld)", (long long)e);
   return PDSCP_OK;
 }
 
@@ -203,6 +135,7 @@ pdscp_status read_header(const void* ws_dev, cudaStream_t s, BatchHeader* bh) {
 }  // namespace pdscp
 
 using namespace pdscp;
+using namespace pdscp::batchhost;
 
 extern "C" {
 
@@ -267,7 +200,7 @@ pdscp_status ses_batch_solve_run(int32_t num, const void* pts_dev, void* ws_dev,
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     for (int k = 0; k < launches_per_poll && e == cudaSuccess; ++k)
-      e = launch_batch(pts_dev, dtype, nullptr, nullptr, ws, nullptr, search, cs, num);
+      e = launch_batch(pts_dev, dtype, nullptr, nullptr, ws, nullptr, search, cs, num, bh.ctas_per_sm);
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
     if (e == cudaSuccess) e = e2;
   }
@@ -310,7 +243,7 @@ pdscp_status ses_batch_autotune(int32_t num, const void* pts_dev, int32_t dtype,
                                 const int64_t* offset_host,
                                 const int64_t* n_host, const int32_t* d_host, const pdscp_options* opts,
                                 void* ws_dev, size_t ws_bytes, pdscp_stream stream, int32_t* tile_rows_host,
-                                float* ms_per_launch_host) {
+                                float* ms_per_launch_host, int32_t* ctas_per_sm_host, int32_t* layout_host) {
   if (!tile_rows_host) return err(PDSCP_ERR_INVALID_ARG, "batch: null output pointer");
   static const int32_t cand[] = {512, 1024, 2048, 4096, 8192, 16384, 32768};
   cudaStream_t s = (cudaStream_t)stream;
@@ -318,31 +251,42 @@ pdscp_status ses_batch_autotune(int32_t num, const void* pts_dev, int32_t dtype,
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e != cudaSuccess) return err(PDSCP_ERR_CUDA, "batch: event create failed (%lld)", (long long)e);
-  int32_t best = 0;
+  int32_t best = 0, best_ctas = 0, best_layout = 0;
   float best_ms = INFINITY;
   pdscp_status st = PDSCP_OK;
+  // every tile size that fits, with 1, 2 or 3 CTAs per SM and either layout policy
   for (int32_t tr : cand) {
     BatchLayout L;
     if (batch_layout(num, n_host, d_host, tr, &L, nullptr, nullptr, nullptr) != PDSCP_OK || L.total > ws_bytes) continue;
-    st = solve_setup(num, pts_dev, dtype, pts_len, offset_host, n_host, d_host, tr, opts, ws_dev, ws_bytes, s);
-    if (st != PDSCP_OK) break;
-    BatchHeader bh;
-    if ((st = read_header(ws_dev, s, &bh)) != PDSCP_OK) break;
-    unsigned char* ws = reinterpret_cast<unsigned char*>(ws_dev);
-    BatchSearch* search = reinterpret_cast<BatchSearch*>(ws + bh.search_off);
-    // the bounds pass and one iteration untimed, then four timed iterations
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_batch(pts_dev, dtype, nullptr, nullptr, ws, nullptr, search, s, num);
-    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = launch_batch(pts_dev, dtype, nullptr, nullptr, ws, nullptr, search, s, num);
-    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e != cudaSuccess) break;
-    if (ms / 4.f < best_ms) {
-      best_ms = ms / 4.f;
-      best = tr;
+    for (int layout = 0; layout < 2 && st == PDSCP_OK && e == cudaSuccess; ++layout) {
+      for (int ctas = 1; ctas <= 3 && st == PDSCP_OK && e == cudaSuccess; ++ctas) {
+        st = solve_setup(num, pts_dev, dtype, pts_len, offset_host, n_host, d_host, tr, opts, ws_dev, ws_bytes, s);
+        BatchHeader bh;
+        if (st == PDSCP_OK) st = read_header(ws_dev, s, &bh);
+        if (st == PDSCP_OK) st = set_launch(num, pts_dev, ws_dev, bh, ctas, layout, s);
+        if (st != PDSCP_OK) break;
+        unsigned char* ws = reinterpret_cast<unsigned char*>(ws_dev);
+        BatchSearch* search = reinterpret_cast<BatchSearch*>(ws + bh.search_off);
+        // the bounds pass and one iteration untimed, then four timed iterations
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+          e = launch_batch(pts_dev, dtype, nullptr, nullptr, ws, nullptr, search, s, num, ctas);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+          e = launch_batch(pts_dev, dtype, nullptr, nullptr, ws, nullptr, search, s, num, ctas);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) break;
+        if (ms / 4.f < best_ms) {
+          best_ms = ms / 4.f;
+          best = tr;
+          best_ctas = ctas;
+          best_layout = layout;
+        }
+      }
     }
+    if (st != PDSCP_OK || e != cudaSuccess) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -351,7 +295,22 @@ pdscp_status ses_batch_autotune(int32_t num, const void* pts_dev, int32_t dtype,
   if (best == 0) return err(PDSCP_ERR_WORKSPACE, "batch: workspace too small for every tile size");
   *tile_rows_host = best;
   if (ms_per_launch_host) *ms_per_launch_host = best_ms;
+  if (ctas_per_sm_host) *ctas_per_sm_host = best_ctas;
+  if (layout_host) *layout_host = best_layout;
   return PDSCP_OK;
+}
+
+pdscp_status ses_batch_set_launch(int32_t num, const void* pts_dev, void* ws_dev, int32_t ctas_per_sm,
+                                  int32_t layout, pdscp_stream stream) {
+  if (num < 1 || !pts_dev || !ws_dev) return err(PDSCP_ERR_INVALID_ARG, "batch: bad argument to ses_batch_set_launch");
+  if (ctas_per_sm < 0 || ctas_per_sm > 3 || layout < 0 || layout > 1)
+    return err(PDSCP_ERR_INVALID_ARG, "batch: ctas_per_sm must be in [0, 3] and layout 0 or 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  BatchHeader bh;
+  pdscp_status st = read_header(ws_dev, s, &bh);
+  if (st != PDSCP_OK) return st;
+  if (bh.num != num) return err(PDSCP_ERR_INVALID_ARG, "batch: the workspace holds %lld instances, not %lld", bh.num, num);
+  return set_launch(num, pts_dev, ws_dev, bh, ctas_per_sm, layout, s);
 }
 
 pdscp_status ses_batch_read(int32_t num, const void* ws_dev, float* mean_dev, float* best_dev, pdscp_stream stream) {

@@ -44,8 +44,8 @@ struct BatchHeader {
   int64_t num, ntiles;
   int64_t inst_off, instcnt_off, tile_off, partial_off;
   int64_t search_off;
-  int32_t dtype;  // PDSCP_F32 or PDSCP_BF16: the point type of ses_batch_*init
-  int32_t pad;
+  int32_t dtype;        // PDSCP_F32 or PDSCP_BF16: the point type of ses_batch_*init
+  int32_t ctas_per_sm;  // persistent grid of the search launches: 0 = the occupancy limit (ses_batch_set_launch)
 };
 
 // Device-side search of Sec. 3 for every instance of a batch (the rules of
@@ -101,7 +101,7 @@ struct BatchParams {
 //      rows, and each point's exponentials run once, not on several lanes);
 //   6: scalar, 8 lanes (d <= 8); 7: scalar, 32 lanes (d <= 32);
 //   8: scalar, 32 lanes x 2 (d <= 64); 5 (2 lanes, d <= 2) is kept for callers of old tables
-inline int batch_shape(int d, bool aligned4) {
+__host__ __device__ inline int batch_shape(int d, bool aligned4) {
   if (d % 4 == 0 && aligned4) {
     const int c = d / 4;
     return c <= 1 ? 0 : c <= 2 ? 1 : c <= 4 ? 2 : c <= 8 ? 3 : 4;
@@ -486,7 +486,7 @@ __device__ void batch_tile_t(const T* pts, int d, int64_t r0, int64_t r1, const 
 // (two CTAs per SM); bounded, it needs 78 with no spill, and the extra warps
 // raise the batched iteration from 4.9 to 5.9 TB/s.
 template <typename T>
-__global__ void __launch_bounds__(kBatchBlock, 3) ses_batch_kernel(BatchParams p) {
+static __global__ void __launch_bounds__(kBatchBlock, 3) ses_batch_kernel(BatchParams p) {
   __shared__ float sG[kBatchWarps * kBatchMaxD];
   __shared__ float s_sc[kBatchWarps][4];
   __shared__ float s_cs[kBatchBlock];
@@ -616,7 +616,7 @@ __global__ void __launch_bounds__(kBatchBlock, 3) ses_batch_kernel(BatchParams p
 // The search step of every instance still searching, one warp per instance,
 // after the launch that ran the instance's iteration (or evaluation pass).
 template <typename T>
-__global__ void __launch_bounds__(256) ses_batch_search_kernel(const T* pts, unsigned char* ws, int num) {
+static __global__ void __launch_bounds__(256) ses_batch_search_kernel(const T* pts, unsigned char* ws, int num) {
   const int inst = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (inst >= num) return;
   const BatchHeader* bh = reinterpret_cast<const BatchHeader*>(ws + 256);
@@ -630,7 +630,7 @@ __global__ void __launch_bounds__(256) ses_batch_search_kernel(const T* pts, uns
 
 // Fresh alpha-FTP states for every instance (t = 0, mean = v_1); one CTA per instance.
 template <typename T>
-__global__ void ses_batch_init_kernel(const T* pts, const BatchInst* inst, unsigned char* ws,
+static __global__ void ses_batch_init_kernel(const T* pts, const BatchInst* inst, unsigned char* ws,
                                       unsigned int* inst_counters) {
   const BatchInst in = inst[blockIdx.x];
   void* state = ws + in.state_off;
@@ -659,8 +659,18 @@ __global__ void ses_batch_init_kernel(const T* pts, const BatchInst* inst, unsig
   }
 }
 
+// Lane layouts of every instance for a layout policy (0: 4-element chunks
+// where d % 4 == 0 and the rows start on a 4-element boundary, otherwise
+// the scalar layouts; 1: the scalar layouts only). elem: bytes per element.
+static __global__ void batch_layout_kernel(BatchInst* inst, int num, const void* pts, int elem, int policy) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= num) return;
+  const bool aligned = ((uintptr_t)pts + (uintptr_t)inst[i].pt_off * (uintptr_t)elem) % (uintptr_t)(4 * elem) == 0;
+  inst[i].shape = batch_shape(inst[i].d, aligned && policy == 0);
+}
+
 // Means and best centres of every instance, packed at inst.mean_off.
-__global__ void ses_batch_read_kernel(const BatchInst* inst, unsigned char* ws, float* mean_out, float* best_out) {
+static __global__ void ses_batch_read_kernel(const BatchInst* inst, unsigned char* ws, float* mean_out, float* best_out) {
   const BatchInst in = inst[blockIdx.x];
   void* state = ws + in.state_off;
   for (int j = threadIdx.x; j < in.d; j += blockDim.x) {
@@ -670,7 +680,7 @@ __global__ void ses_batch_read_kernel(const BatchInst* inst, unsigned char* ws, 
 }
 
 // Per-instance search results: reports and centres (packed at inst.mean_off).
-__global__ void ses_batch_solve_read_kernel(const BatchInst* inst, const BatchSearch* search, double eps,
+static __global__ void ses_batch_solve_read_kernel(const BatchInst* inst, const BatchSearch* search, double eps,
                                             pdscp_report* rep, float* center_out) {
   const BatchInst in = inst[blockIdx.x];
   const BatchSearch& r = search[blockIdx.x];

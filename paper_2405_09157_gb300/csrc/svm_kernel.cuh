@@ -509,6 +509,11 @@ __global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
   const int64_t lo = wsp.warm ? p.n : split(gw), hi = wsp.warm ? p.n : split(gw + 1);
   // the first round's point loads do not depend on the state: issue them first
   float x[NI][VW];
+  // BF16 staged rounds are widened into float pairs for paired FP32
+  // arithmetic in the dot products and the class sums (n = 1e6, d = 128,
+  // back to back: 55.9 -> 53.7 us)
+  constexpr bool kPair = sizeof(T) == 2 && NS > 0;
+  unsigned long long x2[kPair ? NI : 1][kPair ? VW / 2 : 1];
   auto load_round = [&](int64_t base) {
 #pragma unroll
     for (int r = 0; r < NI; ++r) {
@@ -551,7 +556,10 @@ __global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
                           ? *reinterpret_cast<const uint4*>(sl + ((size_t)(r * PPW + grp) * d) * sizeof(T) + gl * 16)
                           : make_uint4(0u, 0u, 0u, 0u);
       const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-      if constexpr (sizeof(T) == 2) {
+      if constexpr (sizeof(T) == 2 && NS > 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x2[r][j] = f2_from_bf16x2(w[j]);
+      } else if constexpr (sizeof(T) == 2) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {  // bf16 -> fp32 is a 16-bit left shift of the bit pattern
           x[r][2 * j] = __uint_as_float(w[j] << 16);
@@ -610,6 +618,13 @@ __global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
     ZQ[e] = 0.f;
   }
   float SP = 0.f, SQ = 0.f, minP = INFINITY, maxQ = -INFINITY;
+  unsigned long long wb2[kPair ? VW / 2 : 1], ZP2[kPair ? VW / 2 : 1], ZQ2[kPair ? VW / 2 : 1];
+#pragma unroll
+  for (int q2 = 0; q2 < (kPair ? VW / 2 : 1); ++q2) {
+    wb2[q2] = f2_pack(wb[(2 * q2) % VW], wb[(2 * q2 + 1) % VW]);
+    ZP2[q2] = 0ull;
+    ZQ2[q2] = 0ull;
+  }
 
   int rnd = 0;
   for (int64_t base = lo; base < hi; base += ROUND, ++rnd) {
@@ -628,8 +643,17 @@ __global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
 #pragma unroll
     for (int r = 0; r < NI; ++r) {
       float a = 0.f;
+      if constexpr (kPair) {
+        unsigned long long acc = 0ull;
 #pragma unroll
-      for (int e = 0; e < VW; ++e) a = fmaf(x[r][e], wb[e], a);
+        for (int q2 = 0; q2 < VW / 2; ++q2) acc = f2_fma(x2[r][q2], wb2[q2], acc);
+        float lo2, hi2;
+        f2_unpack(acc, lo2, hi2);
+        a = lo2 + hi2;
+      } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) a = fmaf(x[r][e], wb[e], a);
+      }
       part[r] = a;
     }
     GS::run(part, gl);
@@ -659,10 +683,19 @@ __global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
     for (int r = 0; r < NI; ++r) {
       const float qr = __shfl_sync(0xffffffffu, q[r % GS::OWN], grp * LPP + GS::src_lane(r));
       const float qp = fmaxf(qr, 0.f), qq = fmaxf(-qr, 0.f);
+      if constexpr (kPair) {
+        const unsigned long long qp2 = f2_pack(qp, qp), qq2 = f2_pack(qq, qq);
 #pragma unroll
-      for (int e = 0; e < VW; ++e) {
-        ZP[e] = fmaf(qp, x[r][e], ZP[e]);
-        ZQ[e] = fmaf(qq, x[r][e], ZQ[e]);
+        for (int q2 = 0; q2 < VW / 2; ++q2) {
+          ZP2[q2] = f2_fma(qp2, x2[r][q2], ZP2[q2]);
+          ZQ2[q2] = f2_fma(qq2, x2[r][q2], ZQ2[q2]);
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          ZP[e] = fmaf(qp, x[r][e], ZP[e]);
+          ZQ[e] = fmaf(qq, x[r][e], ZQ[e]);
+        }
       }
     }
     if constexpr (NS > 0) {
@@ -681,6 +714,13 @@ __global__ void __launch_bounds__(BLOCK, 1) svm_iter_t_kernel(SvmParams p) {
     __syncthreads();  // every warp is done with its ring before the shared memory is reused
   }
 
+  if constexpr (kPair) {
+#pragma unroll
+    for (int q2 = 0; q2 < VW / 2; ++q2) {
+      f2_unpack(ZP2[q2], ZP[2 * q2], ZP[(2 * q2 + 1) % VW]);
+      f2_unpack(ZQ2[q2], ZQ[2 * q2], ZQ[(2 * q2 + 1) % VW]);
+    }
+  }
 #pragma unroll
   for (int o = LPP; o < 32; o <<= 1)
 #pragma unroll

@@ -139,6 +139,43 @@ def test_batch_validation_without_gpu(lib):
     assert lib.ses_batch_step(2, fake, 9, alpha, alpha, fake, 1 << 30, None, None) == 1
 
 
+def test_svm_batch_validation_without_gpu(lib):
+    n = (ctypes.c_int64 * 2)(100, 1)
+    d = (ctypes.c_int32 * 2)(8, 8)
+    size = ctypes.c_size_t()
+    assert lib.svm_batch_workspace_size(2, n, d, 4096, ctypes.byref(size)) == 1  # n < 2
+    n[1] = 50
+    d[1] = 65
+    assert lib.svm_batch_workspace_size(2, n, d, 4096, ctypes.byref(size)) == 7  # d > 64
+    d[1] = 8
+    assert lib.svm_batch_workspace_size(2, n, d, 4096, ctypes.byref(size)) == 0
+    ses = ctypes.c_size_t()
+    assert lib.ses_batch_workspace_size(2, n, d, 4096, ctypes.byref(ses)) == 0
+    assert size.value > ses.value  # wider partial rows, label offsets and D per instance
+    offs = (ctypes.c_int64 * 2)(0, 800)
+    loffs = (ctypes.c_int64 * 2)(0, 100)
+    fake = ctypes.c_void_p(1 << 20)
+    lab = ctypes.c_void_p(1 << 22)
+    st = lib.svm_batch_init(2, fake, _ffi.F32, 1000, offs, n, d, lab, 150, loffs, 4096, fake, 1 << 30, None)
+    assert st == 1 and b"extends past" in lib.pdscp_last_error()  # points: 800 + 400 > 1000
+    st = lib.svm_batch_init(2, fake, _ffi.F32, 2000, offs, n, d, lab, 149, loffs, 4096, fake, 1 << 30, None)
+    assert st == 1 and b"labels" in lib.pdscp_last_error()  # labels: 100 + 50 > 149
+    st = lib.svm_batch_init(2, fake, _ffi.F32, 2000, offs, n, d, None, 150, loffs, 4096, fake, 1 << 30, None)
+    assert st == 1 and b"null" in lib.pdscp_last_error()
+    st = lib.svm_batch_init(2, fake, 5, 2000, offs, n, d, lab, 150, loffs, 4096, fake, 1 << 30, None)
+    assert st == 1 and b"dtype" in lib.pdscp_last_error()
+    st = lib.svm_batch_init(2, fake, _ffi.F32, 2000, offs, n, d, lab, 150, loffs, 4096, fake, 64, None)
+    assert st == 8  # workspace too small
+    opts = _ffi.Options(1e-3, 0.0, 10, 7, 1000, 64, 10, 0.0)
+    st = lib.svm_batch_solve_init(2, fake, _ffi.F32, 2000, offs, n, d, lab, 150, loffs, 4096, ctypes.byref(opts),
+                                  fake, 1 << 30, None)
+    assert st == 1 and b"options" in lib.pdscp_last_error()
+    alpha = ctypes.c_void_p(1 << 21)
+    assert lib.svm_batch_step(2, fake, 9, lab, alpha, alpha, fake, 1 << 30, None, None) == 1
+    assert lib.svm_batch_step(2, fake, _ffi.F32, None, alpha, alpha, fake, 1 << 30, None, None) == 1
+    assert lib.svm_batch_solve_run(2, fake, None, fake, 1 << 30, 8, 100, None, None, None) == 1
+
+
 def test_shard_validation_without_gpu(lib):
     w = ctypes.c_int32()
     assert lib.mwu_shard_row_width(_ffi.SES, 32, ctypes.byref(w)) == 0 and w.value == 4 + 32
@@ -180,7 +217,11 @@ def test_batch_search_validation_without_gpu(lib):
     assert lib.ses_batch_solve_run(2, fake, fake, 1 << 30, 0, 10, None, ctypes.byref(launches),
                                    ctypes.byref(done)) == 1
     tr = ctypes.c_int32()
-    assert lib.ses_batch_autotune(2, fake, _ffi.F32, 1200, offs, n, d, None, fake, 1 << 30, None, None, None) == 1
+    assert lib.ses_batch_autotune(2, fake, _ffi.F32, 1200, offs, n, d, None, fake, 1 << 30, None, None, None, None,
+                                  None) == 1
+    assert lib.ses_batch_set_launch(2, fake, fake, 4, 0, None) == 1  # CTAs per SM outside [0, 3]
+    assert lib.ses_batch_set_launch(2, fake, fake, 1, 2, None) == 1  # unknown layout policy
+    assert lib.ses_batch_set_launch(2, None, fake, 1, 0, None) == 1
 
 
 def test_multi_validation_without_gpu(lib):

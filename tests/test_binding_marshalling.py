@@ -112,12 +112,19 @@ def test_every_entry_point_marshals(fake):
         b.step(torch.ones(2, dtype=torch.float64), torch.ones(2, dtype=torch.float64), out=api.new_steps(2, cpu))
         b.read()
         b.autotune()
+        b.set_launch(2, 1)
         b.solve(mode="certified")
+        lab, loffs = api.pack_labels([np.where(np.arange(nn_) % 2 == 0, 1, -1) for nn_ in nn], device=cpu)
+        sb = api.SvmBatch(bp, offs, nn, dd, lab, loffs, tile_rows=512)
+        sb.step(torch.ones(2, dtype=torch.float64), torch.ones(2, dtype=torch.float64), out=api.new_steps(2, cpu))
+        sb.read()
+        sb.solve(mode="certified")
     # every entry point the binding reaches was called with its declared arity
     assert {"mwu_step", "mwu_run", "mwu_backward", "ses_solve", "svm_solve", "ses_multi_step", "mwu_shard_partial",
             "mwu_shard_finish", "ses_batch_init", "ses_batch_step", "ses_batch_autotune", "ses_batch_solve_init",
-            "ses_batch_solve_run", "ses_batch_solve_read", "mwu_step_noalloc", "mwu_state_set",
-            "pdscp_polytope_distance"} <= set(fake.calls)
+            "ses_batch_solve_run", "ses_batch_solve_read", "mwu_step_noalloc", "mwu_state_set", "ses_batch_set_launch",
+            "pdscp_polytope_distance", "svm_batch_init", "svm_batch_step", "svm_batch_read", "svm_batch_solve_init",
+            "svm_batch_solve_run", "svm_batch_solve_read"} <= set(fake.calls)
 
 
 def test_binding_rejects_bad_buffers(fake):

@@ -179,12 +179,45 @@ def test_batch_autotune_and_budget():
     batch = api.SesBatch(pts, offs, n, d, tile_rows=4096)
     tr, ms = batch.autotune()
     assert tr in (512, 1024, 2048, 4096, 8192, 16384, 32768) and ms > 0
+    assert batch.ctas_per_sm in (1, 2, 3) and batch.layout in (0, 1)
     # a budget too small to converge: every instance stops with NOT_CONVERGED and its certificates
     reps, centres, _ = batch.solve(eps=1e-6, max_iters=50)
     for k, a in enumerate(arrays):
         assert reps[k]["status"] == 5 and reps[k]["iters"] <= 50
         f = oses.ses_objective(a.astype(np.float64), None, centres[k].astype(np.float64))
         assert f <= reps[k]["upper_bound"] * (1 + 1e-5)
+
+
+@pytest.mark.parametrize("ctas,layout", [(1, 0), (2, 1), (3, 1)])
+def test_batch_launch_settings_keep_the_results(ctas, layout):
+    # the persistent grid's CTAs per SM and the scalar-only layout change the order of the FP32
+    # partial sums, not the iteration: each search still brackets the exact optimum, and the
+    # layouts' trajectories agree with the default within the tolerance
+    arrays = [datagen.ses_uniform(n, 2, seed=700 + n) for n in (800, 3000)] + \
+             [datagen.ses_gaussian(n, dd, seed=710 + dd) for n, dd in [(4000, 16), (1500, 32), (900, 8)]]
+    from oracle import exact
+    pts, offs, n, d = api.pack_instances(arrays)
+    base = api.SesBatch(pts, offs, n, d, tile_rows=512)
+    tuned = api.SesBatch(pts, offs, n, d, tile_rows=512)
+    tuned.set_launch(ctas, layout)
+    a = torch.tensor([2.0] * len(arrays), dtype=torch.float64, device="cuda")
+    e = torch.tensor([0.01] * len(arrays), dtype=torch.float64, device="cuda")
+    outs = []
+    for b in (base, tuned):
+        out = api.new_steps(len(arrays))
+        for _ in range(10):
+            b.step(a, e, out=out)
+        torch.cuda.synchronize()
+        outs.append(api.decode_steps(out))
+    for key in ("objective", "oracle_value"):
+        assert np.allclose(outs[0][key], outs[1][key], rtol=0, atol=2e-5 * 10.0)
+    reps, _, _ = tuned.solve(eps=1e-3, mode="certified", max_iters=200_000, poll_every=64, launches_per_poll=16)
+    for k in range(2):  # d = 2: Welzl's exact radius
+        opt = exact.mec_2d(arrays[k].astype(np.float64))[1]
+        assert reps[k]["status"] == 0, (k, reps[k])
+        assert reps[k]["lower_bound"] <= opt * (1 + 1e-5) and reps[k]["upper_bound"] >= opt * (1 - 1e-5)
+    assert np.all(reps["status"] == 0)
+    assert np.all(reps["upper_bound"] <= (1 + 1e-3) * reps["lower_bound"] * (1 + 1e-5) + 1e-7)
 
 
 def test_batch_full_workload_sampled_instances():
