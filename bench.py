@@ -658,7 +658,8 @@ def variants(dev, flush):
 def multi_variant(dev, flush, K=50):
     """Multi-candidate pass (ses_multi_step) on the default workload: k alpha-FTPs
     (alpha_j = (1 + 0.05 j) D, never separating) advanced by one pass over the
-    1,000,000 x 32 FP32 points, k in {1, 2, 4, 8}, timed as the main line (L2
+    1,000,000 x 32 FP32 points, k in {1, 2, 4, 8, 16} (k = 16: the tensor-core
+    pass), timed as the main line (L2
     flushed between steps, CUDA events around each step). Bytes per pass are
     those of one iteration; per point the arithmetic grows k-fold."""
     import torch
@@ -669,7 +670,7 @@ def multi_variant(dev, flush, K=50):
     D = float(api.bounds(_ffi.SES, pts).item())
     eor = 0.01 / (3 * D / math.sqrt(2))
     res = {}
-    for k in (1, 2, 4, 8):
+    for k in (1, 2, 4, 8, 16):  # k = 16: the tensor-core pass
         m = api.MultiMWU(pts, k)
         a = torch.tensor([(1.0 + 0.05 * j) * D for j in range(k)], dtype=torch.float64, device=dev)
         e = torch.full((k,), eor, dtype=torch.float64, device=dev)
@@ -690,7 +691,7 @@ def multi_variant(dev, flush, K=50):
         ms = sum(x.elapsed_time(y) for x, y in zip(s0, s1)) / K
         b = N_POINTS * DIM * 4
         res[f"k{k}"] = {"ms_per_pass": ms, "candidate_iters_per_s": k * 1e3 / ms, "GBps": b / ms / 1e6,
-                        "frac_hbm": b / ms / 1e6 / peak}
+                        "frac_hbm": b / ms / 1e6 / peak, "tensor_cores": k == 16}
     return res
 
 

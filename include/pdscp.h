@@ -546,11 +546,15 @@ pdscp_status mwu_shard_finish(int32_t problem, const float* rows_dev, int32_t ra
 
 /*
  * Multi-candidate SES iteration: one streaming pass over the points advances
- * k in {1, 2, 4, 8} independent alpha-FTPs of the same instance (Sec. 3 with
- * the SES data of Sec. 4.1), each with its own alpha_j, eta_j/rho and state:
- * the candidates of a k-ary search over alpha share every byte read. Float32
- * points, d <= 64. Per candidate the result is that of mwu_step with the same
- * alpha_j, eta_j/rho and state (up to the order of the FP32 partial sums).
+ * k in {1, 2, 4, 8, 16} independent alpha-FTPs of the same instance (Sec. 3
+ * with the SES data of Sec. 4.1), each with its own alpha_j, eta_j/rho and
+ * state: the candidates of a k-ary search over alpha share every byte read.
+ * Float32 points, d <= 64; k = 16 needs d = 32 and a 16-byte aligned pts_dev
+ * and runs on the tensor cores (the squared distances' cross terms and the
+ * weighted sums as tf32 MMAs on three-part operand splits, accumulators in
+ * tensor memory, point tiles loaded by TMA).
+ * Per candidate the result is that of mwu_step with the same alpha_j,
+ * eta_j/rho and state (up to the order and splitting of the FP32 sums).
  *   ses_multi_state_stride: bytes between consecutive candidate states in
  *     states_dev (a multiple of 256); each state is started with
  *     mwu_state_init (PDSCP_SES, the same points) at states_dev + j * stride.

@@ -194,7 +194,8 @@ def state_set(problem, pts, t, mean, state, ws, radii=None, labels=None, D=0.0, 
 class MultiMWU:
     """k alpha-FTPs of one SES instance (float32 points, d <= 64) advanced by
     one pass over the points per iteration, each with its own alpha and
-    eta/rho (k in {1, 2, 4, 8})."""
+    eta/rho (k in {1, 2, 4, 8, 16}; k = 16 needs d = 32 and runs on the
+    tensor cores)."""
 
     def __init__(self, pts, k, radii=None, rules=_ffi.RULES_NONE, delta=1e-4, patience=10, stream=None):
         n, d, dt = _points(pts)

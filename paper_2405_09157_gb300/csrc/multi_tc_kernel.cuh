@@ -1,0 +1,502 @@
+// Tensor-core form of the multi-candidate SES pass (multi_kernel.cuh) for
+// float32 points of d = 32 and up to 16 candidates. Per candidate j and point
+// i the pass needs the squared distance |x_i - u_j|^2 and, after the
+// exponentials, the weighted sum G'_j = sum_i c_ij (x_i - u_j) (Sec. 4.1,
+// Eq. implement and Eq. ses_oracle). Both are dense contractions over a tile
+// of 128 points, run as tcgen05 MMAs (kind::tf32) with accumulators in TMEM:
+//   P = Y U~^T        (128 x 16, K = 32):  y_i = x_i - m, u~_j = u_j - m,
+//                     |x_i - u_j|^2 = |y_i|^2 - 2 P_ij + |u~_j|^2
+//   Q = Y^T C         (32 x 16, K = 128 points, accumulated over every tile
+//                     of the CTA): sum_i c_ij y_i, and G'_j = Q_j - (sum_i c_ij) u~_j,
+// with m the average of the candidates' means (FP32, the same in every CTA).
+// Centring on m keeps both identities' cancellation small: u~_j is short, so
+// |y_i|^2 dominates the distance, and Q_j differs from G'_j only by
+// (sum_i c_ij) u~_j (centred on v_1 instead, Q_j carried the whole offset
+// between the means and v_1, and its tf32-split rounding, ~2^-22 of it,
+// showed in the means after a few amplifying iterations). FP32 accuracy
+// from tf32 operands: each operand a is split as a = a_h + a_l with a_h its
+// tf32 truncation, stored as such (exact in tf32), and a_l = a - a_h exact in
+// FP32 (its own tf32 conversion costs at most 2^-22 of a), and a.b = a_h.b_h +
+// a_h.b_l + a_l.b_h up to ~2^-22 relative. That is four times FP32's
+// rounding, and both contractions cancel (the distance identity for points
+// near a mean, G'_j against sum_i c_ij |y_i| near the equilibrium), so both
+// split their operands in three exact tf32 parts (a = a_1 + a_2 + a_3, a_2
+// the truncation of a - a_1, a_3 the rest, at most 2 bits) and keep the six
+// products down to 2^-22 of each other: FP32-grade results. The exponentials stay on the CUDA cores: thread r of the first
+// 128 reads row r of P for candidates 0-7 out of TMEM, thread 128 + r for
+// candidates 8-15.
+//
+// Operands in shared memory use the 128-byte swizzled K-major layout: a tile
+// of 128 points x 32 floats arrives from HBM by one TMA load with the 128-byte
+// swizzle, which is that layout for Y in P (rows: points, K: features; y_1 is
+// written over x in place, y_2 and y_3 beside it). For Q
+// the points must be the K dimension: the threads write Y^T (rows 0-31, 32-63,
+// 64-95: y_1, y_2, y_3) and C^T (16 rows: candidates, one buffer per part) in
+// the same layout, each warp writing one feature (or candidate) row for 32
+// consecutive points, which falls on 32 distinct banks. Q's M dimension is
+// 128: rows 96-127 are not read back. One MMA chain per part of C gives
+// y_1 c_1, y_2 c_1, y_3 c_1 (with c_1), y_1 c_2, y_2 c_2 (with c_2), y_1 c_3.
+//
+// Waits on the TMA loads and on the MMAs' completion are bounded (the
+// staged passes' limit); a wait that gives up poisons the CTA's rows (S =
+// NaN), so that the finishes report PDSCP_ERR_NUMERIC, and the kernel still
+// waits (bounded) for its MMAs before it frees its TMEM.
+#pragma once
+
+#include <cuda.h>
+
+#include "multi_kernel.cuh"
+
+namespace pdscp {
+
+constexpr int kTcTile = 128;   // points per tile (the MMAs' M for P)
+constexpr int kTcD = 32;       // features (one 128-byte swizzle row of floats)
+constexpr int kTcN = 16;       // candidate columns (the MMAs' N)
+constexpr int kTcThreads = 256;
+// dynamic shared memory (bytes from a 1024-aligned base)
+constexpr int kTcStage0 = 0, kTcStage1 = 16384;  // TMA tiles (y_1 written in place)
+constexpr int kTcY2 = 32768, kTcY3 = 49152;       // y_2, y_3: same layout
+constexpr int kTcA2 = 65536;                      // Q's A operand: 128 rows x 128 points
+// P's B operand: [u~_1; u~_2; u~_3] stacked, 48 rows x 32 features (the three
+// 16-row parts are contiguous: each is two 1024-byte atoms)
+constexpr int kTcU = 131072;
+// Q's B operand: [c_1; c_2; c_3] stacked, 48 rows x 128 points
+constexpr int kTcC = 137216;
+constexpr int kTcSmem = 161792 + 1024;  // + alignment slack
+// TMEM columns: P's six products at 0-95 (y_1 [u_1 u_2 u_3], y_2 [u_1 u_2],
+// y_3 u_1: 16 columns each), Q at 128-175 ([c_1 c_2 c_3])
+constexpr int kTcTmemCols = 256;
+constexpr int kTcQCol = 128;
+
+// byte offset of element (row, col) in a 128-byte swizzled K-major operand of
+// `rows` rows (col along K, 32 floats per 128-byte atom row)
+__host__ __device__ __forceinline__ int tc_sw128(int row, int col, int rows) {
+  return (col >> 5) * rows * 128 + (row >> 3) * 1024 + (row & 7) * 128 + ((((col & 31) >> 2) ^ (row & 7)) << 4) +
+         ((col & 3) << 2);
+}
+
+// shared-memory matrix descriptor: 128-byte swizzle, 8-row atoms 1024 bytes apart
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                  // leading byte offset (unused by K-major swizzled layouts)
+  d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;                  // descriptor version of the sm_100 family
+  d |= (uint64_t)2 << 61;                  // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor: kind::tf32, FP32 accumulators, A and B K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t tc_idesc(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, bool acc) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+               ::"r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc ? 1u : 0u)
+               : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+// 8 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tc_ld8(uint32_t addr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(addr)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+// a's tf32 truncation (exactly representable: whatever rounding the tensor
+// core applies to its FP32 operands leaves it unchanged) and the low part
+// a - hi, exact in FP32
+__device__ __forceinline__ float tc_hi(float a) { return __uint_as_float(__float_as_uint(a) & 0xFFFFE000u); }
+__device__ __forceinline__ float tc_lo(float a) { return a - tc_hi(a); }
+// a = p1 + p2 + p3, each exactly representable in tf32
+__device__ __forceinline__ void tc_split3(float a, float& p1, float& p2, float& p3) {
+  p1 = tc_hi(a);
+  const float r = a - p1;
+  p2 = tc_hi(r);
+  p3 = r - p2;
+}
+
+__device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap* map, int row0, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(kTcTile * kTcD * 4)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+      "l"(map), "r"(0), "r"(row0), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// One pass for K <= 16 candidates (states, alphas, step sizes as in
+// ses_multi_kernel), points streamed through TMA in tiles of 128; one CTA per
+// SM takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...; then the completion
+// of ses_multi_kernel (the last CTA reduces the K candidate rows, the warps
+// run the finishes).
+template <int K>
+__global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams p, unsigned int wait_limit,
+                                                                     const __grid_constant__ CUtensorMap tmap) {
+  static_assert(K >= 1 && K <= kTcN, "up to 16 candidates");
+  extern __shared__ __align__(128) unsigned char smem_raw[];  // aligned to 1024 below (the swizzle atoms)
+  unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t s_bar[4];  // TMA stage 0, stage 1, P done, Q done
+  __shared__ uint32_t s_tmem;
+  __shared__ float s_norm[2][kTcTile];
+  __shared__ float s_v1[kTcD], s_ctr[kTcD], s_un[kTcN], s_kr[kTcN], s_H[kTcN], s_al[kTcN];
+  __shared__ int s_live[kTcN];
+  __shared__ float s_sc[kTcThreads / 32][kTcN][4];
+  __shared__ float s_q[kTcN][kTcD];
+  __shared__ float2 s_scr[kBlock];
+  __shared__ __align__(16) double s_hdr[K][sizeof(StateHdr) / 8];
+  __shared__ bool s_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int d = kTcD, dp = kTcD;
+  const int st = ses_partial_stride(d);
+  const float* pts = reinterpret_cast<const float*>(p.pts);
+  const int64_t ntiles = (p.n + kTcTile - 1) / kTcTile;
+
+  // ---- set-up: candidates, v_1, the centre m, U~ in both parts, barriers, TMEM
+  if (tid < kTcD) {
+    s_v1[tid] = __ldg(pts + tid);
+    float m = 0.f;
+    for (int q = 0; q < K; ++q) m += state_mean32(p.states + (size_t)q * p.state_stride, d)[tid];
+    s_ctr[tid] = m * (1.f / (float)K);
+  }
+  if (tid < kTcN) {
+    const int q = tid;
+    if (q < K) {
+      const StateHdr* hdr = reinterpret_cast<const StateHdr*>(p.states + (size_t)q * p.state_stride);
+      s_live[q] = hdr->stopped == 0;
+      s_kr[q] = ses_kr(hdr->t, p.eta_over_rho[q]);
+      s_H[q] = (float)(hdr->hint + hdr->move);
+      s_al[q] = (float)p.alpha[q];
+    } else {
+      s_live[q] = 0;
+      s_kr[q] = 0.f;
+      s_H[q] = 0.f;
+      s_al[q] = 0.f;
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < kTcN * kTcD; idx += kTcThreads) {  // u~_j = u_j - m (0 for padding columns)
+    const int q = idx / kTcD, e = idx % kTcD;
+    const float u = q < K ? state_mean32(p.states + (size_t)q * p.state_stride, d)[e] - s_ctr[e] : 0.f;
+    float u1, u2, u3;
+    tc_split3(u, u1, u2, u3);
+    *reinterpret_cast<float*>(sm + kTcU + tc_sw128(q, e, 3 * kTcN)) = u1;
+    *reinterpret_cast<float*>(sm + kTcU + tc_sw128(kTcN + q, e, 3 * kTcN)) = u2;
+    *reinterpret_cast<float*>(sm + kTcU + tc_sw128(2 * kTcN + q, e, 3 * kTcN)) = u3;
+  }
+  if (tid < kTcN) {
+    float s = 0.f;
+    for (int e = 0; e < kTcD; ++e) {
+      const float u = tid < K ? state_mean32(p.states + (size_t)tid * p.state_stride, d)[e] - s_ctr[e] : 0.f;
+      s = fmaf(u, u, s);
+    }
+    s_un[tid] = s;
+  }
+  if (tid == 0) {
+    for (int b = 0; b < 4; ++b) mbar_init(s_bar + b, 1);
+    mbar_init_fence();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
+                 "r"(kTcTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t sbase = smem_u32(sm);
+
+  // this thread's candidates (half h of the 16 columns) and row r of a tile
+  const int r = tid & (kTcTile - 1), h = tid >> 7;
+  float S[8], W[8], M[8], Cs[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    S[j] = 0.f;
+    W[j] = 0.f;
+    M[j] = -INFINITY;
+    Cs[j] = 0.f;
+  }
+  bool ok = true;
+  int it = 0;
+  // what may still be in flight if a wait gives up: the awaited load or MMAs
+  // (fail_at: 1 the tile's load, 2 P, 3 Q) and the prefetched tile
+  bool pend_tma = false;
+  int fail_at = 0;
+  if (tid == 0 && (int64_t)blockIdx.x < ntiles) tma_load_tile(sbase + kTcStage0, &tmap, blockIdx.x * kTcTile, s_bar + 0);
+  for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+    const int stage = it & 1;
+    const uint32_t tbase = sbase + (stage ? kTcStage1 : kTcStage0);
+    unsigned char* tptr = sm + (stage ? kTcStage1 : kTcStage0);
+    // the next tile into the other stage (its previous tile's MMAs are done)
+    pend_tma = tile + gridDim.x < ntiles;
+    if (tid == 0 && pend_tma)
+      tma_load_tile(sbase + (stage ? kTcStage0 : kTcStage1), &tmap, (int)((tile + gridDim.x) * kTcTile),
+                    s_bar + (stage ? 0 : 1));
+    // every decision to give up is taken by the whole CTA (__syncthreads_and)
+    if (!__syncthreads_and(mbar_wait(s_bar + stage, (unsigned int)(it >> 1) & 1u, wait_limit))) {
+      ok = false;
+      fail_at = 1;
+      break;
+    }
+    // ---- y = x - v_1 in place, its low parts, row norms, and Y^T for Q:
+    // thread (r, h) takes logical chunks 4h .. 4h + 3 of row r (16 features)
+    const int64_t g = tile * kTcTile + r;
+    const bool valid = g < p.n;
+    float nrm = 0.f;
+#pragma unroll
+    for (int c4 = 0; c4 < 4; ++c4) {
+      const int lc = 4 * h + c4;
+      const int off = r * 128 + ((lc ^ (r & 7)) << 4);
+      float4 x = *reinterpret_cast<const float4*>(tptr + off);
+      const int e0 = 4 * lc;
+      float y[4] = {valid ? x.x - s_ctr[e0] : 0.f, valid ? x.y - s_ctr[e0 + 1] : 0.f,
+                    valid ? x.z - s_ctr[e0 + 2] : 0.f, valid ? x.w - s_ctr[e0 + 3] : 0.f};
+      float y1[4], y2[4], y3[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        tc_split3(y[e], y1[e], y2[e], y3[e]);
+        nrm = fmaf(y[e], y[e], nrm);
+      }
+      *reinterpret_cast<float4*>(tptr + off) = make_float4(y1[0], y1[1], y1[2], y1[3]);
+      *reinterpret_cast<float4*>(sm + kTcY2 + off) = make_float4(y2[0], y2[1], y2[2], y2[3]);
+      *reinterpret_cast<float4*>(sm + kTcY3 + off) = make_float4(y3[0], y3[1], y3[2], y3[3]);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        *reinterpret_cast<float*>(sm + kTcA2 + tc_sw128(e0 + e, r, 128)) = y1[e];
+        *reinterpret_cast<float*>(sm + kTcA2 + tc_sw128(kTcD + e0 + e, r, 128)) = y2[e];
+        *reinterpret_cast<float*>(sm + kTcA2 + tc_sw128(2 * kTcD + e0 + e, r, 128)) = y3[e];
+      }
+    }
+    s_norm[h][r] = nrm;
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    // ---- P = Y U~^T: six products of the three-part splits in three MMA
+    // chains (N = 48, 32, 16 rows of the stacked U~ parts), one thread issues;
+    // descriptors advance by (bytes >> 4) in their address field
+    if (tid == 0) {
+      const uint64_t dy1 = tc_desc(tbase), dy2 = tc_desc(sbase + kTcY2), dy3 = tc_desc(sbase + kTcY3);
+      const uint64_t du = tc_desc(sbase + kTcU);
+#pragma unroll
+      for (int s = 0; s < kTcD / 8; ++s) {
+        const uint64_t ks = (uint64_t)(s * 32 >> 4);
+        tc_mma(tmem, dy1 + ks, du + ks, tc_idesc(48), s > 0);       // y_1 [u_1 u_2 u_3]
+        tc_mma(tmem + 48, dy2 + ks, du + ks, tc_idesc(32), s > 0);  // y_2 [u_1 u_2]
+        tc_mma(tmem + 80, dy3 + ks, du + ks, tc_idesc(16), s > 0);  // y_3 u_1
+      }
+      tc_commit(s_bar + 2);
+    }
+    if (!__syncthreads_and(mbar_wait(s_bar + 2, (unsigned int)it & 1u, wait_limit))) {
+      ok = false;
+      fail_at = 2;
+      break;
+    }
+    tc_fence_after();
+    float P[8];
+    {
+      const uint32_t la = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 8 * h;
+      float p11[8], p12[8], p13[8], p21[8], p22[8], p31[8];
+      tc_ld8(la, p11);
+      tc_ld8(la + 16, p12);
+      tc_ld8(la + 32, p13);
+      tc_ld8(la + 48, p21);
+      tc_ld8(la + 64, p22);
+      tc_ld8(la + 80, p31);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) P[j] = (((p31[j] + p22[j]) + p13[j]) + (p21[j] + p12[j])) + p11[j];
+    }
+    // ---- exponentials of the 8 candidates of this thread, C^T for Q
+    const float yn = s_norm[0][r] + s_norm[1][r];
+    const bool cone = valid && g >= 1;
+    const float gam = (cone && p.radii) ? __ldg(p.radii + g) : 0.f;
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      const int q = 8 * h + jj;
+      float c = 0.f;
+      if (cone && s_live[q]) {
+        const float kr = s_kr[q];
+        const float dist = sqrtf(fmaxf(yn - 2.f * P[jj] + s_un[q], 0.f));
+        const float a = s_al[q] - gam;
+        const float E1 = expf(kr * ((dist + gam) - s_H[q]));
+        const float em = -expm1f(-2.f * kr * dist);
+        const float dif = E1 * em;
+        const float sum = E1 * (2.f - em);
+        c = dist > 0.f ? dif / dist : 2.f * kr * E1;
+        S[jj] += sum;
+        W[jj] += a * sum - dist * dif;
+        M[jj] = fmaxf(M[jj], dist + gam);
+        Cs[jj] += c;
+      }
+      float c1, c2, c3;
+      tc_split3(c, c1, c2, c3);
+      *reinterpret_cast<float*>(sm + kTcC + tc_sw128(q, r, 3 * kTcN)) = c1;
+      *reinterpret_cast<float*>(sm + kTcC + tc_sw128(kTcN + q, r, 3 * kTcN)) = c2;
+      *reinterpret_cast<float*>(sm + kTcC + tc_sw128(2 * kTcN + q, r, 3 * kTcN)) = c3;
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    // ---- Q += [Y_1^T; Y_2^T; Y_3^T] [c_1 c_2 c_3] over this tile's 128 points: one
+    // chain of N = 48
+    if (tid == 0) {
+      const uint64_t da = tc_desc(sbase + kTcA2), dc = tc_desc(sbase + kTcC);
+#pragma unroll 4
+      for (int s = 0; s < kTcTile / 8; ++s) {
+        const uint64_t ka = (uint64_t)(((s >> 2) * 128 * 128 + (s & 3) * 32) >> 4);
+        const uint64_t kb = (uint64_t)(((s >> 2) * 3 * kTcN * 128 + (s & 3) * 32) >> 4);
+        tc_mma(tmem + kTcQCol, da + ka, dc + kb, tc_idesc(48), it > 0 || s > 0);
+      }
+      tc_commit(s_bar + 3);
+    }
+    // the operands of Q are rewritten by the next tile: wait for these MMAs
+    if (!__syncthreads_and(mbar_wait(s_bar + 3, (unsigned int)it & 1u, wait_limit))) {
+      ok = false;
+      fail_at = 3;
+      break;
+    }
+    tc_fence_after();
+  }
+  // a wait that gave up: wait (bounded, at least the default tries) for what
+  // this CTA still has in flight before its TMEM and shared memory go
+  if (!ok) {
+    const unsigned int lim = wait_limit > kWaitLimit ? wait_limit : kWaitLimit;
+    if (fail_at == 1) mbar_wait(s_bar + (it & 1), (unsigned int)(it >> 1) & 1u, lim);
+    if (fail_at == 2) mbar_wait(s_bar + 2, (unsigned int)it & 1u, lim);
+    if (fail_at == 3) mbar_wait(s_bar + 3, (unsigned int)it & 1u, lim);
+    if (pend_tma) mbar_wait(s_bar + ((it + 1) & 1), (unsigned int)((it + 1) >> 1) & 1u, lim);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  // ---- Q out of TMEM: lanes 0-31 hold y_1^T C_b (columns kTcQCol + 16 (b - 1) ..),
+  // lanes 32-63 y_2^T C_b, lanes 64-95 y_3^T C_b; the six products kept are
+  // summed smallest first
+  {
+    const bool have = it > 0 && ok;
+    if (warp == 2) {  // y_3 c_1
+      for (int c8 = 0; c8 < 2; ++c8) {
+        float a[8];
+        tc_ld8(tmem + (64u << 16) + kTcQCol + 8 * c8, a);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s_q[8 * c8 + j][lane] = have ? a[j] : 0.f;
+      }
+    }
+    __syncthreads();
+    if (warp == 1) {  // y_2 c_2, y_2 c_1
+      for (int c8 = 0; c8 < 2; ++c8) {
+        float a[8], b[8];
+        tc_ld8(tmem + (32u << 16) + kTcQCol + 16 + 8 * c8, b);
+        tc_ld8(tmem + (32u << 16) + kTcQCol + 8 * c8, a);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (have) s_q[8 * c8 + j][lane] += b[j] + a[j];
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {  // y_1 c_3, y_1 c_2, y_1 c_1
+      for (int c8 = 0; c8 < 2; ++c8) {
+        float a[8], b[8], c[8];
+        tc_ld8(tmem + kTcQCol + 32 + 8 * c8, c);
+        tc_ld8(tmem + kTcQCol + 16 + 8 * c8, b);
+        tc_ld8(tmem + kTcQCol + 8 * c8, a);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (have) s_q[8 * c8 + j][lane] = ((s_q[8 * c8 + j][lane] + c[j]) + b[j]) + a[j];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
+  // ---- per-CTA candidate rows [S, Wt, maxd, 0, G'_1..G'_32]
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
+    float s0 = S[jj], s1 = W[jj], m = M[jj], cs = Cs[jj];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      cs += __shfl_xor_sync(0xffffffffu, cs, o);
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if (lane == 0) {
+      s_sc[warp][8 * h + jj][0] = s0;
+      s_sc[warp][8 * h + jj][1] = s1;
+      s_sc[warp][8 * h + jj][2] = m;
+      s_sc[warp][8 * h + jj][3] = cs;
+    }
+  }
+  __syncthreads();
+  const int wst = K * st;
+  float* prow = p.partials + (size_t)blockIdx.x * wst;
+  __shared__ float s_tot[kTcN][4];
+  if (tid < K) {
+    const int q = tid, w0 = q < 8 ? 0 : 4;  // warps 0-3 hold candidates 0-7, warps 4-7 candidates 8-15
+    float s0 = 0.f, s1 = 0.f, cs = 0.f, m = -INFINITY;
+    for (int w = w0; w < w0 + 4; ++w) {
+      s0 += s_sc[w][q][0];
+      s1 += s_sc[w][q][1];
+      m = fmaxf(m, s_sc[w][q][2]);
+      cs += s_sc[w][q][3];
+    }
+    s_tot[q][0] = ok ? s0 : NAN;  // a wait that gave up poisons the row
+    s_tot[q][1] = s1;
+    s_tot[q][2] = m;
+    s_tot[q][3] = cs;
+    prow[q * st + 0] = s_tot[q][0];
+    prow[q * st + 1] = s1;
+    prow[q * st + 2] = m;
+    prow[q * st + 3] = 0.f;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < K * dp; idx += kTcThreads) {
+    const int q = idx / dp, e = idx % dp;
+    const float u = state_mean32(p.states + (size_t)q * p.state_stride, d)[e] - s_ctr[e];
+    prow[q * st + 4 + e] = s_q[q][e] - s_tot[q][3] * u;  // sum_i c_ij (y_i - u~_j)
+  }
+
+  // ---- completion (as ses_multi_kernel): the last CTA reduces, warps finish candidates
+  auto opof = [st](int pc) { return (pc % st) == 2 ? 1 : 0; };
+  if (!arrive_pass(p.partials, wst, p.grows, p.counter, s_scr, &s_flag, opof, p.single)) return;
+  float2* raw = reinterpret_cast<float2*>(sm);
+  double* s_mean = reinterpret_cast<double*>(sm) + wst;
+  double* s_v1d = s_mean + K * dp;
+  float* stage = reinterpret_cast<float*>(s_v1d + dp);
+  constexpr int HW = (int)(sizeof(StateHdr) / 8);
+  for (int idx = tid; idx < K * HW; idx += kTcThreads) {
+    const int q = idx / HW, w = idx % HW;
+    s_hdr[q][w] = reinterpret_cast<const double*>(p.states + (size_t)q * p.state_stride)[w];
+  }
+  for (int idx = tid; idx < K * dp; idx += kTcThreads) {
+    const int q = idx / dp, e = idx % dp;
+    s_mean[idx] = state_mean(p.states + (size_t)q * p.state_stride)[e];
+  }
+  if (tid < d) s_v1d[tid] = (double)s_v1[tid];
+  final_reduce(p.partials, wst, p.grows, p.counter, s_scr, opof, raw, stage, p.single, 2, -1, st);
+  __syncthreads();
+  const double gam1 = p.radii ? (double)__ldg(p.radii) : 0.0;
+  for (int q = warp; q < K; q += kTcThreads / 32) {
+    const StateHdr& hq = *reinterpret_cast<const StateHdr*>(s_hdr[q]);
+    if (hq.stopped) continue;  // a stopped FTP is left as is
+    ses_finish_warp(raw + q * st, s_mean + q * dp, s_v1d, hq, p.states + (size_t)q * p.state_stride, d, p.alpha[q],
+                    gam1, p.eta_over_rho[q], 0, p.out ? p.out + q : nullptr);
+  }
+}
+
+}  // namespace pdscp
