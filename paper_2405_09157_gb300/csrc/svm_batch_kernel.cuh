@@ -149,6 +149,112 @@ __device__ void svm_batch_tile(const T* pts, const int8_t* lab, int d, int64_t r
   }
 }
 
+// svm_batch_tile for rows of 4-element chunks (d = 4 .. 64, d % 4 == 0, rows
+// aligned): each warp streams one contiguous part of the tile, NI points per
+// lane per round, and each point's margin, label test and exponential run
+// once, on the lane that owns the point after a reduce-scatter of the partial
+// dot products (GroupScatter, as in svm_iter_t_kernel); the signed weight
+// y_i e^{...} is broadcast back for the class sums Z_P, Z_Q.
+template <typename T, int VW, int LPP, int NI>
+__device__ void svm_batch_tile_t(const T* pts, const int8_t* lab, int d, int64_t r0, int64_t r1, const float* s_wb,
+                                 float k, float Hm, float s1, float s2, float* sZ, float (*s_sc)[4]) {
+  using GS = GroupScatter<LPP, NI>;
+  const int nch = d / VW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / LPP, gl = lane % LPP;
+  constexpr int PPW = 32 / LPP;
+  constexpr int ROUND = PPW * NI;
+  const bool owner = (gl % GS::SHARE) == 0;
+  const bool has_chunk = gl < nch;
+  const int64_t len = r1 - r0;
+  const int64_t lo = r0 + (int64_t)warp * len / kBatchWarps, hi = r0 + (int64_t)(warp + 1) * len / kBatchWarps;
+  float wb[VW], ZP[VW], ZQ[VW];
+#pragma unroll
+  for (int e = 0; e < VW; ++e) {
+    wb[e] = has_chunk ? s_wb[gl * VW + e] : 0.f;
+    ZP[e] = 0.f;
+    ZQ[e] = 0.f;
+  }
+  float SP = 0.f, SQ = 0.f, minP = INFINITY, maxQ = -INFINITY;
+  for (int64_t base = lo; base < hi; base += ROUND) {
+    float x[NI][VW];
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const int64_t i = base + r * PPW + grp;
+      if (i < hi && has_chunk) {
+        Chunk<T, VW>::load(pts + i * d, gl, x[r]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) x[r][e] = 0.f;
+      }
+    }
+    float part[NI];
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      float a = 0.f;
+#pragma unroll
+      for (int e = 0; e < VW; ++e) a = fmaf(x[r][e], wb[e], a);
+      part[r] = a;
+    }
+    GS::run(part, gl);
+    float q[GS::OWN];  // y_i e^{-k (m_i - Hm)}, signed by the label
+#pragma unroll
+    for (int kk = 0; kk < GS::OWN; ++kk) {
+      const int64_t i = base + GS::owned(gl, kk) * PPW + grp;
+      q[kk] = 0.f;
+      if (i < hi) {
+        const float dot = part[kk];
+        const bool pos = __ldg(lab + i) > 0;
+        const float margin = pos ? dot - s1 : -dot - s2;
+        const float pt = expf(-k * (margin - Hm));
+        q[kk] = pos ? pt : -pt;
+        if (owner) {
+          if (pos) {
+            SP += pt;
+            minP = fminf(minP, dot);
+          } else {
+            SQ += pt;
+            maxQ = fmaxf(maxQ, dot);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const float qr = __shfl_sync(0xffffffffu, q[r % GS::OWN], grp * LPP + GS::src_lane(r));
+      const float qp = fmaxf(qr, 0.f), qq = fmaxf(-qr, 0.f);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        ZP[e] = fmaf(qp, x[r][e], ZP[e]);
+        ZQ[e] = fmaf(qq, x[r][e], ZQ[e]);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = LPP; o < 32; o <<= 1)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      ZP[e] += __shfl_xor_sync(0xffffffffu, ZP[e], o);
+      ZQ[e] += __shfl_xor_sync(0xffffffffu, ZQ[e], o);
+    }
+  SP = warp_sum(SP);
+  SQ = warp_sum(SQ);
+  minP = warp_min(minP);
+  maxQ = warp_max(maxQ);
+  if (grp == 0 && has_chunk)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      sZ[warp * 2 * kBatchMaxD + gl * VW + e] = ZP[e];
+      sZ[warp * 2 * kBatchMaxD + kBatchMaxD + gl * VW + e] = ZQ[e];
+    }
+  if (lane == 0) {
+    s_sc[warp][0] = SP;
+    s_sc[warp][1] = SQ;
+    s_sc[warp][2] = minP;
+    s_sc[warp][3] = maxQ;
+  }
+}
+
 // A fresh alpha-FTP of an SVM instance: t = 0, means 0 (uniform weights on
 // each class at t = 0), as mwu_state_init does for SVM. One warp.
 __device__ __forceinline__ void svm_batch_fresh_state(void* state, int d, const BatchSolveOpts* o) {
@@ -389,11 +495,11 @@ static __global__ void __launch_bounds__(kBatchBlock, 3) svm_batch_kernel(SvmBat
       if (tid < d) s_wb[tid] = mean32[tid];
       __syncthreads();
       switch (in.shape) {
-        case 0: svm_batch_tile<T, 4, 1, 1, 4>(pts, lab, d, tl.r0, tl.r1, s_wb, k, Hm, s1, s2, sZ, s_sc); break;
-        case 1: svm_batch_tile<T, 4, 2, 1, 4>(pts, lab, d, tl.r0, tl.r1, s_wb, k, Hm, s1, s2, sZ, s_sc); break;
-        case 2: svm_batch_tile<T, 4, 4, 1, 4>(pts, lab, d, tl.r0, tl.r1, s_wb, k, Hm, s1, s2, sZ, s_sc); break;
-        case 3: svm_batch_tile<T, 4, 8, 1, 4>(pts, lab, d, tl.r0, tl.r1, s_wb, k, Hm, s1, s2, sZ, s_sc); break;
-        case 4: svm_batch_tile<T, 4, 16, 1, 4>(pts, lab, d, tl.r0, tl.r1, s_wb, k, Hm, s1, s2, sZ, s_sc); break;
+        case 0: svm_batch_tile_t<T, 4, 1, 8>(pts, lab, d, tl.r0, tl.r1, s_wb, k, Hm, s1, s2, sZ, s_sc); break;
+        case 1: svm_batch_tile_t<T, 4, 2, 8>(pts, lab, d, tl.r0, tl.r1, s_wb, k, Hm, s1, s2, sZ, s_sc); break;
+        case 2: svm_batch_tile_t<T, 4, 4, 8>(pts, lab, d, tl.r0, tl.r1, s_wb, k, Hm, s1, s2, sZ, s_sc); break;
+        case 3: svm_batch_tile_t<T, 4, 8, 8>(pts, lab, d, tl.r0, tl.r1, s_wb, k, Hm, s1, s2, sZ, s_sc); break;
+        case 4: svm_batch_tile_t<T, 4, 16, 8>(pts, lab, d, tl.r0, tl.r1, s_wb, k, Hm, s1, s2, sZ, s_sc); break;
         case 5: svm_batch_tile<T, 1, 2, 1, 4>(pts, lab, d, tl.r0, tl.r1, s_wb, k, Hm, s1, s2, sZ, s_sc); break;
         case 6: svm_batch_tile<T, 1, 8, 1, 4>(pts, lab, d, tl.r0, tl.r1, s_wb, k, Hm, s1, s2, sZ, s_sc); break;
         case 7: svm_batch_tile<T, 1, 32, 1, 4>(pts, lab, d, tl.r0, tl.r1, s_wb, k, Hm, s1, s2, sZ, s_sc); break;
