@@ -117,6 +117,23 @@ __device__ __forceinline__ void tc_ld8(uint32_t addr, float (&v)[8]) {
 // a - hi, exact in FP32
 __device__ __forceinline__ float tc_hi(float a) { return __uint_as_float(__float_as_uint(a) & 0xFFFFE000u); }
 __device__ __forceinline__ float tc_lo(float a) { return a - tc_hi(a); }
+// 1 - e^{-x} for x >= 0: the Maclaurin series x - x^2/2! + ... - x^10/10!
+// (Horner form; truncation below 2.7e-10 relative) for x < 0.5, 1 - e^{-x}
+// from expf above (no cancellation there: the result is at least 0.39)
+__device__ __forceinline__ float tc_one_minus_exp_neg(float x) {
+  if (x >= 0.5f) return 1.f - expf(-x);
+  float t = 1.f / 3628800.f;  // 1/10!
+  t = fmaf(-x, t, 1.f / 362880.f);
+  t = fmaf(-x, t, 1.f / 40320.f);
+  t = fmaf(-x, t, 1.f / 5040.f);
+  t = fmaf(-x, t, 1.f / 720.f);
+  t = fmaf(-x, t, 1.f / 120.f);
+  t = fmaf(-x, t, 1.f / 24.f);
+  t = fmaf(-x, t, 1.f / 6.f);
+  t = fmaf(-x, t, 0.5f);
+  t = fmaf(-x, t, 1.f);
+  return x * t;
+}
 // a = p1 + p2 + p3, each exactly representable in tf32
 __device__ __forceinline__ void tc_split3(float a, float& p1, float& p2, float& p3) {
   p1 = tc_hi(a);
@@ -244,17 +261,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
     if (tid == 0 && pend_tma)
       tma_load_tile(sbase + (stage ? kTcStage0 : kTcStage1), &tmap, (int)((tile + gridDim.x) * kTcTile),
                     s_bar + (stage ? 0 : 1));
-    // every decision to give up is taken by the whole CTA (__syncthreads_and)
-    if (!__syncthreads_and(mbar_wait(s_bar + stage, (unsigned int)(it >> 1) & 1u, wait_limit))) {
-      ok = false;
-      fail_at = 1;
-      break;
-    }
+    // every decision to give up is taken by the whole CTA, at the next barrier
+    // (__syncthreads_and): a thread whose wait gave up still runs the flat
+    // pass below on whatever the stage holds
+    const bool okw = mbar_wait(s_bar + stage, (unsigned int)(it >> 1) & 1u, wait_limit);
     // ---- y = x - v_1 in place, its low parts, row norms, and Y^T for Q:
     // thread (r, h) takes logical chunks 4h .. 4h + 3 of row r (16 features)
     const int64_t g = tile * kTcTile + r;
     const bool valid = g < p.n;
     float nrm = 0.f;
+    const int rc = (r & 31) >> 2;                                    // the swizzle's chunk of point r
+    const int a2b = (r >> 5) * 128 * 128 + ((r & 3) << 2) + (2 * h << 10);  // A2: point r, features 16 h ..
 #pragma unroll
     for (int c4 = 0; c4 < 4; ++c4) {
       const int lc = 4 * h + c4;
@@ -273,16 +290,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
       *reinterpret_cast<float4*>(sm + kTcY2 + off) = make_float4(y2[0], y2[1], y2[2], y2[3]);
       *reinterpret_cast<float4*>(sm + kTcY3 + off) = make_float4(y3[0], y3[1], y3[2], y3[3]);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        *reinterpret_cast<float*>(sm + kTcA2 + tc_sw128(e0 + e, r, 128)) = y1[e];
-        *reinterpret_cast<float*>(sm + kTcA2 + tc_sw128(kTcD + e0 + e, r, 128)) = y2[e];
-        *reinterpret_cast<float*>(sm + kTcA2 + tc_sw128(2 * kTcD + e0 + e, r, 128)) = y3[e];
+      for (int e = 0; e < 4; ++e) {  // tc_sw128(32 part + e0 + e, r, 128), its row-dependent part hoisted
+        const int f = 4 * c4 + e;  // e0 + e = 16 h + f: (e0 + e) & 7 = f & 7
+        const int o = a2b + ((f >> 3) << 10) + ((f & 7) << 7) + ((rc ^ (f & 7)) << 4);
+        *reinterpret_cast<float*>(sm + kTcA2 + o) = y1[e];
+        *reinterpret_cast<float*>(sm + kTcA2 + o + 4 * 1024) = y2[e];
+        *reinterpret_cast<float*>(sm + kTcA2 + o + 8 * 1024) = y3[e];
       }
     }
     s_norm[h][r] = nrm;
     fence_proxy_async_smem();
     tc_fence_before();
-    __syncthreads();
+    if (!__syncthreads_and(okw)) {
+      ok = false;
+      fail_at = 1;
+      break;
+    }
     tc_fence_after();
     // ---- P = Y U~^T: six products of the three-part splits in three MMA
     // chains (N = 48, 32, 16 rows of the stacked U~ parts), one thread issues;
@@ -299,14 +322,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
       }
       tc_commit(s_bar + 2);
     }
-    if (!__syncthreads_and(mbar_wait(s_bar + 2, (unsigned int)it & 1u, wait_limit))) {
-      ok = false;
-      fail_at = 2;
-      break;
-    }
+    // (a warp reads TMEM only if all its lanes saw the MMAs complete)
+    const bool okp = __all_sync(0xffffffffu, mbar_wait(s_bar + 2, (unsigned int)it & 1u, wait_limit));
     tc_fence_after();
-    float P[8];
-    {
+    float P[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (okp) {
       const uint32_t la = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 8 * h;
       float p11[8], p12[8], p13[8], p21[8], p22[8], p31[8];
       tc_ld8(la, p11);
@@ -320,6 +340,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
     }
     // ---- exponentials of the 8 candidates of this thread, C^T for Q
     const float yn = s_norm[0][r] + s_norm[1][r];
+    const int rcc = (r & 31) >> 2;
+    const int cb = (r >> 5) * 3 * kTcN * 128 + (h << 10) + ((r & 3) << 2);
     const bool cone = valid && g >= 1;
     const float gam = (cone && p.radii) ? __ldg(p.radii + g) : 0.f;
 #pragma unroll
@@ -328,13 +350,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
       float c = 0.f;
       if (cone && s_live[q]) {
         const float kr = s_kr[q];
-        const float dist = sqrtf(fmaxf(yn - 2.f * P[jj] + s_un[q], 0.f));
+        const float d2 = fmaxf(yn - 2.f * P[jj] + s_un[q], 0.f);
+        const float rd = d2 > 0.f ? rsqrtf(d2) : 0.f;
+        const float dist = d2 * rd;
         const float a = s_al[q] - gam;
         const float E1 = expf(kr * ((dist + gam) - s_H[q]));
-        const float em = -expm1f(-2.f * kr * dist);
+        const float em = tc_one_minus_exp_neg(2.f * kr * dist);
         const float dif = E1 * em;
         const float sum = E1 * (2.f - em);
-        c = dist > 0.f ? dif / dist : 2.f * kr * E1;
+        c = d2 > 0.f ? dif * rd : 2.f * kr * E1;
         S[jj] += sum;
         W[jj] += a * sum - dist * dif;
         M[jj] = fmaxf(M[jj], dist + gam);
@@ -342,13 +366,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
       }
       float c1, c2, c3;
       tc_split3(c, c1, c2, c3);
-      *reinterpret_cast<float*>(sm + kTcC + tc_sw128(q, r, 3 * kTcN)) = c1;
-      *reinterpret_cast<float*>(sm + kTcC + tc_sw128(kTcN + q, r, 3 * kTcN)) = c2;
-      *reinterpret_cast<float*>(sm + kTcC + tc_sw128(2 * kTcN + q, r, 3 * kTcN)) = c3;
+      // tc_sw128(16 b + q, r, 48) with q = 8 h + jj, the row-dependent part hoisted
+      const int o = cb + (jj << 7) + ((rcc ^ jj) << 4);
+      *reinterpret_cast<float*>(sm + kTcC + o) = c1;
+      *reinterpret_cast<float*>(sm + kTcC + o + 2048) = c2;
+      *reinterpret_cast<float*>(sm + kTcC + o + 4096) = c3;
     }
     fence_proxy_async_smem();
     tc_fence_before();
-    __syncthreads();
+    if (!__syncthreads_and(okp)) {
+      ok = false;
+      fail_at = 2;
+      break;
+    }
     tc_fence_after();
     // ---- Q += [Y_1^T; Y_2^T; Y_3^T] [c_1 c_2 c_3] over this tile's 128 points: one
     // chain of N = 48
