@@ -22,25 +22,44 @@
 // near a mean, G'_j against sum_i c_ij |y_i| near the equilibrium), so both
 // split their operands in three exact tf32 parts (a = a_1 + a_2 + a_3, a_2
 // the truncation of a - a_1, a_3 the rest, at most 2 bits) and keep the six
-// products down to 2^-22 of each other: FP32-grade results. The exponentials stay on the CUDA cores: thread r of the first
-// 128 reads row r of P for candidates 0-7 out of TMEM, thread 128 + r for
-// candidates 8-15.
+// products down to 2^-22 of each other: FP32-grade results.
 //
 // Operands in shared memory use the 128-byte swizzled K-major layout: a tile
 // of 128 points x 32 floats arrives from HBM by one TMA load with the 128-byte
 // swizzle, which is that layout for Y in P (rows: points, K: features; y_1 is
-// written over x in place, y_2 and y_3 beside it). For Q
-// the points must be the K dimension: the threads write Y^T (rows 0-31, 32-63,
-// 64-95: y_1, y_2, y_3) and C^T (16 rows: candidates, one buffer per part) in
-// the same layout, each warp writing one feature (or candidate) row for 32
-// consecutive points, which falls on 32 distinct banks. Q's M dimension is
-// 128: rows 96-127 are not read back. One MMA chain per part of C gives
-// y_1 c_1, y_2 c_1, y_3 c_1 (with c_1), y_1 c_2, y_2 c_2 (with c_2), y_1 c_3.
+// written over x in place, y_2 and y_3 beside it). For Q the points must be
+// the K dimension: the threads write Y^T (rows 0-31, 32-63, 64-95: y_1, y_2,
+// y_3; each K-block of 32 points is 96 rows) and C^T (48 rows: the three
+// parts of the 16 candidates) in the same layout, each warp writing one
+// feature (or candidate) row for 32 consecutive points, which falls on 32
+// distinct banks. Q's M dimension is 128: its rows 96-127 read the next
+// K-block's first rows and are not read back. One MMA chain of N = 48 gives
+// the products y_p c_q of all three parts of C; the six kept are summed
+// smallest first.
 //
-// Waits on the TMA loads and on the MMAs' completion are bounded (the
-// staged passes' limit); a wait that gives up poisons the CTA's rows (S =
-// NaN), so that the finishes report PDSCP_ERR_NUMERIC, and the kernel still
-// waits (bounded) for its MMAs before it frees its TMEM.
+// The CTA is warp-specialised so that the work on consecutive tiles
+// overlaps (one CTA per SM, tiles blockIdx.x, blockIdx.x + gridDim.x, ...):
+//   warps 8-11, one thread per point: centring, splits, y_1 in place and
+//     y_2, y_3 for P (tile u), then Y^T for Q into one of two buffers;
+//   warp 12, one thread: the TMA loads (three stages) and every MMA, P(u)
+//     into one of two TMEM buffers as soon as tile u's operands are written,
+//     Q(u - 1) once its coefficients are;
+//   warps 0-7: thread r + 128 h reads row r of P(u) out of TMEM (candidates
+//     8 h .. 8 h + 7: warp w reads TMEM lanes 32 (w % 4) ..), the
+//     exponentials, and writes C^T once Q(u - 1) has released it.
+// So while the exponential warps work on tile u, the split warps prepare
+// tile u + 1 and the tensor cores run Q(u - 1) and P(u + 1). Every hand-over
+// is an mbarrier: the producer's writes to shared memory are fenced for the
+// async proxy before it arrives, the MMAs' completion arrives through
+// tcgen05.commit. Each barrier's waits are separated from its next
+// completion by a chain of hand-overs through the waiting role itself, so a
+// parity never aliases (the arguments are beside the waits).
+//
+// Waits are bounded (the staged passes' limit, and a CTA-wide abort flag
+// ends every other role's waits early); a wait that gives up poisons the
+// CTA's rows (S = NaN), so that the finishes report PDSCP_ERR_NUMERIC, and
+// the MMA thread still waits (bounded) for its MMAs and loads in flight
+// before the TMEM and shared memory go.
 #pragma once
 
 #include <cuda.h>
@@ -49,24 +68,36 @@
 
 namespace pdscp {
 
-constexpr int kTcTile = 128;   // points per tile (the MMAs' M for P)
-constexpr int kTcD = 32;       // features (one 128-byte swizzle row of floats)
-constexpr int kTcN = 16;       // candidate columns (the MMAs' N)
-constexpr int kTcThreads = 256;
+constexpr int kTcTile = 128;  // points per tile (the MMAs' M for P)
+constexpr int kTcD = 32;      // features (one 128-byte swizzle row of floats)
+constexpr int kTcN = 16;      // candidate columns
+constexpr int kTcExpWarps = 8, kTcSplitWarps = 4;
+constexpr int kTcMmaWarp = kTcExpWarps + kTcSplitWarps;
+constexpr int kTcThreads = 32 * (kTcMmaWarp + 1);
+constexpr int kTcStages = 3;
 // dynamic shared memory (bytes from a 1024-aligned base)
-constexpr int kTcStage0 = 0, kTcStage1 = 16384;  // TMA tiles (y_1 written in place)
-constexpr int kTcY2 = 32768, kTcY3 = 49152;       // y_2, y_3: same layout
-constexpr int kTcA2 = 65536;                      // Q's A operand: 128 rows x 128 points
+constexpr int kTcTileBytes = kTcTile * kTcD * 4;
+constexpr int kTcY2 = kTcStages * kTcTileBytes;  // after the TMA stages (y_1 written in place)
+constexpr int kTcY3 = kTcY2 + kTcTileBytes;
+// Q's A operand, two buffers: Y^T, 4 K-blocks of 32 points x 96 rows
+constexpr int kTcA2Blk = 3 * kTcD * 128;
+constexpr int kTcA2Bytes = 4 * kTcA2Blk;
+constexpr int kTcA2 = kTcY3 + kTcTileBytes;
 // P's B operand: [u~_1; u~_2; u~_3] stacked, 48 rows x 32 features (the three
-// 16-row parts are contiguous: each is two 1024-byte atoms)
-constexpr int kTcU = 131072;
+// 16-row parts are contiguous: each is two 1024-byte atoms); the last Q
+// buffer's rows past its end read here
+constexpr int kTcU = kTcA2 + 2 * kTcA2Bytes;
 // Q's B operand: [c_1; c_2; c_3] stacked, 48 rows x 128 points
-constexpr int kTcC = 137216;
-constexpr int kTcSmem = 161792 + 1024;  // + alignment slack
-// TMEM columns: P's six products at 0-95 (y_1 [u_1 u_2 u_3], y_2 [u_1 u_2],
-// y_3 u_1: 16 columns each), Q at 128-175 ([c_1 c_2 c_3])
+constexpr int kTcC = kTcU + 3 * kTcN * kTcD * 4;
+constexpr int kTcCBlk = 3 * kTcN * 128;
+constexpr int kTcSmem = kTcC + 4 * kTcCBlk + 1024;  // + alignment slack
+static_assert(kTcA2 % 1024 == 0 && kTcU % 1024 == 0 && kTcC % 1024 == 0 && kTcA2Blk % 1024 == 0, "swizzle atoms");
+static_assert(3 * kTcA2Blk + 128 * 128 <= kTcA2Bytes + 3 * kTcN * kTcD * 4, "Q's rows past the last buffer stay in U");
+// TMEM columns: P(u) in buffer u & 1 at 96 (u & 1): six products (y_1 [u_1
+// u_2 u_3], y_2 [u_1 u_2], y_3 u_1: 16 columns each); Q at 192-239 ([c_1 c_2 c_3])
 constexpr int kTcTmemCols = 256;
-constexpr int kTcQCol = 128;
+constexpr int kTcPCols = 96;
+constexpr int kTcQCol = 192;
 
 // byte offset of element (row, col) in a 128-byte swizzled K-major operand of
 // `rows` rows (col along K, 32 floats per 128-byte atom row)
@@ -101,6 +132,15 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+// 8 consecutive FP32 columns of this thread's TMEM lane, without the wait
+// (tcgen05.wait::ld before the registers are used)
+__device__ __forceinline__ void tc_ld8_nw(uint32_t addr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(addr)
+               : "memory");
+}
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 // 8 consecutive FP32 columns of this thread's TMEM lane
 __device__ __forceinline__ void tc_ld8(uint32_t addr, float (&v)[8]) {
   uint32_t r[8];
@@ -151,34 +191,62 @@ __device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap* m
       : "memory");
 }
 
+// arrive (release, CTA scope) on an mbarrier
+__device__ __forceinline__ void tc_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+// bounded wait for the completion of the phase of parity `parity`; gives up
+// after `limit` tries, or earlier once another role has set the abort flag
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, unsigned int parity, unsigned int limit,
+                                        const volatile int* abort) {
+  for (unsigned int i = 0; i < limit; ++i) {
+    unsigned int done;
+    asm volatile(
+        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((i & 15u) == 15u && *abort) return false;
+  }
+  return false;
+}
+
 // One pass for K <= 16 candidates (states, alphas, step sizes as in
-// ses_multi_kernel), points streamed through TMA in tiles of 128; one CTA per
-// SM takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...; then the completion
-// of ses_multi_kernel (the last CTA reduces the K candidate rows, the warps
-// run the finishes).
+// ses_multi_kernel), points streamed through TMA in tiles of 128 by the
+// warp-specialised pipeline above; then the completion of ses_multi_kernel
+// (the last CTA reduces the K candidate rows, the warps run the finishes).
 template <int K>
 __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams p, unsigned int wait_limit,
                                                                      const __grid_constant__ CUtensorMap tmap) {
   static_assert(K >= 1 && K <= kTcN, "up to 16 candidates");
   extern __shared__ __align__(128) unsigned char smem_raw[];  // aligned to 1024 below (the swizzle atoms)
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t s_bar[4];  // TMA stage 0, stage 1, P done, Q done
+  // mbarriers: TMA stage loaded / read by P; tile operands of P written (per
+  // stage), Y^T written (per buffer); P done (per TMEM buffer); C written;
+  // Q done (per Y^T buffer); everything issued done
+  __shared__ uint64_t s_full[kTcStages], s_sempty[kTcStages], s_yready[kTcStages];
+  __shared__ uint64_t s_a2ready[2], s_pdone[2], s_qdone[2], s_cready, s_fin;
   __shared__ uint32_t s_tmem;
-  __shared__ float s_norm[2][kTcTile];
+  __shared__ int s_abort;
+  __shared__ float s_norm[kTcStages][kTcTile];
   __shared__ float s_v1[kTcD], s_ctr[kTcD], s_un[kTcN], s_kr[kTcN], s_H[kTcN], s_al[kTcN];
   __shared__ int s_live[kTcN];
-  __shared__ float s_sc[kTcThreads / 32][kTcN][4];
+  __shared__ float s_sc[kTcExpWarps][kTcN][4];
   __shared__ float s_q[kTcN][kTcD];
-  __shared__ float2 s_scr[kBlock];
+  __shared__ float2 s_scr[kTcThreads];
   __shared__ __align__(16) double s_hdr[K][sizeof(StateHdr) / 8];
   __shared__ bool s_flag;
+  volatile int* abort_flag = &s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int d = kTcD, dp = kTcD;
   const int st = ses_partial_stride(d);
   const float* pts = reinterpret_cast<const float*>(p.pts);
   const int64_t ntiles = (p.n + kTcTile - 1) / kTcTile;
+  // this CTA's tiles: blockIdx.x + u gridDim.x for u < nt
+  const int nt = (int64_t)blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
 
-  // ---- set-up: candidates, v_1, the centre m, U~ in both parts, barriers, TMEM
+  // ---- set-up: candidates, v_1, the centre m, U~ in three parts, barriers, TMEM
   if (tid < kTcD) {
     s_v1[tid] = __ldg(pts + tid);
     float m = 0.f;
@@ -219,7 +287,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
     s_un[tid] = s;
   }
   if (tid == 0) {
-    for (int b = 0; b < 4; ++b) mbar_init(s_bar + b, 1);
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(s_full + s, 1);
+      mbar_init(s_sempty + s, 1);
+      mbar_init(s_yready + s, 32 * kTcSplitWarps);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(s_a2ready + b, 32 * kTcSplitWarps);
+      mbar_init(s_pdone + b, 1);
+      mbar_init(s_qdone + b, 1);
+    }
+    mbar_init(&s_cready, 32 * kTcExpWarps);
+    mbar_init(&s_fin, 1);
+    s_abort = 0;
     mbar_init_fence();
   }
   if (warp == 0) {
@@ -235,188 +315,269 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
   const uint32_t tmem = s_tmem;
   const uint32_t sbase = smem_u32(sm);
 
-  // this thread's candidates (half h of the 16 columns) and row r of a tile
-  const int r = tid & (kTcTile - 1), h = tid >> 7;
-  float S[8], W[8], M[8], Cs[8];
+  const unsigned int wl = wait_limit;
+
+  if (warp < kTcExpWarps) {
+    // ---- exponential warps: thread (r, h) takes point r of each tile and
+    // candidates 8 h .. 8 h + 7 (TMEM lane r: warp w reads lanes 32 (w % 4) ..)
+    const int r = tid & (kTcTile - 1), h = tid >> 7;
+    float S[8], W[8], M[8], Cs[8];  // sums over this thread's points
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    S[j] = 0.f;
-    W[j] = 0.f;
-    M[j] = -INFINITY;
-    Cs[j] = 0.f;
-  }
-  bool ok = true;
-  int it = 0;
-  // what may still be in flight if a wait gives up: the awaited load or MMAs
-  // (fail_at: 1 the tile's load, 2 P, 3 Q) and the prefetched tile
-  bool pend_tma = false;
-  int fail_at = 0;
-  if (tid == 0 && (int64_t)blockIdx.x < ntiles) tma_load_tile(sbase + kTcStage0, &tmap, blockIdx.x * kTcTile, s_bar + 0);
-  for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
-    const int stage = it & 1;
-    const uint32_t tbase = sbase + (stage ? kTcStage1 : kTcStage0);
-    unsigned char* tptr = sm + (stage ? kTcStage1 : kTcStage0);
-    // the next tile into the other stage (its previous tile's MMAs are done)
-    pend_tma = tile + gridDim.x < ntiles;
-    if (tid == 0 && pend_tma)
-      tma_load_tile(sbase + (stage ? kTcStage0 : kTcStage1), &tmap, (int)((tile + gridDim.x) * kTcTile),
-                    s_bar + (stage ? 0 : 1));
-    // every decision to give up is taken by the whole CTA, at the next barrier
-    // (__syncthreads_and): a thread whose wait gave up still runs the flat
-    // pass below on whatever the stage holds
-    const bool okw = mbar_wait(s_bar + stage, (unsigned int)(it >> 1) & 1u, wait_limit);
-    // ---- y = x - v_1 in place, its low parts, row norms, and Y^T for Q:
-    // thread (r, h) takes logical chunks 4h .. 4h + 3 of row r (16 features)
-    const int64_t g = tile * kTcTile + r;
-    const bool valid = g < p.n;
-    float nrm = 0.f;
-    const int rc = (r & 31) >> 2;                                    // the swizzle's chunk of point r
-    const int a2b = (r >> 5) * 128 * 128 + ((r & 3) << 2) + (2 * h << 10);  // A2: point r, features 16 h ..
-#pragma unroll
-    for (int c4 = 0; c4 < 4; ++c4) {
-      const int lc = 4 * h + c4;
-      const int off = r * 128 + ((lc ^ (r & 7)) << 4);
-      float4 x = *reinterpret_cast<const float4*>(tptr + off);
-      const int e0 = 4 * lc;
-      float y[4] = {valid ? x.x - s_ctr[e0] : 0.f, valid ? x.y - s_ctr[e0 + 1] : 0.f,
-                    valid ? x.z - s_ctr[e0 + 2] : 0.f, valid ? x.w - s_ctr[e0 + 3] : 0.f};
-      float y1[4], y2[4], y3[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        tc_split3(y[e], y1[e], y2[e], y3[e]);
-        nrm = fmaf(y[e], y[e], nrm);
-      }
-      *reinterpret_cast<float4*>(tptr + off) = make_float4(y1[0], y1[1], y1[2], y1[3]);
-      *reinterpret_cast<float4*>(sm + kTcY2 + off) = make_float4(y2[0], y2[1], y2[2], y2[3]);
-      *reinterpret_cast<float4*>(sm + kTcY3 + off) = make_float4(y3[0], y3[1], y3[2], y3[3]);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {  // tc_sw128(32 part + e0 + e, r, 128), its row-dependent part hoisted
-        const int f = 4 * c4 + e;  // e0 + e = 16 h + f: (e0 + e) & 7 = f & 7
-        const int o = a2b + ((f >> 3) << 10) + ((f & 7) << 7) + ((rc ^ (f & 7)) << 4);
-        *reinterpret_cast<float*>(sm + kTcA2 + o) = y1[e];
-        *reinterpret_cast<float*>(sm + kTcA2 + o + 4 * 1024) = y2[e];
-        *reinterpret_cast<float*>(sm + kTcA2 + o + 8 * 1024) = y3[e];
-      }
+    for (int j = 0; j < 8; ++j) {
+      S[j] = 0.f;
+      W[j] = 0.f;
+      M[j] = -INFINITY;
+      Cs[j] = 0.f;
     }
-    s_norm[h][r] = nrm;
-    fence_proxy_async_smem();
-    tc_fence_before();
-    if (!__syncthreads_and(okw)) {
-      ok = false;
-      fail_at = 1;
-      break;
-    }
-    tc_fence_after();
-    // ---- P = Y U~^T: six products of the three-part splits in three MMA
-    // chains (N = 48, 32, 16 rows of the stacked U~ parts), one thread issues;
-    // descriptors advance by (bytes >> 4) in their address field
-    if (tid == 0) {
-      const uint64_t dy1 = tc_desc(tbase), dy2 = tc_desc(sbase + kTcY2), dy3 = tc_desc(sbase + kTcY3);
-      const uint64_t du = tc_desc(sbase + kTcU);
-#pragma unroll
-      for (int s = 0; s < kTcD / 8; ++s) {
-        const uint64_t ks = (uint64_t)(s * 32 >> 4);
-        tc_mma(tmem, dy1 + ks, du + ks, tc_idesc(48), s > 0);       // y_1 [u_1 u_2 u_3]
-        tc_mma(tmem + 48, dy2 + ks, du + ks, tc_idesc(32), s > 0);  // y_2 [u_1 u_2]
-        tc_mma(tmem + 80, dy3 + ks, du + ks, tc_idesc(16), s > 0);  // y_3 u_1
-      }
-      tc_commit(s_bar + 2);
-    }
-    // (a warp reads TMEM only if all its lanes saw the MMAs complete)
-    const bool okp = __all_sync(0xffffffffu, mbar_wait(s_bar + 2, (unsigned int)it & 1u, wait_limit));
-    tc_fence_after();
-    float P[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (okp) {
-      const uint32_t la = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 8 * h;
-      float p11[8], p12[8], p13[8], p21[8], p22[8], p31[8];
-      tc_ld8(la, p11);
-      tc_ld8(la + 16, p12);
-      tc_ld8(la + 32, p13);
-      tc_ld8(la + 48, p21);
-      tc_ld8(la + 64, p22);
-      tc_ld8(la + 80, p31);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) P[j] = (((p31[j] + p22[j]) + p13[j]) + (p21[j] + p12[j])) + p11[j];
-    }
-    // ---- exponentials of the 8 candidates of this thread, C^T for Q
-    const float yn = s_norm[0][r] + s_norm[1][r];
+    const uint32_t lrow = (uint32_t)(32 * (warp & 3)) << 16;
     const int rcc = (r & 31) >> 2;
-    const int cb = (r >> 5) * 3 * kTcN * 128 + (h << 10) + ((r & 3) << 2);
-    const bool cone = valid && g >= 1;
-    const float gam = (cone && p.radii) ? __ldg(p.radii + g) : 0.f;
+    const int cb = (r >> 5) * kTcCBlk + (h << 10) + ((r & 3) << 2);
+    for (int u = 0, s = 0; u < nt; ++u, s = s + 1 == kTcStages ? 0 : s + 1) {
+      const int b = u & 1;
+      // yready[s] completes next for tile u + 3, whose split waits for
+      // P(u + 2); pdone[b] next for P(u + 2): both issued after this role's
+      // C of tile u (the MMA thread waits for it before Q(u), then P(u + 2))
+      bool okw = tc_wait(s_yready + s, (unsigned int)(u / kTcStages) & 1u, wl, abort_flag);
+      okw = okw && tc_wait(s_pdone + b, (unsigned int)(u >> 1) & 1u, wl, abort_flag);
+      if (!__all_sync(0xffffffffu, okw)) {  // (a warp reads TMEM only if all its lanes saw the MMAs complete)
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      float P[8];
+      {
+        const uint32_t la = tmem + lrow + kTcPCols * b + 8 * h;
+        uint32_t p11[8], p12[8], p13[8], p21[8], p22[8], p31[8];
+        tc_ld8_nw(la, p11);
+        tc_ld8_nw(la + 16, p12);
+        tc_ld8_nw(la + 32, p13);
+        tc_ld8_nw(la + 48, p21);
+        tc_ld8_nw(la + 64, p22);
+        tc_ld8_nw(la + 80, p31);
+        tc_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          P[j] = (((__uint_as_float(p31[j]) + __uint_as_float(p22[j])) + __uint_as_float(p13[j])) +
+                  (__uint_as_float(p21[j]) + __uint_as_float(p12[j]))) +
+                 __uint_as_float(p11[j]);
+      }
+      tc_fence_before();  // (these TMEM reads before the arrival that lets P(u + 2) overwrite them)
+      const int64_t g = (blockIdx.x + (int64_t)u * gridDim.x) * kTcTile + r;
+      const bool cone = g < p.n && g >= 1;
+      const float gam = (cone && p.radii) ? __ldg(p.radii + g) : 0.f;
+      const float yn = s_norm[s][r];
+      float c1[8], c2[8], c3[8];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int q = 8 * h + jj;
+        float c = 0.f;
+        if (cone && s_live[q]) {
+          const float kr = s_kr[q];
+          const float d2 = fmaxf(yn - 2.f * P[jj] + s_un[q], 0.f);
+          const float rd = d2 > 0.f ? rsqrtf(d2) : 0.f;
+          const float dist = d2 * rd;
+          const float a = s_al[q] - gam;
+          const float E1 = expf(kr * ((dist + gam) - s_H[q]));
+          const float em = tc_one_minus_exp_neg(2.f * kr * dist);
+          const float dif = E1 * em;
+          const float sum = E1 * (2.f - em);
+          c = d2 > 0.f ? dif * rd : 2.f * kr * E1;
+          S[jj] += sum;
+          W[jj] += a * sum - dist * dif;
+          M[jj] = fmaxf(M[jj], dist + gam);
+          Cs[jj] += c;
+        }
+        tc_split3(c, c1[jj], c2[jj], c3[jj]);
+      }
+      // C is free once Q(u - 1) is done; qdone[(u - 1) & 1] completes next
+      // for Q(u + 1), which waits for this role's C of tile u + 1
+      if (u >= 1 && !__all_sync(0xffffffffu, tc_wait(s_qdone + ((u - 1) & 1), (unsigned int)((u - 1) >> 1) & 1u, wl,
+                                                      abort_flag))) {
+        *abort_flag = 1;
+        break;
+      }
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {  // tc_sw128(16 part + 8 h + jj, r, 48), the row-dependent part hoisted
+        const int o = cb + (jj << 7) + ((rcc ^ jj) << 4);
+        *reinterpret_cast<float*>(sm + kTcC + o) = c1[jj];
+        *reinterpret_cast<float*>(sm + kTcC + o + 2048) = c2[jj];
+        *reinterpret_cast<float*>(sm + kTcC + o + 4096) = c3[jj];
+      }
+      fence_proxy_async_smem();
+      tc_arrive(&s_cready);
+    }
+    // the warp's sums per candidate [S, Wt, maxd, sum c]
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) {
-      const int q = 8 * h + jj;
-      float c = 0.f;
-      if (cone && s_live[q]) {
-        const float kr = s_kr[q];
-        const float d2 = fmaxf(yn - 2.f * P[jj] + s_un[q], 0.f);
-        const float rd = d2 > 0.f ? rsqrtf(d2) : 0.f;
-        const float dist = d2 * rd;
-        const float a = s_al[q] - gam;
-        const float E1 = expf(kr * ((dist + gam) - s_H[q]));
-        const float em = tc_one_minus_exp_neg(2.f * kr * dist);
-        const float dif = E1 * em;
-        const float sum = E1 * (2.f - em);
-        c = d2 > 0.f ? dif * rd : 2.f * kr * E1;
-        S[jj] += sum;
-        W[jj] += a * sum - dist * dif;
-        M[jj] = fmaxf(M[jj], dist + gam);
-        Cs[jj] += c;
+      float s0 = S[jj], s1 = W[jj], m = M[jj], cs = Cs[jj];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        cs += __shfl_xor_sync(0xffffffffu, cs, o);
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
       }
-      float c1, c2, c3;
-      tc_split3(c, c1, c2, c3);
-      // tc_sw128(16 b + q, r, 48) with q = 8 h + jj, the row-dependent part hoisted
-      const int o = cb + (jj << 7) + ((rcc ^ jj) << 4);
-      *reinterpret_cast<float*>(sm + kTcC + o) = c1;
-      *reinterpret_cast<float*>(sm + kTcC + o + 2048) = c2;
-      *reinterpret_cast<float*>(sm + kTcC + o + 4096) = c3;
+      if (lane == 0) {
+        s_sc[warp][8 * h + jj][0] = s0;
+        s_sc[warp][8 * h + jj][1] = s1;
+        s_sc[warp][8 * h + jj][2] = m;
+        s_sc[warp][8 * h + jj][3] = cs;
+      }
     }
-    fence_proxy_async_smem();
-    tc_fence_before();
-    if (!__syncthreads_and(okp)) {
-      ok = false;
-      fail_at = 2;
-      break;
+  } else if (warp < kTcMmaWarp) {
+    // ---- split warps: thread r takes point r of each tile (warp 8 + w the
+    // points 32 w .., one K-block of Y^T)
+    const int r = tid - 32 * kTcExpWarps;
+    const int rc = lane >> 2;
+    const int a2b = (r >> 5) * kTcA2Blk + ((lane & 3) << 2);
+    for (int u = 0, s = 0; u < nt; ++u, s = s + 1 == kTcStages ? 0 : s + 1) {
+      const int b = u & 1;
+      // full[s] completes next for tile u + 3, loaded after P(u) read this
+      // stage; pdone[(u - 1) & 1] next for P(u + 1): both after this role's
+      // tile u (y_2, y_3 are free once P(u - 1) is done)
+      bool okw = tc_wait(s_full + s, (unsigned int)(u / kTcStages) & 1u, wl, abort_flag);
+      if (u >= 1) okw = okw && tc_wait(s_pdone + ((u - 1) & 1), (unsigned int)((u - 1) >> 1) & 1u, wl, abort_flag);
+      if (!__all_sync(0xffffffffu, okw)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const int64_t g = (blockIdx.x + (int64_t)u * gridDim.x) * kTcTile + r;
+      const bool valid = g < p.n;
+      unsigned char* tptr = sm + s * kTcTileBytes;
+      // y = x - m (kept for Y^T), its three parts (y_1 over x in place), the row norm
+      float y[kTcD];
+      float nrm = 0.f;
+#pragma unroll
+      for (int c4 = 0; c4 < kTcD / 4; ++c4) {
+        const int off = r * 128 + ((c4 ^ (r & 7)) << 4);
+        const float4 x = *reinterpret_cast<const float4*>(tptr + off);
+        const int e0 = 4 * c4;
+        y[e0] = valid ? x.x - s_ctr[e0] : 0.f;
+        y[e0 + 1] = valid ? x.y - s_ctr[e0 + 1] : 0.f;
+        y[e0 + 2] = valid ? x.z - s_ctr[e0 + 2] : 0.f;
+        y[e0 + 3] = valid ? x.w - s_ctr[e0 + 3] : 0.f;
+        float y1[4], y2[4], y3[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          tc_split3(y[e0 + e], y1[e], y2[e], y3[e]);
+          nrm = fmaf(y[e0 + e], y[e0 + e], nrm);
+        }
+        *reinterpret_cast<float4*>(tptr + off) = make_float4(y1[0], y1[1], y1[2], y1[3]);
+        *reinterpret_cast<float4*>(sm + kTcY2 + off) = make_float4(y2[0], y2[1], y2[2], y2[3]);
+        *reinterpret_cast<float4*>(sm + kTcY3 + off) = make_float4(y3[0], y3[1], y3[2], y3[3]);
+      }
+      s_norm[s][r] = nrm;
+      fence_proxy_async_smem();
+      tc_arrive(s_yready + s);
+      // Y^T buffer b is free once Q(u - 2) is done; qdone[b] completes next
+      // for Q(u), which waits for this role's Y^T of tile u
+      if (u >= 2 && !__all_sync(0xffffffffu, tc_wait(s_qdone + b, (unsigned int)((u - 2) >> 1) & 1u, wl, abort_flag))) {
+        *abort_flag = 1;
+        break;
+      }
+      unsigned char* a2 = sm + kTcA2 + b * kTcA2Bytes + a2b;
+#pragma unroll
+      for (int e = 0; e < kTcD; ++e) {  // tc_sw128(32 part + e, r, 96) in K-block r / 32, the lane's part hoisted
+        const int o = ((e >> 3) << 10) + ((e & 7) << 7) + ((rc ^ (e & 7)) << 4);
+        float y1, y2, y3;  // (split again: cheaper than holding the parts)
+        tc_split3(y[e], y1, y2, y3);
+        *reinterpret_cast<float*>(a2 + o) = y1;
+        *reinterpret_cast<float*>(a2 + o + 4 * 1024) = y2;
+        *reinterpret_cast<float*>(a2 + o + 8 * 1024) = y3;
+      }
+      fence_proxy_async_smem();
+      tc_arrive(s_a2ready + b);
     }
-    tc_fence_after();
-    // ---- Q += [Y_1^T; Y_2^T; Y_3^T] [c_1 c_2 c_3] over this tile's 128 points: one
-    // chain of N = 48
-    if (tid == 0) {
-      const uint64_t da = tc_desc(sbase + kTcA2), dc = tc_desc(sbase + kTcC);
+  } else if (lane == 0) {
+    // ---- the MMA thread: TMA loads three tiles ahead of the split, P(u) as
+    // soon as tile u's operands are written, then Q(u - 1)
+    auto load = [&](int u) {
+      const int s = u % kTcStages;
+      tma_load_tile(sbase + s * kTcTileBytes, &tmap, (int)((blockIdx.x + (int64_t)u * gridDim.x) * kTcTile),
+                    s_full + s);
+    };
+    const uint64_t du = tc_desc(sbase + kTcU), dy2 = tc_desc(sbase + kTcY2), dy3 = tc_desc(sbase + kTcY3);
+    const uint64_t dc = tc_desc(sbase + kTcC);
+    // Q(u) += [Y_1^T; Y_2^T; Y_3^T] [c_1 c_2 c_3] over tile u's 128 points: one
+    // chain of N = 48; descriptors advance by (bytes >> 4) in their address field
+    auto issue_q = [&](int u) {
+      const uint64_t da = tc_desc(sbase + kTcA2 + (u & 1) * kTcA2Bytes);
 #pragma unroll 4
-      for (int s = 0; s < kTcTile / 8; ++s) {
-        const uint64_t ka = (uint64_t)(((s >> 2) * 128 * 128 + (s & 3) * 32) >> 4);
-        const uint64_t kb = (uint64_t)(((s >> 2) * 3 * kTcN * 128 + (s & 3) * 32) >> 4);
-        tc_mma(tmem + kTcQCol, da + ka, dc + kb, tc_idesc(48), it > 0 || s > 0);
+      for (int k = 0; k < kTcTile / 8; ++k) {
+        const uint64_t ka = (uint64_t)(((k >> 2) * kTcA2Blk + (k & 3) * 32) >> 4);
+        const uint64_t kb = (uint64_t)(((k >> 2) * kTcCBlk + (k & 3) * 32) >> 4);
+        tc_mma(tmem + kTcQCol, da + ka, dc + kb, tc_idesc(48), u > 0 || k > 0);
       }
-      tc_commit(s_bar + 3);
+      tc_commit(s_qdone + (u & 1));
+    };
+    int issued = 0;
+    for (; issued < nt && issued < kTcStages; ++issued) load(issued);
+    bool ok = true;
+    for (int u = 0, s = 0; u < nt; ++u, s = s + 1 == kTcStages ? 0 : s + 1) {
+      const int b = u & 1;
+      if (u >= 1 && u + 2 < nt) {  // tile u + 2 into the stage P(u - 1) read (sempty: next for P(u + 2), below)
+        const int sp = s == 0 ? kTcStages - 1 : s - 1;
+        ok = tc_wait(s_sempty + sp, (unsigned int)((u - 1) / kTcStages) & 1u, wl, abort_flag);
+        if (!ok) break;
+        load(u + 2);
+        ++issued;
+      }
+      // yready[s] completes next for tile u + 3, loaded after P(u)
+      ok = tc_wait(s_yready + s, (unsigned int)(u / kTcStages) & 1u, wl, abort_flag);
+      if (!ok) break;
+      tc_fence_after();
+      // P(u) = Y U~^T: six products of the three-part splits in three MMA
+      // chains (N = 48, 32, 16 rows of the stacked U~ parts)
+      const uint32_t tp = tmem + kTcPCols * b;
+      const uint64_t dy1 = tc_desc(sbase + s * kTcTileBytes);
+#pragma unroll
+      for (int k = 0; k < kTcD / 8; ++k) {
+        const uint64_t ks = (uint64_t)(k * 32 >> 4);
+        tc_mma(tp, dy1 + ks, du + ks, tc_idesc(48), k > 0);       // y_1 [u_1 u_2 u_3]
+        tc_mma(tp + 48, dy2 + ks, du + ks, tc_idesc(32), k > 0);  // y_2 [u_1 u_2]
+        tc_mma(tp + 80, dy3 + ks, du + ks, tc_idesc(16), k > 0);  // y_3 u_1
+      }
+      tc_commit(s_pdone + b);
+      tc_commit(s_sempty + s);
+      if (u >= 1) {
+        // cready completes next for tile u, whose C waits for Q(u - 1);
+        // a2ready[(u - 1) & 1] next for tile u + 1, whose Y^T waits for Q(u - 1)
+        ok = tc_wait(&s_cready, (unsigned int)(u - 1) & 1u, wl, abort_flag) &&
+             tc_wait(s_a2ready + ((u - 1) & 1), (unsigned int)((u - 1) >> 1) & 1u, wl, abort_flag);
+        if (!ok) break;
+        tc_fence_after();
+        issue_q(u - 1);
+      }
     }
-    // the operands of Q are rewritten by the next tile: wait for these MMAs
-    if (!__syncthreads_and(mbar_wait(s_bar + 3, (unsigned int)it & 1u, wait_limit))) {
-      ok = false;
-      fail_at = 3;
-      break;
+    if (ok && nt >= 1) {
+      ok = tc_wait(&s_cready, (unsigned int)(nt - 1) & 1u, wl, abort_flag) &&
+           tc_wait(s_a2ready + ((nt - 1) & 1), (unsigned int)((nt - 1) >> 1) & 1u, wl, abort_flag);
+      if (ok) {
+        tc_fence_after();
+        issue_q(nt - 1);
+      }
     }
-    tc_fence_after();
-  }
-  // a wait that gave up: wait (bounded, at least the default tries) for what
-  // this CTA still has in flight before its TMEM and shared memory go
-  if (!ok) {
-    const unsigned int lim = wait_limit > kWaitLimit ? wait_limit : kWaitLimit;
-    if (fail_at == 1) mbar_wait(s_bar + (it & 1), (unsigned int)(it >> 1) & 1u, lim);
-    if (fail_at == 2) mbar_wait(s_bar + 2, (unsigned int)it & 1u, lim);
-    if (fail_at == 3) mbar_wait(s_bar + 3, (unsigned int)it & 1u, lim);
-    if (pend_tma) mbar_wait(s_bar + ((it + 1) & 1), (unsigned int)((it + 1) >> 1) & 1u, lim);
+    if (!ok) *abort_flag = 1;
+    // every MMA, then every load issued, complete (bounded, at least the
+    // default tries) before the TMEM and shared memory go
+    const unsigned int lim = wl > kWaitLimit ? wl : kWaitLimit;
+    tc_commit(&s_fin);
+    mbar_wait(&s_fin, 0u, lim);
+    for (int s = 0; s < kTcStages && s < issued; ++s) {
+      const int last = s + kTcStages * ((issued - 1 - s) / kTcStages);
+      mbar_wait(s_full + s, (unsigned int)(last / kTcStages) & 1u, lim);
+    }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  const bool ok = *abort_flag == 0;
   // ---- Q out of TMEM: lanes 0-31 hold y_1^T C_b (columns kTcQCol + 16 (b - 1) ..),
   // lanes 32-63 y_2^T C_b, lanes 64-95 y_3^T C_b; the six products kept are
   // summed smallest first
   {
-    const bool have = it > 0 && ok;
+    const bool have = nt > 0 && ok;
     if (warp == 2) {  // y_3 c_1
       for (int c8 = 0; c8 < 2; ++c8) {
         float a[8];
@@ -455,24 +616,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
   // ---- per-CTA candidate rows [S, Wt, maxd, 0, G'_1..G'_32]
-#pragma unroll
-  for (int jj = 0; jj < 8; ++jj) {
-    float s0 = S[jj], s1 = W[jj], m = M[jj], cs = Cs[jj];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-      cs += __shfl_xor_sync(0xffffffffu, cs, o);
-      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    }
-    if (lane == 0) {
-      s_sc[warp][8 * h + jj][0] = s0;
-      s_sc[warp][8 * h + jj][1] = s1;
-      s_sc[warp][8 * h + jj][2] = m;
-      s_sc[warp][8 * h + jj][3] = cs;
-    }
-  }
-  __syncthreads();
   const int wst = K * st;
   float* prow = p.partials + (size_t)blockIdx.x * wst;
   __shared__ float s_tot[kTcN][4];
