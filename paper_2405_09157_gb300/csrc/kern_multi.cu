@@ -117,12 +117,10 @@ pdscp_status launch_multi_tc(const MultiParams& p, cudaStream_t s) {
   if (r != CUDA_SUCCESS) return merr(PDSCP_ERR_CUDA, "multi: tensor map encoding failed (%lld)", (long long)r);
   const int64_t ntiles = (p.n + kTcTile - 1) / kTcTile;
   const int grid = (int)(ntiles < device_sm_count() ? ntiles : device_sm_count());
-  const int wst = K * ses_partial_stride(kTcD);
   MultiParams q = p;
-  q.single = single_level(grid, wst, kStageBytesManyCta) ? 1 : 0;
-  const size_t fin = (size_t)(wst + K * kTcD + kTcD) * sizeof(double) +
-                     (q.single ? (size_t)grid * wst * sizeof(float) : 0) + 1024;
-  if (fin > (size_t)kTcSmem) q.single = 0;  // the staged completion must fit the pass's shared memory
+  // single level: the finishing CTA stages the rows in chunks of whole
+  // candidates in the pass's shared memory (else two levels)
+  q.single = tc_stage_candidates(grid, K) >= 1 ? 1 : 0;
   auto kern = ses_multi_tc_kernel<K>;
   cudaError_t e = allow_smem(kern, kTcSmem);
   if (e == cudaSuccess) {

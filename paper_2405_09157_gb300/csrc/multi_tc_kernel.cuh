@@ -72,8 +72,8 @@ constexpr int kTcTile = 128;  // points per tile (the MMAs' M for P)
 constexpr int kTcD = 32;      // features (one 128-byte swizzle row of floats)
 constexpr int kTcN = 16;      // candidate columns
 constexpr int kTcExpWarps = 8, kTcSplitWarps = 4;
-constexpr int kTcMmaWarp = kTcExpWarps + kTcSplitWarps;
-constexpr int kTcThreads = 32 * (kTcMmaWarp + 1);
+constexpr int kTcMmaWarp = kTcExpWarps + kTcSplitWarps;  // TMA loads and P; the next warp: Q
+constexpr int kTcThreads = 32 * (kTcMmaWarp + 2);
 constexpr int kTcStages = 3;
 // dynamic shared memory (bytes from a 1024-aligned base)
 constexpr int kTcTileBytes = kTcTile * kTcD * 4;
@@ -159,9 +159,11 @@ __device__ __forceinline__ float tc_hi(float a) { return __uint_as_float(__float
 __device__ __forceinline__ float tc_lo(float a) { return a - tc_hi(a); }
 // 1 - e^{-x} for x >= 0: the Maclaurin series x - x^2/2! + ... - x^10/10!
 // (Horner form; truncation below 2.7e-10 relative) for x < 0.5, 1 - e^{-x}
-// from expf above (no cancellation there: the result is at least 0.39)
+// from expf above (no cancellation there: the result is at least 0.39).
+// Both are computed and one selected: no branch, so that the candidates of a
+// thread interleave.
 __device__ __forceinline__ float tc_one_minus_exp_neg(float x) {
-  if (x >= 0.5f) return 1.f - expf(-x);
+  const float big = 1.f - expf(-x);
   float t = 1.f / 3628800.f;  // 1/10!
   t = fmaf(-x, t, 1.f / 362880.f);
   t = fmaf(-x, t, 1.f / 40320.f);
@@ -172,7 +174,7 @@ __device__ __forceinline__ float tc_one_minus_exp_neg(float x) {
   t = fmaf(-x, t, 1.f / 6.f);
   t = fmaf(-x, t, 0.5f);
   t = fmaf(-x, t, 1.f);
-  return x * t;
+  return x < 0.5f ? x * t : big;
 }
 // a = p1 + p2 + p3, each exactly representable in tf32
 __device__ __forceinline__ void tc_split3(float a, float& p1, float& p2, float& p3) {
@@ -212,6 +214,43 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, unsigned int parity, unsi
   return false;
 }
 
+// Candidates per chunk of the staged completion: the rows of nb CTAs (st
+// floats per candidate) after the finishing CTA's head (pairs of the totals,
+// the K means and v_1 in FP64); 0 if not even one candidate fits.
+__host__ __device__ constexpr int tc_stage_candidates(int nb, int K) {
+  return (int)(((size_t)kTcSmem - 1024 - (size_t)(K * (4 + kTcD) + K * kTcD + kTcD) * 8) /
+               ((size_t)nb * (4 + kTcD) * 4));
+}
+
+// Warp-wide forms: every lane of the warp executes them (uniform control
+// flow, warp-uniform operands); one lane, chosen by elect.sync, issues.
+__device__ __forceinline__ void tc_mma_w(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, bool acc) {
+  asm volatile(
+      "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc ? 1u : 0u)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit_w(uint64_t* bar) {
+  asm volatile(
+      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_tile_w(uint32_t dst, const CUtensorMap* map, int row0, uint64_t* bar) {
+  asm volatile(
+      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+      " @e mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+      " @e cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%2], [%3, {%4, %5}], [%0];\n}\n"
+      ::"r"(smem_u32(bar)), "r"(kTcTile * kTcD * 4), "r"(dst), "l"(map), "r"(0), "r"(row0)
+      : "memory");
+}
+// a bounded wait by every lane of a warp, its outcome the same in all lanes
+__device__ __forceinline__ bool tc_wait_w(uint64_t* bar, unsigned int parity, unsigned int limit,
+                                          const volatile int* abort) {
+  return __all_sync(0xffffffffu, tc_wait(bar, parity, limit, abort));
+}
+
 // One pass for K <= 16 candidates (states, alphas, step sizes as in
 // ses_multi_kernel), points streamed through TMA in tiles of 128 by the
 // warp-specialised pipeline above; then the completion of ses_multi_kernel
@@ -223,10 +262,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
   extern __shared__ __align__(128) unsigned char smem_raw[];  // aligned to 1024 below (the swizzle atoms)
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   // mbarriers: TMA stage loaded / read by P; tile operands of P written (per
-  // stage), Y^T written (per buffer); P done (per TMEM buffer); C written;
-  // Q done (per Y^T buffer); everything issued done
+  // stage), Y^T written (per buffer); P done, P read (per TMEM buffer); C
+  // written; Q done (per Y^T buffer); everything issued done
   __shared__ uint64_t s_full[kTcStages], s_sempty[kTcStages], s_yready[kTcStages];
-  __shared__ uint64_t s_a2ready[2], s_pdone[2], s_qdone[2], s_cready, s_fin;
+  __shared__ uint64_t s_a2ready[2], s_pdone[2], s_pfree[2], s_qdone[2], s_cready, s_fin;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   __shared__ float s_norm[kTcStages][kTcTile];
@@ -295,10 +334,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
     for (int b = 0; b < 2; ++b) {
       mbar_init(s_a2ready + b, 32 * kTcSplitWarps);
       mbar_init(s_pdone + b, 1);
+      mbar_init(s_pfree + b, 32 * kTcExpWarps);
       mbar_init(s_qdone + b, 1);
     }
     mbar_init(&s_cready, 32 * kTcExpWarps);
-    mbar_init(&s_fin, 1);
+    mbar_init(&s_fin, 2);
     s_abort = 0;
     mbar_init_fence();
   }
@@ -336,7 +376,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
       const int b = u & 1;
       // yready[s] completes next for tile u + 3, whose split waits for
       // P(u + 2); pdone[b] next for P(u + 2): both issued after this role's
-      // C of tile u (the MMA thread waits for it before Q(u), then P(u + 2))
+      // reads of P(u) (pfree)
       bool okw = tc_wait(s_yready + s, (unsigned int)(u / kTcStages) & 1u, wl, abort_flag);
       okw = okw && tc_wait(s_pdone + b, (unsigned int)(u >> 1) & 1u, wl, abort_flag);
       if (!__all_sync(0xffffffffu, okw)) {  // (a warp reads TMEM only if all its lanes saw the MMAs complete)
@@ -361,32 +401,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
                   (__uint_as_float(p21[j]) + __uint_as_float(p12[j]))) +
                  __uint_as_float(p11[j]);
       }
-      tc_fence_before();  // (these TMEM reads before the arrival that lets P(u + 2) overwrite them)
+      // these reads of TMEM and of the norm, then the arrival that lets P(u + 2)
+      // (and after it the split of tile u + 3) overwrite them
+      const float yn = s_norm[s][r];
+      tc_fence_before();
+      tc_arrive(s_pfree + b);
       const int64_t g = (blockIdx.x + (int64_t)u * gridDim.x) * kTcTile + r;
       const bool cone = g < p.n && g >= 1;
       const float gam = (cone && p.radii) ? __ldg(p.radii + g) : 0.f;
-      const float yn = s_norm[s][r];
       float c1[8], c2[8], c3[8];
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
+      for (int jj = 0; jj < 8; ++jj) {  // straight-line (selects, no branches): the 8 chains interleave
         const int q = 8 * h + jj;
-        float c = 0.f;
-        if (cone && s_live[q]) {
-          const float kr = s_kr[q];
-          const float d2 = fmaxf(yn - 2.f * P[jj] + s_un[q], 0.f);
-          const float rd = d2 > 0.f ? rsqrtf(d2) : 0.f;
-          const float dist = d2 * rd;
-          const float a = s_al[q] - gam;
-          const float E1 = expf(kr * ((dist + gam) - s_H[q]));
-          const float em = tc_one_minus_exp_neg(2.f * kr * dist);
-          const float dif = E1 * em;
-          const float sum = E1 * (2.f - em);
-          c = d2 > 0.f ? dif * rd : 2.f * kr * E1;
-          S[jj] += sum;
-          W[jj] += a * sum - dist * dif;
-          M[jj] = fmaxf(M[jj], dist + gam);
-          Cs[jj] += c;
-        }
+        const bool on = cone && s_live[q] != 0;
+        const float kr = s_kr[q];
+        const float d2 = fmaxf(yn - 2.f * P[jj] + s_un[q], 0.f);
+        const float rd = d2 > 0.f ? rsqrtf(d2) : 0.f;
+        const float dist = d2 * rd;
+        const float a = s_al[q] - gam;
+        const float E1 = expf(kr * ((dist + gam) - s_H[q]));
+        const float em = tc_one_minus_exp_neg(2.f * kr * dist);
+        const float dif = E1 * em;
+        const float sum = E1 * (2.f - em);
+        const float c = on ? (d2 > 0.f ? dif * rd : 2.f * kr * E1) : 0.f;
+        S[jj] += on ? sum : 0.f;
+        W[jj] += on ? a * sum - dist * dif : 0.f;
+        M[jj] = on ? fmaxf(M[jj], dist + gam) : M[jj];
+        Cs[jj] += c;
         tc_split3(c, c1[jj], c2[jj], c3[jj]);
       }
       // C is free once Q(u - 1) is done; qdone[(u - 1) & 1] completes next
@@ -489,28 +530,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
       fence_proxy_async_smem();
       tc_arrive(s_a2ready + b);
     }
-  } else if (lane == 0) {
-    // ---- the MMA thread: TMA loads three tiles ahead of the split, P(u) as
-    // soon as tile u's operands are written, then Q(u - 1)
+  } else if (warp == kTcMmaWarp) {
+    // ---- the P warp (one elected lane issues): TMA loads three tiles ahead
+    // of the split, P(u) as soon as tile u's operands are written and P(u - 2)
+    // has been read
     auto load = [&](int u) {
       const int s = u % kTcStages;
-      tma_load_tile(sbase + s * kTcTileBytes, &tmap, (int)((blockIdx.x + (int64_t)u * gridDim.x) * kTcTile),
-                    s_full + s);
+      tma_load_tile_w(sbase + s * kTcTileBytes, &tmap, (int)((blockIdx.x + (int64_t)u * gridDim.x) * kTcTile),
+                      s_full + s);
     };
     const uint64_t du = tc_desc(sbase + kTcU), dy2 = tc_desc(sbase + kTcY2), dy3 = tc_desc(sbase + kTcY3);
-    const uint64_t dc = tc_desc(sbase + kTcC);
-    // Q(u) += [Y_1^T; Y_2^T; Y_3^T] [c_1 c_2 c_3] over tile u's 128 points: one
-    // chain of N = 48; descriptors advance by (bytes >> 4) in their address field
-    auto issue_q = [&](int u) {
-      const uint64_t da = tc_desc(sbase + kTcA2 + (u & 1) * kTcA2Bytes);
-#pragma unroll 4
-      for (int k = 0; k < kTcTile / 8; ++k) {
-        const uint64_t ka = (uint64_t)(((k >> 2) * kTcA2Blk + (k & 3) * 32) >> 4);
-        const uint64_t kb = (uint64_t)(((k >> 2) * kTcCBlk + (k & 3) * 32) >> 4);
-        tc_mma(tmem + kTcQCol, da + ka, dc + kb, tc_idesc(48), u > 0 || k > 0);
-      }
-      tc_commit(s_qdone + (u & 1));
-    };
     int issued = 0;
     for (; issued < nt && issued < kTcStages; ++issued) load(issued);
     bool ok = true;
@@ -518,56 +547,68 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
       const int b = u & 1;
       if (u >= 1 && u + 2 < nt) {  // tile u + 2 into the stage P(u - 1) read (sempty: next for P(u + 2), below)
         const int sp = s == 0 ? kTcStages - 1 : s - 1;
-        ok = tc_wait(s_sempty + sp, (unsigned int)((u - 1) / kTcStages) & 1u, wl, abort_flag);
+        ok = tc_wait_w(s_sempty + sp, (unsigned int)((u - 1) / kTcStages) & 1u, wl, abort_flag);
         if (!ok) break;
         load(u + 2);
         ++issued;
       }
-      // yready[s] completes next for tile u + 3, loaded after P(u)
-      ok = tc_wait(s_yready + s, (unsigned int)(u / kTcStages) & 1u, wl, abort_flag);
+      // yready[s] completes next for tile u + 3, loaded after P(u); pfree[b]
+      // next when P(u) has been read
+      ok = tc_wait_w(s_yready + s, (unsigned int)(u / kTcStages) & 1u, wl, abort_flag);
+      if (ok && u >= 2) ok = tc_wait_w(s_pfree + b, (unsigned int)((u - 2) >> 1) & 1u, wl, abort_flag);
       if (!ok) break;
       tc_fence_after();
       // P(u) = Y U~^T: six products of the three-part splits in three MMA
-      // chains (N = 48, 32, 16 rows of the stacked U~ parts)
+      // chains (N = 48, 32, 16 rows of the stacked U~ parts); descriptors
+      // advance by (bytes >> 4) in their address field
       const uint32_t tp = tmem + kTcPCols * b;
       const uint64_t dy1 = tc_desc(sbase + s * kTcTileBytes);
 #pragma unroll
       for (int k = 0; k < kTcD / 8; ++k) {
         const uint64_t ks = (uint64_t)(k * 32 >> 4);
-        tc_mma(tp, dy1 + ks, du + ks, tc_idesc(48), k > 0);       // y_1 [u_1 u_2 u_3]
-        tc_mma(tp + 48, dy2 + ks, du + ks, tc_idesc(32), k > 0);  // y_2 [u_1 u_2]
-        tc_mma(tp + 80, dy3 + ks, du + ks, tc_idesc(16), k > 0);  // y_3 u_1
+        tc_mma_w(tp, dy1 + ks, du + ks, tc_idesc(48), k > 0);       // y_1 [u_1 u_2 u_3]
+        tc_mma_w(tp + 48, dy2 + ks, du + ks, tc_idesc(32), k > 0);  // y_2 [u_1 u_2]
+        tc_mma_w(tp + 80, dy3 + ks, du + ks, tc_idesc(16), k > 0);  // y_3 u_1
       }
-      tc_commit(s_pdone + b);
-      tc_commit(s_sempty + s);
-      if (u >= 1) {
-        // cready completes next for tile u, whose C waits for Q(u - 1);
-        // a2ready[(u - 1) & 1] next for tile u + 1, whose Y^T waits for Q(u - 1)
-        ok = tc_wait(&s_cready, (unsigned int)(u - 1) & 1u, wl, abort_flag) &&
-             tc_wait(s_a2ready + ((u - 1) & 1), (unsigned int)((u - 1) >> 1) & 1u, wl, abort_flag);
-        if (!ok) break;
-        tc_fence_after();
-        issue_q(u - 1);
-      }
-    }
-    if (ok && nt >= 1) {
-      ok = tc_wait(&s_cready, (unsigned int)(nt - 1) & 1u, wl, abort_flag) &&
-           tc_wait(s_a2ready + ((nt - 1) & 1), (unsigned int)((nt - 1) >> 1) & 1u, wl, abort_flag);
-      if (ok) {
-        tc_fence_after();
-        issue_q(nt - 1);
-      }
+      tc_commit_w(s_pdone + b);
+      tc_commit_w(s_sempty + s);
     }
     if (!ok) *abort_flag = 1;
-    // every MMA, then every load issued, complete (bounded, at least the
-    // default tries) before the TMEM and shared memory go
+    // every MMA of this warp, then every load issued, complete (bounded, at
+    // least the default tries) before the TMEM and shared memory go
     const unsigned int lim = wl > kWaitLimit ? wl : kWaitLimit;
-    tc_commit(&s_fin);
-    mbar_wait(&s_fin, 0u, lim);
+    tc_commit_w(&s_fin);
+    mbar_wait(&s_fin, 0u, lim);  // (not cut short by the abort flag)
     for (int s = 0; s < kTcStages && s < issued; ++s) {
       const int last = s + kTcStages * ((issued - 1 - s) / kTcStages);
       mbar_wait(s_full + s, (unsigned int)(last / kTcStages) & 1u, lim);
     }
+  } else if (warp == kTcMmaWarp + 1) {
+    // ---- the Q warp (one elected lane issues): Q(u) += [Y_1^T; Y_2^T; Y_3^T]
+    // [c_1 c_2 c_3] over tile u's 128 points, one chain of N = 48, once C and
+    // Y^T of tile u are written
+    const uint64_t dc = tc_desc(sbase + kTcC);
+    bool ok = true;
+    for (int u = 0; u < nt; ++u) {
+      // cready completes next for tile u + 1, whose C waits for Q(u);
+      // a2ready[u & 1] next for tile u + 2, whose Y^T waits for Q(u)
+      ok = tc_wait_w(&s_cready, (unsigned int)u & 1u, wl, abort_flag) &&
+           tc_wait_w(s_a2ready + (u & 1), (unsigned int)(u >> 1) & 1u, wl, abort_flag);
+      if (!ok) break;
+      tc_fence_after();
+      const uint64_t da = tc_desc(sbase + kTcA2 + (u & 1) * kTcA2Bytes);
+#pragma unroll 4
+      for (int k = 0; k < kTcTile / 8; ++k) {
+        const uint64_t ka = (uint64_t)(((k >> 2) * kTcA2Blk + (k & 3) * 32) >> 4);
+        const uint64_t kb = (uint64_t)(((k >> 2) * kTcCBlk + (k & 3) * 32) >> 4);
+        tc_mma_w(tmem + kTcQCol, da + ka, dc + kb, tc_idesc(48), u > 0 || k > 0);
+      }
+      tc_commit_w(s_qdone + (u & 1));
+    }
+    if (!ok) *abort_flag = 1;
+    const unsigned int lim = wl > kWaitLimit ? wl : kWaitLimit;
+    tc_commit_w(&s_fin);
+    mbar_wait(&s_fin, 0u, lim);  // (not cut short by the abort flag)
   }
   tc_fence_before();
   __syncthreads();
@@ -640,7 +681,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
   __syncthreads();
   for (int idx = tid; idx < K * dp; idx += kTcThreads) {
     const int q = idx / dp, e = idx % dp;
-    const float u = state_mean32(p.states + (size_t)q * p.state_stride, d)[e] - s_ctr[e];
+    // u~_j from its exact parts in shared memory (u_1 + (u_2 + u_3) = u~_j in FP32)
+    const float u = *reinterpret_cast<const float*>(sm + kTcU + tc_sw128(q, e, 3 * kTcN)) +
+                    (*reinterpret_cast<const float*>(sm + kTcU + tc_sw128(kTcN + q, e, 3 * kTcN)) +
+                     *reinterpret_cast<const float*>(sm + kTcU + tc_sw128(2 * kTcN + q, e, 3 * kTcN)));
     prow[q * st + 4 + e] = s_q[q][e] - s_tot[q][3] * u;  // sum_i c_ij (y_i - u~_j)
   }
 
@@ -661,7 +705,45 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
     s_mean[idx] = state_mean(p.states + (size_t)q * p.state_stride)[e];
   }
   if (tid < d) s_v1d[tid] = (double)s_v1[tid];
-  final_reduce(p.partials, wst, p.grows, p.counter, s_scr, opof, raw, stage, p.single, 2, -1, st);
+  if (p.single) {
+    // the CTAs' rows staged in shared memory in chunks of whole candidates
+    // (every row's columns of candidates q0 ..), then reduced column by column
+    const int nb = gridDim.x;
+    const int cap = tc_stage_candidates(nb, K);
+    for (int q0 = 0; q0 < K; q0 += cap) {
+      const int w = (K - q0 < cap ? K - q0 : cap) * st, w4 = w / 4;
+      for (int i = tid; i < nb * w4; i += kTcThreads) {
+        const int b = i / w4, j = i - b * w4;
+        const unsigned int saddr = smem_u32(stage + (size_t)b * w + 4 * j);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr),
+                     "l"(p.partials + (size_t)b * wst + q0 * st + 4 * j)
+                     : "memory");
+      }
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      __syncthreads();
+      // one thread per column: four compensated partial sums over rows
+      // b = k mod 4 (independent chains), combined in a fixed order
+      for (int pc = tid; pc < w; pc += kTcThreads) {
+        const int op = (pc % st) == 2 ? 1 : 0;  // the maxd column of each candidate
+        float2 acc[4] = {col_init2(op), col_init2(op), col_init2(op), col_init2(op)};
+        int b = 0;
+        for (; b + 4 <= nb; b += 4) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) col_comb2(op, acc[k], make_float2(stage[(size_t)(b + k) * w + pc], 0.f));
+        }
+        for (int k = 0; b + k < nb; ++k) col_comb2(op, acc[k], make_float2(stage[(size_t)(b + k) * w + pc], 0.f));
+        col_comb2(op, acc[0], acc[1]);
+        col_comb2(op, acc[2], acc[3]);
+        col_comb2(op, acc[0], acc[2]);
+        raw[q0 * st + pc] = acc[0];
+      }
+      __syncthreads();
+    }
+    if (tid == 0) p.counter[0] = 0u;
+  } else {
+    final_reduce(p.partials, wst, p.grows, p.counter, s_scr, opof, raw, stage, false, 2, -1, st);
+  }
   __syncthreads();
   const double gam1 = p.radii ? (double)__ldg(p.radii) : 0.0;
   for (int q = warp; q < K; q += kTcThreads / 32) {

@@ -236,3 +236,37 @@ def test_candidates_single_steps_from_checkpoints(n, d, k, radii):
             assert r["t"] == (t if o["failed"] else t + 1)
         mean, _ = m.read(j)
         assert np.linalg.norm(mean.cpu().numpy().astype(np.float64) - o["ubar_next"]) <= tol, j
+
+
+def test_tensor_core_pass_wait_limit_poisons_rows_then_normal_steps(monkeypatch):
+    """PDSCP_WAIT_LIMIT=0 makes every bounded wait of the tensor-core pass give
+    up at once: each role stops, the MMA warps still wait (with the default
+    limit) for their loads and MMAs, and the poisoned rows make every
+    candidate's finish report PDSCP_ERR_NUMERIC. The same process then runs a
+    normal pass that matches the oracle."""
+    V32 = datagen.ses_gaussian(50_000, 32, seed=12)
+    V = V32.astype(np.float64)
+    D = oses.ses_D(V)
+    rho = oses.ses_width(D)
+    k = 16
+    alphas = np.array([(0.7 + 0.03 * j) * D for j in range(k)])
+    pts = torch.from_numpy(V32).cuda()
+    a_dev = torch.tensor(alphas, dtype=torch.float64, device="cuda")
+    e_dev = torch.full((k,), 0.5 / rho, dtype=torch.float64, device="cuda")
+    out = api.new_steps(k)
+    m = api.MultiMWU(pts, k)
+    monkeypatch.setenv("PDSCP_WAIT_LIMIT", "0")
+    m.step(a_dev, e_dev, out=out)
+    torch.cuda.synchronize()
+    monkeypatch.delenv("PDSCP_WAIT_LIMIT")
+    r = api.decode_steps(out)
+    assert np.all(r["status"] == 6) and np.all(r["stopped"] == 1), r["status"]
+    m2 = api.MultiMWU(pts, k)
+    m2.step(a_dev, e_dev, out=out)
+    torch.cuda.synchronize()
+    r = api.decode_steps(out)
+    for j in range(k):
+        o = oses.ses_step(V, None, V[0].copy(), 0, alphas[j], 0.5, rho)
+        assert r[j]["status"] == 0
+        for key in ("objective", "oracle_value", "lower_bound"):
+            assert abs(r[j][key] - o[key]) <= RTOL * D, (j, key)
