@@ -76,28 +76,33 @@ constexpr int kTcMmaWarp = kTcExpWarps + kTcSplitWarps;  // TMA loads and P; the
 constexpr int kTcThreads = 32 * (kTcMmaWarp + 2);
 constexpr int kTcStages = 3;
 // dynamic shared memory (bytes from a 1024-aligned base)
-constexpr int kTcTileBytes = kTcTile * kTcD * 4;
-constexpr int kTcY2 = kTcStages * kTcTileBytes;  // after the TMA stages (y_1 written in place)
-constexpr int kTcY3 = kTcY2 + kTcTileBytes;
+constexpr int kTcTileBytes = kTcTile * kTcD * 4;  // TMA stages first
 // Q's A operand, two buffers: Y^T, 4 K-blocks of 32 points x 96 rows
 constexpr int kTcA2Blk = 3 * kTcD * 128;
 constexpr int kTcA2Bytes = 4 * kTcA2Blk;
-constexpr int kTcA2 = kTcY3 + kTcTileBytes;
+constexpr int kTcA2 = kTcStages * kTcTileBytes;
 // P's B operand: [u~_1; u~_2; u~_3] stacked, 48 rows x 32 features (the three
 // 16-row parts are contiguous: each is two 1024-byte atoms); the last Q
 // buffer's rows past its end read here
 constexpr int kTcU = kTcA2 + 2 * kTcA2Bytes;
-// Q's B operand: [c_1; c_2; c_3] stacked, 48 rows x 128 points
+// Q's B operand, two buffers: [c_1; c_2; c_3] stacked, 48 rows x 128 points
 constexpr int kTcC = kTcU + 3 * kTcN * kTcD * 4;
 constexpr int kTcCBlk = 3 * kTcN * 128;
-constexpr int kTcSmem = kTcC + 4 * kTcCBlk + 1024;  // + alignment slack
-static_assert(kTcA2 % 1024 == 0 && kTcU % 1024 == 0 && kTcC % 1024 == 0 && kTcA2Blk % 1024 == 0, "swizzle atoms");
+constexpr int kTcCBytes = 4 * kTcCBlk;
+constexpr int kTcSmem = kTcC + 2 * kTcCBytes + 1024;  // + alignment slack
+static_assert(kTcA2 % 1024 == 0 && kTcU % 1024 == 0 && kTcC % 1024 == 0 && kTcA2Blk % 1024 == 0 &&
+                  kTcCBytes % 1024 == 0,
+              "swizzle atoms");
 static_assert(3 * kTcA2Blk + 128 * 128 <= kTcA2Bytes + 3 * kTcN * kTcD * 4, "Q's rows past the last buffer stay in U");
-// TMEM columns: P(u) in buffer u & 1 at 96 (u & 1): six products (y_1 [u_1
-// u_2 u_3], y_2 [u_1 u_2], y_3 u_1: 16 columns each); Q at 192-239 ([c_1 c_2 c_3])
-constexpr int kTcTmemCols = 256;
+// TMEM columns (all 512 of the SM): tile u's parts [y_1 y_2 y_3] (P's A
+// operand, lane = point) in buffer u & 1 at 96 (u & 1); P(u) in buffer u & 1
+// at 192 + 96 (u & 1): six products (y_1 [u_1 u_2 u_3], y_2 [u_1 u_2], y_3 u_1:
+// 16 columns each); Q at 384-431 ([c_1 c_2 c_3])
+constexpr int kTcTmemCols = 512;
+constexpr int kTcYCol = 0;
+constexpr int kTcPCol = 192;
 constexpr int kTcPCols = 96;
-constexpr int kTcQCol = 192;
+constexpr int kTcQCol = 384;
 
 // byte offset of element (row, col) in a 128-byte swizzled K-major operand of
 // `rows` rows (col along K, 32 floats per 128-byte atom row)
@@ -245,6 +250,33 @@ __device__ __forceinline__ void tma_load_tile_w(uint32_t dst, const CUtensorMap*
       ::"r"(smem_u32(bar)), "r"(kTcTile * kTcD * 4), "r"(dst), "l"(map), "r"(0), "r"(row0)
       : "memory");
 }
+// the same with A in TMEM (lane = row of A, one column per K element)
+__device__ __forceinline__ void tc_mma_tw(uint32_t tmem, uint32_t ta, uint64_t db, uint32_t idesc, bool acc) {
+  asm volatile(
+      "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem),
+      "r"(ta), "l"(db), "r"(idesc), "r"(acc ? 1u : 0u)
+      : "memory");
+}
+// 32 consecutive FP32 columns of this thread's TMEM lane (tcgen05.wait::st
+// before the data is handed on)
+__device__ __forceinline__ void tc_st32(uint32_t addr, const float (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};\n" ::"r"(addr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])),
+      "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])),
+      "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])),
+      "r"(__float_as_uint(v[23])), "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])),
+      "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])),
+      "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
+}
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 // a bounded wait by every lane of a warp, its outcome the same in all lanes
 __device__ __forceinline__ bool tc_wait_w(uint64_t* bar, unsigned int parity, unsigned int limit,
                                           const volatile int* abort) {
@@ -261,14 +293,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
   static_assert(K >= 1 && K <= kTcN, "up to 16 candidates");
   extern __shared__ __align__(128) unsigned char smem_raw[];  // aligned to 1024 below (the swizzle atoms)
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  // mbarriers: TMA stage loaded / read by P; tile operands of P written (per
-  // stage), Y^T written (per buffer); P done, P read (per TMEM buffer); C
-  // written; Q done (per Y^T buffer); everything issued done
-  __shared__ uint64_t s_full[kTcStages], s_sempty[kTcStages], s_yready[kTcStages];
-  __shared__ uint64_t s_a2ready[2], s_pdone[2], s_pfree[2], s_qdone[2], s_cready, s_fin;
+  // mbarriers: TMA stage loaded / read by the split; per buffer (tile u in
+  // buffer u & 1): Y parts and norms written, Y^T written, P done, P read,
+  // C written, Q done; everything issued done
+  __shared__ uint64_t s_full[kTcStages], s_sempty[kTcStages];
+  __shared__ uint64_t s_yready[2], s_a2ready[2], s_pdone[2], s_pfree[2], s_cready[2], s_qdone[2], s_fin;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
-  __shared__ float s_norm[kTcStages][kTcTile];
+  __shared__ float s_norm[2][kTcTile];
   __shared__ float s_v1[kTcD], s_ctr[kTcD], s_un[kTcN], s_kr[kTcN], s_H[kTcN], s_al[kTcN];
   __shared__ int s_live[kTcN];
   __shared__ float s_sc[kTcExpWarps][kTcN][4];
@@ -328,16 +360,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
   if (tid == 0) {
     for (int s = 0; s < kTcStages; ++s) {
       mbar_init(s_full + s, 1);
-      mbar_init(s_sempty + s, 1);
-      mbar_init(s_yready + s, 32 * kTcSplitWarps);
+      mbar_init(s_sempty + s, 32 * kTcSplitWarps);
     }
     for (int b = 0; b < 2; ++b) {
+      mbar_init(s_yready + b, 32 * kTcSplitWarps);
       mbar_init(s_a2ready + b, 32 * kTcSplitWarps);
       mbar_init(s_pdone + b, 1);
       mbar_init(s_pfree + b, 32 * kTcExpWarps);
+      mbar_init(s_cready + b, 32 * kTcExpWarps);
       mbar_init(s_qdone + b, 1);
     }
-    mbar_init(&s_cready, 32 * kTcExpWarps);
     mbar_init(&s_fin, 2);
     s_abort = 0;
     mbar_init_fence();
@@ -372,12 +404,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
     const uint32_t lrow = (uint32_t)(32 * (warp & 3)) << 16;
     const int rcc = (r & 31) >> 2;
     const int cb = (r >> 5) * kTcCBlk + (h << 10) + ((r & 3) << 2);
-    for (int u = 0, s = 0; u < nt; ++u, s = s + 1 == kTcStages ? 0 : s + 1) {
+    for (int u = 0; u < nt; ++u) {
       const int b = u & 1;
-      // yready[s] completes next for tile u + 3, whose split waits for
-      // P(u + 2); pdone[b] next for P(u + 2): both issued after this role's
-      // reads of P(u) (pfree)
-      bool okw = tc_wait(s_yready + s, (unsigned int)(u / kTcStages) & 1u, wl, abort_flag);
+      // yready[b] completes next for tile u + 2, whose split waits for this
+      // role's reads of tile u (pfree[b]); pdone[b] next for P(u + 2), which
+      // waits for them too
+      bool okw = tc_wait(s_yready + b, (unsigned int)(u >> 1) & 1u, wl, abort_flag);
       okw = okw && tc_wait(s_pdone + b, (unsigned int)(u >> 1) & 1u, wl, abort_flag);
       if (!__all_sync(0xffffffffu, okw)) {  // (a warp reads TMEM only if all its lanes saw the MMAs complete)
         *abort_flag = 1;
@@ -386,7 +418,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
       tc_fence_after();
       float P[8];
       {
-        const uint32_t la = tmem + lrow + kTcPCols * b + 8 * h;
+        const uint32_t la = tmem + lrow + kTcPCol + kTcPCols * b + 8 * h;
         uint32_t p11[8], p12[8], p13[8], p21[8], p22[8], p31[8];
         tc_ld8_nw(la, p11);
         tc_ld8_nw(la + 16, p12);
@@ -401,9 +433,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
                   (__uint_as_float(p21[j]) + __uint_as_float(p12[j]))) +
                  __uint_as_float(p11[j]);
       }
-      // these reads of TMEM and of the norm, then the arrival that lets P(u + 2)
-      // (and after it the split of tile u + 3) overwrite them
-      const float yn = s_norm[s][r];
+      // these reads of TMEM and of the norm, then the arrival that lets the
+      // split of tile u + 2 and P(u + 2) overwrite them
+      const float yn = s_norm[b][r];
       tc_fence_before();
       tc_arrive(s_pfree + b);
       const int64_t g = (blockIdx.x + (int64_t)u * gridDim.x) * kTcTile + r;
@@ -430,22 +462,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
         Cs[jj] += c;
         tc_split3(c, c1[jj], c2[jj], c3[jj]);
       }
-      // C is free once Q(u - 1) is done; qdone[(u - 1) & 1] completes next
-      // for Q(u + 1), which waits for this role's C of tile u + 1
-      if (u >= 1 && !__all_sync(0xffffffffu, tc_wait(s_qdone + ((u - 1) & 1), (unsigned int)((u - 1) >> 1) & 1u, wl,
+      // C buffer b is free once Q(u - 2) is done; qdone[b] completes next
+      // for Q(u), which waits for this role's C of tile u
+      if (u >= 2 && !__all_sync(0xffffffffu, tc_wait(s_qdone + b, (unsigned int)((u - 2) >> 1) & 1u, wl,
                                                       abort_flag))) {
         *abort_flag = 1;
         break;
       }
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {  // tc_sw128(16 part + 8 h + jj, r, 48), the row-dependent part hoisted
-        const int o = cb + (jj << 7) + ((rcc ^ jj) << 4);
-        *reinterpret_cast<float*>(sm + kTcC + o) = c1[jj];
-        *reinterpret_cast<float*>(sm + kTcC + o + 2048) = c2[jj];
-        *reinterpret_cast<float*>(sm + kTcC + o + 4096) = c3[jj];
+        const int o = kTcC + b * kTcCBytes + cb + (jj << 7) + ((rcc ^ jj) << 4);
+        *reinterpret_cast<float*>(sm + o) = c1[jj];
+        *reinterpret_cast<float*>(sm + o + 2048) = c2[jj];
+        *reinterpret_cast<float*>(sm + o + 4096) = c3[jj];
       }
       fence_proxy_async_smem();
-      tc_arrive(&s_cready);
+      tc_arrive(s_cready + b);
     }
     // the warp's sums per candidate [S, Wt, maxd, sum c]
 #pragma unroll
@@ -467,17 +499,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
     }
   } else if (warp < kTcMmaWarp) {
     // ---- split warps: thread r takes point r of each tile (warp 8 + w the
-    // points 32 w .., one K-block of Y^T)
+    // points 32 w .., TMEM lanes 32 w .., one K-block of Y^T)
     const int r = tid - 32 * kTcExpWarps;
     const int rc = lane >> 2;
     const int a2b = (r >> 5) * kTcA2Blk + ((lane & 3) << 2);
+    const uint32_t ty = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + kTcYCol;
     for (int u = 0, s = 0; u < nt; ++u, s = s + 1 == kTcStages ? 0 : s + 1) {
       const int b = u & 1;
-      // full[s] completes next for tile u + 3, loaded after P(u) read this
-      // stage; pdone[(u - 1) & 1] next for P(u + 1): both after this role's
-      // tile u (y_2, y_3 are free once P(u - 1) is done)
+      // full[s] completes next for tile u + 3, loaded after this role's
+      // reads of tile u (sempty[s]); pfree[b] next once P(u) has been read,
+      // which waits for this role's parts of tile u (the parts and the norm
+      // of tile u - 2 in buffer b are free once P(u - 2) has been read)
       bool okw = tc_wait(s_full + s, (unsigned int)(u / kTcStages) & 1u, wl, abort_flag);
-      if (u >= 1) okw = okw && tc_wait(s_pdone + ((u - 1) & 1), (unsigned int)((u - 1) >> 1) & 1u, wl, abort_flag);
+      if (u >= 2) okw = okw && tc_wait(s_pfree + b, (unsigned int)((u - 2) >> 1) & 1u, wl, abort_flag);
       if (!__all_sync(0xffffffffu, okw)) {
         *abort_flag = 1;
         break;
@@ -485,32 +519,42 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
       tc_fence_after();
       const int64_t g = (blockIdx.x + (int64_t)u * gridDim.x) * kTcTile + r;
       const bool valid = g < p.n;
-      unsigned char* tptr = sm + s * kTcTileBytes;
-      // y = x - m (kept for Y^T), its three parts (y_1 over x in place), the row norm
+      const unsigned char* tptr = sm + s * kTcTileBytes;
+      // y = x - m (kept for Y^T) and the row norm; the stage is then free
       float y[kTcD];
       float nrm = 0.f;
 #pragma unroll
       for (int c4 = 0; c4 < kTcD / 4; ++c4) {
-        const int off = r * 128 + ((c4 ^ (r & 7)) << 4);
-        const float4 x = *reinterpret_cast<const float4*>(tptr + off);
+        const float4 x = *reinterpret_cast<const float4*>(tptr + r * 128 + ((c4 ^ (r & 7)) << 4));
         const int e0 = 4 * c4;
         y[e0] = valid ? x.x - s_ctr[e0] : 0.f;
         y[e0 + 1] = valid ? x.y - s_ctr[e0 + 1] : 0.f;
         y[e0 + 2] = valid ? x.z - s_ctr[e0 + 2] : 0.f;
         y[e0 + 3] = valid ? x.w - s_ctr[e0 + 3] : 0.f;
-        float y1[4], y2[4], y3[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          tc_split3(y[e0 + e], y1[e], y2[e], y3[e]);
-          nrm = fmaf(y[e0 + e], y[e0 + e], nrm);
-        }
-        *reinterpret_cast<float4*>(tptr + off) = make_float4(y1[0], y1[1], y1[2], y1[3]);
-        *reinterpret_cast<float4*>(sm + kTcY2 + off) = make_float4(y2[0], y2[1], y2[2], y2[3]);
-        *reinterpret_cast<float4*>(sm + kTcY3 + off) = make_float4(y3[0], y3[1], y3[2], y3[3]);
       }
-      s_norm[s][r] = nrm;
-      fence_proxy_async_smem();
-      tc_arrive(s_yready + s);
+      tc_arrive(s_sempty + s);
+#pragma unroll
+      for (int e = 0; e < kTcD; ++e) nrm = fmaf(y[e], y[e], nrm);
+      // the three parts into TMEM lane r, buffer b: [y_1 y_2 y_3]
+      {
+        float v[kTcD];
+#pragma unroll
+        for (int e = 0; e < kTcD; ++e) v[e] = tc_hi(y[e]);
+        tc_st32(ty + kTcPCols * b, v);
+#pragma unroll
+        for (int e = 0; e < kTcD; ++e) v[e] = tc_hi(y[e] - tc_hi(y[e]));
+        tc_st32(ty + kTcPCols * b + kTcD, v);
+#pragma unroll
+        for (int e = 0; e < kTcD; ++e) {
+          const float rr = y[e] - tc_hi(y[e]);
+          v[e] = rr - tc_hi(rr);
+        }
+        tc_st32(ty + kTcPCols * b + 2 * kTcD, v);
+      }
+      s_norm[b][r] = nrm;
+      tc_wait_st();
+      tc_fence_before();
+      tc_arrive(s_yready + b);
       // Y^T buffer b is free once Q(u - 2) is done; qdone[b] completes next
       // for Q(u), which waits for this role's Y^T of tile u
       if (u >= 2 && !__all_sync(0xffffffffu, tc_wait(s_qdone + b, (unsigned int)((u - 2) >> 1) & 1u, wl, abort_flag))) {
@@ -531,47 +575,46 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
       tc_arrive(s_a2ready + b);
     }
   } else if (warp == kTcMmaWarp) {
-    // ---- the P warp (one elected lane issues): TMA loads three tiles ahead
-    // of the split, P(u) as soon as tile u's operands are written and P(u - 2)
-    // has been read
+    // ---- the P warp (one elected lane issues): TMA loads up to three tiles
+    // ahead of the split, P(u) as soon as tile u's parts are in TMEM and
+    // P(u - 2) has been read
     auto load = [&](int u) {
       const int s = u % kTcStages;
       tma_load_tile_w(sbase + s * kTcTileBytes, &tmap, (int)((blockIdx.x + (int64_t)u * gridDim.x) * kTcTile),
                       s_full + s);
     };
-    const uint64_t du = tc_desc(sbase + kTcU), dy2 = tc_desc(sbase + kTcY2), dy3 = tc_desc(sbase + kTcY3);
+    const uint64_t du = tc_desc(sbase + kTcU);
     int issued = 0;
     for (; issued < nt && issued < kTcStages; ++issued) load(issued);
     bool ok = true;
     for (int u = 0, s = 0; u < nt; ++u, s = s + 1 == kTcStages ? 0 : s + 1) {
       const int b = u & 1;
-      if (u >= 1 && u + 2 < nt) {  // tile u + 2 into the stage P(u - 1) read (sempty: next for P(u + 2), below)
+      if (u >= 1 && u + 2 < nt) {  // tile u + 2 into the stage of tile u - 1 (sempty: next for tile u + 2)
         const int sp = s == 0 ? kTcStages - 1 : s - 1;
         ok = tc_wait_w(s_sempty + sp, (unsigned int)((u - 1) / kTcStages) & 1u, wl, abort_flag);
         if (!ok) break;
         load(u + 2);
         ++issued;
       }
-      // yready[s] completes next for tile u + 3, loaded after P(u); pfree[b]
-      // next when P(u) has been read
-      ok = tc_wait_w(s_yready + s, (unsigned int)(u / kTcStages) & 1u, wl, abort_flag);
+      // yready[b] completes next for tile u + 2, whose split waits for P(u)
+      // to be read; pfree[b] next when P(u) has been read
+      ok = tc_wait_w(s_yready + b, (unsigned int)(u >> 1) & 1u, wl, abort_flag);
       if (ok && u >= 2) ok = tc_wait_w(s_pfree + b, (unsigned int)((u - 2) >> 1) & 1u, wl, abort_flag);
       if (!ok) break;
       tc_fence_after();
       // P(u) = Y U~^T: six products of the three-part splits in three MMA
-      // chains (N = 48, 32, 16 rows of the stacked U~ parts); descriptors
-      // advance by (bytes >> 4) in their address field
-      const uint32_t tp = tmem + kTcPCols * b;
-      const uint64_t dy1 = tc_desc(sbase + s * kTcTileBytes);
+      // chains (N = 48, 32, 16 rows of the stacked U~ parts), A from TMEM
+      // (8 columns per K step), B's descriptor advancing by (bytes >> 4)
+      const uint32_t tp = tmem + kTcPCol + kTcPCols * b;
+      const uint32_t ta = tmem + kTcYCol + kTcPCols * b;
 #pragma unroll
       for (int k = 0; k < kTcD / 8; ++k) {
         const uint64_t ks = (uint64_t)(k * 32 >> 4);
-        tc_mma_w(tp, dy1 + ks, du + ks, tc_idesc(48), k > 0);       // y_1 [u_1 u_2 u_3]
-        tc_mma_w(tp + 48, dy2 + ks, du + ks, tc_idesc(32), k > 0);  // y_2 [u_1 u_2]
-        tc_mma_w(tp + 80, dy3 + ks, du + ks, tc_idesc(16), k > 0);  // y_3 u_1
+        tc_mma_tw(tp, ta + 8 * k, du + ks, tc_idesc(48), k > 0);                 // y_1 [u_1 u_2 u_3]
+        tc_mma_tw(tp + 48, ta + kTcD + 8 * k, du + ks, tc_idesc(32), k > 0);     // y_2 [u_1 u_2]
+        tc_mma_tw(tp + 80, ta + 2 * kTcD + 8 * k, du + ks, tc_idesc(16), k > 0);  // y_3 u_1
       }
       tc_commit_w(s_pdone + b);
-      tc_commit_w(s_sempty + s);
     }
     if (!ok) *abort_flag = 1;
     // every MMA of this warp, then every load issued, complete (bounded, at
@@ -587,16 +630,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) ses_multi_tc_kernel(MultiParams
     // ---- the Q warp (one elected lane issues): Q(u) += [Y_1^T; Y_2^T; Y_3^T]
     // [c_1 c_2 c_3] over tile u's 128 points, one chain of N = 48, once C and
     // Y^T of tile u are written
-    const uint64_t dc = tc_desc(sbase + kTcC);
     bool ok = true;
     for (int u = 0; u < nt; ++u) {
-      // cready completes next for tile u + 1, whose C waits for Q(u);
-      // a2ready[u & 1] next for tile u + 2, whose Y^T waits for Q(u)
-      ok = tc_wait_w(&s_cready, (unsigned int)u & 1u, wl, abort_flag) &&
+      // cready[u & 1] and a2ready[u & 1] complete next for tile u + 2, whose
+      // C and Y^T wait for Q(u)
+      ok = tc_wait_w(s_cready + (u & 1), (unsigned int)(u >> 1) & 1u, wl, abort_flag) &&
            tc_wait_w(s_a2ready + (u & 1), (unsigned int)(u >> 1) & 1u, wl, abort_flag);
       if (!ok) break;
       tc_fence_after();
       const uint64_t da = tc_desc(sbase + kTcA2 + (u & 1) * kTcA2Bytes);
+      const uint64_t dc = tc_desc(sbase + kTcC + (u & 1) * kTcCBytes);
 #pragma unroll 4
       for (int k = 0; k < kTcTile / 8; ++k) {
         const uint64_t ka = (uint64_t)(((k >> 2) * kTcA2Blk + (k & 3) * 32) >> 4);
