@@ -24,41 +24,44 @@
 // the truncation of a - a_1, a_3 the rest, at most 2 bits) and keep the six
 // products down to 2^-22 of each other: FP32-grade results.
 //
-// Operands in shared memory use the 128-byte swizzled K-major layout: a tile
-// of 128 points x 32 floats arrives from HBM by one TMA load with the 128-byte
-// swizzle, which is that layout for Y in P (rows: points, K: features; y_1 is
-// written over x in place, y_2 and y_3 beside it). For Q the points must be
-// the K dimension: the threads write Y^T (rows 0-31, 32-63, 64-95: y_1, y_2,
-// y_3; each K-block of 32 points is 96 rows) and C^T (48 rows: the three
-// parts of the 16 candidates) in the same layout, each warp writing one
-// feature (or candidate) row for 32 consecutive points, which falls on 32
-// distinct banks. Q's M dimension is 128: its rows 96-127 read the next
-// K-block's first rows and are not read back. One MMA chain of N = 48 gives
-// the products y_p c_q of all three parts of C; the six kept are summed
-// smallest first.
+// Operands. P's A operand, the three parts of Y (lane = point, one column
+// per feature), sits in TMEM: the thread of point r stores its parts into
+// TMEM lane r (tcgen05.st). Q's operands sit in shared memory in the
+// 128-byte swizzled K-major layout, with the points as the K dimension: the
+// threads write Y^T (rows 0-31, 32-63, 64-95: y_1, y_2, y_3; each K-block of
+// 32 points is 96 rows) and C^T (48 rows: the three parts of the 16
+// candidates), each warp writing one feature (or candidate) row for 32
+// consecutive points, which falls on 32 distinct banks. Q's M dimension is
+// 128: its rows 96-127 read the next K-block's first rows and are not read
+// back. One MMA chain of N = 48 gives the products y_p c_q of all three parts
+// of C; the six kept are summed smallest first. The points arrive from HBM
+// as tiles of 128 x 32 by TMA loads (three-stage ring, 128-byte swizzle).
 //
 // The CTA is warp-specialised so that the work on consecutive tiles
-// overlaps (one CTA per SM, tiles blockIdx.x, blockIdx.x + gridDim.x, ...):
-//   warps 8-11, one thread per point: centring, splits, y_1 in place and
-//     y_2, y_3 for P (tile u), then Y^T for Q into one of two buffers;
-//   warp 12, one thread: the TMA loads (three stages) and every MMA, P(u)
-//     into one of two TMEM buffers as soon as tile u's operands are written,
-//     Q(u - 1) once its coefficients are;
+// overlaps (one CTA per SM, tiles blockIdx.x, blockIdx.x + gridDim.x, ...;
+// tile u uses buffer u & 1 of every double buffer):
+//   warps 8-11, one thread per point: centring, the row norm, the three
+//     parts into TMEM for P(u), then Y^T for Q into shared memory;
+//   warp 12 (one elected lane issues): the TMA loads, and P(u) as soon as
+//     tile u's parts are in TMEM and P(u - 2)'s accumulators have been read;
+//   warp 13 (likewise): Q(u) once C^T and Y^T of tile u are written;
 //   warps 0-7: thread r + 128 h reads row r of P(u) out of TMEM (candidates
 //     8 h .. 8 h + 7: warp w reads TMEM lanes 32 (w % 4) ..), the
-//     exponentials, and writes C^T once Q(u - 1) has released it.
+//     exponentials (straight-line code, so that the 8 candidates of a thread
+//     interleave), and writes C^T once Q(u - 2) has released its buffer.
 // So while the exponential warps work on tile u, the split warps prepare
 // tile u + 1 and the tensor cores run Q(u - 1) and P(u + 1). Every hand-over
 // is an mbarrier: the producer's writes to shared memory are fenced for the
-// async proxy before it arrives, the MMAs' completion arrives through
-// tcgen05.commit. Each barrier's waits are separated from its next
-// completion by a chain of hand-overs through the waiting role itself, so a
-// parity never aliases (the arguments are beside the waits).
+// async proxy (its TMEM stores waited for and fenced) before it arrives, the
+// MMAs' completion arrives through tcgen05.commit. Each barrier's waits are
+// separated from its next completion by a chain of hand-overs through the
+// waiting role itself, so a parity never aliases (the arguments are beside
+// the waits).
 //
 // Waits are bounded (the staged passes' limit, and a CTA-wide abort flag
 // ends every other role's waits early); a wait that gives up poisons the
 // CTA's rows (S = NaN), so that the finishes report PDSCP_ERR_NUMERIC, and
-// the MMA thread still waits (bounded) for its MMAs and loads in flight
+// the MMA warps still wait (bounded) for their MMAs and loads in flight
 // before the TMEM and shared memory go.
 #pragma once
 
