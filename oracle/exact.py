@@ -18,7 +18,7 @@ polytope-distance problem PD), written out plainly in FP64.
   pd_mdm            the same problem for sets of any size by the
                     Mitchell-Dem'yanov-Malozemov descent (1974), which the
                     paper names among the geometric PD methods (Sec. 4.2):
-                    the certificates of reading 25 solve it on a core set.
+                    the core-set certificates of the SVM search solve it on a core set.
 """
 
 import itertools

@@ -44,14 +44,14 @@ MODE_PRACTICAL = "practical"
 MODE_THEORY = "theory"
 MODE_FIXED = "fixed"
 MODE_CERTIFIED = "certified"
-MODE_CORESET = "coreset"         # CERTIFIED with the core-set certificates of reading 25
+MODE_CORESET = "coreset"         # CERTIFIED with core-set certificates (beyond the paper)
 OUT_STUCK = "stuck"              # CERTIFIED mode: the certificate gap stopped shrinking (eta is halved)
 CERT_FIRST_CHECK = 1024          # CERTIFIED: first progress check of an alpha-FTP at eta = 1 (then 2x, 4x, ...)
 CERT_SHRINK = 0.8                # CERTIFIED: the FTP's own gap must shrink by this factor while t doubles
 CERT_MIN_ETA = 1.0 / 64.0        # CERTIFIED: eta is not halved below this (no progress test there)
 
 SVM_R = 2.0  # Sec. 4.2
-CORESET_K = 512        # points per class in a core set (reading 25)
+CORESET_K = 512        # points per class in a core set
 CORESET_FIRST = 256    # first core-set check after this many iterations of the search, then every doubling
 CORESET_ROUNDS = 4     # active-set rounds of one check
 
@@ -179,7 +179,8 @@ def svm_margin(X, y, wbar):
 
 
 def svm_coreset_pick(X, y, w, K):
-    """The core set picked by a direction w (reading 25): in each class the K
+    """The core set picked by a direction w (core-set certificates, a reading
+    beyond the paper built on Eq. (PD) and Sec. 4.2): in each class the K
     points (all, if fewer) with the smallest y_i x_i^T w, the points nearest
     the hyperplane with normal w, which are also the points the MWU weighs
     most in that class (the class-normalised weights fall with y_i x_i^T w).
@@ -194,7 +195,7 @@ def svm_coreset_pick(X, y, w, K):
 
 
 def svm_coreset_bounds(X, y, w, eps, K=CORESET_K, rounds=CORESET_ROUNDS):
-    """Certificates from core sets (reading 25): restricting Eq. (PD) to a
+    """Certificates from core sets (beyond the paper): restricting Eq. (PD) to a
     subset of each class can only raise its minimum, so the exact polytope
     distance of a core set C (the points svm_coreset_pick takes from w) is an
     upper bound on OPT; the direction z_C of that solution is a separating
@@ -273,7 +274,7 @@ def svm_ftp(X, y, alpha, eta, rho, T, D, mode=MODE_FIXED, delta=1e-4, patience=1
     since the previous such poll (no check once eta <= 1/64). ub_best is the
     best of the per-iteration and the averaged Claim 8 values.
 
-    With cert["coreset"] (mode "coreset" of the search: reading 25), a poll at
+    With cert["coreset"] (mode "coreset" of the search), a poll at
     which the search's iteration count cert["coreset"]["base"] + t has reached
     cert["coreset"]["next"] also runs svm_coreset_bounds from the FTP's best
     direction (wbar when no direction separates yet), folds its bounds into
@@ -353,7 +354,7 @@ def svm_solve(X, y, eps=1e-2, mode=MODE_PRACTICAL, max_iters=10**7, delta=1e-4,
     min(ub, U) <= (1+eps) lb or the budget is spent; eta defaults to 1 and
     upper_bound reports min(ub, U).
 
-    CORESET mode is CERTIFIED with the core-set certificates of reading 25:
+    CORESET mode is CERTIFIED with core-set certificates (beyond the paper):
     at the polls where the search's iteration count first reaches 256, 512,
     1024, ..., svm_coreset_bounds runs from the running FTP's best direction.
     """

@@ -31,40 +31,6 @@ namespace pdscp {
 // ---------------------------------------------------------------------------
 namespace {
 
-// Solves the (k + 2) x (k + 2) system M x = r in place by Gaussian
-// elimination with partial pivoting. Returns false if a pivot vanishes.
-bool solve_dense(std::vector<double>& M, std::vector<double>& r, int m) {
-  for (int c = 0; c < m; ++c) {
-    int piv = c;
-    double best = std::fabs(M[(size_t)c * m + c]);
-    for (int i = c + 1; i < m; ++i) {
-      const double v = std::fabs(M[(size_t)i * m + c]);
-      if (v > best) {
-        best = v;
-        piv = i;
-      }
-    }
-    if (!(best > 1e-300)) return false;
-    if (piv != c) {
-      for (int j = 0; j < m; ++j) std::swap(M[(size_t)c * m + j], M[(size_t)piv * m + j]);
-      std::swap(r[c], r[piv]);
-    }
-    const double inv = 1.0 / M[(size_t)c * m + c];
-    for (int i = c + 1; i < m; ++i) {
-      const double f = M[(size_t)i * m + c] * inv;
-      if (f == 0.0) continue;
-      for (int j = c; j < m; ++j) M[(size_t)i * m + j] -= f * M[(size_t)c * m + j];
-      r[i] -= f * r[c];
-    }
-  }
-  for (int i = m - 1; i >= 0; --i) {
-    double acc = r[i];
-    for (int j = i + 1; j < m; ++j) acc -= M[(size_t)i * m + j] * r[j];
-    r[i] = acc / M[(size_t)i * m + i];
-  }
-  return true;
-}
-
 struct ActiveSet {
   const double* P;
   const double* Q;
@@ -90,10 +56,146 @@ struct ActiveSet {
   }
 };
 
+// A symmetric matrix of variable order k kept in a buffer of a larger
+// stride (capacity), so that a row/column is appended in O(k) and removed in
+// O(k^2) without reallocating.
+struct SymBuf {
+  std::vector<double> a;
+  int k = 0, cap = 0;
+  void reserve(int c) {
+    if (c <= cap) return;
+    int nc = cap > 0 ? cap : 16;
+    while (nc < c) nc *= 2;
+    std::vector<double> b((size_t)nc * nc, 0.0);
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) b[(size_t)i * nc + j] = a[(size_t)i * cap + j];
+    a.swap(b);
+    cap = nc;
+  }
+  double& at(int i, int j) { return a[(size_t)i * cap + j]; }
+  double at(int i, int j) const { return a[(size_t)i * cap + j]; }
+  void drop(int p) {  // removes row and column p
+    for (int i = 0; i < k; ++i) {
+      if (i == p) continue;
+      double* row = a.data() + (size_t)i * cap;
+      for (int j = p; j + 1 < k; ++j) row[j] = row[j + 1];
+    }
+    for (int i = p; i + 1 < k; ++i)
+      std::copy(a.begin() + (size_t)(i + 1) * cap, a.begin() + (size_t)(i + 1) * cap + k - 1, a.begin() + (size_t)i * cap);
+    --k;
+  }
+};
+
+// Inverse of the KKT matrix of the affine least-distance problem on the
+// support, K = [[0, E^T], [E, G]] (rows 0, 1: the two classes' sums; then
+// the support's Gram matrix G and class indicators E), kept up to date by
+// bordering (a point added) and by the inverse's partition formula (a point
+// removed), O(k^2) each; rebuilt by Gauss-Jordan elimination when a pivot or
+// the check of a solve's residual says the updates have lost accuracy.
+struct KktInverse {
+  SymBuf inv;
+  std::vector<double> u, M;
+  bool rebuild(const SymBuf& G, const std::vector<int>& cls) {
+    const int k = G.k, n = k + 2;
+    inv.reserve(n);
+    inv.k = n;
+    M.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < k; ++i) {
+      M[(size_t)cls[i] * n + 2 + i] = M[(size_t)(2 + i) * n + cls[i]] = 1.0;
+      for (int j = 0; j < k; ++j) M[(size_t)(2 + i) * n + 2 + j] = G.at(i, j);
+    }
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) inv.at(i, j) = i == j ? 1.0 : 0.0;
+    for (int c = 0; c < n; ++c) {
+      int piv = c;
+      double best = std::fabs(M[(size_t)c * n + c]);
+      for (int i = c + 1; i < n; ++i) {
+        const double v = std::fabs(M[(size_t)i * n + c]);
+        if (v > best) best = v, piv = i;
+      }
+      if (!(best > 1e-300)) return false;
+      if (piv != c)
+        for (int j = 0; j < n; ++j) {
+          std::swap(M[(size_t)c * n + j], M[(size_t)piv * n + j]);
+          std::swap(inv.at(c, j), inv.at(piv, j));
+        }
+      const double dv = 1.0 / M[(size_t)c * n + c];
+      for (int j = 0; j < n; ++j) {
+        M[(size_t)c * n + j] *= dv;
+        inv.at(c, j) *= dv;
+      }
+      for (int i = 0; i < n; ++i) {
+        if (i == c) continue;
+        const double f = M[(size_t)i * n + c];
+        if (f == 0.0) continue;
+        for (int j = 0; j < n; ++j) {
+          M[(size_t)i * n + j] -= f * M[(size_t)c * n + j];
+          inv.at(i, j) -= f * inv.at(c, j);
+        }
+      }
+    }
+    return true;
+  }
+  // bordering: a new last row/column b (length n) with diagonal dd
+  bool append(const std::vector<double>& b, double dd) {
+    const int n = inv.k;
+    u.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int j = 0; j < n; ++j) s += inv.at(i, j) * b[j];
+      u[i] = s;
+    }
+    double bu = 0.0;
+    for (int i = 0; i < n; ++i) bu += b[i] * u[i];
+    const double sc = dd - bu;
+    if (!(std::fabs(sc) > 1e-12 * (std::fabs(dd) + std::fabs(bu)))) return false;
+    inv.reserve(n + 1);
+    const double is = 1.0 / sc;
+    for (int i = 0; i < n; ++i) {
+      const double ui = u[i] * is;
+      for (int j = 0; j < n; ++j) inv.at(i, j) += ui * u[j];
+      inv.at(i, n) = -ui;
+      inv.at(n, i) = -ui;
+    }
+    inv.at(n, n) = is;
+    inv.k = n + 1;
+    return true;
+  }
+  // removal of row/column p
+  bool remove(int p) {
+    const int n = inv.k;
+    const double pp = inv.at(p, p);
+    if (!(std::fabs(pp) > 1e-300)) return false;
+    const double ip = 1.0 / pp;
+    for (int i = 0; i < n; ++i) {
+      if (i == p) continue;
+      const double f = inv.at(i, p) * ip;
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j)
+        if (j != p) inv.at(i, j) -= f * inv.at(p, j);
+    }
+    inv.drop(p);
+    return true;
+  }
+};
+
+// out[k] = X[k] . v for the rows of a matrix given transposed (XT: d x rows),
+// as one scaled-row sum per feature (vectorisable; each dot product summed
+// over the features in order)
+void transposed_dots(const double* __restrict__ XT, int rows, int d, const double* __restrict__ v,
+                     double* __restrict__ out) {
+  std::fill(out, out + rows, 0.0);
+  for (int j = 0; j < d; ++j) {
+    const double vj = v[j];
+    const double* x = XT + (size_t)j * rows;
+    for (int k = 0; k < rows; ++k) out[k] += x[k] * vj;
+  }
+}
+
 }  // namespace
 
 int pd_active_set(const double* P, int nP, const double* Q, int nQ, int d, double tol, int max_iter, double* mu,
-                  double* ga, double* z, double* gap_out) {
+                  double* ga, double* z, double* gap_out, const double* mu0, const double* ga0) {
   ActiveSet A{P, Q, nP, nQ, d};
   const int m = nP + nQ;
   std::vector<double> zc(d, 0.0), cen(d, 0.0);
@@ -101,6 +203,12 @@ int pd_active_set(const double* P, int nP, const double* Q, int nQ, int d, doubl
     for (int j = 0; j < d; ++j) cen[j] += P[(size_t)i * d + j] / nP;
   for (int i = 0; i < nQ; ++i)
     for (int j = 0; j < d; ++j) cen[j] -= Q[(size_t)i * d + j] / nQ;
+  // the candidates transposed (features x candidates, Q negated) for the scans
+  std::vector<double> AT((size_t)d * m);
+  for (int k = 0; k < nP; ++k)
+    for (int j = 0; j < d; ++j) AT[(size_t)j * m + k] = P[(size_t)k * d + j];
+  for (int k = 0; k < nQ; ++k)
+    for (int j = 0; j < d; ++j) AT[(size_t)j * m + nP + k] = -Q[(size_t)k * d + j];
   // start: the pair nearest along the difference of the centroids
   int s0 = 0, s1 = nP;
   double b0 = INFINITY, b1 = INFINITY;
@@ -110,42 +218,94 @@ int pd_active_set(const double* P, int nP, const double* Q, int nQ, int d, doubl
     if (k >= nP && v < b1) b1 = v, s1 = k;
   }
   std::vector<int> S = {s0, s1};       // support (candidate indices)
+  std::vector<int> cls = {0, 1};       // their classes
   std::vector<double> c = {1.0, 1.0};  // weights on the support
-  std::vector<double> G = {A.dot_aa(s0, s0), A.dot_aa(s0, s1), A.dot_aa(s1, s0), A.dot_aa(s1, s1)};
+  if (mu0 && ga0) {
+    // warm start: the positive weights given (renormalised per class), if
+    // each class has some
+    std::vector<int> S2, cls2;
+    std::vector<double> c2;
+    double w[2] = {0.0, 0.0};
+    for (int k = 0; k < m; ++k) {
+      const double v = k < nP ? mu0[k] : ga0[k - nP];
+      if (v > 0.0) {
+        S2.push_back(k);
+        cls2.push_back(k < nP ? 0 : 1);
+        c2.push_back(v);
+        w[k < nP ? 0 : 1] += v;
+      }
+    }
+    if (w[0] > 0.0 && w[1] > 0.0) {
+      for (size_t i = 0; i < S2.size(); ++i) c2[i] /= w[cls2[i]];
+      S.swap(S2);
+      cls.swap(cls2);
+      c.swap(c2);
+    }
+  }
+  SymBuf G;  // the support's Gram matrix
+  G.reserve(std::max<int>(2 * d + 8, (int)S.size() + 8));
+  G.k = (int)S.size();
+  for (int i = 0; i < G.k; ++i)
+    for (int j = 0; j < G.k; ++j) G.at(i, j) = A.dot_aa(S[i], S[j]);
   std::vector<char> in(m, 0);
-  in[s0] = in[s1] = 1;
+  for (int k : S) in[k] = 1;
+  KktInverse K;
+  K.inv.reserve(G.cap + 2);
+  bool have_inv = K.rebuild(G, cls);
   auto rebuild_z = [&]() {
     std::fill(zc.begin(), zc.end(), 0.0);
     for (size_t i = 0; i < S.size(); ++i) A.axpy_a(S[i], c[i], zc.data());
   };
   auto remove_at = [&](size_t pos) {
-    const size_t k = S.size();
-    std::vector<double> G2;
-    G2.reserve((k - 1) * (k - 1));
-    for (size_t i = 0; i < k; ++i) {
-      if (i == pos) continue;
-      for (size_t j = 0; j < k; ++j)
-        if (j != pos) G2.push_back(G[i * k + j]);
-    }
-    G.swap(G2);
+    G.drop((int)pos);
     in[S[pos]] = 0;
     S.erase(S.begin() + pos);
+    cls.erase(cls.begin() + pos);
     c.erase(c.begin() + pos);
+    if (have_inv) have_inv = K.remove(2 + (int)pos);
   };
+  // the affine optimum on the support: x = K^-1 (1, 1, 0, ..., 0), checked
+  // by its residual against G (rebuilt once if the updates drifted)
+  std::vector<double> x;
+  auto solve = [&]() -> bool {
+    const int ks = (int)S.size(), n = ks + 2;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      if (!have_inv) have_inv = K.rebuild(G, cls);
+      if (!have_inv) return false;
+      x.assign(n, 0.0);
+      for (int i = 0; i < n; ++i) x[i] = K.inv.at(i, 0) + K.inv.at(i, 1);
+      double scale = 1.0, s0c = 0.0, s1c = 0.0;
+      for (int i = 0; i < ks; ++i) (cls[i] ? s1c : s0c) += x[2 + i];
+      double res = std::max(std::fabs(s0c - 1.0), std::fabs(s1c - 1.0));
+      for (int i = 0; i < ks; ++i) {
+        double gi = x[cls[i]], mag = std::fabs(gi);
+        for (int j = 0; j < ks; ++j) {
+          const double t = G.at(i, j) * x[2 + j];
+          gi += t;
+          mag += std::fabs(t);
+        }
+        res = std::max(res, std::fabs(gi));
+        scale = std::max(scale, mag);
+      }
+      if (res <= 1e-10 * scale) return true;
+      have_inv = false;  // drifted: rebuild and solve again
+    }
+    return false;
+  };
+  std::vector<double> av(m), bcol;
   rebuild_z();
   double gap = INFINITY;
   int it = 0;
   for (; it < max_iter; ++it) {
-    // optimality: z.z = lam0 + lam1 with lam_c the weighted projection of
-    // class c; the margin of z times |z| is min_P a.z + min_Q a.z
     double zz = 0.0;
     for (int j = 0; j < d; ++j) zz += zc[j] * zc[j];
+    transposed_dots(AT.data(), m, d, zc.data(), av.data());  // a_k . z for every candidate
     double lam[2] = {0.0, 0.0};
-    for (size_t i = 0; i < S.size(); ++i) lam[S[i] < nP ? 0 : 1] += c[i] * A.dot_a(S[i], zc.data());
+    for (size_t i = 0; i < S.size(); ++i) lam[cls[i]] += c[i] * av[S[i]];
     double mn[2] = {INFINITY, INFINITY};
     int arg[2] = {-1, -1};
     for (int k = 0; k < m; ++k) {
-      const double v = A.dot_a(k, zc.data());
+      const double v = av[k];
       const int cl = k < nP ? 0 : 1;
       if (v < mn[cl]) mn[cl] = v, arg[cl] = k;
     }
@@ -153,58 +313,52 @@ int pd_active_set(const double* P, int nP, const double* Q, int nQ, int d, doubl
     if (gap <= tol * zz) break;
     const int cl = (lam[0] - mn[0] >= lam[1] - mn[1]) ? 0 : 1;
     const int add = arg[cl];
-    if (add < 0 || in[add]) break;  // no progress possible in this arithmetic
-    // add with weight 0
-    const size_t k = S.size();
-    std::vector<double> G2((k + 1) * (k + 1));
-    for (size_t i = 0; i < k; ++i)
-      for (size_t j = 0; j < k; ++j) G2[i * (k + 1) + j] = G[i * k + j];
-    for (size_t i = 0; i < k; ++i) G2[i * (k + 1) + k] = G2[k * (k + 1) + i] = A.dot_aa(S[i], add);
-    G2[k * (k + 1) + k] = A.dot_aa(add, add);
-    G.swap(G2);
+    if (add < 0 || in[add]) break;
+    const int k = (int)S.size();
+    bcol.assign(k + 2, 0.0);
+    bcol[cl] = 1.0;
+    G.reserve(k + 1);
+    for (int i = 0; i < k; ++i) {
+      const double g = A.dot_aa(S[i], add);
+      G.at(i, k) = G.at(k, i) = g;
+      bcol[2 + i] = g;
+    }
+    const double gaa = A.dot_aa(add, add);
+    G.at(k, k) = gaa;
+    G.k = k + 1;
     S.push_back(add);
+    cls.push_back(cl);
     c.push_back(0.0);
     in[add] = 1;
-    // minor cycles: move toward the affine optimum on the support, dropping
-    // points whose weight reaches zero on the way
+    if (have_inv) have_inv = K.append(bcol, gaa);
     bool stalled = false;
     for (int minor = 0; minor < 4 * m + 8; ++minor) {
-      const int ks = (int)S.size(), ms = ks + 2;
-      std::vector<double> M((size_t)ms * ms, 0.0), r(ms, 0.0);
-      for (int i = 0; i < ks; ++i) {
-        for (int j = 0; j < ks; ++j) M[(size_t)i * ms + j] = G[(size_t)i * ks + j];
-        const int cl2 = S[i] < nP ? 0 : 1;
-        M[(size_t)i * ms + ks + cl2] = 1.0;
-        M[(size_t)(ks + cl2) * ms + i] = 1.0;
-      }
-      r[ks] = r[ks + 1] = 1.0;
-      if (!solve_dense(M, r, ms)) {
+      const int ks = (int)S.size();
+      if (!solve()) {
         stalled = true;
         break;
       }
       bool all_pos = true;
       for (int i = 0; i < ks; ++i)
-        if (!(r[i] > 0.0)) all_pos = false;
+        if (!(x[2 + i] > 0.0)) all_pos = false;
       if (all_pos) {
-        for (int i = 0; i < ks; ++i) c[i] = r[i];
+        for (int i = 0; i < ks; ++i) c[i] = x[2 + i];
         break;
       }
-      // largest step theta in [0, 1] keeping c + theta (r - c) >= 0
       double theta = 1.0;
       int hit = -1;
       for (int i = 0; i < ks; ++i)
-        if (r[i] <= 0.0 && c[i] - r[i] > 0.0) {
-          const double th = c[i] / (c[i] - r[i]);
+        if (x[2 + i] <= 0.0 && c[i] - x[2 + i] > 0.0) {
+          const double th = c[i] / (c[i] - x[2 + i]);
           if (th < theta) theta = th, hit = i;
         }
-      for (int i = 0; i < ks; ++i) c[i] += theta * (r[i] - c[i]);
+      for (int i = 0; i < ks; ++i) c[i] += theta * (x[2 + i] - c[i]);
       if (hit >= 0) c[hit] = 0.0;
       bool removed = false;
       for (int i = ks - 1; i >= 0; --i) {
-        const int cl2 = S[i] < nP ? 0 : 1;
         int others = 0;
-        for (int j = 0; j < ks; ++j)
-          if (j != i && (S[j] < nP ? 0 : 1) == cl2) ++others;
+        for (int j = 0; j < (int)S.size(); ++j)
+          if (j != i && cls[j] == cls[i]) ++others;
         if (c[i] <= 0.0 && others > 0) {
           remove_at((size_t)i);
           removed = true;
@@ -216,9 +370,8 @@ int pd_active_set(const double* P, int nP, const double* Q, int nQ, int d, doubl
       }
     }
     rebuild_z();
-    if (stalled || !in[add]) break;  // the point just added left again: no progress in this arithmetic
+    if (stalled || !in[add]) break;
   }
-  // weights on the two simplices (clamped, renormalised) and the final z
   double s0w = 0.0, s1w = 0.0;
   for (size_t i = 0; i < S.size(); ++i) {
     if (c[i] < 0.0) c[i] = 0.0;
@@ -415,7 +568,8 @@ pdscp_status svm_coreset_check(const void* X, int dtype, const int8_t* y, int64_
   cudaError_t e = project(w, mmh);
   if (e != cudaSuccess) return fail_cuda(e, "coreset: projection");
   std::vector<float> rowsh;
-  std::vector<double> Pd, Qd, mu, ga, z(d);
+  std::vector<double> Pd, Qd, mu, ga, z(d), mu0, ga0;
+  std::vector<std::pair<int, double>> prev[2];  // the last round's solution: (row, weight) per class
   for (int round = 0; round < kCoresetRounds; ++round) {
     // per class: a threshold taking between K and 2K points (bisection on
     // its float value over [min, max] of the class), or every point of a
@@ -497,9 +651,24 @@ pdscp_status svm_coreset_check(const void* X, int dtype, const int8_t* y, int64_
     Qd.assign(rowsh.begin() + (size_t)nP * d, rowsh.end());
     mu.assign(nP, 0.0);
     ga.assign(nQ, 0.0);
+    // warm start from the last round's solution (its rows are in the merged
+    // core sets unless the size cap cut them)
+    mu0.assign(nP, 0.0);
+    ga0.assign(nQ, 0.0);
+    for (int c = 0; c < 2; ++c)
+      for (const auto& rw : prev[c]) {
+        const auto pos = std::lower_bound(core[c].begin(), core[c].end(), rw.first);
+        if (pos != core[c].end() && *pos == rw.first) (c ? ga0 : mu0)[pos - core[c].begin()] = rw.second;
+      }
     double gap = 0.0;
     pd_active_set(Pd.data(), nP, Qd.data(), nQ, d, eps / 10.0, 4 * (nP + nQ) + 64, mu.data(), ga.data(), z.data(),
-                  &gap);
+                  &gap, round > 0 ? mu0.data() : nullptr, round > 0 ? ga0.data() : nullptr);
+    for (int c = 0; c < 2; ++c) {
+      prev[c].clear();
+      const std::vector<double>& wt = c ? ga : mu;
+      for (size_t i = 0; i < wt.size(); ++i)
+        if (wt[i] > 0.0) prev[c].emplace_back(core[c][i], wt[i]);
+    }
     double zz = 0.0;
     for (int j = 0; j < d; ++j) zz += z[j] * z[j];
     if (!(zz > 0.0)) break;

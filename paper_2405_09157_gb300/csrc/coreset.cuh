@@ -19,14 +19,18 @@ constexpr int64_t kCoresetFirst = 256;  // first check at this many iterations o
 // active-set method; returns the iterations run. mu (nP), ga (nQ): the
 // weights on the two simplices; z (d): P^T mu - Q^T ga; *gap: z.z minus
 // (min_i p_i.z - max_j q_j.z) at the end (>= 0; <= tol z.z when converged).
+// mu0, ga0 (optional): weights to start from (their positive entries are the
+// first support, renormalised per class), e.g. a previous solution on a
+// subset of the points.
 int pd_active_set(const double* P, int nP, const double* Q, int nQ, int d, double tol, int max_iter, double* mu,
-                  double* ga, double* z, double* gap);
+                  double* ga, double* z, double* gap, const double* mu0 = nullptr, const double* ga0 = nullptr);
 
 // Bytes of workspace the core-set checks of svm_solve need for n points in d.
 size_t coreset_bytes(int64_t n, int d);
 
-// One core-set check (reading 25 of the design notes): from direction w0
-// (host, d doubles), core sets picked on the device, solved on the host.
+// One core-set check (core-set certificates, a reading beyond the paper):
+// from direction w0 (host, d doubles), core sets picked on the device,
+// solved on the host.
 // Sets *lb (a margin of some direction over all points), *ub (a core-set
 // distance) and w_lb (that direction, unit norm). ws: coreset_bytes(n, d)
 // bytes of device memory, 256-byte aligned.
