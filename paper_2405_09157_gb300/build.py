@@ -18,7 +18,7 @@ LIB = os.path.join(LIBDIR, "libpdscp.so")
 SOURCES = ["api.cu", "kern_ses.cu", "kern_svm.cu", "batch.cu", "kern_bwd.cu", "kern_bwd_bf16.cu", "kern_multi.cu",
            "coreset.cu", "svm_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3"]
 
 
 def nvcc():
