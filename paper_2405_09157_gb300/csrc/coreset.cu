@@ -192,6 +192,17 @@ void transposed_dots(const double* __restrict__ XT, int rows, int d, const doubl
   }
 }
 
+// the same in FP32
+void transposed_dots_f(const float* __restrict__ XT, int rows, int d, const float* __restrict__ v,
+                       float* __restrict__ out) {
+  std::fill(out, out + rows, 0.0f);
+  for (int j = 0; j < d; ++j) {
+    const float vj = v[j];
+    const float* x = XT + (size_t)j * rows;
+    for (int k = 0; k < rows; ++k) out[k] += x[k] * vj;
+  }
+}
+
 }  // namespace
 
 int pd_active_set(const double* P, int nP, const double* Q, int nQ, int d, double tol, int max_iter, double* mu,
@@ -293,24 +304,48 @@ int pd_active_set(const double* P, int nP, const double* Q, int nQ, int d, doubl
     return false;
   };
   std::vector<double> av(m), bcol;
+  // while far from the stopping gap the scans run in FP32 (on the transposed
+  // candidates rounded once): they only pick the point to add; the stopping
+  // test always rests on an FP64 scan (from the first FP32 estimate within
+  // 4 tol of the gap on, every scan is FP64)
+  const bool fast = tol >= 1e-7;
+  bool exact = !fast;
+  std::vector<float> ATf, zf(d), avf;
+  if (fast) {
+    ATf.resize(AT.size());
+    for (size_t i = 0; i < AT.size(); ++i) ATf[i] = (float)AT[i];
+    avf.resize(m);
+  }
   rebuild_z();
   double gap = INFINITY;
   int it = 0;
   for (; it < max_iter; ++it) {
     double zz = 0.0;
     for (int j = 0; j < d; ++j) zz += zc[j] * zc[j];
-    transposed_dots(AT.data(), m, d, zc.data(), av.data());  // a_k . z for every candidate
-    double lam[2] = {0.0, 0.0};
-    for (size_t i = 0; i < S.size(); ++i) lam[cls[i]] += c[i] * av[S[i]];
-    double mn[2] = {INFINITY, INFINITY};
-    int arg[2] = {-1, -1};
-    for (int k = 0; k < m; ++k) {
-      const double v = av[k];
-      const int cl = k < nP ? 0 : 1;
-      if (v < mn[cl]) mn[cl] = v, arg[cl] = k;
+    double lam[2], mn[2];
+    int arg[2];
+    for (int pass = 0; pass < 2; ++pass) {
+      if (exact) {
+        transposed_dots(AT.data(), m, d, zc.data(), av.data());  // a_k . z for every candidate
+      } else {
+        for (int j = 0; j < d; ++j) zf[j] = (float)zc[j];
+        transposed_dots_f(ATf.data(), m, d, zf.data(), avf.data());
+        for (int k = 0; k < m; ++k) av[k] = avf[k];
+      }
+      lam[0] = lam[1] = 0.0;
+      for (size_t i = 0; i < S.size(); ++i) lam[cls[i]] += c[i] * av[S[i]];
+      mn[0] = mn[1] = INFINITY;
+      arg[0] = arg[1] = -1;
+      for (int k = 0; k < m; ++k) {
+        const double v = av[k];
+        const int cl = k < nP ? 0 : 1;
+        if (v < mn[cl]) mn[cl] = v, arg[cl] = k;
+      }
+      gap = zz - (mn[0] + mn[1]);
+      if (exact || gap > 4.0 * tol * zz) break;
+      exact = true;  // near the stopping gap: FP64 scans from here on
     }
-    gap = zz - (mn[0] + mn[1]);
-    if (gap <= tol * zz) break;
+    if (exact && gap <= tol * zz) break;
     const int cl = (lam[0] - mn[0] >= lam[1] - mn[1]) ? 0 : 1;
     const int add = arg[cl];
     if (add < 0 || in[add]) break;
