@@ -441,3 +441,78 @@ def _ses_solve_certified(V, gamma, eps, max_iters, max_steps, eta, poll_every):
             break  # iteration budget exhausted inside the step
     return {"radius": ub, "center": center, "lower_bound": max(lb, L), "upper_bound": ub,
             "iters": total, "steps": steps, "L": L, "U": U}
+
+
+# ---------------------------------------------------------------------------
+# Core-set certificates for SES (beyond the paper, on the dual pair of Sec. 4.1
+# for points, gamma = 0): any weights mu on the simplex over a subset of the
+# points give phi(mu) = sum_i mu_i |v_i|^2 - |sum_i mu_i v_i|^2 <= OPT^2 (weak
+# duality of the minimum-enclosing-ball QP: a subset's weights are feasible
+# for the whole problem), and every centre c gives the enclosing radius
+# max_i |v_i - c| >= OPT. The subset is the K points farthest from a given
+# centre (the current mean of the MWU), the weights are maximised by
+# Frank-Wolfe steps with away steps on the subset, and the ball at their
+# barycentre c_mu = sum_i mu_i v_i is evaluated on every point.
+# ---------------------------------------------------------------------------
+CORESET_K_SES = 512
+
+
+def ses_coreset_pick(V, c, K):
+    """Indices of the K points (all, if fewer) farthest from c, by descending
+    distance (ties by index)."""
+    d2 = ((V - c) ** 2).sum(axis=1)
+    order = np.lexsort((np.arange(len(V)), -d2))
+    return np.sort(order[:min(K, len(V))])
+
+
+def meb_dual_fw(P, tol, max_iter=200_000):
+    """Weights mu on the simplex over the rows of P maximising phi(mu) by
+    Frank-Wolfe steps toward the farthest point and away steps from the
+    nearest point of the support (exact line searches: phi is a concave
+    quadratic along both), until the farthest point of P from c_mu lies
+    within (1 + tol) sqrt(phi). Returns (mu, c_mu, sqrt(phi), the farthest
+    distance)."""
+    m = len(P)
+    sq = (P * P).sum(axis=1)
+    mu = np.zeros(m)
+    c0 = P.mean(axis=0)
+    j0 = int(np.argmax(((P - c0) ** 2).sum(axis=1)))
+    mu[j0] = 1.0
+    c = P[j0].copy()
+    for _ in range(max_iter):
+        dist2 = ((P - c) ** 2).sum(axis=1)
+        phi = float(mu @ sq - c @ c)
+        j = int(np.argmax(dist2))
+        if dist2[j] <= (1.0 + tol) ** 2 * phi:
+            break
+        supp = np.nonzero(mu > 0.0)[0]
+        a = int(supp[np.argmin(dist2[supp])])
+        g_fw = dist2[j] - phi            # slope of phi toward e_j
+        g_aw = phi - dist2[a]            # slope of phi away from e_a
+        if g_fw >= g_aw or mu[a] >= 1.0:
+            s = min(1.0, g_fw / (2.0 * dist2[j]))
+            mu *= 1.0 - s
+            mu[j] += s
+            c = (1.0 - s) * c + s * P[j]
+        else:
+            smax = mu[a] / (1.0 - mu[a])
+            s = min(smax, g_aw / (2.0 * dist2[a])) if dist2[a] > 0.0 else smax
+            mu *= 1.0 + s
+            mu[a] -= s
+            if s >= smax:
+                mu[a] = 0.0
+            c = (1.0 + s) * c - s * P[a]
+    phi = max(float(mu @ sq - c @ c), 0.0)
+    far = math.sqrt(float(((P - c) ** 2).sum(axis=1).max()))
+    return mu, c, math.sqrt(phi), far
+
+
+def ses_coreset_bounds(V, c, K=CORESET_K_SES, tol=1e-4):
+    """Core-set bounds from centre c: (lb, ub, centre) with lb = sqrt(phi(mu))
+    for the weights of meb_dual_fw on the K points farthest from c (a lower
+    bound on OPT) and ub = max_i |v_i - c_mu| over every point, the radius of
+    an actual enclosing ball at c_mu (an upper bound)."""
+    idx = ses_coreset_pick(V, c, K)
+    mu, cm, lb, _ = meb_dual_fw(V[idx], tol)
+    ub = math.sqrt(float(((V - cm) ** 2).sum(axis=1).max()))
+    return lb, ub, cm
