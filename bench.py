@@ -610,6 +610,12 @@ def variants(dev, flush):
     out["ses_n1e6_d32_bf16"]["time_to_eps"] = {
         "seconds": time.perf_counter() - t0, "iters": rep["iters"], "radius": rep["value"],
         "lower_bound": rep["lower_bound"], "gap": rep["value"] / rep["lower_bound"] - 1, "status": rep["status"]}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, rep = api.ses_solve(pb, eps=1e-3, mode="coreset", max_iters=200_000, poll_every=256)
+    out["ses_n1e6_d32_bf16"]["time_to_eps"]["coreset"] = {
+        "seconds": time.perf_counter() - t0, "iters": rep["iters"], "radius": rep["value"],
+        "lower_bound": rep["lower_bound"], "gap": rep["value"] / rep["lower_bound"] - 1, "status": rep["status"]}
     V4b = torch.from_numpy(datagen.ses_gaussian(4 * N_POINTS, DIM, SEED)).to(dev).to(torch.bfloat16)
     D4 = float(api.bounds(_ffi.SES, V4b).item())
     msb, R = _back_to_back(_ffi.SES, V4b, D4, 0.01 / (3 * D4 / math.sqrt(2)))
@@ -1003,11 +1009,14 @@ def time_to_eps(pts):
     enclosing ball is within 1 + eps of a lower bound), then the same solve
     under the paper's practical rules of Sec. 5 (a stalled alpha-FTP read as
     affirmative), whose search range can close while its certificates stay
-    wide. Wall time of the whole solve, bounds pass and polls included."""
+    wide, and the CORESET mode (CERTIFIED plus core-set certificates: the dual
+    value of Frank-Wolfe weights on the points farthest from the running mean,
+    and the ball at their barycentre). Wall time of the whole solve, bounds
+    pass and polls included."""
     import torch
     from paper_2405_09157_gb300 import api
     out = {}
-    for mode, budget in (("certified", 200_000), ("practical", 200_000)):
+    for mode, budget in (("certified", 200_000), ("practical", 200_000), ("coreset", 200_000)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, rep = api.ses_solve(pts, eps=1e-3, mode=mode, max_iters=budget, poll_every=256)
@@ -1021,6 +1030,7 @@ def time_to_eps(pts):
     res["eps"] = 1e-3
     res["mode"] = "certified (eta starts at 1)"
     res["practical_rules"] = out["practical"]
+    res["coreset"] = out["coreset"]
     res["note"] = ("gap = radius of the returned ball / certified lower bound - 1 (<= eps: done); "
                    "status 5 = budget spent")
     return res

@@ -62,7 +62,7 @@ typedef enum pdscp_status {
 #define PDSCP_MODE_PRACTICAL 0  /* Sec. 5 rules inside each alpha-FTP */
 #define PDSCP_MODE_THEORY 1     /* T_i iterations of Theorem 2/3 per FTP */
 #define PDSCP_MODE_CERTIFIED 2  /* proven conclusions only; ends on the certificates (see ses_solve) */
-#define PDSCP_MODE_CORESET 3    /* SVM: CERTIFIED plus core-set certificates (see svm_solve); SES: CERTIFIED */
+#define PDSCP_MODE_CORESET 3    /* CERTIFIED plus core-set certificates (see ses_solve, svm_solve) */
 
 /* Largest supported dimension d. */
 #define PDSCP_MAX_D 1024
@@ -170,7 +170,9 @@ pdscp_status pdscp_polytope_distance(const double* P_host, int32_t nP, const dou
  * per-CTA partial sums and a completion counter; it must be zeroed once before
  * first use (mwu_state_init and the solves do this) and may be reused by
  * consecutive calls on one stream. Calls that share a workspace must not
- * overlap on the GPU.
+ * overlap on the GPU. The size includes the region of the core-set
+ * certificates (PDSCP_MODE_CORESET of ses_solve / svm_solve); the other
+ * calls need only its first part and accept the larger size.
  */
 pdscp_status pdscp_workspace_size(int32_t problem, int64_t n, int32_t d, size_t* bytes_host);
 
@@ -315,6 +317,19 @@ pdscp_status mwu_state_read(int32_t problem, int32_t d, const void* state_dev,
  * previous such poll, after which eta is halved (not below 1/64, where the
  * test stops); the solve ends only on the certificates (or the budget) and
  * report.lower_bound is max(lb, L). eta 0 means 1 in this mode.
+ * PDSCP_MODE_CORESET (points, radii_dev NULL; with radii it is CERTIFIED) is
+ * CERTIFIED plus core-set certificates (not in the paper; built on the dual
+ * pair of Sec. 4.1): at the polls where the search's iteration count first
+ * reaches 256, 512, 1024, ..., the points farthest from the running mean
+ * (between 512 and 1024, by a threshold found on the device) form a core set;
+ * Frank-Wolfe steps with away steps on the host give weights mu on it whose
+ * dual value sqrt(sum_i mu_i |v_i|^2 - |sum_i mu_i v_i|^2) is a lower bound on
+ * OPT (weak duality), and the radius of the ball at sum_i mu_i v_i over every
+ * point (one pass on the device) an upper bound; up to four rounds add the
+ * points farthest from each new centre. The bounds join the FTP's own; the
+ * returned centre is the one of the smallest ball found. The workspace then
+ * also holds the n distances and the core set's rows (pdscp_workspace_size
+ * counts them).
  */
 pdscp_status ses_solve(const void* pts_dev, int32_t dtype, const float* radii_dev,
                        int64_t n, int32_t d, const pdscp_options* opts,
@@ -340,7 +355,7 @@ pdscp_status ses_solve(const void* pts_dev, int32_t dtype, const float* radii_de
  * the core set of each new direction. The bounds join the FTP's own; the
  * returned direction is the one of the best margin. The workspace then also
  * holds the projections of the n points and the core set's rows (see
- * pdscp_workspace_size, which counts them for SVM).
+ * pdscp_workspace_size, which counts them).
  */
 pdscp_status svm_solve(const void* X_dev, int32_t dtype, const int8_t* labels_dev,
                        int64_t n, int32_t d, const pdscp_options* opts,

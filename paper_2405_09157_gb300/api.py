@@ -464,9 +464,12 @@ def ses_solve(pts, radii=None, eps=1e-3, mode="practical", max_iters=1_000_000, 
     stay wide), "theory" (T_i iterations of Theorem 2 per FTP) or "certified"
     (only proven conclusions; ends when the ball's radius is within 1 + eps of
     a certified lower bound; eta defaults to 1 and is halved when an FTP's own
-    certificate gap stops shrinking). The report holds the radius of an actual
-    enclosing ball ("value" = "upper_bound"), the best lower bound, the search
-    range, iterations and status (5 = budget spent, with valid bounds)."""
+    certificate gap stops shrinking); "coreset" (points only) is "certified"
+    plus core-set certificates: the dual value of Frank-Wolfe weights on the
+    points farthest from the running mean bounds the radius from below, the
+    ball at their barycentre from above. The report holds the radius of an
+    actual enclosing ball ("value" = "upper_bound"), the best lower bound, the
+    search range, iterations and status (5 = budget spent, with valid bounds)."""
     n, d, dt = _points(pts)
     _rows(radii, n, torch.float32, "radii")
     ws = workspace(SES, n, d, pts.device) if ws is None else ws

@@ -207,7 +207,7 @@ pdscp_status pdscp_workspace_size(int32_t problem, int64_t n, int32_t d, size_t*
   if (d < 1 || d > PDSCP_MAX_D) return fail(PDSCP_ERR_NOT_IMPLEMENTED, "d=%d outside [1, %d]", d, PDSCP_MAX_D);
   if (n < 1) return fail(PDSCP_ERR_INVALID_ARG, "n must be >= 1");
   const size_t base = layout(problem, d).total;
-  *bytes = problem == PDSCP_SVM ? round256(base) + coreset_bytes(n, d) : base;
+  *bytes = round256(base) + coreset_bytes(n, d);  // (the core-set checks' region after the solve's)
   return PDSCP_OK;
 }
 
@@ -620,10 +620,11 @@ double own_gap(int problem, const StateHdr& h) {
   return h.best_f > 0.0 ? h.ub_best / h.best_f - 1.0 : INFINITY;
 }
 
-// Core-set certificates of the certified SVM search (PDSCP_MODE_CORESET).
+// Core-set certificates of the certified searches (PDSCP_MODE_CORESET).
 // next: the search's iteration count of the next check (256, then doubling,
-// kept across FTPs); base: the search's count when this FTP began; lb, ub,
-// w: the best bounds this FTP's checks found (lb with its unit direction).
+// kept across FTPs); base: the search's count when this FTP began; lb, ub:
+// the best bounds this FTP's checks found; w: SVM, the unit direction of lb;
+// SES, the centre of the ball of radius ub.
 struct CoresetHook {
   int64_t next = kCoresetFirst, base = 0;
   double lb = 0.0, ub = INFINITY;
@@ -687,7 +688,26 @@ pdscp_status run_ftp(int problem, const void* pts, int dtype, const float* radii
       stopped = true;
       break;
     }
-    if (cs && cs->base + h.t >= cs->next) {
+    if (cs && problem == PDSCP_SES && cs->base + h.t >= cs->next) {
+      // SES: from the current mean
+      float* tmp = reinterpret_cast<float*>(cs->ws);
+      std::vector<float> cf(d);
+      st = mwu_state_read(problem, d, state, tmp, nullptr, (pdscp_stream)s);
+      if (st != PDSCP_OK) return st;
+      e = cudaMemcpyAsync(cf.data(), tmp, (size_t)d * sizeof(float), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_fail(e, "core-set centre read");
+      std::vector<double> c0(cf.begin(), cf.end()), cc;
+      double lbc = 0.0, ubc = INFINITY;
+      st = ses_coreset_check(pts, dtype, n, d, c0.data(), cert.eps, cs->ws, s, &lbc, &ubc, cc);
+      if (st != PDSCP_OK) return st;
+      cs->lb = std::max(cs->lb, lbc);
+      if (ubc < cs->ub) {
+        cs->ub = ubc;
+        cs->w = cc;
+      }
+      cs->next *= 2;
+    } else if (cs && cs->base + h.t >= cs->next) {
       // the check starts from the FTP's best direction so far: a core-set
       // direction of this FTP, else the device's best, else the mean
       std::vector<double> w0(d);
@@ -716,7 +736,10 @@ pdscp_status run_ftp(int problem, const void* pts, int dtype, const float* radii
       cs->next *= 2;
     }
     StateHdr hc = h;  // the core-set bounds join the FTP's own
-    if (cs) {
+    if (cs && problem == PDSCP_SES) {
+      hc.lb_best = std::max(hc.lb_best, cs->lb);
+      hc.best_f = std::min(hc.best_f, cs->ub);
+    } else if (cs) {
       hc.best_f = std::max(hc.best_f, cs->lb);
       hc.ub_best = std::min(hc.ub_best, cs->ub);
     }
@@ -764,7 +787,12 @@ pdscp_status ses_solve(const void* pts, int32_t dtype, const float* radii, int64
   if (!ws || !center || !rep) return fail(PDSCP_ERR_INVALID_ARG, "null workspace/center/report pointer");
   if (!aligned(ws, 256)) return fail(PDSCP_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
   const Layout L = layout(PDSCP_SES, d);
-  if (ws_bytes < L.total) return fail(PDSCP_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws_bytes, L.total);
+  // core-set certificates for points (with radii the mode is CERTIFIED)
+  const bool use_cs = o->mode == PDSCP_MODE_CORESET && !radii;
+  const size_t need = use_cs ? round256(L.total) + coreset_bytes(n, d) : L.total;
+  if (ws_bytes < need) return fail(PDSCP_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws_bytes, need);
+  CoresetHook cs;
+  cs.ws = reinterpret_cast<char*>(ws) + round256(L.total);
   cudaStream_t s = (cudaStream_t)stream;
   memset(rep, 0, sizeof(*rep));
   double* Ddev = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + L.dval);
@@ -816,8 +844,11 @@ pdscp_status ses_solve(const void* pts, int32_t dtype, const float* radii, int64
     const double eta = eta_c;
     FtpResult r;
     const CertCheck c{true, std::max(lb, Lo), ub, eps, eta};
+    cs.base = total;
+    cs.lb = 0.0;
+    cs.ub = INFINITY;
     if ((st = run_ftp(PDSCP_SES, pts, dtype, radii, nullptr, n, d, alpha, eta / rho, 0.0, rules, o, o->max_iters - total,
-                      ws, ws_bytes, s, &r, c)) != PDSCP_OK)
+                      ws, ws_bytes, s, &r, c, use_cs ? &cs : nullptr)) != PDSCP_OK)
       return st;
     total += r.iters;
     if (r.hdr.best_f < ub) {
@@ -827,6 +858,15 @@ pdscp_status ses_solve(const void* pts, int32_t dtype, const float* radii, int64
       have_center = true;
     }
     if (r.hdr.lb_best > lb) lb = r.hdr.lb_best;
+    if (cs.ub < ub) {  // a core-set centre gives the smallest enclosing ball
+      ub = cs.ub;
+      std::vector<float> cf(cs.w.begin(), cs.w.end());
+      e = cudaMemcpyAsync(center, cf.data(), (size_t)d * sizeof(float), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_fail(e, "core-set centre write");
+      have_center = true;
+    }
+    if (cs.lb > lb) lb = cs.lb;
     const int oc = r.hdr.stopped ? r.hdr.outcome : PDSCP_OUT_RUNNING;
     if (oc == PDSCP_OUT_SEPARATED) Lo = std::max(Lo, alpha);
     if (r.stuck) eta_c *= 0.5;  // smaller steps resolve alpha closer to OPT

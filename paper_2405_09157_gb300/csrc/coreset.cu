@@ -429,6 +429,93 @@ int pd_active_set(const double* P, int nP, const double* Q, int nQ, int d, doubl
   return it;
 }
 
+// Minimum enclosing ball of the rows of P (m x d, FP64, translated near the
+// origin by the caller) through its dual: weights mu on the simplex
+// maximising phi(mu) = sum_i mu_i |p_i|^2 - |c_mu|^2, c_mu = sum_i mu_i p_i
+// (phi(mu) <= OPT^2 for any mu: weak duality), by Frank-Wolfe steps toward
+// the farthest row and away steps from the nearest row of the support, each
+// with its exact line search (phi is a concave quadratic along both), until
+// the farthest row lies within (1 + tol) sqrt(phi) of c_mu. Returns
+// sqrt(phi); c (d): c_mu; *far: the farthest row's distance from it.
+double meb_dual_fw(const double* P, int m, int d, double tol, int max_iter, std::vector<double>& mu,
+                   std::vector<double>& c, double* far) {
+  std::vector<double> PT((size_t)d * m), sq(m, 0.0), pc(m), d2(m);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < d; ++j) {
+      const double v = P[(size_t)i * d + j];
+      PT[(size_t)j * m + i] = v;
+      sq[i] += v * v;
+    }
+  mu.assign(m, 0.0);
+  c.assign(d, 0.0);
+  // start: the row farthest from the rows' mean, with all the weight
+  std::vector<double> mean(d, 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < d; ++j) mean[j] += P[(size_t)i * d + j] / m;
+  int j0 = 0;
+  double best = -1.0;
+  for (int i = 0; i < m; ++i) {
+    double t = 0.0;
+    for (int j = 0; j < d; ++j) t += (P[(size_t)i * d + j] - mean[j]) * (P[(size_t)i * d + j] - mean[j]);
+    if (t > best) best = t, j0 = i;
+  }
+  mu[j0] = 1.0;
+  for (int j = 0; j < d; ++j) c[j] = P[(size_t)j0 * d + j];
+  double phi = 0.0;
+  for (int it = 0; it < max_iter; ++it) {
+    double cc = 0.0, msq = 0.0;
+    for (int j = 0; j < d; ++j) cc += c[j] * c[j];
+    std::fill(pc.begin(), pc.end(), 0.0);
+    for (int j = 0; j < d; ++j) {
+      const double cj = c[j];
+      const double* x = PT.data() + (size_t)j * m;
+      for (int i = 0; i < m; ++i) pc[i] += x[i] * cj;
+    }
+    int jf = 0, ja = -1;
+    for (int i = 0; i < m; ++i) {
+      d2[i] = std::max(sq[i] - 2.0 * pc[i] + cc, 0.0);
+      msq += mu[i] * sq[i];
+      if (d2[i] > d2[jf]) jf = i;
+      if (mu[i] > 0.0 && (ja < 0 || d2[i] < d2[ja])) ja = i;
+    }
+    phi = std::max(msq - cc, 0.0);
+    if (d2[jf] <= (1.0 + tol) * (1.0 + tol) * phi) break;
+    const double gfw = d2[jf] - phi, gaw = phi - d2[ja];
+    if (gfw >= gaw || mu[ja] >= 1.0) {
+      const double st = std::min(1.0, gfw / (2.0 * d2[jf]));
+      for (int i = 0; i < m; ++i) mu[i] *= 1.0 - st;
+      mu[jf] += st;
+      for (int j = 0; j < d; ++j) c[j] = (1.0 - st) * c[j] + st * P[(size_t)jf * d + j];
+    } else {
+      const double smax = mu[ja] / (1.0 - mu[ja]);
+      const double st = d2[ja] > 0.0 ? std::min(smax, gaw / (2.0 * d2[ja])) : smax;
+      for (int i = 0; i < m; ++i) mu[i] *= 1.0 + st;
+      mu[ja] -= st;
+      if (st >= smax) mu[ja] = 0.0;
+      for (int j = 0; j < d; ++j) c[j] = (1.0 + st) * c[j] - st * P[(size_t)ja * d + j];
+    }
+  }
+  // the final weights renormalised onto the simplex, then c_mu, phi and the
+  // farthest distance recomputed from them directly
+  double wsum = 0.0;
+  for (int i = 0; i < m; ++i) wsum += mu[i];
+  for (int i = 0; i < m; ++i) mu[i] /= wsum;
+  std::fill(c.begin(), c.end(), 0.0);
+  for (int i = 0; i < m; ++i)
+    if (mu[i] > 0.0)
+      for (int j = 0; j < d; ++j) c[j] += mu[i] * P[(size_t)i * d + j];
+  double msq = 0.0, cc = 0.0, fmax = 0.0;
+  for (int j = 0; j < d; ++j) cc += c[j] * c[j];
+  for (int i = 0; i < m; ++i) {
+    msq += mu[i] * sq[i];
+    double t = 0.0;
+    for (int j = 0; j < d; ++j) t += (P[(size_t)i * d + j] - c[j]) * (P[(size_t)i * d + j] - c[j]);
+    fmax = std::max(fmax, t);
+  }
+  if (far) *far = std::sqrt(fmax);
+  return std::sqrt(std::max(msq - cc, 0.0));
+}
+
 }  // namespace pdscp
 
 // ---------------------------------------------------------------------------
@@ -482,12 +569,40 @@ __global__ void __launch_bounds__(256) svm_project_kernel(const T* X, const int8
   }
 }
 
-// cnt[c] = number of rows of class c (0: P, 1: Q) with s <= th[c]
+// s_i = -|x_i - c|^2 for every row (SES core sets: the smallest s are the
+// farthest points), one warp per row; mm[0], mm[1] = images of min s, max s
+template <typename T>
+__global__ void __launch_bounds__(256) ses_dist_kernel(const T* X, int64_t n, int d, const float* c, float* s,
+                                                       unsigned int* mm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float lo = INFINITY, hi = -INFINITY;
+  for (int64_t i = wid; i < n; i += nw) {
+    const T* row = X + i * d;
+    float acc = 0.f;
+    for (int j = lane; j < d; j += 32) {
+      const float t = elem_to_float<T>(row + j) - __ldg(c + j);
+      acc = fmaf(t, t, acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) s[i] = -acc;
+    lo = fminf(lo, -acc);
+    hi = fmaxf(hi, -acc);
+  }
+  if (lane == 0 && lo <= hi) {
+    atomicMin(mm, f2o(lo));
+    atomicMax(mm + 1, f2o(hi));
+  }
+}
+
+// cnt[c] = number of rows of class c (0: P, 1: Q; every row is of class 0
+// when y is null) with s <= th[c]
 __global__ void __launch_bounds__(256) count_le_kernel(const float* s, const int8_t* y, int64_t n, float thP,
                                                        float thQ, unsigned long long* cnt) {
   unsigned int a = 0, b = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const bool pos = __ldg(y + i) > 0;
+    const bool pos = y ? __ldg(y + i) > 0 : true;
     const float v = s[i];
     if (pos) a += v <= thP ? 1u : 0u;
     else b += v <= thQ ? 1u : 0u;
@@ -508,7 +623,7 @@ __global__ void __launch_bounds__(256) count_le_kernel(const float* s, const int
 __global__ void __launch_bounds__(256) select_le_kernel(const float* s, const int8_t* y, int64_t n, float thP,
                                                         float thQ, int* idx, int cap, unsigned int* pos) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int c = __ldg(y + i) > 0 ? 0 : 1;
+    const int c = (y ? __ldg(y + i) > 0 : true) ? 0 : 1;
     if (s[i] <= (c == 0 ? thP : thQ)) {
       const unsigned int k = atomicAdd(pos + c, 1u);
       if (k < (unsigned int)cap) idx[(size_t)c * cap + k] = (int)i;
@@ -555,6 +670,17 @@ cudaError_t launch_project(const void* X, const int8_t* y, int64_t n, int d, con
   if (e != cudaSuccess) return e;
   const int grid = device_sm_count() * 8;
   svm_project_kernel<T><<<grid, 256, 0, st>>>(reinterpret_cast<const T*>(X), y, n, d, w, s, mm);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_ses_dist(const void* X, int64_t n, int d, const float* c, float* s, unsigned int* mm,
+                            cudaStream_t st) {
+  const unsigned int init[2] = {0xffffffffu, 0u};
+  cudaError_t e = cudaMemcpyAsync(mm, init, sizeof(init), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  const int grid = device_sm_count() * 8;
+  ses_dist_kernel<T><<<grid, 256, 0, st>>>(reinterpret_cast<const T*>(X), n, d, c, s, mm);
   return cudaGetLastError();
 }
 
@@ -717,6 +843,130 @@ pdscp_status svm_coreset_check(const void* X, int dtype, const int8_t* y, int64_
       *lb = m;
       const double inv = 1.0 / std::sqrt(zz);
       for (int j = 0; j < d; ++j) w_lb[j] = z[j] * inv;
+    }
+    if (*ub <= (1.0 + eps) * *lb) break;
+  }
+  return PDSCP_OK;
+}
+
+pdscp_status ses_coreset_check(const void* X, int dtype, int64_t n, int d, const double* c0, double eps, void* ws,
+                               cudaStream_t st, double* lb, double* ub, std::vector<double>& c_ub) {
+  const CsLayout L = cs_layout(n, d);
+  char* base = reinterpret_cast<char*>(ws);
+  float* s = reinterpret_cast<float*>(base + L.s);
+  unsigned int* mm = reinterpret_cast<unsigned int*>(base + L.mm);
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(base + L.cnt);
+  unsigned int* pos = reinterpret_cast<unsigned int*>(base + L.pos);
+  int* sel = reinterpret_cast<int*>(base + L.sel);
+  int* gidx = reinterpret_cast<int*>(base + L.gidx);
+  float* rows = reinterpret_cast<float*>(base + L.rows);
+  float* cdev = reinterpret_cast<float*>(base + L.w);
+  const int cap = 2 * kCoresetK;
+  const int kmax = 2 * kCoresetMaxPerClass;  // the rows region holds both classes' caps of the SVM checks
+  const int grid = device_sm_count() * 4;
+  std::vector<float> cf(d);
+  *lb = 0.0;
+  *ub = INFINITY;
+  c_ub.assign(c0, c0 + d);
+  auto fail_cuda = [](cudaError_t, const char* what) { return report_error(PDSCP_ERR_CUDA, what); };
+  // s_i = -|x_i - c|^2 for every point; returns min s and max s
+  auto dist_pass = [&](const std::vector<double>& c, float* smin, float* smax) -> cudaError_t {
+    for (int j = 0; j < d; ++j) cf[j] = (float)c[j];
+    cudaError_t e = cudaMemcpyAsync(cdev, cf.data(), (size_t)d * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = dtype == PDSCP_F32 ? launch_ses_dist<float>(X, n, d, cdev, s, mm, st)
+                             : launch_ses_dist<__nv_bfloat16>(X, n, d, cdev, s, mm, st);
+    unsigned int mmh[2];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mmh, mm, sizeof(mmh), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) {
+      *smin = o2f(mmh[0]);
+      *smax = o2f(mmh[1]);
+    }
+    return e;
+  };
+  std::vector<double> c(c0, c0 + d);
+  float smin = 0.f, smax = 0.f;
+  cudaError_t e = dist_pass(c, &smin, &smax);
+  if (e != cudaSuccess) return fail_cuda(e, "ses core set: distances");
+  *ub = std::sqrt(std::max(-(double)smin, 0.0));  // the ball at c0 itself
+  std::vector<int> core;  // the core set: sorted row indices
+  std::vector<float> rowsh;
+  std::vector<double> Pd, mu, cm;
+  for (int round = 0; round < kCoresetRounds; ++round) {
+    // a threshold on s taking between K and 2K points (the farthest from c),
+    // by bisection over [min s, max s], or every point when n <= K
+    auto count = [&](float th, unsigned long long* got) -> cudaError_t {
+      const unsigned long long z2[2] = {0ull, 0ull};
+      cudaError_t e2 = cudaMemcpyAsync(cnt, z2, sizeof(z2), cudaMemcpyHostToDevice, st);
+      if (e2 == cudaSuccess) count_le_kernel<<<grid, 256, 0, st>>>(s, nullptr, n, th, th, cnt);
+      if (e2 == cudaSuccess) e2 = cudaGetLastError();
+      if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(got, cnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+      if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+      return e2;
+    };
+    float lo = smin, hi = smax;
+    unsigned long long got[2];
+    if ((e = count(lo, got)) != cudaSuccess) return fail_cuda(e, "ses core set: count");
+    bool need = got[0] < (unsigned long long)kCoresetK;
+    if (!need) hi = lo;
+    for (int itb = 0; itb < 40 && need; ++itb) {
+      const float mid = lo + 0.5f * (hi - lo);
+      if (!(mid > lo && mid < hi)) break;  // no float left between lo and hi
+      if ((e = count(mid, got)) != cudaSuccess) return fail_cuda(e, "ses core set: count");
+      if (got[0] < (unsigned long long)kCoresetK) {
+        lo = mid;
+      } else {
+        hi = mid;
+        if (got[0] <= (unsigned long long)cap) need = false;
+      }
+    }
+    unsigned int posh[2] = {0u, 0u};
+    e = cudaMemcpyAsync(pos, posh, sizeof(posh), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) select_le_kernel<<<grid, 256, 0, st>>>(s, nullptr, n, hi, hi, sel, cap, pos);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(posh, pos, sizeof(posh), cudaMemcpyDeviceToHost, st);
+    std::vector<int> selh(cap);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(selh.data(), sel, selh.size() * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail_cuda(e, "ses core set: select");
+    // merged into the core set, sorted (independent of the atomic appends' order)
+    std::vector<int> picked(selh.begin(), selh.begin() + std::min<unsigned int>(posh[0], cap));
+    std::sort(picked.begin(), picked.end());
+    std::vector<int> merged;
+    std::set_union(core.begin(), core.end(), picked.begin(), picked.end(), std::back_inserter(merged));
+    if ((int)merged.size() > kmax) merged.resize(kmax);
+    core.swap(merged);
+    const int k = (int)core.size();
+    if (k == 0) break;
+    rowsh.resize((size_t)k * d);
+    e = cudaMemcpyAsync(gidx, core.data(), (size_t)k * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+      if (dtype == PDSCP_F32)
+        gather_rows_kernel<float><<<grid, 256, 0, st>>>(reinterpret_cast<const float*>(X), gidx, k, d, rows);
+      else
+        gather_rows_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(X), gidx, k,
+                                                                d, rows);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rowsh.data(), rows, rowsh.size() * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail_cuda(e, "ses core set: gather");
+    // the dual on the core set, translated by c0 (the ball problem is
+    // translation invariant; near the origin phi loses no digits)
+    Pd.resize((size_t)k * d);
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < d; ++j) Pd[(size_t)i * d + j] = (double)rowsh[(size_t)i * d + j] - c0[j];
+    double far = 0.0;
+    const double lbr = meb_dual_fw(Pd.data(), k, d, eps / 10.0, 200000, mu, cm, &far);
+    *lb = std::max(*lb, lbr);
+    for (int j = 0; j < d; ++j) c[j] = cm[j] + c0[j];
+    // the ball at c_mu over every point: an upper bound (and the distances
+    // the next round picks from)
+    if ((e = dist_pass(c, &smin, &smax)) != cudaSuccess) return fail_cuda(e, "ses core set: distances");
+    const double r = std::sqrt(std::max(-(double)smin, 0.0));
+    if (r < *ub) {
+      *ub = r;
+      c_ub = c;
     }
     if (*ub <= (1.0 + eps) * *lb) break;
   }

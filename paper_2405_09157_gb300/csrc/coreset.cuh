@@ -34,6 +34,14 @@ size_t coreset_bytes(int64_t n, int d);
 // Sets *lb (a margin of some direction over all points), *ub (a core-set
 // distance) and w_lb (that direction, unit norm). ws: coreset_bytes(n, d)
 // bytes of device memory, 256-byte aligned.
+// The SES counterpart (points, no radii): the core set is the K farthest
+// points from centre c0 (host, d doubles), then from each new centre; *lb =
+// sqrt(phi) of the Frank-Wolfe dual weights on the core set (weak duality of
+// the enclosing-ball QP), *ub the radius over every point of the ball at the
+// best centre found, c_ub that centre. Same workspace as the SVM check.
+pdscp_status ses_coreset_check(const void* X, int dtype, int64_t n, int d, const double* c0, double eps, void* ws,
+                               cudaStream_t s, double* lb, double* ub, std::vector<double>& c_ub);
+
 pdscp_status svm_coreset_check(const void* X, int dtype, const int8_t* y, int64_t n, int d, const double* w0,
                                double eps, void* ws, cudaStream_t s, double* lb, double* ub,
                                std::vector<double>& w_lb);

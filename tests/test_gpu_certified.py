@@ -201,3 +201,51 @@ def test_svm_coreset_full_size():
     w, rep = api.svm_solve(_cuda(X32), _cuda(y), eps=1e-3, mode="coreset", max_iters=200_000, poll_every=256)
     assert rep["status"] == 0 and rep["upper_bound"] <= (1 + 1e-3) * rep["lower_bound"]
     assert math.isclose(_margin64(X32.astype(np.float64), y, w), rep["value"], rel_tol=1e-4)
+
+
+# ---------------------------------------------------------------- SES core sets
+@pytest.mark.parametrize("n,seed", [(3000, 0), (20_000, 1), (2, 2), (700, 3)])
+def test_ses_coreset_brackets_welzl_in_the_plane(n, seed):
+    """SES core-set mode on points in the plane against Welzl's exact radius:
+    the certificates bracket it and close within eps (the returned centre's
+    ball encloses every point)."""
+    from oracle import exact
+    V32 = datagen.ses_uniform(n, 2, seed=seed)
+    V = V32.astype(np.float64)
+    opt = exact.mec_2d(V)[1]
+    eps = 1e-3
+    c, rep = api.ses_solve(torch.from_numpy(V32).cuda(), eps=eps, mode="coreset", max_iters=100_000)
+    assert rep["status"] == 0, rep
+    assert rep["lower_bound"] <= opt * (1 + FP) and rep["upper_bound"] >= opt * (1 - FP), (rep, opt)
+    assert rep["upper_bound"] <= (1 + eps) * rep["lower_bound"]
+    far = float(np.linalg.norm(V - c.cpu().numpy().astype(np.float64), axis=1).max())
+    assert far <= rep["upper_bound"] * (1 + FP), (far, rep["upper_bound"])
+
+
+def test_ses_coreset_full_size_closes_early():
+    """The benchmark workload (n = 1e6, d = 32, N(0, I)): the core-set mode
+    closes eps = 1e-3 within the first checks, its centre's ball encloses
+    every point, and its interval and the plain CERTIFIED mode's overlap."""
+    V32 = datagen.ses_gaussian(1_000_000, 32, seed=0)
+    pts = torch.from_numpy(V32).cuda()
+    eps = 1e-3
+    c, rep = api.ses_solve(pts, eps=eps, mode="coreset", max_iters=200_000)
+    assert rep["status"] == 0, rep
+    assert rep["iters"] <= 1024, rep
+    assert rep["upper_bound"] <= (1 + eps) * rep["lower_bound"]
+    V = V32.astype(np.float64)
+    far = float(np.linalg.norm(V - c.cpu().numpy().astype(np.float64), axis=1).max())
+    assert far <= rep["upper_bound"] * (1 + FP)
+    _, rep2 = api.ses_solve(pts, eps=eps, mode="certified", max_iters=200_000)
+    assert rep["lower_bound"] <= rep2["upper_bound"] * (1 + FP) and rep2["lower_bound"] <= rep["upper_bound"] * (1 + FP)
+
+
+def test_ses_coreset_with_radii_is_certified():
+    """With radii the core-set mode runs as CERTIFIED: same report."""
+    V32 = datagen.ses_uniform(500, 3, seed=4)
+    g = np.random.default_rng(4).random(500).astype(np.float32) * 0.05
+    pts = torch.from_numpy(V32).cuda()
+    rad = torch.from_numpy(g).cuda()
+    _, a = api.ses_solve(pts, radii=rad, eps=1e-2, mode="coreset", max_iters=50_000)
+    _, b = api.ses_solve(pts, radii=rad, eps=1e-2, mode="certified", max_iters=50_000)
+    assert a["iters"] == b["iters"] and a["upper_bound"] == b["upper_bound"] and a["lower_bound"] == b["lower_bound"]
