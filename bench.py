@@ -1032,7 +1032,8 @@ def time_to_eps(pts):
     res["practical_rules"] = out["practical"]
     res["coreset"] = out["coreset"]
     res["note"] = ("gap = radius of the returned ball / certified lower bound - 1 (<= eps: done); "
-                   "status 5 = budget spent")
+                   "status 5 = budget spent; the top-level figures are the MWU-only certified search, "
+                   "'coreset' the same search with core-set certificates (the fastest certified solve)")
     return res
 
 

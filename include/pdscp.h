@@ -165,6 +165,26 @@ pdscp_status pdscp_polytope_distance(const double* P_host, int32_t nP, const dou
                                      double* gamma_host, double* dist_host);
 
 /*
+ * Dual bound of the minimum enclosing ball of a small point set on the host
+ * (the solver of the SES core-set certificates, ses_solve's
+ * PDSCP_MODE_CORESET): weights mu on the simplex over the m rows of P_host
+ * (m x d row-major doubles, caller-owned) maximising phi(mu) =
+ * sum_i mu_i |p_i|^2 - |sum_i mu_i p_i|^2 (Sec. 4.1's dual pair for points:
+ * phi(mu) <= OPT^2 for any such mu) by Frank-Wolfe steps toward the farthest
+ * row and away steps from the nearest row of the support, each with its exact
+ * line search, until the farthest row lies within (1 + tol) sqrt(phi) of the
+ * barycentre c = sum_i mu_i p_i, or max_iter steps. Writes mu_host (m),
+ * center_host (d) = c, *lb_host = sqrt(phi(mu)) (a lower bound on the ball's
+ * radius whatever the convergence) and *far_host = max_i |p_i - c| (the
+ * radius of an enclosing ball, an upper bound). Best conditioned with the
+ * rows near the origin (the ball is translation invariant). Synchronous,
+ * host only. PDSCP_ERR_INVALID_ARG for null pointers, m < 1, d < 1, tol < 0
+ * or max_iter < 1.
+ */
+pdscp_status pdscp_meb_dual(const double* P_host, int32_t m, int32_t d, double tol, int32_t max_iter,
+                            double* mu_host, double* center_host, double* lb_host, double* far_host);
+
+/*
  * Bytes of device workspace needed by pdscp_bounds / mwu_step / the solves for
  * a problem of this kind and size on the current device. The workspace holds
  * per-CTA partial sums and a completion counter; it must be zeroed once before

@@ -51,6 +51,7 @@ assert ctypes.sizeof(StepOut) == 72
 SIGNATURES = {
     "pdscp_version": (c_i32, []),
     "pdscp_polytope_distance": (c_i32, [c_vp, c_i32, c_vp, c_i32, c_i32, c_dbl, c_i32, c_vp, c_vp, c_vp]),
+    "pdscp_meb_dual": (c_i32, [c_vp, c_i32, c_i32, c_dbl, c_i32, c_vp, c_vp, c_vp, c_vp]),
     "pdscp_last_error": (ctypes.c_char_p, []),
     "pdscp_workspace_size": (c_i32, [c_i32, c_i64, c_i32, ctypes.POINTER(c_sz)]),
     "pdscp_state_size": (c_i32, [c_i32, c_i32, ctypes.POINTER(c_sz)]),

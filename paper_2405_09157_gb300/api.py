@@ -529,6 +529,25 @@ def polytope_distance(P, Q, tol=1e-9, max_iter=None):
     return dist.value, mu[:nP], ga[:nQ]
 
 
+def meb_dual(P, tol=1e-9, max_iter=200_000):
+    """Dual bound of the minimum enclosing ball of a small point set (the host
+    solver of the SES core-set certificates): P (m x d) array-like, taken as
+    float64. Returns (lb, far, mu, centre): lb = sqrt(phi(mu)) <= OPT <= far,
+    the radius of the ball at the centre (the weights' barycentre)."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    if P.ndim != 2:
+        raise ValueError("P must be 2-D")
+    m, d = P.shape
+    mu = np.zeros(max(m, 1))
+    c = np.zeros(max(d, 1))
+    lb = ctypes.c_double(0.0)
+    far = ctypes.c_double(0.0)
+    st = load().pdscp_meb_dual(P.ctypes.data, m, d, float(tol), int(max_iter), mu.ctypes.data, c.ctypes.data,
+                               ctypes.byref(lb), ctypes.byref(far))
+    check(st, "pdscp_meb_dual")
+    return lb.value, far.value, mu[:m], c[:d]
+
+
 # ------------------------------------------------------------------ batched SES
 def pack_instances(arrays, device="cuda", dtype=torch.float32):
     """Pack (n_i, d_i) arrays into one device buffer of dtype (torch.float32 or

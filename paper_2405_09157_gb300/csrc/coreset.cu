@@ -977,6 +977,18 @@ pdscp_status ses_coreset_check(const void* X, int dtype, int64_t n, int d, const
 
 using namespace pdscp;
 
+extern "C" pdscp_status pdscp_meb_dual(const double* P, int32_t m, int32_t d, double tol, int32_t max_iter,
+                                       double* mu, double* center, double* lb, double* far) {
+  if (!P || !mu || !center || !lb || !far) return report_error(PDSCP_ERR_INVALID_ARG, "pdscp_meb_dual: null pointer");
+  if (m < 1 || d < 1) return report_error(PDSCP_ERR_INVALID_ARG, "pdscp_meb_dual: m < 1 or d < 1");
+  if (!(tol >= 0.0) || max_iter < 1) return report_error(PDSCP_ERR_INVALID_ARG, "pdscp_meb_dual: tol < 0 or max_iter < 1");
+  std::vector<double> w, c;
+  *lb = meb_dual_fw(P, m, d, tol, max_iter, w, c, far);
+  std::copy(w.begin(), w.end(), mu);
+  std::copy(c.begin(), c.end(), center);
+  return PDSCP_OK;
+}
+
 extern "C" pdscp_status pdscp_polytope_distance(const double* P, int32_t nP, const double* Q, int32_t nQ, int32_t d,
                                                 double tol, int32_t max_iter, double* mu, double* gamma,
                                                 double* dist) {
