@@ -39,6 +39,8 @@ MODE_PRACTICAL = "practical"
 MODE_THEORY = "theory"
 MODE_FIXED = "fixed"
 MODE_CERTIFIED = "certified"
+MODE_CORESET = "coreset"         # CERTIFIED with core-set certificates (points; beyond the paper)
+CORESET_FIRST = 256              # first core-set check at this many iterations of the search, then every doubling
 OUT_STUCK = "stuck"              # CERTIFIED mode: the certificate gap stopped shrinking (eta is halved)
 CERT_FIRST_CHECK = 1024          # CERTIFIED: first progress check of an alpha-FTP at eta = 1 (then 2x, 4x, ...)
 CERT_SHRINK = 0.8                # CERTIFIED: the FTP's own gap must shrink by this factor while t doubles
@@ -325,6 +327,15 @@ def ses_ftp(V, gamma, alpha, eta, rho, T, mode=MODE_FIXED, delta=1e-4, patience=
         ubar = rec["ubar_next"]
         t += 1
         if mode == MODE_CERTIFIED and t % cert["poll_every"] == 0:
+            cs = cert.get("coreset")
+            if cs is not None and cs["base"] + t >= cs["next"]:
+                # core-set bounds from the current mean: their ball joins the
+                # FTP's best, their dual value its lower bound
+                lb_c, ub_c, c_c = ses_coreset_bounds(V, ubar, tol=cert["eps"] / 10.0, rounds=4, eps=cert["eps"])
+                lb_best = max(lb_best, lb_c)
+                if ub_c < f_best:
+                    f_best, c_best = ub_c, c_c
+                cs["next"] *= 2
             if min(cert["ub"], f_best) <= (1.0 + cert["eps"]) * max(cert["lb"], lb_best):
                 outcome = OUT_CERTIFIED
                 break
@@ -370,10 +381,15 @@ def ses_solve(V, gamma=None, eps=1e-2, mode=MODE_PRACTICAL, max_iters=10**7,
     ub <= (1+eps) max(lb, L) or the budget is spent. Its step size is eta
     (default 1, the largest Theorem 1 allows). The search range (L, U) is then
     a certificate too and lower_bound reports max(lb, L).
+
+    CORESET mode (points only; with radii it is CERTIFIED) adds core-set
+    certificates: at the polls where the search's iteration count first
+    reaches 256, 512, 1024, ..., ses_coreset_bounds runs from the current
+    mean, its dual value joining the lower bounds and its ball the upper ones.
     """
-    if mode == MODE_CERTIFIED:
+    if mode in (MODE_CERTIFIED, MODE_CORESET):
         return _ses_solve_certified(V, gamma, eps, max_iters, max_steps, 1.0 if eta is None else float(eta),
-                                    poll_every)
+                                    poll_every, coreset=mode == MODE_CORESET and gamma is None)
     V, gm = _prep(V, gamma)
     n = V.shape[0]
     D = ses_D(V, gm)
@@ -409,7 +425,7 @@ def ses_solve(V, gamma=None, eps=1e-2, mode=MODE_PRACTICAL, max_iters=10**7,
             "iters": total, "steps": steps, "L": L, "U": U}
 
 
-def _ses_solve_certified(V, gamma, eps, max_iters, max_steps, eta, poll_every):
+def _ses_solve_certified(V, gamma, eps, max_iters, max_steps, eta, poll_every, coreset=False):
     V, gm = _prep(V, gamma)
     n = V.shape[0]
     D = ses_D(V, gm)
@@ -420,9 +436,13 @@ def _ses_solve_certified(V, gamma, eps, max_iters, max_steps, eta, poll_every):
     if D == 0.0:
         return {"radius": ub, "center": center, "lower_bound": ub, "upper_bound": ub,
                 "iters": 0, "steps": steps, "L": 0.0, "U": 0.0}
+    cs = {"next": CORESET_FIRST, "base": 0} if coreset else None
     while ub > (1.0 + eps) * max(lb, L) and total < max_iters and len(steps) < max_steps:
         alpha = L + (U - L) / 3.0
         cert = {"lb": max(lb, L), "ub": ub, "eps": eps, "poll_every": poll_every}
+        if cs is not None:
+            cs["base"] = total
+            cert["coreset"] = cs
         res = ses_ftp(V, gm, alpha, eta, rho, max_iters - total, mode=MODE_CERTIFIED, cert=cert)
         total += res["iters"]
         eta_used = eta
@@ -507,12 +527,23 @@ def meb_dual_fw(P, tol, max_iter=200_000):
     return mu, c, math.sqrt(phi), far
 
 
-def ses_coreset_bounds(V, c, K=CORESET_K_SES, tol=1e-4):
+def ses_coreset_bounds(V, c, K=CORESET_K_SES, tol=1e-4, rounds=1, eps=None):
     """Core-set bounds from centre c: (lb, ub, centre) with lb = sqrt(phi(mu))
     for the weights of meb_dual_fw on the K points farthest from c (a lower
     bound on OPT) and ub = max_i |v_i - c_mu| over every point, the radius of
-    an actual enclosing ball at c_mu (an upper bound)."""
-    idx = ses_coreset_pick(V, c, K)
-    mu, cm, lb, _ = meb_dual_fw(V[idx], tol)
-    ub = math.sqrt(float(((V - cm) ** 2).sum(axis=1).max()))
-    return lb, ub, cm
+    an actual enclosing ball at c_mu (an upper bound). With rounds > 1 the K
+    points farthest from each new centre join the core set for up to that
+    many rounds, until ub <= (1 + eps) lb; the best bounds are returned."""
+    core = np.zeros(0, dtype=np.int64)
+    lb, ub, best_c = 0.0, math.inf, np.asarray(c, dtype=np.float64).copy()
+    for _ in range(rounds):
+        core = np.union1d(core, ses_coreset_pick(V, c, K))
+        _, cm, lb_r, _ = meb_dual_fw(V[core], tol)
+        lb = max(lb, lb_r)
+        ub_r = math.sqrt(float(((V - cm) ** 2).sum(axis=1).max()))
+        if ub_r < ub:
+            ub, best_c = ub_r, cm
+        c = cm
+        if eps is not None and ub <= (1.0 + eps) * lb:
+            break
+    return lb, ub, best_c

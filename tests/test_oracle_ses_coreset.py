@@ -59,3 +59,30 @@ def test_pick_is_the_farthest():
     d = np.linalg.norm(V - c, axis=1)
     assert len(idx) == 20 and np.all(np.diff(idx) > 0)
     assert d[idx].min() >= np.sort(d)[-20]
+
+
+def test_rounds_only_tighten():
+    rng = np.random.default_rng(9)
+    V = rng.normal(size=(2000, 6))
+    c = V[0] + 0.3
+    lb1, ub1, _ = oses.ses_coreset_bounds(V, c, K=16, tol=1e-6)
+    lb4, ub4, _ = oses.ses_coreset_bounds(V, c, K=16, tol=1e-6, rounds=4)
+    opt_lb, opt_ub, _ = oses.ses_coreset_bounds(V, V.mean(0), K=2000, tol=1e-9)
+    assert lb4 >= lb1 * (1 - 1e-12) and ub4 <= ub1 * (1 + 1e-12)
+    assert lb4 <= opt_ub * (1 + 1e-12) and ub4 >= opt_lb * (1 - 1e-12)
+
+
+@pytest.mark.parametrize("n,seed", [(400, 0), (1500, 1)])
+def test_coreset_search_brackets_welzl(n, seed):
+    """The search in CORESET mode (points in the plane, eps = 1e-3) brackets
+    Welzl's radius, closes within eps, returns an enclosing ball, and needs
+    no more iterations than the MWU-only CERTIFIED search."""
+    rng = np.random.default_rng(seed)
+    V = rng.random((n, 2))
+    opt = exact.mec_2d(V)[1]
+    res = oses.ses_solve(V, eps=1e-3, mode=oses.MODE_CORESET, max_iters=20_000)
+    assert res["lower_bound"] <= opt * (1 + 1e-12) and res["upper_bound"] >= opt * (1 - 1e-12), (res, opt)
+    assert res["upper_bound"] <= (1 + 1e-3) * res["lower_bound"]
+    assert float(np.linalg.norm(V - res["center"], axis=1).max()) <= res["upper_bound"] * (1 + 1e-12)
+    plain = oses.ses_solve(V, eps=1e-3, mode=oses.MODE_CERTIFIED, max_iters=20_000)
+    assert res["iters"] <= plain["iters"]
